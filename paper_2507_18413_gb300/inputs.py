@@ -1,0 +1,268 @@
+"""Seeded synthetic inputs for table constraints (shared by tests, bench and smoke).
+
+This module holds random-number generation and the shapes of the synthetic
+workloads only: tuple lists, scopes and domain-reduction edits. It contains no
+part of the propagation arithmetic (no supports, no currTable, no filtering),
+so both the CPU oracle and the CUDA path can be fed from it without sharing
+any of the method's code.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used in its counter form:
+output i of stream ``seed`` is ``mix(seed + i * 0x9E3779B97F4A7C15)``.
+
+The workloads stand in for the paper's instance sets (Sec. 5.1: LIN_B, LIN_EB,
+the Gecode set and Orienteering), whose files are not available; their shapes
+(arity, domain sizes, tuple counts) follow the synthetic configurations listed
+in the project's design notes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, start: int, n: int) -> np.ndarray:
+    """Outputs ``start+1 .. start+n`` of the SplitMix64 stream ``seed`` (uint64)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+class Rng:
+    """Sequential view of one SplitMix64 stream."""
+
+    def __init__(self, seed: int):
+        self.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        self.pos = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        out = splitmix64(self.seed, self.pos, n)
+        self.pos += n
+        return out
+
+    def below(self, n: int, hi) -> np.ndarray:
+        """n integers uniform in [0, hi) (hi may be an array); modulo bias < 2^-40 for hi < 2^24."""
+        hi = np.asarray(hi, dtype=np.uint64)
+        return (self.u64(n) % hi).astype(np.int64)
+
+    def uniform(self, n: int) -> np.ndarray:
+        """n doubles uniform in [0, 1) from the top 53 bits."""
+        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+    def int(self, hi: int) -> int:
+        return int(self.below(1, hi)[0])
+
+    def choice(self, seq):
+        return seq[self.int(len(seq))]
+
+
+def derive_seed(*parts: int) -> int:
+    """A child seed from a tuple of integers (first output of a stream keyed by them)."""
+    s = 0x5EED
+    for p in parts:
+        s = int(splitmix64((s ^ (int(p) & 0xFFFFFFFFFFFFFFFF)), 0, 1)[0])
+    return s
+
+
+# --------------------------------------------------------------------------
+# tuple lists
+# --------------------------------------------------------------------------
+
+def _decode(codes: np.ndarray, dom_lo, dom_size) -> np.ndarray:
+    """Mixed-radix decode of tuple codes into int32 columns (column 0 least significant)."""
+    arity = len(dom_size)
+    out = np.empty((codes.shape[0], arity), dtype=np.int32)
+    c = codes.copy()
+    for i in range(arity):
+        d = np.uint64(dom_size[i])
+        out[:, i] = (c % d).astype(np.int64) + int(dom_lo[i])
+        c //= d
+    return out
+
+
+def distinct_uniform_tuples(seed: int, dom_lo, dom_size, t: int) -> np.ndarray:
+    """``t`` distinct tuples drawn uniformly from the product of the domains, in draw order.
+
+    Raises if ``t`` exceeds the number of distinct tuples; callers that may ask for
+    more (tiny domains) cap ``t`` first with :func:`cap_distinct`.
+    """
+    space = 1
+    for d in dom_size:
+        space *= int(d)
+    if t > space:
+        raise ValueError(f"cannot draw {t} distinct tuples from a space of {space}")
+    if space >= 2 ** 63:
+        raise ValueError("tuple space too large for 64-bit codes")
+    rng = Rng(seed)
+    got = np.empty(0, dtype=np.uint64)
+    order = np.empty(0, dtype=np.int64)
+    drawn = 0
+    while got.shape[0] < t:
+        need = t - got.shape[0]
+        batch = int(need * 1.25) + 64
+        codes = rng.u64(batch) % np.uint64(space)
+        allc = np.concatenate([got, codes])
+        allo = np.concatenate([order, np.arange(drawn, drawn + batch, dtype=np.int64)])
+        drawn += batch
+        _, first = np.unique(allc, return_index=True)
+        first.sort()
+        got = allc[first][:t]
+        order = allo[first][:t]
+    return _decode(got, dom_lo, dom_size)
+
+
+def cap_distinct(dom_size, t: int) -> int:
+    """Tuple count capped at half the product of the domain sizes (distinct draws must end)."""
+    space = math.prod(int(d) for d in dom_size)
+    return int(min(t, max(1, space // 2)))
+
+
+def zipf_tuples(seed: int, dom_lo, dom_size, t: int, s: float = 1.2) -> np.ndarray:
+    """``t`` tuples (duplicates allowed) whose columns are independent Zipf(s) draws.
+
+    Value rank k (0-based) of column i has probability proportional to (k+1)^-s; the
+    rank is mapped to the value ``dom_lo[i] + perm_i[k]`` with a seeded permutation so
+    that the heavy values are not always the smallest ones.
+    """
+    rng = Rng(seed)
+    arity = len(dom_size)
+    out = np.empty((t, arity), dtype=np.int32)
+    for i in range(arity):
+        d = int(dom_size[i])
+        w = 1.0 / np.power(np.arange(1, d + 1, dtype=np.float64), s)
+        cdf = np.cumsum(w)
+        cdf /= cdf[-1]
+        u = rng.uniform(t)
+        rank = np.minimum(np.searchsorted(cdf, u, side="right"), d - 1)
+        perm = np.argsort(rng.u64(d), kind="stable")
+        out[:, i] = perm[rank].astype(np.int64) + int(dom_lo[i])
+    return out
+
+
+def random_scope(rng: Rng, nvars: int, arity: int) -> list:
+    """``arity`` distinct variable indices in [0, nvars), in draw order."""
+    picked = []
+    while len(picked) < arity:
+        v = rng.int(nvars)
+        if v not in picked:
+            picked.append(v)
+    return picked
+
+
+# --------------------------------------------------------------------------
+# domain-reduction streams (what a search would do between propagations)
+# --------------------------------------------------------------------------
+
+def present_values(mask: np.ndarray) -> np.ndarray:
+    return np.flatnonzero(mask)
+
+
+def remove_random_values(rng: Rng, masks: list, k: int, min_left: int = 1):
+    """Remove up to ``k`` present values, each from a random variable with more than
+    ``min_left`` values left. Returns the new masks (copies) and the number removed."""
+    masks = [m.copy() for m in masks]
+    removed = 0
+    for _ in range(k):
+        cand = [i for i, m in enumerate(masks) if int(m.sum()) > min_left]
+        if not cand:
+            break
+        i = cand[rng.int(len(cand))]
+        vals = present_values(masks[i])
+        a = int(vals[rng.int(len(vals))])
+        masks[i][a] = False
+        removed += 1
+    return masks, removed
+
+
+def delta_step(rng: Rng, masks: list):
+    """Remove 1-2 values of one variable that has at least 3 values (a delta-path edit)."""
+    masks = [m.copy() for m in masks]
+    cand = [i for i, m in enumerate(masks) if int(m.sum()) >= 3]
+    if not cand:
+        return masks, None
+    i = cand[rng.int(len(cand))]
+    vals = present_values(masks[i])
+    k = 1 + rng.int(2)
+    k = min(k, len(vals) - 1)
+    pick = rng.below(len(vals), 1 << 62)
+    order = np.argsort(pick, kind="stable")[:k]
+    masks[i][vals[order]] = False
+    return masks, i
+
+
+def reset_step(rng: Rng, masks: list):
+    """Remove more than half of one variable's values, leaving at least one (a reset-path edit).
+
+    The count removed is uniform in [ceil(|D|/2)+1, |D|-1] for a variable with |D| >= 4.
+    """
+    masks = [m.copy() for m in masks]
+    cand = [i for i, m in enumerate(masks) if int(m.sum()) >= 4]
+    if not cand:
+        return masks, None
+    i = cand[rng.int(len(cand))]
+    vals = present_values(masks[i])
+    n = len(vals)
+    lo = (n + 1) // 2 + 1
+    hi = n - 1
+    k = lo + rng.int(hi - lo + 1)
+    pick = rng.below(n, 1 << 62)
+    order = np.argsort(pick, kind="stable")[:k]
+    masks[i][vals[order]] = False
+    return masks, i
+
+
+# --------------------------------------------------------------------------
+# workload descriptions
+# --------------------------------------------------------------------------
+
+@dataclass
+class TableSpec:
+    scope: list
+    tuples: np.ndarray  # int32 [t, arity], actual values
+
+
+@dataclass
+class CspSpec:
+    nvars: int
+    dom_lo: list
+    dom_size: list
+    tables: list = field(default_factory=list)
+
+
+def tiny_table(seed: int = 1):
+    """Arity 3, domains {0..7}, 200 distinct uniform tuples."""
+    dom_lo, dom_size = [0, 0, 0], [8, 8, 8]
+    return dom_lo, dom_size, distinct_uniform_tuples(seed, dom_lo, dom_size, 200)
+
+
+def large_table(seed: int, t: int, arity: int = 6, d: int = 32):
+    """Arity 6, 32-value domains {0..31}, ``t`` distinct uniform tuples."""
+    dom_lo, dom_size = [0] * arity, [d] * arity
+    return dom_lo, dom_size, distinct_uniform_tuples(seed, dom_lo, dom_size, t)
+
+
+def random_csp(seed: int, nvars: int, ntables: int, arity: int, d: int, t: int,
+               dist: str = "uniform") -> CspSpec:
+    """``ntables`` tables of ``arity`` over random distinct-within-table scopes of ``nvars``
+    variables with domains {0..d-1}; ``t`` tuples each (distinct uniform or Zipf)."""
+    rng = Rng(seed)
+    csp = CspSpec(nvars=nvars, dom_lo=[0] * nvars, dom_size=[d] * nvars)
+    for k in range(ntables):
+        scope = random_scope(rng, nvars, arity)
+        ts = derive_seed(seed, k)
+        if dist == "uniform":
+            tt = cap_distinct([d] * arity, t)
+            tup = distinct_uniform_tuples(ts, [0] * arity, [d] * arity, tt)
+        else:
+            tup = zipf_tuples(ts, [0] * arity, [d] * arity, t)
+        csp.tables.append(TableSpec(scope=scope, tuples=tup))
+    return csp
