@@ -1,0 +1,247 @@
+/*
+ * ct.h -- C ABI of the GB300 Compact-Table propagation library (libct.so).
+ *
+ * The library propagates table constraints with the Compact-Table (CT)
+ * algorithm of "GPU Accelerated Compact-Table Propagation" (Santi, Tardivo,
+ * Dovier, Formisano, 2025): Algorithm 1 (enforceGAC), Algorithm 2
+ * (updateTable, with both the delta and the reset mask) and Algorithm 3
+ * (filterDomains, with residues), run as CUDA kernels on one GPU with all
+ * table state resident in device memory. A table constraint, its currTable
+ * and its supports bitsets are defined in Sec. 2 (Table 1); the serial data
+ * structures (_supports, _supportJmp, _variablesOffsets, 32-bit words) in
+ * Sec. 3; the GPU propagators that this design generalises in Sec. 4.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value: CT_OK (0), CT_INFEASIBLE (1, the constraint or the network has
+ *   no solution under the given domains -- a CSP failure in the sense of
+ *   Algorithm 1, not an error) or a negative CT_ERR_* code. After an error,
+ *   ct_last_error() returns a message for the calling thread.
+ * Domains: the domain of a variable with initial range
+ *   [dom_lo, dom_lo + dom_size) is a bitset of ceil(dom_size / 32) uint32
+ *   words; value v is bit (v - dom_lo) % 32 of word (v - dom_lo) / 32 (least
+ *   significant bit first). Bits at or above dom_size must be zero. The
+ *   domains of a table's scope are stored back to back in scope order.
+ * Words: currTable and the supports rows are 32-bit words (Sec. 3), tuple j
+ *   at bit j % 32 of word j / 32, where j counts the retained tuples (tuples
+ *   with every value inside the initial domains, in input order; duplicates
+ *   are kept).
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ *   it keeps (tuples, scopes, domains) during the call. Handles belong to the
+ *   caller until the matching destroy call.
+ * Streams and threads: every handle runs its work on one CUDA stream (the
+ *   stream given at creation, or a stream the library creates). A handle must
+ *   not be used from two host threads at once; distinct handles may.
+ * Device pointers: arguments documented as "device" must point to memory of
+ *   the current CUDA device that the handle's stream can access.
+ */
+#ifndef CT_H
+#define CT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CT_OK 0
+#define CT_INFEASIBLE 1
+#define CT_ERR_ARG (-1)     /* invalid argument (null pointer, bad size, duplicate scope variable) */
+#define CT_ERR_OOM (-2)     /* host or device allocation failed */
+#define CT_ERR_CUDA (-3)    /* a CUDA call failed; see ct_last_error() */
+#define CT_ERR_STATE (-4)   /* domains grew without a restore, or use after a failure without restore */
+#define CT_ERR_TIMEOUT (-5) /* a bounded device-side wait ran out */
+#define CT_ERR_LEVEL (-6)   /* restore to a level that is not on the stack */
+
+typedef struct ct_table ct_table;
+typedef struct ct_model ct_model;
+
+/* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
+typedef struct ct_options {
+    int32_t entries_per_lane; /* 0 = auto; 1, 2 or 4 currTable chunks per lane of a segment warp */
+    int32_t warps_per_block;  /* 0 = auto (4); 1..16 */
+    int32_t no_residues;      /* 1 = skip the residue probe and scan for every value */
+    int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
+    int32_t reserved[4];
+} ct_options;
+
+/* Static shape and live state of a table (ct_get_info). */
+typedef struct ct_table_info {
+    int32_t arity;
+    int32_t rows;          /* supports rows = sum of the initial domain sizes (_supportSize, Sec. 3) */
+    int64_t tuples;        /* retained tuples t */
+    int64_t words;         /* ceil(t / 32) 32-bit currTable words (_currTableSize, Sec. 3) */
+    int64_t chunks;        /* ceil(words / 4): 128-bit units of the sparse index */
+    int32_t segments;      /* index segments (one warp each) */
+    int32_t seg_capacity;  /* chunks per segment */
+    int64_t live_chunks;   /* chunks currently in the non-zero index */
+    int64_t trail_size;    /* trail entries in use */
+    int32_t depth;         /* saved levels on the stack */
+    int32_t entries_per_lane;
+    int64_t device_bytes;  /* device memory held by the table */
+} ct_table_info;
+
+/* Figures of the last ct_propagate call (ct_get_call_stats). */
+typedef struct ct_call_stats {
+    int32_t status;
+    int32_t changed_vars;   /* |s_val|: scope variables whose domain shrank since the last call */
+    int32_t delta_vars;     /* of those, masked with the removed values (|Delta| < |dom|) */
+    int32_t reset_vars;     /* of those, masked with the remaining values */
+    int32_t rows_ored;      /* supports rows OR-ed by updateTable (sum of k_i) */
+    int32_t sup_vars;       /* |s_sup|: scope variables with more than one value */
+    int32_t residue_hits;   /* values found supported by their residue word */
+    int32_t residue_misses; /* values that needed a scan of the index */
+    int32_t pruned;         /* values removed by filterDomains */
+    int32_t trail_added;    /* trail entries appended */
+    int64_t live_chunks_in;  /* non-zero index size at entry (128-bit chunks) */
+    int64_t live_chunks_out; /* ... and at exit */
+    int64_t live_words_in;   /* non-zero 32-bit currTable words at entry (N) */
+} ct_call_stats;
+
+/* Accumulated kernel times (ct_options.profile = 1). */
+typedef struct ct_profile {
+    int64_t calls;
+    double plan_ms;   /* change detection: Delta, s_val, s_sup, row plan (Algorithm 1 lines 1-3) */
+    double update_ms; /* updateTable (Algorithm 2) + residue probes */
+    double scan_ms;   /* index scans of missed values + domain write-back (Algorithm 3) */
+    int64_t update_bytes; /* algorithmic bytes of updateTable: 4 * N * (rows_ored + 2), summed */
+} ct_profile;
+
+/* ---------------------------------------------------------------- table --
+ * ct_create: build a table constraint (Sec. 2; constructor of class Table,
+ * Sec. 3, and its device copy, Sec. 4).
+ *   arity      number of scope variables (1 .. 2048)
+ *   dom_lo     host int32[arity]: first value of each initial domain
+ *              (_variablesOffsets, Sec. 3)
+ *   dom_size   host int32[arity]: initial domain sizes (1 .. 65536)
+ *   tuples     host int32[t * arity], row-major: tuple j is
+ *              tuples[j*arity .. j*arity+arity-1]; may be NULL when t == 0
+ *   t          number of input tuples (>= 0)
+ *   opt        tuning knobs or NULL
+ *   cuda_stream cudaStream_t to run on, or NULL for a stream owned by the table
+ *   out        receives the handle (also on CT_INFEASIBLE)
+ * Tuples with a value outside the initial domains are dropped. Returns
+ * CT_INFEASIBLE when no tuple is left (the constructor's unsatisfiability
+ * check, Sec. 3); the handle is still valid and every propagation of it
+ * fails. The first ct_propagate starts from the initial domains, so values
+ * already removed by the caller count as removed since the last call.
+ */
+int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size,
+              const int32_t* tuples, int64_t t, const ct_options* opt,
+              void* cuda_stream, ct_table** out);
+
+/* ct_propagate: enforce GAC on the table (Algorithm 1: change detection,
+ * updateTable of Algorithm 2, failure test, filterDomains of Algorithm 3).
+ *   dom_bits      device uint32, in/out: the scope domains (layout above).
+ *                 They must be subsets of the domains at the end of the
+ *                 previous call (or at the restored level); otherwise
+ *                 CT_ERR_STATE. On CT_OK the unsupported values are cleared.
+ *   changed_vars  host uint32[ceil(arity/32)] or NULL: bit i set iff the call
+ *                 removed a value of scope variable i.
+ * Blocks until the result is known (one small device-to-host copy). On
+ * CT_INFEASIBLE the domain contents are unspecified and the table must be
+ * restored (ct_restore) before it is propagated again.
+ */
+int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_vars);
+
+/* ct_propagate_host: as ct_propagate, with dom_bits in host memory; the
+ * domains are copied to the device and the filtered domains back. */
+int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t* changed_vars);
+
+/* ct_save: push a backtrack level (the trail of Sec. 4: MiniCP alternates
+ * search and propagation with backtracking). *level_out receives the level
+ * number (the stack depth before the push, starting at 0). */
+int ct_save(ct_table* ct, int* level_out);
+
+/* ct_restore: return currTable, its non-zero index and the last-seen domains
+ * to their state at ct_save(level), and drop that level and every level
+ * above it (depth becomes `level`). CT_ERR_LEVEL if level is not in
+ * [0, depth). Residues are hints and are not restored. */
+int ct_restore(ct_table* ct, int level);
+
+/* ct_get_currtable: copy currTable (Sec. 2, Table 1(c)) to the host.
+ *   words_host          host uint32[ceil(t/32)] or NULL
+ *   nonzero_words_out   host or NULL: number of non-zero 32-bit words */
+int ct_get_currtable(ct_table* ct, uint32_t* words_host, int64_t* nonzero_words_out);
+
+/* ct_get_support_row: copy supports row `row` (Sec. 2, Table 1(b); row of
+ * value v of scope variable i = sum of the first i domain sizes + v - dom_lo[i],
+ * _supportJmp of Sec. 3) to host uint32[ceil(t/32)]. */
+int ct_get_support_row(ct_table* ct, int row, uint32_t* words_host);
+
+/* ct_get_index: copy the non-zero index (128-bit chunk numbers, each live
+ * chunk exactly once, in no particular order) to host int32[live_chunks];
+ * *count_out receives live_chunks. index_host may be NULL. */
+int ct_get_index(ct_table* ct, int32_t* index_host, int64_t* count_out);
+
+int ct_get_info(ct_table* ct, ct_table_info* info);
+int ct_get_call_stats(ct_table* ct, ct_call_stats* stats);
+int ct_get_profile(ct_table* ct, ct_profile* prof);
+int ct_reset_profile(ct_table* ct);
+
+/* ct_destroy: free the table (NULL is accepted). */
+int ct_destroy(ct_table* ct);
+
+/* ---------------------------------------------------------------- model --
+ * A model is a set of integer variables and table constraints over them,
+ * propagated to a common fixpoint (Sec. 2: propagation removes unsupported
+ * values until GAC holds everywhere or a failure is found) and searched
+ * depth-first (Sec. 4). Domains of all variables live on the device in the
+ * layout above, variable after variable.
+ */
+typedef struct ct_search_stats {
+    int64_t nodes;        /* fixpoints computed on search nodes, root and failed nodes included */
+    int64_t fails;        /* nodes whose fixpoint failed */
+    int64_t solutions;    /* nodes where every variable is fixed after propagation */
+    int64_t propagations; /* table propagations (ct_propagate-equivalent calls) */
+    int32_t max_depth;
+    int32_t complete;     /* 1 if the tree was exhausted or the first solution found as asked */
+    double seconds;
+} ct_search_stats;
+
+/* ct_model_create: nvars variables with initial ranges [dom_lo[v], dom_lo[v] + dom_size[v]). */
+int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* dom_size,
+                    const ct_options* opt, void* cuda_stream, ct_model** out);
+
+/* ct_model_add_table: add a table over `scope` (host int32[arity] of distinct
+ * variable indices); tuples as in ct_create. CT_INFEASIBLE if no tuple fits
+ * the initial domains (the model then has no solution). */
+int ct_model_add_table(ct_model* m, const int32_t* scope, int arity,
+                       const int32_t* tuples, int64_t t);
+
+/* ct_model_propagate: run table propagations until no domain changes
+ * (fixpoint) or a table fails (CT_INFEASIBLE). */
+int ct_model_propagate(ct_model* m);
+
+/* ct_model_get_domains / ct_model_set_domains: host copies of all domains
+ * (sum over variables of ceil(dom_size/32) words). Set domains must be
+ * subsets of the current ones. */
+int ct_model_get_domains(ct_model* m, uint32_t* words_host);
+int ct_model_set_domains(ct_model* m, const uint32_t* words_host);
+
+int ct_model_save(ct_model* m, int* level_out);
+int ct_model_restore(ct_model* m, int level);
+
+/* ct_search_dfs: depth-first search with first-fail binary branching: the
+ * unfixed variable with the smallest domain (ties: lowest index); left branch
+ * x = min(dom x), right branch x != min(dom x). Propagates at every node.
+ *   node_limit      stop after this many nodes (<= 0: no limit)
+ *   count_all       0: stop at the first solution; 1: count all solutions
+ *   out             host, receives the counters
+ *   first_solution  host int32[nvars] or NULL: values of the first solution
+ * Returns CT_OK whether or not a solution exists; the model's domains are
+ * back at their state before the call. */
+int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all,
+                  ct_search_stats* out, int32_t* first_solution);
+
+int ct_model_destroy(ct_model* m);
+
+/* ---------------------------------------------------------------- misc -- */
+const char* ct_last_error(void);
+const char* ct_status_string(int status);
+int ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CT_H */

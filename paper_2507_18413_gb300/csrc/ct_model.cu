@@ -1,0 +1,452 @@
+// ct_model.cu -- networks of table constraints: propagation to a common
+// fixpoint and depth-first search (Sec. 4: the solver alternates search and
+// propagation, backtracking through the trail; Sec. 2: propagation removes
+// unsupported values until GAC holds or a failure is found).
+//
+// All domains live in one device array; every table reads and prunes its
+// scope variables in place. The fixpoint queue runs on the host: after each
+// table propagation the host learns which scope variables changed (from the
+// 16-byte status header plus the changed mask copied back by the table) and
+// schedules the other tables that share them. One table pass is GAC for that
+// table, so a table is not re-queued by its own pruning.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+using namespace ctk;
+
+struct ct_model {
+    int nvars = 0;
+    std::vector<int32_t> lo, size, nw, off;
+    int DWg = 0;
+    uint32_t* d_dom = nullptr;
+    std::vector<uint32_t> h_dom;
+    std::vector<ct_table*> tables;
+    std::vector<std::vector<int>> scopes;
+    std::vector<int32_t*> d_tabOff;
+    std::vector<std::vector<int>> varTables;
+    std::vector<char> dirty;
+    struct Level {
+        std::vector<uint32_t> dom;
+        std::vector<char> dirty;
+    };
+    std::vector<Level> levels;
+    uint32_t* d_levelDom = nullptr;
+    int levelCap = 0;
+    cudaStream_t stream = nullptr;
+    bool ownStream = false;
+    ct_options opt{};
+    bool staticInfeasible = false;
+    bool failed = false;
+    int64_t propagations = 0;
+};
+
+namespace {
+
+int popcount_var(const ct_model* m, int v) {
+    int s = 0;
+    for (int q = 0; q < m->nw[v]; ++q) s += __builtin_popcount(m->h_dom[(size_t)m->off[v] + q]);
+    return s;
+}
+
+int ensure_model_levels(ct_model* m, int need) {
+    if (need <= m->levelCap) return CT_OK;
+    const int cap = std::max(need, std::max(8, 2 * m->levelCap));
+    uint32_t* nd = nullptr;
+    cudaError_t e = cudaMalloc(&nd, (size_t)cap * std::max(m->DWg, 1) * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("model level stack: %s", cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    const int used = (int)m->levels.size();
+    if (used > 0)
+        CT_CUDA(cudaMemcpyAsync(nd, m->d_levelDom, (size_t)used * m->DWg * sizeof(uint32_t),
+                                cudaMemcpyDeviceToDevice, m->stream));
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    if (m->d_levelDom) cudaFree(m->d_levelDom);
+    m->d_levelDom = nd;
+    m->levelCap = cap;
+    return CT_OK;
+}
+
+void mark_var(ct_model* m, int v, int except, std::deque<int>* q) {
+    for (int T : m->varTables[v]) {
+        if (T == except || m->dirty[T]) continue;
+        m->dirty[T] = 1;
+        if (q) q->push_back(T);
+    }
+}
+
+// Replace the domain of variable v (host mirror and device), scheduling its tables.
+int set_var(ct_model* m, int v, const uint32_t* words) {
+    std::memcpy(m->h_dom.data() + m->off[v], words, (size_t)m->nw[v] * sizeof(uint32_t));
+    CT_CUDA(launch_set_words(m->d_dom + m->off[v], words, m->nw[v], m->stream));
+    mark_var(m, v, -1, nullptr);
+    return CT_OK;
+}
+
+}  // namespace
+
+extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* dom_size, const ct_options* opt,
+                               void* cuda_stream, ct_model** out) {
+    if (!out || nvars < 1 || !dom_lo || !dom_size) {
+        ct_set_error("ct_model_create: bad argument");
+        return CT_ERR_ARG;
+    }
+    *out = nullptr;
+    for (int v = 0; v < nvars; ++v) {
+        if (dom_size[v] < 1 || dom_size[v] > kMaxDomSize) {
+            ct_set_error("ct_model_create: dom_size[%d] = %d out of range", v, dom_size[v]);
+            return CT_ERR_ARG;
+        }
+    }
+    ct_model* m = new (std::nothrow) ct_model();
+    if (!m) return CT_ERR_OOM;
+    m->nvars = nvars;
+    m->lo.assign(dom_lo, dom_lo + nvars);
+    m->size.assign(dom_size, dom_size + nvars);
+    m->nw.resize(nvars);
+    m->off.resize(nvars);
+    for (int v = 0; v < nvars; ++v) {
+        m->nw[v] = (m->size[v] + 31) / 32;
+        m->off[v] = m->DWg;
+        m->DWg += m->nw[v];
+    }
+    m->varTables.resize(nvars);
+    m->h_dom.assign(m->DWg, 0u);
+    for (int v = 0; v < nvars; ++v)
+        for (int a = 0; a < m->size[v]; ++a) m->h_dom[(size_t)m->off[v] + a / 32] |= 1u << (a % 32);
+    if (opt) m->opt = *opt;
+    cudaError_t e;
+    if (cuda_stream) {
+        m->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete m;
+            return ct_cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        m->ownStream = true;
+    }
+    e = cudaMalloc(&m->d_dom, (size_t)m->DWg * sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_dom, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        const int st = ct_cuda_fail(e, "model domain array");
+        ct_model_destroy(m);
+        return st;
+    }
+    *out = m;
+    return CT_OK;
+}
+
+extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t) {
+    if (!m || !scope || arity < 1 || arity > kMaxArity) {
+        ct_set_error("ct_model_add_table: bad argument");
+        return CT_ERR_ARG;
+    }
+    if (!m->levels.empty()) {
+        ct_set_error("ct_model_add_table: tables must be added before the first save");
+        return CT_ERR_STATE;
+    }
+    std::vector<int> sc(scope, scope + arity);
+    std::vector<char> seen(m->nvars, 0);
+    for (int v : sc) {
+        if (v < 0 || v >= m->nvars || seen[v]) {
+            ct_set_error("ct_model_add_table: scope variable %d out of range or repeated", v);
+            return CT_ERR_ARG;
+        }
+        seen[v] = 1;
+    }
+    std::vector<int32_t> lo(arity), sz(arity), offs(arity);
+    for (int k = 0; k < arity; ++k) {
+        lo[k] = m->lo[sc[k]];
+        sz[k] = m->size[sc[k]];
+        offs[k] = m->off[sc[k]];
+    }
+    ct_table* tab = nullptr;
+    const int st = ct_create(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab);
+    if (st < 0) return st;
+    int32_t* d_off = nullptr;
+    cudaError_t e = cudaMalloc(&d_off, (size_t)arity * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off, offs.data(), (size_t)arity * sizeof(int32_t), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        if (d_off) cudaFree(d_off);
+        ct_destroy(tab);
+        return ct_cuda_fail(e, "ct_model_add_table offsets");
+    }
+    const int T = (int)m->tables.size();
+    m->tables.push_back(tab);
+    m->scopes.push_back(sc);
+    m->d_tabOff.push_back(d_off);
+    m->dirty.push_back(1);
+    for (int v : sc) m->varTables[v].push_back(T);
+    if (st == CT_INFEASIBLE) m->staticInfeasible = true;
+    return st;
+}
+
+extern "C" int ct_model_propagate(ct_model* m) {
+    if (!m) {
+        ct_set_error("ct_model_propagate: null handle");
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_model_propagate: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    if (m->staticInfeasible) {
+        m->failed = true;
+        return CT_INFEASIBLE;
+    }
+    for (int v = 0; v < m->nvars; ++v) {
+        if (popcount_var(m, v) == 0) {
+            m->failed = true;
+            return CT_INFEASIBLE;
+        }
+    }
+    std::deque<int> q;
+    for (int T = 0; T < (int)m->tables.size(); ++T)
+        if (m->dirty[T]) q.push_back(T);
+    std::vector<uint32_t> changed;
+    while (!q.empty()) {
+        const int T = q.front();
+        q.pop_front();
+        m->dirty[T] = 0;
+        ct_table* tab = m->tables[T];
+        changed.assign((size_t)ct_table_changed_words(tab), 0u);
+        const int st = ct_table_propagate_on(tab, m->d_dom, m->d_tabOff[T], changed.data());
+        m->propagations += 1;
+        if (st == CT_INFEASIBLE) {
+            m->failed = true;
+            return CT_INFEASIBLE;
+        }
+        if (st < 0) return st;
+        const int32_t* h = ct_table_status_host(tab);
+        const uint32_t* newDom = reinterpret_cast<const uint32_t*>(h + kStatusHdr + ct_table_changed_words(tab));
+        const int32_t* ld = ct_table_var_ld(tab);
+        const std::vector<int>& sc = m->scopes[T];
+        for (int k = 0; k < (int)sc.size(); ++k) {
+            if (!((changed[k >> 5] >> (k & 31)) & 1u)) continue;
+            const int v = sc[k];
+            std::memcpy(m->h_dom.data() + m->off[v], newDom + ld[k], (size_t)m->nw[v] * sizeof(uint32_t));
+            mark_var(m, v, T, &q);
+        }
+    }
+    return CT_OK;
+}
+
+extern "C" int ct_model_get_domains(ct_model* m, uint32_t* words_host) {
+    if (!m || !words_host) {
+        ct_set_error("ct_model_get_domains: null argument");
+        return CT_ERR_ARG;
+    }
+    std::memcpy(words_host, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t));
+    return CT_OK;
+}
+
+extern "C" int ct_model_set_domains(ct_model* m, const uint32_t* words_host) {
+    if (!m || !words_host) {
+        ct_set_error("ct_model_set_domains: null argument");
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_model_set_domains: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    for (int q = 0; q < m->DWg; ++q) {
+        if (words_host[q] & ~m->h_dom[q]) {
+            ct_set_error("ct_model_set_domains: domains may only shrink");
+            return CT_ERR_STATE;
+        }
+    }
+    for (int v = 0; v < m->nvars; ++v) {
+        bool diff = false;
+        for (int q = 0; q < m->nw[v]; ++q) diff |= words_host[m->off[v] + q] != m->h_dom[(size_t)m->off[v] + q];
+        if (!diff) continue;
+        const int st = set_var(m, v, words_host + m->off[v]);
+        if (st != CT_OK) return st;
+    }
+    return CT_OK;
+}
+
+extern "C" int ct_model_save(ct_model* m, int* level_out) {
+    if (!m) {
+        ct_set_error("ct_model_save: null handle");
+        return CT_ERR_ARG;
+    }
+    const int L = (int)m->levels.size();
+    int st;
+    if ((st = ensure_model_levels(m, L + 1)) != CT_OK) return st;
+    for (ct_table* tab : m->tables) {
+        int l = 0;
+        if ((st = ct_save(tab, &l)) != CT_OK) return st;
+    }
+    CT_CUDA(launch_copy_words(m->d_levelDom + (size_t)L * m->DWg, m->d_dom, m->DWg, m->stream));
+    ct_model::Level lev;
+    lev.dom = m->h_dom;
+    lev.dirty = m->dirty;
+    m->levels.push_back(std::move(lev));
+    if (level_out) *level_out = L;
+    return CT_OK;
+}
+
+extern "C" int ct_model_restore(ct_model* m, int level) {
+    if (!m) {
+        ct_set_error("ct_model_restore: null handle");
+        return CT_ERR_ARG;
+    }
+    if (level < 0 || level >= (int)m->levels.size()) {
+        ct_set_error("ct_model_restore: level %d not in [0, %d)", level, (int)m->levels.size());
+        return CT_ERR_LEVEL;
+    }
+    int st;
+    for (ct_table* tab : m->tables)
+        if ((st = ct_restore(tab, level)) != CT_OK) return st;
+    CT_CUDA(launch_copy_words(m->d_dom, m->d_levelDom + (size_t)level * m->DWg, m->DWg, m->stream));
+    m->h_dom = m->levels[level].dom;
+    m->dirty = m->levels[level].dirty;
+    m->levels.resize(level);
+    m->failed = false;
+    return CT_OK;
+}
+
+namespace {
+
+struct Dfs {
+    ct_model* m;
+    int64_t limit;
+    bool countAll;
+    ct_search_stats st{};
+    int32_t* firstSol;
+    bool haveFirst = false;
+    bool stop = false;
+    bool hitLimit = false;
+
+    // Returns CT_OK or a negative error.
+    int node(int depth) {
+        if (limit > 0 && st.nodes >= limit) {
+            stop = true;
+            hitLimit = true;
+            return CT_OK;
+        }
+        st.nodes += 1;
+        if (depth > st.max_depth) st.max_depth = depth;
+        const int r = ct_model_propagate(m);
+        if (r < 0) return r;
+        if (r == CT_INFEASIBLE) {
+            st.fails += 1;
+            return CT_OK;
+        }
+        // First-fail: smallest domain among unfixed variables, ties to the lowest index.
+        int x = -1, best = 0;
+        for (int v = 0; v < m->nvars; ++v) {
+            const int s = popcount_var(m, v);
+            if (s > 1 && (x < 0 || s < best)) {
+                x = v;
+                best = s;
+            }
+        }
+        if (x < 0) {
+            st.solutions += 1;
+            if (!haveFirst) {
+                haveFirst = true;
+                if (firstSol) {
+                    for (int v = 0; v < m->nvars; ++v) {
+                        int a = 0;
+                        for (int q = 0; q < m->nw[v]; ++q) {
+                            const uint32_t w = m->h_dom[(size_t)m->off[v] + q];
+                            if (w) {
+                                a = q * 32 + __builtin_ctz(w);
+                                break;
+                            }
+                        }
+                        firstSol[v] = m->lo[v] + a;
+                    }
+                }
+            }
+            if (!countAll) stop = true;
+            return CT_OK;
+        }
+        // Value: the minimum of dom(x).
+        const int nwx = m->nw[x];
+        std::vector<uint32_t> cur(m->h_dom.begin() + m->off[x], m->h_dom.begin() + m->off[x] + nwx);
+        int a = 0;
+        for (int q = 0; q < nwx; ++q) {
+            if (cur[q]) {
+                a = q * 32 + __builtin_ctz(cur[q]);
+                break;
+            }
+        }
+        std::vector<uint32_t> left(nwx, 0u), right(cur);
+        left[a >> 5] = 1u << (a & 31);
+        right[a >> 5] &= ~(1u << (a & 31));
+        for (int branch = 0; branch < 2; ++branch) {
+            int L = 0;
+            int rc = ct_model_save(m, &L);
+            if (rc != CT_OK) return rc;
+            rc = set_var(m, x, branch == 0 ? left.data() : right.data());
+            if (rc == CT_OK) rc = node(depth + 1);
+            const int rr = ct_model_restore(m, L);
+            if (rc != CT_OK) return rc;
+            if (rr != CT_OK) return rr;
+            if (stop) return CT_OK;
+        }
+        return CT_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_search_stats* out,
+                             int32_t* first_solution) {
+    if (!m || !out) {
+        ct_set_error("ct_search_dfs: null argument");
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_search_dfs: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t p0 = m->propagations;
+    Dfs d;
+    d.m = m;
+    d.limit = node_limit;
+    d.countAll = count_all != 0;
+    d.firstSol = first_solution;
+    int L0 = 0;
+    int st = ct_model_save(m, &L0);
+    if (st != CT_OK) return st;
+    st = d.node(0);
+    const int rr = ct_model_restore(m, L0);
+    if (st != CT_OK) return st;
+    if (rr != CT_OK) return rr;
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    d.st.complete = d.hitLimit ? 0 : 1;
+    d.st.propagations = m->propagations - p0;
+    d.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = d.st;
+    return CT_OK;
+}
+
+extern "C" int ct_model_destroy(ct_model* m) {
+    if (!m) return CT_OK;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (ct_table* t : m->tables) ct_destroy(t);
+    for (int32_t* p : m->d_tabOff) cudaFree(p);
+    if (m->d_dom) cudaFree(m->d_dom);
+    if (m->d_levelDom) cudaFree(m->d_levelDom);
+    if (m->ownStream && m->stream) cudaStreamDestroy(m->stream);
+    cudaGetLastError();
+    delete m;
+    return CT_OK;
+}

@@ -1,0 +1,677 @@
+// ct_table.cu -- host side of one table constraint: construction of the
+// device layout (Sec. 3 constructor, Sec. 4 device copies), propagation calls,
+// backtrack levels and inspection.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+using namespace ctk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+void ct_set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int ct_cuda_fail(cudaError_t e, const char* what) {
+    ct_set_error("%s: %s", what, cudaGetErrorString(e));
+    return CT_ERR_CUDA;
+}
+
+extern "C" const char* ct_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* ct_status_string(int s) {
+    switch (s) {
+        case CT_OK: return "CT_OK";
+        case CT_INFEASIBLE: return "CT_INFEASIBLE";
+        case CT_ERR_ARG: return "CT_ERR_ARG";
+        case CT_ERR_OOM: return "CT_ERR_OOM";
+        case CT_ERR_CUDA: return "CT_ERR_CUDA";
+        case CT_ERR_STATE: return "CT_ERR_STATE";
+        case CT_ERR_TIMEOUT: return "CT_ERR_TIMEOUT";
+        case CT_ERR_LEVEL: return "CT_ERR_LEVEL";
+        default: return "CT_UNKNOWN";
+    }
+}
+
+extern "C" int ct_version(void) { return 10000; }
+
+// ---------------------------------------------------------------------------
+// the table object
+// ---------------------------------------------------------------------------
+struct ct_table {
+    int arity = 0;
+    std::vector<int32_t> lo, size, nw, ld, row0, rowVar;
+    int R = 0;
+    int64_t t = 0, W = 0, W4 = 0;
+    int nseg = 0, S = 32, E = 1, wpb = 4, DW = 0, nChW = 0;
+    TableDev dev{};
+    cudaStream_t stream = nullptr;
+    bool ownStream = false;
+    int32_t* h_status = nullptr;
+    size_t statusInts = 0;
+    int trailTop = 0, trailCap = 0;
+    std::vector<int> marks;
+    int levelCap = 0;
+    bool failed = false;
+    bool empty = false;
+    ct_call_stats last{};
+    bool profile = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ct_profile prof{};
+    int64_t deviceBytes = 0;
+    uint32_t* d_domScratch = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(ct_table* ct, T** p, size_t count) {
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    ct->allocs.push_back(q);
+    ct->deviceBytes += (int64_t)bytes;
+    *p = static_cast<T*>(q);
+    return CT_OK;
+}
+
+template <typename T>
+int upload(ct_table* ct, T* dst, const std::vector<T>& src) {
+    if (src.empty()) return CT_OK;
+    CT_CUDA(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, ct->stream));
+    return CT_OK;
+}
+
+int sync(ct_table* ct) {
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    return CT_OK;
+}
+
+int choose_entries_per_lane(int64_t W4, int requested) {
+    if (requested == 1 || requested == 2 || requested == 4) return requested;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    }
+    cudaGetLastError();
+    // Enough segments to give every SM several warps before growing segments.
+    const int64_t cap = 16LL * sms;
+    if ((W4 + 31) / 32 <= cap) return 1;
+    if ((W4 + 63) / 64 <= cap) return 2;
+    return 4;
+}
+
+// Grow the trail so that `need` entries fit.
+int ensure_trail(ct_table* ct, int64_t need) {
+    if (need <= ct->trailCap) return CT_OK;
+    if (need > 0x7fffffffLL) {
+        ct_set_error("trail would exceed 2^31 entries");
+        return CT_ERR_OOM;
+    }
+    int64_t cap = std::max<int64_t>(need, 2LL * ct->trailCap);
+    if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
+    int2* nk = nullptr;
+    uint4* no = nullptr;
+    cudaError_t e = cudaMalloc(&nk, (size_t)cap * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&no, (size_t)cap * sizeof(uint4));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (nk) cudaFree(nk);
+        ct_set_error("trail growth to %lld entries: %s", (long long)cap, cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    if (ct->trailTop > 0) {
+        CT_CUDA(cudaMemcpyAsync(nk, ct->dev.trailKey, (size_t)ct->trailTop * sizeof(int2), cudaMemcpyDeviceToDevice,
+                                ct->stream));
+        CT_CUDA(cudaMemcpyAsync(no, ct->dev.trailOld, (size_t)ct->trailTop * sizeof(uint4),
+                                cudaMemcpyDeviceToDevice, ct->stream));
+    }
+    int32_t capi = (int32_t)cap;
+    CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->trail_cap, &capi, sizeof(int32_t), cudaMemcpyHostToDevice, ct->stream));
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
+    if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
+    ct->deviceBytes += (cap - ct->trailCap) * (int64_t)(sizeof(int2) + sizeof(uint4));
+    ct->dev.trailKey = nk;
+    ct->dev.trailOld = no;
+    ct->trailCap = (int)cap;
+    return CT_OK;
+}
+
+int ensure_levels(ct_table* ct, int need) {
+    if (need <= ct->levelCap) return CT_OK;
+    const int cap = std::max(need, 2 * ct->levelCap);
+    int32_t* ns = nullptr;
+    uint32_t* nd = nullptr;
+    cudaError_t e = cudaMalloc(&ns, (size_t)cap * std::max(ct->nseg, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&nd, (size_t)cap * std::max(ct->DW, 1) * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ns) cudaFree(ns);
+        ct_set_error("level stack growth: %s", cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    const int used = (int)ct->marks.size();
+    if (used > 0) {
+        CT_CUDA(cudaMemcpyAsync(ns, ct->dev.levelSeg, (size_t)used * ct->nseg * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, ct->stream));
+        CT_CUDA(cudaMemcpyAsync(nd, ct->dev.levelDom, (size_t)used * ct->DW * sizeof(uint32_t),
+                                cudaMemcpyDeviceToDevice, ct->stream));
+    }
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
+    if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+    ct->deviceBytes += (int64_t)(cap - ct->levelCap) * (ct->nseg * 4 + ct->DW * 4);
+    ct->dev.levelSeg = ns;
+    ct->dev.levelDom = nd;
+    ct->levelCap = cap;
+    return CT_OK;
+}
+
+void free_table(ct_table* ct) {
+    if (!ct) return;
+    if (ct->stream) cudaStreamSynchronize(ct->stream);
+    for (void* p : ct->allocs) cudaFree(p);
+    if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
+    if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
+    if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
+    if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+    if (ct->h_status) cudaFreeHost(ct->h_status);
+    for (auto& e : ct->ev)
+        if (e) cudaEventDestroy(e);
+    if (ct->ownStream && ct->stream) cudaStreamDestroy(ct->stream);
+    cudaGetLastError();
+    delete ct;
+}
+
+int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples, int64_t t,
+          const ct_options* opt) {
+    const int n = ct->arity;
+    ct->lo.assign(dom_lo, dom_lo + n);
+    ct->size.assign(dom_size, dom_size + n);
+    ct->nw.resize(n);
+    ct->ld.resize(n);
+    ct->row0.resize(n + 1);
+    int DW = 0, R = 0;
+    for (int i = 0; i < n; ++i) {
+        ct->nw[i] = (ct->size[i] + 31) / 32;
+        ct->ld[i] = DW;
+        DW += ct->nw[i];
+        ct->row0[i] = R;
+        R += ct->size[i];
+    }
+    ct->row0[n] = R;
+    ct->DW = DW;
+    ct->R = R;
+    ct->nChW = (n + 31) / 32;
+    ct->rowVar.resize(R);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < ct->size[i]; ++a) ct->rowVar[ct->row0[i] + a] = i;
+
+    // Retained tuples: every value inside its initial domain (input order kept).
+    std::vector<int64_t> keep;
+    keep.reserve((size_t)t);
+    for (int64_t j = 0; j < t; ++j) {
+        const int32_t* tu = tuples + j * n;
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) {
+            const int64_t off = (int64_t)tu[i] - ct->lo[i];
+            ok = off >= 0 && off < ct->size[i];
+        }
+        if (ok) keep.push_back(j);
+    }
+    ct->t = (int64_t)keep.size();
+    ct->W = (ct->t + 31) / 32;
+    ct->W4 = (ct->W + 3) / 4;
+    ct->profile = opt && opt->profile;
+    if (ct->t == 0) {
+        ct->empty = true;
+        return CT_INFEASIBLE;
+    }
+    if (ct->W4 > 0x3fffffffLL) {
+        ct_set_error("too many tuples");
+        return CT_ERR_ARG;
+    }
+    const int64_t W4 = ct->W4;
+    ct->E = choose_entries_per_lane(W4, opt ? opt->entries_per_lane : 0);
+    ct->S = 32 * ct->E;
+    ct->nseg = (int)((W4 + ct->S - 1) / ct->S);
+    ct->wpb = (opt && opt->warps_per_block >= 1 && opt->warps_per_block <= 16) ? opt->warps_per_block : 4;
+
+    // supports rows (Sec. 2), value-major, 16-byte aligned rows of W4 chunks
+    const size_t rowWords = (size_t)W4 * 4;
+    std::vector<uint32_t> hsup((size_t)R * rowWords, 0u);
+    for (int64_t jj = 0; jj < ct->t; ++jj) {
+        const int32_t* tu = tuples + keep[(size_t)jj] * n;
+        const uint32_t bit = 1u << (jj & 31);
+        const size_t word = (size_t)(jj >> 5);
+        for (int i = 0; i < n; ++i) {
+            const int row = ct->row0[i] + (tu[i] - ct->lo[i]);
+            hsup[(size_t)row * rowWords + word] |= bit;
+        }
+    }
+    std::vector<int32_t> hres(R, 0);
+    for (int r = 0; r < R; ++r) {
+        const uint32_t* row = hsup.data() + (size_t)r * rowWords;
+        for (int64_t c = 0; c < W4; ++c) {
+            if (row[c * 4] | row[c * 4 + 1] | row[c * 4 + 2] | row[c * 4 + 3]) {
+                hres[r] = (int32_t)c;
+                break;
+            }
+        }
+    }
+    // currTable: every retained tuple is valid under the initial domains.
+    std::vector<uint32_t> hcurr(rowWords, 0u);
+    for (int64_t w = 0; w < ct->W; ++w) {
+        const int64_t rem = ct->t - w * 32;
+        hcurr[(size_t)w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    std::vector<int32_t> hidx((size_t)ct->nseg * ct->S, 0), hcnt(ct->nseg, 0);
+    for (int s = 0; s < ct->nseg; ++s) {
+        int c = 0;
+        for (int j = 0; j < ct->S; ++j) {
+            const int64_t ch = (int64_t)s * ct->S + j;
+            if (ch >= W4) break;
+            hidx[(size_t)s * ct->S + c++] = (int32_t)ch;
+        }
+        hcnt[s] = c;
+    }
+    std::vector<uint32_t> hdom(DW, 0u);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < ct->size[i]; ++a) hdom[ct->ld[i] + a / 32] |= 1u << (a % 32);
+
+    TableDev& d = ct->dev;
+    int st;
+    uint4* sup = nullptr;
+    int32_t *rowVar = nullptr, *varRow0 = nullptr, *varNW = nullptr, *varLD = nullptr;
+    if ((st = dalloc(ct, &sup, (size_t)R * W4)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.curr, (size_t)W4)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.idx, (size_t)ct->nseg * ct->S)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.segCnt, (size_t)ct->nseg)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.lastpos, (size_t)W4)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.residue, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.lastDom, (size_t)DW)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.groups, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.planRows, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.varSup, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.changed, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.missRow, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.foundChunk, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &rowVar, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &varRow0, (size_t)n + 1)) != CT_OK) return st;
+    if ((st = dalloc(ct, &varNW, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &varLD, (size_t)n)) != CT_OK) return st;
+    ct->statusInts = (size_t)kStatusHdr + ct->nChW + DW;
+    if ((st = dalloc(ct, &d.statusBlk, ct->statusInts)) != CT_OK) return st;
+    if ((st = dalloc(ct, &ct->d_domScratch, (size_t)DW)) != CT_OK) return st;
+    d.sup = sup;
+    d.rowVar = rowVar;
+    d.varRow0 = varRow0;
+    d.varNW = varNW;
+    d.varLD = varLD;
+    d.arity = n;
+    d.R = R;
+    d.W4 = (int32_t)W4;
+    d.nseg = ct->nseg;
+    d.S = ct->S;
+    d.DW = DW;
+    d.nChangedWords = ct->nChW;
+    d.useResidues = (opt && opt->no_residues) ? 0 : 1;
+
+    if (cudaHostAlloc((void**)&ct->h_status, ct->statusInts * sizeof(int32_t), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        ct->h_status = nullptr;
+        ct_set_error("cudaHostAlloc of the status block failed");
+        return CT_ERR_OOM;
+    }
+    std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
+
+    CT_CUDA(cudaMemcpyAsync(sup, hsup.data(), hsup.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ct->stream));
+    CT_CUDA(cudaMemcpyAsync(d.curr, hcurr.data(), hcurr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            ct->stream));
+    if ((st = upload(ct, d.idx, hidx)) != CT_OK) return st;
+    if ((st = upload(ct, d.segCnt, hcnt)) != CT_OK) return st;
+    CT_CUDA(cudaMemsetAsync(d.lastpos, 0xff, (size_t)W4 * sizeof(int32_t), ct->stream));
+    if ((st = upload(ct, d.residue, hres)) != CT_OK) return st;
+    if ((st = upload(ct, d.lastDom, hdom)) != CT_OK) return st;
+    if ((st = upload(ct, rowVar, ct->rowVar)) != CT_OK) return st;
+    if ((st = upload(ct, varRow0, ct->row0)) != CT_OK) return st;
+    if ((st = upload(ct, varNW, ct->nw)) != CT_OK) return st;
+    if ((st = upload(ct, varLD, ct->ld)) != CT_OK) return st;
+    CT_CUDA(cudaMemsetAsync(d.changed, 0, (size_t)n * sizeof(int32_t), ct->stream));
+    CT_CUDA(cudaMemsetAsync(d.statusBlk, 0, ct->statusInts * sizeof(int32_t), ct->stream));
+
+    Ctrl c{};
+    c.status = CT_OK;
+    c.trail_top = 0;
+    c.cur_mark = -1;
+    c.trail_cap = 0;
+    CT_CUDA(cudaMemcpyAsync(d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, ct->stream));
+    if ((st = sync(ct)) != CT_OK) return st;
+    if ((st = ensure_levels(ct, 8)) != CT_OK) return st;
+    if (ct->profile) {
+        for (auto& e : ct->ev) CT_CUDA(cudaEventCreate(&e));
+    }
+    return sync(ct);
+}
+
+void fill_stats(ct_table* ct) {
+    const int32_t* h = ct->h_status;
+    ct_call_stats& s = ct->last;
+    s.status = h[kSlotStatus];
+    s.changed_vars = h[kSlotNval];
+    s.delta_vars = h[kSlotNdelta];
+    s.reset_vars = h[kSlotNreset];
+    s.rows_ored = h[kSlotRowsOred];
+    s.sup_vars = h[kSlotNsup];
+    s.residue_hits = h[kSlotHits];
+    s.residue_misses = h[kSlotMisses];
+    s.pruned = h[kSlotPruned];
+    s.trail_added = h[kSlotTrailAdded];
+    s.live_chunks_in = (uint32_t)h[kSlotLiveIn];
+    s.live_chunks_out = (uint32_t)h[kSlotLiveOut];
+    s.live_words_in = (uint32_t)h[kSlotWordsIn];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// internal entry points for the model
+// ---------------------------------------------------------------------------
+int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, uint32_t* changed) {
+    if (!ct || !dom) {
+        ct_set_error("ct_propagate: null argument");
+        return CT_ERR_ARG;
+    }
+    if (ct->empty) {
+        ct->last = ct_call_stats{};
+        ct->last.status = CT_INFEASIBLE;
+        ct->failed = true;
+        return CT_INFEASIBLE;
+    }
+    if (ct->failed) {
+        ct_set_error("ct_propagate: the previous call failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    int st;
+    if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
+    cudaStream_t s = ct->stream;
+    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
+    CT_CUDA(launch_plan(ct->dev, dom, domOffDev, s));
+    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
+    CT_CUDA(launch_update(ct->dev, ct->E, ct->wpb, dom, domOffDev, s));
+    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[2], s));
+    CT_CUDA(launch_scan(ct->dev, ct->E, ct->wpb, dom, domOffDev, s));
+    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[3], s));
+    CT_CUDA(cudaMemcpyAsync(ct->h_status, ct->dev.statusBlk, ct->statusInts * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaStreamSynchronize(s));
+    fill_stats(ct);
+    const int32_t* h = ct->h_status;
+    const int status = h[kSlotStatus];
+    ct->trailTop = h[kSlotTrailTop];
+    if (ct->profile) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        CT_CUDA(cudaEventElapsedTime(&a, ct->ev[0], ct->ev[1]));
+        CT_CUDA(cudaEventElapsedTime(&b, ct->ev[1], ct->ev[2]));
+        CT_CUDA(cudaEventElapsedTime(&c, ct->ev[2], ct->ev[3]));
+        ct->prof.calls += 1;
+        ct->prof.plan_ms += a;
+        ct->prof.update_ms += b;
+        ct->prof.scan_ms += c;
+        if (ct->last.rows_ored > 0)
+            ct->prof.update_bytes += 4LL * ct->last.live_words_in * (ct->last.rows_ored + 2);
+    }
+    if (status == CT_INFEASIBLE) {
+        ct->failed = true;
+    } else if (status == CT_ERR_STATE) {
+        ct_set_error("ct_propagate: a domain grew since the last call without a restore");
+    } else if (status == CT_ERR_OOM) {
+        ct->failed = true;
+        ct_set_error("ct_propagate: trail overflow");
+    } else if (status != CT_OK) {
+        ct->failed = true;
+        ct_set_error("ct_propagate: device status %d", status);
+    }
+    if (changed) std::memcpy(changed, h + kStatusHdr, (size_t)ct->nChW * sizeof(uint32_t));
+    return status;
+}
+
+const int32_t* ct_table_status_host(const ct_table* ct) { return ct->h_status; }
+int ct_table_dom_words(const ct_table* ct) { return ct->DW; }
+const int32_t* ct_table_var_ld(const ct_table* ct) { return ct->ld.data(); }
+int ct_table_changed_words(const ct_table* ct) { return ct->nChW; }
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
+                         int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out) {
+    if (!out) {
+        ct_set_error("ct_create: out is null");
+        return CT_ERR_ARG;
+    }
+    *out = nullptr;
+    if (arity < 1 || arity > kMaxArity || !dom_lo || !dom_size || t < 0 || (t > 0 && !tuples)) {
+        ct_set_error("ct_create: invalid arity/domains/tuples (arity %d, t %lld)", arity, (long long)t);
+        return CT_ERR_ARG;
+    }
+    for (int i = 0; i < arity; ++i) {
+        if (dom_size[i] < 1 || dom_size[i] > kMaxDomSize) {
+            ct_set_error("ct_create: dom_size[%d] = %d out of [1, %d]", i, dom_size[i], kMaxDomSize);
+            return CT_ERR_ARG;
+        }
+    }
+    ct_table* ct = new (std::nothrow) ct_table();
+    if (!ct) return CT_ERR_OOM;
+    ct->arity = arity;
+    if (cuda_stream) {
+        ct->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        const cudaError_t e = cudaStreamCreateWithFlags(&ct->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ct;
+            return ct_cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        ct->ownStream = true;
+    }
+    const int st = build(ct, dom_lo, dom_size, tuples, t, opt);
+    if (st < 0) {
+        free_table(ct);
+        return st;
+    }
+    *out = ct;
+    return st;
+}
+
+extern "C" int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_vars) {
+    if (!ct) {
+        ct_set_error("ct_propagate: null handle");
+        return CT_ERR_ARG;
+    }
+    return ct_table_propagate_on(ct, dom_bits, ct->dev.varLD, changed_vars);
+}
+
+extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t* changed_vars) {
+    if (!ct || !dom_bits_host) {
+        ct_set_error("ct_propagate_host: null argument");
+        return CT_ERR_ARG;
+    }
+    if (ct->empty) return ct_table_propagate_on(ct, dom_bits_host, nullptr, changed_vars);
+    CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, dom_bits_host, (size_t)ct->DW * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, ct->stream));
+    const int st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, changed_vars);
+    if (st == CT_OK)
+        std::memcpy(dom_bits_host, ct->h_status + kStatusHdr + ct->nChW, (size_t)ct->DW * sizeof(uint32_t));
+    return st;
+}
+
+extern "C" int ct_save(ct_table* ct, int* level_out) {
+    if (!ct) {
+        ct_set_error("ct_save: null handle");
+        return CT_ERR_ARG;
+    }
+    const int L = (int)ct->marks.size();
+    if (!ct->empty) {
+        int st;
+        if ((st = ensure_levels(ct, L + 1)) != CT_OK) return st;
+        CT_CUDA(launch_save(ct->dev, L, ct->stream));
+    }
+    ct->marks.push_back(ct->trailTop);
+    if (level_out) *level_out = L;
+    return CT_OK;
+}
+
+extern "C" int ct_restore(ct_table* ct, int level) {
+    if (!ct) {
+        ct_set_error("ct_restore: null handle");
+        return CT_ERR_ARG;
+    }
+    if (level < 0 || level >= (int)ct->marks.size()) {
+        ct_set_error("ct_restore: level %d not in [0, %d)", level, (int)ct->marks.size());
+        return CT_ERR_LEVEL;
+    }
+    const int mark = ct->marks[level];
+    const int newMark = level > 0 ? ct->marks[level - 1] : -1;
+    if (!ct->empty) {
+        CT_CUDA(launch_restore(ct->dev, level, mark, ct->trailTop, newMark, ct->stream));
+        ct->trailTop = mark;
+        ct->failed = false;
+    }
+    ct->marks.resize(level);
+    return CT_OK;
+}
+
+extern "C" int ct_get_currtable(ct_table* ct, uint32_t* words_host, int64_t* nonzero_words_out) {
+    if (!ct) {
+        ct_set_error("ct_get_currtable: null handle");
+        return CT_ERR_ARG;
+    }
+    if (ct->empty) {
+        if (nonzero_words_out) *nonzero_words_out = 0;
+        return CT_OK;
+    }
+    std::vector<uint32_t> buf((size_t)ct->W4 * 4);
+    CT_CUDA(cudaMemcpyAsync(buf.data(), ct->dev.curr, buf.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            ct->stream));
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    int64_t nz = 0;
+    for (int64_t w = 0; w < ct->W; ++w) nz += buf[(size_t)w] != 0u;
+    if (words_host) std::memcpy(words_host, buf.data(), (size_t)ct->W * sizeof(uint32_t));
+    if (nonzero_words_out) *nonzero_words_out = nz;
+    return CT_OK;
+}
+
+extern "C" int ct_get_support_row(ct_table* ct, int row, uint32_t* words_host) {
+    if (!ct || !words_host || row < 0 || row >= ct->R) {
+        ct_set_error("ct_get_support_row: bad argument");
+        return CT_ERR_ARG;
+    }
+    if (ct->empty) return CT_OK;
+    CT_CUDA(cudaMemcpyAsync(words_host, ct->dev.sup + (size_t)row * ct->W4, (size_t)ct->W * sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, ct->stream));
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    return CT_OK;
+}
+
+extern "C" int ct_get_index(ct_table* ct, int32_t* index_host, int64_t* count_out) {
+    if (!ct) {
+        ct_set_error("ct_get_index: null handle");
+        return CT_ERR_ARG;
+    }
+    if (ct->empty) {
+        if (count_out) *count_out = 0;
+        return CT_OK;
+    }
+    std::vector<int32_t> cnt(ct->nseg), idx((size_t)ct->nseg * ct->S);
+    CT_CUDA(cudaMemcpyAsync(cnt.data(), ct->dev.segCnt, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ct->stream));
+    CT_CUDA(cudaMemcpyAsync(idx.data(), ct->dev.idx, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ct->stream));
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    int64_t n = 0;
+    for (int s = 0; s < ct->nseg; ++s) {
+        for (int j = 0; j < cnt[s]; ++j) {
+            if (index_host) index_host[n] = idx[(size_t)s * ct->S + j];
+            ++n;
+        }
+    }
+    if (count_out) *count_out = n;
+    return CT_OK;
+}
+
+extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
+    if (!ct || !info) {
+        ct_set_error("ct_get_info: null argument");
+        return CT_ERR_ARG;
+    }
+    ct_table_info r{};
+    r.arity = ct->arity;
+    r.rows = ct->R;
+    r.tuples = ct->t;
+    r.words = ct->W;
+    r.chunks = ct->W4;
+    r.segments = ct->nseg;
+    r.seg_capacity = ct->S;
+    r.trail_size = ct->trailTop;
+    r.depth = (int)ct->marks.size();
+    r.entries_per_lane = ct->E;
+    r.device_bytes = ct->deviceBytes;
+    int64_t live = 0;
+    const int st = ct_get_index(ct, nullptr, &live);
+    if (st != CT_OK) return st;
+    r.live_chunks = live;
+    *info = r;
+    return CT_OK;
+}
+
+extern "C" int ct_get_call_stats(ct_table* ct, ct_call_stats* stats) {
+    if (!ct || !stats) {
+        ct_set_error("ct_get_call_stats: null argument");
+        return CT_ERR_ARG;
+    }
+    *stats = ct->last;
+    return CT_OK;
+}
+
+extern "C" int ct_get_profile(ct_table* ct, ct_profile* prof) {
+    if (!ct || !prof) {
+        ct_set_error("ct_get_profile: null argument");
+        return CT_ERR_ARG;
+    }
+    *prof = ct->prof;
+    return CT_OK;
+}
+
+extern "C" int ct_reset_profile(ct_table* ct) {
+    if (!ct) return CT_ERR_ARG;
+    ct->prof = ct_profile{};
+    return CT_OK;
+}
+
+extern "C" int ct_destroy(ct_table* ct) {
+    free_table(ct);
+    return CT_OK;
+}

@@ -1,0 +1,373 @@
+"""Python binding of libct.so (ctypes): argument marshalling only.
+
+Every function keeps the name of the C entry point it wraps (include/ct.h)
+and returns the C status code together with any outputs. Device buffers are
+passed as torch CUDA tensors (or raw device addresses); PyTorch provides the
+device memory and the stream, all propagation work runs in the library's
+CUDA kernels. There is no CPU fallback: if libct.so has not been built the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CT_OK = 0
+CT_INFEASIBLE = 1
+CT_ERR_ARG = -1
+CT_ERR_OOM = -2
+CT_ERR_CUDA = -3
+CT_ERR_STATE = -4
+CT_ERR_TIMEOUT = -5
+CT_ERR_LEVEL = -6
+
+
+class CtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class ct_options(ctypes.Structure):
+    _fields_ = [("entries_per_lane", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class ct_table_info(ctypes.Structure):
+    _fields_ = [("arity", ctypes.c_int32), ("rows", ctypes.c_int32), ("tuples", ctypes.c_int64),
+                ("words", ctypes.c_int64), ("chunks", ctypes.c_int64), ("segments", ctypes.c_int32),
+                ("seg_capacity", ctypes.c_int32), ("live_chunks", ctypes.c_int64),
+                ("trail_size", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("entries_per_lane", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class ct_call_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("changed_vars", ctypes.c_int32),
+                ("delta_vars", ctypes.c_int32), ("reset_vars", ctypes.c_int32),
+                ("rows_ored", ctypes.c_int32), ("sup_vars", ctypes.c_int32),
+                ("residue_hits", ctypes.c_int32), ("residue_misses", ctypes.c_int32),
+                ("pruned", ctypes.c_int32), ("trail_added", ctypes.c_int32),
+                ("live_chunks_in", ctypes.c_int64), ("live_chunks_out", ctypes.c_int64),
+                ("live_words_in", ctypes.c_int64)]
+
+
+class ct_profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("update_ms", ctypes.c_double),
+                ("scan_ms", ctypes.c_double), ("update_bytes", ctypes.c_int64)]
+
+
+class ct_search_stats(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_int64), ("fails", ctypes.c_int64), ("solutions", ctypes.c_int64),
+                ("propagations", ctypes.c_int64), ("max_depth", ctypes.c_int32),
+                ("complete", ctypes.c_int32), ("seconds", ctypes.c_double)]
+
+
+def _as_dict(s):
+    return {k: (list(getattr(s, k)) if k == "reserved" else getattr(s, k)) for k, _ in s._fields_}
+
+
+_P = ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+_SIGS = {
+    "ct_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64,
+                                 ctypes.POINTER(ct_options), _P, ctypes.POINTER(_P)]),
+    "ct_propagate": (ctypes.c_int, [_P, _P, _U32P]),
+    "ct_propagate_host": (ctypes.c_int, [_P, _U32P, _U32P]),
+    "ct_save": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "ct_restore": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ct_get_currtable": (ctypes.c_int, [_P, _U32P, _I64P]),
+    "ct_get_support_row": (ctypes.c_int, [_P, ctypes.c_int, _U32P]),
+    "ct_get_index": (ctypes.c_int, [_P, _I32P, _I64P]),
+    "ct_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ct_table_info)]),
+    "ct_get_call_stats": (ctypes.c_int, [_P, ctypes.POINTER(ct_call_stats)]),
+    "ct_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ct_profile)]),
+    "ct_reset_profile": (ctypes.c_int, [_P]),
+    "ct_destroy": (ctypes.c_int, [_P]),
+    "ct_model_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, ctypes.POINTER(ct_options), _P,
+                                       ctypes.POINTER(_P)]),
+    "ct_model_add_table": (ctypes.c_int, [_P, _I32P, ctypes.c_int, _I32P, ctypes.c_int64]),
+    "ct_model_propagate": (ctypes.c_int, [_P]),
+    "ct_model_get_domains": (ctypes.c_int, [_P, _U32P]),
+    "ct_model_set_domains": (ctypes.c_int, [_P, _U32P]),
+    "ct_model_save": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "ct_model_restore": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ct_search_dfs": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ct_search_stats), _I32P]),
+    "ct_model_destroy": (ctypes.c_int, [_P]),
+    "ct_last_error": (ctypes.c_char_p, []),
+    "ct_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ct_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libct.so (built by paper_2507_18413_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libct.so not found at {p}; build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def last_error() -> str:
+    return load().ct_last_error().decode()
+
+
+def status_string(st: int) -> str:
+    try:
+        return load().ct_status_string(int(st)).decode()
+    except RuntimeError:
+        return str(st)
+
+
+def check(st: int) -> int:
+    if st < 0:
+        raise CtError(st, last_error())
+    return st
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+
+def _i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(_I32P)
+
+
+def _u32_out(n):
+    a = np.zeros(max(int(n), 1), dtype=np.uint32)
+    return a, a.ctypes.data_as(_U32P)
+
+
+def _dev_ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_options(entries_per_lane=0, warps_per_block=0, no_residues=0, profile=0):
+    o = ct_options()
+    o.entries_per_lane = entries_per_lane
+    o.warps_per_block = warps_per_block
+    o.no_residues = no_residues
+    o.profile = profile
+    return o
+
+
+def dom_layout(dom_size):
+    """Word offsets and word counts of domains stored back to back."""
+    nw = [(int(d) + 31) // 32 for d in dom_size]
+    off = np.concatenate([[0], np.cumsum(nw)]).astype(np.int64)
+    return off, nw
+
+
+def masks_to_words(masks) -> np.ndarray:
+    """Domains as bool masks -> packed uint32 words (bit a of word a // 32 = value dom_lo + a)."""
+    out = []
+    for m in masks:
+        m = np.asarray(m, dtype=bool)
+        nw = (m.shape[0] + 31) // 32
+        padded = np.zeros(nw * 32, dtype=bool)
+        padded[: m.shape[0]] = m
+        by = np.packbits(padded.reshape(-1, 8), axis=1, bitorder="little").reshape(-1)
+        out.append(by.view("<u4").astype(np.uint32))
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.uint32)
+
+
+def words_to_masks(words, dom_size):
+    words = np.asarray(words, dtype=np.uint32)
+    off, nw = dom_layout(dom_size)
+    masks = []
+    for i, d in enumerate(dom_size):
+        w = words[off[i]: off[i] + nw[i]].astype("<u4")
+        bits = np.unpackbits(w.view(np.uint8), bitorder="little")[: int(d)]
+        masks.append(bits.astype(bool))
+    return masks
+
+
+# --------------------------------------------------------------------------
+# table
+# --------------------------------------------------------------------------
+
+def ct_create(arity, dom_lo, dom_size, tuples, opt=None, stream=None):
+    """Returns (status, handle). tuples: int32 [t, arity] (host)."""
+    L = load()
+    lo, plo = _i32(dom_lo)
+    sz, psz = _i32(dom_size)
+    tup = np.ascontiguousarray(np.asarray(tuples, dtype=np.int32).reshape(-1, arity))
+    t = tup.shape[0]
+    ptup = tup.ctypes.data_as(_I32P) if t else None
+    h = _P()
+    st = L.ct_create(int(arity), plo, psz, ptup, int(t), ctypes.byref(opt) if opt is not None else None,
+                     _stream_ptr(stream), ctypes.byref(h))
+    return st, h
+
+
+def ct_propagate(h, dom_bits, changed_words: int = 0):
+    """dom_bits: device buffer (torch tensor or address). Returns (status, changed uint32 words)."""
+    ch, pch = _u32_out(changed_words)
+    st = load().ct_propagate(h, _dev_ptr(dom_bits), pch if changed_words else None)
+    return st, ch[:changed_words]
+
+
+def ct_propagate_host(h, dom_words: np.ndarray, changed_words: int = 0):
+    """dom_words: host uint32 array, filtered in place on CT_OK."""
+    assert dom_words.dtype == np.uint32 and dom_words.flags["C_CONTIGUOUS"]
+    ch, pch = _u32_out(changed_words)
+    st = load().ct_propagate_host(h, dom_words.ctypes.data_as(_U32P), pch if changed_words else None)
+    return st, ch[:changed_words]
+
+
+def ct_save(h):
+    lv = ctypes.c_int(-1)
+    st = load().ct_save(h, ctypes.byref(lv))
+    return st, lv.value
+
+
+def ct_restore(h, level):
+    return load().ct_restore(h, int(level))
+
+
+def ct_get_currtable(h, nwords):
+    w, pw = _u32_out(nwords)
+    nz = ctypes.c_int64(0)
+    st = load().ct_get_currtable(h, pw, ctypes.byref(nz))
+    return st, w[:nwords], nz.value
+
+
+def ct_get_support_row(h, row, nwords):
+    w, pw = _u32_out(nwords)
+    st = load().ct_get_support_row(h, int(row), pw)
+    return st, w[:nwords]
+
+
+def ct_get_index(h):
+    n = ctypes.c_int64(0)
+    L = load()
+    st = L.ct_get_index(h, None, ctypes.byref(n))
+    if st != CT_OK:
+        return st, None
+    a = np.zeros(max(n.value, 1), dtype=np.int32)
+    st = L.ct_get_index(h, a.ctypes.data_as(_I32P), ctypes.byref(n))
+    return st, a[: n.value]
+
+
+def ct_get_info(h):
+    i = ct_table_info()
+    st = load().ct_get_info(h, ctypes.byref(i))
+    return st, _as_dict(i)
+
+
+def ct_get_call_stats(h):
+    s = ct_call_stats()
+    st = load().ct_get_call_stats(h, ctypes.byref(s))
+    return st, _as_dict(s)
+
+
+def ct_get_profile(h):
+    p = ct_profile()
+    st = load().ct_get_profile(h, ctypes.byref(p))
+    return st, _as_dict(p)
+
+
+def ct_reset_profile(h):
+    return load().ct_reset_profile(h)
+
+
+def ct_destroy(h):
+    return load().ct_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# model
+# --------------------------------------------------------------------------
+
+def ct_model_create(dom_lo, dom_size, opt=None, stream=None):
+    L = load()
+    lo, plo = _i32(dom_lo)
+    sz, psz = _i32(dom_size)
+    h = _P()
+    st = L.ct_model_create(len(lo), plo, psz, ctypes.byref(opt) if opt is not None else None,
+                           _stream_ptr(stream), ctypes.byref(h))
+    return st, h
+
+
+def ct_model_add_table(m, scope, tuples):
+    sc, psc = _i32(scope)
+    tup = np.ascontiguousarray(np.asarray(tuples, dtype=np.int32).reshape(-1, len(sc)))
+    ptup = tup.ctypes.data_as(_I32P) if tup.shape[0] else None
+    return load().ct_model_add_table(m, psc, len(sc), ptup, int(tup.shape[0]))
+
+
+def ct_model_propagate(m):
+    return load().ct_model_propagate(m)
+
+
+def ct_model_get_domains(m, nwords):
+    w, pw = _u32_out(nwords)
+    st = load().ct_model_get_domains(m, pw)
+    return st, w[:nwords]
+
+
+def ct_model_set_domains(m, words):
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
+    return load().ct_model_set_domains(m, w.ctypes.data_as(_U32P))
+
+
+def ct_model_save(m):
+    lv = ctypes.c_int(-1)
+    st = load().ct_model_save(m, ctypes.byref(lv))
+    return st, lv.value
+
+
+def ct_model_restore(m, level):
+    return load().ct_model_restore(m, int(level))
+
+
+def ct_search_dfs(m, nvars, node_limit=0, count_all=True):
+    s = ct_search_stats()
+    sol = np.zeros(nvars, dtype=np.int32)
+    st = load().ct_search_dfs(m, int(node_limit), 1 if count_all else 0, ctypes.byref(s),
+                              sol.ctypes.data_as(_I32P))
+    d = _as_dict(s)
+    d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
+    return st, d
+
+
+def ct_model_destroy(m):
+    return load().ct_model_destroy(m)

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every symbol include/ct.h declares.
+
+No compute call is made here (no GPU needed): only entry points that touch no
+device (status strings, version, last error) are called.
+"""
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from paper_2507_18413_gb300 import build as B
+from paper_2507_18413_gb300 import ct as C
+
+HEADER = os.path.join(B.ROOT, "include", "ct.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const\s+char\s*\*)\s*(ct_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists(os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")):
+        if not os.path.exists(B.LIB):
+            pytest.skip("no nvcc and no prebuilt libct.so")
+    else:
+        B.build()
+    return C.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["ct_create", "ct_propagate", "ct_save", "ct_restore", "ct_get_currtable", "ct_destroy",
+              "ct_model_create", "ct_model_add_table", "ct_model_propagate", "ct_search_dfs",
+              "ct_model_destroy"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    assert sorted(C.exported_names()) == _declared()
+
+
+def test_host_only_entry_points(lib):
+    assert C.status_string(C.CT_OK) == "CT_OK"
+    assert C.status_string(C.CT_INFEASIBLE) == "CT_INFEASIBLE"
+    assert C.status_string(C.CT_ERR_LEVEL) == "CT_ERR_LEVEL"
+    assert lib.ct_version() >= 10000
+    assert isinstance(C.last_error(), str)
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    assert lib.ct_create(3, None, None, None, 0, None, None, None) == C.CT_ERR_ARG
+    assert lib.ct_propagate(None, None, None) == C.CT_ERR_ARG
+    assert lib.ct_restore(None, 0) == C.CT_ERR_ARG
+    assert lib.ct_destroy(None) == C.CT_OK
+    assert lib.ct_model_destroy(None) == C.CT_OK
+
+
+def test_domain_word_marshalling_round_trip():
+    rng = np.random.default_rng(0)
+    sizes = [1, 7, 32, 33, 64, 100]
+    masks = [rng.random(d) < 0.5 for d in sizes]
+    words = C.masks_to_words(masks)
+    off, nw = C.dom_layout(sizes)
+    assert words.shape[0] == off[-1] == sum(nw)
+    back = C.words_to_masks(words, sizes)
+    for a, b in zip(masks, back):
+        assert np.array_equal(a, b)
+    # value a of variable i is bit a % 32 of word off[i] + a // 32
+    for i, m in enumerate(masks):
+        for a in range(sizes[i]):
+            assert bool((int(words[off[i] + a // 32]) >> (a % 32)) & 1) == bool(m[a])
