@@ -1,0 +1,527 @@
+#!/usr/bin/env python3
+"""Benchmark: Compact-Table propagations/s on one large table (plus context figures).
+
+Workload (one "step"): a seeded domain-reduction stream on one table of arity 6
+over 32-value domains with 4e6 distinct uniform tuples. The stream dives from
+the root: before every propagation it saves a level, then removes either 1-2
+values of one variable (a delta-path update) or more than half of one
+variable's values (a reset-path update) with equal probability; a dive returns
+to the root after 8 calls or on failure. Every propagation runs the whole
+hot path: change detection, updateTable, the failure test and filterDomains.
+
+The edit sequence of each step is planned once, untimed, by running it through
+the library, and replayed in the timed region with the input domains already
+in device memory. L2 is flushed (a 256 MB write) between timed steps; the
+per-step device time is taken with CUDA events on the table's stream.
+
+`e2e` replays the same sequence through ct_propagate_host (host buffers:
+domains copied in, filtered domains and status copied out every call).
+`roofline` reports the update kernel (dominant) over the timed region:
+algorithmic bytes 4 * N * (rows_ored + 2) per launch / CUDA-event duration.
+`cpu_baseline` times the CPU oracle on a bounded sample of the same inputs.
+
+Multi-GPU: one process per GPU, each with its own seeded stream (weak scaling,
+no collective on the data path); value = all ranks' propagations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2507_18413_gb300 import inputs as G  # noqa: E402
+
+METRIC = "CT propagations/s"
+UNIT = "propagations/s"
+ARITY, DOM = 6, 32
+KERNELS_PER_PROPAGATE = 3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--tuples", type=int, default=4_000_000)
+    p.add_argument("--calls", type=int, default=256, help="propagations per step")
+    p.add_argument("--depth", type=int, default=8)
+    p.add_argument("--seed", type=int, default=20250724)
+    p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--case", default="stream", choices=["stream", "bulk4e6", "bulk1e7"],
+                   help="bulk*: only the one-call bandwidth case (for profiling)")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# seeded stream (host logic shared by the GPU planner and the oracle arm)
+# --------------------------------------------------------------------------
+
+def next_edit(rng, masks):
+    if rng.int(2) == 0:
+        new, i = G.delta_step(rng, masks)
+    else:
+        new, i = G.reset_step(rng, masks)
+    if i is None:
+        new, _ = G.remove_random_values(rng, masks, 1)
+    return new
+
+
+def clocks_start(gpu_index):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200", "-i", str(gpu_index)],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def clocks_stop(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for k, n in enumerate(names):
+            if f[5 + k].lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+class Replay:
+    """A planned stream: ops over a table and the input domains of each call."""
+
+    def __init__(self):
+        self.ops = []      # ("save",) | ("restore", level) | ("prop", k)
+        self.inputs = []   # uint32 words per propagation
+        self.statuses = []
+
+
+def plan_steps(C, torch, h, dom, dom_size, root_words, nsteps, calls, depth, seed):
+    """Run the stream once through the library and record what each step does."""
+    plans = []
+    for s in range(nsteps):
+        rng = G.Rng(G.derive_seed(seed, s))
+        rp = Replay()
+        masks = C.words_to_masks(root_words, dom_size)
+        d = 0
+        for c in range(calls):
+            C.check(C.ct_save(h)[0])
+            rp.ops.append(("save",))
+            new = next_edit(rng, masks)
+            w = C.masks_to_words(new)
+            k = len(rp.inputs)
+            rp.inputs.append(w.copy())
+            rp.ops.append(("prop", k))
+            dom.copy_(torch.from_numpy(w.view(np.int32).copy()))
+            st, _ = C.ct_propagate(h, dom, 0)
+            C.check(st)
+            rp.statuses.append(st)
+            d += 1
+            if st == C.CT_INFEASIBLE or d >= depth:
+                C.check(C.ct_restore(h, 1))
+                rp.ops.append(("restore", 1))
+                masks = C.words_to_masks(root_words, dom_size)
+                d = 0
+            else:
+                masks = C.words_to_masks(dom.cpu().numpy().view(np.uint32), dom_size)
+        if d:
+            C.check(C.ct_restore(h, 1))
+            rp.ops.append(("restore", 1))
+        plans.append(rp)
+    return plans
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2507_18413_gb300 import build as B
+    from paper_2507_18413_gb300 import ct as C
+
+    B.build()
+    C.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    seed = args.seed + 1000 * rank
+    dom_lo, dom_size, tup = G.large_table(seed, args.tuples, ARITY, DOM)
+    opt = C.make_options(profile=1)
+    st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, opt=opt, stream=stream)
+    C.check(st)
+    st, info = C.ct_get_info(h)
+    off, nw = C.dom_layout(dom_size)
+    DW = int(off[-1])
+    dom = torch.zeros(DW, dtype=torch.int32, device="cuda")
+    # root: filter once with full domains, then keep it as level 0
+    full = C.masks_to_words([np.ones(d, bool) for d in dom_size])
+    dom.copy_(torch.from_numpy(full.view(np.int32).copy()))
+    C.check(C.ct_propagate(h, dom, 0)[0])
+    root_words = dom.cpu().numpy().view(np.uint32).copy()
+    C.check(C.ct_save(h)[0])  # level 0: root
+
+    nsteps = args.warmup + args.steps
+    plans = plan_steps(C, torch, h, dom, dom_size, root_words, nsteps, args.calls, args.depth, seed)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
+
+    def device_inputs(rp):
+        return torch.from_numpy(np.stack(rp.inputs).view(np.int32).copy()).cuda()
+
+    dev_in = [device_inputs(rp) for rp in plans]
+
+    def replay(rp, work):
+        base = work.data_ptr()
+        nprop = nsave = nres = 0
+        for op in rp.ops:
+            if op[0] == "save":
+                C.ct_save(h)
+                nsave += 1
+            elif op[0] == "restore":
+                C.ct_restore(h, op[1])
+                nres += 1
+            else:
+                st, _ = C.ct_propagate(h, base + op[1] * DW * 4, 0)
+                if st < 0:
+                    raise RuntimeError(C.last_error())
+                nprop += 1
+        return nprop, nsave, nres
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, props, launches = [], 0, 0
+    clk = None
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or str(local)
+    for s, rp in enumerate(plans):
+        work = dev_in[s].clone()
+        flush.zero_()
+        if s == args.warmup:
+            C.ct_reset_profile(h)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            clk = clocks_start(gpu_index if world == 1 else local)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        n, ns, nr = replay(rp, work)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            step_ms.append(ev0.elapsed_time(ev1))
+            props += n
+            launches += KERNELS_PER_PROPAGATE * n + ns + nr
+    clocks = clocks_stop(clk)
+    if world > 1:
+        torch.distributed.barrier()
+    st, prof = C.ct_get_profile(h)
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms, float(props)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        total_ms_all, props_all = float(tmax[0]), float(tsum[1])
+    else:
+        total_ms_all, props_all = total_ms, float(props)
+    value = props_all / (total_ms_all / 1e3)
+
+    # e2e: the same replay through host buffers (copies in the timed region)
+    e2e_ms, e2e_props = 0.0, 0
+    h2d = d2h = 0
+    status_bytes = (16 + (ARITY + 31) // 32 + DW) * 4
+    for s in range(args.warmup, nsteps):
+        rp = plans[s]
+        host_in = [w.copy() for w in rp.inputs]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for op in rp.ops:
+            if op[0] == "save":
+                C.ct_save(h)
+            elif op[0] == "restore":
+                C.ct_restore(h, op[1])
+            else:
+                st, _ = C.ct_propagate_host(h, host_in[op[1]], 0)
+                e2e_props += 1
+                h2d += DW * 4
+                d2h += status_bytes
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e = {"value": e2e_props / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
+           "h2d_bytes_per_step": h2d // max(args.steps, 1), "d2h_bytes_per_step": d2h // max(args.steps, 1)}
+
+    peak, peak_kind = peaks()
+    achieved = (prof["update_bytes"] / (prof["update_ms"] / 1e3) / 1e9) if prof["update_ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "kernel": "ct_update_kernel",
+                "launches": int(prof["calls"]),
+                "avg_bytes_per_launch": prof["update_bytes"] / max(prof["calls"], 1),
+                "avg_launch_us": prof["update_ms"] * 1e3 / max(prof["calls"], 1),
+                "kernel_ms": {"plan": prof["plan_ms"], "update": prof["update_ms"], "scan": prof["scan_ms"]}}
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / max(args.steps, 1), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded SplitMix64; stands in for the paper's LIN/Gecode/OP instances)",
+        "config": {"workload": f"ct_stream_t{args.tuples}_arity{ARITY}_d{DOM}", "tuples": args.tuples,
+                   "arity": ARITY, "domain": DOM, "calls_per_step": args.calls, "dive_depth": args.depth,
+                   "edits": "50% delta (1-2 values), 50% reset (> half a domain)", "seed": args.seed,
+                   "l2": "flushed between steps (256 MB write), flush excluded from timing",
+                   "timing": "sum of per-step CUDA-event intervals on the table stream",
+                   "parallelism": f"replicas x{world}", "entries_per_lane": info["entries_per_lane"],
+                   "segments": info["segments"]},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    C.ct_destroy(h)
+    del flush
+    if rank == 0 and not args.no_extra:
+        result["extra"] = extras(args, C, torch, stream)
+    if rank == 0:
+        result["cpu_baseline"] = cpu_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
+    return result
+
+
+def _bulk_update(C, torch, stream, t, arity, d, seed, reps=5):
+    """One big reset call per repetition (every variable keeps < half its values):
+    the bandwidth regime of updateTable on a large table, L2 flushed before each."""
+    dom_lo, dom_size, tup = G.large_table(seed, t, arity, d)
+    st, h = C.ct_create(arity, dom_lo, dom_size, tup, opt=C.make_options(profile=1), stream=stream)
+    C.check(st)
+    off, _ = C.dom_layout(dom_size)
+    dom = torch.zeros(int(off[-1]), dtype=torch.int32, device="cuda")
+    full = C.masks_to_words([np.ones(x, bool) for x in dom_size])
+    dom.copy_(torch.from_numpy(full.view(np.int32).copy()))
+    C.check(C.ct_propagate(h, dom, 0)[0])
+    C.check(C.ct_save(h)[0])
+    keep = d // 2 - 1
+    masks = []
+    rng = G.Rng(seed)
+    for i in range(arity):
+        m = np.zeros(d, bool)
+        m[np.argsort(rng.u64(d))[:keep]] = True
+        masks.append(m)
+    w = C.masks_to_words(masks).view(np.int32).copy()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+    C.ct_reset_profile(h)
+    stats = None
+    for r in range(reps):
+        C.check(C.ct_save(h)[0])
+        dom.copy_(torch.from_numpy(w))
+        flush.zero_()
+        torch.cuda.synchronize()
+        st, _ = C.ct_propagate(h, dom, 0)
+        C.check(st)
+        stats = C.ct_get_call_stats(h)[1]
+        C.check(C.ct_restore(h, 1))
+    st, prof = C.ct_get_profile(h)
+    C.ct_destroy(h)
+    gbs = prof["update_bytes"] / (prof["update_ms"] / 1e3) / 1e9
+    return {"tuples": t, "arity": arity, "domain": d, "rows_ored": stats["rows_ored"],
+            "bytes_per_launch": prof["update_bytes"] / reps, "update_us": prof["update_ms"] * 1e3 / reps,
+            "update_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peaks()[0], 4),
+            "propagate_us": (prof["plan_ms"] + prof["update_ms"] + prof["scan_ms"]) * 1e3 / reps}
+
+
+def _stream_rate(C, torch, stream, t, calls, seed):
+    dom_lo, dom_size, tup = G.large_table(seed, t, ARITY, DOM)
+    st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, stream=stream)
+    C.check(st)
+    off, _ = C.dom_layout(dom_size)
+    dom = torch.zeros(int(off[-1]), dtype=torch.int32, device="cuda")
+    full = C.masks_to_words([np.ones(x, bool) for x in dom_size])
+    dom.copy_(torch.from_numpy(full.view(np.int32).copy()))
+    C.check(C.ct_propagate(h, dom, 0)[0])
+    root = dom.cpu().numpy().view(np.uint32).copy()
+    C.check(C.ct_save(h)[0])
+    plans = plan_steps(C, torch, h, dom, dom_size, root, 2, calls, 8, seed)
+    DW = int(off[-1])
+    best = None
+    for rp in plans:
+        work = torch.from_numpy(np.stack(rp.inputs).view(np.int32).copy()).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for op in rp.ops:
+            if op[0] == "save":
+                C.ct_save(h)
+            elif op[0] == "restore":
+                C.ct_restore(h, op[1])
+            else:
+                C.ct_propagate(h, work.data_ptr() + op[1] * DW * 4, 0)
+        torch.cuda.synchronize()
+        rate = len(rp.inputs) / (time.perf_counter() - t0)
+        best = rate if best is None else max(best, rate)
+    C.ct_destroy(h)
+    return round(best, 1)
+
+
+def _dfs_rate(C, node_limit=3000):
+    nvars, ntables, arity, d, t, seed = 20, 8, 6, 32, 100_000, 2024
+    rng = G.Rng(seed)
+    st, m = C.ct_model_create([0] * nvars, [d] * nvars)
+    C.check(st)
+    for k in range(ntables):
+        scope = G.random_scope(rng, nvars, arity)
+        tup = G.distinct_uniform_tuples(G.derive_seed(seed, k), [0] * arity, [d] * arity, t)
+        C.check(C.ct_model_add_table(m, scope, tup))
+    st, s = C.ct_search_dfs(m, nvars, node_limit, True)
+    C.check(st)
+    C.ct_model_destroy(m)
+    return {"csp": "20 vars d=32, 8 tables arity 6 x 1e5 tuples", "nodes": s["nodes"], "fails": s["fails"],
+            "solutions": s["solutions"], "complete": s["complete"], "propagations": s["propagations"],
+            "seconds": round(s["seconds"], 3), "nodes_per_s": round(s["nodes"] / s["seconds"], 1),
+            "table_propagations_per_s": round(s["propagations"] / s["seconds"], 1)}
+
+
+def extras(args, C, torch, stream):
+    out = {}
+    try:
+        out["stream_props_per_s"] = {str(t): _stream_rate(C, torch, stream, t, 128, 99 + t)
+                                     for t in (100_000, 1_000_000)}
+        out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
+        out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)
+        out["dfs_plain_first_fail"] = _dfs_rate(C)
+    except Exception as e:  # context figures must not hide the main line
+        out["error"] = repr(e)
+    return out
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# --------------------------------------------------------------------------
+
+def cpu_baseline(args, plans, dom_lo, dom_size, tup):
+    from oracle import ct_oracle as O
+    import paper_2507_18413_gb300.ct as C
+    tup_ret = O.retained_tuples(tup, dom_lo, dom_size)
+    inputs = [w for rp in plans for w in rp.inputs]
+    done, t0 = 0, time.perf_counter()
+    while done < len(inputs) and time.perf_counter() - t0 < args.cpu_seconds:
+        O.gac_table(tup_ret, dom_lo, C.words_to_masks(inputs[done], dom_size))
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} propagations of the timed stream ({args.tuples} tuples), "
+                      f"{dt:.1f} s, numpy single thread"}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle on the same workload: each step a bounded sample of the stream."""
+    from oracle import ct_oracle as O
+    seed = args.seed
+    dom_lo, dom_size, tup = G.large_table(seed, args.tuples, ARITY, DOM)
+    tup_ret = O.retained_tuples(tup, dom_lo, dom_size)
+    st, root, _ = O.gac_table(tup_ret, dom_lo, [np.ones(d, bool) for d in dom_size])
+    per_step = max(1, int(os.environ.get("CT_REF_CALLS", "4")))
+    times, props = [], 0
+    for s in range(args.warmup + args.steps):
+        rng = G.Rng(G.derive_seed(seed, s))
+        masks, d = root, 0
+        t0 = time.perf_counter()
+        for c in range(per_step):
+            new = next_edit(rng, masks)
+            st, out, _ = O.gac_table(tup_ret, dom_lo, new)
+            d += 1
+            if st == O.INFEASIBLE or d >= args.depth:
+                masks, d = root, 0
+            else:
+                masks = out
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            props += per_step
+    total = sum(times)
+    value = props / total
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded SplitMix64)", "impl": "reference",
+            "config": {"workload": f"ct_stream_t{args.tuples}_arity{ARITY}_d{DOM}", "tuples": args.tuples,
+                       "arity": ARITY, "domain": DOM, "calls_per_step": per_step, "dive_depth": args.depth},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} propagations of the stream per step, numpy single thread"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)))
+        return
+    if args.case != "stream":
+        import torch
+        from paper_2507_18413_gb300 import build as B
+        from paper_2507_18413_gb300 import ct as C
+        B.build()
+        C.load()
+        stream = torch.cuda.current_stream()
+        if args.case == "bulk4e6":
+            print(json.dumps(_bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)))
+        else:
+            print(json.dumps(_bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
