@@ -59,7 +59,7 @@ typedef struct ct_model ct_model;
 /* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
 typedef struct ct_options {
     int32_t entries_per_lane; /* 0 = auto; 1, 2 or 4 currTable chunks per lane of a segment warp */
-    int32_t warps_per_block;  /* 0 = auto (4); 1..16 */
+    int32_t grid_blocks;      /* 0 = auto; CTAs of the cooperative propagation launch (capped at residency) */
     int32_t no_residues;      /* 1 = skip the residue probe and scan for every value */
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
     int32_t reserved[4];
@@ -89,22 +89,26 @@ typedef struct ct_call_stats {
     int32_t reset_vars;     /* of those, masked with the remaining values */
     int32_t rows_ored;      /* supports rows OR-ed by updateTable (sum of k_i) */
     int32_t sup_vars;       /* |s_sup|: scope variables with more than one value */
-    int32_t residue_hits;   /* values found supported by their residue word */
-    int32_t residue_misses; /* values that needed a scan of the index */
+    int32_t residue_hits;   /* values found supported by their residue chunk */
+    int32_t local_found;    /* values found in the 32-chunk windows after a missed residue */
+    int32_t hard;           /* values that needed the full index scan */
+    int32_t windows;        /* 32-chunk windows probed */
     int32_t pruned;         /* values removed by filterDomains */
     int32_t trail_added;    /* trail entries appended */
     int64_t live_chunks_in;  /* non-zero index size at entry (128-bit chunks) */
     int64_t live_chunks_out; /* ... and at exit */
     int64_t live_words_in;   /* non-zero 32-bit currTable words at entry (N) */
+    int64_t update_bytes;    /* algorithmic bytes of updateTable: 4 * N * (rows_ored + 2), 0 if no row */
+    int64_t filter_bytes;    /* algorithmic bytes of filterDomains: 4 * supports words tested */
 } ct_call_stats;
 
-/* Accumulated kernel times (ct_options.profile = 1). */
+/* Accumulated launch times (ct_options.profile = 1): CUDA events recorded on
+ * the table's stream right before and after each propagation launch. */
 typedef struct ct_profile {
     int64_t calls;
-    double plan_ms;   /* change detection: Delta, s_val, s_sup, row plan (Algorithm 1 lines 1-3) */
-    double update_ms; /* updateTable (Algorithm 2) + residue probes */
-    double scan_ms;   /* index scans of missed values + domain write-back (Algorithm 3) */
-    int64_t update_bytes; /* algorithmic bytes of updateTable: 4 * N * (rows_ored + 2), summed */
+    double kernel_ms;     /* sum of the event intervals around the propagation kernel */
+    int64_t update_bytes; /* sum of ct_call_stats.update_bytes */
+    int64_t filter_bytes; /* sum of ct_call_stats.filter_bytes */
 } ct_profile;
 
 /* ---------------------------------------------------------------- table --

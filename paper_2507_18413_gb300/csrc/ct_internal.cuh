@@ -27,13 +27,19 @@ namespace ctk {
 
 constexpr int kMaxArity = 2048;
 constexpr int kMaxDomSize = 65536;
-constexpr int kPlanThreads = 256;
-constexpr int kStatusHdr = 16;  // int32 slots before the changed mask
-constexpr int kModeDelta = 0;   // mask = ~OR(supports[x, a], a in Delta)
-constexpr int kModeReset = 1;   // mask =  OR(supports[x, a], a in dom)
+constexpr int kThreads = 256;          // threads per CTA of the propagation kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kCodeCap = 8192;         // row codes staged in shared memory per CTA
+constexpr int kStatusHdr = 24;         // int32 slots before the changed mask
 constexpr int32_t kNoChunk = 0x7fffffff;
+// Row code of the update plan: supports row | flags.
+constexpr int32_t kCodeLast = 1 << 30;   // last row of its variable: apply the mask
+constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~OR(rows)
+constexpr int32_t kCodeRow = (1 << 29) - 1;
+constexpr int kLocalProbes = 2;          // 32-chunk windows searched after a residue miss
+constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
-// Status block header slots (copied to the host after every call).
+// Status block header slots (written to mapped host memory after every call).
 enum StatusSlot {
     kSlotStatus = 0,
     kSlotLiveOut = 1,
@@ -49,14 +55,9 @@ enum StatusSlot {
     kSlotNreset = 11,
     kSlotTrailAdded = 12,
     kSlotLiveIn = 13,
-};
-
-// One changed scope variable in the update plan.
-struct Group {
-    int32_t row_begin;  // first entry in planRows
-    int32_t row_count;  // k_i
-    int32_t mode;       // kModeDelta / kModeReset
-    int32_t var;        // scope position
+    kSlotLocal = 14,
+    kSlotHard = 15,
+    kSlotWindows = 16,
 };
 
 // Per-table control block: persistent state and per-call counters.
@@ -68,14 +69,14 @@ struct Ctrl {
     uint32_t live;       // per call: chunks alive after updateTable
     uint32_t live_in;    // per call: chunks live at entry
     uint32_t words_in;   // per call: non-zero 32-bit words at entry
-    uint32_t nmiss;      // per call: values whose residue probe missed
-    uint32_t done_update;
-    uint32_t done_scan;
-    int32_t ngroups;
-    int32_t nrows;
+    uint32_t nhard;      // per call: values left for the full index scan
+    uint32_t done;       // last-block-done ticket
+    uint32_t bar_count;  // grid barrier arrivals
+    uint32_t bar_gen;    // grid barrier generation
+    int32_t nrows;       // rows in the update plan
     int32_t nval, ndelta, nreset, nsup;
-    int32_t hits, pruned, trail_added;
-    int32_t pad[13];
+    int32_t hits, pruned, trail_added, local_found, misses, windows;
+    int32_t pad[10];
 };
 
 // Everything a kernel needs, passed by value.
@@ -90,17 +91,16 @@ struct TableDev {
     int32_t* residue;
     uint32_t* lastDom;
     Ctrl* ctrl;
-    Group* groups;
-    int32_t* planRows;
-    int32_t* varSup;
-    int32_t* changed;
-    int32_t* missRow;
-    int32_t* foundChunk;
+    int32_t* codes;          // [R] update plan: row codes
+    int32_t* varSup;         // [arity] 1 if |dom| > 1 (s_sup)
+    int32_t* changed;        // [arity]
+    int32_t* hardRow;        // [R] values left for the full scan
+    int32_t* foundChunk;     // [R]
     const int32_t* rowVar;   // [R] scope position of each row
     const int32_t* varRow0;  // [arity+1] first row of each variable (_supportJmp)
     const int32_t* varNW;    // [arity] words of each domain
     const int32_t* varLD;    // [arity] offset of each domain in lastDom / packed layout
-    int32_t* statusBlk;      // [kStatusHdr + nChangedWords + DW]
+    int32_t* statusBlk;      // [kStatusHdr + nChangedWords + DW], mapped host memory
     int32_t* levelSeg;       // [levelCap][nseg]
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
@@ -108,11 +108,11 @@ struct TableDev {
 
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
 // offset of scope variable i in it. All run on `s` and return the launch error.
-cudaError_t launch_plan(const TableDev& T, const uint32_t* dom, const int32_t* domOff, cudaStream_t s);
-cudaError_t launch_update(const TableDev& T, int E, int wpb, const uint32_t* dom, const int32_t* domOff,
-                          cudaStream_t s);
-cudaError_t launch_scan(const TableDev& T, int E, int wpb, uint32_t* dom, const int32_t* domOff,
-                        cudaStream_t s);
+// The propagation kernel is a cooperative launch of `grid` CTAs that must all
+// be resident at once (grid <= max_coresident_blocks(E)).
+int max_coresident_blocks(int E);
+cudaError_t launch_propagate(const TableDev& T, int E, int grid, uint32_t* dom, const int32_t* domOff,
+                             cudaStream_t s);
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s);
 cudaError_t launch_restore(const TableDev& T, int level, int mark, int top, int newMark, cudaStream_t s);
 cudaError_t launch_set_words(uint32_t* dst, const uint32_t* words, int n, cudaStream_t s);

@@ -1,26 +1,28 @@
 // ct_kernels.cu -- CUDA kernels of Compact-Table propagation for sm_103a.
 //
-// One propagation (Algorithm 1, enforceGAC) is three launches on the table's
-// stream:
-//   plan    1 CTA.  Change detection: Delta_x = lastDom_x & ~dom_x, s_val,
-//                   s_sup, the delta/reset choice of Algorithm 2 (delta iff
-//                   |Delta| < |dom|) and the list of supports rows to OR.
-//   update  one warp per index segment. Algorithm 2 for every live chunk:
-//                   the OR of the planned rows per changed variable
-//                   (complemented on the delta path), AND-ed together and
-//                   into currTable; changed chunks go to the trail; the
-//                   segment's index is compacted with warp ballots (survivors
-//                   first, removed chunks after them, so that a restore only
-//                   resets the count). The last CTA to finish tests
-//                   currTable = 0 (failure) and probes the residue of every
-//                   value of s_sup (Algorithm 3, residues of CT).
-//   scan    one warp per index segment. Values whose residue missed are
-//                   searched in the live chunks (128-bit loads, the segment's
-//                   currTable chunks held in registers); the last CTA removes
-//                   the values nobody supports, stores new residues, writes
-//                   lastDom and the status block.
-// There is no spin-wait anywhere: cross-CTA completion uses the
-// last-block-done pattern (fence + atomic ticket).
+// One propagation (Algorithm 1, enforceGAC) is ONE cooperative launch; its
+// CTAs step through four phases separated by grid barriers:
+//   0 plan     CTA 0: Delta_x = lastDom_x & ~dom_x, s_val, s_sup, the
+//              delta/reset choice of Algorithm 2 (delta iff |Delta| < |dom|)
+//              and the list of supports rows to OR, as row codes.
+//   1 update   one warp per index segment (grid-stride): Algorithm 2 for
+//              every live 128-bit chunk of currTable. The row list is walked
+//              flat across variables with U independent 128-bit loads in
+//              flight per lane; each variable's OR is complemented on the
+//              delta path and AND-ed into the chunk. Changed chunks go to the
+//              trail; the segment's index is compacted with warp ballots
+//              (survivors first, removed chunks after them, so that a restore
+//              only resets the count).
+//   2 probe    Algorithm 1 line 5 (fail when currTable = 0), then one warp
+//              per value of s_sup (Algorithm 3 with residues): the residue
+//              chunk first; on a miss, two 32-chunk windows after it; values
+//              still unresolved go to the hard list.
+//   3 scan     one warp per index segment holds its live chunks in registers
+//              and tests every hard value against them; the last CTA to finish
+//              removes the values no chunk supports, stores new residues,
+//              writes lastDom and the status block (mapped host memory).
+// Grid barriers spin with a bounded iteration count; running out sets
+// CT_ERR_TIMEOUT and every CTA returns.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -56,52 +58,84 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Read-only, keep-in-L1 128-bit load of a supports chunk.
+// Read-only 128-bit load of a supports chunk (the supports never change).
 __device__ __forceinline__ uint4 ld_sup(const uint4* p) { return __ldg(p); }
 
-__device__ void write_header(const TableDev& T, int status) {
-    Ctrl* C = T.ctrl;
-    int32_t* h = T.statusBlk;
-    h[kSlotStatus] = status;
-    h[kSlotLiveOut] = (int32_t)__ldcg(&C->live);
-    h[kSlotWordsIn] = (int32_t)__ldcg(&C->words_in);
-    h[kSlotTrailTop] = __ldcg(&C->trail_top);
-    h[kSlotMisses] = (int32_t)__ldcg(&C->nmiss);
-    h[kSlotPruned] = __ldcg(&C->pruned);
-    h[kSlotHits] = __ldcg(&C->hits);
-    h[kSlotRowsOred] = __ldcg(&C->nrows);
-    h[kSlotNval] = __ldcg(&C->nval);
-    h[kSlotNsup] = __ldcg(&C->nsup);
-    h[kSlotNdelta] = __ldcg(&C->ndelta);
-    h[kSlotNreset] = __ldcg(&C->nreset);
-    h[kSlotTrailAdded] = __ldcg(&C->trail_added);
-    h[kSlotLiveIn] = (int32_t)__ldcg(&C->live_in);
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// ---------------------------------------------------------------------------
-// plan: Algorithm 1 lines 1-3 plus the row selection of Algorithm 2
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPlanThreads)
-ct_plan_kernel(TableDev T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
-    __shared__ int32_t s_k[kMaxArity];     // rows to OR for each variable (0 if unchanged)
-    __shared__ int32_t s_mode[kMaxArity];
-    __shared__ int32_t s_rowOff[kMaxArity];
-    __shared__ int32_t s_grpOff[kMaxArity];
-    __shared__ int32_t s_scanA[kPlanThreads], s_scanB[kPlanThreads];
-    __shared__ int s_grow, s_empty, s_nval, s_ndelta, s_nreset, s_nsup;
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-    Ctrl* C = T.ctrl;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        s_grow = 0; s_empty = 0; s_nval = 0; s_ndelta = 0; s_nreset = 0; s_nsup = 0;
-        C->status = CT_OK;
-        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nmiss = 0u;
-        C->done_update = 0u; C->done_scan = 0u;
-        C->hits = 0; C->pruned = 0; C->trail_added = 0;
+// Grid-wide barrier for a cooperative launch (all CTAs resident). The last CTA
+// to arrive resets the count and advances the generation; the others wait on
+// the generation for at most kBarrierSpinLimit polls. Returns false (and sets
+// CT_ERR_TIMEOUT) when the wait ran out.
+__device__ bool grid_sync(Ctrl* C, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(&C->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            C->bar_count = 0u;
+            __threadfence();
+            st_release(&C->bar_gen, g + 1u);
+        } else {
+            unsigned it = 0;
+            while (ld_acquire(&C->bar_gen) == g) {
+                if (++it > kBarrierSpinLimit) {
+                    ok = 0;
+                    atomicExch(&C->status, CT_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        *s_flag = ok;
     }
     __syncthreads();
+    return *s_flag != 0;
+}
 
-    for (int i = tid; i < T.arity; i += kPlanThreads) {
+struct PlanSmem {
+    int32_t k[kMaxArity];       // rows to OR per variable | kCodeDelta
+    int32_t rowOff[kMaxArity];  // first code of each variable
+    int32_t scan[kThreads];
+    int flags[8];               // grow, empty, nval, ndelta, nreset, nsup
+};
+
+struct Smem {
+    union {
+        PlanSmem plan;
+        int32_t codes[kCodeCap];
+    } u;
+    uint32_t cnt[12];
+    int flag[4];
+};
+
+enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin };
+
+// ---------------------------------------------------------------------------
+// phase 0: Algorithm 1 lines 1-3 and the row selection of Algorithm 2 (CTA 0)
+// ---------------------------------------------------------------------------
+__device__ void plan_block(const TableDev& T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
+                           PlanSmem& P) {
+    Ctrl* C = T.ctrl;
+    const int tid = threadIdx.x;
+    if (tid < 8) P.flags[tid] = 0;
+    if (tid == 0) {
+        C->status = CT_OK;
+        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u;
+        C->hits = 0; C->pruned = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < T.arity; i += kThreads) {
         const int nw = T.varNW[i];
         const uint32_t* d = dom + domOff[i];
         const uint32_t* l = T.lastDom + T.varLD[i];
@@ -115,403 +149,456 @@ ct_plan_kernel(TableDev T, const uint32_t* __restrict__ dom, const int32_t* __re
         }
         T.changed[i] = 0;
         T.varSup[i] = nd > 1;
-        if (grow) atomicExch(&s_grow, 1);
-        if (nd == 0) atomicExch(&s_empty, 1);
-        if (nd > 1) atomicAdd(&s_nsup, 1);
-        int k = 0, mode = kModeReset;
+        if (grow) atomicExch(&P.flags[0], 1);
+        if (nd == 0) atomicExch(&P.flags[1], 1);
+        if (nd > 1) atomicAdd(&P.flags[5], 1);
+        int k = 0;
         if (ndel > 0) {
             // Algorithm 2, line 3: the delta mask when |Delta| < |dom| (strict).
-            if (ndel < nd) { k = ndel; mode = kModeDelta; atomicAdd(&s_ndelta, 1); }
-            else { k = nd; mode = kModeReset; atomicAdd(&s_nreset, 1); }
-            atomicAdd(&s_nval, 1);
+            if (ndel < nd) { k = ndel | kCodeDelta; atomicAdd(&P.flags[3], 1); }
+            else { k = nd; atomicAdd(&P.flags[4], 1); }
+            atomicAdd(&P.flags[2], 1);
         }
-        s_k[i] = k;
-        s_mode[i] = mode;
+        P.k[i] = k;
     }
     __syncthreads();
-    // A grown domain (including stray bits above dom_size) or an empty one ends
-    // the call here, before any row is listed.
-    if (s_grow || s_empty) {
+    if (P.flags[0] || P.flags[1]) {
+        // A grown domain (stray bits above dom_size included) or an empty one
+        // ends the call before any row is listed.
         if (tid == 0) {
-            C->nval = s_nval; C->ndelta = s_ndelta; C->nreset = s_nreset; C->nsup = s_nsup;
-            C->ngroups = 0; C->nrows = 0;
-            C->status = s_grow ? CT_ERR_STATE : CT_INFEASIBLE;
+            C->nval = P.flags[2]; C->ndelta = P.flags[3]; C->nreset = P.flags[4]; C->nsup = P.flags[5];
+            C->nrows = 0;
+            C->status = P.flags[0] ? CT_ERR_STATE : CT_INFEASIBLE;
         }
         return;
     }
-
-    // Exclusive scans of k (row offsets) and of [k > 0] (group slots), each
-    // thread owning a contiguous run of variables.
-    const int per = (T.arity + kPlanThreads - 1) / kPlanThreads;
+    // Exclusive scan of the row counts, each thread owning a run of variables.
+    const int per = (T.arity + kThreads - 1) / kThreads;
     const int b0 = tid * per, b1 = min(T.arity, b0 + per);
-    int sumA = 0, sumB = 0;
-    for (int i = b0; i < b1; ++i) { sumA += s_k[i]; sumB += s_k[i] > 0; }
-    s_scanA[tid] = sumA;
-    s_scanB[tid] = sumB;
+    int sum = 0;
+    for (int i = b0; i < b1; ++i) sum += P.k[i] & kCodeRow;
+    P.scan[tid] = sum;
     __syncthreads();
-    for (int off = 1; off < kPlanThreads; off <<= 1) {
-        int a = 0, b = 0;
-        if (tid >= off) { a = s_scanA[tid - off]; b = s_scanB[tid - off]; }
+    for (int off = 1; off < kThreads; off <<= 1) {
+        const int a = tid >= off ? P.scan[tid - off] : 0;
         __syncthreads();
-        s_scanA[tid] += a;
-        s_scanB[tid] += b;
+        P.scan[tid] += a;
         __syncthreads();
     }
-    int runA = s_scanA[tid] - sumA, runB = s_scanB[tid] - sumB;
+    int run = P.scan[tid] - sum;
     for (int i = b0; i < b1; ++i) {
-        s_rowOff[i] = runA;
-        s_grpOff[i] = runB;
-        runA += s_k[i];
-        runB += s_k[i] > 0;
+        P.rowOff[i] = run;
+        run += P.k[i] & kCodeRow;
     }
     __syncthreads();
-
-    // Rows of each changed variable: the removed values (delta) or the
-    // remaining ones (reset).
-    for (int i = tid; i < T.arity; i += kPlanThreads) {
-        const int k = s_k[i];
+    // Codes: the removed values (delta) or the remaining ones (reset).
+    for (int i = tid; i < T.arity; i += kThreads) {
+        const int k = P.k[i] & kCodeRow;
         if (k == 0) continue;
+        const bool delta = (P.k[i] & kCodeDelta) != 0;
         const int nw = T.varNW[i];
         const uint32_t* d = dom + domOff[i];
         const uint32_t* l = T.lastDom + T.varLD[i];
         const int row0 = T.varRow0[i];
-        int out = s_rowOff[i];
+        int out = P.rowOff[i];
+        const int last = out + k - 1;
         for (int q = 0; q < nw; ++q) {
-            uint32_t bits = (s_mode[i] == kModeDelta) ? (l[q] & ~d[q]) : d[q];
+            uint32_t bits = delta ? (l[q] & ~d[q]) : d[q];
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                T.planRows[out++] = row0 + q * 32 + b;
+                int code = row0 + q * 32 + b;
+                if (delta) code |= kCodeDelta;
+                if (out == last) code |= kCodeLast;
+                T.codes[out++] = code;
             }
         }
-        Group g;
-        g.row_begin = s_rowOff[i];
-        g.row_count = k;
-        g.mode = s_mode[i];
-        g.var = i;
-        T.groups[s_grpOff[i]] = g;
-    }
-    if (tid == kPlanThreads - 1) {
-        C->ngroups = s_scanB[kPlanThreads - 1];
-        C->nrows = s_scanA[kPlanThreads - 1];
     }
     __syncthreads();
-    if (tid == 0) { C->nval = s_nval; C->ndelta = s_ndelta; C->nreset = s_nreset; C->nsup = s_nsup; }
+    if (tid == 0) {
+        C->nrows = P.scan[kThreads - 1];
+        C->nval = P.flags[2]; C->ndelta = P.flags[3]; C->nreset = P.flags[4]; C->nsup = P.flags[5];
+    }
 }
 
 // ---------------------------------------------------------------------------
-// update: Algorithm 2 over the live chunks, trail, index compaction; the last
-// CTA tests for failure and probes residues.
+// phase 1: Algorithm 2 on one index segment
 // ---------------------------------------------------------------------------
-template <int E>
-__global__ void __launch_bounds__(512)
-ct_update_kernel(TableDev T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
-    Ctrl* C = T.ctrl;
-    if (C->status != CT_OK) return;
-
-    __shared__ uint32_t s_live, s_livein, s_words, s_trail;
-    __shared__ int s_last;
-    if (threadIdx.x == 0) { s_live = 0u; s_livein = 0u; s_words = 0u; s_trail = 0u; }
-    __syncthreads();
-
+template <int E, int U>
+__device__ __forceinline__ void update_segment(const TableDev& T, int seg, int nrows, const int32_t* s_codes,
+                                               int mark, int cap, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
-    const int seg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int ngroups = C->ngroups;
-
-    if (seg < T.nseg) {
-        const int c = T.segCnt[seg];
-        const int base = seg * T.S;
-        int32_t* idx = T.idx + base;
-        if (ngroups == 0) {
-            if (lane == 0) { atomicAdd(&s_live, (uint32_t)c); atomicAdd(&s_livein, (uint32_t)c); }
-        } else {
-            bool act[E];
-            int w[E];
-            uint4 cur[E], acc[E];
-            uint32_t words = 0u;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                act[e] = e * 32 + lane < c;
-                w[e] = act[e] ? idx[e * 32 + lane] : 0;
-            }
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                cur[e] = act[e] ? T.curr[w[e]] : make_uint4(0u, 0u, 0u, 0u);
-                acc[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
-                words += nzwords(cur[e]);
-            }
-            const size_t W4 = (size_t)T.W4;
-            for (int g = 0; g < ngroups; ++g) {
-                const Group G = T.groups[g];
-                const int32_t* rows = T.planRows + G.row_begin;
-                uint4 m[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) m[e] = make_uint4(0u, 0u, 0u, 0u);
-                int q = 0;
-                for (; q + 4 <= G.row_count; q += 4) {
-                    const uint4* r0 = T.sup + (size_t)rows[q] * W4;
-                    const uint4* r1 = T.sup + (size_t)rows[q + 1] * W4;
-                    const uint4* r2 = T.sup + (size_t)rows[q + 2] * W4;
-                    const uint4* r3 = T.sup + (size_t)rows[q + 3] * W4;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        if (act[e]) {
-                            const uint4 a0 = ld_sup(r0 + w[e]);
-                            const uint4 a1 = ld_sup(r1 + w[e]);
-                            const uint4 a2 = ld_sup(r2 + w[e]);
-                            const uint4 a3 = ld_sup(r3 + w[e]);
-                            m[e] = or4(m[e], or4(or4(a0, a1), or4(a2, a3)));
-                        }
-                    }
-                }
-                for (; q < G.row_count; ++q) {
-                    const uint4* r0 = T.sup + (size_t)rows[q] * W4;
-#pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if (act[e]) m[e] = or4(m[e], ld_sup(r0 + w[e]));
-                }
-                const bool delta = G.mode == kModeDelta;
-                bool any = false;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    acc[e] = and4(acc[e], delta ? not4(m[e]) : m[e]);
-                    any |= act[e] && nz(and4(acc[e], cur[e]));
-                }
-                // Every chunk of this warp is already zero: later masks cannot revive it.
-                if (!__any_sync(0xffffffffu, any)) break;
-            }
-
-            const int mark = C->cur_mark;
-            bool alive[E], need[E];
-            int prev[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const uint4 nv = and4(cur[e], acc[e]);
-                const bool chg = act[e] && !eq4(nv, cur[e]);
-                alive[e] = act[e] && nz(nv);
-                if (chg) T.curr[w[e]] = nv;
-                prev[e] = (chg && mark >= 0) ? T.lastpos[w[e]] : 0x7fffffff;
-                need[e] = chg && mark >= 0 && prev[e] < mark;
-            }
-
-            // Trail: one reservation per warp.
-            uint32_t nb[E];
-            int ntr = 0;
-#pragma unroll
-            for (int e = 0; e < E; ++e) { nb[e] = __ballot_sync(0xffffffffu, need[e]); ntr += __popc(nb[e]); }
-            if (ntr) {
-                int tb = 0;
-                if (lane == 0) tb = atomicAdd(&C->trail_top, ntr);
-                tb = __shfl_sync(0xffffffffu, tb, 0);
-                if (tb + ntr > C->trail_cap) {
-                    if (lane == 0) atomicExch(&C->status, CT_ERR_OOM);
-                } else {
-                    int off = tb;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        if (need[e]) {
-                            const int p = off + __popc(nb[e] & lanemask_lt());
-                            T.trailKey[p] = make_int2(w[e], prev[e]);
-                            T.trailOld[p] = cur[e];
-                            T.lastpos[w[e]] = p;
-                        }
-                        off += __popc(nb[e]);
-                    }
-                }
-            }
-
-            // Stable partition of the segment: survivors first, removed after.
-            uint32_t ab[E];
-            int nal = 0;
-#pragma unroll
-            for (int e = 0; e < E; ++e) { ab[e] = __ballot_sync(0xffffffffu, alive[e]); nal += __popc(ab[e]); }
-            if (nal != c) {
-                int before = 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if (act[e]) {
-                        const int sb = before + __popc(ab[e] & lanemask_lt());
-                        const int pos = e * 32 + lane;
-                        idx[alive[e] ? sb : nal + (pos - sb)] = w[e];
-                    }
-                    before += __popc(ab[e]);
-                }
-                if (lane == 0) T.segCnt[seg] = nal;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(0xffffffffu, words, o);
-            if (lane == 0) {
-                atomicAdd(&s_live, (uint32_t)nal);
-                atomicAdd(&s_livein, (uint32_t)c);
-                atomicAdd(&s_words, words);
-                atomicAdd(&s_trail, (uint32_t)ntr);
-            }
-        }
-    }
-
-    // Last-block-done: every thread fences its own writes before the ticket.
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&C->live, s_live);
-        atomicAdd(&C->live_in, s_livein);
-        atomicAdd(&C->words_in, s_words);
-        if (s_trail) atomicAdd(&C->trail_added, (int)s_trail);
-        __threadfence();
-        const unsigned t = atomicAdd(&C->done_update, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-
-    // Algorithm 1, line 5: fail when currTable is all zero.
-    if (__ldcg(&C->live) == 0u) {
-        if (threadIdx.x == 0) atomicExch(&C->status, CT_INFEASIBLE);
+    Ctrl* C = T.ctrl;
+    const int c = T.segCnt[seg];
+    int32_t* idx = T.idx + (size_t)seg * T.S;
+    if (nrows == 0) {
+        if (lane == 0) { atomicAdd(&s_cnt[kCntLive], (uint32_t)c); atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)c); }
         return;
     }
-    if (__ldcg(&C->status) != CT_OK) return;
-
-    // Residue probes for every value of s_sup (Algorithm 3 with residues).
-    __shared__ int s_hits;
-    if (threadIdx.x == 0) s_hits = 0;
-    __syncthreads();
+    if (c == 0) return;
+    bool act[E];
+    int w[E];
+    uint4 cur[E], acc[E], m[E];
+    uint32_t words = 0u;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        act[e] = e * 32 + lane < c;
+        w[e] = act[e] ? idx[e * 32 + lane] : 0;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        cur[e] = act[e] ? T.curr[w[e]] : make_uint4(0u, 0u, 0u, 0u);
+        acc[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        m[e] = make_uint4(0u, 0u, 0u, 0u);
+        words += nzwords(cur[e]);
+    }
     const size_t W4 = (size_t)T.W4;
-    int hits = 0;
-    for (int r = threadIdx.x; r < T.R; r += blockDim.x) {
-        const int i = T.rowVar[r];
-        if (!T.varSup[i]) continue;
-        const int a = r - T.varRow0[i];
-        if (!((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u)) continue;
-        bool hit = false;
-        if (T.useResidues) {
-            const int res = T.residue[r];
-            hit = nz(and4(ld_sup(T.sup + (size_t)r * W4 + res), __ldcg(T.curr + res)));
+    for (int q0 = 0; q0 < nrows; q0 += U) {
+        int code[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u;
+            code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
         }
-        if (hit) {
-            ++hits;
+        uint4 v[U][E];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint4* row = T.sup + (size_t)(code[u] & kCodeRow) * W4;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                v[u][e] = (act[e] && q0 + u < nrows) ? ld_sup(row + w[e]) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (q0 + u < nrows) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) m[e] = or4(m[e], v[u][e]);
+                if (code[u] & kCodeLast) {
+                    const bool delta = (code[u] & kCodeDelta) != 0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        acc[e] = and4(acc[e], delta ? not4(m[e]) : m[e]);
+                        m[e] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) any |= act[e] && nz(and4(acc[e], cur[e]));
+        // Every chunk of this warp is already zero: later masks cannot revive it.
+        if (!__any_sync(0xffffffffu, any)) break;
+    }
+
+    bool alive[E], need[E];
+    int prev[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint4 nv = and4(cur[e], acc[e]);
+        const bool chg = act[e] && !eq4(nv, cur[e]);
+        alive[e] = act[e] && nz(nv);
+        if (chg) T.curr[w[e]] = nv;
+        prev[e] = (chg && mark >= 0) ? T.lastpos[w[e]] : 0x7fffffff;
+        need[e] = chg && mark >= 0 && prev[e] < mark;
+    }
+    // Trail: one reservation per warp.
+    uint32_t nb[E];
+    int ntr = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        nb[e] = __ballot_sync(0xffffffffu, need[e]);
+        ntr += __popc(nb[e]);
+    }
+    if (ntr) {
+        int tb = 0;
+        if (lane == 0) tb = atomicAdd(&C->trail_top, ntr);
+        tb = __shfl_sync(0xffffffffu, tb, 0);
+        if (tb + ntr > cap) {
+            if (lane == 0) atomicExch(&C->status, CT_ERR_OOM);
         } else {
-            const unsigned m = atomicAdd(&C->nmiss, 1u);
-            T.missRow[m] = r;
-            T.foundChunk[m] = kNoChunk;
+            int off = tb;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (need[e]) {
+                    const int p = off + __popc(nb[e] & lanemask_lt());
+                    T.trailKey[p] = make_int2(w[e], prev[e]);
+                    T.trailOld[p] = cur[e];
+                    T.lastpos[w[e]] = p;
+                }
+                off += __popc(nb[e]);
+            }
         }
     }
-    if (hits) atomicAdd(&s_hits, hits);
-    __syncthreads();
-    if (threadIdx.x == 0) C->hits = s_hits;
-}
-
-// ---------------------------------------------------------------------------
-// scan: search the live chunks for the values whose residue missed; the last
-// CTA applies the result (Algorithm 3) and writes the status block.
-// ---------------------------------------------------------------------------
-template <int E>
-__global__ void __launch_bounds__(512)
-ct_scan_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
-    Ctrl* C = T.ctrl;
-    const int st = C->status;
-    if (st != CT_OK) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) write_header(T, st);
-        return;
+    // Stable partition of the segment: survivors first, removed after.
+    uint32_t ab[E];
+    int nal = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        ab[e] = __ballot_sync(0xffffffffu, alive[e]);
+        nal += __popc(ab[e]);
     }
-    __shared__ int s_last, s_pruned;
-
-    const int lane = threadIdx.x & 31;
-    const int seg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nm = (int)C->nmiss;
-
-    if (nm > 0 && seg < T.nseg) {
-        const int c = T.segCnt[seg];
-        const int32_t* idx = T.idx + seg * T.S;
-        bool act[E];
-        int w[E];
-        uint4 cur[E];
+    if (nal != c) {
+        int before = 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            act[e] = e * 32 + lane < c;
-            w[e] = act[e] ? idx[e * 32 + lane] : 0;
-            cur[e] = act[e] ? T.curr[w[e]] : make_uint4(0u, 0u, 0u, 0u);
+            if (act[e]) {
+                const int sb = before + __popc(ab[e] & lanemask_lt());
+                const int pos = e * 32 + lane;
+                idx[alive[e] ? sb : nal + (pos - sb)] = w[e];
+            }
+            before += __popc(ab[e]);
         }
-        if (__any_sync(0xffffffffu, act[0])) {
-            const size_t W4 = (size_t)T.W4;
-            constexpr int U = 4;
-            for (int m0 = 0; m0 < nm; m0 += U) {
-                int cand[U];
+        if (lane == 0) T.segCnt[seg] = nal;
+    }
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    cand[k] = kNoChunk;
-                    if (m0 + k < nm) {
-                        const uint4* row = T.sup + (size_t)T.missRow[m0 + k] * W4;
-#pragma unroll
-                        for (int e = 0; e < E; ++e)
-                            if (act[e] && nz(and4(ld_sup(row + w[e]), cur[e]))) cand[k] = min(cand[k], w[e]);
-                    }
+    for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(0xffffffffu, words, o);
+    if (lane == 0) {
+        atomicAdd(&s_cnt[kCntLive], (uint32_t)nal);
+        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)c);
+        atomicAdd(&s_cnt[kCntWords], words);
+        atomicAdd(&s_cnt[kCntTrail], (uint32_t)ntr);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 2: residue probe of one value (warp per supports row)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void probe_row(const TableDev& T, int r, const uint32_t* __restrict__ dom,
+                                          const int32_t* __restrict__ domOff, uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    const int i = T.rowVar[r];
+    if (!__ldcg(&T.varSup[i])) return;
+    const int a = r - T.varRow0[i];
+    if (!((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u)) return;
+    const int W4 = T.W4;
+    const uint4* row = T.sup + (size_t)r * W4;
+    if (T.useResidues) {
+        const int res = T.residue[r];
+        bool hit = false;
+        if (lane == 0) hit = nz(and4(ld_sup(row + res), __ldcg(T.curr + res)));
+        if (__shfl_sync(0xffffffffu, hit, 0)) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
+            return;
+        }
+        // Windows of 32 chunks following the residue.
+        for (int b = 0; b < kLocalProbes; ++b) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
+            const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
+            const bool h = nz(and4(ld_sup(row + c), __ldcg(T.curr + c)));
+            const unsigned bal = __ballot_sync(0xffffffffu, h);
+            if (bal) {
+                const int cf = __shfl_sync(0xffffffffu, c, __ffs(bal) - 1);
+                if (lane == 0) {
+                    T.residue[r] = cf;
+                    atomicAdd(&s_cnt[kCntLocal], 1u);
                 }
-#pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    if (m0 + k < nm) {
-                        const int mn = __reduce_min_sync(0xffffffffu, cand[k]);
-                        if (lane == 0 && mn != kNoChunk) atomicMin(&T.foundChunk[m0 + k], mn);
-                    }
-                }
+                return;
             }
         }
     }
-
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(&C->done_scan, 1u);
-        s_last = (t == gridDim.x - 1);
-        s_pruned = 0;
+    if (lane == 0) {
+        const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
+        T.hardRow[m] = r;
+        T.foundChunk[m] = kNoChunk;
+        atomicAdd(&s_cnt[kCntMiss], 1u);
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+}
 
-    // Apply: a value with no supporting chunk leaves its domain (Algorithm 3 line 4).
-    int pruned = 0;
-    for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-        const int r = __ldcg(&T.missRow[m]);
-        const int fc = __ldcg(&T.foundChunk[m]);
-        if (fc != kNoChunk) {
-            T.residue[r] = fc;
-        } else {
-            const int i = T.rowVar[r];
-            const int a = r - T.varRow0[i];
-            atomicAnd(&dom[domOff[i] + (a >> 5)], ~(1u << (a & 31)));
-            T.changed[i] = 1;
-            ++pruned;
+// ---------------------------------------------------------------------------
+// phase 3: full index scan of the hard values over one segment
+// ---------------------------------------------------------------------------
+template <int E, int U>
+__device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh, const int32_t* s_rows) {
+    const int lane = threadIdx.x & 31;
+    const int c = __ldcg(&T.segCnt[seg]);
+    if (c == 0) return;
+    const int32_t* idx = T.idx + (size_t)seg * T.S;
+    bool act[E];
+    int w[E];
+    uint4 cur[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        act[e] = e * 32 + lane < c;
+        w[e] = act[e] ? __ldcg(idx + e * 32 + lane) : 0;
+        cur[e] = act[e] ? __ldcg(T.curr + w[e]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    const size_t W4 = (size_t)T.W4;
+    for (int m0 = 0; m0 < nh; m0 += U) {
+        int cand[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cand[u] = kNoChunk;
+            const int mm = m0 + u;
+            if (mm < nh) {
+                const int r = mm < kCodeCap ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
+                const uint4* row = T.sup + (size_t)r * W4;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (act[e] && nz(and4(ld_sup(row + w[e]), cur[e]))) cand[u] = min(cand[u], w[e]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (m0 + u < nh) {
+                const int mn = __reduce_min_sync(0xffffffffu, cand[u]);
+                if (lane == 0 && mn != kNoChunk) atomicMin(&T.foundChunk[m0 + u], mn);
+            }
         }
     }
-    if (pruned) atomicAdd(&s_pruned, pruned);
-    __syncthreads();
+}
 
-    // lastDom := the filtered domains (lastSizes update of Algorithm 3 line 5);
-    // the same words go to the status block for the host.
-    uint32_t* outDom = reinterpret_cast<uint32_t*>(T.statusBlk + kStatusHdr + T.nChangedWords);
-    for (int i = threadIdx.x; i < T.arity; i += blockDim.x) {
-        const int nw = T.varNW[i];
-        const uint32_t* d = dom + domOff[i];
-        uint32_t* l = T.lastDom + T.varLD[i];
-        uint32_t* o = outDom + T.varLD[i];
-        for (int q = 0; q < nw; ++q) {
-            const uint32_t v = __ldcg(d + q);
-            l[q] = v;
-            o[q] = v;
+// ---------------------------------------------------------------------------
+// last CTA: apply Algorithm 3's removals and publish the result
+// ---------------------------------------------------------------------------
+__device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
+                         Smem& sm) {
+    Ctrl* C = T.ctrl;
+    const int tid = threadIdx.x;
+    const int st = __ldcg(&C->status);
+    int32_t* H = T.statusBlk;
+    if (tid == 0) sm.cnt[kCntPruned] = 0u;
+    __syncthreads();
+    if (st == CT_OK) {
+        const int nh = (int)__ldcg(&C->nhard);
+        uint32_t pruned = 0;
+        for (int m = tid; m < nh; m += kThreads) {
+            const int r = __ldcg(&T.hardRow[m]);
+            const int fc = __ldcg(&T.foundChunk[m]);
+            if (fc != kNoChunk) {
+                T.residue[r] = fc;
+            } else {
+                const int i = T.rowVar[r];
+                const int a = r - T.varRow0[i];
+                atomicAnd(&dom[domOff[i] + (a >> 5)], ~(1u << (a & 31)));
+                T.changed[i] = 1;
+                ++pruned;
+            }
+        }
+        if (pruned) atomicAdd(&sm.cnt[kCntPruned], pruned);
+        __syncthreads();
+        // lastDom := the filtered domains (lastSizes of Algorithm 3 line 5);
+        // the same words go to the host.
+        uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kStatusHdr + T.nChangedWords);
+        for (int i = tid; i < T.arity; i += kThreads) {
+            const int nw = T.varNW[i];
+            const uint32_t* d = dom + domOff[i];
+            uint32_t* l = T.lastDom + T.varLD[i];
+            uint32_t* o = outDom + T.varLD[i];
+            for (int q = 0; q < nw; ++q) {
+                const uint32_t v = __ldcg(d + q);
+                l[q] = v;
+                o[q] = v;
+            }
+        }
+        for (int q = tid; q < T.nChangedWords; q += kThreads) {
+            uint32_t bits = 0u;
+            for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b)
+                if (__ldcg(&T.changed[q * 32 + b])) bits |= 1u << b;
+            H[kStatusHdr + q] = (int32_t)bits;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        H[kSlotLiveOut] = (int32_t)__ldcg(&C->live);
+        H[kSlotWordsIn] = (int32_t)__ldcg(&C->words_in);
+        H[kSlotTrailTop] = __ldcg(&C->trail_top);
+        H[kSlotMisses] = __ldcg(&C->misses);
+        H[kSlotPruned] = (int32_t)sm.cnt[kCntPruned];
+        H[kSlotHits] = __ldcg(&C->hits);
+        H[kSlotRowsOred] = __ldcg(&C->nrows);
+        H[kSlotNval] = __ldcg(&C->nval);
+        H[kSlotNsup] = __ldcg(&C->nsup);
+        H[kSlotNdelta] = __ldcg(&C->ndelta);
+        H[kSlotNreset] = __ldcg(&C->nreset);
+        H[kSlotTrailAdded] = __ldcg(&C->trail_added);
+        H[kSlotLiveIn] = (int32_t)__ldcg(&C->live_in);
+        H[kSlotLocal] = __ldcg(&C->local_found);
+        H[kSlotHard] = (int32_t)__ldcg(&C->nhard);
+        H[kSlotWindows] = __ldcg(&C->windows);
+        C->pruned = (int32_t)sm.cnt[kCntPruned];
+        __threadfence_system();
+        H[kSlotStatus] = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the propagation kernel
+// ---------------------------------------------------------------------------
+template <int E, int U>
+__global__ void __launch_bounds__(kThreads, 2)
+ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
+    __shared__ Smem sm;
+    Ctrl* C = T.ctrl;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // phase 0
+    if (blockIdx.x == 0) plan_block(T, dom, domOff, sm.u.plan);
+    if (!grid_sync(C, &sm.flag[0])) return;
+    const int status0 = __ldcg(&C->status);
+    const int nrows = __ldcg(&C->nrows);
+
+    // phase 1
+    if (tid < 12) sm.cnt[tid] = 0u;
+    if (status0 == CT_OK) {
+        const int staged = min(nrows, kCodeCap);
+        for (int q = tid; q < staged; q += kThreads) sm.u.codes[q] = __ldcg(&T.codes[q]);
+        __syncthreads();
+        const int mark = __ldcg(&C->cur_mark);
+        const int cap = __ldcg(&C->trail_cap);
+        for (int seg = blockIdx.x * kWarps + warp; seg < T.nseg; seg += gridDim.x * kWarps)
+            update_segment<E, U>(T, seg, nrows, sm.u.codes, mark, cap, sm.cnt);
+        __syncthreads();
+        if (tid == 0) {
+            atomicAdd(&C->live, sm.cnt[kCntLive]);
+            atomicAdd(&C->live_in, sm.cnt[kCntLiveIn]);
+            atomicAdd(&C->words_in, sm.cnt[kCntWords]);
+            if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
         }
     }
-    for (int q = threadIdx.x; q < T.nChangedWords; q += blockDim.x) {
-        uint32_t bits = 0u;
-        for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b)
-            if (T.changed[q * 32 + b]) bits |= 1u << b;
-        T.statusBlk[kStatusHdr + q] = (int32_t)bits;
+    if (!grid_sync(C, &sm.flag[0])) return;
+
+    // phase 2: failure test (Algorithm 1 line 5), then residue probes
+    const int status1 = __ldcg(&C->status);
+    const uint32_t live = __ldcg(&C->live);
+    const bool run = status1 == CT_OK && live > 0u;
+    if (status1 == CT_OK && live == 0u && blockIdx.x == 0 && tid == 0) atomicExch(&C->status, CT_INFEASIBLE);
+    if (tid < 12) sm.cnt[tid] = 0u;
+    __syncthreads();
+    if (run) {
+        for (int r = blockIdx.x * kWarps + warp; r < T.R; r += gridDim.x * kWarps) probe_row(T, r, dom, domOff, sm.cnt);
+        __syncthreads();
+        if (tid == 0) {
+            if (sm.cnt[kCntHits]) atomicAdd(&C->hits, (int)sm.cnt[kCntHits]);
+            if (sm.cnt[kCntLocal]) atomicAdd(&C->local_found, (int)sm.cnt[kCntLocal]);
+            if (sm.cnt[kCntMiss]) atomicAdd(&C->misses, (int)sm.cnt[kCntMiss]);
+            if (sm.cnt[kCntWin]) atomicAdd(&C->windows, (int)sm.cnt[kCntWin]);
+        }
     }
-    if (threadIdx.x == 0) {
-        C->pruned = s_pruned;
-        write_header(T, CT_OK);
-        T.statusBlk[kSlotPruned] = s_pruned;
+    if (!grid_sync(C, &sm.flag[0])) return;
+
+    // phase 3
+    const int nh = run ? (int)__ldcg(&C->nhard) : 0;
+    if (nh > 0) {
+        const int staged = min(nh, kCodeCap);
+        for (int q = tid; q < staged; q += kThreads) sm.u.codes[q] = __ldcg(&T.hardRow[q]);
+        __syncthreads();
+        for (int seg = blockIdx.x * kWarps + warp; seg < T.nseg; seg += gridDim.x * kWarps)
+            scan_segment<E, U>(T, seg, nh, sm.u.codes);
     }
+    (void)lane;
+
+    // last-block-done
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned t = atomicAdd(&C->done, 1u);
+        sm.flag[1] = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!sm.flag[1]) return;
+    __threadfence();
+    finalize(T, dom, domOff, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,35 +651,46 @@ __global__ void ct_copy_words_kernel(uint32_t* dst, const uint32_t* src, int n) 
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) dst[q] = src[q];
 }
 
+template <int E, int U>
+cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, cudaStream_t s) {
+    TableDev t = T;
+    void* args[] = {&t, &dom, (void*)&domOff};
+    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<E, U>, dim3(grid), dim3(kThreads), args, 0,
+                                       s);
+}
+
+template <int E, int U>
+int coresident() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<E, U>, kThreads, 0) != cudaSuccess)
+        return 0;
+    return per * sms;
+}
+
 }  // namespace
 
-cudaError_t launch_plan(const TableDev& T, const uint32_t* dom, const int32_t* domOff, cudaStream_t s) {
-    ct_plan_kernel<<<1, kPlanThreads, 0, s>>>(T, dom, domOff);
-    return cudaGetLastError();
+int max_coresident_blocks(int E) {
+    int r = 0;
+    switch (E) {
+        case 1: r = coresident<1, 16>(); break;
+        case 2: r = coresident<2, 8>(); break;
+        case 4: r = coresident<4, 4>(); break;
+        default: r = 0;
+    }
+    cudaGetLastError();
+    return r;
 }
 
-cudaError_t launch_update(const TableDev& T, int E, int wpb, const uint32_t* dom, const int32_t* domOff,
-                          cudaStream_t s) {
-    const int grid = (T.nseg + wpb - 1) / wpb;
+cudaError_t launch_propagate(const TableDev& T, int E, int grid, uint32_t* dom, const int32_t* domOff,
+                             cudaStream_t s) {
     switch (E) {
-        case 1: ct_update_kernel<1><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
-        case 2: ct_update_kernel<2><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
-        case 4: ct_update_kernel<4><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
+        case 1: return launch_coop<1, 16>(T, grid, dom, domOff, s);
+        case 2: return launch_coop<2, 8>(T, grid, dom, domOff, s);
+        case 4: return launch_coop<4, 4>(T, grid, dom, domOff, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scan(const TableDev& T, int E, int wpb, uint32_t* dom, const int32_t* domOff,
-                        cudaStream_t s) {
-    const int grid = (T.nseg + wpb - 1) / wpb;
-    switch (E) {
-        case 1: ct_scan_kernel<1><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
-        case 2: ct_scan_kernel<2><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
-        case 4: ct_scan_kernel<4><<<grid, wpb * 32, 0, s>>>(T, dom, domOff); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

@@ -57,7 +57,7 @@ struct ct_table {
     std::vector<int32_t> lo, size, nw, ld, row0, rowVar;
     int R = 0;
     int64_t t = 0, W = 0, W4 = 0;
-    int nseg = 0, S = 32, E = 1, wpb = 4, DW = 0, nChW = 0;
+    int nseg = 0, S = 32, E = 1, grid = 1, DW = 0, nChW = 0;
     TableDev dev{};
     cudaStream_t stream = nullptr;
     bool ownStream = false;
@@ -70,7 +70,7 @@ struct ct_table {
     bool empty = false;
     ct_call_stats last{};
     bool profile = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     ct_profile prof{};
     int64_t deviceBytes = 0;
     uint32_t* d_domScratch = nullptr;
@@ -114,7 +114,7 @@ int choose_entries_per_lane(int64_t W4, int requested) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
     }
     cudaGetLastError();
-    // Enough segments to give every SM several warps before growing segments.
+    // One 32-chunk segment per warp until every SM holds 16 warps of them.
     const int64_t cap = 16LL * sms;
     if ((W4 + 31) / 32 <= cap) return 1;
     if ((W4 + 63) / 64 <= cap) return 2;
@@ -256,7 +256,6 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     ct->E = choose_entries_per_lane(W4, opt ? opt->entries_per_lane : 0);
     ct->S = 32 * ct->E;
     ct->nseg = (int)((W4 + ct->S - 1) / ct->S);
-    ct->wpb = (opt && opt->warps_per_block >= 1 && opt->warps_per_block <= 16) ? opt->warps_per_block : 4;
 
     // supports rows (Sec. 2), value-major, 16-byte aligned rows of W4 chunks
     const size_t rowWords = (size_t)W4 * 4;
@@ -312,18 +311,16 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = dalloc(ct, &d.residue, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.lastDom, (size_t)DW)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.groups, (size_t)n)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.planRows, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.codes, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.varSup, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.changed, (size_t)n)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.missRow, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.hardRow, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.foundChunk, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &rowVar, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &varRow0, (size_t)n + 1)) != CT_OK) return st;
     if ((st = dalloc(ct, &varNW, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &varLD, (size_t)n)) != CT_OK) return st;
     ct->statusInts = (size_t)kStatusHdr + ct->nChW + DW;
-    if ((st = dalloc(ct, &d.statusBlk, ct->statusInts)) != CT_OK) return st;
     if ((st = dalloc(ct, &ct->d_domScratch, (size_t)DW)) != CT_OK) return st;
     d.sup = sup;
     d.rowVar = rowVar;
@@ -339,7 +336,9 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     d.nChangedWords = ct->nChW;
     d.useResidues = (opt && opt->no_residues) ? 0 : 1;
 
-    if (cudaHostAlloc((void**)&ct->h_status, ct->statusInts * sizeof(int32_t), cudaHostAllocDefault) !=
+    // The status block lives in mapped host memory: the kernel's last CTA writes
+    // it directly and the host reads it after the stream synchronises.
+    if (cudaHostAlloc((void**)&ct->h_status, ct->statusInts * sizeof(int32_t), cudaHostAllocMapped) !=
         cudaSuccess) {
         cudaGetLastError();
         ct->h_status = nullptr;
@@ -347,6 +346,18 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
         return CT_ERR_OOM;
     }
     std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
+    CT_CUDA(cudaHostGetDevicePointer((void**)&d.statusBlk, ct->h_status, 0));
+    {
+        const int maxCo = max_coresident_blocks(ct->E);
+        if (maxCo <= 0) {
+            ct_set_error("ct_create: the propagation kernel cannot be made resident on this device");
+            return CT_ERR_CUDA;
+        }
+        int want = (ct->nseg + kWarps - 1) / kWarps;
+        want = std::max(want, (R + 2 * kWarps - 1) / (2 * kWarps));
+        if (opt && opt->grid_blocks > 0) want = opt->grid_blocks;
+        ct->grid = std::max(1, std::min(want, maxCo));
+    }
 
     CT_CUDA(cudaMemcpyAsync(sup, hsup.data(), hsup.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ct->stream));
     CT_CUDA(cudaMemcpyAsync(d.curr, hcurr.data(), hcurr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
@@ -361,7 +372,6 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = upload(ct, varNW, ct->nw)) != CT_OK) return st;
     if ((st = upload(ct, varLD, ct->ld)) != CT_OK) return st;
     CT_CUDA(cudaMemsetAsync(d.changed, 0, (size_t)n * sizeof(int32_t), ct->stream));
-    CT_CUDA(cudaMemsetAsync(d.statusBlk, 0, ct->statusInts * sizeof(int32_t), ct->stream));
 
     Ctrl c{};
     c.status = CT_OK;
@@ -387,12 +397,20 @@ void fill_stats(ct_table* ct) {
     s.rows_ored = h[kSlotRowsOred];
     s.sup_vars = h[kSlotNsup];
     s.residue_hits = h[kSlotHits];
-    s.residue_misses = h[kSlotMisses];
+    s.local_found = h[kSlotLocal];
+    s.hard = h[kSlotHard];
+    s.windows = h[kSlotWindows];
     s.pruned = h[kSlotPruned];
     s.trail_added = h[kSlotTrailAdded];
     s.live_chunks_in = (uint32_t)h[kSlotLiveIn];
     s.live_chunks_out = (uint32_t)h[kSlotLiveOut];
     s.live_words_in = (uint32_t)h[kSlotWordsIn];
+    // Algorithmic bytes (what CT itself must move, 4-byte words): updateTable
+    // reads k rows and currTable and writes currTable over the N live words;
+    // filterDomains reads one word per residue hit, the windows it probes and
+    // the whole live table for every value scanned in full.
+    s.update_bytes = s.rows_ored > 0 ? 4LL * s.live_words_in * (s.rows_ored + 2) : 0;
+    s.filter_bytes = 4LL * s.residue_hits + 4LL * 128 * s.windows + 16LL * s.hard * s.live_chunks_out;
 }
 
 }  // namespace
@@ -418,31 +436,36 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     int st;
     if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
     cudaStream_t s = ct->stream;
+    int32_t* h = ct->h_status;
+    h[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
-    CT_CUDA(launch_plan(ct->dev, dom, domOffDev, s));
+    CT_CUDA(launch_propagate(ct->dev, ct->E, ct->grid, dom, domOffDev, s));
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
-    CT_CUDA(launch_update(ct->dev, ct->E, ct->wpb, dom, domOffDev, s));
-    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[2], s));
-    CT_CUDA(launch_scan(ct->dev, ct->E, ct->wpb, dom, domOffDev, s));
-    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[3], s));
-    CT_CUDA(cudaMemcpyAsync(ct->h_status, ct->dev.statusBlk, ct->statusInts * sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, s));
     CT_CUDA(cudaStreamSynchronize(s));
+    int status = h[kSlotStatus];
+    if (status == kNoChunk) {
+        // The kernel returned before publishing: a grid barrier timed out.
+        Ctrl c{};
+        CT_CUDA(cudaMemcpy(&c, ct->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        status = c.status == CT_OK ? CT_ERR_TIMEOUT : c.status;
+        c.bar_count = 0;
+        c.status = CT_OK;
+        CT_CUDA(cudaMemcpy(ct->dev.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+        ct->failed = true;
+        ct->last = ct_call_stats{};
+        ct->last.status = status;
+        ct_set_error("ct_propagate: a device-side wait ran out (status %d)", status);
+        return status;
+    }
     fill_stats(ct);
-    const int32_t* h = ct->h_status;
-    const int status = h[kSlotStatus];
     ct->trailTop = h[kSlotTrailTop];
     if (ct->profile) {
-        float a = 0.f, b = 0.f, c = 0.f;
+        float a = 0.f;
         CT_CUDA(cudaEventElapsedTime(&a, ct->ev[0], ct->ev[1]));
-        CT_CUDA(cudaEventElapsedTime(&b, ct->ev[1], ct->ev[2]));
-        CT_CUDA(cudaEventElapsedTime(&c, ct->ev[2], ct->ev[3]));
         ct->prof.calls += 1;
-        ct->prof.plan_ms += a;
-        ct->prof.update_ms += b;
-        ct->prof.scan_ms += c;
-        if (ct->last.rows_ored > 0)
-            ct->prof.update_bytes += 4LL * ct->last.live_words_in * (ct->last.rows_ored + 2);
+        ct->prof.kernel_ms += a;
+        ct->prof.update_bytes += ct->last.update_bytes;
+        ct->prof.filter_bytes += ct->last.filter_bytes;
     }
     if (status == CT_INFEASIBLE) {
         ct->failed = true;

@@ -33,7 +33,7 @@ class CtError(RuntimeError):
 
 
 class ct_options(ctypes.Structure):
-    _fields_ = [("entries_per_lane", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+    _fields_ = [("entries_per_lane", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 4)]
 
@@ -50,15 +50,17 @@ class ct_call_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("changed_vars", ctypes.c_int32),
                 ("delta_vars", ctypes.c_int32), ("reset_vars", ctypes.c_int32),
                 ("rows_ored", ctypes.c_int32), ("sup_vars", ctypes.c_int32),
-                ("residue_hits", ctypes.c_int32), ("residue_misses", ctypes.c_int32),
+                ("residue_hits", ctypes.c_int32), ("local_found", ctypes.c_int32),
+                ("hard", ctypes.c_int32), ("windows", ctypes.c_int32),
                 ("pruned", ctypes.c_int32), ("trail_added", ctypes.c_int32),
                 ("live_chunks_in", ctypes.c_int64), ("live_chunks_out", ctypes.c_int64),
-                ("live_words_in", ctypes.c_int64)]
+                ("live_words_in", ctypes.c_int64), ("update_bytes", ctypes.c_int64),
+                ("filter_bytes", ctypes.c_int64)]
 
 
 class ct_profile(ctypes.Structure):
-    _fields_ = [("calls", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("update_ms", ctypes.c_double),
-                ("scan_ms", ctypes.c_double), ("update_bytes", ctypes.c_int64)]
+    _fields_ = [("calls", ctypes.c_int64), ("kernel_ms", ctypes.c_double), ("update_bytes", ctypes.c_int64),
+                ("filter_bytes", ctypes.c_int64)]
 
 
 class ct_search_stats(ctypes.Structure):
@@ -180,10 +182,10 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)
 
 
-def make_options(entries_per_lane=0, warps_per_block=0, no_residues=0, profile=0):
+def make_options(entries_per_lane=0, grid_blocks=0, no_residues=0, profile=0):
     o = ct_options()
     o.entries_per_lane = entries_per_lane
-    o.warps_per_block = warps_per_block
+    o.grid_blocks = grid_blocks
     o.no_residues = no_residues
     o.profile = profile
     return o

@@ -79,3 +79,31 @@ def test_domain_word_marshalling_round_trip():
     for i, m in enumerate(masks):
         for a in range(sizes[i]):
             assert bool((int(words[off[i] + a // 32]) >> (a % 32)) & 1) == bool(m[a])
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives the header."""
+    import ctypes
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [C.ct_options, C.ct_table_info, C.ct_call_stats, C.ct_profile, C.ct_search_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ct.h"', "int main(void){"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-I", os.path.join(B.ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for st in structs:
+        n = st.__name__
+        assert int(out[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(out[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"

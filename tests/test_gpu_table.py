@@ -82,8 +82,8 @@ def test_tiny_stream_1000_calls():
     assert counts["fail"] > 0 and counts["ok"] > 0 and counts["restores"] > 0
 
 
-@pytest.mark.parametrize("opt", [dict(entries_per_lane=2), dict(entries_per_lane=4, warps_per_block=1),
-                                 dict(no_residues=1), dict(warps_per_block=8)])
+@pytest.mark.parametrize("opt", [dict(entries_per_lane=2), dict(entries_per_lane=4, grid_blocks=1),
+                                 dict(no_residues=1), dict(grid_blocks=3)])
 def test_tiny_stream_options(opt):
     _tiny_stream(seed=2, calls=150, opt=C.make_options(**opt))
 
