@@ -58,7 +58,7 @@ typedef struct ct_model ct_model;
 
 /* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
 typedef struct ct_options {
-    int32_t entries_per_lane; /* 0 = auto; 1, 2 or 4 currTable chunks per lane of a segment warp */
+    int32_t reserved0;        /* must be 0 */
     int32_t grid_blocks;      /* 0 = auto; CTAs of the cooperative propagation launch (capped at residency) */
     int32_t no_residues;      /* 1 = skip the residue probe and scan for every value */
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
@@ -72,12 +72,14 @@ typedef struct ct_table_info {
     int64_t tuples;        /* retained tuples t */
     int64_t words;         /* ceil(t / 32) 32-bit currTable words (_currTableSize, Sec. 3) */
     int64_t chunks;        /* ceil(words / 4): 128-bit units of the sparse index */
-    int32_t segments;      /* index segments (one warp each) */
-    int32_t seg_capacity;  /* chunks per segment */
+    int32_t segments;      /* segments of 32 chunks; the non-zero index keeps one live mask per segment */
+    int32_t seg_capacity;  /* chunks per segment (32) */
     int64_t live_chunks;   /* chunks currently in the non-zero index */
     int64_t trail_size;    /* trail entries in use */
     int32_t depth;         /* saved levels on the stack */
-    int32_t entries_per_lane;
+    int32_t local_plan;    /* 1: every CTA computes the update plan in shared memory */
+    int32_t grid_blocks;   /* CTAs of the propagation launch */
+    int32_t reserved;
     int64_t device_bytes;  /* device memory held by the table */
 } ct_table_info;
 
@@ -100,6 +102,8 @@ typedef struct ct_call_stats {
     int64_t live_words_in;   /* non-zero 32-bit currTable words at entry (N) */
     int64_t update_bytes;    /* algorithmic bytes of updateTable: 4 * N * (rows_ored + 2), 0 if no row */
     int64_t filter_bytes;    /* algorithmic bytes of filterDomains: 4 * supports words tested */
+    int32_t phase_ns[4];     /* %globaltimer, ns from the first CTA's start to: plan done, update done,
+                                probes done, result published (device-side, no launch latency) */
 } ct_call_stats;
 
 /* Accumulated launch times (ct_options.profile = 1): CUDA events recorded on
@@ -109,6 +113,7 @@ typedef struct ct_profile {
     double kernel_ms;     /* sum of the event intervals around the propagation kernel */
     int64_t update_bytes; /* sum of ct_call_stats.update_bytes */
     int64_t filter_bytes; /* sum of ct_call_stats.filter_bytes */
+    double device_ms;     /* sum of ct_call_stats.phase_ns[3] (kernel time without launch latency) */
 } ct_profile;
 
 /* ---------------------------------------------------------------- table --
@@ -174,8 +179,8 @@ int ct_get_currtable(ct_table* ct, uint32_t* words_host, int64_t* nonzero_words_
 int ct_get_support_row(ct_table* ct, int row, uint32_t* words_host);
 
 /* ct_get_index: copy the non-zero index (128-bit chunk numbers, each live
- * chunk exactly once, in no particular order) to host int32[live_chunks];
- * *count_out receives live_chunks. index_host may be NULL. */
+ * chunk exactly once, ascending) to host int32[live_chunks]; *count_out
+ * receives live_chunks. index_host may be NULL. */
 int ct_get_index(ct_table* ct, int32_t* index_host, int64_t* count_out);
 
 int ct_get_info(ct_table* ct, ct_table_info* info);

@@ -6,10 +6,8 @@
 //                             row jmp[i] + v - lo[i] holds bit j for every
 //                             tuple j with tau_j[i] == v; 16-byte aligned rows
 //   curr     uint4 [W4]      currTable (Sec. 2, Table 1(c)) as 128-bit chunks
-//   idx      int32 [nseg*S]  non-zero index, cut into segments of S chunk
-//                             numbers; segment s lists live chunks of the
-//                             range [s*S, (s+1)*S) in its first segCnt[s] slots
-//   segCnt   int32 [nseg]
+//   segMask  uint32 [nseg]   non-zero index: bit l of segMask[s] is set iff
+//                             chunk 32*s + l of currTable is non-zero
 //   lastpos  int32 [W4]      trail position of the latest entry of each chunk
 //   trailKey int2  [cap]     (chunk, previous trail position of that chunk)
 //   trailOld uint4 [cap]     chunk value before the change
@@ -29,7 +27,9 @@ constexpr int kMaxArity = 2048;
 constexpr int kMaxDomSize = 65536;
 constexpr int kThreads = 256;          // threads per CTA of the propagation kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kCodeCap = 8192;         // row codes staged in shared memory per CTA
+constexpr int kCodeCap = 4096;         // row codes staged in shared memory per CTA
+constexpr int kLocalMaxArity = 512;    // every CTA plans for itself up to this arity,
+constexpr int kLocalMaxDW = 2048;      // this many domain words and kCodeCap rows
 constexpr int kStatusHdr = 24;         // int32 slots before the changed mask
 constexpr int32_t kNoChunk = 0x7fffffff;
 // Row code of the update plan: supports row | flags.
@@ -58,6 +58,10 @@ enum StatusSlot {
     kSlotLocal = 14,
     kSlotHard = 15,
     kSlotWindows = 16,
+    kSlotT1 = 17,  // ns from kernel start to: plan done,
+    kSlotT2 = 18,  // update done (after the barrier),
+    kSlotT3 = 19,  // probes done (after the barrier),
+    kSlotT4 = 20,  // finalize
 };
 
 // Per-table control block: persistent state and per-call counters.
@@ -76,23 +80,25 @@ struct Ctrl {
     int32_t nrows;       // rows in the update plan
     int32_t nval, ndelta, nreset, nsup;
     int32_t hits, pruned, trail_added, local_found, misses, windows;
-    int32_t pad[10];
+    int32_t pad[2];
+    uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
 };
 
 // Everything a kernel needs, passed by value.
 struct TableDev {
     const uint4* sup;
     uint4* curr;
-    int32_t* idx;
-    int32_t* segCnt;
+    uint32_t* segMask;
     int32_t* lastpos;
     int2* trailKey;
     uint4* trailOld;
     int32_t* residue;
     uint32_t* lastDom;
     Ctrl* ctrl;
-    int32_t* codes;          // [R] update plan: row codes
-    int32_t* varSup;         // [arity] 1 if |dom| > 1 (s_sup)
+    int32_t* codes;          // [R] update plan: row codes (global plan mode)
+    int32_t* planK;          // [arity] rows to OR | delta flag (global plan mode)
+    int32_t* planRowOff;     // [arity] first code of each variable (global plan mode)
+    int32_t* varSup;         // [arity] 1 if |dom| > 1 (s_sup, global plan mode)
     int32_t* changed;        // [arity]
     int32_t* hardRow;        // [R] values left for the full scan
     int32_t* foundChunk;     // [R]
@@ -101,7 +107,7 @@ struct TableDev {
     const int32_t* varNW;    // [arity] words of each domain
     const int32_t* varLD;    // [arity] offset of each domain in lastDom / packed layout
     int32_t* statusBlk;      // [kStatusHdr + nChangedWords + DW], mapped host memory
-    int32_t* levelSeg;       // [levelCap][nseg]
+    uint32_t* levelSeg;      // [levelCap][nseg] live masks
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
 };
@@ -109,9 +115,9 @@ struct TableDev {
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
 // offset of scope variable i in it. All run on `s` and return the launch error.
 // The propagation kernel is a cooperative launch of `grid` CTAs that must all
-// be resident at once (grid <= max_coresident_blocks(E)).
-int max_coresident_blocks(int E);
-cudaError_t launch_propagate(const TableDev& T, int E, int grid, uint32_t* dom, const int32_t* domOff,
+// be resident at once (grid <= max_coresident_blocks(localPlan)).
+int max_coresident_blocks(bool localPlan);
+cudaError_t launch_propagate(const TableDev& T, bool localPlan, int grid, uint32_t* dom, const int32_t* domOff,
                              cudaStream_t s);
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s);
 cudaError_t launch_restore(const TableDev& T, int level, int mark, int top, int newMark, cudaStream_t s);

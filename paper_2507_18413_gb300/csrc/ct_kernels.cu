@@ -1,26 +1,30 @@
 // ct_kernels.cu -- CUDA kernels of Compact-Table propagation for sm_103a.
 //
-// One propagation (Algorithm 1, enforceGAC) is ONE cooperative launch; its
-// CTAs step through four phases separated by grid barriers:
-//   0 plan     CTA 0: Delta_x = lastDom_x & ~dom_x, s_val, s_sup, the
-//              delta/reset choice of Algorithm 2 (delta iff |Delta| < |dom|)
-//              and the list of supports rows to OR, as row codes.
-//   1 update   one warp per index segment (grid-stride): Algorithm 2 for
-//              every live 128-bit chunk of currTable. The row list is walked
-//              flat across variables with U independent 128-bit loads in
-//              flight per lane; each variable's OR is complemented on the
-//              delta path and AND-ed into the chunk. Changed chunks go to the
-//              trail; the segment's index is compacted with warp ballots
-//              (survivors first, removed chunks after them, so that a restore
-//              only resets the count).
-//   2 probe    Algorithm 1 line 5 (fail when currTable = 0), then one warp
-//              per value of s_sup (Algorithm 3 with residues): the residue
-//              chunk first; on a miss, two 32-chunk windows after it; values
-//              still unresolved go to the hard list.
-//   3 scan     one warp per index segment holds its live chunks in registers
-//              and tests every hard value against them; the last CTA to finish
-//              removes the values no chunk supports, stores new residues,
-//              writes lastDom and the status block (mapped host memory).
+// One propagation (Algorithm 1, enforceGAC) is ONE cooperative launch whose
+// CTAs step through these phases:
+//   plan     Delta_x = lastDom_x & ~dom_x, s_val, s_sup, the delta/reset
+//            choice of Algorithm 2 (delta iff |Delta| < |dom|) and the list
+//            of supports rows to OR (row codes). For tables whose plan fits in
+//            shared memory every CTA computes it for itself; otherwise CTA 0
+//            writes it to global memory and a grid barrier follows.
+//   update   one warp per 32-chunk segment of currTable (grid-stride):
+//            Algorithm 2 on every live 128-bit chunk. The row list is walked
+//            flat across variables with 16 independent 128-bit loads in
+//            flight per lane; each variable's OR is complemented on the delta
+//            path and AND-ed into the chunk. Changed chunks go to the trail;
+//            the segment's live mask (the non-zero index) is rebuilt with one
+//            warp ballot.
+//   -- grid barrier --
+//   probe    Algorithm 1 line 5 (fail when currTable = 0), then one warp per
+//            value of s_sup (Algorithm 3 with residues): the residue chunk
+//            first; on a miss, two 32-chunk windows after it; values still
+//            unresolved go to the hard list.
+//   -- grid barrier --
+//   scan     one warp per segment holds its live chunks in registers and
+//            tests every hard value against them; the last CTA to finish
+//            removes the values no chunk supports, stores new residues, writes
+//            lastDom and the status block (mapped host memory), and resets the
+//            per-call counters for the next call.
 // Grid barriers spin with a bounded iteration count; running out sets
 // CT_ERR_TIMEOUT and every CTA returns.
 #include <cstdint>
@@ -58,6 +62,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Read-only 128-bit load of a supports chunk (the supports never change).
 __device__ __forceinline__ uint4 ld_sup(const uint4* p) { return __ldg(p); }
 
@@ -72,8 +82,8 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident). The last CTA
-// to arrive resets the count and advances the generation; the others wait on
-// the generation for at most kBarrierSpinLimit polls. Returns false (and sets
+// to arrive resets the count and advances the generation; the others poll the
+// generation at most kBarrierSpinLimit times. Returns false (after setting
 // CT_ERR_TIMEOUT) when the wait ran out.
 __device__ bool grid_sync(Ctrl* C, int* s_flag) {
     __syncthreads();
@@ -94,7 +104,7 @@ __device__ bool grid_sync(Ctrl* C, int* s_flag) {
                     atomicExch(&C->status, CT_ERR_TIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                if (it > 64) __nanosleep(32);
             }
         }
         *s_flag = ok;
@@ -103,37 +113,28 @@ __device__ bool grid_sync(Ctrl* C, int* s_flag) {
     return *s_flag != 0;
 }
 
-struct PlanSmem {
-    int32_t k[kMaxArity];       // rows to OR per variable | kCodeDelta
-    int32_t rowOff[kMaxArity];  // first code of each variable
-    int32_t scan[kThreads];
-    int flags[8];               // grow, empty, nval, ndelta, nreset, nsup
-};
-
 struct Smem {
-    union {
-        PlanSmem plan;
-        int32_t codes[kCodeCap];
-    } u;
+    int32_t codes[kCodeCap];        // row codes of the plan; hard rows in the scan phase
+    uint32_t dom[kLocalMaxDW];      // domains at entry, packed in scope order (local plan)
+    int32_t k[kLocalMaxArity];      // rows to OR per variable | kCodeDelta
+    int32_t rowOff[kLocalMaxArity]; // first code of each variable
+    int32_t sup[kLocalMaxArity];    // |dom| > 1
+    int32_t scan[kThreads];
     uint32_t cnt[12];
+    int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
     int flag[4];
 };
 
 enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin };
 
 // ---------------------------------------------------------------------------
-// phase 0: Algorithm 1 lines 1-3 and the row selection of Algorithm 2 (CTA 0)
+// plan: Algorithm 1 lines 1-3 and the row selection of Algorithm 2.
+// Writes k/rowOff/sup/codes through generic pointers (shared or global).
 // ---------------------------------------------------------------------------
-__device__ void plan_block(const TableDev& T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
-                           PlanSmem& P) {
-    Ctrl* C = T.ctrl;
+__device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
+                     int32_t* K, int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm) {
     const int tid = threadIdx.x;
-    if (tid < 8) P.flags[tid] = 0;
-    if (tid == 0) {
-        C->status = CT_OK;
-        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u;
-        C->hits = 0; C->pruned = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
-    }
+    if (tid < 8) sm.flags[tid] = 0;
     __syncthreads();
     for (int i = tid; i < T.arity; i += kThreads) {
         const int nw = T.varNW[i];
@@ -146,61 +147,56 @@ __device__ void plan_block(const TableDev& T, const uint32_t* __restrict__ dom, 
             grow |= dv & ~lv;
             nd += __popc(dv);
             ndel += __popc(lv & ~dv);
+            if (domCopy) domCopy[T.varLD[i] + q] = dv;
         }
-        T.changed[i] = 0;
-        T.varSup[i] = nd > 1;
-        if (grow) atomicExch(&P.flags[0], 1);
-        if (nd == 0) atomicExch(&P.flags[1], 1);
-        if (nd > 1) atomicAdd(&P.flags[5], 1);
+        sup[i] = nd > 1;
+        if (grow) atomicExch(&sm.flags[0], 1);
+        if (nd == 0) atomicExch(&sm.flags[1], 1);
+        if (nd > 1) atomicAdd(&sm.flags[5], 1);
         int k = 0;
         if (ndel > 0) {
             // Algorithm 2, line 3: the delta mask when |Delta| < |dom| (strict).
-            if (ndel < nd) { k = ndel | kCodeDelta; atomicAdd(&P.flags[3], 1); }
-            else { k = nd; atomicAdd(&P.flags[4], 1); }
-            atomicAdd(&P.flags[2], 1);
+            if (ndel < nd) { k = ndel | kCodeDelta; atomicAdd(&sm.flags[3], 1); }
+            else { k = nd; atomicAdd(&sm.flags[4], 1); }
+            atomicAdd(&sm.flags[2], 1);
         }
-        P.k[i] = k;
+        K[i] = k;
     }
     __syncthreads();
-    if (P.flags[0] || P.flags[1]) {
-        // A grown domain (stray bits above dom_size included) or an empty one
-        // ends the call before any row is listed.
-        if (tid == 0) {
-            C->nval = P.flags[2]; C->ndelta = P.flags[3]; C->nreset = P.flags[4]; C->nsup = P.flags[5];
-            C->nrows = 0;
-            C->status = P.flags[0] ? CT_ERR_STATE : CT_INFEASIBLE;
-        }
+    if (sm.flags[0] || sm.flags[1]) {
+        if (tid == 0) sm.flags[6] = 0;
+        __syncthreads();
         return;
     }
     // Exclusive scan of the row counts, each thread owning a run of variables.
     const int per = (T.arity + kThreads - 1) / kThreads;
     const int b0 = tid * per, b1 = min(T.arity, b0 + per);
     int sum = 0;
-    for (int i = b0; i < b1; ++i) sum += P.k[i] & kCodeRow;
-    P.scan[tid] = sum;
+    for (int i = b0; i < b1; ++i) sum += K[i] & kCodeRow;
+    sm.scan[tid] = sum;
     __syncthreads();
     for (int off = 1; off < kThreads; off <<= 1) {
-        const int a = tid >= off ? P.scan[tid - off] : 0;
+        const int a = tid >= off ? sm.scan[tid - off] : 0;
         __syncthreads();
-        P.scan[tid] += a;
+        sm.scan[tid] += a;
         __syncthreads();
     }
-    int run = P.scan[tid] - sum;
+    int run = sm.scan[tid] - sum;
     for (int i = b0; i < b1; ++i) {
-        P.rowOff[i] = run;
-        run += P.k[i] & kCodeRow;
+        rowOff[i] = run;
+        run += K[i] & kCodeRow;
     }
     __syncthreads();
     // Codes: the removed values (delta) or the remaining ones (reset).
     for (int i = tid; i < T.arity; i += kThreads) {
-        const int k = P.k[i] & kCodeRow;
+        const int k = K[i] & kCodeRow;
         if (k == 0) continue;
-        const bool delta = (P.k[i] & kCodeDelta) != 0;
+        const bool delta = (K[i] & kCodeDelta) != 0;
         const int nw = T.varNW[i];
         const uint32_t* d = dom + domOff[i];
         const uint32_t* l = T.lastDom + T.varLD[i];
         const int row0 = T.varRow0[i];
-        int out = P.rowOff[i];
+        int out = rowOff[i];
         const int last = out + k - 1;
         for (int q = 0; q < nw; ++q) {
             uint32_t bits = delta ? (l[q] & ~d[q]) : d[q];
@@ -210,48 +206,36 @@ __device__ void plan_block(const TableDev& T, const uint32_t* __restrict__ dom, 
                 int code = row0 + q * 32 + b;
                 if (delta) code |= kCodeDelta;
                 if (out == last) code |= kCodeLast;
-                T.codes[out++] = code;
+                codes[out++] = code;
             }
         }
     }
+    if (tid == 0) sm.flags[6] = sm.scan[kThreads - 1];
     __syncthreads();
-    if (tid == 0) {
-        C->nrows = P.scan[kThreads - 1];
-        C->nval = P.flags[2]; C->ndelta = P.flags[3]; C->nreset = P.flags[4]; C->nsup = P.flags[5];
-    }
 }
 
 // ---------------------------------------------------------------------------
-// phase 1: Algorithm 2 on one index segment
+// update: Algorithm 2 on one 32-chunk segment (lane l owns chunk 32*seg + l)
 // ---------------------------------------------------------------------------
-template <int E, int U>
+template <int U>
 __device__ __forceinline__ void update_segment(const TableDev& T, int seg, int nrows, const int32_t* s_codes,
                                                int mark, int cap, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     Ctrl* C = T.ctrl;
-    const int c = T.segCnt[seg];
-    int32_t* idx = T.idx + (size_t)seg * T.S;
+    const uint32_t mask = T.segMask[seg];
+    if (mask == 0u) return;
     if (nrows == 0) {
-        if (lane == 0) { atomicAdd(&s_cnt[kCntLive], (uint32_t)c); atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)c); }
+        if (lane == 0) {
+            atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(mask));
+            atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
+        }
         return;
     }
-    if (c == 0) return;
-    bool act[E];
-    int w[E];
-    uint4 cur[E], acc[E], m[E];
-    uint32_t words = 0u;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        act[e] = e * 32 + lane < c;
-        w[e] = act[e] ? idx[e * 32 + lane] : 0;
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        cur[e] = act[e] ? T.curr[w[e]] : make_uint4(0u, 0u, 0u, 0u);
-        acc[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
-        m[e] = make_uint4(0u, 0u, 0u, 0u);
-        words += nzwords(cur[e]);
-    }
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
+    const uint4 cur = act ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
+    const int lp = (act && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const size_t W4 = (size_t)T.W4;
     for (int q0 = 0; q0 < nrows; q0 += U) {
         int code[U];
@@ -260,116 +244,65 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int seg, int n
             const int q = q0 + u;
             code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
         }
-        uint4 v[U][E];
+        uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint4* row = T.sup + (size_t)(code[u] & kCodeRow) * W4;
-#pragma unroll
-            for (int e = 0; e < E; ++e)
-                v[u][e] = (act[e] && q0 + u < nrows) ? ld_sup(row + w[e]) : make_uint4(0u, 0u, 0u, 0u);
-        }
+        for (int u = 0; u < U; ++u)
+            v[u] = (act && q0 + u < nrows) ? ld_sup(T.sup + (size_t)(code[u] & kCodeRow) * W4 + w)
+                                           : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (q0 + u < nrows) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) m[e] = or4(m[e], v[u][e]);
+                m = or4(m, v[u]);
                 if (code[u] & kCodeLast) {
-                    const bool delta = (code[u] & kCodeDelta) != 0;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        acc[e] = and4(acc[e], delta ? not4(m[e]) : m[e]);
-                        m[e] = make_uint4(0u, 0u, 0u, 0u);
-                    }
+                    acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
+                    m = make_uint4(0u, 0u, 0u, 0u);
                 }
             }
         }
-        bool any = false;
-#pragma unroll
-        for (int e = 0; e < E; ++e) any |= act[e] && nz(and4(acc[e], cur[e]));
         // Every chunk of this warp is already zero: later masks cannot revive it.
-        if (!__any_sync(0xffffffffu, any)) break;
+        if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
     }
-
-    bool alive[E], need[E];
-    int prev[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const uint4 nv = and4(cur[e], acc[e]);
-        const bool chg = act[e] && !eq4(nv, cur[e]);
-        alive[e] = act[e] && nz(nv);
-        if (chg) T.curr[w[e]] = nv;
-        prev[e] = (chg && mark >= 0) ? T.lastpos[w[e]] : 0x7fffffff;
-        need[e] = chg && mark >= 0 && prev[e] < mark;
-    }
+    const uint4 nv = and4(cur, acc);
+    const bool chg = act && !eq4(nv, cur);
+    const bool alive = act && nz(nv);
+    if (chg) T.curr[w] = nv;
+    const bool need = chg && mark >= 0 && lp < mark;
     // Trail: one reservation per warp.
-    uint32_t nb[E];
-    int ntr = 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        nb[e] = __ballot_sync(0xffffffffu, need[e]);
-        ntr += __popc(nb[e]);
-    }
+    const uint32_t nb = __ballot_sync(0xffffffffu, need);
+    const int ntr = __popc(nb);
     if (ntr) {
         int tb = 0;
         if (lane == 0) tb = atomicAdd(&C->trail_top, ntr);
         tb = __shfl_sync(0xffffffffu, tb, 0);
         if (tb + ntr > cap) {
             if (lane == 0) atomicExch(&C->status, CT_ERR_OOM);
-        } else {
-            int off = tb;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (need[e]) {
-                    const int p = off + __popc(nb[e] & lanemask_lt());
-                    T.trailKey[p] = make_int2(w[e], prev[e]);
-                    T.trailOld[p] = cur[e];
-                    T.lastpos[w[e]] = p;
-                }
-                off += __popc(nb[e]);
-            }
+        } else if (need) {
+            const int p = tb + __popc(nb & lanemask_lt());
+            T.trailKey[p] = make_int2(w, lp);
+            T.trailOld[p] = cur;
+            T.lastpos[w] = p;
         }
     }
-    // Stable partition of the segment: survivors first, removed after.
-    uint32_t ab[E];
-    int nal = 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        ab[e] = __ballot_sync(0xffffffffu, alive[e]);
-        nal += __popc(ab[e]);
-    }
-    if (nal != c) {
-        int before = 0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            if (act[e]) {
-                const int sb = before + __popc(ab[e] & lanemask_lt());
-                const int pos = e * 32 + lane;
-                idx[alive[e] ? sb : nal + (pos - sb)] = w[e];
-            }
-            before += __popc(ab[e]);
-        }
-        if (lane == 0) T.segCnt[seg] = nal;
-    }
+    // The segment's part of the non-zero index: the live chunks after the update.
+    const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
+    uint32_t words = nzwords(cur);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(0xffffffffu, words, o);
     if (lane == 0) {
-        atomicAdd(&s_cnt[kCntLive], (uint32_t)nal);
-        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)c);
+        if (nmask != mask) T.segMask[seg] = nmask;
+        atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(nmask));
+        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
         atomicAdd(&s_cnt[kCntWords], words);
-        atomicAdd(&s_cnt[kCntTrail], (uint32_t)ntr);
+        if (ntr) atomicAdd(&s_cnt[kCntTrail], (uint32_t)ntr);
     }
 }
 
 // ---------------------------------------------------------------------------
-// phase 2: residue probe of one value (warp per supports row)
+// probe: residue of one value (warp per supports row); Algorithm 3 with residues
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void probe_row(const TableDev& T, int r, const uint32_t* __restrict__ dom,
-                                          const int32_t* __restrict__ domOff, uint32_t* s_cnt) {
+__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
-    const int i = T.rowVar[r];
-    if (!__ldcg(&T.varSup[i])) return;
-    const int a = r - T.varRow0[i];
-    if (!((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u)) return;
+    if (!present) return;
     const int W4 = T.W4;
     const uint4* row = T.sup + (size_t)r * W4;
     if (T.useResidues) {
@@ -405,50 +338,40 @@ __device__ __forceinline__ void probe_row(const TableDev& T, int r, const uint32
 }
 
 // ---------------------------------------------------------------------------
-// phase 3: full index scan of the hard values over one segment
+// scan: the hard values against the live chunks of one segment
 // ---------------------------------------------------------------------------
-template <int E, int U>
+template <int U>
 __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh, const int32_t* s_rows) {
     const int lane = threadIdx.x & 31;
-    const int c = __ldcg(&T.segCnt[seg]);
-    if (c == 0) return;
-    const int32_t* idx = T.idx + (size_t)seg * T.S;
-    bool act[E];
-    int w[E];
-    uint4 cur[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        act[e] = e * 32 + lane < c;
-        w[e] = act[e] ? __ldcg(idx + e * 32 + lane) : 0;
-        cur[e] = act[e] ? __ldcg(T.curr + w[e]) : make_uint4(0u, 0u, 0u, 0u);
-    }
+    const uint32_t mask = __ldcg(&T.segMask[seg]);
+    if (mask == 0u) return;
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
+    const uint4 cur = act ? __ldcg(T.curr + w) : make_uint4(0u, 0u, 0u, 0u);
     const size_t W4 = (size_t)T.W4;
     for (int m0 = 0; m0 < nh; m0 += U) {
-        int cand[U];
+        bool hit[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            cand[u] = kNoChunk;
             const int mm = m0 + u;
-            if (mm < nh) {
+            hit[u] = false;
+            if (act && mm < nh) {
                 const int r = mm < kCodeCap ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
-                const uint4* row = T.sup + (size_t)r * W4;
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (act[e] && nz(and4(ld_sup(row + w[e]), cur[e]))) cand[u] = min(cand[u], w[e]);
+                hit[u] = nz(and4(ld_sup(T.sup + (size_t)r * W4 + w), cur));
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (m0 + u < nh) {
-                const int mn = __reduce_min_sync(0xffffffffu, cand[u]);
-                if (lane == 0 && mn != kNoChunk) atomicMin(&T.foundChunk[m0 + u], mn);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
+                if (lane == 0 && bal) atomicMin(&T.foundChunk[m0 + u], seg * 32 + __ffs(bal) - 1);
             }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// last CTA: apply Algorithm 3's removals and publish the result
+// last CTA: apply Algorithm 3's removals, publish, reset the call counters
 // ---------------------------------------------------------------------------
 __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
                          Smem& sm) {
@@ -490,14 +413,19 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
                 o[q] = v;
             }
         }
-        for (int q = tid; q < T.nChangedWords; q += kThreads) {
-            uint32_t bits = 0u;
-            for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b)
-                if (__ldcg(&T.changed[q * 32 + b])) bits |= 1u << b;
-            H[kStatusHdr + q] = (int32_t)bits;
-        }
-        __syncthreads();
     }
+    __syncthreads();
+    for (int q = tid; q < T.nChangedWords; q += kThreads) {
+        uint32_t bits = 0u;
+        for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b) {
+            if (__ldcg(&T.changed[q * 32 + b])) {
+                bits |= 1u << b;
+                T.changed[q * 32 + b] = 0;
+            }
+        }
+        H[kStatusHdr + q] = (int32_t)bits;
+    }
+    __syncthreads();
     if (tid == 0) {
         H[kSlotLiveOut] = (int32_t)__ldcg(&C->live);
         H[kSlotWordsIn] = (int32_t)__ldcg(&C->words_in);
@@ -515,7 +443,17 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
         H[kSlotLocal] = __ldcg(&C->local_found);
         H[kSlotHard] = (int32_t)__ldcg(&C->nhard);
         H[kSlotWindows] = __ldcg(&C->windows);
-        C->pruned = (int32_t)sm.cnt[kCntPruned];
+        const uint64_t t0 = __ldcg(&C->t[0]);
+        const uint64_t t4 = gtimer();
+        H[kSlotT1] = (int32_t)(__ldcg(&C->t[1]) - t0);
+        H[kSlotT2] = (int32_t)(__ldcg(&C->t[2]) - t0);
+        H[kSlotT3] = (int32_t)(__ldcg(&C->t[3]) - t0);
+        H[kSlotT4] = (int32_t)(t4 - t0);
+        // Reset the per-call counters for the next call.
+        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u;
+        C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
+        C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
+        C->status = CT_OK;
         __threadfence_system();
         H[kSlotStatus] = st;
     }
@@ -524,30 +462,53 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
 // ---------------------------------------------------------------------------
 // the propagation kernel
 // ---------------------------------------------------------------------------
-template <int E, int U>
+template <bool kLocal, int U>
 __global__ void __launch_bounds__(kThreads, 2)
 ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
     __shared__ Smem sm;
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int warp = tid >> 5;
+    const int gwarp = blockIdx.x * kWarps + warp;
+    const int nwarps = gridDim.x * kWarps;
+    if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
 
-    // phase 0
-    if (blockIdx.x == 0) plan_block(T, dom, domOff, sm.u.plan);
-    if (!grid_sync(C, &sm.flag[0])) return;
-    const int status0 = __ldcg(&C->status);
-    const int nrows = __ldcg(&C->nrows);
-
-    // phase 1
-    if (tid < 12) sm.cnt[tid] = 0u;
-    if (status0 == CT_OK) {
+    // plan
+    int nrows;
+    bool ok;
+    if (kLocal) {
+        plan(T, dom, domOff, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm);
+        ok = !(sm.flags[0] || sm.flags[1]);
+        nrows = sm.flags[6];
+        if (blockIdx.x == 0 && tid == 0) {
+            C->nval = sm.flags[2]; C->ndelta = sm.flags[3]; C->nreset = sm.flags[4]; C->nsup = sm.flags[5];
+            C->nrows = nrows;
+            if (!ok) C->status = sm.flags[0] ? CT_ERR_STATE : CT_INFEASIBLE;
+        }
+    } else {
+        if (blockIdx.x == 0) {
+            plan(T, dom, domOff, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            if (tid == 0) {
+                C->nval = sm.flags[2]; C->ndelta = sm.flags[3]; C->nreset = sm.flags[4]; C->nsup = sm.flags[5];
+                C->nrows = sm.flags[6];
+                if (sm.flags[0] || sm.flags[1]) C->status = sm.flags[0] ? CT_ERR_STATE : CT_INFEASIBLE;
+            }
+        }
+        if (!grid_sync(C, &sm.flag[0])) return;
+        ok = __ldcg(&C->status) == CT_OK;
+        nrows = __ldcg(&C->nrows);
         const int staged = min(nrows, kCodeCap);
-        for (int q = tid; q < staged; q += kThreads) sm.u.codes[q] = __ldcg(&T.codes[q]);
-        __syncthreads();
+        for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.codes[q]);
+    }
+    if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
+
+    // update (Algorithm 2)
+    if (tid < 12) sm.cnt[tid] = 0u;
+    __syncthreads();
+    if (ok) {
         const int mark = __ldcg(&C->cur_mark);
         const int cap = __ldcg(&C->trail_cap);
-        for (int seg = blockIdx.x * kWarps + warp; seg < T.nseg; seg += gridDim.x * kWarps)
-            update_segment<E, U>(T, seg, nrows, sm.u.codes, mark, cap, sm.cnt);
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) update_segment<U>(T, seg, nrows, sm.codes, mark, cap, sm.cnt);
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&C->live, sm.cnt[kCntLive]);
@@ -557,8 +518,9 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
         }
     }
     if (!grid_sync(C, &sm.flag[0])) return;
+    if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
 
-    // phase 2: failure test (Algorithm 1 line 5), then residue probes
+    // failure test (Algorithm 1 line 5), then residue probes (Algorithm 3)
     const int status1 = __ldcg(&C->status);
     const uint32_t live = __ldcg(&C->live);
     const bool run = status1 == CT_OK && live > 0u;
@@ -566,7 +528,17 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     if (tid < 12) sm.cnt[tid] = 0u;
     __syncthreads();
     if (run) {
-        for (int r = blockIdx.x * kWarps + warp; r < T.R; r += gridDim.x * kWarps) probe_row(T, r, dom, domOff, sm.cnt);
+        for (int r = gwarp; r < T.R; r += nwarps) {
+            const int i = __ldg(&T.rowVar[r]);
+            const int a = r - __ldg(&T.varRow0[i]);
+            bool present;
+            if (kLocal) {
+                present = sm.sup[i] && ((sm.dom[T.varLD[i] + (a >> 5)] >> (a & 31)) & 1u);
+            } else {
+                present = __ldcg(&T.varSup[i]) && ((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u);
+            }
+            probe_row(T, r, present, sm.cnt);
+        }
         __syncthreads();
         if (tid == 0) {
             if (sm.cnt[kCntHits]) atomicAdd(&C->hits, (int)sm.cnt[kCntHits]);
@@ -576,17 +548,16 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
         }
     }
     if (!grid_sync(C, &sm.flag[0])) return;
+    if (blockIdx.x == 0 && tid == 0) C->t[3] = gtimer();
 
-    // phase 3
+    // full scan of the hard values
     const int nh = run ? (int)__ldcg(&C->nhard) : 0;
     if (nh > 0) {
         const int staged = min(nh, kCodeCap);
-        for (int q = tid; q < staged; q += kThreads) sm.u.codes[q] = __ldcg(&T.hardRow[q]);
+        for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.hardRow[q]);
         __syncthreads();
-        for (int seg = blockIdx.x * kWarps + warp; seg < T.nseg; seg += gridDim.x * kWarps)
-            scan_segment<E, U>(T, seg, nh, sm.u.codes);
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) scan_segment<U>(T, seg, nh, sm.codes);
     }
-    (void)lane;
 
     // last-block-done
     __threadfence();
@@ -607,9 +578,9 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
 __global__ void ct_save_kernel(TableDev T, int level) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
-    int32_t* ls = T.levelSeg + (size_t)level * T.nseg;
+    uint32_t* ls = T.levelSeg + (size_t)level * T.nseg;
     uint32_t* ld = T.levelDom + (size_t)level * T.DW;
-    for (int s = tid; s < T.nseg; s += nth) ls[s] = T.segCnt[s];
+    for (int s = tid; s < T.nseg; s += nth) ls[s] = T.segMask[s];
     for (int q = tid; q < T.DW; q += nth) ld[q] = T.lastDom[q];
     if (tid == 0) T.ctrl->cur_mark = T.ctrl->trail_top;
 }
@@ -627,9 +598,9 @@ __global__ void ct_restore_kernel(TableDev T, int level, int mark, int top, int 
             T.lastpos[k.x] = k.y;
         }
     }
-    const int32_t* ls = T.levelSeg + (size_t)level * T.nseg;
+    const uint32_t* ls = T.levelSeg + (size_t)level * T.nseg;
     const uint32_t* ld = T.levelDom + (size_t)level * T.DW;
-    for (int s = tid; s < T.nseg; s += nth) T.segCnt[s] = ls[s];
+    for (int s = tid; s < T.nseg; s += nth) T.segMask[s] = ls[s];
     for (int q = tid; q < T.DW; q += nth) T.lastDom[q] = ld[q];
     if (tid == 0) {
         T.ctrl->trail_top = mark;
@@ -651,46 +622,37 @@ __global__ void ct_copy_words_kernel(uint32_t* dst, const uint32_t* src, int n) 
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) dst[q] = src[q];
 }
 
-template <int E, int U>
+constexpr int kU = 16;
+
+template <bool L>
 cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, cudaStream_t s) {
     TableDev t = T;
     void* args[] = {&t, &dom, (void*)&domOff};
-    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<E, U>, dim3(grid), dim3(kThreads), args, 0,
+    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, kU>, dim3(grid), dim3(kThreads), args, 0,
                                        s);
 }
 
-template <int E, int U>
+template <bool L>
 int coresident() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<E, U>, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, kU>, kThreads, 0) != cudaSuccess)
         return 0;
     return per * sms;
 }
 
 }  // namespace
 
-int max_coresident_blocks(int E) {
-    int r = 0;
-    switch (E) {
-        case 1: r = coresident<1, 16>(); break;
-        case 2: r = coresident<2, 8>(); break;
-        case 4: r = coresident<4, 4>(); break;
-        default: r = 0;
-    }
+int max_coresident_blocks(bool localPlan) {
+    const int r = localPlan ? coresident<true>() : coresident<false>();
     cudaGetLastError();
     return r;
 }
 
-cudaError_t launch_propagate(const TableDev& T, int E, int grid, uint32_t* dom, const int32_t* domOff,
+cudaError_t launch_propagate(const TableDev& T, bool localPlan, int grid, uint32_t* dom, const int32_t* domOff,
                              cudaStream_t s) {
-    switch (E) {
-        case 1: return launch_coop<1, 16>(T, grid, dom, domOff, s);
-        case 2: return launch_coop<2, 8>(T, grid, dom, domOff, s);
-        case 4: return launch_coop<4, 4>(T, grid, dom, domOff, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return localPlan ? launch_coop<true>(T, grid, dom, domOff, s) : launch_coop<false>(T, grid, dom, domOff, s);
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

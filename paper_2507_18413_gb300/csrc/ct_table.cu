@@ -57,7 +57,8 @@ struct ct_table {
     std::vector<int32_t> lo, size, nw, ld, row0, rowVar;
     int R = 0;
     int64_t t = 0, W = 0, W4 = 0;
-    int nseg = 0, S = 32, E = 1, grid = 1, DW = 0, nChW = 0;
+    int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
+    bool localPlan = true;
     TableDev dev{};
     cudaStream_t stream = nullptr;
     bool ownStream = false;
@@ -107,20 +108,6 @@ int sync(ct_table* ct) {
     return CT_OK;
 }
 
-int choose_entries_per_lane(int64_t W4, int requested) {
-    if (requested == 1 || requested == 2 || requested == 4) return requested;
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) {
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
-    }
-    cudaGetLastError();
-    // One 32-chunk segment per warp until every SM holds 16 warps of them.
-    const int64_t cap = 16LL * sms;
-    if ((W4 + 31) / 32 <= cap) return 1;
-    if ((W4 + 63) / 64 <= cap) return 2;
-    return 4;
-}
-
 // Grow the trail so that `need` entries fit.
 int ensure_trail(ct_table* ct, int64_t need) {
     if (need <= ct->trailCap) return CT_OK;
@@ -161,9 +148,9 @@ int ensure_trail(ct_table* ct, int64_t need) {
 int ensure_levels(ct_table* ct, int need) {
     if (need <= ct->levelCap) return CT_OK;
     const int cap = std::max(need, 2 * ct->levelCap);
-    int32_t* ns = nullptr;
+    uint32_t* ns = nullptr;
     uint32_t* nd = nullptr;
-    cudaError_t e = cudaMalloc(&ns, (size_t)cap * std::max(ct->nseg, 1) * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&ns, (size_t)cap * std::max(ct->nseg, 1) * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&nd, (size_t)cap * std::max(ct->DW, 1) * sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -173,7 +160,7 @@ int ensure_levels(ct_table* ct, int need) {
     }
     const int used = (int)ct->marks.size();
     if (used > 0) {
-        CT_CUDA(cudaMemcpyAsync(ns, ct->dev.levelSeg, (size_t)used * ct->nseg * sizeof(int32_t),
+        CT_CUDA(cudaMemcpyAsync(ns, ct->dev.levelSeg, (size_t)used * ct->nseg * sizeof(uint32_t),
                                 cudaMemcpyDeviceToDevice, ct->stream));
         CT_CUDA(cudaMemcpyAsync(nd, ct->dev.levelDom, (size_t)used * ct->DW * sizeof(uint32_t),
                                 cudaMemcpyDeviceToDevice, ct->stream));
@@ -253,9 +240,9 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
         return CT_ERR_ARG;
     }
     const int64_t W4 = ct->W4;
-    ct->E = choose_entries_per_lane(W4, opt ? opt->entries_per_lane : 0);
-    ct->S = 32 * ct->E;
-    ct->nseg = (int)((W4 + ct->S - 1) / ct->S);
+    ct->S = 32;
+    ct->nseg = (int)((W4 + 31) / 32);
+    ct->localPlan = n <= kLocalMaxArity && DW <= kLocalMaxDW && R <= kCodeCap;
 
     // supports rows (Sec. 2), value-major, 16-byte aligned rows of W4 chunks
     const size_t rowWords = (size_t)W4 * 4;
@@ -285,15 +272,11 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
         const int64_t rem = ct->t - w * 32;
         hcurr[(size_t)w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
     }
-    std::vector<int32_t> hidx((size_t)ct->nseg * ct->S, 0), hcnt(ct->nseg, 0);
+    // Non-zero index: every chunk below W4 holds a retained tuple at creation.
+    std::vector<uint32_t> hmask(ct->nseg, 0u);
     for (int s = 0; s < ct->nseg; ++s) {
-        int c = 0;
-        for (int j = 0; j < ct->S; ++j) {
-            const int64_t ch = (int64_t)s * ct->S + j;
-            if (ch >= W4) break;
-            hidx[(size_t)s * ct->S + c++] = (int32_t)ch;
-        }
-        hcnt[s] = c;
+        const int64_t left = W4 - (int64_t)s * 32;
+        hmask[s] = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
     }
     std::vector<uint32_t> hdom(DW, 0u);
     for (int i = 0; i < n; ++i)
@@ -305,13 +288,14 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     int32_t *rowVar = nullptr, *varRow0 = nullptr, *varNW = nullptr, *varLD = nullptr;
     if ((st = dalloc(ct, &sup, (size_t)R * W4)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.curr, (size_t)W4)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.idx, (size_t)ct->nseg * ct->S)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.segCnt, (size_t)ct->nseg)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.segMask, (size_t)ct->nseg)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.lastpos, (size_t)W4)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.residue, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.lastDom, (size_t)DW)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.codes, (size_t)R)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.planK, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.planRowOff, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.varSup, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.changed, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.hardRow, (size_t)R)) != CT_OK) return st;
@@ -348,7 +332,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
     CT_CUDA(cudaHostGetDevicePointer((void**)&d.statusBlk, ct->h_status, 0));
     {
-        const int maxCo = max_coresident_blocks(ct->E);
+        const int maxCo = max_coresident_blocks(ct->localPlan);
         if (maxCo <= 0) {
             ct_set_error("ct_create: the propagation kernel cannot be made resident on this device");
             return CT_ERR_CUDA;
@@ -362,8 +346,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     CT_CUDA(cudaMemcpyAsync(sup, hsup.data(), hsup.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ct->stream));
     CT_CUDA(cudaMemcpyAsync(d.curr, hcurr.data(), hcurr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                             ct->stream));
-    if ((st = upload(ct, d.idx, hidx)) != CT_OK) return st;
-    if ((st = upload(ct, d.segCnt, hcnt)) != CT_OK) return st;
+    if ((st = upload(ct, d.segMask, hmask)) != CT_OK) return st;
     CT_CUDA(cudaMemsetAsync(d.lastpos, 0xff, (size_t)W4 * sizeof(int32_t), ct->stream));
     if ((st = upload(ct, d.residue, hres)) != CT_OK) return st;
     if ((st = upload(ct, d.lastDom, hdom)) != CT_OK) return st;
@@ -411,6 +394,10 @@ void fill_stats(ct_table* ct) {
     // the whole live table for every value scanned in full.
     s.update_bytes = s.rows_ored > 0 ? 4LL * s.live_words_in * (s.rows_ored + 2) : 0;
     s.filter_bytes = 4LL * s.residue_hits + 4LL * 128 * s.windows + 16LL * s.hard * s.live_chunks_out;
+    s.phase_ns[0] = h[kSlotT1];
+    s.phase_ns[1] = h[kSlotT2];
+    s.phase_ns[2] = h[kSlotT3];
+    s.phase_ns[3] = h[kSlotT4];
 }
 
 }  // namespace
@@ -439,7 +426,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     int32_t* h = ct->h_status;
     h[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
-    CT_CUDA(launch_propagate(ct->dev, ct->E, ct->grid, dom, domOffDev, s));
+    CT_CUDA(launch_propagate(ct->dev, ct->localPlan, ct->grid, dom, domOffDev, s));
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
     CT_CUDA(cudaStreamSynchronize(s));
     int status = h[kSlotStatus];
@@ -466,6 +453,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         ct->prof.kernel_ms += a;
         ct->prof.update_bytes += ct->last.update_bytes;
         ct->prof.filter_bytes += ct->last.filter_bytes;
+        ct->prof.device_ms += ct->last.phase_ns[3] * 1e-6;
     }
     if (status == CT_INFEASIBLE) {
         ct->failed = true;
@@ -628,16 +616,15 @@ extern "C" int ct_get_index(ct_table* ct, int32_t* index_host, int64_t* count_ou
         if (count_out) *count_out = 0;
         return CT_OK;
     }
-    std::vector<int32_t> cnt(ct->nseg), idx((size_t)ct->nseg * ct->S);
-    CT_CUDA(cudaMemcpyAsync(cnt.data(), ct->dev.segCnt, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                            ct->stream));
-    CT_CUDA(cudaMemcpyAsync(idx.data(), ct->dev.idx, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+    std::vector<uint32_t> mask(ct->nseg);
+    CT_CUDA(cudaMemcpyAsync(mask.data(), ct->dev.segMask, mask.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                             ct->stream));
     CT_CUDA(cudaStreamSynchronize(ct->stream));
     int64_t n = 0;
     for (int s = 0; s < ct->nseg; ++s) {
-        for (int j = 0; j < cnt[s]; ++j) {
-            if (index_host) index_host[n] = idx[(size_t)s * ct->S + j];
+        for (int j = 0; j < 32; ++j) {
+            if (!((mask[s] >> j) & 1u)) continue;
+            if (index_host) index_host[n] = s * 32 + j;
             ++n;
         }
     }
@@ -660,7 +647,8 @@ extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
     r.seg_capacity = ct->S;
     r.trail_size = ct->trailTop;
     r.depth = (int)ct->marks.size();
-    r.entries_per_lane = ct->E;
+    r.local_plan = ct->localPlan ? 1 : 0;
+    r.grid_blocks = ct->grid;
     r.device_bytes = ct->deviceBytes;
     int64_t live = 0;
     const int st = ct_get_index(ct, nullptr, &live);

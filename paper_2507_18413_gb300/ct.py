@@ -33,7 +33,7 @@ class CtError(RuntimeError):
 
 
 class ct_options(ctypes.Structure):
-    _fields_ = [("entries_per_lane", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+    _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 4)]
 
@@ -43,7 +43,8 @@ class ct_table_info(ctypes.Structure):
                 ("words", ctypes.c_int64), ("chunks", ctypes.c_int64), ("segments", ctypes.c_int32),
                 ("seg_capacity", ctypes.c_int32), ("live_chunks", ctypes.c_int64),
                 ("trail_size", ctypes.c_int64), ("depth", ctypes.c_int32),
-                ("entries_per_lane", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
 
 
 class ct_call_stats(ctypes.Structure):
@@ -55,12 +56,12 @@ class ct_call_stats(ctypes.Structure):
                 ("pruned", ctypes.c_int32), ("trail_added", ctypes.c_int32),
                 ("live_chunks_in", ctypes.c_int64), ("live_chunks_out", ctypes.c_int64),
                 ("live_words_in", ctypes.c_int64), ("update_bytes", ctypes.c_int64),
-                ("filter_bytes", ctypes.c_int64)]
+                ("filter_bytes", ctypes.c_int64), ("phase_ns", ctypes.c_int32 * 4)]
 
 
 class ct_profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_ms", ctypes.c_double), ("update_bytes", ctypes.c_int64),
-                ("filter_bytes", ctypes.c_int64)]
+                ("filter_bytes", ctypes.c_int64), ("device_ms", ctypes.c_double)]
 
 
 class ct_search_stats(ctypes.Structure):
@@ -70,7 +71,11 @@ class ct_search_stats(ctypes.Structure):
 
 
 def _as_dict(s):
-    return {k: (list(getattr(s, k)) if k == "reserved" else getattr(s, k)) for k, _ in s._fields_}
+    out = {}
+    for k, _ in s._fields_:
+        v = getattr(s, k)
+        out[k] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 _P = ctypes.c_void_p
@@ -182,9 +187,8 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)
 
 
-def make_options(entries_per_lane=0, grid_blocks=0, no_residues=0, profile=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0):
     o = ct_options()
-    o.entries_per_lane = entries_per_lane
     o.grid_blocks = grid_blocks
     o.no_residues = no_residues
     o.profile = profile

@@ -82,8 +82,8 @@ def test_tiny_stream_1000_calls():
     assert counts["fail"] > 0 and counts["ok"] > 0 and counts["restores"] > 0
 
 
-@pytest.mark.parametrize("opt", [dict(entries_per_lane=2), dict(entries_per_lane=4, grid_blocks=1),
-                                 dict(no_residues=1), dict(grid_blocks=3)])
+@pytest.mark.parametrize("opt", [dict(grid_blocks=1), dict(grid_blocks=2), dict(no_residues=1),
+                                 dict(grid_blocks=3, no_residues=1)])
 def test_tiny_stream_options(opt):
     _tiny_stream(seed=2, calls=150, opt=C.make_options(**opt))
 
@@ -135,9 +135,32 @@ def test_large_stream_1e5():
     assert seen["delta"] > 0 and seen["reset"] > 0
 
 
-@pytest.mark.parametrize("epl", [1, 2, 4])
-def test_large_stream_entries_per_lane(epl):
-    _large_stream(60_000, calls=60, seed=12, opt=C.make_options(entries_per_lane=epl), depth=12)
+@pytest.mark.parametrize("grid", [1, 5, 0])
+def test_large_stream_grid_sizes(grid):
+    _large_stream(60_000, calls=60, seed=12, opt=C.make_options(grid_blocks=grid), depth=12)
+
+
+def test_global_plan_path():
+    """More supports rows than one CTA stages in shared memory: CTA 0 plans for the grid."""
+    dom_lo, dom_size = [0, 0, 0], [3000, 1500, 7]
+    tup = G.distinct_uniform_tuples(77, dom_lo, dom_size, 30000)
+    tup_ret = O.retained_tuples(tup, dom_lo, dom_size)
+    gt = GpuTable(dom_lo, dom_size, tup)
+    assert gt.info["local_plan"] == 0 and gt.info["rows"] > 4096
+    rng = G.Rng(12)
+    masks = [np.ones(d, bool) for d in dom_size]
+    st, masks = compare_call(gt, tup_ret, masks)
+    gt.save()
+    for k in range(8):
+        gt.save()
+        new, _ = (G.reset_step if k % 2 else G.delta_step)(rng, masks)
+        st, out = compare_call(gt, tup_ret, new)
+        if st != O.OK:
+            gt.restore(0)
+            gt.save()
+            continue
+        masks = out
+    gt.close()
 
 
 def test_large_stream_1e6_sampled():
