@@ -114,6 +114,7 @@ typedef struct ct_profile {
     int64_t update_bytes; /* sum of ct_call_stats.update_bytes */
     int64_t filter_bytes; /* sum of ct_call_stats.filter_bytes */
     double device_ms;     /* sum of ct_call_stats.phase_ns[3] (kernel time without launch latency) */
+    double host_ms;       /* wall time spent inside the propagation calls */
 } ct_profile;
 
 /* ---------------------------------------------------------------- table --

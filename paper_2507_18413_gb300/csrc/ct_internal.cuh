@@ -38,6 +38,7 @@ constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~
 constexpr int32_t kCodeRow = (1 << 29) - 1;
 constexpr int kLocalProbes = 2;          // 32-chunk windows searched after a residue miss
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
+constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
 
 // Status block header slots (written to mapped host memory after every call).
 enum StatusSlot {
@@ -112,13 +113,23 @@ struct TableDev {
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
 };
 
+// Per-call parameters of the propagation kernel.
+struct CallParams {
+    int32_t mark;      // trail position of the newest saved level, -1 with no level
+    int32_t snapFrom;  // levels [snapFrom, snapTo) were saved since the last call:
+    int32_t snapTo;    // the kernel snapshots the index and lastDom into them first
+    int32_t pad;
+};
+
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
 // offset of scope variable i in it. All run on `s` and return the launch error.
 // The propagation kernel is a cooperative launch of `grid` CTAs that must all
-// be resident at once (grid <= max_coresident_blocks(localPlan)).
-int max_coresident_blocks(bool localPlan);
-cudaError_t launch_propagate(const TableDev& T, bool localPlan, int grid, uint32_t* dom, const int32_t* domOff,
-                             cudaStream_t s);
+// be resident at once (grid <= max_coresident_blocks(variant)).
+// variant: bit 0 = every CTA plans in shared memory, bit 1 = 8 loads in flight
+// per lane with 3 CTAs per SM (else 16 loads, 2 CTAs per SM).
+int max_coresident_blocks(int variant);
+cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
+                             const CallParams& P, cudaStream_t s);
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s);
 cudaError_t launch_restore(const TableDev& T, int level, int mark, int top, int newMark, cudaStream_t s);
 cudaError_t launch_set_words(uint32_t* dst, const uint32_t* words, int n, cudaStream_t s);

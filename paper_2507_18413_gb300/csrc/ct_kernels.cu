@@ -71,6 +71,20 @@ __device__ __forceinline__ uint64_t gtimer() {
 // Read-only 128-bit load of a supports chunk (the supports never change).
 __device__ __forceinline__ uint4 ld_sup(const uint4* p) { return __ldg(p); }
 
+// Predicated read-only 128-bit load (zero when `pred` is false). Written as
+// volatile PTX so that a batch of them issues back to back, before any use.
+__device__ __forceinline__ uint4 ld_sup_pred(const uint4* p, bool pred) {
+    uint4 v;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
+        "@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "r"((int)pred));
+    return v;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -218,11 +232,14 @@ __device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const 
 // update: Algorithm 2 on one 32-chunk segment (lane l owns chunk 32*seg + l)
 // ---------------------------------------------------------------------------
 template <int U>
-__device__ __forceinline__ void update_segment(const TableDev& T, int seg, int nrows, const int32_t* s_codes,
-                                               int mark, int cap, uint32_t* s_cnt) {
+__device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, int nrows,
+                                               const int32_t* s_codes, int cap, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     Ctrl* C = T.ctrl;
+    const int mark = P.mark;
     const uint32_t mask = T.segMask[seg];
+    // Levels saved since the last call snapshot the index as it is now.
+    for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
     if (mask == 0u) return;
     if (nrows == 0) {
         if (lane == 0) {
@@ -236,19 +253,22 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int seg, int n
     const uint4 cur = act ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
     const int lp = (act && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
+    const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
-    for (int q0 = 0; q0 < nrows; q0 += U) {
-        int code[U];
+    int code[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + u;
-            code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
-        }
+    for (int u = 0; u < U; ++u) code[u] = u < nrows ? (u < kCodeCap ? s_codes[u] : __ldcg(&T.codes[u])) : 0;
+    for (int q0 = 0; q0 < nrows; q0 += U) {
         uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            v[u] = (act && q0 + u < nrows) ? ld_sup(T.sup + (size_t)(code[u] & kCodeRow) * W4 + w)
-                                           : make_uint4(0u, 0u, 0u, 0u);
+        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+        // Codes of the next batch while the loads are in flight.
+        int nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + U + u;
+            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (q0 + u < nrows) {
@@ -259,6 +279,8 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int seg, int n
                 }
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) code[u] = nxt[u];
         // Every chunk of this warp is already zero: later masks cannot revive it.
         if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
     }
@@ -300,15 +322,15 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int seg, int n
 // ---------------------------------------------------------------------------
 // probe: residue of one value (warp per supports row); Algorithm 3 with residues
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, uint32_t* s_cnt) {
+__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, int res, uint4 supRes,
+                                          uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     if (!present) return;
     const int W4 = T.W4;
     const uint4* row = T.sup + (size_t)r * W4;
     if (T.useResidues) {
-        const int res = T.residue[r];
         bool hit = false;
-        if (lane == 0) hit = nz(and4(ld_sup(row + res), __ldcg(T.curr + res)));
+        if (lane == 0) hit = nz(and4(supRes, __ldcg(T.curr + res)));
         if (__shfl_sync(0xffffffffu, hit, 0)) {
             if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
             return;
@@ -390,40 +412,37 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
             if (fc != kNoChunk) {
                 T.residue[r] = fc;
             } else {
+                // Algorithm 3 line 4: no live tuple carries the value.
                 const int i = T.rowVar[r];
                 const int a = r - T.varRow0[i];
                 atomicAnd(&dom[domOff[i] + (a >> 5)], ~(1u << (a & 31)));
+                atomicAnd(&T.lastDom[T.varLD[i] + (a >> 5)], ~(1u << (a & 31)));
                 T.changed[i] = 1;
                 ++pruned;
             }
         }
         if (pruned) atomicAdd(&sm.cnt[kCntPruned], pruned);
         __syncthreads();
-        // lastDom := the filtered domains (lastSizes of Algorithm 3 line 5);
-        // the same words go to the host.
-        uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kStatusHdr + T.nChangedWords);
-        for (int i = tid; i < T.arity; i += kThreads) {
-            const int nw = T.varNW[i];
-            const uint32_t* d = dom + domOff[i];
-            uint32_t* l = T.lastDom + T.varLD[i];
-            uint32_t* o = outDom + T.varLD[i];
-            for (int q = 0; q < nw; ++q) {
-                const uint32_t v = __ldcg(d + q);
-                l[q] = v;
-                o[q] = v;
+        if (sm.cnt[kCntPruned]) {
+            // The filtered domains of the variables that lost values go to the host;
+            // changed flags are cleared for the next call.
+            uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kStatusHdr + T.nChangedWords);
+            for (int q = tid; q < T.nChangedWords; q += kThreads) {
+                uint32_t bits = 0u;
+                for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b) {
+                    const int i = q * 32 + b;
+                    if (__ldcg(&T.changed[i])) {
+                        bits |= 1u << b;
+                        T.changed[i] = 0;
+                        const int nw = T.varNW[i];
+                        for (int k = 0; k < nw; ++k) outDom[T.varLD[i] + k] = __ldcg(&dom[domOff[i] + k]);
+                    }
+                }
+                H[kStatusHdr + q] = (int32_t)bits;
             }
+        } else {
+            for (int q = tid; q < T.nChangedWords; q += kThreads) H[kStatusHdr + q] = 0;
         }
-    }
-    __syncthreads();
-    for (int q = tid; q < T.nChangedWords; q += kThreads) {
-        uint32_t bits = 0u;
-        for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b) {
-            if (__ldcg(&T.changed[q * 32 + b])) {
-                bits |= 1u << b;
-                T.changed[q * 32 + b] = 0;
-            }
-        }
-        H[kStatusHdr + q] = (int32_t)bits;
     }
     __syncthreads();
     if (tid == 0) {
@@ -454,24 +473,40 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
         C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
         C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
         C->status = CT_OK;
+        // Everything above reaches the host before the status word that publishes it.
         __threadfence_system();
-        H[kSlotStatus] = st;
+        *reinterpret_cast<volatile int32_t*>(&H[kSlotStatus]) = st;
     }
 }
 
 // ---------------------------------------------------------------------------
 // the propagation kernel
 // ---------------------------------------------------------------------------
-template <bool kLocal, int U>
-__global__ void __launch_bounds__(kThreads, 2)
-ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff) {
+template <bool kLocal, int U, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff, CallParams P) {
     __shared__ Smem sm;
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
-    const int warp = tid >> 5;
+    const int warp = tid >> 5, lane = tid & 31;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
+
+    // Residue of the first value this warp will probe, and its supports chunk
+    // (read-only), fetched while the update runs.
+    int res0 = 0;
+    uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
+    if (T.useResidues && gwarp < T.R && lane == 0) {
+        res0 = T.residue[gwarp];
+        supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
+    }
+
+    // Levels saved since the last call snapshot lastDom as it is now.
+    if (blockIdx.x == 0) {
+        for (int l = P.snapFrom; l < P.snapTo; ++l)
+            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = T.lastDom[q];
+    }
 
     // plan
     int nrows;
@@ -506,9 +541,8 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     if (tid < 12) sm.cnt[tid] = 0u;
     __syncthreads();
     if (ok) {
-        const int mark = __ldcg(&C->cur_mark);
         const int cap = __ldcg(&C->trail_cap);
-        for (int seg = gwarp; seg < T.nseg; seg += nwarps) update_segment<U>(T, seg, nrows, sm.codes, mark, cap, sm.cnt);
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) update_segment<U>(T, P, seg, nrows, sm.codes, cap, sm.cnt);
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&C->live, sm.cnt[kCntLive]);
@@ -516,6 +550,10 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
             atomicAdd(&C->words_in, sm.cnt[kCntWords]);
             if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
         }
+    } else {
+        // No update: the pending snapshots of the index still have to be taken.
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps)
+            for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = T.segMask[seg];
     }
     if (!grid_sync(C, &sm.flag[0])) return;
     if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
@@ -528,6 +566,16 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     if (tid < 12) sm.cnt[tid] = 0u;
     __syncthreads();
     if (run) {
+        // lastDom := the domains of this call (values pruned below are cleared
+        // again by the finalizing CTA).
+        if (blockIdx.x == 0) {
+            if (kLocal) {
+                for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = sm.dom[q];
+            } else {
+                for (int i = tid; i < T.arity; i += kThreads)
+                    for (int q = 0; q < T.varNW[i]; ++q) T.lastDom[T.varLD[i] + q] = dom[domOff[i] + q];
+            }
+        }
         for (int r = gwarp; r < T.R; r += nwarps) {
             const int i = __ldg(&T.rowVar[r]);
             const int a = r - __ldg(&T.varRow0[i]);
@@ -537,7 +585,14 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
             } else {
                 present = __ldcg(&T.varSup[i]) && ((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u);
             }
-            probe_row(T, r, present, sm.cnt);
+            int res = res0;
+            uint4 sr = supRes0;
+            if (r != gwarp && T.useResidues && present && lane == 0) {
+                res = T.residue[r];
+                sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
+            }
+            res = __shfl_sync(0xffffffffu, res, 0);
+            probe_row(T, r, present, res, sr, sm.cnt);
         }
         __syncthreads();
         if (tid == 0) {
@@ -604,7 +659,6 @@ __global__ void ct_restore_kernel(TableDev T, int level, int mark, int top, int 
     for (int q = tid; q < T.DW; q += nth) T.lastDom[q] = ld[q];
     if (tid == 0) {
         T.ctrl->trail_top = mark;
-        T.ctrl->cur_mark = newMark;
         T.ctrl->status = CT_OK;
     }
 }
@@ -622,37 +676,49 @@ __global__ void ct_copy_words_kernel(uint32_t* dst, const uint32_t* src, int n) 
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) dst[q] = src[q];
 }
 
-constexpr int kU = 16;
-
-template <bool L>
-cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, cudaStream_t s) {
+template <bool L, int U, int B>
+cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, const CallParams& P,
+                        cudaStream_t s) {
     TableDev t = T;
-    void* args[] = {&t, &dom, (void*)&domOff};
-    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, kU>, dim3(grid), dim3(kThreads), args, 0,
-                                       s);
+    CallParams p = P;
+    void* args[] = {&t, &dom, (void*)&domOff, &p};
+    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, U, B>, dim3(grid), dim3(kThreads), args,
+                                       0, s);
 }
 
-template <bool L>
+template <bool L, int U, int B>
 int coresident() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, kU>, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, U, B>, kThreads, 0) != cudaSuccess)
         return 0;
     return per * sms;
 }
 
 }  // namespace
 
-int max_coresident_blocks(bool localPlan) {
-    const int r = localPlan ? coresident<true>() : coresident<false>();
+// variant: bit 0 = local plan, bit 1 = wide (8 loads in flight, 3 CTAs per SM)
+int max_coresident_blocks(int variant) {
+    int r = 0;
+    switch (variant & 3) {
+        case 0: r = coresident<false, 16, 2>(); break;
+        case 1: r = coresident<true, 16, 2>(); break;
+        case 2: r = coresident<false, 8, 3>(); break;
+        default: r = coresident<true, 8, 3>(); break;
+    }
     cudaGetLastError();
     return r;
 }
 
-cudaError_t launch_propagate(const TableDev& T, bool localPlan, int grid, uint32_t* dom, const int32_t* domOff,
-                             cudaStream_t s) {
-    return localPlan ? launch_coop<true>(T, grid, dom, domOff, s) : launch_coop<false>(T, grid, dom, domOff, s);
+cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
+                             const CallParams& P, cudaStream_t s) {
+    switch (variant & 3) {
+        case 0: return launch_coop<false, 16, 2>(T, grid, dom, domOff, P, s);
+        case 1: return launch_coop<true, 16, 2>(T, grid, dom, domOff, P, s);
+        case 2: return launch_coop<false, 8, 3>(T, grid, dom, domOff, P, s);
+        default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
+    }
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

@@ -35,8 +35,7 @@ struct ct_model {
         std::vector<char> dirty;
     };
     std::vector<Level> levels;
-    uint32_t* d_levelDom = nullptr;
-    int levelCap = 0;
+    uint32_t* h_stage = nullptr;  // pinned staging of the domains copied back on restore
     cudaStream_t stream = nullptr;
     bool ownStream = false;
     ct_options opt{};
@@ -51,27 +50,6 @@ int popcount_var(const ct_model* m, int v) {
     int s = 0;
     for (int q = 0; q < m->nw[v]; ++q) s += __builtin_popcount(m->h_dom[(size_t)m->off[v] + q]);
     return s;
-}
-
-int ensure_model_levels(ct_model* m, int need) {
-    if (need <= m->levelCap) return CT_OK;
-    const int cap = std::max(need, std::max(8, 2 * m->levelCap));
-    uint32_t* nd = nullptr;
-    cudaError_t e = cudaMalloc(&nd, (size_t)cap * std::max(m->DWg, 1) * sizeof(uint32_t));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        ct_set_error("model level stack: %s", cudaGetErrorString(e));
-        return CT_ERR_OOM;
-    }
-    const int used = (int)m->levels.size();
-    if (used > 0)
-        CT_CUDA(cudaMemcpyAsync(nd, m->d_levelDom, (size_t)used * m->DWg * sizeof(uint32_t),
-                                cudaMemcpyDeviceToDevice, m->stream));
-    CT_CUDA(cudaStreamSynchronize(m->stream));
-    if (m->d_levelDom) cudaFree(m->d_levelDom);
-    m->d_levelDom = nd;
-    m->levelCap = cap;
-    return CT_OK;
 }
 
 void mark_var(ct_model* m, int v, int except, std::deque<int>* q) {
@@ -134,6 +112,7 @@ extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* 
         m->ownStream = true;
     }
     e = cudaMalloc(&m->d_dom, (size_t)m->DWg * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->h_stage, (size_t)m->DWg * sizeof(uint32_t), cudaHostAllocDefault);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_dom, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyHostToDevice,
                             m->stream);
@@ -283,14 +262,16 @@ extern "C" int ct_model_save(ct_model* m, int* level_out) {
         ct_set_error("ct_model_save: null handle");
         return CT_ERR_ARG;
     }
+    if (m->failed) {
+        ct_set_error("ct_model_save: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
     const int L = (int)m->levels.size();
     int st;
-    if ((st = ensure_model_levels(m, L + 1)) != CT_OK) return st;
     for (ct_table* tab : m->tables) {
         int l = 0;
         if ((st = ct_save(tab, &l)) != CT_OK) return st;
     }
-    CT_CUDA(launch_copy_words(m->d_levelDom + (size_t)L * m->DWg, m->d_dom, m->DWg, m->stream));
     ct_model::Level lev;
     lev.dom = m->h_dom;
     lev.dirty = m->dirty;
@@ -311,8 +292,12 @@ extern "C" int ct_model_restore(ct_model* m, int level) {
     int st;
     for (ct_table* tab : m->tables)
         if ((st = ct_restore(tab, level)) != CT_OK) return st;
-    CT_CUDA(launch_copy_words(m->d_dom, m->d_levelDom + (size_t)level * m->DWg, m->DWg, m->stream));
+    // The host copy is authoritative: send it back through the pinned stage
+    // (stream-ordered before any later kernel of the model).
     m->h_dom = m->levels[level].dom;
+    std::memcpy(m->h_stage, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t));
+    CT_CUDA(cudaMemcpyAsync(m->d_dom, m->h_stage, (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            m->stream));
     m->dirty = m->levels[level].dirty;
     m->levels.resize(level);
     m->failed = false;
@@ -444,7 +429,7 @@ extern "C" int ct_model_destroy(ct_model* m) {
     for (ct_table* t : m->tables) ct_destroy(t);
     for (int32_t* p : m->d_tabOff) cudaFree(p);
     if (m->d_dom) cudaFree(m->d_dom);
-    if (m->d_levelDom) cudaFree(m->d_levelDom);
+    if (m->h_stage) cudaFreeHost(m->h_stage);
     if (m->ownStream && m->stream) cudaStreamDestroy(m->stream);
     cudaGetLastError();
     delete m;

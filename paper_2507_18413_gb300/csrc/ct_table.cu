@@ -2,6 +2,7 @@
 // device layout (Sec. 3 constructor, Sec. 4 device copies), propagation calls,
 // backtrack levels and inspection.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -59,6 +60,8 @@ struct ct_table {
     int64_t t = 0, W = 0, W4 = 0;
     int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
     bool localPlan = true;
+    int variant = 1;
+    int pendingFrom = 0;  // levels [pendingFrom, marks.size()) are not snapshotted yet
     TableDev dev{};
     cudaStream_t stream = nullptr;
     bool ownStream = false;
@@ -68,6 +71,7 @@ struct ct_table {
     std::vector<int> marks;
     int levelCap = 0;
     bool failed = false;
+    bool broken = false;  // a device-side wait ran out: the table is unusable
     bool empty = false;
     ct_call_stats last{};
     bool profile = false;
@@ -332,7 +336,12 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
     CT_CUDA(cudaHostGetDevicePointer((void**)&d.statusBlk, ct->h_status, 0));
     {
-        const int maxCo = max_coresident_blocks(ct->localPlan);
+        // 16 loads in flight per lane at 2 CTAs per SM while one wave of warps
+        // covers every segment; beyond that 8 loads at 3 CTAs per SM.
+        const int narrow = (ct->localPlan ? 1 : 0);
+        const int maxNarrow = max_coresident_blocks(narrow);
+        ct->variant = (ct->nseg > maxNarrow * kWarps) ? (narrow | 2) : narrow;
+        const int maxCo = max_coresident_blocks(ct->variant);
         if (maxCo <= 0) {
             ct_set_error("ct_create: the propagation kernel cannot be made resident on this device");
             return CT_ERR_CUDA;
@@ -416,6 +425,10 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         ct->failed = true;
         return CT_INFEASIBLE;
     }
+    if (ct->broken) {
+        ct_set_error("ct_propagate: the table is unusable after a device-side timeout");
+        return CT_ERR_TIMEOUT;
+    }
     if (ct->failed) {
         ct_set_error("ct_propagate: the previous call failed; restore a level first");
         return CT_ERR_STATE;
@@ -424,12 +437,31 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
     cudaStream_t s = ct->stream;
     int32_t* h = ct->h_status;
-    h[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
+    volatile int32_t* hv = h;
+    const auto t0 = std::chrono::steady_clock::now();
+    CallParams P{};
+    P.mark = ct->marks.empty() ? -1 : ct->marks.back();
+    P.snapFrom = ct->pendingFrom;
+    P.snapTo = (int)ct->marks.size();
+    hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
-    CT_CUDA(launch_propagate(ct->dev, ct->localPlan, ct->grid, dom, domOffDev, s));
+    CT_CUDA(launch_propagate(ct->dev, ct->variant, ct->grid, dom, domOffDev, P, s));
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
-    CT_CUDA(cudaStreamSynchronize(s));
-    int status = h[kSlotStatus];
+    ct->pendingFrom = (int)ct->marks.size();
+    // Wait for the status word the kernel publishes last (bounded), then fall
+    // back to a stream synchronisation to collect any CUDA error.
+    bool seen = false;
+    for (uint64_t it = 0;; ++it) {
+        if (hv[kSlotStatus] != kNoChunk) {
+            seen = true;
+            break;
+        }
+        if ((it & 1023u) == 1023u &&
+            std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(kHostWaitMs))
+            break;
+    }
+    if (!seen) CT_CUDA(cudaStreamSynchronize(s));
+    int status = hv[kSlotStatus];
     if (status == kNoChunk) {
         // The kernel returned before publishing: a grid barrier timed out.
         Ctrl c{};
@@ -437,8 +469,10 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         status = c.status == CT_OK ? CT_ERR_TIMEOUT : c.status;
         c.bar_count = 0;
         c.status = CT_OK;
+        c.live = c.live_in = c.words_in = c.nhard = c.done = 0u;
         CT_CUDA(cudaMemcpy(ct->dev.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
         ct->failed = true;
+        ct->broken = true;
         ct->last = ct_call_stats{};
         ct->last.status = status;
         ct_set_error("ct_propagate: a device-side wait ran out (status %d)", status);
@@ -448,7 +482,10 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     ct->trailTop = h[kSlotTrailTop];
     if (ct->profile) {
         float a = 0.f;
+        CT_CUDA(cudaEventSynchronize(ct->ev[1]));
         CT_CUDA(cudaEventElapsedTime(&a, ct->ev[0], ct->ev[1]));
+        ct->prof.host_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         ct->prof.calls += 1;
         ct->prof.kernel_ms += a;
         ct->prof.update_bytes += ct->last.update_bytes;
@@ -534,8 +571,15 @@ extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t
     CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, dom_bits_host, (size_t)ct->DW * sizeof(uint32_t),
                             cudaMemcpyHostToDevice, ct->stream));
     const int st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, changed_vars);
-    if (st == CT_OK)
-        std::memcpy(dom_bits_host, ct->h_status + kStatusHdr + ct->nChW, (size_t)ct->DW * sizeof(uint32_t));
+    if (st == CT_OK) {
+        // Only the variables that lost values differ from the input.
+        const int32_t* h = ct->h_status;
+        const uint32_t* outDom = reinterpret_cast<const uint32_t*>(h + kStatusHdr + ct->nChW);
+        for (int i = 0; i < ct->arity; ++i) {
+            if (!(((uint32_t)h[kStatusHdr + (i >> 5)] >> (i & 31)) & 1u)) continue;
+            std::memcpy(dom_bits_host + ct->ld[i], outDom + ct->ld[i], (size_t)ct->nw[i] * sizeof(uint32_t));
+        }
+    }
     return st;
 }
 
@@ -544,12 +588,17 @@ extern "C" int ct_save(ct_table* ct, int* level_out) {
         ct_set_error("ct_save: null handle");
         return CT_ERR_ARG;
     }
+    if (ct->failed) {
+        ct_set_error("ct_save: the previous call failed; restore a level first");
+        return CT_ERR_STATE;
+    }
     const int L = (int)ct->marks.size();
     if (!ct->empty) {
         int st;
         if ((st = ensure_levels(ct, L + 1)) != CT_OK) return st;
-        CT_CUDA(launch_save(ct->dev, L, ct->stream));
     }
+    // The snapshot itself is taken by the next propagation (or never, if the
+    // level is restored before any propagation changed the state).
     ct->marks.push_back(ct->trailTop);
     if (level_out) *level_out = L;
     return CT_OK;
@@ -564,14 +613,19 @@ extern "C" int ct_restore(ct_table* ct, int level) {
         ct_set_error("ct_restore: level %d not in [0, %d)", level, (int)ct->marks.size());
         return CT_ERR_LEVEL;
     }
-    const int mark = ct->marks[level];
-    const int newMark = level > 0 ? ct->marks[level - 1] : -1;
-    if (!ct->empty) {
-        CT_CUDA(launch_restore(ct->dev, level, mark, ct->trailTop, newMark, ct->stream));
-        ct->trailTop = mark;
-        ct->failed = false;
+    if (ct->broken) {
+        ct_set_error("ct_restore: the table is unusable after a device-side timeout");
+        return CT_ERR_TIMEOUT;
     }
+    const int mark = ct->marks[level];
+    if (!ct->empty && level < ct->pendingFrom) {
+        CT_CUDA(launch_restore(ct->dev, level, mark, ct->trailTop, -1, ct->stream));
+        ct->trailTop = mark;
+    }
+    // A level saved after the last propagation still equals the current state.
+    ct->failed = false;
     ct->marks.resize(level);
+    ct->pendingFrom = std::min(ct->pendingFrom, level);
     return CT_OK;
 }
 
