@@ -115,6 +115,8 @@ typedef struct ct_profile {
     int64_t filter_bytes; /* sum of ct_call_stats.filter_bytes */
     double device_ms;     /* sum of ct_call_stats.phase_ns[3] (kernel time without launch latency) */
     double host_ms;       /* wall time spent inside the propagation calls */
+    double launch_ms;     /* ... of which in the launch call */
+    double wait_ms;       /* ... of which waiting for the result */
 } ct_profile;
 
 /* ---------------------------------------------------------------- table --

@@ -39,6 +39,7 @@ constexpr int32_t kCodeRow = (1 << 29) - 1;
 constexpr int kLocalProbes = 2;          // 32-chunk windows searched after a residue miss
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
+constexpr int kParamArity = 16;        // scopes up to this arity carry their layout in kernel parameters
 
 // Status block header slots (written to mapped host memory after every call).
 enum StatusSlot {
@@ -111,6 +112,9 @@ struct TableDev {
     uint32_t* levelSeg;      // [levelCap][nseg] live masks
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
+    // Scopes of at most kParamArity variables: words, lastDom offset and first
+    // supports row of each variable, so that the plan reads no global table.
+    int32_t pNW[kParamArity], pLD[kParamArity], pRow0[kParamArity];
 };
 
 // Per-call parameters of the propagation kernel.
@@ -118,7 +122,8 @@ struct CallParams {
     int32_t mark;      // trail position of the newest saved level, -1 with no level
     int32_t snapFrom;  // levels [snapFrom, snapTo) were saved since the last call:
     int32_t snapTo;    // the kernel snapshots the index and lastDom into them first
-    int32_t pad;
+    int32_t prevLive;  // live chunks of the current state (reported when no row is OR-ed)
+    int32_t domOff[kParamArity];  // word offset of each scope domain (arity <= kParamArity)
 };
 
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
@@ -147,7 +152,8 @@ int ct_cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // Internal table entry points used by the model (ct_table.cu).
-int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, uint32_t* changed);
+int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
+                          uint32_t* changed);
 const int32_t* ct_table_status_host(const ct_table* ct);
 int ct_table_dom_words(const ct_table* ct);
 const int32_t* ct_table_var_ld(const ct_table* ct);

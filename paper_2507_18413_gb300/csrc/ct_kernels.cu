@@ -145,15 +145,29 @@ enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCnt
 // plan: Algorithm 1 lines 1-3 and the row selection of Algorithm 2.
 // Writes k/rowOff/sup/codes through generic pointers (shared or global).
 // ---------------------------------------------------------------------------
-__device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
-                     int32_t* K, int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm) {
+// Layout of scope variable i: from the kernel parameters for small scopes.
+struct VarLayout {
+    const TableDev& T;
+    const CallParams& P;
+    const int32_t* domOff;
+    bool small;
+    __device__ VarLayout(const TableDev& t, const CallParams& p, const int32_t* d)
+        : T(t), P(p), domOff(d), small(t.arity <= kParamArity) {}
+    __device__ int nw(int i) const { return small ? T.pNW[i] : T.varNW[i]; }
+    __device__ int ld(int i) const { return small ? T.pLD[i] : T.varLD[i]; }
+    __device__ int row0(int i) const { return small ? T.pRow0[i] : T.varRow0[i]; }
+    __device__ int off(int i) const { return small ? P.domOff[i] : domOff[i]; }
+};
+
+__device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __restrict__ dom, int32_t* K,
+                     int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm) {
     const int tid = threadIdx.x;
     if (tid < 8) sm.flags[tid] = 0;
     __syncthreads();
     for (int i = tid; i < T.arity; i += kThreads) {
-        const int nw = T.varNW[i];
-        const uint32_t* d = dom + domOff[i];
-        const uint32_t* l = T.lastDom + T.varLD[i];
+        const int nw = V.nw(i);
+        const uint32_t* d = dom + V.off(i);
+        const uint32_t* l = T.lastDom + V.ld(i);
         int nd = 0, ndel = 0;
         uint32_t grow = 0u;
         for (int q = 0; q < nw; ++q) {
@@ -161,7 +175,7 @@ __device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const 
             grow |= dv & ~lv;
             nd += __popc(dv);
             ndel += __popc(lv & ~dv);
-            if (domCopy) domCopy[T.varLD[i] + q] = dv;
+            if (domCopy) domCopy[V.ld(i) + q] = dv;
         }
         sup[i] = nd > 1;
         if (grow) atomicExch(&sm.flags[0], 1);
@@ -206,10 +220,10 @@ __device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const 
         const int k = K[i] & kCodeRow;
         if (k == 0) continue;
         const bool delta = (K[i] & kCodeDelta) != 0;
-        const int nw = T.varNW[i];
-        const uint32_t* d = dom + domOff[i];
-        const uint32_t* l = T.lastDom + T.varLD[i];
-        const int row0 = T.varRow0[i];
+        const int nw = V.nw(i);
+        const uint32_t* d = dom + V.off(i);
+        const uint32_t* l = T.lastDom + V.ld(i);
+        const int row0 = V.row0(i);
         int out = rowOff[i];
         const int last = out + k - 1;
         for (int q = 0; q < nw; ++q) {
@@ -231,27 +245,36 @@ __device__ void plan(const TableDev& T, const uint32_t* __restrict__ dom, const 
 // ---------------------------------------------------------------------------
 // update: Algorithm 2 on one 32-chunk segment (lane l owns chunk 32*seg + l)
 // ---------------------------------------------------------------------------
+// Segment state read before the plan is known (it does not depend on it).
+struct SegState {
+    uint32_t mask;
+    uint4 cur;  // dead chunks are zero
+    int lp;
+};
+
+__device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int mark) {
+    const int w = seg * 32 + (threadIdx.x & 31);
+    SegState st;
+    st.mask = T.segMask[seg];
+    st.cur = T.curr[w];
+    st.lp = mark >= 0 ? T.lastpos[w] : 0x7fffffff;
+    return st;
+}
+
 template <int U>
-__device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, int nrows,
-                                               const int32_t* s_codes, int cap, uint32_t* s_cnt) {
+__device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, const SegState& S,
+                                               int nrows, const int32_t* s_codes, int cap, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     Ctrl* C = T.ctrl;
     const int mark = P.mark;
-    const uint32_t mask = T.segMask[seg];
+    const uint32_t mask = S.mask;
     // Levels saved since the last call snapshot the index as it is now.
     for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
     if (mask == 0u) return;
-    if (nrows == 0) {
-        if (lane == 0) {
-            atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(mask));
-            atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
-        }
-        return;
-    }
     const bool act = (mask >> lane) & 1u;
     const int w = seg * 32 + lane;
-    const uint4 cur = act ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
-    const int lp = (act && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
+    const uint4 cur = S.cur;
+    const int lp = S.lp;
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
@@ -395,16 +418,25 @@ __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh,
 // ---------------------------------------------------------------------------
 // last CTA: apply Algorithm 3's removals, publish, reset the call counters
 // ---------------------------------------------------------------------------
-__device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff,
-                         Smem& sm) {
+__device__ __forceinline__ void st_release_sys(int32_t* p, int32_t v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Run by exactly one CTA once every other CTA is done with the call.
+__device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh) {
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
-    const int st = __ldcg(&C->status);
     int32_t* H = T.statusBlk;
-    if (tid == 0) sm.cnt[kCntPruned] = 0u;
+    if (tid == 0) {
+        // Thread 0 may have written control fields just before: make them
+        // visible at device scope, then share the status through shared memory.
+        __threadfence();
+        sm.flag[2] = __ldcg(&C->status);
+        sm.cnt[kCntPruned] = 0u;
+    }
     __syncthreads();
-    if (st == CT_OK) {
-        const int nh = (int)__ldcg(&C->nhard);
+    const int st = sm.flag[2];
+    if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
             const int r = __ldcg(&T.hardRow[m]);
@@ -414,9 +446,9 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
             } else {
                 // Algorithm 3 line 4: no live tuple carries the value.
                 const int i = T.rowVar[r];
-                const int a = r - T.varRow0[i];
-                atomicAnd(&dom[domOff[i] + (a >> 5)], ~(1u << (a & 31)));
-                atomicAnd(&T.lastDom[T.varLD[i] + (a >> 5)], ~(1u << (a & 31)));
+                const int a = r - V.row0(i);
+                atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+                atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 T.changed[i] = 1;
                 ++pruned;
             }
@@ -424,8 +456,7 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
         if (pruned) atomicAdd(&sm.cnt[kCntPruned], pruned);
         __syncthreads();
         if (sm.cnt[kCntPruned]) {
-            // The filtered domains of the variables that lost values go to the host;
-            // changed flags are cleared for the next call.
+            // Domains of the variables that lost values go to the host.
             uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kStatusHdr + T.nChangedWords);
             for (int q = tid; q < T.nChangedWords; q += kThreads) {
                 uint32_t bits = 0u;
@@ -434,48 +465,50 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
                     if (__ldcg(&T.changed[i])) {
                         bits |= 1u << b;
                         T.changed[i] = 0;
-                        const int nw = T.varNW[i];
-                        for (int k = 0; k < nw; ++k) outDom[T.varLD[i] + k] = __ldcg(&dom[domOff[i] + k]);
+                        for (int k = 0; k < V.nw(i); ++k) outDom[V.ld(i) + k] = __ldcg(&dom[V.off(i) + k]);
                     }
                 }
                 H[kStatusHdr + q] = (int32_t)bits;
             }
-        } else {
-            for (int q = tid; q < T.nChangedWords; q += kThreads) H[kStatusHdr + q] = 0;
         }
     }
+    // Header: one counter per thread, loaded in parallel.
+    if (tid < kStatusHdr) {
+        int32_t v = 0;
+        switch (tid) {
+            case kSlotLiveOut: v = (int32_t)__ldcg(&C->live); break;
+            case kSlotWordsIn: v = (int32_t)__ldcg(&C->words_in); break;
+            case kSlotTrailTop: v = __ldcg(&C->trail_top); break;
+            case kSlotMisses: v = __ldcg(&C->misses); break;
+            case kSlotPruned: v = (int32_t)sm.cnt[kCntPruned]; break;
+            case kSlotHits: v = __ldcg(&C->hits); break;
+            case kSlotRowsOred: v = __ldcg(&C->nrows); break;
+            case kSlotNval: v = __ldcg(&C->nval); break;
+            case kSlotNsup: v = __ldcg(&C->nsup); break;
+            case kSlotNdelta: v = __ldcg(&C->ndelta); break;
+            case kSlotNreset: v = __ldcg(&C->nreset); break;
+            case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
+            case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
+            case kSlotLocal: v = __ldcg(&C->local_found); break;
+            case kSlotHard: v = nh; break;
+            case kSlotWindows: v = __ldcg(&C->windows); break;
+            case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
+            case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
+            case kSlotT3: v = (int32_t)(__ldcg(&C->t[3]) - __ldcg(&C->t[0])); break;
+            case kSlotT4: v = (int32_t)(gtimer() - __ldcg(&C->t[0])); break;
+            default: v = 0;
+        }
+        if (tid != kSlotStatus) H[tid] = v;
+    }
     __syncthreads();
+    // Reset the per-call counters for the next call (after every read above).
     if (tid == 0) {
-        H[kSlotLiveOut] = (int32_t)__ldcg(&C->live);
-        H[kSlotWordsIn] = (int32_t)__ldcg(&C->words_in);
-        H[kSlotTrailTop] = __ldcg(&C->trail_top);
-        H[kSlotMisses] = __ldcg(&C->misses);
-        H[kSlotPruned] = (int32_t)sm.cnt[kCntPruned];
-        H[kSlotHits] = __ldcg(&C->hits);
-        H[kSlotRowsOred] = __ldcg(&C->nrows);
-        H[kSlotNval] = __ldcg(&C->nval);
-        H[kSlotNsup] = __ldcg(&C->nsup);
-        H[kSlotNdelta] = __ldcg(&C->ndelta);
-        H[kSlotNreset] = __ldcg(&C->nreset);
-        H[kSlotTrailAdded] = __ldcg(&C->trail_added);
-        H[kSlotLiveIn] = (int32_t)__ldcg(&C->live_in);
-        H[kSlotLocal] = __ldcg(&C->local_found);
-        H[kSlotHard] = (int32_t)__ldcg(&C->nhard);
-        H[kSlotWindows] = __ldcg(&C->windows);
-        const uint64_t t0 = __ldcg(&C->t[0]);
-        const uint64_t t4 = gtimer();
-        H[kSlotT1] = (int32_t)(__ldcg(&C->t[1]) - t0);
-        H[kSlotT2] = (int32_t)(__ldcg(&C->t[2]) - t0);
-        H[kSlotT3] = (int32_t)(__ldcg(&C->t[3]) - t0);
-        H[kSlotT4] = (int32_t)(t4 - t0);
-        // Reset the per-call counters for the next call.
         C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u;
         C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
         C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
         C->status = CT_OK;
-        // Everything above reaches the host before the status word that publishes it.
-        __threadfence_system();
-        *reinterpret_cast<volatile int32_t*>(&H[kSlotStatus]) = st;
+        // Everything written above reaches the host before the word that publishes it.
+        st_release_sys(&H[kSlotStatus], st);
     }
 }
 
@@ -484,24 +517,27 @@ __device__ void finalize(const TableDev& T, uint32_t* __restrict__ dom, const in
 // ---------------------------------------------------------------------------
 template <bool kLocal, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
-ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __restrict__ domOff, CallParams P) {
+ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ dom,
+                    const int32_t* __restrict__ domOff, const __grid_constant__ CallParams P) {
     __shared__ Smem sm;
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
+    const VarLayout V(T, P, domOff);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
 
-    // Residue of the first value this warp will probe, and its supports chunk
-    // (read-only), fetched while the update runs.
+    // Prologue loads that do not depend on the plan: the warp's first segment
+    // and the residue (with its supports chunk) of the first value it probes.
+    SegState seg0;
+    if (gwarp < T.nseg) seg0 = load_segment(T, gwarp, P.mark);
     int res0 = 0;
     uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
     if (T.useResidues && gwarp < T.R && lane == 0) {
         res0 = T.residue[gwarp];
         supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
     }
-
     // Levels saved since the last call snapshot lastDom as it is now.
     if (blockIdx.x == 0) {
         for (int l = P.snapFrom; l < P.snapTo; ++l)
@@ -512,7 +548,7 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     int nrows;
     bool ok;
     if (kLocal) {
-        plan(T, dom, domOff, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm);
+        plan(T, V, dom, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm);
         ok = !(sm.flags[0] || sm.flags[1]);
         nrows = sm.flags[6];
         if (blockIdx.x == 0 && tid == 0) {
@@ -522,7 +558,7 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
         }
     } else {
         if (blockIdx.x == 0) {
-            plan(T, dom, domOff, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            plan(T, V, dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
             if (tid == 0) {
                 C->nval = sm.flags[2]; C->ndelta = sm.flags[3]; C->nreset = sm.flags[4]; C->nsup = sm.flags[5];
                 C->nrows = sm.flags[6];
@@ -537,12 +573,32 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     }
     if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
 
-    // update (Algorithm 2)
-    if (tid < 12) sm.cnt[tid] = 0u;
-    __syncthreads();
-    if (ok) {
+    if (!ok || nrows == 0) {
+        // Nothing to update: currTable stays as it is. Pending level snapshots
+        // of the index are still taken.
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
+            const uint32_t mk = seg == gwarp ? seg0.mask : T.segMask[seg];
+            for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mk;
+        }
+        if (!ok) {
+            // Domain error or empty domain: publish without filtering.
+            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
+            return;
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            C->live = (uint32_t)P.prevLive;
+            C->live_in = (uint32_t)P.prevLive;
+            C->t[2] = C->t[1];
+        }
+    } else {
+        // update (Algorithm 2)
+        if (tid < 12) sm.cnt[tid] = 0u;
+        __syncthreads();
         const int cap = __ldcg(&C->trail_cap);
-        for (int seg = gwarp; seg < T.nseg; seg += nwarps) update_segment<U>(T, P, seg, nrows, sm.codes, cap, sm.cnt);
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
+            const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
+            update_segment<U>(T, P, seg, S, nrows, sm.codes, cap, sm.cnt);
+        }
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&C->live, sm.cnt[kCntLive]);
@@ -550,70 +606,73 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
             atomicAdd(&C->words_in, sm.cnt[kCntWords]);
             if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
         }
-    } else {
-        // No update: the pending snapshots of the index still have to be taken.
-        for (int seg = gwarp; seg < T.nseg; seg += nwarps)
-            for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = T.segMask[seg];
+        if (!grid_sync(C, &sm.flag[0])) return;
+        if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
+        // Algorithm 1 line 5: fail when currTable is all zero.
+        if (__ldcg(&C->status) != CT_OK || __ldcg(&C->live) == 0u) {
+            if (blockIdx.x == 0) {
+                if (tid == 0 && __ldcg(&C->status) == CT_OK) C->status = CT_INFEASIBLE;
+                __syncthreads();
+                finalize(T, V, dom, sm, 0);
+            }
+            return;
+        }
     }
-    if (!grid_sync(C, &sm.flag[0])) return;
-    if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
 
-    // failure test (Algorithm 1 line 5), then residue probes (Algorithm 3)
-    const int status1 = __ldcg(&C->status);
-    const uint32_t live = __ldcg(&C->live);
-    const bool run = status1 == CT_OK && live > 0u;
-    if (status1 == CT_OK && live == 0u && blockIdx.x == 0 && tid == 0) atomicExch(&C->status, CT_INFEASIBLE);
+    // residue probes (Algorithm 3)
     if (tid < 12) sm.cnt[tid] = 0u;
     __syncthreads();
-    if (run) {
-        // lastDom := the domains of this call (values pruned below are cleared
-        // again by the finalizing CTA).
-        if (blockIdx.x == 0) {
-            if (kLocal) {
-                for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = sm.dom[q];
-            } else {
-                for (int i = tid; i < T.arity; i += kThreads)
-                    for (int q = 0; q < T.varNW[i]; ++q) T.lastDom[T.varLD[i] + q] = dom[domOff[i] + q];
-            }
+    // lastDom := the domains of this call (values pruned below are cleared
+    // again by the finalizing CTA).
+    if (blockIdx.x == 0) {
+        if (kLocal) {
+            for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = sm.dom[q];
+        } else {
+            for (int i = tid; i < T.arity; i += kThreads)
+                for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = dom[V.off(i) + q];
         }
-        for (int r = gwarp; r < T.R; r += nwarps) {
-            const int i = __ldg(&T.rowVar[r]);
-            const int a = r - __ldg(&T.varRow0[i]);
-            bool present;
-            if (kLocal) {
-                present = sm.sup[i] && ((sm.dom[T.varLD[i] + (a >> 5)] >> (a & 31)) & 1u);
-            } else {
-                present = __ldcg(&T.varSup[i]) && ((dom[domOff[i] + (a >> 5)] >> (a & 31)) & 1u);
-            }
-            int res = res0;
-            uint4 sr = supRes0;
-            if (r != gwarp && T.useResidues && present && lane == 0) {
-                res = T.residue[r];
-                sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
-            }
-            res = __shfl_sync(0xffffffffu, res, 0);
-            probe_row(T, r, present, res, sr, sm.cnt);
+    }
+    for (int r = gwarp; r < T.R; r += nwarps) {
+        const int i = __ldg(&T.rowVar[r]);
+        const int a = r - V.row0(i);
+        bool present;
+        if (kLocal) {
+            present = sm.sup[i] && ((sm.dom[V.ld(i) + (a >> 5)] >> (a & 31)) & 1u);
+        } else {
+            present = __ldcg(&T.varSup[i]) && ((dom[V.off(i) + (a >> 5)] >> (a & 31)) & 1u);
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (sm.cnt[kCntHits]) atomicAdd(&C->hits, (int)sm.cnt[kCntHits]);
-            if (sm.cnt[kCntLocal]) atomicAdd(&C->local_found, (int)sm.cnt[kCntLocal]);
-            if (sm.cnt[kCntMiss]) atomicAdd(&C->misses, (int)sm.cnt[kCntMiss]);
-            if (sm.cnt[kCntWin]) atomicAdd(&C->windows, (int)sm.cnt[kCntWin]);
+        int res = res0;
+        uint4 sr = supRes0;
+        if (r != gwarp && T.useResidues && present && lane == 0) {
+            res = T.residue[r];
+            sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
         }
+        res = __shfl_sync(0xffffffffu, res, 0);
+        probe_row(T, r, present, res, sr, sm.cnt);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (sm.cnt[kCntHits]) atomicAdd(&C->hits, (int)sm.cnt[kCntHits]);
+        if (sm.cnt[kCntLocal]) atomicAdd(&C->local_found, (int)sm.cnt[kCntLocal]);
+        if (sm.cnt[kCntMiss]) atomicAdd(&C->misses, (int)sm.cnt[kCntMiss]);
+        if (sm.cnt[kCntWin]) atomicAdd(&C->windows, (int)sm.cnt[kCntWin]);
     }
     if (!grid_sync(C, &sm.flag[0])) return;
     if (blockIdx.x == 0 && tid == 0) C->t[3] = gtimer();
 
+    const int nh = (int)__ldcg(&C->nhard);
+    if (nh == 0) {
+        // Every value kept its support: CTA 0 publishes, the others are done.
+        if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
+        return;
+    }
     // full scan of the hard values
-    const int nh = run ? (int)__ldcg(&C->nhard) : 0;
-    if (nh > 0) {
+    {
         const int staged = min(nh, kCodeCap);
         for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.hardRow[q]);
         __syncthreads();
         for (int seg = gwarp; seg < T.nseg; seg += nwarps) scan_segment<U>(T, seg, nh, sm.codes);
     }
-
     // last-block-done
     __threadfence();
     __syncthreads();
@@ -624,7 +683,7 @@ ct_propagate_kernel(TableDev T, uint32_t* __restrict__ dom, const int32_t* __res
     __syncthreads();
     if (!sm.flag[1]) return;
     __threadfence();
-    finalize(T, dom, domOff, sm);
+    finalize(T, V, dom, sm, nh);
 }
 
 // ---------------------------------------------------------------------------

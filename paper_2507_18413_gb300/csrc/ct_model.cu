@@ -28,6 +28,7 @@ struct ct_model {
     std::vector<ct_table*> tables;
     std::vector<std::vector<int>> scopes;
     std::vector<int32_t*> d_tabOff;
+    std::vector<std::vector<int32_t>> tabOff;
     std::vector<std::vector<int>> varTables;
     std::vector<char> dirty;
     struct Level {
@@ -167,6 +168,7 @@ extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, 
     m->tables.push_back(tab);
     m->scopes.push_back(sc);
     m->d_tabOff.push_back(d_off);
+    m->tabOff.push_back(offs);
     m->dirty.push_back(1);
     for (int v : sc) m->varTables[v].push_back(T);
     if (st == CT_INFEASIBLE) m->staticInfeasible = true;
@@ -202,7 +204,7 @@ extern "C" int ct_model_propagate(ct_model* m) {
         m->dirty[T] = 0;
         ct_table* tab = m->tables[T];
         changed.assign((size_t)ct_table_changed_words(tab), 0u);
-        const int st = ct_table_propagate_on(tab, m->d_dom, m->d_tabOff[T], changed.data());
+        const int st = ct_table_propagate_on(tab, m->d_dom, m->d_tabOff[T], m->tabOff[T].data(), changed.data());
         m->propagations += 1;
         if (st == CT_INFEASIBLE) {
             m->failed = true;

@@ -68,7 +68,9 @@ struct ct_table {
     int32_t* h_status = nullptr;
     size_t statusInts = 0;
     int trailTop = 0, trailCap = 0;
-    std::vector<int> marks;
+    std::vector<int> marks;       // trail position of each saved level
+    std::vector<int> levelLive;   // live chunks of each saved level
+    int live = 0;                 // live chunks of the current state
     int levelCap = 0;
     bool failed = false;
     bool broken = false;  // a device-side wait ran out: the table is unusable
@@ -323,6 +325,12 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     d.DW = DW;
     d.nChangedWords = ct->nChW;
     d.useResidues = (opt && opt->no_residues) ? 0 : 1;
+    for (int i = 0; i < n && i < kParamArity; ++i) {
+        d.pNW[i] = ct->nw[i];
+        d.pLD[i] = ct->ld[i];
+        d.pRow0[i] = ct->row0[i];
+    }
+    ct->live = (int)W4;
 
     // The status block lives in mapped host memory: the kernel's last CTA writes
     // it directly and the host reads it after the stream synchronises.
@@ -414,7 +422,8 @@ void fill_stats(ct_table* ct) {
 // ---------------------------------------------------------------------------
 // internal entry points for the model
 // ---------------------------------------------------------------------------
-int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, uint32_t* changed) {
+int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
+                          uint32_t* changed) {
     if (!ct || !dom) {
         ct_set_error("ct_propagate: null argument");
         return CT_ERR_ARG;
@@ -443,10 +452,13 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.mark = ct->marks.empty() ? -1 : ct->marks.back();
     P.snapFrom = ct->pendingFrom;
     P.snapTo = (int)ct->marks.size();
+    P.prevLive = ct->live;
+    for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
     CT_CUDA(launch_propagate(ct->dev, ct->variant, ct->grid, dom, domOffDev, P, s));
     if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
+    const auto t1 = std::chrono::steady_clock::now();
     ct->pendingFrom = (int)ct->marks.size();
     // Wait for the status word the kernel publishes last (bounded), then fall
     // back to a stream synchronisation to collect any CUDA error.
@@ -461,6 +473,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
             break;
     }
     if (!seen) CT_CUDA(cudaStreamSynchronize(s));
+    const auto t2 = std::chrono::steady_clock::now();
     int status = hv[kSlotStatus];
     if (status == kNoChunk) {
         // The kernel returned before publishing: a grid barrier timed out.
@@ -480,12 +493,15 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     }
     fill_stats(ct);
     ct->trailTop = h[kSlotTrailTop];
+    if (status == CT_OK) ct->live = h[kSlotLiveOut];
     if (ct->profile) {
         float a = 0.f;
         CT_CUDA(cudaEventSynchronize(ct->ev[1]));
         CT_CUDA(cudaEventElapsedTime(&a, ct->ev[0], ct->ev[1]));
         ct->prof.host_ms +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ct->prof.launch_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+        ct->prof.wait_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
         ct->prof.calls += 1;
         ct->prof.kernel_ms += a;
         ct->prof.update_bytes += ct->last.update_bytes;
@@ -503,7 +519,13 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         ct->failed = true;
         ct_set_error("ct_propagate: device status %d", status);
     }
-    if (changed) std::memcpy(changed, h + kStatusHdr, (size_t)ct->nChW * sizeof(uint32_t));
+    if (changed) {
+        // The changed mask is only written when a value was pruned.
+        if (status == CT_OK && h[kSlotPruned] > 0)
+            std::memcpy(changed, h + kStatusHdr, (size_t)ct->nChW * sizeof(uint32_t));
+        else
+            std::memset(changed, 0, (size_t)ct->nChW * sizeof(uint32_t));
+    }
     return status;
 }
 
@@ -559,7 +581,7 @@ extern "C" int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_
         ct_set_error("ct_propagate: null handle");
         return CT_ERR_ARG;
     }
-    return ct_table_propagate_on(ct, dom_bits, ct->dev.varLD, changed_vars);
+    return ct_table_propagate_on(ct, dom_bits, ct->dev.varLD, ct->ld.data(), changed_vars);
 }
 
 extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t* changed_vars) {
@@ -567,11 +589,11 @@ extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t
         ct_set_error("ct_propagate_host: null argument");
         return CT_ERR_ARG;
     }
-    if (ct->empty) return ct_table_propagate_on(ct, dom_bits_host, nullptr, changed_vars);
+    if (ct->empty) return ct_table_propagate_on(ct, dom_bits_host, nullptr, nullptr, changed_vars);
     CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, dom_bits_host, (size_t)ct->DW * sizeof(uint32_t),
                             cudaMemcpyHostToDevice, ct->stream));
-    const int st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, changed_vars);
-    if (st == CT_OK) {
+    const int st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, ct->ld.data(), changed_vars);
+    if (st == CT_OK && ct->h_status[kSlotPruned] > 0) {
         // Only the variables that lost values differ from the input.
         const int32_t* h = ct->h_status;
         const uint32_t* outDom = reinterpret_cast<const uint32_t*>(h + kStatusHdr + ct->nChW);
@@ -600,6 +622,7 @@ extern "C" int ct_save(ct_table* ct, int* level_out) {
     // The snapshot itself is taken by the next propagation (or never, if the
     // level is restored before any propagation changed the state).
     ct->marks.push_back(ct->trailTop);
+    ct->levelLive.push_back(ct->live);
     if (level_out) *level_out = L;
     return CT_OK;
 }
@@ -624,7 +647,9 @@ extern "C" int ct_restore(ct_table* ct, int level) {
     }
     // A level saved after the last propagation still equals the current state.
     ct->failed = false;
+    ct->live = ct->levelLive[level];
     ct->marks.resize(level);
+    ct->levelLive.resize(level);
     ct->pendingFrom = std::min(ct->pendingFrom, level);
     return CT_OK;
 }

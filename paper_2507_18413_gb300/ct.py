@@ -61,7 +61,8 @@ class ct_call_stats(ctypes.Structure):
 
 class ct_profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_ms", ctypes.c_double), ("update_bytes", ctypes.c_int64),
-                ("filter_bytes", ctypes.c_int64), ("device_ms", ctypes.c_double), ("host_ms", ctypes.c_double)]
+                ("filter_bytes", ctypes.c_int64), ("device_ms", ctypes.c_double), ("host_ms", ctypes.c_double),
+                ("launch_ms", ctypes.c_double), ("wait_ms", ctypes.c_double)]
 
 
 class ct_search_stats(ctypes.Structure):
