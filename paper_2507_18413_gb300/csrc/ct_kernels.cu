@@ -104,11 +104,12 @@ __device__ bool grid_sync(Ctrl* C, int* s_flag) {
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned g = ld_acquire(&C->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+        unsigned arrived;
+        // Release this CTA's writes (ordered before by the CTA barrier) and, for
+        // the last arrival, acquire everybody else's.
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&C->bar_count) : "memory");
         if (arrived == gridDim.x - 1) {
             C->bar_count = 0u;
-            __threadfence();
             st_release(&C->bar_gen, g + 1u);
         } else {
             unsigned it = 0;
@@ -137,6 +138,8 @@ struct Smem {
     uint32_t cnt[12];
     int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
     int flag[4];
+    int tr[kWarps];                 // trail entries per warp, then their offsets
+    int trBase;
 };
 
 enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin };
@@ -196,25 +199,41 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
         __syncthreads();
         return;
     }
-    // Exclusive scan of the row counts, each thread owning a run of variables.
-    const int per = (T.arity + kThreads - 1) / kThreads;
-    const int b0 = tid * per, b1 = min(T.arity, b0 + per);
-    int sum = 0;
-    for (int i = b0; i < b1; ++i) sum += K[i] & kCodeRow;
-    sm.scan[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < kThreads; off <<= 1) {
-        const int a = tid >= off ? sm.scan[tid - off] : 0;
+    if (T.arity <= 32) {
+        // One warp: lane i owns variable i.
+        if (tid < 32) {
+            const int k = tid < T.arity ? (K[tid] & kCodeRow) : 0;
+            int incl = k;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += a;
+            }
+            if (tid < T.arity) rowOff[tid] = incl - k;
+            if (tid == 31) sm.scan[kThreads - 1] = incl;
+        }
         __syncthreads();
-        sm.scan[tid] += a;
+    } else {
+        // Exclusive scan of the row counts, each thread owning a run of variables.
+        const int per = (T.arity + kThreads - 1) / kThreads;
+        const int b0 = tid * per, b1 = min(T.arity, b0 + per);
+        int sum = 0;
+        for (int i = b0; i < b1; ++i) sum += K[i] & kCodeRow;
+        sm.scan[tid] = sum;
+        __syncthreads();
+        for (int off = 1; off < kThreads; off <<= 1) {
+            const int a = tid >= off ? sm.scan[tid - off] : 0;
+            __syncthreads();
+            sm.scan[tid] += a;
+            __syncthreads();
+        }
+        int run = sm.scan[tid] - sum;
+        for (int i = b0; i < b1; ++i) {
+            rowOff[i] = run;
+            run += K[i] & kCodeRow;
+        }
         __syncthreads();
     }
-    int run = sm.scan[tid] - sum;
-    for (int i = b0; i < b1; ++i) {
-        rowOff[i] = run;
-        run += K[i] & kCodeRow;
-    }
-    __syncthreads();
     // Codes: the removed values (delta) or the remaining ones (reset).
     for (int i = tid; i < T.arity; i += kThreads) {
         const int k = K[i] & kCodeRow;
@@ -261,13 +280,20 @@ __device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int
     return st;
 }
 
+struct TrailItem {
+    bool need;  // the chunk changed and has no entry above the newest mark yet
+    int w;
+    int lp;
+    uint4 cur;
+};
+
 template <int U>
 __device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, const SegState& S,
-                                               int nrows, const int32_t* s_codes, int cap, uint32_t* s_cnt) {
+                                               int nrows, const int32_t* s_codes, uint32_t* s_cnt, TrailItem& out) {
     const int lane = threadIdx.x & 31;
-    Ctrl* C = T.ctrl;
     const int mark = P.mark;
     const uint32_t mask = S.mask;
+    out.need = false;
     // Levels saved since the last call snapshot the index as it is now.
     for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
     if (mask == 0u) return;
@@ -311,23 +337,10 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
     const bool chg = act && !eq4(nv, cur);
     const bool alive = act && nz(nv);
     if (chg) T.curr[w] = nv;
-    const bool need = chg && mark >= 0 && lp < mark;
-    // Trail: one reservation per warp.
-    const uint32_t nb = __ballot_sync(0xffffffffu, need);
-    const int ntr = __popc(nb);
-    if (ntr) {
-        int tb = 0;
-        if (lane == 0) tb = atomicAdd(&C->trail_top, ntr);
-        tb = __shfl_sync(0xffffffffu, tb, 0);
-        if (tb + ntr > cap) {
-            if (lane == 0) atomicExch(&C->status, CT_ERR_OOM);
-        } else if (need) {
-            const int p = tb + __popc(nb & lanemask_lt());
-            T.trailKey[p] = make_int2(w, lp);
-            T.trailOld[p] = cur;
-            T.lastpos[w] = p;
-        }
-    }
+    out.need = chg && mark >= 0 && lp < mark;
+    out.w = w;
+    out.lp = lp;
+    out.cur = cur;
     // The segment's part of the non-zero index: the live chunks after the update.
     const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
     uint32_t words = nzwords(cur);
@@ -338,7 +351,39 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
         atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(nmask));
         atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
         atomicAdd(&s_cnt[kCntWords], words);
-        if (ntr) atomicAdd(&s_cnt[kCntTrail], (uint32_t)ntr);
+    }
+}
+
+// Trail entries of one round of segments: one reservation per CTA.
+__device__ __forceinline__ void trail_round(const TableDev& T, const TrailItem& it, int cap, Smem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nb = __ballot_sync(0xffffffffu, it.need);
+    if (lane == 0) sm.tr[warp] = __popc(nb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < kWarps; ++k) {
+            const int c = sm.tr[k];
+            sm.tr[k] = tot;
+            tot += c;
+        }
+        int base = 0;
+        if (tot) {
+            base = atomicAdd(&T.ctrl->trail_top, tot);
+            if (base + tot > cap) {
+                atomicExch(&T.ctrl->status, CT_ERR_OOM);
+                base = -1;
+            }
+            sm.cnt[kCntTrail] += (uint32_t)tot;
+        }
+        sm.trBase = base;
+    }
+    __syncthreads();
+    if (it.need && sm.trBase >= 0) {
+        const int p = sm.trBase + sm.tr[warp] + __popc(nb & lanemask_lt());
+        T.trailKey[p] = make_int2(it.w, it.lp);
+        T.trailOld[p] = it.cur;
+        T.lastpos[it.w] = p;
     }
 }
 
@@ -595,9 +640,17 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         if (tid < 12) sm.cnt[tid] = 0u;
         __syncthreads();
         const int cap = __ldcg(&C->trail_cap);
-        for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
-            const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
-            update_segment<U>(T, P, seg, S, nrows, sm.codes, cap, sm.cnt);
+        // Rounds of one segment per warp; every warp of a CTA runs every round
+        // so that the trail reservation can synchronise the CTA.
+        for (int base = blockIdx.x * kWarps; base < T.nseg; base += nwarps) {
+            const int seg = base + warp;
+            TrailItem it;
+            it.need = false;
+            if (seg < T.nseg) {
+                const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
+                update_segment<U>(T, P, seg, S, nrows, sm.codes, sm.cnt, it);
+            }
+            if (P.mark >= 0) trail_round(T, it, cap, sm);
         }
         __syncthreads();
         if (tid == 0) {
