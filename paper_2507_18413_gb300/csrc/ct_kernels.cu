@@ -273,10 +273,11 @@ struct SegState {
 
 __device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int mark) {
     const int w = seg * 32 + (threadIdx.x & 31);
+    const bool in = w < T.W4;  // the last segment may be partial
     SegState st;
     st.mask = T.segMask[seg];
-    st.cur = T.curr[w];
-    st.lp = mark >= 0 ? T.lastpos[w] : 0x7fffffff;
+    st.cur = in ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
+    st.lp = (in && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
     return st;
 }
 

@@ -293,9 +293,11 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     uint4* sup = nullptr;
     int32_t *rowVar = nullptr, *varRow0 = nullptr, *varNW = nullptr, *varLD = nullptr;
     if ((st = dalloc(ct, &sup, (size_t)R * W4)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.curr, (size_t)W4)) != CT_OK) return st;
+    // currTable and lastpos are padded to whole 32-chunk segments.
+    const size_t padChunks = (size_t)ct->nseg * 32;
+    if ((st = dalloc(ct, &d.curr, padChunks)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.segMask, (size_t)ct->nseg)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.lastpos, (size_t)W4)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.lastpos, padChunks)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.residue, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.lastDom, (size_t)DW)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) return st;
@@ -361,10 +363,11 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     }
 
     CT_CUDA(cudaMemcpyAsync(sup, hsup.data(), hsup.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ct->stream));
+    CT_CUDA(cudaMemsetAsync(d.curr, 0, padChunks * sizeof(uint4), ct->stream));
     CT_CUDA(cudaMemcpyAsync(d.curr, hcurr.data(), hcurr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                             ct->stream));
     if ((st = upload(ct, d.segMask, hmask)) != CT_OK) return st;
-    CT_CUDA(cudaMemsetAsync(d.lastpos, 0xff, (size_t)W4 * sizeof(int32_t), ct->stream));
+    CT_CUDA(cudaMemsetAsync(d.lastpos, 0xff, padChunks * sizeof(int32_t), ct->stream));
     if ((st = upload(ct, d.residue, hres)) != CT_OK) return st;
     if ((st = upload(ct, d.lastDom, hdom)) != CT_OK) return st;
     if ((st = upload(ct, rowVar, ct->rowVar)) != CT_OK) return st;
