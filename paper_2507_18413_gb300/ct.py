@@ -180,12 +180,17 @@ def _dev_ptr(x) -> int:
     return int(x.data_ptr())
 
 
+_CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream as an explicit handle
+
+
 def _stream_ptr(stream):
+    """A torch stream (or raw handle) as a cudaStream_t. Torch's default stream has
+    handle 0, which the C API reads as "no stream given"; it is passed as
+    cudaStreamLegacy instead so that the library runs in order with torch."""
     if stream is None:
         return None
-    if isinstance(stream, int):
-        return stream
-    return int(stream.cuda_stream)
+    h = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
 def make_options(grid_blocks=0, no_residues=0, profile=0):

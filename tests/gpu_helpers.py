@@ -24,8 +24,10 @@ class GpuTable:
         self.size = list(dom_size)
         self.arity = len(dom_lo)
         self.tuples = np.asarray(tuples, dtype=np.int32).reshape(-1, self.arity)
-        self.stream = stream
-        st, self.h = C.ct_create(self.arity, self.lo, self.size, self.tuples, opt=opt, stream=stream)
+        # torch's current stream: the domain copies below and the library's
+        # kernels run in stream order
+        self.stream = stream if stream is not None else self.torch.cuda.current_stream()
+        st, self.h = C.ct_create(self.arity, self.lo, self.size, self.tuples, opt=opt, stream=self.stream)
         assert st >= 0, C.last_error()
         self.create_status = st
         self.off, self.nw = C.dom_layout(self.size)

@@ -20,10 +20,10 @@ pytestmark = pytest.mark.gpu
 
 class GpuModel:
     def __init__(self, csp: O.Csp, raw_tables, opt=None):
-        torch_cuda()
+        torch = torch_cuda()
         C.load()
         self.csp = csp
-        st, self.h = C.ct_model_create(csp.dom_lo, csp.dom_size, opt=opt)
+        st, self.h = C.ct_model_create(csp.dom_lo, csp.dom_size, opt=opt, stream=torch.cuda.current_stream())
         assert st == C.CT_OK, C.last_error()
         self.add_status = []
         for scope, tup in raw_tables:
