@@ -194,6 +194,39 @@ int ct_reset_profile(ct_table* ct);
 /* ct_destroy: free the table (NULL is accepted). */
 int ct_destroy(ct_table* ct);
 
+/* ct_propagate_noalloc: one propagation of a table held entirely in buffers
+ * the caller owns, for callers that cannot allocate device memory when they
+ * propagate (a framework's memory pool owns the device, allocation is only
+ * allowed at start-up, or the implicit synchronisation of cudaMalloc/cudaFree
+ * is not acceptable). The paper has no counterpart; it is a convenience of this
+ * library. Same computation as ct_propagate (change detection, updateTable,
+ * failure test, filterDomains), without backtrack levels.
+ *   arity         1 .. 16 scope variables
+ *   dom_size      host int32[arity]; the sum of the sizes (supports rows) at most 1024
+ *   t             tuples, 1 .. 8,388,608
+ *   supports      device, 16-byte aligned: sum(dom_size) rows of Wp = 4*ceil(ceil(t/32)/4)
+ *                 uint32 words; row sum(dom_size[0..i-1]) + a holds bit j for every
+ *                 tuple j whose i-th value is dom_lo[i] + a (ct_get_support_row gives them)
+ *   curr_table    device, 16-byte aligned, in/out: Wp words of currTable; first call:
+ *                 the bits of the t tuples set, later calls: the previous output
+ *   dom_bits      device, in/out: the scope domains (layout above); filtered on CT_OK
+ *   last_dom_bits device, in/out: the domains at the end of the previous call (the full
+ *                 initial domains for the first call); dom_bits must be a subset
+ *   changed_vars  host uint32[1] or NULL: bit i set iff the call removed a value of x_i
+ *   cuda_stream   stream to run on (NULL: the legacy default stream); the call blocks
+ *                 until the result is known
+ * It allocates nothing: its scratch is one static device array of about 32 KB
+ * that every GPU loading the library keeps until the process exits. The first
+ * call on a device looks the array's device address up (and the kernel's
+ * residency); make that first call before any stream capture. All calls on a
+ * device share the array and it keeps the last call's contents (each call
+ * clears what it needs cleared), so calls that overlap on the GPU -- two host
+ * threads, or two streams -- race and must be serialised by the caller.
+ * Sizes beyond the limits return CT_ERR_ARG with a message. */
+int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t t, const uint32_t* supports,
+                         uint32_t* curr_table, uint32_t* dom_bits, uint32_t* last_dom_bits,
+                         uint32_t* changed_vars, void* cuda_stream);
+
 /* ---------------------------------------------------------------- model --
  * A model is a set of integer variables and table constraints over them,
  * propagated to a common fixpoint (Sec. 2: propagation removes unsupported

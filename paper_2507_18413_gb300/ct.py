@@ -99,6 +99,7 @@ _SIGS = {
     "ct_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ct_profile)]),
     "ct_reset_profile": (ctypes.c_int, [_P]),
     "ct_destroy": (ctypes.c_int, [_P]),
+    "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
     "ct_model_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, ctypes.POINTER(ct_options), _P,
                                        ctypes.POINTER(_P)]),
     "ct_model_add_table": (ctypes.c_int, [_P, _I32P, ctypes.c_int, _I32P, ctypes.c_int64]),
@@ -323,6 +324,15 @@ def ct_reset_profile(h):
 
 def ct_destroy(h):
     return load().ct_destroy(h)
+
+
+def ct_propagate_noalloc(dom_size, t, supports, curr_table, dom_bits, last_dom_bits, stream=None):
+    """Device buffers as torch tensors or addresses. Returns (status, changed mask word)."""
+    sz, psz = _i32(dom_size)
+    ch, pch = _u32_out(1)
+    st = load().ct_propagate_noalloc(len(sz), psz, int(t), _dev_ptr(supports), _dev_ptr(curr_table),
+                                     _dev_ptr(dom_bits), _dev_ptr(last_dom_bits), pch, _stream_ptr(stream))
+    return st, int(ch[0])
 
 
 # --------------------------------------------------------------------------
