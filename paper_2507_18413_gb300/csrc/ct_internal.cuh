@@ -130,8 +130,9 @@ struct CallParams {
 // offset of scope variable i in it. All run on `s` and return the launch error.
 // The propagation kernel is a cooperative launch of `grid` CTAs that must all
 // be resident at once (grid <= max_coresident_blocks(variant)).
-// variant: bit 0 = every CTA plans in shared memory, bit 1 = 8 loads in flight
-// per lane with 3 CTAs per SM (else 16 loads, 2 CTAs per SM).
+// variant: bit 0 = every CTA plans in shared memory, bit 1 = batches of 4 rows
+// with 3 CTAs per SM (else batches of 8 rows, 2 CTAs per SM); two batches of
+// loads are in flight per lane.
 int max_coresident_blocks(int variant);
 cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
                              const CallParams& P, cudaStream_t s);

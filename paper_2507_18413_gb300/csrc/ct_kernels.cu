@@ -9,8 +9,8 @@
 //            writes it to global memory and a grid barrier follows.
 //   update   one warp per 32-chunk segment of currTable (grid-stride):
 //            Algorithm 2 on every live 128-bit chunk. The row list is walked
-//            flat across variables with 16 independent 128-bit loads in
-//            flight per lane; each variable's OR is complemented on the delta
+//            flat across variables, software-pipelined so that each lane
+//            keeps two batches of 128-bit loads in flight; each variable's OR is complemented on the delta
 //            path and AND-ed into the chunk. Changed chunks go to the trail;
 //            the segment's live mask (the non-zero index) is rebuilt with one
 //            warp ballot.
@@ -281,6 +281,36 @@ __device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int
     return st;
 }
 
+// Row codes and supports loads of the batch of rows [q0, q0 + U).
+template <int U>
+__device__ __forceinline__ void issue_batch(const TableDev& T, const uint4* base, const int32_t* s_codes, int q0,
+                                            int nrows, size_t W4, bool act, int (&code)[U], uint4 (&v)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int q = q0 + u;
+        code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+}
+
+// OR the batch into the running mask; at the last row of a variable apply the
+// mask to the accumulator, complemented on the delta path (Algorithm 2).
+template <int U>
+__device__ __forceinline__ void combine_batch(int q0, int nrows, const int (&code)[U], const uint4 (&v)[U], uint4& m,
+                                              uint4& acc) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (q0 + u < nrows) {
+            m = or4(m, v[u]);
+            if (code[u] & kCodeLast) {
+                acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
+                m = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+}
+
 struct TrailItem {
     bool need;  // the chunk changed and has no entry above the newest mark yet
     int w;
@@ -305,34 +335,22 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
-    int code[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) code[u] = u < nrows ? (u < kCodeCap ? s_codes[u] : __ldcg(&T.codes[u])) : 0;
-    for (int q0 = 0; q0 < nrows; q0 += U) {
-        uint4 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
-        // Codes of the next batch while the loads are in flight.
-        int nxt[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + U + u;
-            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (q0 + u < nrows) {
-                m = or4(m, v[u]);
-                if (code[u] & kCodeLast) {
-                    acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
-                    m = make_uint4(0u, 0u, 0u, 0u);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) code[u] = nxt[u];
+    // Software pipeline over the row list: the loads of the next batch are in
+    // flight while the current one is combined, so a lane keeps between U and
+    // 2U loads outstanding (two register sets, no copies between them).
+    int cA[U], cB[U];
+    uint4 vA[U], vB[U];
+    issue_batch<U>(T, base, s_codes, 0, nrows, W4, act, cA, vA);
+    for (int q0 = 0; q0 < nrows; q0 += 2 * U) {
+        if (q0 + U < nrows) issue_batch<U>(T, base, s_codes, q0 + U, nrows, W4, act, cB, vB);
+        combine_batch<U>(q0, nrows, cA, vA, m, acc);
         // Every chunk of this warp is already zero: later masks cannot revive it.
         if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
+        if (q0 + 2 * U < nrows) issue_batch<U>(T, base, s_codes, q0 + 2 * U, nrows, W4, act, cA, vA);
+        if (q0 + U < nrows) {
+            combine_batch<U>(q0 + U, nrows, cB, vB, m, acc);
+            if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
+        }
     }
     const uint4 nv = and4(cur, acc);
     const bool chg = act && !eq4(nv, cur);
@@ -815,10 +833,10 @@ int coresident() {
 int max_coresident_blocks(int variant) {
     int r = 0;
     switch (variant & 3) {
-        case 0: r = coresident<false, 16, 2>(); break;
-        case 1: r = coresident<true, 16, 2>(); break;
-        case 2: r = coresident<false, 8, 3>(); break;
-        default: r = coresident<true, 8, 3>(); break;
+        case 0: r = coresident<false, 8, 2>(); break;
+        case 1: r = coresident<true, 8, 2>(); break;
+        case 2: r = coresident<false, 4, 3>(); break;
+        default: r = coresident<true, 4, 3>(); break;
     }
     cudaGetLastError();
     return r;
@@ -827,10 +845,10 @@ int max_coresident_blocks(int variant) {
 cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
                              const CallParams& P, cudaStream_t s) {
     switch (variant & 3) {
-        case 0: return launch_coop<false, 16, 2>(T, grid, dom, domOff, P, s);
-        case 1: return launch_coop<true, 16, 2>(T, grid, dom, domOff, P, s);
-        case 2: return launch_coop<false, 8, 3>(T, grid, dom, domOff, P, s);
-        default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
+        case 0: return launch_coop<false, 8, 2>(T, grid, dom, domOff, P, s);
+        case 1: return launch_coop<true, 8, 2>(T, grid, dom, domOff, P, s);
+        case 2: return launch_coop<false, 4, 3>(T, grid, dom, domOff, P, s);
+        default: return launch_coop<true, 4, 3>(T, grid, dom, domOff, P, s);
     }
 }
 
