@@ -130,9 +130,8 @@ struct CallParams {
 // offset of scope variable i in it. All run on `s` and return the launch error.
 // The propagation kernel is a cooperative launch of `grid` CTAs that must all
 // be resident at once (grid <= max_coresident_blocks(variant)).
-// variant: bit 0 = every CTA plans in shared memory, bit 1 = batches of 4 rows
-// with 3 CTAs per SM (else batches of 8 rows, 2 CTAs per SM); two batches of
-// loads are in flight per lane.
+// variant: bit 0 = every CTA plans in shared memory, bit 1 = batches of 8 rows
+// with 3 CTAs per SM (else batches of 16 rows with 2 CTAs per SM).
 int max_coresident_blocks(int variant);
 cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
                              const CallParams& P, cudaStream_t s);

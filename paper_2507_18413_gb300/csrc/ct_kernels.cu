@@ -9,8 +9,8 @@
 //            writes it to global memory and a grid barrier follows.
 //   update   one warp per 32-chunk segment of currTable (grid-stride):
 //            Algorithm 2 on every live 128-bit chunk. The row list is walked
-//            flat across variables, software-pipelined so that each lane
-//            keeps two batches of 128-bit loads in flight; each variable's OR is complemented on the delta
+//            flat across variables in batches of 16 (or 8) independent
+//            128-bit loads per lane that bypass L1; each variable's OR is complemented on the delta
 //            path and AND-ed into the chunk. Changed chunks go to the trail;
 //            the segment's live mask (the non-zero index) is rebuilt with one
 //            warp ballot.
@@ -71,15 +71,16 @@ __device__ __forceinline__ uint64_t gtimer() {
 // Read-only 128-bit load of a supports chunk (the supports never change).
 __device__ __forceinline__ uint4 ld_sup(const uint4* p) { return __ldg(p); }
 
-// Predicated read-only 128-bit load (zero when `pred` is false). Written as
-// volatile PTX so that a batch of them issues back to back, before any use.
+// Predicated read-only 128-bit load (zero when `pred` is false), not kept in
+// L1 (the supports rows stream through once per call). Written as volatile PTX
+// so that a batch of them issues back to back, before any use.
 __device__ __forceinline__ uint4 ld_sup_pred(const uint4* p, bool pred) {
     uint4 v;
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
         "setp.ne.b32 q, %5, 0;\n\t"
         "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
-        "@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+        "@q ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p), "r"((int)pred));
     return v;
@@ -281,19 +282,6 @@ __device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int
     return st;
 }
 
-// Row codes and supports loads of the batch of rows [q0, q0 + U).
-template <int U>
-__device__ __forceinline__ void issue_batch(const TableDev& T, const uint4* base, const int32_t* s_codes, int q0,
-                                            int nrows, size_t W4, bool act, int (&code)[U], uint4 (&v)[U]) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int q = q0 + u;
-        code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
-}
-
 // OR the batch into the running mask; at the last row of a variable apply the
 // mask to the accumulator, complemented on the delta path (Algorithm 2).
 template <int U>
@@ -335,22 +323,26 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
-    // Software pipeline over the row list: the loads of the next batch are in
-    // flight while the current one is combined, so a lane keeps between U and
-    // 2U loads outstanding (two register sets, no copies between them).
-    int cA[U], cB[U];
-    uint4 vA[U], vB[U];
-    issue_batch<U>(T, base, s_codes, 0, nrows, W4, act, cA, vA);
-    for (int q0 = 0; q0 < nrows; q0 += 2 * U) {
-        if (q0 + U < nrows) issue_batch<U>(T, base, s_codes, q0 + U, nrows, W4, act, cB, vB);
-        combine_batch<U>(q0, nrows, cA, vA, m, acc);
+    // Batches of U rows: U independent 128-bit loads in flight per lane; the
+    // codes of the next batch are read from shared memory meanwhile.
+    int code[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) code[u] = u < nrows ? (u < kCodeCap ? s_codes[u] : __ldcg(&T.codes[u])) : 0;
+    for (int q0 = 0; q0 < nrows; q0 += U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+        int nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + U + u;
+            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+        }
+        combine_batch<U>(q0, nrows, code, v, m, acc);
+#pragma unroll
+        for (int u = 0; u < U; ++u) code[u] = nxt[u];
         // Every chunk of this warp is already zero: later masks cannot revive it.
         if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
-        if (q0 + 2 * U < nrows) issue_batch<U>(T, base, s_codes, q0 + 2 * U, nrows, W4, act, cA, vA);
-        if (q0 + U < nrows) {
-            combine_batch<U>(q0 + U, nrows, cB, vB, m, acc);
-            if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
-        }
     }
     const uint4 nv = and4(cur, acc);
     const bool chg = act && !eq4(nv, cur);
@@ -833,10 +825,10 @@ int coresident() {
 int max_coresident_blocks(int variant) {
     int r = 0;
     switch (variant & 3) {
-        case 0: r = coresident<false, 8, 2>(); break;
-        case 1: r = coresident<true, 8, 2>(); break;
-        case 2: r = coresident<false, 4, 3>(); break;
-        default: r = coresident<true, 4, 3>(); break;
+        case 0: r = coresident<false, 16, 2>(); break;
+        case 1: r = coresident<true, 16, 2>(); break;
+        case 2: r = coresident<false, 8, 3>(); break;
+        default: r = coresident<true, 8, 3>(); break;
     }
     cudaGetLastError();
     return r;
@@ -845,10 +837,10 @@ int max_coresident_blocks(int variant) {
 cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
                              const CallParams& P, cudaStream_t s) {
     switch (variant & 3) {
-        case 0: return launch_coop<false, 8, 2>(T, grid, dom, domOff, P, s);
-        case 1: return launch_coop<true, 8, 2>(T, grid, dom, domOff, P, s);
-        case 2: return launch_coop<false, 4, 3>(T, grid, dom, domOff, P, s);
-        default: return launch_coop<true, 4, 3>(T, grid, dom, domOff, P, s);
+        case 0: return launch_coop<false, 16, 2>(T, grid, dom, domOff, P, s);
+        case 1: return launch_coop<true, 16, 2>(T, grid, dom, domOff, P, s);
+        case 2: return launch_coop<false, 8, 3>(T, grid, dom, domOff, P, s);
+        default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
     }
 }
 
