@@ -81,6 +81,25 @@ def next_edit(rng, masks):
     return new
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank propagates its own seeded stream (weak scaling, no shared data)."""
+    return seed + 1000 * rank
+
+
+def reduce_over_ranks(total_ms: float, props: int, world: int, device: str):
+    """Whole-job figures: the slowest rank's time and the propagations of all ranks."""
+    if world <= 1:
+        return total_ms, float(props)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, float(props)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def clocks_start(gpu_index):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -189,7 +208,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    seed = args.seed + 1000 * rank
+    seed = rank_seed(args.seed, rank)
     dom_lo, dom_size, tup = G.large_table(seed, args.tuples, ARITY, DOM)
     opt = C.make_options(profile=1)
     st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, opt=opt, stream=stream)
@@ -269,15 +288,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     st, prof = C.ct_get_profile(h)
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms, float(props)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        total_ms_all, props_all = float(tmax[0]), float(tsum[1])
-    else:
-        total_ms_all, props_all = total_ms, float(props)
+    total_ms_all, props_all = reduce_over_ranks(total_ms, props, world, "cuda")
     value = props_all / (total_ms_all / 1e3)
 
     # e2e: the same replay through host buffers (copies in the timed region)
@@ -347,6 +358,7 @@ def run_ours(args, rank, world):
         result["extra"] = extras(args, C, torch, stream)
     if rank == 0:
         result["cpu_baseline"] = cpu_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
+        result["cpu_baseline_bitset"] = cpu_bitset_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
     return result
 
 
@@ -458,6 +470,34 @@ def extras(args, C, torch, stream):
 # --------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # --------------------------------------------------------------------------
+
+def cpu_bitset_baseline(args, plans, dom_lo, dom_size, tup, seconds=8.0):
+    """The serial CPU bitset CT (Algorithms 1-3, 64-bit words, residues, trail) on
+    the same planned calls, saves and restores, one host thread."""
+    from oracle.serial_ct import SerialCT
+    ct = SerialCT(dom_lo, dom_size, tup)
+    import paper_2507_18413_gb300.ct as C
+    full = C.masks_to_words([np.ones(d, bool) for d in dom_size])
+    ct.propagate(full.copy())
+    ct.save()
+    done, t0 = 0, time.perf_counter()
+    for rp in plans:
+        ins = [w.copy() for w in rp.inputs]
+        for op in rp.ops:
+            if op[0] == "save":
+                ct.save()
+            elif op[0] == "restore":
+                ct.restore(op[1])
+            else:
+                ct.propagate(ins[op[1]])
+                done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    ct.close()
+    return {"value": round(done / dt, 1), "unit": UNIT, "cores": 1, "kind": "serial bitset CT (Algorithms 1-3)",
+            "sample": f"{done} propagations of the timed stream with their saves/restores, {dt:.1f} s, one thread"}
+
 
 def cpu_baseline(args, plans, dom_lo, dom_size, tup):
     from oracle import ct_oracle as O
