@@ -141,6 +141,23 @@ def clocks_stop(proc):
             "samples": len(sm)}
 
 
+def profiled_traffic():
+    """DRAM bytes per launch of the propagation kernel from the committed ncu
+    summary, if it was taken on the kernel source as it is now (else None)."""
+    import hashlib
+    import re
+    try:
+        src = open(os.path.join(ROOT, "paper_2507_18413_gb300", "csrc", "ct_kernels.cu"), "rb").read()
+        md = open(os.path.join(ROOT, "profiles", "dram_ct_propagate_kernel_stream_t4000000.md")).read()
+    except OSError:
+        return None
+    h = re.search(r"kernel_sha256_16: ([0-9a-f]{16})", md)
+    v = re.search(r"traffic_bytes_per_launch: (\d+)", md)
+    if not h or not v or hashlib.sha256(src).hexdigest()[:16] != h.group(1):
+        return None
+    return int(v.group(1))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -325,7 +342,7 @@ def run_ours(args, rank, world):
     alg = prof["update_bytes"] + prof["filter_bytes"]
     achieved = (alg / (prof["kernel_ms"] / 1e3) / 1e9) if prof["kernel_ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(), "peak_kind": peak_kind,
                 "kernel": "ct_propagate_kernel",
                 "launches": int(prof["calls"]),
                 "avg_bytes_per_launch": alg / max(prof["calls"], 1),
