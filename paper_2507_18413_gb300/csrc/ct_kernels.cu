@@ -325,25 +325,14 @@ __device__ __forceinline__ void update_unit(const TableDev& T, const CallParams&
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
-    // Batches of U*F rows: U independent 128-bit loads in flight per lane. The
-    // codes of this lane's rows of the next batch are fetched while the loads
-    // of the current one are in flight.
-    int code[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int q = u * F + sub;
-        code[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
-    }
+    // Batches of U*F rows: U independent 128-bit loads in flight per lane.
     for (int q0 = 0; q0 < nrows; q0 += U * F) {
         uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u * F + sub < nrows);
-        int nxt[U];
-#pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int q = q0 + U * F + u * F + sub;
-            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+            const int q = q0 + u * F + sub;
+            const int code = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+            v[u] = ld_sup_pred(base + (size_t)(code & kCodeRow) * W4, act && q < nrows);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -352,9 +341,8 @@ __device__ __forceinline__ void update_unit(const TableDev& T, const CallParams&
                 const int q = q0 + u * F + j;
                 if (q < nrows) {
                     if (sub == j) m = or4(m, v[u]);
-                    // flags of row q: this lane's own code when F == 1
-                    const int c = F == 1 ? code[u] : (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]));
-                    if (c & kCodeLast) {
+                    const int code = q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]);
+                    if (code & kCodeLast) {
                         uint4 M = m;
 #pragma unroll
                         for (int o = CPW; o < 32; o <<= 1) {
@@ -363,14 +351,12 @@ __device__ __forceinline__ void update_unit(const TableDev& T, const CallParams&
                             M.z |= __shfl_xor_sync(0xffffffffu, M.z, o);
                             M.w |= __shfl_xor_sync(0xffffffffu, M.w, o);
                         }
-                        acc = and4(acc, (c & kCodeDelta) ? not4(M) : M);
+                        acc = and4(acc, (code & kCodeDelta) ? not4(M) : M);
                         m = make_uint4(0u, 0u, 0u, 0u);
                     }
                 }
             }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) code[u] = nxt[u];
         // Every chunk of this warp is already zero: later masks cannot revive it.
         if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
     }
