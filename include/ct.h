@@ -58,7 +58,7 @@ typedef struct ct_model ct_model;
 
 /* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
 typedef struct ct_options {
-    int32_t lanes_per_chunk;  /* 0 = auto; 1, 2, 4 or 8 lanes share a currTable chunk in updateTable */
+    int32_t reserved0;        /* must be 0 */
     int32_t grid_blocks;      /* 0 = auto; CTAs of the cooperative propagation launch (capped at residency) */
     int32_t no_residues;      /* 1 = skip the residue probe and scan for every value */
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
@@ -79,7 +79,7 @@ typedef struct ct_table_info {
     int32_t depth;         /* saved levels on the stack */
     int32_t local_plan;    /* 1: every CTA computes the update plan in shared memory */
     int32_t grid_blocks;   /* CTAs of the propagation launch */
-    int32_t lanes_per_chunk; /* lanes sharing one chunk in updateTable */
+    int32_t reserved;
     int64_t device_bytes;  /* device memory held by the table */
 } ct_table_info;
 

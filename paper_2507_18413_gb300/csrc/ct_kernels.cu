@@ -272,23 +272,31 @@ struct SegState {
     int lp;
 };
 
-// Work unit u of the update: segment u / F, part u % F; with F lanes per chunk
-// the part covers 32 / F chunks and lane l works on chunk (l mod 32/F) of it.
-template <int F>
-__device__ __forceinline__ int unit_chunk(int unit) {
-    constexpr int CPW = 32 / F;
-    return (unit / F) * 32 + (unit % F) * CPW + ((threadIdx.x & 31) % CPW);
-}
-
-template <int F>
-__device__ __forceinline__ SegState load_segment(const TableDev& T, int unit, int mark) {
-    const int w = unit_chunk<F>(unit);
+__device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int mark) {
+    const int w = seg * 32 + (threadIdx.x & 31);
     const bool in = w < T.W4;  // the last segment may be partial
     SegState st;
-    st.mask = T.segMask[unit / F];
+    st.mask = T.segMask[seg];
     st.cur = in ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
     st.lp = (in && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
     return st;
+}
+
+// OR the batch into the running mask; at the last row of a variable apply the
+// mask to the accumulator, complemented on the delta path (Algorithm 2).
+template <int U>
+__device__ __forceinline__ void combine_batch(int q0, int nrows, const int (&code)[U], const uint4 (&v)[U], uint4& m,
+                                              uint4& acc) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (q0 + u < nrows) {
+            m = or4(m, v[u]);
+            if (code[u] & kCodeLast) {
+                acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
+                m = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
 }
 
 struct TrailItem {
@@ -298,90 +306,61 @@ struct TrailItem {
     uint4 cur;
 };
 
-// Algorithm 2 on one work unit. The F lanes that share a chunk split the flat
-// row list (lane sub takes rows q with q mod F == sub); at the last row of a
-// variable their partial ORs are combined with shuffles before the mask is
-// applied, so every lane of the chunk ends with the same accumulator.
-template <int U, int F>
-__device__ __forceinline__ void update_unit(const TableDev& T, const CallParams& P, int unit, const SegState& S,
-                                            int nrows, const int32_t* s_codes, uint32_t* s_cnt, TrailItem& out) {
-    constexpr int CPW = 32 / F;
+template <int U>
+__device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, const SegState& S,
+                                               int nrows, const int32_t* s_codes, uint32_t* s_cnt, TrailItem& out) {
     const int lane = threadIdx.x & 31;
-    const int seg = unit / F, part = unit % F;
-    const int sub = lane / CPW;
-    const int bit = part * CPW + lane % CPW;
     const int mark = P.mark;
     const uint32_t mask = S.mask;
     out.need = false;
     // Levels saved since the last call snapshot the index as it is now.
-    if (part == 0)
-        for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
-    const uint32_t partBits = F == 1 ? mask : (mask >> (part * CPW)) & ((1u << CPW) - 1u);
-    if (partBits == 0u) return;
-    const bool act = (mask >> bit) & 1u;
-    const int w = seg * 32 + bit;
+    for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
+    if (mask == 0u) return;
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
     const uint4 cur = S.cur;
     const int lp = S.lp;
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
     const size_t W4 = (size_t)T.W4;
-    // Batches of U*F rows: U independent 128-bit loads in flight per lane.
-    for (int q0 = 0; q0 < nrows; q0 += U * F) {
+    // Batches of U rows: U independent 128-bit loads in flight per lane; the
+    // codes of the next batch are read from shared memory meanwhile.
+    int code[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) code[u] = u < nrows ? (u < kCodeCap ? s_codes[u] : __ldcg(&T.codes[u])) : 0;
+    for (int q0 = 0; q0 < nrows; q0 += U) {
         uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + u * F + sub;
-            const int code = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
-            v[u] = ld_sup_pred(base + (size_t)(code & kCodeRow) * W4, act && q < nrows);
-        }
+        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+        int nxt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-#pragma unroll
-            for (int j = 0; j < F; ++j) {
-                const int q = q0 + u * F + j;
-                if (q < nrows) {
-                    if (sub == j) m = or4(m, v[u]);
-                    const int code = q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]);
-                    if (code & kCodeLast) {
-                        uint4 M = m;
-#pragma unroll
-                        for (int o = CPW; o < 32; o <<= 1) {
-                            M.x |= __shfl_xor_sync(0xffffffffu, M.x, o);
-                            M.y |= __shfl_xor_sync(0xffffffffu, M.y, o);
-                            M.z |= __shfl_xor_sync(0xffffffffu, M.z, o);
-                            M.w |= __shfl_xor_sync(0xffffffffu, M.w, o);
-                        }
-                        acc = and4(acc, (code & kCodeDelta) ? not4(M) : M);
-                        m = make_uint4(0u, 0u, 0u, 0u);
-                    }
-                }
-            }
+            const int q = q0 + U + u;
+            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
         }
+        combine_batch<U>(q0, nrows, code, v, m, acc);
+#pragma unroll
+        for (int u = 0; u < U; ++u) code[u] = nxt[u];
         // Every chunk of this warp is already zero: later masks cannot revive it.
         if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
     }
-    // The first lane of each chunk writes it back.
-    const bool own = act && sub == 0;
     const uint4 nv = and4(cur, acc);
-    const bool chg = own && !eq4(nv, cur);
-    const bool alive = own && nz(nv);
+    const bool chg = act && !eq4(nv, cur);
+    const bool alive = act && nz(nv);
     if (chg) T.curr[w] = nv;
     out.need = chg && mark >= 0 && lp < mark;
     out.w = w;
     out.lp = lp;
     out.cur = cur;
-    // This part of the non-zero index: the live chunks after the update.
-    const uint32_t newBits = __ballot_sync(0xffffffffu, alive) & (F == 1 ? 0xffffffffu : ((1u << CPW) - 1u));
-    uint32_t words = sub == 0 ? nzwords(cur) : 0u;
+    // The segment's part of the non-zero index: the live chunks after the update.
+    const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
+    uint32_t words = nzwords(cur);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(0xffffffffu, words, o);
     if (lane == 0) {
-        if (newBits != partBits) {
-            if (F == 1) T.segMask[seg] = newBits;
-            else atomicAnd(&T.segMask[seg], ~((partBits & ~newBits) << (part * CPW)));
-        }
-        atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(newBits));
-        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(partBits));
+        if (nmask != mask) T.segMask[seg] = nmask;
+        atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(nmask));
+        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
         atomicAdd(&s_cnt[kCntWords], words);
     }
 }
@@ -592,7 +571,7 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
 // ---------------------------------------------------------------------------
 // the propagation kernel
 // ---------------------------------------------------------------------------
-template <bool kLocal, int U, int kMinBlocks, int F>
+template <bool kLocal, int U, int kMinBlocks>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ dom,
                     const int32_t* __restrict__ domOff, const __grid_constant__ CallParams P) {
@@ -607,9 +586,8 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
 
     // Prologue loads that do not depend on the plan: the warp's first segment
     // and the residue (with its supports chunk) of the first value it probes.
-    const int nunits = T.nseg * F;
     SegState seg0;
-    if (gwarp < nunits) seg0 = load_segment<F>(T, gwarp, P.mark);
+    if (gwarp < T.nseg) seg0 = load_segment(T, gwarp, P.mark);
     int res0 = 0;
     uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
     if (T.useResidues && gwarp < T.R && lane == 0) {
@@ -654,11 +632,9 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     if (!ok || nrows == 0) {
         // Nothing to update: currTable stays as it is. Pending level snapshots
         // of the index are still taken.
-        if (P.snapTo > P.snapFrom) {
-            for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
-                const uint32_t mk = T.segMask[seg];
-                for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mk;
-            }
+        for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
+            const uint32_t mk = seg == gwarp ? seg0.mask : T.segMask[seg];
+            for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mk;
         }
         if (!ok) {
             // Domain error or empty domain: publish without filtering.
@@ -677,13 +653,13 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         const int cap = __ldcg(&C->trail_cap);
         // Rounds of one segment per warp; every warp of a CTA runs every round
         // so that the trail reservation can synchronise the CTA.
-        for (int base = blockIdx.x * kWarps; base < nunits; base += nwarps) {
-            const int unit = base + warp;
+        for (int base = blockIdx.x * kWarps; base < T.nseg; base += nwarps) {
+            const int seg = base + warp;
             TrailItem it;
             it.need = false;
-            if (unit < nunits) {
-                const SegState S = unit == gwarp ? seg0 : load_segment<F>(T, unit, P.mark);
-                update_unit<U, F>(T, P, unit, S, nrows, sm.codes, sm.cnt, it);
+            if (seg < T.nseg) {
+                const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
+                update_segment<U>(T, P, seg, S, nrows, sm.codes, sm.cnt, it);
             }
             if (P.mark >= 0) trail_round(T, it, cap, sm);
         }
@@ -823,64 +799,49 @@ __global__ void ct_copy_words_kernel(uint32_t* dst, const uint32_t* src, int n) 
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) dst[q] = src[q];
 }
 
-template <bool L, int U, int B, int F>
+template <bool L, int U, int B>
 cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, const CallParams& P,
                         cudaStream_t s) {
     TableDev t = T;
     CallParams p = P;
     void* args[] = {&t, &dom, (void*)&domOff, &p};
-    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, U, B, F>, dim3(grid), dim3(kThreads),
-                                       args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, U, B>, dim3(grid), dim3(kThreads), args,
+                                       0, s);
 }
 
-template <bool L, int U, int B, int F>
+template <bool L, int U, int B>
 int coresident() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, U, B, F>, kThreads, 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, U, B>, kThreads, 0) != cudaSuccess)
         return 0;
     return per * sms;
 }
 
-// Dispatch over the instantiated variants: bit 0 local plan, bit 1 wide (8 rows
-// per batch, 3 CTAs per SM, F = 1 only), bits 2-3 log2(F).
-template <bool L>
-int coresident_f(int variant) {
-    if (variant & 2) return coresident<L, 8, 3, 1>();
-    switch ((variant >> 2) & 3) {
-        case 0: return coresident<L, 16, 2, 1>();
-        case 1: return coresident<L, 16, 2, 2>();
-        case 2: return coresident<L, 16, 2, 4>();
-        default: return coresident<L, 16, 2, 8>();
-    }
-}
-
-template <bool L>
-cudaError_t launch_f(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
-                     const CallParams& P, cudaStream_t s) {
-    if (variant & 2) return launch_coop<L, 8, 3, 1>(T, grid, dom, domOff, P, s);
-    switch ((variant >> 2) & 3) {
-        case 0: return launch_coop<L, 16, 2, 1>(T, grid, dom, domOff, P, s);
-        case 1: return launch_coop<L, 16, 2, 2>(T, grid, dom, domOff, P, s);
-        case 2: return launch_coop<L, 16, 2, 4>(T, grid, dom, domOff, P, s);
-        default: return launch_coop<L, 16, 2, 8>(T, grid, dom, domOff, P, s);
-    }
-}
-
 }  // namespace
 
+// variant: bit 0 = local plan, bit 1 = wide (8 loads in flight, 3 CTAs per SM)
 int max_coresident_blocks(int variant) {
-    const int r = (variant & 1) ? coresident_f<true>(variant) : coresident_f<false>(variant);
+    int r = 0;
+    switch (variant & 3) {
+        case 0: r = coresident<false, 16, 2>(); break;
+        case 1: r = coresident<true, 16, 2>(); break;
+        case 2: r = coresident<false, 8, 3>(); break;
+        default: r = coresident<true, 8, 3>(); break;
+    }
     cudaGetLastError();
     return r;
 }
 
 cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t* dom, const int32_t* domOff,
                              const CallParams& P, cudaStream_t s) {
-    return (variant & 1) ? launch_f<true>(T, variant, grid, dom, domOff, P, s)
-                         : launch_f<false>(T, variant, grid, dom, domOff, P, s);
+    switch (variant & 3) {
+        case 0: return launch_coop<false, 16, 2>(T, grid, dom, domOff, P, s);
+        case 1: return launch_coop<true, 16, 2>(T, grid, dom, domOff, P, s);
+        case 2: return launch_coop<false, 8, 3>(T, grid, dom, domOff, P, s);
+        default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
+    }
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

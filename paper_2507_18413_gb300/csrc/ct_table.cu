@@ -61,7 +61,6 @@ struct ct_table {
     int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
     bool localPlan = true;
     int variant = 1;
-    int F = 1;  // lanes sharing one currTable chunk in the update
     int pendingFrom = 0;  // levels [pendingFrom, marks.size()) are not snapshotted yet
     TableDev dev{};
     cudaStream_t stream = nullptr;
@@ -347,35 +346,17 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
     CT_CUDA(cudaHostGetDevicePointer((void**)&d.statusBlk, ct->h_status, 0));
     {
-        // Batches of 16 rows at 2 CTAs per SM while one wave of warps covers every
-        // segment (then up to 8 lanes share a chunk, splitting its rows, as long
-        // as the wave still covers the work); beyond one wave, batches of 8
-        // rows at 3 CTAs per SM.
+        // 16 loads in flight per lane at 2 CTAs per SM while one wave of warps
+        // covers every segment; beyond that 8 loads at 3 CTAs per SM.
         const int narrow = (ct->localPlan ? 1 : 0);
         const int maxNarrow = max_coresident_blocks(narrow);
-        const int forced = opt ? opt->lanes_per_chunk : 0;
-        int lg = 0;
-        if (ct->nseg > maxNarrow * kWarps && forced <= 1) {
-            ct->variant = narrow | 2;
-        } else {
-            for (int k = 3; k >= 1; --k) {
-                const int want_f = 1 << k;
-                if (forced > 0 && forced != want_f) continue;
-                if (forced == want_f ||
-                    (int64_t)ct->nseg * want_f <= (int64_t)max_coresident_blocks(narrow | (k << 2)) * kWarps) {
-                    lg = k;
-                    break;
-                }
-            }
-            ct->variant = narrow | (lg << 2);
-        }
-        ct->F = 1 << lg;
+        ct->variant = (ct->nseg > maxNarrow * kWarps) ? (narrow | 2) : narrow;
         const int maxCo = max_coresident_blocks(ct->variant);
         if (maxCo <= 0) {
             ct_set_error("ct_create: the propagation kernel cannot be made resident on this device");
             return CT_ERR_CUDA;
         }
-        int want = (ct->nseg * ct->F + kWarps - 1) / kWarps;
+        int want = (ct->nseg + kWarps - 1) / kWarps;
         want = std::max(want, (R + 2 * kWarps - 1) / (2 * kWarps));
         if (opt && opt->grid_blocks > 0) want = opt->grid_blocks;
         ct->grid = std::max(1, std::min(want, maxCo));
@@ -750,7 +731,6 @@ extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
     r.depth = (int)ct->marks.size();
     r.local_plan = ct->localPlan ? 1 : 0;
     r.grid_blocks = ct->grid;
-    r.lanes_per_chunk = ct->F;
     r.device_bytes = ct->deviceBytes;
     int64_t live = 0;
     const int st = ct_get_index(ct, nullptr, &live);

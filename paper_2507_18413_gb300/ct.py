@@ -33,7 +33,7 @@ class CtError(RuntimeError):
 
 
 class ct_options(ctypes.Structure):
-    _fields_ = [("lanes_per_chunk", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+    _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 4)]
 
@@ -43,7 +43,7 @@ class ct_table_info(ctypes.Structure):
                 ("words", ctypes.c_int64), ("chunks", ctypes.c_int64), ("segments", ctypes.c_int32),
                 ("seg_capacity", ctypes.c_int32), ("live_chunks", ctypes.c_int64),
                 ("trail_size", ctypes.c_int64), ("depth", ctypes.c_int32),
-                ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("lanes_per_chunk", ctypes.c_int32),
+                ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64)]
 
 
@@ -194,9 +194,8 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0, lanes_per_chunk=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0):
     o = ct_options()
-    o.lanes_per_chunk = lanes_per_chunk
     o.grid_blocks = grid_blocks
     o.no_residues = no_residues
     o.profile = profile

@@ -140,13 +140,6 @@ def test_large_stream_grid_sizes(grid):
     _large_stream(60_000, calls=60, seed=12, opt=C.make_options(grid_blocks=grid), depth=12)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
-def test_large_stream_lanes_per_chunk(lanes):
-    """Rows split over 1-8 lanes per chunk: the same results bit for bit."""
-    seen = _large_stream(70_000, calls=80, seed=14, opt=C.make_options(lanes_per_chunk=lanes), depth=10)
-    assert seen["delta"] > 0 and seen["reset"] > 0
-
-
 def test_global_plan_path():
     """More supports rows than one CTA stages in shared memory: CTA 0 plans for the grid."""
     dom_lo, dom_size = [0, 0, 0], [3000, 1500, 7]
