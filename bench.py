@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--seed", type=int, default=20250724)
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--case", default="stream", choices=["stream", "bulk4e6", "bulk1e7"],
+    p.add_argument("--case", default="stream", choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7"],
                    help="bulk*: only the one-call bandwidth case (for profiling)")
     return p.parse_args()
 
@@ -476,6 +476,7 @@ def extras(args, C, torch, stream):
     try:
         out["stream_props_per_s"] = {str(t): _stream_rate(C, torch, stream, t, 128, 99 + t)
                                      for t in (100_000, 1_000_000)}
+        out["bulk_update_1e6"] = _bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)
         out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
         out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)
         out["dfs_plain_first_fail"] = _dfs_rate(C)
@@ -584,7 +585,9 @@ def main():
         B.build()
         C.load()
         stream = torch.cuda.current_stream()
-        if args.case == "bulk4e6":
+        if args.case == "bulk1e6":
+            print(json.dumps(_bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)))
+        elif args.case == "bulk4e6":
             print(json.dumps(_bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)))
         else:
             print(json.dumps(_bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)))
