@@ -453,10 +453,10 @@ def _stream_rate(C, torch, stream, t, calls, seed):
     return round(best, 1)
 
 
-def _dfs_rate(C, node_limit=3000):
+def _dfs_rate(C, node_limit=3000, host_fixpoint=0):
     nvars, ntables, arity, d, t, seed = 20, 8, 6, 32, 100_000, 2024
     rng = G.Rng(seed)
-    st, m = C.ct_model_create([0] * nvars, [d] * nvars)
+    st, m = C.ct_model_create([0] * nvars, [d] * nvars, opt=C.make_options(host_fixpoint=host_fixpoint))
     C.check(st)
     for k in range(ntables):
         scope = G.random_scope(rng, nvars, arity)
@@ -465,7 +465,9 @@ def _dfs_rate(C, node_limit=3000):
     st, s = C.ct_search_dfs(m, nvars, node_limit, True)
     C.check(st)
     C.ct_model_destroy(m)
-    return {"csp": "20 vars d=32, 8 tables arity 6 x 1e5 tuples", "nodes": s["nodes"], "fails": s["fails"],
+    return {"csp": "20 vars d=32, 8 tables arity 6 x 1e5 tuples",
+            "fixpoint": "host queue, one launch per table" if host_fixpoint else "one launch per fixpoint",
+            "nodes": s["nodes"], "fails": s["fails"],
             "solutions": s["solutions"], "complete": s["complete"], "propagations": s["propagations"],
             "seconds": round(s["seconds"], 3), "nodes_per_s": round(s["nodes"] / s["seconds"], 1),
             "table_propagations_per_s": round(s["propagations"] / s["seconds"], 1)}
@@ -480,6 +482,7 @@ def extras(args, C, torch, stream):
         out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
         out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)
         out["dfs_plain_first_fail"] = _dfs_rate(C)
+        out["dfs_plain_first_fail_host_queue"] = _dfs_rate(C, host_fixpoint=1)
     except Exception as e:  # context figures must not hide the main line
         out["error"] = repr(e)
     return out

@@ -62,7 +62,9 @@ typedef struct ct_options {
     int32_t grid_blocks;      /* 0 = auto; CTAs of the cooperative propagation launch (capped at residency) */
     int32_t no_residues;      /* 1 = skip the residue probe and scan for every value */
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
-    int32_t reserved[4];
+    int32_t host_fixpoint;    /* models: 1 = run the fixpoint queue on the host, one launch per table
+                                 propagation (default: the whole fixpoint in one launch) */
+    int32_t reserved[3];
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */

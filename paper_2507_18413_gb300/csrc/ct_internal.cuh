@@ -82,7 +82,8 @@ struct Ctrl {
     int32_t nrows;       // rows in the update plan
     int32_t nval, ndelta, nreset, nsup;
     int32_t hits, pruned, trail_added, local_found, misses, windows;
-    int32_t pad[2];
+    int32_t live_state;  // live chunks after the last update (kept across calls)
+    int32_t pad;
     uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
 };
 
@@ -126,6 +127,57 @@ struct CallParams {
     int32_t domOff[kParamArity];  // word offset of each scope domain (arity <= kParamArity)
 };
 
+// ---------------------------------------------------------------------------
+// A network of tables propagated to its fixpoint in one launch.
+// ---------------------------------------------------------------------------
+constexpr int kModelMaxTables = 2047;  // prefix arrays of a round live in shared memory
+constexpr int kModelHdr = 8;           // status block: header ints before the per-table pairs
+
+struct ModelTabCall {
+    int32_t mark;      // trail position of the table's newest level, -1 with none
+    int32_t snapFrom;  // pending level snapshots [snapFrom, snapTo)
+    int32_t snapTo;
+    int32_t pad;
+};
+
+struct ModelCtrl {
+    int32_t status;
+    uint32_t bar_count, bar_gen;
+    int32_t nwork;       // tables to propagate in the current round
+    int32_t rounds;
+    int32_t props;       // table propagations done
+    int32_t pad[10];
+};
+
+struct ModelDev {
+    const TableDev* tabs;       // [ntables]
+    const ModelTabCall* calls;  // [ntables]
+    const int32_t* scopeBase;   // [ntables + 1] prefix of the arities
+    const int32_t* scopeOff;    // word offset of every scope variable in dom
+    const int32_t* scopeVar;    // global index of every scope variable
+    int32_t* work;              // [2][ntables] work lists (ping-pong by round)
+    int32_t* unitPrefix;        // [ntables + 1] segments of the work list
+    int32_t* rowPrefix;         // [ntables + 1] supports rows of the work list
+    int32_t* prunedBy;          // [nvars] -1 none, t one table, -2 several
+    ModelCtrl* ctrl;
+    uint32_t* dom;
+    int32_t* statusBlk;         // mapped host: header, (trail_top, live) per table, domains
+    int32_t ntables, nvars, DWg, maxRounds;
+};
+
+struct RestoreDesc {
+    int32_t table, level, mark, top;
+};
+constexpr int kRestoreBatch = 256;
+struct RestoreBatch {
+    RestoreDesc d[kRestoreBatch];
+    int32_t n;
+};
+
+int max_coresident_model_blocks();
+cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s);
+cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s);
+
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
 // offset of scope variable i in it. All run on `s` and return the launch error.
 // The propagation kernel is a cooperative launch of `grid` CTAs that must all
@@ -155,6 +207,14 @@ int ct_cuda_fail(cudaError_t e, const char* what);
 int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
                           uint32_t* changed);
 const int32_t* ct_table_status_host(const ct_table* ct);
+const ctk::TableDev& ct_table_dev(const ct_table* ct);
+int ct_table_version(const ct_table* ct);
+int ct_table_is_empty(const ct_table* ct);
+int ct_table_batch_prepare(ct_table* ct, ctk::ModelTabCall* call);
+void ct_table_batch_done(ct_table* ct, int trailTop, int live);
+// Host bookkeeping of a restore; returns 1 (and fills d) when a device undo is needed.
+int ct_table_restore_prepare(ct_table* ct, int level, ctk::RestoreDesc* d);
+int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);
 int ct_table_dom_words(const ct_table* ct);
 const int32_t* ct_table_var_ld(const ct_table* ct);
 int ct_table_changed_words(const ct_table* ct);

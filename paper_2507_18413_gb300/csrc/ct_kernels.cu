@@ -100,24 +100,24 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // to arrive resets the count and advances the generation; the others poll the
 // generation at most kBarrierSpinLimit times. Returns false (after setting
 // CT_ERR_TIMEOUT) when the wait ran out.
-__device__ bool grid_sync(Ctrl* C, int* s_flag) {
+__device__ bool grid_sync_raw(unsigned* count, unsigned* gen, int* status, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = ld_acquire(&C->bar_gen);
+        const unsigned g = ld_acquire(gen);
         unsigned arrived;
         // Release this CTA's writes (ordered before by the CTA barrier) and, for
         // the last arrival, acquire everybody else's.
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&C->bar_count) : "memory");
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(count) : "memory");
         if (arrived == gridDim.x - 1) {
-            C->bar_count = 0u;
-            st_release(&C->bar_gen, g + 1u);
+            *count = 0u;
+            st_release(gen, g + 1u);
         } else {
             unsigned it = 0;
-            while (ld_acquire(&C->bar_gen) == g) {
+            while (ld_acquire(gen) == g) {
                 if (++it > kBarrierSpinLimit) {
                     ok = 0;
-                    atomicExch(&C->status, CT_ERR_TIMEOUT);
+                    atomicExch(status, CT_ERR_TIMEOUT);
                     break;
                 }
                 if (it > 64) __nanosleep(32);
@@ -127,6 +127,10 @@ __device__ bool grid_sync(Ctrl* C, int* s_flag) {
     }
     __syncthreads();
     return *s_flag != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl* C, int* s_flag) {
+    return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, s_flag);
 }
 
 struct Smem {
@@ -149,18 +153,19 @@ enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCnt
 // plan: Algorithm 1 lines 1-3 and the row selection of Algorithm 2.
 // Writes k/rowOff/sup/codes through generic pointers (shared or global).
 // ---------------------------------------------------------------------------
-// Layout of scope variable i: from the kernel parameters for small scopes.
+// Layout of scope variable i: from the kernel parameters for small scopes
+// (pOff: domain offsets passed as parameters, or null to read domOff).
 struct VarLayout {
     const TableDev& T;
-    const CallParams& P;
+    const int32_t* pOff;
     const int32_t* domOff;
     bool small;
-    __device__ VarLayout(const TableDev& t, const CallParams& p, const int32_t* d)
-        : T(t), P(p), domOff(d), small(t.arity <= kParamArity) {}
+    __device__ VarLayout(const TableDev& t, const int32_t* p, const int32_t* d)
+        : T(t), pOff(p), domOff(d), small(t.arity <= kParamArity) {}
     __device__ int nw(int i) const { return small ? T.pNW[i] : T.varNW[i]; }
     __device__ int ld(int i) const { return small ? T.pLD[i] : T.varLD[i]; }
     __device__ int row0(int i) const { return small ? T.pRow0[i] : T.varRow0[i]; }
-    __device__ int off(int i) const { return small ? P.domOff[i] : domOff[i]; }
+    __device__ int off(int i) const { return (small && pOff) ? pOff[i] : domOff[i]; }
 };
 
 __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __restrict__ dom, int32_t* K,
@@ -306,15 +311,23 @@ struct TrailItem {
     uint4 cur;
 };
 
-template <int U>
-__device__ __forceinline__ void update_segment(const TableDev& T, const CallParams& P, int seg, const SegState& S,
-                                               int nrows, const int32_t* s_codes, uint32_t* s_cnt, TrailItem& out) {
+// Row code q: from the shared-memory copy, or from global memory through L2
+// when another CTA wrote the plan in this launch (kGlobal).
+template <bool kGlobal>
+__device__ __forceinline__ int code_at(const TableDev& T, const int32_t* s_codes, int q) {
+    if (kGlobal) return __ldcg(&T.codes[q]);
+    return q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]);
+}
+
+template <int U, bool kGlobal = false>
+__device__ __forceinline__ void update_segment(const TableDev& T, int mark, int snapFrom, int snapTo, int seg,
+                                               const SegState& S, int nrows, const int32_t* s_codes,
+                                               uint32_t* s_cnt, TrailItem& out) {
     const int lane = threadIdx.x & 31;
-    const int mark = P.mark;
     const uint32_t mask = S.mask;
     out.need = false;
     // Levels saved since the last call snapshot the index as it is now.
-    for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
+    for (int l = snapFrom + lane; l < snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
     if (mask == 0u) return;
     const bool act = (mask >> lane) & 1u;
     const int w = seg * 32 + lane;
@@ -327,7 +340,7 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
     // codes of the next batch are read from shared memory meanwhile.
     int code[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) code[u] = u < nrows ? (u < kCodeCap ? s_codes[u] : __ldcg(&T.codes[u])) : 0;
+    for (int u = 0; u < U; ++u) code[u] = u < nrows ? code_at<kGlobal>(T, s_codes, u) : 0;
     for (int q0 = 0; q0 < nrows; q0 += U) {
         uint4 v[U];
 #pragma unroll
@@ -336,7 +349,7 @@ __device__ __forceinline__ void update_segment(const TableDev& T, const CallPara
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = q0 + U + u;
-            nxt[u] = q < nrows ? (q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q])) : 0;
+            nxt[u] = q < nrows ? code_at<kGlobal>(T, s_codes, q) : 0;
         }
         combine_batch<U>(q0, nrows, code, v, m, acc);
 #pragma unroll
@@ -398,6 +411,27 @@ __device__ __forceinline__ void trail_round(const TableDev& T, const TrailItem& 
     }
 }
 
+// Trail entries of one warp: one reservation per warp (used when the CTA's
+// warps work on different tables).
+__device__ __forceinline__ void trail_warp(const TableDev& T, const TrailItem& it, int cap, int* status) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nb = __ballot_sync(0xffffffffu, it.need);
+    if (!nb) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&T.ctrl->trail_top, __popc(nb));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + __popc(nb) > cap) {
+        if (lane == 0) atomicCAS(status, CT_OK, CT_ERR_OOM);
+        return;
+    }
+    if (it.need) {
+        const int p = base + __popc(nb & lanemask_lt());
+        T.trailKey[p] = make_int2(it.w, it.lp);
+        T.trailOld[p] = it.cur;
+        T.lastpos[it.w] = p;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // probe: residue of one value (warp per supports row); Algorithm 3 with residues
 // ---------------------------------------------------------------------------
@@ -441,7 +475,7 @@ __device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present
 // ---------------------------------------------------------------------------
 // scan: the hard values against the live chunks of one segment
 // ---------------------------------------------------------------------------
-template <int U>
+template <int U, bool kGlobal = false>
 __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh, const int32_t* s_rows) {
     const int lane = threadIdx.x & 31;
     const uint32_t mask = __ldcg(&T.segMask[seg]);
@@ -457,7 +491,7 @@ __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh,
             const int mm = m0 + u;
             hit[u] = false;
             if (act && mm < nh) {
-                const int r = mm < kCodeCap ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
+                const int r = (!kGlobal && mm < kCodeCap) ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
                 hit[u] = nz(and4(ld_sup(T.sup + (size_t)r * W4 + w), cur));
             }
         }
@@ -581,7 +615,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     const int warp = tid >> 5, lane = tid & 31;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
-    const VarLayout V(T, P, domOff);
+    const VarLayout V(T, P.domOff, domOff);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
 
     // Prologue loads that do not depend on the plan: the warp's first segment
@@ -659,7 +693,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             it.need = false;
             if (seg < T.nseg) {
                 const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
-                update_segment<U>(T, P, seg, S, nrows, sm.codes, sm.cnt, it);
+                update_segment<U>(T, P.mark, P.snapFrom, P.snapTo, seg, S, nrows, sm.codes, sm.cnt, it);
             }
             if (P.mark >= 0) trail_round(T, it, cap, sm);
         }
@@ -786,6 +820,290 @@ __global__ void ct_restore_kernel(TableDev T, int level, int mark, int top, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// A network of tables to its fixpoint in one cooperative launch (Sec. 2:
+// propagation removes unsupported values until GAC holds everywhere or a
+// failure is found). Rounds are Jacobi steps: every table of the round's work
+// list propagates on the same domains (plan, updateTable, failure test,
+// filterDomains); their removals are applied together; a table joins the next
+// round when another table removed a value of one of its variables. The GAC
+// closure is unique, so the order of the propagations does not matter.
+// ---------------------------------------------------------------------------
+
+// Position k of the work list whose prefix range holds u (prefix in smem).
+__device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Exclusive prefix of val(work[k]) over k < n into out[0..n] (one CTA).
+template <typename F>
+__device__ void block_prefix(const int32_t* work, int n, F val, int32_t* out, Smem& sm) {
+    const int tid = threadIdx.x;
+    const int per = (n + kThreads - 1) / kThreads;
+    const int b0 = tid * per, b1 = min(n, b0 + per);
+    int sum = 0;
+    for (int k = b0; k < b1; ++k) sum += val(__ldcg(&work[k]));
+    sm.scan[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < kThreads; off <<= 1) {
+        const int a = tid >= off ? sm.scan[tid - off] : 0;
+        __syncthreads();
+        sm.scan[tid] += a;
+        __syncthreads();
+    }
+    int run = sm.scan[tid] - sum;
+    for (int k = b0; k < b1; ++k) {
+        out[k] = run;
+        run += val(__ldcg(&work[k]));
+    }
+    if (tid == kThreads - 1) out[n] = sm.scan[kThreads - 1];
+    __syncthreads();
+}
+
+template <int U>
+__global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_constant__ ModelDev M) {
+    __shared__ Smem sm;
+    ModelCtrl* C = M.ctrl;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int gwarp = blockIdx.x * kWarps + warp;
+    const int nwarps = gridDim.x * kWarps;
+    int32_t* preU = sm.codes;                               // unit prefix of the round (smem copy)
+    int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
+    auto sync = [&]() { return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, &sm.flag[0]); };
+
+    // Levels saved since each table's last propagation snapshot it as it is now.
+    for (int t = blockIdx.x; t < M.ntables; t += gridDim.x) {
+        const TableDev& T = M.tabs[t];
+        const ModelTabCall cl = M.calls[t];
+        for (int l = cl.snapFrom; l < cl.snapTo; ++l) {
+            for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[(size_t)l * T.nseg + q] = T.segMask[q];
+            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = T.lastDom[q];
+        }
+    }
+    int cur = 0, round = 0;
+    for (;;) {
+        const int nwork = __ldcg(&C->nwork);
+        const int32_t* work = M.work + (size_t)cur * M.ntables;
+
+        // plan (Algorithm 1 lines 1-3), one CTA per table of the round
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            if (tid == 0) {
+                Ctrl* Tc = T.ctrl;
+                Tc->nrows = sm.flags[6];
+                Tc->nval = sm.flags[2];
+                Tc->ndelta = sm.flags[3];
+                Tc->nreset = sm.flags[4];
+                Tc->nsup = sm.flags[5];
+                if (sm.flags[0]) atomicCAS(&C->status, CT_OK, CT_ERR_STATE);
+                else if (sm.flags[1]) atomicCAS(&C->status, CT_OK, CT_INFEASIBLE);
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0) {
+            block_prefix(work, nwork, [&](int t) { return M.tabs[t].nseg; }, M.unitPrefix, sm);
+            block_prefix(work, nwork, [&](int t) { return M.tabs[t].R; }, M.rowPrefix, sm);
+        }
+        if (!sync()) return;
+        if (__ldcg(&C->status) != CT_OK) break;
+        for (int k = tid; k <= nwork; k += kThreads) {
+            preU[k] = __ldcg(&M.unitPrefix[k]);
+            preR[k] = __ldcg(&M.rowPrefix[k]);
+        }
+        __syncthreads();
+        const int totalUnits = preU[nwork];
+        const int totalRows = preR[nwork];
+
+        // updateTable (Algorithm 2) over (table, segment) units
+        for (int u = gwarp; u < totalUnits; u += nwarps) {
+            const int k = find_prefix(preU, nwork, u);
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const int nrows = __ldcg(&T.ctrl->nrows);
+            if (nrows == 0) continue;
+            const int seg = u - preU[k];
+            const int mark = M.calls[t].mark;
+            const SegState S = load_segment(T, seg, mark);
+            TrailItem it;
+            update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
+                                    reinterpret_cast<uint32_t*>(&T.ctrl->live), it);
+            trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
+        }
+        if (!sync()) return;
+
+        // Algorithm 1 line 5: a table whose currTable became zero fails the network.
+        bool failed = __ldcg(&C->status) != CT_OK;
+        for (int k = 0; k < nwork && !failed; ++k) {
+            const Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
+            failed = __ldcg(&Tc->nrows) > 0 && __ldcg(&Tc->live) == 0u;
+        }
+        if (failed) {
+            if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_INFEASIBLE);
+            break;
+        }
+        // lastDom := the domains of this round (removals below clear their bits)
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            for (int i = tid; i < T.arity; i += kThreads)
+                for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = __ldcg(&M.dom[V.off(i) + q]);
+        }
+        // filterDomains (Algorithm 3): residue probes over (table, row) units
+        for (int u = gwarp; u < totalRows; u += nwarps) {
+            const int k = find_prefix(preR, nwork, u);
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            const int r = u - preR[k];
+            const int i = __ldg(&T.rowVar[r]);
+            const int a = r - V.row0(i);
+            const bool present =
+                __ldcg(&T.varSup[i]) && ((__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u);
+            int res = 0;
+            uint4 sr = make_uint4(0u, 0u, 0u, 0u);
+            if (present && T.useResidues && lane == 0) {
+                res = T.residue[r];
+                sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
+            }
+            res = __shfl_sync(0xffffffffu, res, 0);
+            probe_row(T, r, present, res, sr, sm.cnt);
+        }
+        if (!sync()) return;
+
+        // full scans of the values whose residues and windows missed
+        for (int u = gwarp; u < totalUnits; u += nwarps) {
+            const int k = find_prefix(preU, nwork, u);
+            const TableDev& T = M.tabs[__ldcg(&work[k])];
+            const int nh = (int)__ldcg(&T.ctrl->nhard);
+            if (nh == 0) continue;
+            scan_segment<U, true>(T, u - preU[k], nh, nullptr);
+        }
+        if (!sync()) return;
+
+        // Algorithm 3 line 4: remove the values no live tuple carries
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const int nh = (int)__ldcg(&T.ctrl->nhard);
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            for (int m = tid; m < nh; m += kThreads) {
+                const int r = __ldcg(&T.hardRow[m]);
+                const int fc = __ldcg(&T.foundChunk[m]);
+                if (fc != kNoChunk) {
+                    T.residue[r] = fc;
+                } else {
+                    const int i = T.rowVar[r];
+                    const int a = r - V.row0(i);
+                    atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+                    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+                    const int v = M.scopeVar[M.scopeBase[t] + i];
+                    const int old = atomicCAS(&M.prunedBy[v], -1, t);
+                    if (old != -1 && old != t) atomicExch(&M.prunedBy[v], -2);
+                }
+            }
+        }
+        if (!sync()) return;
+
+        // next round: every table that shares a variable another table pruned
+        if (blockIdx.x == 0) {
+            int32_t* next = M.work + (size_t)(cur ^ 1) * M.ntables;
+            for (int k = tid; k < nwork; k += kThreads) {
+                Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
+                if (__ldcg(&Tc->nrows) > 0) Tc->live_state = (int32_t)__ldcg(&Tc->live);
+                Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+            }
+            if (tid == 0) sm.flag[2] = 0;
+            __syncthreads();
+            for (int t = tid; t < M.ntables; t += kThreads) {
+                bool dirty = false;
+                for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
+                    const int p = __ldcg(&M.prunedBy[M.scopeVar[j]]);
+                    dirty = p != -1 && p != t;
+                }
+                if (dirty) next[atomicAdd(&sm.flag[2], 1)] = t;
+            }
+            __syncthreads();
+            for (int v = tid; v < M.nvars; v += kThreads) M.prunedBy[v] = -1;
+            if (tid == 0) {
+                C->nwork = sm.flag[2];
+                C->rounds += 1;
+                C->props += nwork;
+            }
+        }
+        cur ^= 1;
+        ++round;
+        if (!sync()) return;
+        if (__ldcg(&C->nwork) == 0) break;
+        if (round >= M.maxRounds) {
+            if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_ERR_TIMEOUT);
+            break;
+        }
+    }
+
+    // publish (CTA 0; every CTA left the loop at the same point)
+    if (blockIdx.x != 0) return;
+    __threadfence();
+    __syncthreads();
+    int32_t* H = M.statusBlk;
+    for (int t = tid; t < M.ntables; t += kThreads) {
+        Ctrl* Tc = M.tabs[t].ctrl;
+        H[kModelHdr + 2 * t] = __ldcg(&Tc->trail_top);
+        H[kModelHdr + 2 * t + 1] = __ldcg(&Tc->live_state);
+        // leave every table's per-call counters clear
+        Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+        Tc->hits = 0; Tc->local_found = 0; Tc->misses = 0; Tc->windows = 0; Tc->trail_added = 0;
+        Tc->status = CT_OK;
+    }
+    uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kModelHdr + 2 * M.ntables);
+    for (int q = tid; q < M.DWg; q += kThreads) outDom[q] = __ldcg(&M.dom[q]);
+    for (int v = tid; v < M.nvars; v += kThreads) M.prunedBy[v] = -1;
+    __syncthreads();
+    if (tid == 0) {
+        const int st = __ldcg(&C->status);
+        H[1] = __ldcg(&C->rounds);
+        H[2] = __ldcg(&C->props);
+        C->status = CT_OK;
+        C->rounds = 0;
+        C->props = 0;
+        C->nwork = 0;
+        st_release_sys(&H[0], st);
+    }
+}
+
+// Restores of several tables in one launch: blockIdx.y picks the table.
+__global__ void ct_restore_batch_kernel(const TableDev* __restrict__ tabs, const __grid_constant__ RestoreBatch B) {
+    const RestoreDesc d = B.d[blockIdx.y];
+    const TableDev& T = tabs[d.table];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    for (int p = d.mark + tid; p < d.top; p += nth) {
+        const int2 k = T.trailKey[p];
+        if (k.y < d.mark) {
+            T.curr[k.x] = T.trailOld[p];
+            T.lastpos[k.x] = k.y;
+        }
+    }
+    const uint32_t* ls = T.levelSeg + (size_t)d.level * T.nseg;
+    const uint32_t* ld = T.levelDom + (size_t)d.level * T.DW;
+    for (int s = tid; s < T.nseg; s += nth) T.segMask[s] = ls[s];
+    for (int q = tid; q < T.DW; q += nth) T.lastDom[q] = ld[q];
+    if (tid == 0) {
+        T.ctrl->trail_top = d.mark;
+        T.ctrl->status = CT_OK;
+    }
+}
+
 struct WordsParam {
     uint32_t w[64];
 };
@@ -842,6 +1160,28 @@ cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t*
         case 2: return launch_coop<false, 8, 3>(T, grid, dom, domOff, P, s);
         default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
     }
+}
+
+int max_coresident_model_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_model_kernel<16>, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per * sms;
+}
+
+cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s) {
+    ModelDev m = M;
+    void* args[] = {&m};
+    return cudaLaunchCooperativeKernel((const void*)ct_model_kernel<16>, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s) {
+    if (B.n <= 0) return cudaSuccess;
+    ct_restore_batch_kernel<<<dim3(8, B.n), 256, 0, s>>>(tabs, B);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

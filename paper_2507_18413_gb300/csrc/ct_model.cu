@@ -4,11 +4,13 @@
 // unsupported values until GAC holds or a failure is found).
 //
 // All domains live in one device array; every table reads and prunes its
-// scope variables in place. The fixpoint queue runs on the host: after each
-// table propagation the host learns which scope variables changed (from the
-// 16-byte status header plus the changed mask copied back by the table) and
-// schedules the other tables that share them. One table pass is GAC for that
-// table, so a table is not re-queued by its own pruning.
+// scope variables in place. By default the whole fixpoint is one cooperative
+// launch (ct_model_kernel): rounds of all dirty tables propagated together,
+// removals applied together, until no table needs another pass. With
+// ct_options.host_fixpoint the queue runs on the host instead: after each
+// table propagation the host learns which scope variables changed and
+// schedules the other tables that share them. Either way one table pass is
+// GAC for that table, so a table is not re-queued by its own pruning.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -43,9 +45,174 @@ struct ct_model {
     bool staticInfeasible = false;
     bool failed = false;
     int64_t propagations = 0;
+    // the one-launch fixpoint
+    bool batch = true;
+    bool batchReady = false;
+    ModelDev md{};
+    TableDev* d_tabs = nullptr;
+    ModelTabCall* d_calls = nullptr;
+    ModelTabCall* h_calls = nullptr;  // pinned
+    int32_t* h_work = nullptr;        // pinned: [0] = count, then the tables
+    int32_t* h_mstatus = nullptr;     // mapped pinned
+    std::vector<int> tabVersion;
+    std::vector<void*> allocs;
+    int grid = 1;
 };
 
 namespace {
+
+template <typename T>
+int m_alloc(ct_model* m, T** p, size_t n) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("model: cudaMalloc: %s", cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    m->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CT_OK;
+}
+
+// Device descriptors of the network for the one-launch fixpoint (built once,
+// after the last table was added).
+int batch_setup(ct_model* m) {
+    const int n = (int)m->tables.size();
+    std::vector<int32_t> base(n + 1, 0), off, var;
+    for (int t = 0; t < n; ++t) {
+        base[t + 1] = base[t] + (int)m->scopes[t].size();
+        for (int k = 0; k < (int)m->scopes[t].size(); ++k) {
+            off.push_back(m->tabOff[t][k]);
+            var.push_back(m->scopes[t][k]);
+        }
+    }
+    ModelDev& M = m->md;
+    int st;
+    int32_t *dBase, *dOff, *dVar, *dPruned;
+    ModelCtrl* dCtrl;
+    if ((st = m_alloc(m, &m->d_tabs, n)) != CT_OK) return st;
+    if ((st = m_alloc(m, &m->d_calls, n)) != CT_OK) return st;
+    if ((st = m_alloc(m, &dBase, n + 1)) != CT_OK) return st;
+    if ((st = m_alloc(m, &dOff, off.size())) != CT_OK) return st;
+    if ((st = m_alloc(m, &dVar, var.size())) != CT_OK) return st;
+    if ((st = m_alloc(m, &M.work, 2 * (size_t)n)) != CT_OK) return st;
+    if ((st = m_alloc(m, &M.unitPrefix, (size_t)n + 1)) != CT_OK) return st;
+    if ((st = m_alloc(m, &M.rowPrefix, (size_t)n + 1)) != CT_OK) return st;
+    if ((st = m_alloc(m, &dPruned, (size_t)m->nvars)) != CT_OK) return st;
+    if ((st = m_alloc(m, &dCtrl, 1)) != CT_OK) return st;
+    CT_CUDA(cudaMemcpyAsync(dBase, base.data(), base.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    if (!off.empty()) {
+        CT_CUDA(cudaMemcpyAsync(dOff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        CT_CUDA(cudaMemcpyAsync(dVar, var.data(), var.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    }
+    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, (size_t)m->nvars * 4, m->stream));
+    CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), m->stream));
+    if (cudaHostAlloc((void**)&m->h_calls, std::max(n, 1) * sizeof(ModelTabCall), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&m->h_work, (size_t)(n + 1) * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg) * sizeof(int32_t),
+                      cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("model: pinned host buffers");
+        return CT_ERR_OOM;
+    }
+    int32_t* dStatus = nullptr;
+    CT_CUDA(cudaHostGetDevicePointer((void**)&dStatus, m->h_mstatus, 0));
+    M.tabs = m->d_tabs;
+    M.calls = m->d_calls;
+    M.scopeBase = dBase;
+    M.scopeOff = dOff;
+    M.scopeVar = dVar;
+    M.prunedBy = dPruned;
+    M.ctrl = dCtrl;
+    M.dom = m->d_dom;
+    M.statusBlk = dStatus;
+    M.ntables = n;
+    M.nvars = m->nvars;
+    M.DWg = m->DWg;
+    int64_t domBits = 0;
+    for (int v = 0; v < m->nvars; ++v) domBits += m->size[v];
+    M.maxRounds = (int)std::min<int64_t>(domBits + 2, 1 << 30);
+    m->tabVersion.assign(n, -1);
+    const int maxCo = max_coresident_model_blocks();
+    if (maxCo <= 0) {
+        ct_set_error("model: the fixpoint kernel cannot be made resident on this device");
+        return CT_ERR_CUDA;
+    }
+    int64_t segs = 0, rows = 0;
+    for (ct_table* tab : m->tables) {
+        segs += ct_table_dev(tab).nseg;
+        rows += ct_table_dev(tab).R;
+    }
+    int64_t want = std::max<int64_t>({(int64_t)n, (segs + kWarps - 1) / kWarps, (rows + 2 * kWarps - 1) / (2 * kWarps), 1});
+    if (m->opt.grid_blocks > 0) want = m->opt.grid_blocks;
+    m->grid = (int)std::min<int64_t>(want, maxCo);
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    m->batchReady = true;
+    return CT_OK;
+}
+
+int batch_propagate(ct_model* m) {
+    int st;
+    if (!m->batchReady && (st = batch_setup(m)) != CT_OK) return st;
+    const int n = (int)m->tables.size();
+    int nwork = 0;
+    for (int t = 0; t < n; ++t) {
+        if ((st = ct_table_batch_prepare(m->tables[t], &m->h_calls[t])) != CT_OK) return st;
+        if (m->dirty[t]) m->h_work[1 + nwork++] = t;
+    }
+    if (nwork == 0) return CT_OK;
+    // device copies of the tables whose buffers moved (trail or level growth)
+    for (int t = 0; t < n; ++t) {
+        const int v = ct_table_version(m->tables[t]);
+        if (v != m->tabVersion[t]) {
+            CT_CUDA(cudaMemcpyAsync(m->d_tabs + t, &ct_table_dev(m->tables[t]), sizeof(TableDev), cudaMemcpyHostToDevice,
+                                    m->stream));
+            m->tabVersion[t] = v;
+        }
+    }
+    m->h_work[0] = nwork;
+    CT_CUDA(cudaMemcpyAsync(m->d_calls, m->h_calls, (size_t)n * sizeof(ModelTabCall), cudaMemcpyHostToDevice, m->stream));
+    CT_CUDA(cudaMemcpyAsync(m->md.work, m->h_work + 1, (size_t)nwork * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            m->stream));
+    CT_CUDA(cudaMemcpyAsync(&m->md.ctrl->nwork, m->h_work, sizeof(int32_t), cudaMemcpyHostToDevice, m->stream));
+    volatile int32_t* H = m->h_mstatus;
+    H[0] = kNoChunk;
+    const auto t0 = std::chrono::steady_clock::now();
+    CT_CUDA(launch_model(m->md, m->grid, m->stream));
+    bool seen = false;
+    for (uint64_t it = 0;; ++it) {
+        if (H[0] != kNoChunk) {
+            seen = true;
+            break;
+        }
+        if ((it & 1023u) == 1023u && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(kHostWaitMs))
+            break;
+    }
+    if (!seen) CT_CUDA(cudaStreamSynchronize(m->stream));
+    const int status = H[0];
+    if (status == kNoChunk) {
+        ct_set_error("model: the fixpoint kernel did not publish (a device-side wait ran out)");
+        m->batch = false;
+        m->failed = true;
+        return CT_ERR_TIMEOUT;
+    }
+    m->propagations += H[2];
+    for (int t = 0; t < n; ++t) ct_table_batch_done(m->tables[t], H[kModelHdr + 2 * t], H[kModelHdr + 2 * t + 1]);
+    if (status == CT_INFEASIBLE) {
+        m->failed = true;
+        return CT_INFEASIBLE;
+    }
+    if (status != CT_OK) {
+        m->failed = true;
+        ct_set_error("model: fixpoint kernel status %d", status);
+        return status;
+    }
+    const uint32_t* outDom = reinterpret_cast<const uint32_t*>(const_cast<const int32_t*>(m->h_mstatus) + kModelHdr + 2 * n);
+    std::memcpy(m->h_dom.data(), outDom, (size_t)m->DWg * sizeof(uint32_t));
+    std::fill(m->dirty.begin(), m->dirty.end(), 0);
+    return CT_OK;
+}
 
 int popcount_var(const ct_model* m, int v) {
     int s = 0;
@@ -101,6 +268,7 @@ extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* 
     for (int v = 0; v < nvars; ++v)
         for (int a = 0; a < m->size[v]; ++a) m->h_dom[(size_t)m->off[v] + a / 32] |= 1u << (a % 32);
     if (opt) m->opt = *opt;
+    m->batch = !(opt && opt->host_fixpoint);
     cudaError_t e;
     if (cuda_stream) {
         m->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -132,8 +300,8 @@ extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, 
         ct_set_error("ct_model_add_table: bad argument");
         return CT_ERR_ARG;
     }
-    if (!m->levels.empty()) {
-        ct_set_error("ct_model_add_table: tables must be added before the first save");
+    if (!m->levels.empty() || m->batchReady) {
+        ct_set_error("ct_model_add_table: tables must be added before the first save or propagation");
         return CT_ERR_STATE;
     }
     std::vector<int> sc(scope, scope + arity);
@@ -194,6 +362,7 @@ extern "C" int ct_model_propagate(ct_model* m) {
             return CT_INFEASIBLE;
         }
     }
+    if (m->batch && (int)m->tables.size() <= kModelMaxTables) return batch_propagate(m);
     std::deque<int> q;
     for (int T = 0; T < (int)m->tables.size(); ++T)
         if (m->dirty[T]) q.push_back(T);
@@ -291,9 +460,33 @@ extern "C" int ct_model_restore(ct_model* m, int level) {
         ct_set_error("ct_model_restore: level %d not in [0, %d)", level, (int)m->levels.size());
         return CT_ERR_LEVEL;
     }
-    int st;
-    for (ct_table* tab : m->tables)
-        if ((st = ct_restore(tab, level)) != CT_OK) return st;
+    // One launch undoes the trails of every table that changed since the level.
+    RestoreBatch B;
+    B.n = 0;
+    for (int t = 0; t < (int)m->tables.size(); ++t) {
+        RestoreDesc d{};
+        const int need = ct_table_restore_prepare(m->tables[t], level, &d);
+        if (need < 0) return need;
+        if (!need) continue;
+        if (!m->batchReady) {
+            // no device copies of the tables yet: restore through the table itself
+            const int r = ct_table_restore_device(m->tables[t], d);
+            if (r != CT_OK) return r;
+            continue;
+        }
+        if (ct_table_version(m->tables[t]) != m->tabVersion[t]) {
+            CT_CUDA(cudaMemcpyAsync(m->d_tabs + t, &ct_table_dev(m->tables[t]), sizeof(TableDev),
+                                    cudaMemcpyHostToDevice, m->stream));
+            m->tabVersion[t] = ct_table_version(m->tables[t]);
+        }
+        d.table = t;
+        B.d[B.n++] = d;
+        if (B.n == kRestoreBatch) {
+            CT_CUDA(launch_restore_batch(m->d_tabs, B, m->stream));
+            B.n = 0;
+        }
+    }
+    CT_CUDA(launch_restore_batch(m->d_tabs, B, m->stream));
     // The host copy is authoritative: send it back through the pinned stage
     // (stream-ordered before any later kernel of the model).
     m->h_dom = m->levels[level].dom;
@@ -432,6 +625,10 @@ extern "C" int ct_model_destroy(ct_model* m) {
     for (int32_t* p : m->d_tabOff) cudaFree(p);
     if (m->d_dom) cudaFree(m->d_dom);
     if (m->h_stage) cudaFreeHost(m->h_stage);
+    for (void* p : m->allocs) cudaFree(p);
+    if (m->h_calls) cudaFreeHost(m->h_calls);
+    if (m->h_work) cudaFreeHost(m->h_work);
+    if (m->h_mstatus) cudaFreeHost(m->h_mstatus);
     if (m->ownStream && m->stream) cudaStreamDestroy(m->stream);
     cudaGetLastError();
     delete m;

@@ -62,6 +62,7 @@ struct ct_table {
     bool localPlan = true;
     int variant = 1;
     int pendingFrom = 0;  // levels [pendingFrom, marks.size()) are not snapshotted yet
+    int version = 0;      // bumped when device buffers behind `dev` are reallocated
     TableDev dev{};
     cudaStream_t stream = nullptr;
     bool ownStream = false;
@@ -148,6 +149,7 @@ int ensure_trail(ct_table* ct, int64_t need) {
     ct->dev.trailKey = nk;
     ct->dev.trailOld = no;
     ct->trailCap = (int)cap;
+    ct->version++;
     return CT_OK;
 }
 
@@ -178,6 +180,7 @@ int ensure_levels(ct_table* ct, int need) {
     ct->dev.levelSeg = ns;
     ct->dev.levelDom = nd;
     ct->levelCap = cap;
+    ct->version++;
     return CT_OK;
 }
 
@@ -533,6 +536,63 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
 }
 
 const int32_t* ct_table_status_host(const ct_table* ct) { return ct->h_status; }
+
+// --- the batched network path (ct_model.cu) ---
+const TableDev& ct_table_dev(const ct_table* ct) { return ct->dev; }
+int ct_table_version(const ct_table* ct) { return ct->version; }
+int ct_table_is_empty(const ct_table* ct) { return ct->empty ? 1 : 0; }
+
+int ct_table_batch_prepare(ct_table* ct, ModelTabCall* call) {
+    if (ct->broken) {
+        ct_set_error("a table is unusable after a device-side timeout");
+        return CT_ERR_TIMEOUT;
+    }
+    int st;
+    if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
+    call->mark = ct->marks.empty() ? -1 : ct->marks.back();
+    call->snapFrom = ct->pendingFrom;
+    call->snapTo = (int)ct->marks.size();
+    call->pad = 0;
+    return CT_OK;
+}
+
+void ct_table_batch_done(ct_table* ct, int trailTop, int live) {
+    ct->trailTop = trailTop;
+    if (live > 0) ct->live = live;
+    ct->pendingFrom = (int)ct->marks.size();
+    ct->failed = false;
+}
+
+int ct_table_restore_device(ct_table* ct, const RestoreDesc& d) {
+    CT_CUDA(launch_restore(ct->dev, d.level, d.mark, d.top, -1, ct->stream));
+    return CT_OK;
+}
+
+int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
+    if (level < 0 || level >= (int)ct->marks.size()) {
+        ct_set_error("restore: level %d not in [0, %d)", level, (int)ct->marks.size());
+        return CT_ERR_LEVEL;
+    }
+    if (ct->broken) {
+        ct_set_error("restore: the table is unusable after a device-side timeout");
+        return CT_ERR_TIMEOUT;
+    }
+    int need = 0;
+    const int mark = ct->marks[level];
+    if (!ct->empty && level < ct->pendingFrom) {
+        d->level = level;
+        d->mark = mark;
+        d->top = ct->trailTop;
+        ct->trailTop = mark;
+        need = 1;
+    }
+    ct->failed = false;
+    ct->live = ct->levelLive[level];
+    ct->marks.resize(level);
+    ct->levelLive.resize(level);
+    ct->pendingFrom = std::min(ct->pendingFrom, level);
+    return need;
+}
 int ct_table_dom_words(const ct_table* ct) { return ct->DW; }
 const int32_t* ct_table_var_ld(const ct_table* ct) { return ct->ld.data(); }
 int ct_table_changed_words(const ct_table* ct) { return ct->nChW; }

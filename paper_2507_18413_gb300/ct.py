@@ -35,7 +35,7 @@ class CtError(RuntimeError):
 class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("host_fixpoint", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -194,8 +194,9 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0):
     o = ct_options()
+    o.host_fixpoint = host_fixpoint
     o.grid_blocks = grid_blocks
     o.no_residues = no_residues
     o.profile = profile

@@ -17,9 +17,14 @@ from gpu_helpers import torch_cuda
 
 pytestmark = pytest.mark.gpu
 
+# both fixpoint paths: the whole fixpoint in one launch, and the host queue
+MODES = [pytest.param(0, id="device_fixpoint"), pytest.param(1, id="host_queue")]
+
 
 class GpuModel:
-    def __init__(self, csp: O.Csp, raw_tables, opt=None):
+    def __init__(self, csp: O.Csp, raw_tables, opt=None, host_fixpoint=0):
+        if opt is None:
+            opt = C.make_options(host_fixpoint=host_fixpoint)
         torch = torch_cuda()
         C.load()
         self.csp = csp
@@ -75,33 +80,36 @@ def _assert_search_equal(gm, csp, node_limit=0, count_all=True):
     return got
 
 
-def test_table1_search(golden_dir):
+@pytest.mark.parametrize("mode", MODES)
+def test_table1_search(golden_dir, mode):
     with open(os.path.join(golden_dir, "table1.json")) as f:
         g = json.load(f)
     csp = O.Csp(g["scope_dom_lo"], g["scope_dom_size"])
     csp.add_table([0, 1, 2], g["tuples"]["rows"])
-    gm = GpuModel(csp, [([0, 1, 2], g["tuples"]["rows"])])
+    gm = GpuModel(csp, [([0, 1, 2], g["tuples"]["rows"])], host_fixpoint=mode)
     d = _assert_search_equal(gm, csp)
     assert (d["nodes"], d["fails"], d["solutions"]) == (9, 0, 5)
     assert d["first_solution"] == [1, 4, 1]
     gm.close()
 
 
-def test_triangle_with_failures():
+@pytest.mark.parametrize("mode", MODES)
+def test_triangle_with_failures(mode):
     csp = O.Csp([0, 0, 0], [2, 2, 2])
     raw = [([0, 1], [[0, 0], [1, 1]]), ([1, 2], [[0, 1], [1, 0]]), ([0, 2], [[0, 0], [1, 1]])]
     for s, t in raw:
         csp.add_table(s, t)
-    gm = GpuModel(csp, raw)
+    gm = GpuModel(csp, raw, host_fixpoint=mode)
     d = _assert_search_equal(gm, csp)
     assert (d["nodes"], d["fails"], d["solutions"]) == (3, 2, 0)
     gm.close()
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("seed", range(8))
-def test_random_networks_fixpoint_and_search(seed):
+def test_random_networks_fixpoint_and_search(seed, mode):
     csp, raw = _build(300 + seed, nvars=7, ntables=5, arity=3, d=5, t=30 + 5 * seed)
-    gm = GpuModel(csp, raw)
+    gm = GpuModel(csp, raw, host_fixpoint=mode)
     st = C.ct_model_propagate(gm.h)
     st_o, masks_o, _ = O.gac_network(csp, csp.full_masks())
     assert st == st_o
@@ -110,18 +118,19 @@ def test_random_networks_fixpoint_and_search(seed):
             assert np.array_equal(m, masks_o[v])
     # the search starts from the current (propagated) state and restores it afterwards
     gm.close()
-    gm = GpuModel(csp, raw)
+    gm = GpuModel(csp, raw, host_fixpoint=mode)
     _assert_search_equal(gm, csp)
     _assert_search_equal(gm, csp, count_all=False)
     _assert_search_equal(gm, csp, node_limit=7)
     gm.close()
 
 
-def test_tiny_config_solution_count():
+@pytest.mark.parametrize("mode", MODES)
+def test_tiny_config_solution_count(mode):
     dom_lo, dom_size, tup = G.tiny_table(seed=1)
     csp = O.Csp(dom_lo, dom_size)
     csp.add_table([0, 1, 2], tup)
-    gm = GpuModel(csp, [([0, 1, 2], tup)])
+    gm = GpuModel(csp, [([0, 1, 2], tup)], host_fixpoint=mode)
     d = gm.dfs()
     assert d["solutions"] == 200 and d["complete"] == 1
     want = O.dfs(csp)
@@ -129,9 +138,10 @@ def test_tiny_config_solution_count():
     gm.close()
 
 
-def test_set_domains_save_restore():
+@pytest.mark.parametrize("mode", MODES)
+def test_set_domains_save_restore(mode):
     csp, raw = _build(901, nvars=6, ntables=4, arity=3, d=6, t=60)
-    gm = GpuModel(csp, raw)
+    gm = GpuModel(csp, raw, host_fixpoint=mode)
     assert C.ct_model_propagate(gm.h) in (C.CT_OK, C.CT_INFEASIBLE)
     st, lv = C.ct_model_save(gm.h)
     assert st == C.CT_OK
@@ -154,9 +164,10 @@ def test_set_domains_save_restore():
     gm.close()
 
 
-def test_large_config_search_prefix():
+@pytest.mark.parametrize("mode", MODES)
+def test_large_config_search_prefix(mode):
     """20 variables, d = 32, 8 tables of arity 6 x 1e5 tuples: the first nodes of the tree."""
     csp, raw = _build(2024, nvars=20, ntables=8, arity=6, d=32, t=100_000)
-    gm = GpuModel(csp, raw)
+    gm = GpuModel(csp, raw, host_fixpoint=mode)
     _assert_search_equal(gm, csp, node_limit=60)
     gm.close()
