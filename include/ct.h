@@ -281,6 +281,50 @@ int ct_model_restore(ct_model* m, int level);
 int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all,
                   ct_search_stats* out, int32_t* first_solution);
 
+/* ct_search_batch: the search of ct_search_dfs (same branching, same counts
+ * when count_all = 1 and node_limit <= 0) with many search nodes propagated
+ * together. Not in the paper, whose solver propagates one node at a time
+ * (Sec. 4); this is the batched driver of the search. The tree is first
+ * expanded depth-first down to split_depth on the model itself; the nodes
+ * found there ("open nodes", kept in depth-first order) are handed to `slots`
+ * copies of the network (the copies share the supports rows of the model's
+ * tables and own their currTable, index, trail and levels). Every slot
+ * searches the subtree of one open node depth-first; one cooperative launch
+ * per step undoes the trails the slots backtrack over and propagates the
+ * current node of every active slot to its fixpoint. A slot whose subtree is
+ * done takes the next open node, or else the untried right branch nearest the
+ * root of another slot's subtree.
+ *   slots        1 .. 4096 copies; slots x tables <= 1,048,576
+ *   split_depth  0 .. 64 (0: the root itself is the only open node)
+ *   node_limit   stop issuing nodes after this many (<= 0: no limit); the
+ *                nodes visited then differ from ct_search_dfs's
+ *   count_all    1: count every solution; 0: stop once the first solution in
+ *                depth-first order is known (nodes after it are not started,
+ *                nodes before it are finished), so first_solution equals
+ *                ct_search_dfs's while nodes and fails can differ
+ *   out          host, receives the counters as in ct_search_dfs
+ *   first_solution  host int32[nvars] or NULL: the first solution in
+ *                depth-first order among those found (with count_all = 1, or
+ *                with count_all = 0 and no node limit, ct_search_dfs's)
+ *   info         host or NULL: counters of the batching itself
+ * Returns CT_OK, CT_ERR_ARG (bad sizes), CT_ERR_STATE (a failed model),
+ * CT_ERR_OOM, CT_ERR_CUDA or CT_ERR_TIMEOUT. The model's domains and tables
+ * are back at their state before the call; the copies are kept for the next
+ * call with the same number of slots and freed by ct_model_destroy. */
+typedef struct ct_batch_info {
+    int64_t open_nodes;   /* nodes handed to the slots at split_depth */
+    int64_t split_nodes;  /* nodes propagated on the model itself above split_depth */
+    int64_t steps;        /* cooperative launches of the slots' phase */
+    int64_t steals;       /* right branches taken over from another slot */
+    int64_t slot_nodes;   /* node propagations done in the slots */
+    int32_t slots;
+    int32_t split_depth;
+    double setup_seconds; /* building or refreshing the copies */
+} ct_batch_info;
+
+int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,
+                    ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
+
 int ct_model_destroy(ct_model* m);
 
 /* ---------------------------------------------------------------- misc -- */

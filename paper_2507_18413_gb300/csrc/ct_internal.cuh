@@ -130,8 +130,13 @@ struct CallParams {
 // ---------------------------------------------------------------------------
 // A network of tables propagated to its fixpoint in one launch.
 // ---------------------------------------------------------------------------
-constexpr int kModelMaxTables = 2047;  // prefix arrays of a round live in shared memory
+constexpr int kModelMaxTables = 1 << 20;
+constexpr int kPrefixSmem = 2047;      // rounds of up to this many tables keep their prefix arrays in shared memory
 constexpr int kModelHdr = 8;           // status block: header ints before the per-table pairs
+
+struct RestoreDesc {
+    int32_t table, level, mark, top;
+};
 
 struct ModelTabCall {
     int32_t mark;      // trail position of the table's newest level, -1 with none
@@ -161,12 +166,15 @@ struct ModelDev {
     int32_t* prunedBy;          // [nvars] -1 none, t one table, -2 several
     ModelCtrl* ctrl;
     uint32_t* dom;
-    int32_t* statusBlk;         // mapped host: header, (trail_top, live) per table, domains
+    int32_t* statusBlk;         // mapped host: header, (trail_top, live) per table, domains, node statuses
+    int32_t* nodeStatus;        // [ntables / nodeTables] CT_OK or CT_INFEASIBLE per node
     int32_t ntables, nvars, DWg, maxRounds;
-};
-
-struct RestoreDesc {
-    int32_t table, level, mark, top;
+    int32_t nodeTables;         // tables per node: node of table t is t / nodeTables
+    // Optional prologue of a launch: trail undos done before anything else,
+    // and the first round's table count read from device memory.
+    const RestoreDesc* restores;  // [nrestores]
+    int32_t nrestores;
+    const int32_t* nworkIn;     // null: the count is already in ctrl->nwork
 };
 constexpr int kRestoreBatch = 256;
 struct RestoreBatch {
@@ -177,6 +185,9 @@ struct RestoreBatch {
 int max_coresident_model_blocks();
 cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s);
 cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s);
+// dst[j] (n clones, j = slot * nsrc + k) takes the state of src[k]: currTable,
+// index, residues, lastDom; empty trail (lastpos = -1) and cleared counters.
+cudaError_t launch_clone_state(const TableDev* src, const TableDev* dst, int nsrc, int n, cudaStream_t s);
 
 // Launchers (ct_kernels.cu). `dom` is the domain array, `domOff[i]` the word
 // offset of scope variable i in it. All run on `s` and return the launch error.
@@ -215,6 +226,12 @@ void ct_table_batch_done(ct_table* ct, int trailTop, int live);
 // Host bookkeeping of a restore; returns 1 (and fills d) when a device undo is needed.
 int ct_table_restore_prepare(ct_table* ct, int level, ctk::RestoreDesc* d);
 int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);
+ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status);
+void ct_table_free(ct_table* ct);
+int ct_table_save_host(ct_table* ct);
+int ct_table_depth(const ct_table* ct);
+void ct_table_adopt_state(ct_table* dst, const ct_table* src);
+int ct_table_live(const ct_table* ct);
 int ct_table_dom_words(const ct_table* ct);
 const int32_t* ct_table_var_ld(const ct_table* ct);
 int ct_table_changed_words(const ct_table* ct);

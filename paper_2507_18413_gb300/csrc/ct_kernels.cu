@@ -830,12 +830,18 @@ __global__ void ct_restore_kernel(TableDev T, int level, int mark, int top, int 
 // closure is unique, so the order of the propagations does not matter.
 // ---------------------------------------------------------------------------
 
-// Position k of the work list whose prefix range holds u (prefix in smem).
-__device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u) {
+// Entry k of a round's prefix array: the shared-memory copy, or the global
+// array itself (read through L2) when the round is too long for the copy.
+__device__ __forceinline__ int pre_at(const int32_t* pre, int k, bool global) {
+    return global ? __ldcg(pre + k) : pre[k];
+}
+
+// Position k of the work list whose prefix range holds u.
+__device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u, bool global) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= u) lo = mid;
+        if (pre_at(pre, mid, global) <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -878,18 +884,43 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
     auto sync = [&]() { return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, &sm.flag[0]); };
 
+    // Trail undos asked for with this launch (one CTA per table): the chunks
+    // changed since the level's mark get their value at the mark back, and the
+    // index and lastDom their snapshot of the level.
+    if (M.nrestores > 0) {
+        for (int i = blockIdx.x; i < M.nrestores; i += gridDim.x) {
+            const RestoreDesc d = M.restores[i];
+            const TableDev& T = M.tabs[d.table];
+            for (int p = d.mark + tid; p < d.top; p += kThreads) {
+                const int2 k = T.trailKey[p];
+                if (k.y < d.mark) {
+                    T.curr[k.x] = T.trailOld[p];
+                    T.lastpos[k.x] = k.y;
+                }
+            }
+            const uint32_t* ls = T.levelSeg + (size_t)d.level * T.nseg;
+            const uint32_t* ld = T.levelDom + (size_t)d.level * T.DW;
+            for (int q = tid; q < T.nseg; q += kThreads) T.segMask[q] = ls[q];
+            for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = ld[q];
+            if (tid == 0) {
+                T.ctrl->trail_top = d.mark;
+                T.ctrl->status = CT_OK;
+            }
+        }
+        if (!sync()) return;
+    }
     // Levels saved since each table's last propagation snapshot it as it is now.
     for (int t = blockIdx.x; t < M.ntables; t += gridDim.x) {
         const TableDev& T = M.tabs[t];
         const ModelTabCall cl = M.calls[t];
         for (int l = cl.snapFrom; l < cl.snapTo; ++l) {
-            for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[(size_t)l * T.nseg + q] = T.segMask[q];
-            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = T.lastDom[q];
+            for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[(size_t)l * T.nseg + q] = __ldcg(&T.segMask[q]);
+            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = __ldcg(&T.lastDom[q]);
         }
     }
     int cur = 0, round = 0;
     for (;;) {
-        const int nwork = __ldcg(&C->nwork);
+        const int nwork = round == 0 && M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
         const int32_t* work = M.work + (size_t)cur * M.ntables;
 
         // plan (Algorithm 1 lines 1-3), one CTA per table of the round
@@ -906,7 +937,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                 Tc->nreset = sm.flags[4];
                 Tc->nsup = sm.flags[5];
                 if (sm.flags[0]) atomicCAS(&C->status, CT_OK, CT_ERR_STATE);
-                else if (sm.flags[1]) atomicCAS(&C->status, CT_OK, CT_INFEASIBLE);
+                else if (sm.flags[1]) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;  // an empty domain
             }
             __syncthreads();
         }
@@ -916,22 +947,27 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
         if (!sync()) return;
         if (__ldcg(&C->status) != CT_OK) break;
-        for (int k = tid; k <= nwork; k += kThreads) {
-            preU[k] = __ldcg(&M.unitPrefix[k]);
-            preR[k] = __ldcg(&M.rowPrefix[k]);
+        const bool gpre = nwork > kPrefixSmem;
+        const int32_t* pU = gpre ? M.unitPrefix : preU;
+        const int32_t* pR = gpre ? M.rowPrefix : preR;
+        if (!gpre) {
+            for (int k = tid; k <= nwork; k += kThreads) {
+                preU[k] = __ldcg(&M.unitPrefix[k]);
+                preR[k] = __ldcg(&M.rowPrefix[k]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int totalUnits = preU[nwork];
-        const int totalRows = preR[nwork];
+        const int totalUnits = pre_at(pU, nwork, gpre);
+        const int totalRows = pre_at(pR, nwork, gpre);
 
         // updateTable (Algorithm 2) over (table, segment) units
         for (int u = gwarp; u < totalUnits; u += nwarps) {
-            const int k = find_prefix(preU, nwork, u);
+            const int k = find_prefix(pU, nwork, u, gpre);
             const int t = __ldcg(&work[k]);
             const TableDev& T = M.tabs[t];
             const int nrows = __ldcg(&T.ctrl->nrows);
             if (nrows == 0) continue;
-            const int seg = u - preU[k];
+            const int seg = u - pre_at(pU, k, gpre);
             const int mark = M.calls[t].mark;
             const SegState S = load_segment(T, seg, mark);
             TrailItem it;
@@ -941,15 +977,13 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
         if (!sync()) return;
 
-        // Algorithm 1 line 5: a table whose currTable became zero fails the network.
-        bool failed = __ldcg(&C->status) != CT_OK;
-        for (int k = 0; k < nwork && !failed; ++k) {
-            const Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
-            failed = __ldcg(&Tc->nrows) > 0 && __ldcg(&Tc->live) == 0u;
-        }
-        if (failed) {
-            if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_INFEASIBLE);
-            break;
+        if (__ldcg(&C->status) != CT_OK) break;
+        // Algorithm 1 line 5: a table whose currTable became zero fails its node;
+        // the node's tables leave the work list from the next round on.
+        for (int k = blockIdx.x * kThreads + tid; k < nwork; k += gridDim.x * kThreads) {
+            const int t = __ldcg(&work[k]);
+            const Ctrl* Tc = M.tabs[t].ctrl;
+            if (__ldcg(&Tc->nrows) > 0 && __ldcg(&Tc->live) == 0u) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;
         }
         // lastDom := the domains of this round (removals below clear their bits)
         for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
@@ -961,11 +995,11 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
         // filterDomains (Algorithm 3): residue probes over (table, row) units
         for (int u = gwarp; u < totalRows; u += nwarps) {
-            const int k = find_prefix(preR, nwork, u);
+            const int k = find_prefix(pR, nwork, u, gpre);
             const int t = __ldcg(&work[k]);
             const TableDev& T = M.tabs[t];
             const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
-            const int r = u - preR[k];
+            const int r = u - pre_at(pR, k, gpre);
             const int i = __ldg(&T.rowVar[r]);
             const int a = r - V.row0(i);
             const bool present =
@@ -983,11 +1017,11 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
 
         // full scans of the values whose residues and windows missed
         for (int u = gwarp; u < totalUnits; u += nwarps) {
-            const int k = find_prefix(preU, nwork, u);
+            const int k = find_prefix(pU, nwork, u, gpre);
             const TableDev& T = M.tabs[__ldcg(&work[k])];
             const int nh = (int)__ldcg(&T.ctrl->nhard);
             if (nh == 0) continue;
-            scan_segment<U, true>(T, u - preU[k], nh, nullptr);
+            scan_segment<U, true>(T, u - pre_at(pU, k, gpre), nh, nullptr);
         }
         if (!sync()) return;
 
@@ -1026,6 +1060,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             if (tid == 0) sm.flag[2] = 0;
             __syncthreads();
             for (int t = tid; t < M.ntables; t += kThreads) {
+                if (__ldcg(&M.nodeStatus[t / M.nodeTables]) != CT_OK) continue;
                 bool dirty = false;
                 for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
                     const int p = __ldcg(&M.prunedBy[M.scopeVar[j]]);
@@ -1067,6 +1102,12 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     }
     uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kModelHdr + 2 * M.ntables);
     for (int q = tid; q < M.DWg; q += kThreads) outDom[q] = __ldcg(&M.dom[q]);
+    const int nnodes = M.ntables / M.nodeTables;
+    int32_t* outNode = H + kModelHdr + 2 * M.ntables + M.DWg;
+    for (int q = tid; q < nnodes; q += kThreads) {
+        outNode[q] = __ldcg(&M.nodeStatus[q]);
+        M.nodeStatus[q] = CT_OK;
+    }
     for (int v = tid; v < M.nvars; v += kThreads) M.prunedBy[v] = -1;
     __syncthreads();
     if (tid == 0) {
@@ -1101,6 +1142,34 @@ __global__ void ct_restore_batch_kernel(const TableDev* __restrict__ tabs, const
     if (tid == 0) {
         T.ctrl->trail_top = d.mark;
         T.ctrl->status = CT_OK;
+    }
+}
+
+// Clone j takes the state of source table j % nsrc (blockIdx.y = j - y0).
+__global__ void ct_clone_state_kernel(const TableDev* __restrict__ src, const TableDev* __restrict__ dst, int nsrc,
+                                      int y0) {
+    const int j = y0 + (int)blockIdx.y;
+    const TableDev& S = src[j % nsrc];
+    const TableDev& D = dst[j];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    const int pad = S.nseg * 32;
+    for (int q = tid; q < pad; q += nth) {
+        D.curr[q] = S.curr[q];
+        D.lastpos[q] = -1;
+    }
+    for (int q = tid; q < S.nseg; q += nth) D.segMask[q] = S.segMask[q];
+    for (int q = tid; q < S.R; q += nth) D.residue[q] = S.residue[q];
+    for (int q = tid; q < S.DW; q += nth) D.lastDom[q] = S.lastDom[q];
+    for (int q = tid; q < S.arity; q += nth) D.changed[q] = 0;
+    if (tid == 0) {
+        const int32_t cap = D.ctrl->trail_cap;
+        const int32_t live = S.ctrl->live_state;
+        int32_t* c = reinterpret_cast<int32_t*>(D.ctrl);
+        for (int q = 0; q < (int)(sizeof(Ctrl) / sizeof(int32_t)); ++q) c[q] = 0;
+        D.ctrl->cur_mark = -1;
+        D.ctrl->trail_cap = cap;
+        D.ctrl->live_state = live;
     }
 }
 
@@ -1182,6 +1251,16 @@ cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cu
     if (B.n <= 0) return cudaSuccess;
     ct_restore_batch_kernel<<<dim3(8, B.n), 256, 0, s>>>(tabs, B);
     return cudaGetLastError();
+}
+
+cudaError_t launch_clone_state(const TableDev* src, const TableDev* dst, int nsrc, int n, cudaStream_t s) {
+    for (int y0 = 0; y0 < n; y0 += 65535) {
+        const int ny = (n - y0) < 65535 ? (n - y0) : 65535;
+        ct_clone_state_kernel<<<dim3(4, ny), 256, 0, s>>>(src, dst, nsrc, y0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {

@@ -17,47 +17,9 @@
 #include <deque>
 #include <vector>
 
-#include "ct_internal.cuh"
+#include "ct_model.cuh"
 
 using namespace ctk;
-
-struct ct_model {
-    int nvars = 0;
-    std::vector<int32_t> lo, size, nw, off;
-    int DWg = 0;
-    uint32_t* d_dom = nullptr;
-    std::vector<uint32_t> h_dom;
-    std::vector<ct_table*> tables;
-    std::vector<std::vector<int>> scopes;
-    std::vector<int32_t*> d_tabOff;
-    std::vector<std::vector<int32_t>> tabOff;
-    std::vector<std::vector<int>> varTables;
-    std::vector<char> dirty;
-    struct Level {
-        std::vector<uint32_t> dom;
-        std::vector<char> dirty;
-    };
-    std::vector<Level> levels;
-    uint32_t* h_stage = nullptr;  // pinned staging of the domains copied back on restore
-    cudaStream_t stream = nullptr;
-    bool ownStream = false;
-    ct_options opt{};
-    bool staticInfeasible = false;
-    bool failed = false;
-    int64_t propagations = 0;
-    // the one-launch fixpoint
-    bool batch = true;
-    bool batchReady = false;
-    ModelDev md{};
-    TableDev* d_tabs = nullptr;
-    ModelTabCall* d_calls = nullptr;
-    ModelTabCall* h_calls = nullptr;  // pinned
-    int32_t* h_work = nullptr;        // pinned: [0] = count, then the tables
-    int32_t* h_mstatus = nullptr;     // mapped pinned
-    std::vector<int> tabVersion;
-    std::vector<void*> allocs;
-    int grid = 1;
-};
 
 namespace {
 
@@ -89,7 +51,7 @@ int batch_setup(ct_model* m) {
     }
     ModelDev& M = m->md;
     int st;
-    int32_t *dBase, *dOff, *dVar, *dPruned;
+    int32_t *dBase, *dOff, *dVar, *dPruned, *dNode;
     ModelCtrl* dCtrl;
     if ((st = m_alloc(m, &m->d_tabs, n)) != CT_OK) return st;
     if ((st = m_alloc(m, &m->d_calls, n)) != CT_OK) return st;
@@ -101,6 +63,10 @@ int batch_setup(ct_model* m) {
     if ((st = m_alloc(m, &M.rowPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &dPruned, (size_t)m->nvars)) != CT_OK) return st;
     if ((st = m_alloc(m, &dCtrl, 1)) != CT_OK) return st;
+    const int nodeTables = std::max(n, 1);  // the whole network is one node
+    const int nnodes = 1;
+    if ((st = m_alloc(m, &dNode, (size_t)nnodes)) != CT_OK) return st;
+    CT_CUDA(cudaMemsetAsync(dNode, 0, (size_t)nnodes * sizeof(int32_t), m->stream));
     CT_CUDA(cudaMemcpyAsync(dBase, base.data(), base.size() * 4, cudaMemcpyHostToDevice, m->stream));
     if (!off.empty()) {
         CT_CUDA(cudaMemcpyAsync(dOff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, m->stream));
@@ -110,7 +76,7 @@ int batch_setup(ct_model* m) {
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), m->stream));
     if (cudaHostAlloc((void**)&m->h_calls, std::max(n, 1) * sizeof(ModelTabCall), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void**)&m->h_work, (size_t)(n + 1) * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg) * sizeof(int32_t),
+        cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg + nnodes) * sizeof(int32_t),
                       cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         ct_set_error("model: pinned host buffers");
@@ -124,6 +90,8 @@ int batch_setup(ct_model* m) {
     M.scopeOff = dOff;
     M.scopeVar = dVar;
     M.prunedBy = dPruned;
+    M.nodeStatus = dNode;
+    M.nodeTables = nodeTables;
     M.ctrl = dCtrl;
     M.dom = m->d_dom;
     M.statusBlk = dStatus;
@@ -199,7 +167,7 @@ int batch_propagate(ct_model* m) {
     }
     m->propagations += H[2];
     for (int t = 0; t < n; ++t) ct_table_batch_done(m->tables[t], H[kModelHdr + 2 * t], H[kModelHdr + 2 * t + 1]);
-    if (status == CT_INFEASIBLE) {
+    if (status == CT_OK && H[kModelHdr + 2 * n + m->DWg] == CT_INFEASIBLE) {
         m->failed = true;
         return CT_INFEASIBLE;
     }
@@ -237,6 +205,9 @@ int set_var(ct_model* m, int v, const uint32_t* words) {
 }
 
 }  // namespace
+
+int ct_model_popcount_var(const ct_model* m, int v) { return popcount_var(m, v); }
+int ct_model_set_var(ct_model* m, int v, const uint32_t* words) { return set_var(m, v, words); }
 
 extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* dom_size, const ct_options* opt,
                                void* cuda_stream, ct_model** out) {
@@ -621,6 +592,7 @@ extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_
 extern "C" int ct_model_destroy(ct_model* m) {
     if (!m) return CT_OK;
     if (m->stream) cudaStreamSynchronize(m->stream);
+    ct_batch_free(m->bsearch);  // the clones share the tables' supports: freed first
     for (ct_table* t : m->tables) ct_destroy(t);
     for (int32_t* p : m->d_tabOff) cudaFree(p);
     if (m->d_dom) cudaFree(m->d_dom);

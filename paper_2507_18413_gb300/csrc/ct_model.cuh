@@ -1,0 +1,54 @@
+// ct_model.cuh -- the network object shared by the model sources
+// (ct_model.cu: fixpoint and depth-first search; ct_search.cu: batched search).
+#pragma once
+#include <vector>
+
+#include "ct_internal.cuh"
+
+struct ct_batch;  // the slots of a batched search (ct_search.cu)
+
+struct ct_model {
+    int nvars = 0;
+    std::vector<int32_t> lo, size, nw, off;
+    int DWg = 0;
+    uint32_t* d_dom = nullptr;
+    std::vector<uint32_t> h_dom;
+    std::vector<ct_table*> tables;
+    std::vector<std::vector<int>> scopes;
+    std::vector<int32_t*> d_tabOff;
+    std::vector<std::vector<int32_t>> tabOff;
+    std::vector<std::vector<int>> varTables;
+    std::vector<char> dirty;
+    struct Level {
+        std::vector<uint32_t> dom;
+        std::vector<char> dirty;
+    };
+    std::vector<Level> levels;
+    uint32_t* h_stage = nullptr;  // pinned staging of the domains copied back on restore
+    cudaStream_t stream = nullptr;
+    bool ownStream = false;
+    ct_options opt{};
+    bool staticInfeasible = false;
+    bool failed = false;
+    int64_t propagations = 0;
+    // the one-launch fixpoint
+    bool batch = true;
+    bool batchReady = false;
+    ctk::ModelDev md{};
+    ctk::TableDev* d_tabs = nullptr;
+    ctk::ModelTabCall* d_calls = nullptr;
+    ctk::ModelTabCall* h_calls = nullptr;  // pinned
+    int32_t* h_work = nullptr;        // pinned: [0] = count, then the tables
+    int32_t* h_mstatus = nullptr;     // mapped pinned
+    std::vector<int> tabVersion;
+    std::vector<void*> allocs;
+    int grid = 1;
+    ct_batch* bsearch = nullptr;  // built by the first batched search, kept for the next ones
+};
+
+// Internal helpers of ct_model.cu used by the batched search.
+int ct_model_popcount_var(const ct_model* m, int v);
+// Replace the domain of variable v (host mirror and device) and schedule its tables.
+int ct_model_set_var(ct_model* m, int v, const uint32_t* words);
+// Free the batched-search slots of m (ct_search.cu).
+void ct_batch_free(ct_batch* b);

@@ -1,0 +1,707 @@
+// ct_search.cu -- batched depth-first search. The solver of Sec. 4 alternates
+// branching and propagation on one node at a time; here many search nodes are
+// propagated to their fixpoints together, one cooperative launch per step.
+//
+// The tree is first expanded on the model itself down to a split depth; the
+// nodes met there (open nodes, in depth-first order) are handed to B slots.
+// A slot is a copy of the network whose tables share the model's supports
+// rows and own their currTable, index, residues, trail and levels; its
+// variables and domain words sit in their own range of one domain array. Each
+// slot searches its open node's subtree depth-first with the model's
+// branching rule (first-fail, left x = min dom x, right x != min dom x). Per
+// step the host turns every slot's last result into its next node (branch,
+// or backtrack to a level and take the right branch), and one launch of the
+// fixpoint kernel first undoes the trails of the backtracking slots, then
+// propagates the dirty tables of all slots together; a table failure fails
+// only its own slot's node. A slot whose subtree is done takes the next open
+// node, or the untried right branch nearest the root of another slot.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "ct_model.cuh"
+
+using namespace ctk;
+
+namespace {
+
+struct Frame {
+    int x;       // branching variable (model index)
+    int a;       // branching value (offset in the initial domain)
+    int branch;  // 0: left subtree open, 1: right subtree open, 2: right subtree given to another slot
+};
+
+struct OpenNode {
+    std::vector<uint32_t> dom;  // domain words before the node's propagation
+    int depth;
+    std::vector<uint8_t> path;  // branch bits from the root (0 left, 1 right)
+};
+
+struct Slot {
+    bool active = false;   // exploring a subtree
+    bool pending = false;  // its current node is propagated by the next launch
+    int depth0 = 0;        // depth of the subtree root
+    size_t path0 = 0;      // path length of the subtree root
+    std::vector<Frame> stack;
+    std::vector<uint32_t> levelDom;  // domain words at each saved level, level-major
+    std::vector<uint8_t> path;       // path of the current node
+};
+
+// P comes after S in depth-first order without being an ancestor of S.
+bool after(const std::vector<uint8_t>& P, const std::vector<uint8_t>& S) {
+    const size_t n = std::min(P.size(), S.size());
+    for (size_t k = 0; k < n; ++k)
+        if (P[k] != S[k]) return P[k] > S[k];
+    return false;
+}
+
+int popcount_words(const uint32_t* w, int n) {
+    int s = 0;
+    for (int q = 0; q < n; ++q) s += __builtin_popcount(w[q]);
+    return s;
+}
+
+// First-fail: the unfixed variable with the smallest domain, ties to the lowest index; -1 if all are fixed.
+int first_fail(const ct_model* m, const uint32_t* dom) {
+    int x = -1, best = 0;
+    for (int v = 0; v < m->nvars; ++v) {
+        const int s = popcount_words(dom + m->off[v], m->nw[v]);
+        if (s > 1 && (x < 0 || s < best)) {
+            x = v;
+            best = s;
+        }
+    }
+    return x;
+}
+
+int min_value(const ct_model* m, const uint32_t* dom, int v) {
+    for (int q = 0; q < m->nw[v]; ++q) {
+        const uint32_t w = dom[m->off[v] + q];
+        if (w) return q * 32 + __builtin_ctz(w);
+    }
+    return 0;
+}
+
+size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+}  // namespace
+
+struct ct_batch {
+    int B = 0, T = 0, n = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<ct_table*> tabs;  // [n], slot-major: table k of slot s is s * T + k
+    TableDev* d_tabs = nullptr;   // [n]
+    TableDev* d_src = nullptr;    // [T] the model's own tables, source of the state copies
+    std::vector<int> tabVersion;
+    // one staging area per step, uploaded with one or two copies:
+    // [nwork | calls[n] | dom[B * DWg] | work[2n] | restores[n]]
+    char* h_stage = nullptr;  // pinned
+    char* d_stage = nullptr;
+    size_t offCalls = 0, offDom = 0, offWork = 0, offRest = 0, stageBytes = 0;
+    int32_t* h_status = nullptr;  // mapped: header, (trail_top, live) per table, domains, node statuses
+    ModelDev md{};
+    int grid = 1;
+    std::vector<void*> allocs;
+    bool broken = false;
+
+    int32_t* nworkHost() { return reinterpret_cast<int32_t*>(h_stage); }
+    ModelTabCall* callsHost() { return reinterpret_cast<ModelTabCall*>(h_stage + offCalls); }
+    uint32_t* domHost() { return reinterpret_cast<uint32_t*>(h_stage + offDom); }
+    int32_t* workHost() { return reinterpret_cast<int32_t*>(h_stage + offWork); }
+    RestoreDesc* restHost() { return reinterpret_cast<RestoreDesc*>(h_stage + offRest); }
+};
+
+void ct_batch_free(ct_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (ct_table* t : b->tabs) ct_table_free(t);
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    cudaGetLastError();
+    delete b;
+}
+
+namespace {
+
+template <typename T>
+int b_alloc(ct_batch* b, T** p, size_t n) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("batched search: cudaMalloc: %s", cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    b->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CT_OK;
+}
+
+// The B copies of the network and the device descriptors of the slot launch.
+int build_batch(ct_model* m, int B, ct_batch** out) {
+    ct_batch* b = new (std::nothrow) ct_batch();
+    if (!b) return CT_ERR_OOM;
+    *out = b;
+    const int T = (int)m->tables.size();
+    const int n = B * T;
+    b->B = B;
+    b->T = T;
+    b->n = n;
+    b->stream = m->stream;
+    int st = CT_OK;
+    b->tabs.reserve(n);
+    for (int s = 0; s < B; ++s) {
+        for (int k = 0; k < T; ++k) {
+            ct_table* c = ct_table_clone(m->tables[k], m->stream, &st);
+            if (!c) return st;
+            b->tabs.push_back(c);
+        }
+    }
+    const int DWs = B * m->DWg;
+    std::vector<int32_t> base(n + 1, 0), off, var;
+    for (int s = 0; s < B; ++s) {
+        for (int k = 0; k < T; ++k) {
+            const int j = s * T + k;
+            base[j + 1] = base[j] + (int)m->scopes[k].size();
+            for (size_t i = 0; i < m->scopes[k].size(); ++i) {
+                off.push_back(m->tabOff[k][i] + s * m->DWg);
+                var.push_back(m->scopes[k][i] + s * m->nvars);
+            }
+        }
+    }
+    int32_t *dBase, *dOff, *dVar, *dPruned, *dNode, *dUnit, *dRow;
+    ModelCtrl* dCtrl;
+    if ((st = b_alloc(b, &b->d_tabs, n)) != CT_OK || (st = b_alloc(b, &b->d_src, T)) != CT_OK ||
+        (st = b_alloc(b, &dBase, n + 1)) != CT_OK || (st = b_alloc(b, &dOff, off.size())) != CT_OK ||
+        (st = b_alloc(b, &dVar, var.size())) != CT_OK || (st = b_alloc(b, &dPruned, (size_t)B * m->nvars)) != CT_OK ||
+        (st = b_alloc(b, &dNode, B)) != CT_OK || (st = b_alloc(b, &dUnit, n + 1)) != CT_OK ||
+        (st = b_alloc(b, &dRow, n + 1)) != CT_OK || (st = b_alloc(b, &dCtrl, 1)) != CT_OK)
+        return st;
+    b->offCalls = 16;
+    b->offDom = align16(b->offCalls + (size_t)n * sizeof(ModelTabCall));
+    b->offWork = align16(b->offDom + (size_t)DWs * sizeof(uint32_t));
+    b->offRest = align16(b->offWork + 2 * (size_t)n * sizeof(int32_t));
+    b->stageBytes = align16(b->offRest + (size_t)n * sizeof(RestoreDesc));
+    if ((st = b_alloc(b, &b->d_stage, b->stageBytes)) != CT_OK) return st;
+    const size_t statusInts = (size_t)kModelHdr + 2 * (size_t)n + DWs + B;
+    if (cudaHostAlloc((void**)&b->h_stage, b->stageBytes, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&b->h_status, statusInts * sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("batched search: pinned host buffers");
+        return CT_ERR_OOM;
+    }
+    std::memset(b->h_stage, 0, b->stageBytes);
+    int32_t* dStatus = nullptr;
+    CT_CUDA(cudaHostGetDevicePointer((void**)&dStatus, b->h_status, 0));
+    cudaStream_t s = m->stream;
+    CT_CUDA(cudaMemcpyAsync(dBase, base.data(), base.size() * 4, cudaMemcpyHostToDevice, s));
+    CT_CUDA(cudaMemcpyAsync(dOff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s));
+    CT_CUDA(cudaMemcpyAsync(dVar, var.data(), var.size() * 4, cudaMemcpyHostToDevice, s));
+    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, (size_t)B * m->nvars * 4, s));
+    CT_CUDA(cudaMemsetAsync(dNode, 0, (size_t)B * 4, s));
+    CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), s));
+    std::vector<TableDev> td(n);
+    b->tabVersion.resize(n);
+    for (int j = 0; j < n; ++j) {
+        td[j] = ct_table_dev(b->tabs[j]);
+        b->tabVersion[j] = ct_table_version(b->tabs[j]);
+    }
+    CT_CUDA(cudaMemcpyAsync(b->d_tabs, td.data(), (size_t)n * sizeof(TableDev), cudaMemcpyHostToDevice, s));
+    CT_CUDA(cudaStreamSynchronize(s));  // td and the host vectors above go out of scope
+    ModelDev& M = b->md;
+    M.tabs = b->d_tabs;
+    M.calls = reinterpret_cast<const ModelTabCall*>(b->d_stage + b->offCalls);
+    M.scopeBase = dBase;
+    M.scopeOff = dOff;
+    M.scopeVar = dVar;
+    M.work = reinterpret_cast<int32_t*>(b->d_stage + b->offWork);
+    M.unitPrefix = dUnit;
+    M.rowPrefix = dRow;
+    M.prunedBy = dPruned;
+    M.ctrl = dCtrl;
+    M.dom = reinterpret_cast<uint32_t*>(b->d_stage + b->offDom);
+    M.statusBlk = dStatus;
+    M.nodeStatus = dNode;
+    M.ntables = n;
+    M.nvars = B * m->nvars;
+    M.DWg = DWs;
+    int64_t domBits = 0;
+    for (int v = 0; v < m->nvars; ++v) domBits += m->size[v];
+    M.maxRounds = (int)std::min<int64_t>(domBits + 2, 1 << 30);
+    M.nodeTables = T;
+    M.restores = reinterpret_cast<const RestoreDesc*>(b->d_stage + b->offRest);
+    M.nrestores = 0;
+    M.nworkIn = reinterpret_cast<const int32_t*>(b->d_stage);
+    const int maxCo = max_coresident_model_blocks();
+    if (maxCo <= 0) {
+        ct_set_error("batched search: the fixpoint kernel cannot be made resident on this device");
+        return CT_ERR_CUDA;
+    }
+    int64_t segs = 0, rows = 0;
+    for (ct_table* tab : m->tables) {
+        segs += ct_table_dev(tab).nseg;
+        rows += ct_table_dev(tab).R;
+    }
+    int64_t want = std::max<int64_t>({(int64_t)n, B * ((segs + kWarps - 1) / kWarps),
+                                      B * ((rows + 2 * kWarps - 1) / (2 * kWarps)), 1});
+    if (m->opt.grid_blocks > 0) want = m->opt.grid_blocks;
+    b->grid = (int)std::min<int64_t>(want, maxCo);
+    return CT_OK;
+}
+
+// Every copy takes the current state of the model's tables (one launch).
+int sync_copies(ct_model* m, ct_batch* b) {
+    std::vector<TableDev> td(b->T);
+    for (int k = 0; k < b->T; ++k) td[k] = ct_table_dev(m->tables[k]);
+    CT_CUDA(cudaMemcpyAsync(b->d_src, td.data(), td.size() * sizeof(TableDev), cudaMemcpyHostToDevice, b->stream));
+    CT_CUDA(launch_clone_state(b->d_src, b->d_tabs, b->T, b->n, b->stream));
+    CT_CUDA(cudaStreamSynchronize(b->stream));
+    for (int j = 0; j < b->n; ++j) ct_table_adopt_state(b->tabs[j], m->tables[j % b->T]);
+    return CT_OK;
+}
+
+struct Search {
+    ct_model* m = nullptr;
+    ct_batch* b = nullptr;
+    int B = 0, splitDepth = 0;
+    int64_t limit = 0;
+    bool countAll = true;
+    ct_search_stats st{};
+    ct_batch_info info{};
+    bool hitLimit = false;
+    bool stopIssue = false;  // no new node is started (node limit)
+    bool splitStop = false;  // the split phase found the first solution it was asked for
+    bool haveBest = false;
+    std::vector<uint8_t> bestPath;
+    std::vector<int32_t> bestVals;
+    std::vector<OpenNode> open;
+    size_t nextOpen = 0;
+    std::vector<uint32_t> rootDom;
+    bool copiesReady = false;
+    std::vector<Slot> slots;
+    std::vector<char> dirty;       // [n]
+    std::vector<int> restPos;      // [n] index in this step's restore list, -1 none
+    int nrest = 0;
+    std::chrono::steady_clock::time_point t0;
+
+    uint32_t* slotDom(int s) { return b->domHost() + (size_t)s * m->DWg; }
+
+    void record_solution(const std::vector<uint8_t>& path, const uint32_t* dom) {
+        st.solutions += 1;
+        if (haveBest && !after(bestPath, path)) return;
+        haveBest = true;
+        bestPath = path;
+        bestVals.resize(m->nvars);
+        for (int v = 0; v < m->nvars; ++v) bestVals[v] = m->lo[v] + min_value(m, dom, v);
+    }
+
+    int ensure_copies() {
+        const auto c0 = std::chrono::steady_clock::now();
+        int rc;
+        if (b && (b->B != B || b->broken)) {
+            ct_batch_free(b);
+            b = m->bsearch = nullptr;
+        }
+        if (!b) {
+            ct_batch* nb = nullptr;
+            rc = build_batch(m, B, &nb);
+            if (rc != CT_OK) {
+                ct_batch_free(nb);
+                return rc;
+            }
+            b = m->bsearch = nb;
+        }
+        if ((rc = sync_copies(m, b)) != CT_OK) {
+            b->broken = true;
+            return rc;
+        }
+        rootDom = m->h_dom;
+        copiesReady = true;
+        info.setup_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
+        return CT_OK;
+    }
+
+    // ---- split phase: depth-first on the model itself ----
+    int split(int depth, std::vector<uint8_t>& path) {
+        if (depth == splitDepth) {
+            open.push_back(OpenNode{m->h_dom, depth, path});
+            return CT_OK;
+        }
+        if (limit > 0 && st.nodes >= limit) {
+            hitLimit = stopIssue = true;
+            return CT_OK;
+        }
+        st.nodes += 1;
+        info.split_nodes += 1;
+        if (depth > st.max_depth) st.max_depth = depth;
+        int r = ct_model_propagate(m);
+        if (r < 0) return r;
+        if (r == CT_INFEASIBLE) {
+            st.fails += 1;
+            return CT_OK;
+        }
+        if (depth == 0 && (r = ensure_copies()) != CT_OK) return r;
+        const int x = first_fail(m, m->h_dom.data());
+        if (x < 0) {
+            record_solution(path, m->h_dom.data());
+            if (!countAll) splitStop = true;
+            return CT_OK;
+        }
+        const int a = min_value(m, m->h_dom.data(), x);
+        const int nwx = m->nw[x];
+        std::vector<uint32_t> left(nwx, 0u), right(m->h_dom.begin() + m->off[x], m->h_dom.begin() + m->off[x] + nwx);
+        left[a >> 5] = 1u << (a & 31);
+        right[a >> 5] &= ~(1u << (a & 31));
+        for (int br = 0; br < 2; ++br) {
+            int L = 0;
+            int rc = ct_model_save(m, &L);
+            if (rc != CT_OK) return rc;
+            rc = ct_model_set_var(m, x, br == 0 ? left.data() : right.data());
+            path.push_back((uint8_t)br);
+            if (rc == CT_OK) rc = split(depth + 1, path);
+            path.pop_back();
+            const int rr = ct_model_restore(m, L);
+            if (rc != CT_OK) return rc;
+            if (rr != CT_OK) return rr;
+            if (stopIssue || splitStop) return CT_OK;
+        }
+        return CT_OK;
+    }
+
+    // ---- slot bookkeeping ----
+    void mark_var(int s, int v) {
+        for (int k : m->varTables[v]) dirty[(size_t)s * b->T + k] = 1;
+    }
+
+    int save_slot(int s) {
+        Slot& S = slots[s];
+        for (int k = 0; k < b->T; ++k) {
+            const int rc = ct_table_save_host(b->tabs[(size_t)s * b->T + k]);
+            if (rc != CT_OK) return rc;
+        }
+        const uint32_t* d = slotDom(s);
+        S.levelDom.insert(S.levelDom.end(), d, d + m->DWg);
+        return CT_OK;
+    }
+
+    // Back to saved level L: trails undone by the next launch (one undo per
+    // table and step, from the lowest level asked for), domains from the host copy.
+    int restore_slot(int s, int L) {
+        Slot& S = slots[s];
+        for (int k = 0; k < b->T; ++k) {
+            const int j = s * b->T + k;
+            RestoreDesc d{};
+            const int need = ct_table_restore_prepare(b->tabs[j], L, &d);
+            if (need < 0) return need;
+            if (!need) continue;
+            d.table = j;
+            RestoreDesc* R = b->restHost();
+            if (restPos[j] >= 0) {
+                RestoreDesc& e = R[restPos[j]];  // an earlier undo of this step: extend it down to level L
+                e.level = d.level;
+                e.mark = d.mark;
+            } else {
+                restPos[j] = nrest;
+                R[nrest++] = d;
+            }
+        }
+        std::memcpy(slotDom(s), S.levelDom.data() + (size_t)L * m->DWg, (size_t)m->DWg * sizeof(uint32_t));
+        S.levelDom.resize((size_t)L * m->DWg);
+        return CT_OK;
+    }
+
+    int cancel(int s) {
+        Slot& S = slots[s];
+        const int rc = S.active ? restore_slot(s, 0) : CT_OK;
+        S.active = false;
+        S.pending = false;
+        S.stack.clear();
+        S.path.clear();
+        return rc;
+    }
+
+    // The slot's current node goes into the next launch.
+    int issue(int s, int depth) {
+        if (limit > 0 && st.nodes >= limit) {
+            hitLimit = stopIssue = true;
+            return cancel(s);
+        }
+        st.nodes += 1;
+        info.slot_nodes += 1;
+        if (depth > st.max_depth) st.max_depth = depth;
+        slots[s].pending = true;
+        return CT_OK;
+    }
+
+    int start(int s, const uint32_t* dom, int depth, const std::vector<uint8_t>& path) {
+        Slot& S = slots[s];
+        int rc = save_slot(s);  // level 0: the root state
+        if (rc != CT_OK) return rc;
+        std::memcpy(slotDom(s), dom, (size_t)m->DWg * sizeof(uint32_t));
+        for (int k = 0; k < b->T; ++k) dirty[(size_t)s * b->T + k] = 1;
+        S.active = true;
+        S.depth0 = depth;
+        S.stack.clear();
+        S.path = path;
+        S.path0 = path.size();
+        return issue(s, depth);
+    }
+
+    // An idle slot takes the next open node, else the untried right branch
+    // nearest the root among the other slots' subtrees.
+    int assign(int s) {
+        while (!stopIssue && nextOpen < open.size()) {
+            const OpenNode& o = open[nextOpen++];
+            if (!countAll && haveBest && after(o.path, bestPath)) continue;
+            info.open_nodes += 1;
+            return start(s, o.dom.data(), o.depth, o.path);
+        }
+        if (stopIssue) return CT_OK;
+        int v = -1, fj = -1, bestDepth = 0;
+        for (int u = 0; u < B; ++u) {
+            const Slot& U = slots[u];
+            if (!U.active) continue;
+            for (int j = 0; j < (int)U.stack.size(); ++j) {
+                if (U.stack[j].branch != 0) continue;
+                if (v < 0 || U.depth0 + j < bestDepth) {
+                    v = u;
+                    fj = j;
+                    bestDepth = U.depth0 + j;
+                }
+                break;  // deeper frames of this slot are further from the root
+            }
+        }
+        if (v < 0) return CT_OK;
+        Slot& V = slots[v];
+        std::vector<uint8_t> path(V.path.begin(), V.path.begin() + (V.path0 + fj));
+        path.push_back(1);
+        if (!countAll && haveBest && after(path, bestPath)) return CT_OK;
+        Frame& f = V.stack[fj];
+        f.branch = 2;
+        std::vector<uint32_t> dom(V.levelDom.begin() + (size_t)(fj + 1) * m->DWg,
+                                  V.levelDom.begin() + (size_t)(fj + 2) * m->DWg);
+        dom[m->off[f.x] + (f.a >> 5)] &= ~(1u << (f.a & 31));
+        info.steals += 1;
+        return start(s, dom.data(), V.depth0 + fj + 1, path);
+    }
+
+    int branch(int s, int x) {
+        Slot& S = slots[s];
+        uint32_t* dom = slotDom(s);
+        const int a = min_value(m, dom, x);
+        int rc = save_slot(s);  // level stack.size() + 1
+        if (rc != CT_OK) return rc;
+        S.stack.push_back(Frame{x, a, 0});
+        for (int q = 0; q < m->nw[x]; ++q) dom[m->off[x] + q] = 0u;
+        dom[m->off[x] + (a >> 5)] = 1u << (a & 31);
+        mark_var(s, x);
+        S.path.push_back(0);
+        return issue(s, S.depth0 + (int)S.stack.size());
+    }
+
+    int backtrack(int s) {
+        Slot& S = slots[s];
+        while (!S.stack.empty()) {
+            const int j = (int)S.stack.size() - 1;
+            Frame& f = S.stack[j];
+            int rc = restore_slot(s, j + 1);
+            if (rc != CT_OK) return rc;
+            S.path.resize(S.path0 + j);
+            if (f.branch == 0) {
+                f.branch = 1;
+                S.path.push_back(1);
+                if (!countAll && haveBest && after(S.path, bestPath)) return cancel(s);
+                if ((rc = save_slot(s)) != CT_OK) return rc;
+                uint32_t* dom = slotDom(s);
+                dom[m->off[f.x] + (f.a >> 5)] &= ~(1u << (f.a & 31));
+                mark_var(s, f.x);
+                return issue(s, S.depth0 + j + 1);
+            }
+            S.stack.pop_back();
+        }
+        return cancel(s);  // subtree done: back to the root state, idle
+    }
+
+    // The result of slot s's node (status of its fixpoint, domains in slotDom).
+    int advance(int s, int nodeStatus) {
+        Slot& S = slots[s];
+        S.pending = false;
+        if (!countAll && haveBest && after(S.path, bestPath)) return cancel(s);
+        if (nodeStatus == CT_INFEASIBLE) {
+            st.fails += 1;
+            return backtrack(s);
+        }
+        const int x = first_fail(m, slotDom(s));
+        if (x < 0) {
+            record_solution(S.path, slotDom(s));
+            return backtrack(s);
+        }
+        return branch(s, x);
+    }
+
+    // One launch: undo the trails of this step, propagate the dirty tables of every slot.
+    int step() {
+        const int n = b->n, T = b->T;
+        int32_t* work = b->workHost();
+        int nwork = 0;
+        for (int j = 0; j < n; ++j)
+            if (dirty[j]) work[nwork++] = j;
+        info.steps += 1;
+        if (nwork == 0 && nrest == 0) {  // nothing to do on the device: the nodes are their own fixpoints
+            std::vector<int> ps;
+            for (int s = 0; s < B; ++s)
+                if (slots[s].pending) ps.push_back(s);
+            for (int s : ps) {
+                const int rc = advance(s, CT_OK);
+                if (rc != CT_OK) return rc;
+            }
+            return CT_OK;
+        }
+        int rc;
+        ModelTabCall* calls = b->callsHost();
+        for (int j = 0; j < n; ++j)
+            if ((rc = ct_table_batch_prepare(b->tabs[j], &calls[j])) != CT_OK) return rc;
+        for (int j = 0; j < n; ++j) {
+            const int v = ct_table_version(b->tabs[j]);
+            if (v != b->tabVersion[j]) {
+                CT_CUDA(cudaMemcpyAsync(b->d_tabs + j, &ct_table_dev(b->tabs[j]), sizeof(TableDev),
+                                        cudaMemcpyHostToDevice, b->stream));
+                b->tabVersion[j] = v;
+            }
+        }
+        b->nworkHost()[0] = nwork;
+        CT_CUDA(cudaMemcpyAsync(b->d_stage, b->h_stage, b->offWork + (size_t)nwork * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, b->stream));
+        if (nrest > 0)
+            CT_CUDA(cudaMemcpyAsync(b->d_stage + b->offRest, b->h_stage + b->offRest,
+                                    (size_t)nrest * sizeof(RestoreDesc), cudaMemcpyHostToDevice, b->stream));
+        b->md.nrestores = nrest;
+        volatile int32_t* H = b->h_status;
+        H[0] = kNoChunk;
+        const auto w0 = std::chrono::steady_clock::now();
+        CT_CUDA(launch_model(b->md, b->grid, b->stream));
+        bool seen = false;
+        for (uint64_t it = 0;; ++it) {
+            if (H[0] != kNoChunk) {
+                seen = true;
+                break;
+            }
+            if ((it & 1023u) == 1023u && std::chrono::steady_clock::now() - w0 > std::chrono::milliseconds(kHostWaitMs))
+                break;
+        }
+        if (!seen) CT_CUDA(cudaStreamSynchronize(b->stream));
+        const int status = H[0];
+        if (status != CT_OK) {
+            b->broken = true;
+            if (status == kNoChunk) {
+                ct_set_error("batched search: the fixpoint kernel did not publish (a device-side wait ran out)");
+                return CT_ERR_TIMEOUT;
+            }
+            ct_set_error("batched search: fixpoint kernel status %d", status);
+            return status < 0 ? status : CT_ERR_STATE;
+        }
+        st.propagations += H[2];
+        for (int j = 0; j < n; ++j) {
+            ct_table_batch_done(b->tabs[j], H[kModelHdr + 2 * j], H[kModelHdr + 2 * j + 1]);
+            restPos[j] = -1;
+        }
+        nrest = 0;
+        std::fill(dirty.begin(), dirty.end(), 0);
+        const uint32_t* outDom = reinterpret_cast<const uint32_t*>(const_cast<const int32_t*>(b->h_status) + kModelHdr + 2 * n);
+        const int32_t* outNode = const_cast<const int32_t*>(b->h_status) + kModelHdr + 2 * n + (size_t)B * m->DWg;
+        (void)T;
+        for (int s = 0; s < B; ++s) {
+            if (!slots[s].pending) continue;
+            std::memcpy(slotDom(s), outDom + (size_t)s * m->DWg, (size_t)m->DWg * sizeof(uint32_t));
+            if ((rc = advance(s, outNode[s])) != CT_OK) return rc;
+        }
+        return CT_OK;
+    }
+
+    int run_slots() {
+        const int n = b->n;
+        slots.assign(B, Slot());
+        dirty.assign(n, 0);
+        restPos.assign(n, -1);
+        nrest = 0;
+        for (int s = 0; s < B; ++s) std::memcpy(slotDom(s), rootDom.data(), (size_t)m->DWg * sizeof(uint32_t));
+        for (;;) {
+            for (int s = 0; s < B; ++s) {
+                if (slots[s].active) continue;
+                const int rc = assign(s);
+                if (rc != CT_OK) return rc;
+            }
+            bool any = nrest > 0;
+            for (int s = 0; s < B && !any; ++s) any = slots[s].pending;
+            if (!any) break;
+            const int rc = step();
+            if (rc != CT_OK) return rc;
+        }
+        return CT_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,
+                               ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
+    if (!m || !out) {
+        ct_set_error("ct_search_batch: null argument");
+        return CT_ERR_ARG;
+    }
+    if (slots < 1 || slots > 4096 || split_depth < 0 || split_depth > 64 ||
+        (int64_t)slots * (int64_t)m->tables.size() > kModelMaxTables) {
+        ct_set_error("ct_search_batch: slots %d or split depth %d out of range", slots, split_depth);
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_search_batch: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (m->tables.empty() || m->staticInfeasible) {
+        // nothing to propagate on the device: the plain search is the same search
+        const int rc = ct_search_dfs(m, node_limit, count_all, out, first_solution);
+        if (info) {
+            info->slots = slots;
+            info->split_nodes = rc == CT_OK ? out->nodes : 0;
+        }
+        return rc;
+    }
+    Search S;
+    S.t0 = std::chrono::steady_clock::now();
+    S.m = m;
+    S.b = m->bsearch;
+    S.B = slots;
+    S.splitDepth = split_depth;
+    S.limit = node_limit;
+    S.countAll = count_all != 0;
+    const int64_t p0 = m->propagations;
+    int L0 = 0;
+    int rc = ct_model_save(m, &L0);
+    if (rc != CT_OK) return rc;
+    std::vector<uint8_t> path;
+    if (split_depth == 0) rc = S.ensure_copies();
+    if (rc == CT_OK) rc = S.split(0, path);
+    const int rr = ct_model_restore(m, L0);
+    if (rc == CT_OK) rc = rr;
+    if (rc == CT_OK && !S.open.empty() && !S.stopIssue) rc = S.run_slots();
+    if (rc != CT_OK) {
+        if (S.b) S.b->broken = true;
+        return rc;
+    }
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    S.st.propagations += m->propagations - p0;
+    S.st.complete = S.hitLimit ? 0 : 1;
+    S.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+    *out = S.st;
+    if (first_solution && S.haveBest) std::memcpy(first_solution, S.bestVals.data(), S.bestVals.size() * sizeof(int32_t));
+    if (info) {
+        *info = S.info;
+        info->slots = slots;
+        info->split_depth = split_depth;
+    }
+    return CT_OK;
+}

@@ -563,6 +563,90 @@ void ct_table_batch_done(ct_table* ct, int trailTop, int live) {
     ct->failed = false;
 }
 
+// A table that shares `src`'s static buffers (supports rows and the layout
+// tables, which stay owned by src) with dynamic buffers of its own (currTable,
+// index, lastDom, residues, trail, levels), filled by launch_clone_state. Used
+// for the independent search nodes of a batched search.
+ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status) {
+    *status = CT_ERR_ARG;
+    if (!src || src->empty) return nullptr;
+    ct_table* ct = new (std::nothrow) ct_table();
+    if (!ct) {
+        *status = CT_ERR_OOM;
+        return nullptr;
+    }
+    ct->arity = src->arity;
+    ct->lo = src->lo;
+    ct->size = src->size;
+    ct->nw = src->nw;
+    ct->ld = src->ld;
+    ct->row0 = src->row0;
+    ct->rowVar = src->rowVar;
+    ct->R = src->R;
+    ct->t = src->t;
+    ct->W = src->W;
+    ct->W4 = src->W4;
+    ct->nseg = src->nseg;
+    ct->S = src->S;
+    ct->grid = src->grid;
+    ct->DW = src->DW;
+    ct->nChW = src->nChW;
+    ct->localPlan = src->localPlan;
+    ct->variant = src->variant;
+    ct->live = src->live;
+    ct->stream = stream;
+    ct->dev = src->dev;  // static pointers shared; dynamic ones replaced below
+    TableDev& d = ct->dev;
+    d.trailKey = nullptr;
+    d.trailOld = nullptr;
+    d.levelSeg = nullptr;
+    d.levelDom = nullptr;
+    const size_t padChunks = (size_t)ct->nseg * 32;
+    int st = CT_OK;
+    if ((st = dalloc(ct, &d.curr, padChunks)) != CT_OK || (st = dalloc(ct, &d.segMask, (size_t)ct->nseg)) != CT_OK ||
+        (st = dalloc(ct, &d.lastpos, padChunks)) != CT_OK || (st = dalloc(ct, &d.residue, (size_t)ct->R)) != CT_OK ||
+        (st = dalloc(ct, &d.lastDom, (size_t)ct->DW)) != CT_OK || (st = dalloc(ct, &d.ctrl, 1)) != CT_OK ||
+        (st = dalloc(ct, &d.codes, (size_t)ct->R)) != CT_OK || (st = dalloc(ct, &d.planK, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.planRowOff, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.varSup, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.changed, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.hardRow, (size_t)ct->R)) != CT_OK || (st = dalloc(ct, &d.foundChunk, (size_t)ct->R)) != CT_OK) {
+        free_table(ct);
+        *status = st;
+        return nullptr;
+    }
+    d.statusBlk = src->dev.statusBlk;  // never written by the batched path; kept valid
+    if ((st = ensure_levels(ct, 8)) != CT_OK) {
+        free_table(ct);
+        *status = st;
+        return nullptr;
+    }
+    *status = CT_OK;
+    return ct;
+}
+
+// Host side of a clone taking its source's state (the device side is
+// launch_clone_state): empty trail, no levels, the source's live count.
+void ct_table_adopt_state(ct_table* dst, const ct_table* src) {
+    dst->live = src->live;
+    dst->trailTop = 0;
+    dst->marks.clear();
+    dst->levelLive.clear();
+    dst->pendingFrom = 0;
+    dst->failed = false;
+}
+
+int ct_table_live(const ct_table* ct) { return ct->live; }
+
+void ct_table_free(ct_table* ct) { free_table(ct); }
+
+int ct_table_save_host(ct_table* ct) {
+    int lv = 0;
+    return ct_save(ct, &lv);
+}
+
+int ct_table_depth(const ct_table* ct) { return (int)ct->marks.size(); }
+
 int ct_table_restore_device(ct_table* ct, const RestoreDesc& d) {
     CT_CUDA(launch_restore(ct->dev, d.level, d.mark, d.top, -1, ct->stream));
     return CT_OK;

@@ -71,6 +71,12 @@ class ct_search_stats(ctypes.Structure):
                 ("complete", ctypes.c_int32), ("seconds", ctypes.c_double)]
 
 
+class ct_batch_info(ctypes.Structure):
+    _fields_ = [("open_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("steals", ctypes.c_int64), ("slot_nodes", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("split_depth", ctypes.c_int32), ("setup_seconds", ctypes.c_double)]
+
+
 def _as_dict(s):
     out = {}
     for k, _ in s._fields_:
@@ -109,6 +115,8 @@ _SIGS = {
     "ct_model_save": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "ct_model_restore": (ctypes.c_int, [_P, ctypes.c_int]),
     "ct_search_dfs": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ct_search_stats), _I32P]),
+    "ct_search_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
     "ct_last_error": (ctypes.c_char_p, []),
     "ct_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -390,6 +398,18 @@ def ct_search_dfs(m, nvars, node_limit=0, count_all=True):
     d = _as_dict(s)
     d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
     return st, d
+
+
+def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True):
+    """Batched search: returns (status, stats dict with first_solution, batch info dict)."""
+    s = ct_search_stats()
+    info = ct_batch_info()
+    sol = np.zeros(nvars, dtype=np.int32)
+    st = load().ct_search_batch(m, int(slots), int(split_depth), int(node_limit), 1 if count_all else 0,
+                                ctypes.byref(s), sol.ctypes.data_as(_I32P), ctypes.byref(info))
+    d = _as_dict(s)
+    d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
+    return st, d, _as_dict(info)
 
 
 def ct_model_destroy(m):

@@ -266,3 +266,23 @@ def random_csp(seed: int, nvars: int, ntables: int, arity: int, d: int, t: int,
             tup = zipf_tuples(ts, [0] * arity, [d] * arity, t)
         csp.tables.append(TableSpec(scope=scope, tuples=tup))
     return csp
+
+
+def batching_csp(seed: int, nvars: int = 40, ntables: int = 60, arity: int = 4, d: int = 24,
+                 t_lo: float = 1e4, t_hi: float = 2e5) -> CspSpec:
+    """The search workload of the batching experiments: ``ntables`` tables of ``arity``
+    over random scopes of ``nvars`` variables with domains {0..d-1}, each holding a
+    log-uniform number of distinct uniform tuples in [t_lo, t_hi] (capped at half the
+    tuple space). With the defaults the expected solution count is of order one (the
+    product of the table densities times d^nvars), i.e. near the satisfiability threshold."""
+    rng = Rng(seed)
+    csp = CspSpec(nvars=nvars, dom_lo=[0] * nvars, dom_size=[d] * nvars)
+    for k in range(ntables):
+        scope = random_scope(rng, nvars, arity)
+        u = float(rng.uniform(1)[0])
+        t = int(round(math.exp(math.log(t_lo) + u * (math.log(t_hi) - math.log(t_lo)))))
+        t = cap_distinct([d] * arity, t)
+        tup = distinct_uniform_tuples(derive_seed(seed, k), [0] * arity, [d] * arity, t)
+        csp.tables.append(TableSpec(scope=scope, tuples=tup))
+    return csp
+

@@ -63,6 +63,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.ct_restore(None, 0) == C.CT_ERR_ARG
     assert lib.ct_destroy(None) == C.CT_OK
     assert lib.ct_model_destroy(None) == C.CT_OK
+    assert lib.ct_search_batch(None, 4, 1, 0, 1, None, None, None) == C.CT_ERR_ARG
 
 
 def test_domain_word_marshalling_round_trip():
@@ -88,7 +89,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [C.ct_options, C.ct_table_info, C.ct_call_stats, C.ct_profile, C.ct_search_stats]
+    structs = [C.ct_options, C.ct_table_info, C.ct_call_stats, C.ct_profile, C.ct_search_stats, C.ct_batch_info]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ct.h"', "int main(void){"]
     for st in structs:
         n = st.__name__

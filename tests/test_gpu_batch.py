@@ -1,0 +1,197 @@
+"""GPU parity of the batched search (ct_search_batch).
+
+Counting every solution visits the whole tree whatever the order of the
+nodes, so with count_all and no node limit the batched search must give the
+oracle's depth-first counts exactly: nodes, fails, solutions, maximum depth,
+and the first solution in depth-first order. Asked for the first solution
+only, it must return the oracle's first solution. Splits at depth 0 (one open
+node, the rest by handing over right branches between slots), at depths with
+fewer and with more open nodes than slots, and with more tables in a round
+than the fixpoint kernel keeps in shared memory.
+"""
+import numpy as np
+import pytest
+
+from oracle import ct_oracle as O
+from paper_2507_18413_gb300 import ct as C
+from paper_2507_18413_gb300 import inputs as G
+from gpu_helpers import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _model(csp, raw, host_fixpoint=0):
+    torch = torch_cuda()
+    C.load()
+    opt = C.make_options(host_fixpoint=host_fixpoint)
+    st, h = C.ct_model_create(csp.dom_lo, csp.dom_size, opt=opt, stream=torch.cuda.current_stream())
+    assert st == C.CT_OK, C.last_error()
+    for scope, tup in raw:
+        assert C.ct_model_add_table(h, scope, tup) >= 0, C.last_error()
+    return h
+
+
+def _random(seed, nvars, ntables, arity, d, t):
+    rng = G.Rng(seed)
+    csp = O.Csp([0] * nvars, [d] * nvars)
+    raw = []
+    for k in range(ntables):
+        scope = G.random_scope(rng, nvars, arity)
+        tt = G.cap_distinct([d] * arity, t)
+        tup = G.distinct_uniform_tuples(G.derive_seed(seed, k), [0] * arity, [d] * arity, tt)
+        csp.add_table(scope, tup)
+        raw.append((scope, tup))
+    return csp, raw
+
+
+def _domains(h, csp):
+    off, _ = C.dom_layout(csp.dom_size)
+    st, w = C.ct_model_get_domains(h, int(off[-1]))
+    assert st == C.CT_OK
+    return w.copy()
+
+
+def _batch(h, csp, slots, split, node_limit=0, count_all=True):
+    st, d, info = C.ct_search_batch(h, csp.nvars, slots, split, node_limit, count_all)
+    assert st == C.CT_OK, C.last_error()
+    return d, info
+
+
+def _assert_counts(got, want):
+    assert (got["nodes"], got["fails"], got["solutions"]) == (want.nodes, want.fails, want.solutions)
+    assert got["max_depth"] == want.max_depth
+    assert bool(got["complete"]) == want.complete
+    if want.solutions:
+        assert got["first_solution"] == want.first_solution
+
+
+SHAPES = [(1, 0), (4, 0), (4, 2), (16, 3), (7, 5), (64, 1)]
+
+
+@pytest.mark.parametrize("slots,split", SHAPES)
+@pytest.mark.parametrize("seed", range(6))
+def test_batch_counts_equal_the_oracle_search(seed, slots, split):
+    csp, raw = _random(300 + seed, nvars=7, ntables=5, arity=3, d=5, t=30 + 5 * seed)
+    want = O.dfs(csp, count_all=True)
+    h = _model(csp, raw)
+    before = _domains(h, csp)
+    got, info = _batch(h, csp, slots, split)
+    _assert_counts(got, want)
+    assert info["split_nodes"] + info["slot_nodes"] == got["nodes"]
+    assert np.array_equal(_domains(h, csp), before), "the model's domains changed"
+    # the model is intact: the plain search still agrees, and a second batched call too
+    st, d = C.ct_search_dfs(h, csp.nvars, 0, True)
+    assert st == C.CT_OK and (d["nodes"], d["solutions"]) == (want.nodes, want.solutions)
+    got2, _ = _batch(h, csp, slots, split)
+    _assert_counts(got2, want)
+    C.ct_model_destroy(h)
+
+
+@pytest.mark.parametrize("slots,split", [(3, 1), (8, 0)])
+def test_batch_table1(golden_dir, slots, split):
+    import json
+    import os
+    with open(os.path.join(golden_dir, "table1.json")) as f:
+        g = json.load(f)
+    csp = O.Csp(g["scope_dom_lo"], g["scope_dom_size"])
+    csp.add_table([0, 1, 2], g["tuples"]["rows"])
+    h = _model(csp, [([0, 1, 2], g["tuples"]["rows"])])
+    got, _ = _batch(h, csp, slots, split)
+    assert (got["nodes"], got["fails"], got["solutions"]) == (9, 0, 5)
+    assert got["first_solution"] == [1, 4, 1]
+    C.ct_model_destroy(h)
+
+
+def test_batch_triangle_all_nodes_fail():
+    csp = O.Csp([0, 0, 0], [2, 2, 2])
+    raw = [([0, 1], [[0, 0], [1, 1]]), ([1, 2], [[0, 1], [1, 0]]), ([0, 2], [[0, 0], [1, 1]])]
+    for s, t in raw:
+        csp.add_table(s, t)
+    h = _model(csp, raw)
+    for slots, split in [(1, 0), (2, 1), (4, 0)]:
+        got, _ = _batch(h, csp, slots, split)
+        assert (got["nodes"], got["fails"], got["solutions"]) == (3, 2, 0)
+    C.ct_model_destroy(h)
+
+
+def test_batch_tiny_config_counts_200_solutions():
+    dom_lo, dom_size, tup = G.tiny_table(seed=1)
+    csp = O.Csp(dom_lo, dom_size)
+    csp.add_table([0, 1, 2], tup)
+    want = O.dfs(csp)
+    h = _model(csp, [([0, 1, 2], tup)])
+    for slots, split in [(8, 2), (32, 4), (128, 0)]:
+        got, info = _batch(h, csp, slots, split)
+        _assert_counts(got, want)
+        assert got["solutions"] == 200
+    C.ct_model_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_batch_first_solution_mode(seed):
+    csp, raw = _random(500 + seed, nvars=8, ntables=6, arity=3, d=5, t=40)
+    want = O.dfs(csp, count_all=False)
+    h = _model(csp, raw)
+    for slots, split in [(4, 2), (16, 0), (9, 4)]:
+        got, _ = _batch(h, csp, slots, split, count_all=False)
+        assert got["complete"] == 1
+        assert (got["solutions"] > 0) == (want.solutions > 0)
+        if want.solutions:
+            assert got["first_solution"] == want.first_solution
+        else:
+            assert (got["nodes"], got["fails"]) == (want.nodes, want.fails)
+    C.ct_model_destroy(h)
+
+
+def test_batch_node_limit():
+    csp, raw = _random(303, nvars=7, ntables=5, arity=3, d=5, t=45)
+    full = O.dfs(csp)
+    assert full.nodes > 1000
+    h = _model(csp, raw)
+    for slots, split, limit in [(4, 2, 25), (8, 0, 40), (2, 6, 10)]:
+        got, _ = _batch(h, csp, slots, split, node_limit=limit)
+        assert got["nodes"] == limit and got["complete"] == 0
+        assert got["fails"] + got["solutions"] <= limit
+    got, _ = _batch(h, csp, 4, 2, node_limit=full.nodes + 5)
+    _assert_counts(got, full)
+    C.ct_model_destroy(h)
+
+
+def test_batch_rounds_longer_than_the_shared_prefix():
+    """136 slots x 16 tables: the first step propagates 2,176 tables in one round
+    (168 open nodes at depth 8), more than the kernel's shared-memory prefix holds."""
+    csp, raw = _random(4242, nvars=12, ntables=16, arity=3, d=5, t=60)
+    want = O.dfs(csp)
+    assert want.complete and want.nodes == 3993
+    h = _model(csp, raw)
+    got, info = _batch(h, csp, 136, 8)
+    _assert_counts(got, want)
+    assert info["open_nodes"] == 168
+    got, info = _batch(h, csp, 24, 0)
+    _assert_counts(got, want)
+    assert info["steals"] > 0
+    C.ct_model_destroy(h)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_multi_segment_tables_match_the_plain_search(mode):
+    """28 tables of 5,000 tuples (40 chunks: two segments each); both fixpoint modes of the model."""
+    csp, raw = _random(91, nvars=8, ntables=28, arity=4, d=10, t=5000)
+    h = _model(csp, raw, host_fixpoint=mode)
+    st, plain = C.ct_search_dfs(h, csp.nvars, 0, True)
+    assert st == C.CT_OK and plain["complete"] == 1
+    got, info = _batch(h, csp, 32, 3)
+    for k in ("nodes", "fails", "solutions", "max_depth", "complete", "first_solution"):
+        assert got[k] == plain[k], k
+    C.ct_model_destroy(h)
+
+
+def test_batch_without_tables_and_bad_arguments():
+    csp = O.Csp([0, 0], [2, 3])
+    want = O.dfs(csp)
+    h = _model(csp, [])
+    got, _ = _batch(h, csp, 4, 1)
+    _assert_counts(got, want)
+    assert C.ct_search_batch(h, csp.nvars, 0, 1)[0] == C.CT_ERR_ARG
+    assert C.ct_search_batch(h, csp.nvars, 4, 65)[0] == C.CT_ERR_ARG
+    C.ct_model_destroy(h)
