@@ -317,9 +317,18 @@ typedef struct ct_batch_info {
     int64_t steps;        /* cooperative launches of the slots' phase */
     int64_t steals;       /* right branches taken over from another slot */
     int64_t slot_nodes;   /* node propagations done in the slots */
+    int64_t rounds;       /* fixpoint rounds summed over the launches */
+    int64_t residue_hits; /* slots' phase, Algorithm 3: values whose residue still held a support, */
+    int64_t window_hits;  /* values found in the windows after the residue, */
+    int64_t hard_values;  /* values left for the full index scan (found or pruned there) */
     int32_t slots;
     int32_t split_depth;
     double setup_seconds; /* building or refreshing the copies */
+    double wait_seconds;  /* slots' phase: from each launch to its results on the host */
+    double slot_seconds;  /* slots' phase in all (host work, copies, launches and waits) */
+    double phase_seconds[8]; /* with ct_options.profile: fixpoint kernel time by phase (prologue,
+                                plan, updateTable, residue probes, index scans, removals,
+                                next-round selection, publication) */
 } ct_batch_info;
 
 int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,

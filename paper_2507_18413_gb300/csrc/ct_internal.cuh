@@ -148,10 +148,15 @@ struct ModelTabCall {
 struct ModelCtrl {
     int32_t status;
     uint32_t bar_count, bar_gen;
-    int32_t nwork;       // tables to propagate in the current round
+    int32_t nwork;       // tables of the first round (when not passed in nworkIn)
     int32_t rounds;
     int32_t props;       // table propagations done
-    int32_t pad[10];
+    int32_t nnext[2];    // tables of round r collected in nnext[r & 1] by round r - 1
+    uint32_t hits;       // values whose residue still had a support
+    uint32_t local;      // values found in the windows after the residue
+    uint32_t hard;       // values left for the full index scan
+    uint32_t windows;    // windows probed
+    int32_t pad[4];
 };
 
 struct ModelDev {
@@ -163,7 +168,7 @@ struct ModelDev {
     int32_t* work;              // [2][ntables] work lists (ping-pong by round)
     int32_t* unitPrefix;        // [ntables + 1] segments of the work list
     int32_t* rowPrefix;         // [ntables + 1] supports rows of the work list
-    int32_t* prunedBy;          // [nvars] -1 none, t one table, -2 several
+    int32_t* prunedBy;          // [2][nvars] by round parity: -1 none, t one table, -2 several
     ModelCtrl* ctrl;
     uint32_t* dom;
     int32_t* statusBlk;         // mapped host: header, (trail_top, live) per table, domains, node statuses
@@ -175,7 +180,9 @@ struct ModelDev {
     const RestoreDesc* restores;  // [nrestores]
     int32_t nrestores;
     const int32_t* nworkIn;     // null: the count is already in ctrl->nwork
+    uint64_t* phaseNs;          // null, or [kModelPhases] nanoseconds added per phase (CTA 0's view)
 };
+constexpr int kModelPhases = 8;  // prologue, plan, update, probe, scan, apply, next round, publish
 constexpr int kRestoreBatch = 256;
 struct RestoreBatch {
     RestoreDesc d[kRestoreBatch];

@@ -433,22 +433,15 @@ __device__ __forceinline__ void trail_warp(const TableDev& T, const TrailItem& i
 }
 
 // ---------------------------------------------------------------------------
-// probe: residue of one value (warp per supports row); Algorithm 3 with residues
+// probe: Algorithm 3 with residues, a warp per value whose residue missed
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, int res, uint4 supRes,
-                                          uint32_t* s_cnt) {
+// A value whose residue missed (whole warp): windows of 32 chunks after the
+// residue; a value missed there too goes to the table's hard list.
+__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
-    if (!present) return;
-    const int W4 = T.W4;
-    const uint4* row = T.sup + (size_t)r * W4;
     if (T.useResidues) {
-        bool hit = false;
-        if (lane == 0) hit = nz(and4(supRes, __ldcg(T.curr + res)));
-        if (__shfl_sync(0xffffffffu, hit, 0)) {
-            if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
-            return;
-        }
-        // Windows of 32 chunks following the residue.
+        const int W4 = T.W4;
+        const uint4* row = T.sup + (size_t)r * W4;
         for (int b = 0; b < kLocalProbes; ++b) {
             if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
             const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
@@ -470,6 +463,21 @@ __device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present
         T.foundChunk[m] = kNoChunk;
         atomicAdd(&s_cnt[kCntMiss], 1u);
     }
+}
+
+__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, int res, uint4 supRes,
+                                          uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (!present) return;
+    if (T.useResidues) {
+        bool hit = false;
+        if (lane == 0) hit = nz(and4(supRes, __ldcg(T.curr + res)));
+        if (__shfl_sync(0xffffffffu, hit, 0)) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
+            return;
+        }
+    }
+    probe_miss(T, r, res, s_cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,15 +844,25 @@ __device__ __forceinline__ int pre_at(const int32_t* pre, int k, bool global) {
     return global ? __ldcg(pre + k) : pre[k];
 }
 
-// Position k of the work list whose prefix range holds u.
+// Position k of the work list whose prefix range holds u: the largest k < n
+// with pre[k] <= u (pre is non-decreasing, pre[0] = 0 <= u). The whole warp
+// calls it with the same u. The answer stays in [lo, hi] with pre[lo] <= u;
+// each pass samples lo + j * step for j < 32, with 32 * step covering the
+// hi - lo + 1 candidates, and keeps the stretch from the last sample <= u to
+// the next sample.
 __device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u, bool global) {
+    const int lane = threadIdx.x & 31;
     int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre_at(pre, mid, global) <= u) lo = mid;
-        else hi = mid - 1;
+    while (hi - lo >= 32) {
+        const int step = (hi - lo + 32) >> 5;
+        const int k = lo + lane * step;
+        const unsigned b = __ballot_sync(0xffffffffu, k <= hi && pre_at(pre, k, global) <= u);
+        lo += (31 - __clz(b)) * step;
+        hi = min(hi, lo + step - 1);
     }
-    return lo;
+    const int k = lo + lane;
+    const unsigned b = __ballot_sync(0xffffffffu, k <= hi && pre_at(pre, k, global) <= u);
+    return lo + (31 - __clz(b));
 }
 
 // Exclusive prefix of val(work[k]) over k < n into out[0..n] (one CTA).
@@ -883,7 +901,19 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     int32_t* preU = sm.codes;                               // unit prefix of the round (smem copy)
     int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
     auto sync = [&]() { return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, &sm.flag[0]); };
+    // optional phase clock: CTA 0 adds the time since its previous mark (a grid
+    // barrier ends every phase, so this is the phase's length across the grid)
+    uint64_t tmark = (M.phaseNs && blockIdx.x == 0 && tid == 0) ? gtimer() : 0ull;
+    auto phase = [&](int p) {
+        if (M.phaseNs && blockIdx.x == 0 && tid == 0) {
+            const uint64_t now = gtimer();
+            M.phaseNs[p] += now - tmark;
+            tmark = now;
+        }
+    };
 
+    if (tid < 12) sm.cnt[tid] = 0u;
+    __syncthreads();
     // Trail undos asked for with this launch (one CTA per table): the chunks
     // changed since the level's mark get their value at the mark back, and the
     // index and lastDom their snapshot of the level.
@@ -920,8 +950,13 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     }
     int cur = 0, round = 0;
     for (;;) {
-        const int nwork = round == 0 && M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
+        const int nwork = round > 0 ? __ldcg(&C->nnext[round & 1]) : M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
+        phase(round == 0 ? 0 : 6);
         const int32_t* work = M.work + (size_t)cur * M.ntables;
+        int32_t* pruned = M.prunedBy + (size_t)(round & 1) * M.nvars;       // written by this round
+        int32_t* prunedNext = M.prunedBy + (size_t)((round + 1) & 1) * M.nvars;
+        // the collector of the next round's tables was last read two rounds ago
+        if (blockIdx.x == 0 && tid == 0) C->nnext[(round + 1) & 1] = 0;
 
         // plan (Algorithm 1 lines 1-3), one CTA per table of the round
         for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
@@ -946,6 +981,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             block_prefix(work, nwork, [&](int t) { return M.tabs[t].R; }, M.rowPrefix, sm);
         }
         if (!sync()) return;
+        phase(1);
         if (__ldcg(&C->status) != CT_OK) break;
         const bool gpre = nwork > kPrefixSmem;
         const int32_t* pU = gpre ? M.unitPrefix : preU;
@@ -976,6 +1012,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
         }
         if (!sync()) return;
+        phase(2);
 
         if (__ldcg(&C->status) != CT_OK) break;
         // Algorithm 1 line 5: a table whose currTable became zero fails its node;
@@ -993,27 +1030,49 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             for (int i = tid; i < T.arity; i += kThreads)
                 for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = __ldcg(&M.dom[V.off(i) + q]);
         }
-        // filterDomains (Algorithm 3): residue probes over (table, row) units
-        for (int u = gwarp; u < totalRows; u += nwarps) {
-            const int k = find_prefix(pR, nwork, u, gpre);
-            const int t = __ldcg(&work[k]);
-            const TableDev& T = M.tabs[t];
-            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
-            const int r = u - pre_at(pR, k, gpre);
-            const int i = __ldg(&T.rowVar[r]);
-            const int a = r - V.row0(i);
-            const bool present =
-                __ldcg(&T.varSup[i]) && ((__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u);
-            int res = 0;
-            uint4 sr = make_uint4(0u, 0u, 0u, 0u);
-            if (present && T.useResidues && lane == 0) {
-                res = T.residue[r];
-                sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
+        // filterDomains (Algorithm 3): the residue test of every (table, row) unit,
+        // one unit per lane; a warp then takes its lanes' misses one by one
+        // through the windows after the residue, and what misses there too
+        // goes to the full scan.
+        // rows per warp: up to 32, fewer when that spreads the rows (and their
+        // misses) over more warps
+        const int rpw = min(32, max(1, (totalRows + nwarps - 1) / nwarps));
+        for (int u0 = gwarp * rpw; u0 < totalRows; u0 += nwarps * rpw) {
+            const int u = u0 + lane;
+            const bool valid = lane < rpw && u < totalRows;
+            int k = find_prefix(pR, nwork, u0, gpre);
+            while (valid && k + 1 < nwork && pre_at(pR, k + 1, gpre) <= u) ++k;
+            bool need = false, hit = false;
+            int t = 0, r = 0, res = 0;
+            if (valid) {
+                t = __ldcg(&work[k]);
+                const TableDev& T = M.tabs[t];
+                const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+                r = u - pre_at(pR, k, gpre);
+                const int i = __ldg(&T.rowVar[r]);
+                const int a = r - V.row0(i);
+                const bool present =
+                    __ldcg(&T.varSup[i]) && ((__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u);
+                if (present) {
+                    if (T.useResidues) {
+                        res = T.residue[r];
+                        hit = nz(and4(ld_sup(T.sup + (size_t)r * T.W4 + res), __ldcg(T.curr + res)));
+                    }
+                    need = !hit;
+                }
             }
-            res = __shfl_sync(0xffffffffu, res, 0);
-            probe_row(T, r, present, res, sr, sm.cnt);
+            unsigned miss = __ballot_sync(0xffffffffu, need);
+            const int nhit = __popc(__ballot_sync(0xffffffffu, hit));
+            if (lane == 0 && nhit) atomicAdd(&sm.cnt[kCntHits], (unsigned)nhit);
+            while (miss) {
+                const int l = __ffs(miss) - 1;
+                miss &= miss - 1u;
+                const int tl = __shfl_sync(0xffffffffu, t, l);
+                probe_miss(M.tabs[tl], __shfl_sync(0xffffffffu, r, l), __shfl_sync(0xffffffffu, res, l), sm.cnt);
+            }
         }
         if (!sync()) return;
+        phase(3);
 
         // full scans of the values whose residues and windows missed
         for (int u = gwarp; u < totalUnits; u += nwarps) {
@@ -1024,6 +1083,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             scan_segment<U, true>(T, u - pre_at(pU, k, gpre), nh, nullptr);
         }
         if (!sync()) return;
+        phase(4);
 
         // Algorithm 3 line 4: remove the values no live tuple carries
         for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
@@ -1042,36 +1102,53 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                     atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
                     atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                     const int v = M.scopeVar[M.scopeBase[t] + i];
-                    const int old = atomicCAS(&M.prunedBy[v], -1, t);
-                    if (old != -1 && old != t) atomicExch(&M.prunedBy[v], -2);
+                    const int old = atomicCAS(&pruned[v], -1, t);
+                    if (old != -1 && old != t) atomicExch(&pruned[v], -2);
                 }
             }
         }
+        __syncthreads();
+        if (tid == 0) {
+            if (sm.cnt[kCntHits]) atomicAdd(&C->hits, sm.cnt[kCntHits]);
+            if (sm.cnt[kCntLocal]) atomicAdd(&C->local, sm.cnt[kCntLocal]);
+            if (sm.cnt[kCntMiss]) atomicAdd(&C->hard, sm.cnt[kCntMiss]);
+            if (sm.cnt[kCntWin]) atomicAdd(&C->windows, sm.cnt[kCntWin]);
+            sm.cnt[kCntHits] = sm.cnt[kCntLocal] = sm.cnt[kCntMiss] = sm.cnt[kCntWin] = 0u;
+        }
         if (!sync()) return;
+        phase(5);
 
-        // next round: every table that shares a variable another table pruned
-        if (blockIdx.x == 0) {
+        // next round (whole grid): every table of a live node that shares a
+        // variable another table pruned; the other parity's marks are cleared
+        // for the round after
+        {
             int32_t* next = M.work + (size_t)(cur ^ 1) * M.ntables;
-            for (int k = tid; k < nwork; k += kThreads) {
+            int32_t* nnext = &C->nnext[(round + 1) & 1];
+            const int gtid = blockIdx.x * kThreads + tid, gth = gridDim.x * kThreads;
+            for (int k = gtid; k < nwork; k += gth) {
                 Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
                 if (__ldcg(&Tc->nrows) > 0) Tc->live_state = (int32_t)__ldcg(&Tc->live);
                 Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
             }
-            if (tid == 0) sm.flag[2] = 0;
-            __syncthreads();
-            for (int t = tid; t < M.ntables; t += kThreads) {
-                if (__ldcg(&M.nodeStatus[t / M.nodeTables]) != CT_OK) continue;
+            for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
+                const int t = t0 + lane;
                 bool dirty = false;
-                for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
-                    const int p = __ldcg(&M.prunedBy[M.scopeVar[j]]);
-                    dirty = p != -1 && p != t;
+                if (t < M.ntables && __ldcg(&M.nodeStatus[t / M.nodeTables]) == CT_OK) {
+                    for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
+                        const int p = __ldcg(&pruned[M.scopeVar[j]]);
+                        dirty = p != -1 && p != t;
+                    }
                 }
-                if (dirty) next[atomicAdd(&sm.flag[2], 1)] = t;
+                const unsigned bal = __ballot_sync(0xffffffffu, dirty);
+                if (bal) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(nnext, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (dirty) next[base + __popc(bal & lanemask_lt())] = t;
+                }
             }
-            __syncthreads();
-            for (int v = tid; v < M.nvars; v += kThreads) M.prunedBy[v] = -1;
-            if (tid == 0) {
-                C->nwork = sm.flag[2];
+            for (int v = gtid; v < M.nvars; v += gth) prunedNext[v] = -1;
+            if (blockIdx.x == 0 && tid == 0) {
                 C->rounds += 1;
                 C->props += nwork;
             }
@@ -1079,7 +1156,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         cur ^= 1;
         ++round;
         if (!sync()) return;
-        if (__ldcg(&C->nwork) == 0) break;
+        if (__ldcg(&C->nnext[round & 1]) == 0) break;
         if (round >= M.maxRounds) {
             if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_ERR_TIMEOUT);
             break;
@@ -1088,6 +1165,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
 
     // publish (CTA 0; every CTA left the loop at the same point)
     if (blockIdx.x != 0) return;
+    phase(6);
     __threadfence();
     __syncthreads();
     int32_t* H = M.statusBlk;
@@ -1108,16 +1186,22 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         outNode[q] = __ldcg(&M.nodeStatus[q]);
         M.nodeStatus[q] = CT_OK;
     }
-    for (int v = tid; v < M.nvars; v += kThreads) M.prunedBy[v] = -1;
+    for (int v = tid; v < 2 * M.nvars; v += kThreads) M.prunedBy[v] = -1;
     __syncthreads();
     if (tid == 0) {
         const int st = __ldcg(&C->status);
         H[1] = __ldcg(&C->rounds);
         H[2] = __ldcg(&C->props);
+        H[3] = (int32_t)__ldcg(&C->hits);
+        H[4] = (int32_t)__ldcg(&C->local);
+        H[5] = (int32_t)__ldcg(&C->hard);
+        H[6] = (int32_t)__ldcg(&C->windows);
+        C->hits = C->local = C->hard = C->windows = 0u;
         C->status = CT_OK;
         C->rounds = 0;
         C->props = 0;
         C->nwork = 0;
+        phase(7);
         st_release_sys(&H[0], st);
     }
 }

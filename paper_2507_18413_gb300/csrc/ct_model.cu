@@ -61,7 +61,7 @@ int batch_setup(ct_model* m) {
     if ((st = m_alloc(m, &M.work, 2 * (size_t)n)) != CT_OK) return st;
     if ((st = m_alloc(m, &M.unitPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &M.rowPrefix, (size_t)n + 1)) != CT_OK) return st;
-    if ((st = m_alloc(m, &dPruned, (size_t)m->nvars)) != CT_OK) return st;
+    if ((st = m_alloc(m, &dPruned, 2 * (size_t)m->nvars)) != CT_OK) return st;
     if ((st = m_alloc(m, &dCtrl, 1)) != CT_OK) return st;
     const int nodeTables = std::max(n, 1);  // the whole network is one node
     const int nnodes = 1;
@@ -72,7 +72,7 @@ int batch_setup(ct_model* m) {
         CT_CUDA(cudaMemcpyAsync(dOff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, m->stream));
         CT_CUDA(cudaMemcpyAsync(dVar, var.data(), var.size() * 4, cudaMemcpyHostToDevice, m->stream));
     }
-    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, (size_t)m->nvars * 4, m->stream));
+    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, 2 * (size_t)m->nvars * 4, m->stream));
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), m->stream));
     if (cudaHostAlloc((void**)&m->h_calls, std::max(n, 1) * sizeof(ModelTabCall), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void**)&m->h_work, (size_t)(n + 1) * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||

@@ -101,6 +101,7 @@ struct ct_batch {
     size_t offCalls = 0, offDom = 0, offWork = 0, offRest = 0, stageBytes = 0;
     int32_t* h_status = nullptr;  // mapped: header, (trail_top, live) per table, domains, node statuses
     ModelDev md{};
+    uint64_t* d_phase = nullptr;  // [kModelPhases] with ct_options.profile
     int grid = 1;
     std::vector<void*> allocs;
     bool broken = false;
@@ -173,9 +174,10 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     }
     int32_t *dBase, *dOff, *dVar, *dPruned, *dNode, *dUnit, *dRow;
     ModelCtrl* dCtrl;
+    if (m->opt.profile && (st = b_alloc(b, &b->d_phase, kModelPhases)) != CT_OK) return st;
     if ((st = b_alloc(b, &b->d_tabs, n)) != CT_OK || (st = b_alloc(b, &b->d_src, T)) != CT_OK ||
         (st = b_alloc(b, &dBase, n + 1)) != CT_OK || (st = b_alloc(b, &dOff, off.size())) != CT_OK ||
-        (st = b_alloc(b, &dVar, var.size())) != CT_OK || (st = b_alloc(b, &dPruned, (size_t)B * m->nvars)) != CT_OK ||
+        (st = b_alloc(b, &dVar, var.size())) != CT_OK || (st = b_alloc(b, &dPruned, 2 * (size_t)B * m->nvars)) != CT_OK ||
         (st = b_alloc(b, &dNode, B)) != CT_OK || (st = b_alloc(b, &dUnit, n + 1)) != CT_OK ||
         (st = b_alloc(b, &dRow, n + 1)) != CT_OK || (st = b_alloc(b, &dCtrl, 1)) != CT_OK)
         return st;
@@ -199,7 +201,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     CT_CUDA(cudaMemcpyAsync(dBase, base.data(), base.size() * 4, cudaMemcpyHostToDevice, s));
     CT_CUDA(cudaMemcpyAsync(dOff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s));
     CT_CUDA(cudaMemcpyAsync(dVar, var.data(), var.size() * 4, cudaMemcpyHostToDevice, s));
-    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, (size_t)B * m->nvars * 4, s));
+    CT_CUDA(cudaMemsetAsync(dPruned, 0xff, 2 * (size_t)B * m->nvars * 4, s));
     CT_CUDA(cudaMemsetAsync(dNode, 0, (size_t)B * 4, s));
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), s));
     std::vector<TableDev> td(n);
@@ -234,6 +236,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     M.restores = reinterpret_cast<const RestoreDesc*>(b->d_stage + b->offRest);
     M.nrestores = 0;
     M.nworkIn = reinterpret_cast<const int32_t*>(b->d_stage);
+    M.phaseNs = b->d_phase;
     const int maxCo = max_coresident_model_blocks();
     if (maxCo <= 0) {
         ct_set_error("batched search: the fixpoint kernel cannot be made resident on this device");
@@ -592,6 +595,7 @@ struct Search {
                 break;
         }
         if (!seen) CT_CUDA(cudaStreamSynchronize(b->stream));
+        info.wait_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
         const int status = H[0];
         if (status != CT_OK) {
             b->broken = true;
@@ -603,6 +607,10 @@ struct Search {
             return status < 0 ? status : CT_ERR_STATE;
         }
         st.propagations += H[2];
+        info.rounds += H[1];
+        info.residue_hits += (uint32_t)H[3];
+        info.window_hits += (uint32_t)H[4];
+        info.hard_values += (uint32_t)H[5];
         for (int j = 0; j < n; ++j) {
             ct_table_batch_done(b->tabs[j], H[kModelHdr + 2 * j], H[kModelHdr + 2 * j + 1]);
             restPos[j] = -1;
@@ -621,6 +629,20 @@ struct Search {
     }
 
     int run_slots() {
+        const auto s0 = std::chrono::steady_clock::now();
+        if (b->d_phase) CT_CUDA(cudaMemsetAsync(b->d_phase, 0, kModelPhases * sizeof(uint64_t), b->stream));
+        int rc = run_slots_inner();
+        if (rc == CT_OK && b->d_phase) {
+            uint64_t ns[kModelPhases];
+            CT_CUDA(cudaMemcpyAsync(ns, b->d_phase, sizeof(ns), cudaMemcpyDeviceToHost, b->stream));
+            CT_CUDA(cudaStreamSynchronize(b->stream));
+            for (int p = 0; p < kModelPhases; ++p) info.phase_seconds[p] = 1e-9 * (double)ns[p];
+        }
+        info.slot_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - s0).count();
+        return rc;
+    }
+
+    int run_slots_inner() {
         const int n = b->n;
         slots.assign(B, Slot());
         dirty.assign(n, 0);

@@ -73,8 +73,11 @@ class ct_search_stats(ctypes.Structure):
 
 class ct_batch_info(ctypes.Structure):
     _fields_ = [("open_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("steps", ctypes.c_int64),
-                ("steals", ctypes.c_int64), ("slot_nodes", ctypes.c_int64), ("slots", ctypes.c_int32),
-                ("split_depth", ctypes.c_int32), ("setup_seconds", ctypes.c_double)]
+                ("steals", ctypes.c_int64), ("slot_nodes", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("residue_hits", ctypes.c_int64), ("window_hits", ctypes.c_int64), ("hard_values", ctypes.c_int64),
+                ("slots", ctypes.c_int32), ("split_depth", ctypes.c_int32), ("setup_seconds", ctypes.c_double),
+                ("wait_seconds", ctypes.c_double), ("slot_seconds", ctypes.c_double),
+                ("phase_seconds", ctypes.c_double * 8)]
 
 
 def _as_dict(s):
