@@ -62,8 +62,9 @@ def parse():
     p.add_argument("--seed", type=int, default=20250724)
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--case", default="stream", choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7"],
-                   help="bulk*: only the one-call bandwidth case (for profiling)")
+    p.add_argument("--case", default="stream", choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search"],
+                   help="bulk*: only the one-call bandwidth case (for profiling); "
+                        "search: only the plain vs batched search figures")
     return p.parse_args()
 
 
@@ -141,19 +142,30 @@ def clocks_stop(proc):
             "samples": len(sm)}
 
 
+def kernel_source_hash():
+    """First 16 hex digits of the sha256 of the propagation kernel's sources
+    (ct_device.cuh followed by ct_kernels.cu)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2507_18413_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("ct_device.cuh", "ct_kernels.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the propagation kernel from the committed ncu
-    summary, if it was taken on the kernel source as it is now (else None)."""
-    import hashlib
+    summary, if it was taken on the kernel sources as they are now (else None)."""
     import re
     try:
-        src = open(os.path.join(ROOT, "paper_2507_18413_gb300", "csrc", "ct_kernels.cu"), "rb").read()
+        src_hash = kernel_source_hash()
         md = open(os.path.join(ROOT, "profiles", "dram_ct_propagate_kernel_stream_t4000000.md")).read()
     except OSError:
         return None
     h = re.search(r"kernel_sha256_16: ([0-9a-f]{16})", md)
     v = re.search(r"traffic_bytes_per_launch: (\d+)", md)
-    if not h or not v or hashlib.sha256(src).hexdigest()[:16] != h.group(1):
+    if not h or not v or src_hash != h.group(1):
         return None
     return int(v.group(1))
 
@@ -473,6 +485,52 @@ def _dfs_rate(C, node_limit=3000, host_fixpoint=0):
             "table_propagations_per_s": round(s["propagations"] / s["seconds"], 1)}
 
 
+def _build_model(C, spec):
+    st, m = C.ct_model_create(spec.dom_lo, spec.dom_size)
+    C.check(st)
+    for tb in spec.tables:
+        C.check(C.ct_model_add_table(m, tb.scope, tb.tuples))
+    return m
+
+
+def _search_compare(C, name, spec, slots=256, split=10, plain_limit=3000, batch_limit=20000):
+    """Nodes/s of the plain search (one node per launch) and of the batched search
+    (slots x tables propagated per launch) on the same CSP, counting all solutions
+    up to a node limit; the batched figure is the second of two calls (the first
+    builds the slot copies and grows their trails)."""
+    m = _build_model(C, spec)
+    try:
+        st, p = C.ct_search_dfs(m, spec.nvars, plain_limit, True)
+        C.check(st)
+        first = None
+        for _ in range(2):
+            st, b, info = C.ct_search_batch(m, spec.nvars, slots, split, batch_limit, True)
+            C.check(st)
+            first = first or (b["seconds"], info["setup_seconds"])
+    finally:
+        C.ct_model_destroy(m)
+    plain_nps = p["nodes"] / p["seconds"]
+    batch_nps = b["nodes"] / b["seconds"]
+    return {"csp": name, "plain": {"nodes": p["nodes"], "seconds": round(p["seconds"], 3),
+                                   "nodes_per_s": round(plain_nps, 1)},
+            "batched": {"slots": slots, "split_depth": split, "nodes": b["nodes"], "fails": b["fails"],
+                        "solutions": b["solutions"], "seconds": round(b["seconds"], 3),
+                        "nodes_per_s": round(batch_nps, 1), "launches": info["steps"],
+                        "rounds": info["rounds"], "open_nodes": info["open_nodes"], "steals": info["steals"],
+                        "device_wait_s": round(info["wait_seconds"], 3),
+                        "first_call_s": round(first[0], 3), "copies_setup_s": round(first[1], 3)},
+            "speedup": round(batch_nps / plain_nps, 2)}
+
+
+def search_extras(C):
+    out = {}
+    out["config2_20v_8t_arity6_1e5"] = _search_compare(
+        C, "20 vars d=32, 8 tables arity 6 x 1e5 tuples", G.random_csp(2024, 20, 8, 6, 32, 100_000))
+    out["config3_40v_60t_arity4"] = _search_compare(
+        C, "40 vars d=24, 60 tables arity 4 x log-uniform 1e4..2e5 tuples", G.batching_csp(3003))
+    return out
+
+
 def extras(args, C, torch, stream):
     out = {}
     try:
@@ -483,6 +541,7 @@ def extras(args, C, torch, stream):
         out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)
         out["dfs_plain_first_fail"] = _dfs_rate(C)
         out["dfs_plain_first_fail_host_queue"] = _dfs_rate(C, host_fixpoint=1)
+        out["search_batched_vs_plain"] = search_extras(C)
     except Exception as e:  # context figures must not hide the main line
         out["error"] = repr(e)
     return out
@@ -588,7 +647,9 @@ def main():
         B.build()
         C.load()
         stream = torch.cuda.current_stream()
-        if args.case == "bulk1e6":
+        if args.case == "search":
+            print(json.dumps(search_extras(C)))
+        elif args.case == "bulk1e6":
             print(json.dumps(_bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)))
         elif args.case == "bulk4e6":
             print(json.dumps(_bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)))

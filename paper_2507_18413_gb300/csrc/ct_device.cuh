@@ -1,0 +1,498 @@
+// ct_device.cuh -- device building blocks shared by the propagation kernel of
+// one table (ct_kernels.cu) and the network fixpoint kernel (ct_model_kernels.cu):
+// 128-bit helpers, the bounded grid barrier, the plan of Algorithms 1-2, the
+// segment update of Algorithm 2 with its trail, the residue probes of
+// Algorithm 3 and the scan of the hard values.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ct_internal.cuh"
+
+namespace ctk {
+namespace {
+
+
+__device__ __forceinline__ bool nz(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
+
+__device__ __forceinline__ uint4 or4(const uint4& a, const uint4& b) {
+    return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+}
+
+__device__ __forceinline__ uint4 and4(const uint4& a, const uint4& b) {
+    return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+__device__ __forceinline__ uint4 not4(const uint4& a) { return make_uint4(~a.x, ~a.y, ~a.z, ~a.w); }
+
+__device__ __forceinline__ bool eq4(const uint4& a, const uint4& b) {
+    return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) == 0u;
+}
+
+__device__ __forceinline__ uint32_t nzwords(const uint4& v) {
+    return (v.x != 0u) + (v.y != 0u) + (v.z != 0u) + (v.w != 0u);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Read-only 128-bit load of a supports chunk (the supports never change).
+__device__ __forceinline__ uint4 ld_sup(const uint4* p) { return __ldg(p); }
+
+// Predicated read-only 128-bit load (zero when `pred` is false), not kept in
+// L1 (the supports rows stream through once per call). Written as volatile PTX
+// so that a batch of them issues back to back, before any use.
+__device__ __forceinline__ uint4 ld_sup_pred(const uint4* p, bool pred) {
+    uint4 v;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
+        "@q ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "r"((int)pred));
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident). The last CTA
+// to arrive resets the count and advances the generation; the others poll the
+// generation at most kBarrierSpinLimit times. Returns false (after setting
+// CT_ERR_TIMEOUT) when the wait ran out.
+__device__ bool grid_sync_raw(unsigned* count, unsigned* gen, int* status, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(gen);
+        unsigned arrived;
+        // Release this CTA's writes (ordered before by the CTA barrier) and, for
+        // the last arrival, acquire everybody else's.
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(count) : "memory");
+        if (arrived == gridDim.x - 1) {
+            *count = 0u;
+            st_release(gen, g + 1u);
+        } else {
+            unsigned it = 0;
+            while (ld_acquire(gen) == g) {
+                if (++it > kBarrierSpinLimit) {
+                    ok = 0;
+                    atomicExch(status, CT_ERR_TIMEOUT);
+                    break;
+                }
+                if (it > 64) __nanosleep(32);
+            }
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl* C, int* s_flag) {
+    return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, s_flag);
+}
+
+struct Smem {
+    int32_t codes[kCodeCap];        // row codes of the plan; hard rows in the scan phase
+    uint32_t dom[kLocalMaxDW];      // domains at entry, packed in scope order (local plan)
+    int32_t k[kLocalMaxArity];      // rows to OR per variable | kCodeDelta
+    int32_t rowOff[kLocalMaxArity]; // first code of each variable
+    int32_t sup[kLocalMaxArity];    // |dom| > 1
+    int32_t scan[kThreads];
+    uint32_t cnt[12];
+    int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
+    int flag[4];
+    int tr[kWarps];                 // trail entries per warp, then their offsets
+    int trBase;
+};
+
+enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin };
+
+// ---------------------------------------------------------------------------
+// plan: Algorithm 1 lines 1-3 and the row selection of Algorithm 2.
+// Writes k/rowOff/sup/codes through generic pointers (shared or global).
+// ---------------------------------------------------------------------------
+// Layout of scope variable i: from the kernel parameters for small scopes
+// (pOff: domain offsets passed as parameters, or null to read domOff).
+struct VarLayout {
+    const TableDev& T;
+    const int32_t* pOff;
+    const int32_t* domOff;
+    bool small;
+    __device__ VarLayout(const TableDev& t, const int32_t* p, const int32_t* d)
+        : T(t), pOff(p), domOff(d), small(t.arity <= kParamArity) {}
+    __device__ int nw(int i) const { return small ? T.pNW[i] : T.varNW[i]; }
+    __device__ int ld(int i) const { return small ? T.pLD[i] : T.varLD[i]; }
+    __device__ int row0(int i) const { return small ? T.pRow0[i] : T.varRow0[i]; }
+    __device__ int off(int i) const { return (small && pOff) ? pOff[i] : domOff[i]; }
+};
+
+__device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __restrict__ dom, int32_t* K,
+                     int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm) {
+    const int tid = threadIdx.x;
+    if (tid < 8) sm.flags[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < T.arity; i += kThreads) {
+        const int nw = V.nw(i);
+        const uint32_t* d = dom + V.off(i);
+        const uint32_t* l = T.lastDom + V.ld(i);
+        int nd = 0, ndel = 0;
+        uint32_t grow = 0u;
+        for (int q = 0; q < nw; ++q) {
+            const uint32_t dv = d[q], lv = l[q];
+            grow |= dv & ~lv;
+            nd += __popc(dv);
+            ndel += __popc(lv & ~dv);
+            if (domCopy) domCopy[V.ld(i) + q] = dv;
+        }
+        sup[i] = nd > 1;
+        if (grow) atomicExch(&sm.flags[0], 1);
+        if (nd == 0) atomicExch(&sm.flags[1], 1);
+        if (nd > 1) atomicAdd(&sm.flags[5], 1);
+        int k = 0;
+        if (ndel > 0) {
+            // Algorithm 2, line 3: the delta mask when |Delta| < |dom| (strict).
+            if (ndel < nd) { k = ndel | kCodeDelta; atomicAdd(&sm.flags[3], 1); }
+            else { k = nd; atomicAdd(&sm.flags[4], 1); }
+            atomicAdd(&sm.flags[2], 1);
+        }
+        K[i] = k;
+    }
+    __syncthreads();
+    if (sm.flags[0] || sm.flags[1]) {
+        if (tid == 0) sm.flags[6] = 0;
+        __syncthreads();
+        return;
+    }
+    if (T.arity <= 32) {
+        // One warp: lane i owns variable i.
+        if (tid < 32) {
+            const int k = tid < T.arity ? (K[tid] & kCodeRow) : 0;
+            int incl = k;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += a;
+            }
+            if (tid < T.arity) rowOff[tid] = incl - k;
+            if (tid == 31) sm.scan[kThreads - 1] = incl;
+        }
+        __syncthreads();
+    } else {
+        // Exclusive scan of the row counts, each thread owning a run of variables.
+        const int per = (T.arity + kThreads - 1) / kThreads;
+        const int b0 = tid * per, b1 = min(T.arity, b0 + per);
+        int sum = 0;
+        for (int i = b0; i < b1; ++i) sum += K[i] & kCodeRow;
+        sm.scan[tid] = sum;
+        __syncthreads();
+        for (int off = 1; off < kThreads; off <<= 1) {
+            const int a = tid >= off ? sm.scan[tid - off] : 0;
+            __syncthreads();
+            sm.scan[tid] += a;
+            __syncthreads();
+        }
+        int run = sm.scan[tid] - sum;
+        for (int i = b0; i < b1; ++i) {
+            rowOff[i] = run;
+            run += K[i] & kCodeRow;
+        }
+        __syncthreads();
+    }
+    // Codes: the removed values (delta) or the remaining ones (reset).
+    for (int i = tid; i < T.arity; i += kThreads) {
+        const int k = K[i] & kCodeRow;
+        if (k == 0) continue;
+        const bool delta = (K[i] & kCodeDelta) != 0;
+        const int nw = V.nw(i);
+        const uint32_t* d = dom + V.off(i);
+        const uint32_t* l = T.lastDom + V.ld(i);
+        const int row0 = V.row0(i);
+        int out = rowOff[i];
+        const int last = out + k - 1;
+        for (int q = 0; q < nw; ++q) {
+            uint32_t bits = delta ? (l[q] & ~d[q]) : d[q];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                int code = row0 + q * 32 + b;
+                if (delta) code |= kCodeDelta;
+                if (out == last) code |= kCodeLast;
+                codes[out++] = code;
+            }
+        }
+    }
+    if (tid == 0) sm.flags[6] = sm.scan[kThreads - 1];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// update: Algorithm 2 on one 32-chunk segment (lane l owns chunk 32*seg + l)
+// ---------------------------------------------------------------------------
+// Segment state read before the plan is known (it does not depend on it).
+struct SegState {
+    uint32_t mask;
+    uint4 cur;  // dead chunks are zero
+    int lp;
+};
+
+__device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int mark) {
+    const int w = seg * 32 + (threadIdx.x & 31);
+    const bool in = w < T.W4;  // the last segment may be partial
+    SegState st;
+    st.mask = T.segMask[seg];
+    st.cur = in ? T.curr[w] : make_uint4(0u, 0u, 0u, 0u);
+    st.lp = (in && mark >= 0) ? T.lastpos[w] : 0x7fffffff;
+    return st;
+}
+
+// OR the batch into the running mask; at the last row of a variable apply the
+// mask to the accumulator, complemented on the delta path (Algorithm 2).
+template <int U>
+__device__ __forceinline__ void combine_batch(int q0, int nrows, const int (&code)[U], const uint4 (&v)[U], uint4& m,
+                                              uint4& acc) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (q0 + u < nrows) {
+            m = or4(m, v[u]);
+            if (code[u] & kCodeLast) {
+                acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
+                m = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+}
+
+struct TrailItem {
+    bool need;  // the chunk changed and has no entry above the newest mark yet
+    int w;
+    int lp;
+    uint4 cur;
+};
+
+// Row code q: from the shared-memory copy, or from global memory through L2
+// when another CTA wrote the plan in this launch (kGlobal).
+template <bool kGlobal>
+__device__ __forceinline__ int code_at(const TableDev& T, const int32_t* s_codes, int q) {
+    if (kGlobal) return __ldcg(&T.codes[q]);
+    return q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]);
+}
+
+template <int U, bool kGlobal = false>
+__device__ __forceinline__ void update_segment(const TableDev& T, int mark, int snapFrom, int snapTo, int seg,
+                                               const SegState& S, int nrows, const int32_t* s_codes,
+                                               uint32_t* s_cnt, TrailItem& out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t mask = S.mask;
+    out.need = false;
+    // Levels saved since the last call snapshot the index as it is now.
+    for (int l = snapFrom + lane; l < snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
+    if (mask == 0u) return;
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
+    const uint4 cur = S.cur;
+    const int lp = S.lp;
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
+    const uint4* base = T.sup + w;
+    const size_t W4 = (size_t)T.W4;
+    // Batches of U rows: U independent 128-bit loads in flight per lane; the
+    // codes of the next batch are read from shared memory meanwhile.
+    int code[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) code[u] = u < nrows ? code_at<kGlobal>(T, s_codes, u) : 0;
+    for (int q0 = 0; q0 < nrows; q0 += U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+        int nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + U + u;
+            nxt[u] = q < nrows ? code_at<kGlobal>(T, s_codes, q) : 0;
+        }
+        combine_batch<U>(q0, nrows, code, v, m, acc);
+#pragma unroll
+        for (int u = 0; u < U; ++u) code[u] = nxt[u];
+        // Every chunk of this warp is already zero: later masks cannot revive it.
+        if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
+    }
+    const uint4 nv = and4(cur, acc);
+    const bool chg = act && !eq4(nv, cur);
+    const bool alive = act && nz(nv);
+    if (chg) T.curr[w] = nv;
+    out.need = chg && mark >= 0 && lp < mark;
+    out.w = w;
+    out.lp = lp;
+    out.cur = cur;
+    // The segment's part of the non-zero index: the live chunks after the update.
+    const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
+    uint32_t words = nzwords(cur);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(0xffffffffu, words, o);
+    if (lane == 0) {
+        if (nmask != mask) T.segMask[seg] = nmask;
+        atomicAdd(&s_cnt[kCntLive], (uint32_t)__popc(nmask));
+        atomicAdd(&s_cnt[kCntLiveIn], (uint32_t)__popc(mask));
+        atomicAdd(&s_cnt[kCntWords], words);
+    }
+}
+
+// Trail entries of one round of segments: one reservation per CTA.
+__device__ __forceinline__ void trail_round(const TableDev& T, const TrailItem& it, int cap, Smem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nb = __ballot_sync(0xffffffffu, it.need);
+    if (lane == 0) sm.tr[warp] = __popc(nb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < kWarps; ++k) {
+            const int c = sm.tr[k];
+            sm.tr[k] = tot;
+            tot += c;
+        }
+        int base = 0;
+        if (tot) {
+            base = atomicAdd(&T.ctrl->trail_top, tot);
+            if (base + tot > cap) {
+                atomicExch(&T.ctrl->status, CT_ERR_OOM);
+                base = -1;
+            }
+            sm.cnt[kCntTrail] += (uint32_t)tot;
+        }
+        sm.trBase = base;
+    }
+    __syncthreads();
+    if (it.need && sm.trBase >= 0) {
+        const int p = sm.trBase + sm.tr[warp] + __popc(nb & lanemask_lt());
+        T.trailKey[p] = make_int2(it.w, it.lp);
+        T.trailOld[p] = it.cur;
+        T.lastpos[it.w] = p;
+    }
+}
+
+// Trail entries of one warp: one reservation per warp (used when the CTA's
+// warps work on different tables).
+__device__ __forceinline__ void trail_warp(const TableDev& T, const TrailItem& it, int cap, int* status) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nb = __ballot_sync(0xffffffffu, it.need);
+    if (!nb) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&T.ctrl->trail_top, __popc(nb));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + __popc(nb) > cap) {
+        if (lane == 0) atomicCAS(status, CT_OK, CT_ERR_OOM);
+        return;
+    }
+    if (it.need) {
+        const int p = base + __popc(nb & lanemask_lt());
+        T.trailKey[p] = make_int2(it.w, it.lp);
+        T.trailOld[p] = it.cur;
+        T.lastpos[it.w] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// probe: Algorithm 3 with residues, a warp per value whose residue missed
+// ---------------------------------------------------------------------------
+// A value whose residue missed (whole warp): windows of 32 chunks after the
+// residue; a value missed there too goes to the table's hard list.
+__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (T.useResidues) {
+        const int W4 = T.W4;
+        const uint4* row = T.sup + (size_t)r * W4;
+        for (int b = 0; b < kLocalProbes; ++b) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
+            const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
+            const bool h = nz(and4(ld_sup(row + c), __ldcg(T.curr + c)));
+            const unsigned bal = __ballot_sync(0xffffffffu, h);
+            if (bal) {
+                const int cf = __shfl_sync(0xffffffffu, c, __ffs(bal) - 1);
+                if (lane == 0) {
+                    T.residue[r] = cf;
+                    atomicAdd(&s_cnt[kCntLocal], 1u);
+                }
+                return;
+            }
+        }
+    }
+    if (lane == 0) {
+        const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
+        T.hardRow[m] = r;
+        T.foundChunk[m] = kNoChunk;
+        atomicAdd(&s_cnt[kCntMiss], 1u);
+    }
+}
+
+__device__ __forceinline__ void probe_row(const TableDev& T, int r, bool present, int res, uint4 supRes,
+                                          uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (!present) return;
+    if (T.useResidues) {
+        bool hit = false;
+        if (lane == 0) hit = nz(and4(supRes, __ldcg(T.curr + res)));
+        if (__shfl_sync(0xffffffffu, hit, 0)) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
+            return;
+        }
+    }
+    probe_miss(T, r, res, s_cnt);
+}
+
+// ---------------------------------------------------------------------------
+// scan: the hard values against the live chunks of one segment
+// ---------------------------------------------------------------------------
+template <int U, bool kGlobal = false>
+__device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh, const int32_t* s_rows) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t mask = __ldcg(&T.segMask[seg]);
+    if (mask == 0u) return;
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
+    const uint4 cur = act ? __ldcg(T.curr + w) : make_uint4(0u, 0u, 0u, 0u);
+    const size_t W4 = (size_t)T.W4;
+    for (int m0 = 0; m0 < nh; m0 += U) {
+        bool hit[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int mm = m0 + u;
+            hit[u] = false;
+            if (act && mm < nh) {
+                const int r = (!kGlobal && mm < kCodeCap) ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
+                hit[u] = nz(and4(ld_sup(T.sup + (size_t)r * W4 + w), cur));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (m0 + u < nh) {
+                const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
+                if (lane == 0 && bal) atomicMin(&T.foundChunk[m0 + u], seg * 32 + __ffs(bal) - 1);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void st_release_sys(int32_t* p, int32_t v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace
+}  // namespace ctk

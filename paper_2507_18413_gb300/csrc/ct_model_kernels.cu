@@ -1,0 +1,476 @@
+// ct_model_kernels.cu -- a network of tables propagated to its fixpoint in one
+// cooperative launch, the batched trail undo of several tables, and the state
+// copies of the batched search's table clones.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ct_device.cuh"
+
+namespace ctk {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// A network of tables to its fixpoint in one cooperative launch (Sec. 2:
+// propagation removes unsupported values until GAC holds everywhere or a
+// failure is found). Rounds are Jacobi steps: every table of the round's work
+// list propagates on the same domains (plan, updateTable, failure test,
+// filterDomains); their removals are applied together; a table joins the next
+// round when another table removed a value of one of its variables. The GAC
+// closure is unique, so the order of the propagations does not matter.
+// ---------------------------------------------------------------------------
+
+// Entry k of a round's prefix array: the shared-memory copy, or the global
+// array itself (read through L2) when the round is too long for the copy.
+__device__ __forceinline__ int pre_at(const int32_t* pre, int k, bool global) {
+    return global ? __ldcg(pre + k) : pre[k];
+}
+
+// Position k of the work list whose prefix range holds u: the largest k < n
+// with pre[k] <= u (pre is non-decreasing, pre[0] = 0 <= u). The whole warp
+// calls it with the same u. The answer stays in [lo, hi] with pre[lo] <= u;
+// each pass samples lo + j * step for j < 32, with 32 * step covering the
+// hi - lo + 1 candidates, and keeps the stretch from the last sample <= u to
+// the next sample.
+__device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u, bool global) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n - 1;
+    while (hi - lo >= 32) {
+        const int step = (hi - lo + 32) >> 5;
+        const int k = lo + lane * step;
+        const unsigned b = __ballot_sync(0xffffffffu, k <= hi && pre_at(pre, k, global) <= u);
+        lo += (31 - __clz(b)) * step;
+        hi = min(hi, lo + step - 1);
+    }
+    const int k = lo + lane;
+    const unsigned b = __ballot_sync(0xffffffffu, k <= hi && pre_at(pre, k, global) <= u);
+    return lo + (31 - __clz(b));
+}
+
+// Exclusive prefix of val(work[k]) over k < n into out[0..n] (one CTA).
+template <typename F>
+__device__ void block_prefix(const int32_t* work, int n, F val, int32_t* out, Smem& sm) {
+    const int tid = threadIdx.x;
+    const int per = (n + kThreads - 1) / kThreads;
+    const int b0 = tid * per, b1 = min(n, b0 + per);
+    int sum = 0;
+    for (int k = b0; k < b1; ++k) sum += val(__ldcg(&work[k]));
+    sm.scan[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < kThreads; off <<= 1) {
+        const int a = tid >= off ? sm.scan[tid - off] : 0;
+        __syncthreads();
+        sm.scan[tid] += a;
+        __syncthreads();
+    }
+    int run = sm.scan[tid] - sum;
+    for (int k = b0; k < b1; ++k) {
+        out[k] = run;
+        run += val(__ldcg(&work[k]));
+    }
+    if (tid == kThreads - 1) out[n] = sm.scan[kThreads - 1];
+    __syncthreads();
+}
+
+template <int U>
+__global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_constant__ ModelDev M) {
+    __shared__ Smem sm;
+    ModelCtrl* C = M.ctrl;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int gwarp = blockIdx.x * kWarps + warp;
+    const int nwarps = gridDim.x * kWarps;
+    int32_t* preU = sm.codes;                               // unit prefix of the round (smem copy)
+    int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
+    auto sync = [&]() { return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, &sm.flag[0]); };
+    // optional phase clock: CTA 0 adds the time since its previous mark (a grid
+    // barrier ends every phase, so this is the phase's length across the grid)
+    uint64_t tmark = (M.phaseNs && blockIdx.x == 0 && tid == 0) ? gtimer() : 0ull;
+    auto phase = [&](int p) {
+        if (M.phaseNs && blockIdx.x == 0 && tid == 0) {
+            const uint64_t now = gtimer();
+            M.phaseNs[p] += now - tmark;
+            tmark = now;
+        }
+    };
+
+    if (tid < 12) sm.cnt[tid] = 0u;
+    __syncthreads();
+    // Trail undos asked for with this launch (one CTA per table): the chunks
+    // changed since the level's mark get their value at the mark back, and the
+    // index and lastDom their snapshot of the level.
+    if (M.nrestores > 0) {
+        for (int i = blockIdx.x; i < M.nrestores; i += gridDim.x) {
+            const RestoreDesc d = M.restores[i];
+            const TableDev& T = M.tabs[d.table];
+            for (int p = d.mark + tid; p < d.top; p += kThreads) {
+                const int2 k = T.trailKey[p];
+                if (k.y < d.mark) {
+                    T.curr[k.x] = T.trailOld[p];
+                    T.lastpos[k.x] = k.y;
+                }
+            }
+            const uint32_t* ls = T.levelSeg + (size_t)d.level * T.nseg;
+            const uint32_t* ld = T.levelDom + (size_t)d.level * T.DW;
+            for (int q = tid; q < T.nseg; q += kThreads) T.segMask[q] = ls[q];
+            for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = ld[q];
+            if (tid == 0) {
+                T.ctrl->trail_top = d.mark;
+                T.ctrl->status = CT_OK;
+            }
+        }
+        if (!sync()) return;
+    }
+    // Levels saved since each table's last propagation snapshot it as it is now.
+    for (int t = blockIdx.x; t < M.ntables; t += gridDim.x) {
+        const TableDev& T = M.tabs[t];
+        const ModelTabCall cl = M.calls[t];
+        for (int l = cl.snapFrom; l < cl.snapTo; ++l) {
+            for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[(size_t)l * T.nseg + q] = __ldcg(&T.segMask[q]);
+            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = __ldcg(&T.lastDom[q]);
+        }
+    }
+    int cur = 0, round = 0;
+    for (;;) {
+        const int nwork = round > 0 ? __ldcg(&C->nnext[round & 1]) : M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
+        phase(round == 0 ? 0 : 6);
+        const int32_t* work = M.work + (size_t)cur * M.ntables;
+        int32_t* pruned = M.prunedBy + (size_t)(round & 1) * M.nvars;       // written by this round
+        int32_t* prunedNext = M.prunedBy + (size_t)((round + 1) & 1) * M.nvars;
+        // the collector of the next round's tables was last read two rounds ago
+        if (blockIdx.x == 0 && tid == 0) C->nnext[(round + 1) & 1] = 0;
+
+        // plan (Algorithm 1 lines 1-3), one CTA per table of the round
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            if (tid == 0) {
+                Ctrl* Tc = T.ctrl;
+                Tc->nrows = sm.flags[6];
+                Tc->nval = sm.flags[2];
+                Tc->ndelta = sm.flags[3];
+                Tc->nreset = sm.flags[4];
+                Tc->nsup = sm.flags[5];
+                if (sm.flags[0]) atomicCAS(&C->status, CT_OK, CT_ERR_STATE);
+                else if (sm.flags[1]) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;  // an empty domain
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0) {
+            block_prefix(work, nwork, [&](int t) { return M.tabs[t].nseg; }, M.unitPrefix, sm);
+            block_prefix(work, nwork, [&](int t) { return M.tabs[t].R; }, M.rowPrefix, sm);
+        }
+        if (!sync()) return;
+        phase(1);
+        if (__ldcg(&C->status) != CT_OK) break;
+        const bool gpre = nwork > kPrefixSmem;
+        const int32_t* pU = gpre ? M.unitPrefix : preU;
+        const int32_t* pR = gpre ? M.rowPrefix : preR;
+        if (!gpre) {
+            for (int k = tid; k <= nwork; k += kThreads) {
+                preU[k] = __ldcg(&M.unitPrefix[k]);
+                preR[k] = __ldcg(&M.rowPrefix[k]);
+            }
+            __syncthreads();
+        }
+        const int totalUnits = pre_at(pU, nwork, gpre);
+        const int totalRows = pre_at(pR, nwork, gpre);
+
+        // updateTable (Algorithm 2) over (table, segment) units
+        for (int u = gwarp; u < totalUnits; u += nwarps) {
+            const int k = find_prefix(pU, nwork, u, gpre);
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const int nrows = __ldcg(&T.ctrl->nrows);
+            if (nrows == 0) continue;
+            const int seg = u - pre_at(pU, k, gpre);
+            const int mark = M.calls[t].mark;
+            const SegState S = load_segment(T, seg, mark);
+            TrailItem it;
+            update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
+                                    reinterpret_cast<uint32_t*>(&T.ctrl->live), it);
+            trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
+        }
+        if (!sync()) return;
+        phase(2);
+
+        if (__ldcg(&C->status) != CT_OK) break;
+        // Algorithm 1 line 5: a table whose currTable became zero fails its node;
+        // the node's tables leave the work list from the next round on.
+        for (int k = blockIdx.x * kThreads + tid; k < nwork; k += gridDim.x * kThreads) {
+            const int t = __ldcg(&work[k]);
+            const Ctrl* Tc = M.tabs[t].ctrl;
+            if (__ldcg(&Tc->nrows) > 0 && __ldcg(&Tc->live) == 0u) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;
+        }
+        // lastDom := the domains of this round (removals below clear their bits)
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            for (int i = tid; i < T.arity; i += kThreads)
+                for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = __ldcg(&M.dom[V.off(i) + q]);
+        }
+        // filterDomains (Algorithm 3): the residue test of every (table, row) unit,
+        // one unit per lane; a warp then takes its lanes' misses one by one
+        // through the windows after the residue, and what misses there too
+        // goes to the full scan.
+        // rows per warp: up to 32, fewer when that spreads the rows (and their
+        // misses) over more warps
+        const int rpw = min(32, max(1, (totalRows + nwarps - 1) / nwarps));
+        for (int u0 = gwarp * rpw; u0 < totalRows; u0 += nwarps * rpw) {
+            const int u = u0 + lane;
+            const bool valid = lane < rpw && u < totalRows;
+            int k = find_prefix(pR, nwork, u0, gpre);
+            while (valid && k + 1 < nwork && pre_at(pR, k + 1, gpre) <= u) ++k;
+            bool need = false, hit = false;
+            int t = 0, r = 0, res = 0;
+            if (valid) {
+                t = __ldcg(&work[k]);
+                const TableDev& T = M.tabs[t];
+                const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+                r = u - pre_at(pR, k, gpre);
+                const int i = __ldg(&T.rowVar[r]);
+                const int a = r - V.row0(i);
+                const bool present =
+                    __ldcg(&T.varSup[i]) && ((__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u);
+                if (present) {
+                    if (T.useResidues) {
+                        res = T.residue[r];
+                        hit = nz(and4(ld_sup(T.sup + (size_t)r * T.W4 + res), __ldcg(T.curr + res)));
+                    }
+                    need = !hit;
+                }
+            }
+            unsigned miss = __ballot_sync(0xffffffffu, need);
+            const int nhit = __popc(__ballot_sync(0xffffffffu, hit));
+            if (lane == 0 && nhit) atomicAdd(&sm.cnt[kCntHits], (unsigned)nhit);
+            while (miss) {
+                const int l = __ffs(miss) - 1;
+                miss &= miss - 1u;
+                const int tl = __shfl_sync(0xffffffffu, t, l);
+                probe_miss(M.tabs[tl], __shfl_sync(0xffffffffu, r, l), __shfl_sync(0xffffffffu, res, l), sm.cnt);
+            }
+        }
+        if (!sync()) return;
+        phase(3);
+
+        // full scans of the values whose residues and windows missed
+        for (int u = gwarp; u < totalUnits; u += nwarps) {
+            const int k = find_prefix(pU, nwork, u, gpre);
+            const TableDev& T = M.tabs[__ldcg(&work[k])];
+            const int nh = (int)__ldcg(&T.ctrl->nhard);
+            if (nh == 0) continue;
+            scan_segment<U, true>(T, u - pre_at(pU, k, gpre), nh, nullptr);
+        }
+        if (!sync()) return;
+        phase(4);
+
+        // Algorithm 3 line 4: remove the values no live tuple carries
+        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+            const int t = __ldcg(&work[k]);
+            const TableDev& T = M.tabs[t];
+            const int nh = (int)__ldcg(&T.ctrl->nhard);
+            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            for (int m = tid; m < nh; m += kThreads) {
+                const int r = __ldcg(&T.hardRow[m]);
+                const int fc = __ldcg(&T.foundChunk[m]);
+                if (fc != kNoChunk) {
+                    T.residue[r] = fc;
+                } else {
+                    const int i = T.rowVar[r];
+                    const int a = r - V.row0(i);
+                    atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+                    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+                    const int v = M.scopeVar[M.scopeBase[t] + i];
+                    const int old = atomicCAS(&pruned[v], -1, t);
+                    if (old != -1 && old != t) atomicExch(&pruned[v], -2);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (sm.cnt[kCntHits]) atomicAdd(&C->hits, sm.cnt[kCntHits]);
+            if (sm.cnt[kCntLocal]) atomicAdd(&C->local, sm.cnt[kCntLocal]);
+            if (sm.cnt[kCntMiss]) atomicAdd(&C->hard, sm.cnt[kCntMiss]);
+            if (sm.cnt[kCntWin]) atomicAdd(&C->windows, sm.cnt[kCntWin]);
+            sm.cnt[kCntHits] = sm.cnt[kCntLocal] = sm.cnt[kCntMiss] = sm.cnt[kCntWin] = 0u;
+        }
+        if (!sync()) return;
+        phase(5);
+
+        // next round (whole grid): every table of a live node that shares a
+        // variable another table pruned; the other parity's marks are cleared
+        // for the round after
+        {
+            int32_t* next = M.work + (size_t)(cur ^ 1) * M.ntables;
+            int32_t* nnext = &C->nnext[(round + 1) & 1];
+            const int gtid = blockIdx.x * kThreads + tid, gth = gridDim.x * kThreads;
+            for (int k = gtid; k < nwork; k += gth) {
+                Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
+                if (__ldcg(&Tc->nrows) > 0) Tc->live_state = (int32_t)__ldcg(&Tc->live);
+                Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+            }
+            for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
+                const int t = t0 + lane;
+                bool dirty = false;
+                if (t < M.ntables && __ldcg(&M.nodeStatus[t / M.nodeTables]) == CT_OK) {
+                    for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
+                        const int p = __ldcg(&pruned[M.scopeVar[j]]);
+                        dirty = p != -1 && p != t;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, dirty);
+                if (bal) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(nnext, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (dirty) next[base + __popc(bal & lanemask_lt())] = t;
+                }
+            }
+            for (int v = gtid; v < M.nvars; v += gth) prunedNext[v] = -1;
+            if (blockIdx.x == 0 && tid == 0) {
+                C->rounds += 1;
+                C->props += nwork;
+            }
+        }
+        cur ^= 1;
+        ++round;
+        if (!sync()) return;
+        if (__ldcg(&C->nnext[round & 1]) == 0) break;
+        if (round >= M.maxRounds) {
+            if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_ERR_TIMEOUT);
+            break;
+        }
+    }
+
+    // publish (CTA 0; every CTA left the loop at the same point)
+    if (blockIdx.x != 0) return;
+    phase(6);
+    __threadfence();
+    __syncthreads();
+    int32_t* H = M.statusBlk;
+    for (int t = tid; t < M.ntables; t += kThreads) {
+        Ctrl* Tc = M.tabs[t].ctrl;
+        H[kModelHdr + 2 * t] = __ldcg(&Tc->trail_top);
+        H[kModelHdr + 2 * t + 1] = __ldcg(&Tc->live_state);
+        // leave every table's per-call counters clear
+        Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+        Tc->hits = 0; Tc->local_found = 0; Tc->misses = 0; Tc->windows = 0; Tc->trail_added = 0;
+        Tc->status = CT_OK;
+    }
+    uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kModelHdr + 2 * M.ntables);
+    for (int q = tid; q < M.DWg; q += kThreads) outDom[q] = __ldcg(&M.dom[q]);
+    const int nnodes = M.ntables / M.nodeTables;
+    int32_t* outNode = H + kModelHdr + 2 * M.ntables + M.DWg;
+    for (int q = tid; q < nnodes; q += kThreads) {
+        outNode[q] = __ldcg(&M.nodeStatus[q]);
+        M.nodeStatus[q] = CT_OK;
+    }
+    for (int v = tid; v < 2 * M.nvars; v += kThreads) M.prunedBy[v] = -1;
+    __syncthreads();
+    if (tid == 0) {
+        const int st = __ldcg(&C->status);
+        H[1] = __ldcg(&C->rounds);
+        H[2] = __ldcg(&C->props);
+        H[3] = (int32_t)__ldcg(&C->hits);
+        H[4] = (int32_t)__ldcg(&C->local);
+        H[5] = (int32_t)__ldcg(&C->hard);
+        H[6] = (int32_t)__ldcg(&C->windows);
+        C->hits = C->local = C->hard = C->windows = 0u;
+        C->status = CT_OK;
+        C->rounds = 0;
+        C->props = 0;
+        C->nwork = 0;
+        phase(7);
+        st_release_sys(&H[0], st);
+    }
+}
+
+// Restores of several tables in one launch: blockIdx.y picks the table.
+__global__ void ct_restore_batch_kernel(const TableDev* __restrict__ tabs, const __grid_constant__ RestoreBatch B) {
+    const RestoreDesc d = B.d[blockIdx.y];
+    const TableDev& T = tabs[d.table];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    for (int p = d.mark + tid; p < d.top; p += nth) {
+        const int2 k = T.trailKey[p];
+        if (k.y < d.mark) {
+            T.curr[k.x] = T.trailOld[p];
+            T.lastpos[k.x] = k.y;
+        }
+    }
+    const uint32_t* ls = T.levelSeg + (size_t)d.level * T.nseg;
+    const uint32_t* ld = T.levelDom + (size_t)d.level * T.DW;
+    for (int s = tid; s < T.nseg; s += nth) T.segMask[s] = ls[s];
+    for (int q = tid; q < T.DW; q += nth) T.lastDom[q] = ld[q];
+    if (tid == 0) {
+        T.ctrl->trail_top = d.mark;
+        T.ctrl->status = CT_OK;
+    }
+}
+
+// Clone j takes the state of source table j % nsrc (blockIdx.y = j - y0).
+__global__ void ct_clone_state_kernel(const TableDev* __restrict__ src, const TableDev* __restrict__ dst, int nsrc,
+                                      int y0) {
+    const int j = y0 + (int)blockIdx.y;
+    const TableDev& S = src[j % nsrc];
+    const TableDev& D = dst[j];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    const int pad = S.nseg * 32;
+    for (int q = tid; q < pad; q += nth) {
+        D.curr[q] = S.curr[q];
+        D.lastpos[q] = -1;
+    }
+    for (int q = tid; q < S.nseg; q += nth) D.segMask[q] = S.segMask[q];
+    for (int q = tid; q < S.R; q += nth) D.residue[q] = S.residue[q];
+    for (int q = tid; q < S.DW; q += nth) D.lastDom[q] = S.lastDom[q];
+    for (int q = tid; q < S.arity; q += nth) D.changed[q] = 0;
+    if (tid == 0) {
+        const int32_t cap = D.ctrl->trail_cap;
+        const int32_t live = S.ctrl->live_state;
+        int32_t* c = reinterpret_cast<int32_t*>(D.ctrl);
+        for (int q = 0; q < (int)(sizeof(Ctrl) / sizeof(int32_t)); ++q) c[q] = 0;
+        D.ctrl->cur_mark = -1;
+        D.ctrl->trail_cap = cap;
+        D.ctrl->live_state = live;
+    }
+}
+
+}  // namespace
+
+int max_coresident_model_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_model_kernel<16>, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per * sms;
+}
+
+cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s) {
+    ModelDev m = M;
+    void* args[] = {&m};
+    return cudaLaunchCooperativeKernel((const void*)ct_model_kernel<16>, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s) {
+    if (B.n <= 0) return cudaSuccess;
+    ct_restore_batch_kernel<<<dim3(8, B.n), 256, 0, s>>>(tabs, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clone_state(const TableDev* src, const TableDev* dst, int nsrc, int n, cudaStream_t s) {
+    for (int y0 = 0; y0 < n; y0 += 65535) {
+        const int ny = (n - y0) < 65535 ? (n - y0) : 65535;
+        ct_clone_state_kernel<<<dim3(4, ny), 256, 0, s>>>(src, dst, nsrc, y0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ctk
