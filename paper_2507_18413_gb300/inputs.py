@@ -286,3 +286,61 @@ def batching_csp(seed: int, nvars: int = 40, ntables: int = 60, arity: int = 4, 
         csp.tables.append(TableSpec(scope=scope, tuples=tup))
     return csp
 
+
+# --------------------------------------------------------------------------
+# learned branching order: initial weights, epoch orders, instances
+# --------------------------------------------------------------------------
+
+MLP_NF, MLP_H = 8, 64
+MLP_NW = MLP_H * MLP_NF + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def mlp_init_weights(seed: int) -> np.ndarray:
+    """Initial float32 weights of the 8 -> 64 -> 64 -> 1 network, flat in the order
+    W1[64][8], b1, W2[64][64], b2, W3[64], b3: weights uniform in +-sqrt(6 / fan_in)
+    (He et al., 2015, uniform form), biases zero."""
+    rng = Rng(seed)
+    w = np.zeros(MLP_NW, dtype=np.float64)
+    o = 0
+    for fan_in, n in ((MLP_NF, MLP_H * MLP_NF), (None, MLP_H), (MLP_H, MLP_H * MLP_H), (None, MLP_H),
+                      (MLP_H, MLP_H), (None, 1)):
+        if fan_in is not None:
+            a = math.sqrt(6.0 / fan_in)
+            w[o:o + n] = (rng.uniform(n) * 2.0 - 1.0) * a
+        o += n
+    return w.astype(np.float32)
+
+
+def epoch_orders(seed: int, n: int, epochs: int) -> np.ndarray:
+    """[epochs, n] int32: one seeded permutation of the n training samples per epoch."""
+    rng = Rng(seed)
+    return np.stack([np.argsort(rng.u64(n), kind="stable").astype(np.int32) for _ in range(epochs)])
+
+
+def learned_csp(seed: int, nvars=(30, 60), dom=(16, 64), ntables=(40, 120), arity=(3, 6),
+                tuples=(1e4, 5e5), log2_solutions: float = 4.0) -> CspSpec:
+    """A random CSP for the learned-order experiments: the number of variables,
+    each domain size, the number of tables and each arity uniform in the given
+    inclusive ranges; random scopes. Each table's tuple count is its share of a
+    target expected solution count of 2^log2_solutions (the product of the
+    table densities times the product of the domain sizes), clamped to the
+    `tuples` range and to half the tuple space; distinct uniform tuples."""
+    rng = Rng(seed)
+    nv = nvars[0] + rng.int(nvars[1] - nvars[0] + 1)
+    sizes = [dom[0] + rng.int(dom[1] - dom[0] + 1) for _ in range(nv)]
+    nt = ntables[0] + rng.int(ntables[1] - ntables[0] + 1)
+    scopes = [random_scope(rng, nv, arity[0] + rng.int(arity[1] - arity[0] + 1)) for _ in range(nt)]
+    space_bits = sum(math.log2(d) for d in sizes)
+    # log2 density per table so that space_bits + sum(log2 density) = log2_solutions
+    per_table = (log2_solutions - space_bits) / nt
+    csp = CspSpec(nvars=nv, dom_lo=[0] * nv, dom_size=sizes)
+    for k, sc in enumerate(scopes):
+        ds = [sizes[v] for v in sc]
+        tbits = sum(math.log2(d) for d in ds)
+        t = int(round(2.0 ** (tbits + per_table)))
+        t = max(int(tuples[0]), min(int(tuples[1]), t))
+        t = cap_distinct(ds, t)
+        tup = distinct_uniform_tuples(derive_seed(seed, k), [0] * len(sc), ds, t)
+        csp.tables.append(TableSpec(scope=sc, tuples=tup))
+    return csp
+
