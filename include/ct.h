@@ -336,6 +336,80 @@ int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit,
 
 int ct_model_destroy(ct_model* m);
 
+/* ------------------------------------------------------- learned order -- */
+/* Not in the paper, whose solver branches first-fail (Sec. 4): a small network
+ * scores the unfixed variables of a search node and the search branches on
+ * the best one (ties to the lowest index); values stay min-first, so every
+ * propagated domain is the same GAC fixpoint as with first-fail.
+ *
+ * Features of variable x (8 floats; all 0 when |D(x)| < 2). s = |D(x)|, d0 its
+ * initial size, deg(x) the tables holding x (degmax the largest, >= 1), smax
+ * the largest |D| among unfixed variables; for every table c holding x with
+ * live_c > 0 valid tuples (the set bits of its currTable),
+ * p_c(a) = popcount(supports[x,a] AND currTable_c) / live_c for a in D(x):
+ *   f0 = s/d0, f1 = log2(s)/8, f2 = deg/degmax, f3 = mean_c s*min_a p_c(a),
+ *   f4 = mean_c max_a p_c(a), f5 = mean_c (-sum_a p_c(a) log2 p_c(a))/log2(s),
+ *   f6 = mean_c log2(1 + live_c)/32, f7 = s/smax
+ * (f3-f6 are 0 when no table holding x has a valid tuple).
+ *
+ * Network: float32, 8 -> 64 -> 64 -> 1, ReLU after the first two layers;
+ * CT_MLP_WEIGHTS floats, flat: W1[64][8], b1[64], W2[64][64], b2[64], W3[64],
+ * b3 (rows are output units). Training minimises sum (out - y)^2 / (2B) per
+ * batch of B samples with Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected); its state persists across ct_mlp_train calls and is reset
+ * by ct_mlp_set_weights. */
+#define CT_MLP_FEATURES 8
+#define CT_MLP_HIDDEN 64
+#define CT_MLP_WEIGHTS 4801
+#define CT_MLP_MAX_BATCH 128
+
+typedef struct ct_mlp ct_mlp;
+
+/* ct_mlp_create: a network with the given weights (host, CT_MLP_WEIGHTS
+ * floats, copied) on `cuda_stream` (NULL: a library-created stream). */
+int ct_mlp_create(const float* weights_host, void* cuda_stream, ct_mlp** out);
+int ct_mlp_set_weights(ct_mlp* m, const float* weights_host);
+int ct_mlp_get_weights(ct_mlp* m, float* weights_host);
+/* ct_mlp_forward: scores of n feature rows; x_dev float[n][8] and scores_dev
+ * float[n] are device buffers of the caller; stream-ordered, no sync. */
+int ct_mlp_forward(ct_mlp* m, const float* x_dev, int64_t n, float* scores_dev);
+/* ct_mlp_grad: loss and gradient (host float[CT_MLP_WEIGHTS]) of one batch of
+ * 1 <= n <= CT_MLP_MAX_BATCH host rows; the weights do not change. */
+int ct_mlp_grad(ct_mlp* m, const float* x_host, const float* y_host, int n, float* loss_out, float* grad_host);
+/* ct_mlp_train: Adam over `epochs` passes; pass e visits the samples in the
+ * order orders_host[e*n .. e*n+n) (a permutation of 0..n-1 per epoch) in
+ * consecutive batches of `batch` <= CT_MLP_MAX_BATCH (the last may be
+ * shorter). epoch_loss_host (float[epochs] or NULL) receives each epoch's mean
+ * batch loss. One kernel launch; inputs are copied to the device. */
+int ct_mlp_train(ct_mlp* m, const float* x_host, const float* y_host, int64_t n, const int32_t* orders_host,
+                 int epochs, int batch, float lr, float* epoch_loss_host);
+int ct_mlp_destroy(ct_mlp* m);
+
+/* ct_model_features: features (host float[nvars][8]) of the model's current
+ * state (after ct_model_propagate; CT_ERR_STATE on a failed model). */
+int ct_model_features(ct_model* m, float* features_host);
+/* ct_model_set_policy: branch with the network's scores in ct_search_dfs and
+ * ct_search_batch (NULL: first-fail). The network must outlive its use. */
+int ct_model_set_policy(ct_model* m, ct_mlp* policy);
+/* ct_model_set_trace: ct_search_dfs records the branching variable of every
+ * branching node, in depth-first order, into decisions_host[0 .. capacity)
+ * and the number recorded into *count_host (NULL buffer: no trace). */
+int ct_model_set_trace(ct_model* m, int32_t* decisions_host, int64_t capacity, int64_t* count_host);
+/* ct_model_lookahead: labels (host float[nvars]) of the model's state after
+ * ct_model_propagate: for each unfixed variable x, the fixpoint of D with
+ * D(x) := {min D(x)} is computed on the slot copies of the batched search
+ * (`slots` at a time); label 1 if it fails, else (L - L')/L with
+ * L = sum_v log2|D_v| before and L' after. NaN for fixed variables. */
+int ct_model_lookahead(ct_model* m, int slots, float* labels_host);
+/* ct_search_collect: the first-fail search of ct_search_dfs (any policy set is
+ * ignored) for at most node_limit nodes; at every branching node the features
+ * and lookahead labels of its unfixed variables are appended as samples
+ * (features_host float[max_samples][8], labels_host float[max_samples]) until
+ * max_samples. *samples_out receives the count. The model is back at its
+ * state before the call. */
+int ct_search_collect(ct_model* m, int64_t node_limit, int slots, int64_t max_samples, float* features_host,
+                      float* labels_host, int64_t* samples_out);
+
 /* ---------------------------------------------------------------- misc -- */
 const char* ct_last_error(void);
 const char* ct_status_string(int status);

@@ -207,6 +207,72 @@ int set_var(ct_model* m, int v, const uint32_t* words) {
 }  // namespace
 
 int ct_model_popcount_var(const ct_model* m, int v) { return popcount_var(m, v); }
+
+namespace {
+
+// The model's feature view and an up-to-date device copy of every table.
+int ensure_features(ct_model* m) {
+    int st;
+    if (!m->batchReady && (st = batch_setup(m)) != CT_OK) return st;
+    const int n = (int)m->tables.size();
+    for (int t = 0; t < n; ++t) {
+        const int v = ct_table_version(m->tables[t]);
+        if (v != m->tabVersion[t]) {
+            CT_CUDA(cudaMemcpyAsync(m->d_tabs + t, &ct_table_dev(m->tables[t]), sizeof(TableDev), cudaMemcpyHostToDevice,
+                                    m->stream));
+            m->tabVersion[t] = v;
+        }
+    }
+    if (m->fview) return CT_OK;
+    std::vector<int> R(n), seg(n);
+    for (int t = 0; t < n; ++t) {
+        R[t] = ct_table_dev(m->tables[t]).R;
+        seg[t] = ct_table_dev(m->tables[t]).nseg;
+    }
+    FeatView* f = new (std::nothrow) FeatView();
+    if (!f) return CT_ERR_OOM;
+    st = ct_feat_view_build(f, 1, m->scopes, R, seg, m->off, m->nw, m->size, m->DWg);
+    if (st != CT_OK) {
+        ct_feat_view_free(f);
+        delete f;
+        return st;
+    }
+    m->fview = f;
+    return CT_OK;
+}
+
+}  // namespace
+
+int ct_model_pick_var(ct_model* m, bool usePolicy, int* x) {
+    *x = -1;
+    const float* sc = nullptr;
+    if (usePolicy && m->policy) {
+        bool any = false;
+        for (int v = 0; v < m->nvars && !any; ++v) any = popcount_var(m, v) > 1;
+        if (!any) return CT_OK;
+        int st = ensure_features(m);
+        if (st == CT_OK) st = ct_feat_compute(m->fview, m->d_tabs, m->d_dom, nullptr, m->stream);
+        if (st == CT_OK) st = ct_feat_scores(m->fview, m->policy, m->stream);
+        if (st != CT_OK) return st;
+        sc = m->fview->h_scores;
+    }
+    int best = 0;
+    float bestScore = 0.0f;
+    for (int v = 0; v < m->nvars; ++v) {
+        const int s = popcount_var(m, v);
+        if (s < 2) continue;
+        if (sc) {
+            if (*x < 0 || sc[v] > bestScore) {
+                *x = v;
+                bestScore = sc[v];
+            }
+        } else if (*x < 0 || s < best) {
+            *x = v;
+            best = s;
+        }
+    }
+    return CT_OK;
+}
 int ct_model_set_var(ct_model* m, int v, const uint32_t* words) { return set_var(m, v, words); }
 
 extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* dom_size, const ct_options* opt,
@@ -476,6 +542,10 @@ struct Dfs {
     ct_model* m;
     int64_t limit;
     bool countAll;
+    bool usePolicy = true;
+    ct_branch_hook hook = nullptr;
+    void* ctx = nullptr;
+    int64_t traceN = 0;
     ct_search_stats st{};
     int32_t* firstSol;
     bool haveFirst = false;
@@ -497,15 +567,11 @@ struct Dfs {
             st.fails += 1;
             return CT_OK;
         }
-        // First-fail: smallest domain among unfixed variables, ties to the lowest index.
-        int x = -1, best = 0;
-        for (int v = 0; v < m->nvars; ++v) {
-            const int s = popcount_var(m, v);
-            if (s > 1 && (x < 0 || s < best)) {
-                x = v;
-                best = s;
-            }
-        }
+        // First-fail (smallest domain among unfixed variables, ties to the lowest
+        // index) or the policy's best-scored unfixed variable.
+        int x = -1;
+        const int ps = ct_model_pick_var(m, usePolicy, &x);
+        if (ps != CT_OK) return ps;
         if (x < 0) {
             st.solutions += 1;
             if (!haveFirst) {
@@ -526,6 +592,12 @@ struct Dfs {
             }
             if (!countAll) stop = true;
             return CT_OK;
+        }
+        if (m->trace && traceN < m->traceCap) m->trace[traceN] = x;
+        ++traceN;
+        if (hook) {
+            const int hs = hook(ctx, m);
+            if (hs != CT_OK) return hs;
         }
         // Value: the minimum of dom(x).
         const int nwx = m->nw[x];
@@ -557,8 +629,8 @@ struct Dfs {
 
 }  // namespace
 
-extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_search_stats* out,
-                             int32_t* first_solution) {
+int ct_model_dfs(ct_model* m, int64_t node_limit, bool countAll, bool usePolicy, ct_search_stats* out,
+                 int32_t* first_solution, ct_branch_hook hook, void* ctx) {
     if (!m || !out) {
         ct_set_error("ct_search_dfs: null argument");
         return CT_ERR_ARG;
@@ -572,7 +644,10 @@ extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_
     Dfs d;
     d.m = m;
     d.limit = node_limit;
-    d.countAll = count_all != 0;
+    d.countAll = countAll;
+    d.usePolicy = usePolicy;
+    d.hook = hook;
+    d.ctx = ctx;
     d.firstSol = first_solution;
     int L0 = 0;
     int st = ct_model_save(m, &L0);
@@ -586,6 +661,50 @@ extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_
     d.st.propagations = m->propagations - p0;
     d.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = d.st;
+    if (m->trace && m->traceCount && !hook) *m->traceCount = std::min(d.traceN, m->traceCap);
+    return CT_OK;
+}
+
+extern "C" int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all, ct_search_stats* out,
+                             int32_t* first_solution) {
+    return ct_model_dfs(m, node_limit, count_all != 0, true, out, first_solution, nullptr, nullptr);
+}
+
+extern "C" int ct_model_features(ct_model* m, float* features_host) {
+    if (!m || !features_host) {
+        ct_set_error("ct_model_features: null argument");
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_model_features: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    int st = ensure_features(m);
+    if (st == CT_OK) st = ct_feat_compute(m->fview, m->d_tabs, m->d_dom, nullptr, m->stream);
+    if (st != CT_OK) return st;
+    CT_CUDA(cudaMemcpyAsync(features_host, m->fview->feat, (size_t)m->nvars * kNF * sizeof(float),
+                            cudaMemcpyDeviceToHost, m->stream));
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    return CT_OK;
+}
+
+extern "C" int ct_model_set_policy(ct_model* m, ct_mlp* policy) {
+    if (!m) {
+        ct_set_error("ct_model_set_policy: null handle");
+        return CT_ERR_ARG;
+    }
+    m->policy = policy;
+    return CT_OK;
+}
+
+extern "C" int ct_model_set_trace(ct_model* m, int32_t* decisions_host, int64_t capacity, int64_t* count_host) {
+    if (!m || capacity < 0) {
+        ct_set_error("ct_model_set_trace: bad argument");
+        return CT_ERR_ARG;
+    }
+    m->trace = decisions_host;
+    m->traceCap = decisions_host ? capacity : 0;
+    m->traceCount = count_host;
     return CT_OK;
 }
 
@@ -593,6 +712,10 @@ extern "C" int ct_model_destroy(ct_model* m) {
     if (!m) return CT_OK;
     if (m->stream) cudaStreamSynchronize(m->stream);
     ct_batch_free(m->bsearch);  // the clones share the tables' supports: freed first
+    if (m->fview) {
+        ct_feat_view_free(m->fview);
+        delete m->fview;
+    }
     for (ct_table* t : m->tables) ct_destroy(t);
     for (int32_t* p : m->d_tabOff) cudaFree(p);
     if (m->d_dom) cudaFree(m->d_dom);

@@ -3,7 +3,7 @@
 #pragma once
 #include <vector>
 
-#include "ct_internal.cuh"
+#include "ct_learn.cuh"
 
 struct ct_batch;  // the slots of a batched search (ct_search.cu)
 
@@ -44,6 +44,12 @@ struct ct_model {
     std::vector<void*> allocs;
     int grid = 1;
     ct_batch* bsearch = nullptr;  // built by the first batched search, kept for the next ones
+    // learned branching order
+    ct_mlp* policy = nullptr;          // NULL: first-fail
+    ctk::FeatView* fview = nullptr;    // feature view of the model (one node), built on first use
+    int32_t* trace = nullptr;          // branching variables of ct_search_dfs (host)
+    int64_t traceCap = 0;
+    int64_t* traceCount = nullptr;
 };
 
 // Internal helpers of ct_model.cu used by the batched search.
@@ -52,3 +58,12 @@ int ct_model_popcount_var(const ct_model* m, int v);
 int ct_model_set_var(ct_model* m, int v, const uint32_t* words);
 // Free the batched-search slots of m (ct_search.cu).
 void ct_batch_free(ct_batch* b);
+// The branching variable of the model's current (propagated) state: the
+// policy's best-scored unfixed variable, or first-fail without a policy (or
+// when usePolicy is false); -1 when every variable is fixed.
+int ct_model_pick_var(ct_model* m, bool usePolicy, int* x);
+// Called at every branching node of ct_model_dfs, before the branches.
+typedef int (*ct_branch_hook)(void* ctx, ct_model* m);
+// The depth-first search of ct_search_dfs with an optional hook.
+int ct_model_dfs(ct_model* m, int64_t node_limit, bool countAll, bool usePolicy, ct_search_stats* out,
+                 int32_t* first_solution, ct_branch_hook hook, void* ctx);

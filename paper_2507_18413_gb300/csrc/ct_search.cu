@@ -17,6 +17,7 @@
 // node, or the untried right branch nearest the root of another slot.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -102,6 +103,9 @@ struct ct_batch {
     int32_t* h_status = nullptr;  // mapped: header, (trail_top, live) per table, domains, node statuses
     ModelDev md{};
     uint64_t* d_phase = nullptr;  // [kModelPhases] with ct_options.profile
+    FeatView* fview = nullptr;    // features of the slots (built when a policy is first used)
+    uint8_t* d_active = nullptr;  // [B] slots whose features are wanted
+    std::vector<uint8_t> h_active;
     int grid = 1;
     std::vector<void*> allocs;
     bool broken = false;
@@ -120,6 +124,10 @@ void ct_batch_free(ct_batch* b) {
     for (void* p : b->allocs) cudaFree(p);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->fview) {
+        ct_feat_view_free(b->fview);
+        delete b->fview;
+    }
     cudaGetLastError();
     delete b;
 }
@@ -254,6 +262,29 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     return CT_OK;
 }
 
+// The feature view of the B slots (for a policy).
+int ensure_slot_features(ct_model* m, ct_batch* b) {
+    if (b->fview) return CT_OK;
+    const int T = b->T;
+    std::vector<int> R(T), seg(T);
+    for (int k = 0; k < T; ++k) {
+        R[k] = ct_table_dev(m->tables[k]).R;
+        seg[k] = ct_table_dev(m->tables[k]).nseg;
+    }
+    FeatView* f = new (std::nothrow) FeatView();
+    if (!f) return CT_ERR_OOM;
+    int st = ct_feat_view_build(f, b->B, m->scopes, R, seg, m->off, m->nw, m->size, m->DWg);
+    if (st == CT_OK) st = b_alloc(b, &b->d_active, b->B);
+    if (st != CT_OK) {
+        ct_feat_view_free(f);
+        delete f;
+        return st;
+    }
+    b->fview = f;
+    b->h_active.assign(b->B, 0);
+    return CT_OK;
+}
+
 // Every copy takes the current state of the model's tables (one launch).
 int sync_copies(ct_model* m, ct_batch* b) {
     std::vector<TableDev> td(b->T);
@@ -287,6 +318,12 @@ struct Search {
     std::vector<char> dirty;       // [n]
     std::vector<int> restPos;      // [n] index in this step's restore list, -1 none
     int nrest = 0;
+    bool usePolicy = false;        // branch with the model's policy (scores of the slots per step)
+    const float* scores = nullptr; // this step's scores of the slots' variables
+    // lookahead probes instead of a search: per slot, the label of its probe
+    bool probeMode = false;
+    double probeL = 0.0;
+    std::vector<float> probeLabel;
     std::chrono::steady_clock::time_point t0;
 
     uint32_t* slotDom(int s) { return b->domHost() + (size_t)s * m->DWg; }
@@ -346,7 +383,8 @@ struct Search {
             return CT_OK;
         }
         if (depth == 0 && (r = ensure_copies()) != CT_OK) return r;
-        const int x = first_fail(m, m->h_dom.data());
+        int x = -1;
+        if ((r = ct_model_pick_var(m, usePolicy, &x)) != CT_OK) return r;
         if (x < 0) {
             record_solution(path, m->h_dom.data());
             if (!countAll) splitStop = true;
@@ -536,7 +574,15 @@ struct Search {
             st.fails += 1;
             return backtrack(s);
         }
-        const int x = first_fail(m, slotDom(s));
+        int x = -1;
+        if (scores) {
+            const float* sc = scores + (size_t)s * m->nvars;
+            const uint32_t* dom = slotDom(s);
+            for (int v = 0; v < m->nvars; ++v)
+                if (popcount_words(dom + m->off[v], m->nw[v]) > 1 && (x < 0 || sc[v] > sc[x])) x = v;
+        } else {
+            x = first_fail(m, slotDom(s));
+        }
         if (x < 0) {
             record_solution(S.path, slotDom(s));
             return backtrack(s);
@@ -552,7 +598,7 @@ struct Search {
         for (int j = 0; j < n; ++j)
             if (dirty[j]) work[nwork++] = j;
         info.steps += 1;
-        if (nwork == 0 && nrest == 0) {  // nothing to do on the device: the nodes are their own fixpoints
+        if (nwork == 0 && nrest == 0 && !usePolicy && !probeMode) {  // the nodes are their own fixpoints
             std::vector<int> ps;
             for (int s = 0; s < B; ++s)
                 if (slots[s].pending) ps.push_back(s);
@@ -620,9 +666,34 @@ struct Search {
         const uint32_t* outDom = reinterpret_cast<const uint32_t*>(const_cast<const int32_t*>(b->h_status) + kModelHdr + 2 * n);
         const int32_t* outNode = const_cast<const int32_t*>(b->h_status) + kModelHdr + 2 * n + (size_t)B * m->DWg;
         (void)T;
+        for (int s = 0; s < B; ++s)
+            if (slots[s].pending)
+                std::memcpy(slotDom(s), outDom + (size_t)s * m->DWg, (size_t)m->DWg * sizeof(uint32_t));
+        scores = nullptr;
+        if (usePolicy && !probeMode) {
+            bool any = false;
+            for (int s = 0; s < B; ++s) {
+                b->h_active[s] = slots[s].pending && outNode[s] == CT_OK;
+                any |= b->h_active[s] != 0;
+            }
+            if (any) {
+                CT_CUDA(cudaMemcpyAsync(b->d_active, b->h_active.data(), (size_t)B, cudaMemcpyHostToDevice, b->stream));
+                if ((rc = ct_feat_compute(b->fview, b->d_tabs, b->md.dom, b->d_active, b->stream)) != CT_OK) return rc;
+                if ((rc = ct_feat_scores(b->fview, m->policy, b->stream)) != CT_OK) return rc;
+                scores = b->fview->h_scores;
+            }
+        }
         for (int s = 0; s < B; ++s) {
             if (!slots[s].pending) continue;
-            std::memcpy(slotDom(s), outDom + (size_t)s * m->DWg, (size_t)m->DWg * sizeof(uint32_t));
+            if (probeMode) {
+                slots[s].pending = false;
+                double L2 = 0.0;
+                const uint32_t* dom = slotDom(s);
+                for (int v = 0; v < m->nvars; ++v) L2 += std::log2((double)popcount_words(dom + m->off[v], m->nw[v]));
+                probeLabel[s] = outNode[s] != CT_OK ? 1.0f : (float)((probeL - L2) / probeL);
+                if ((rc = cancel(s)) != CT_OK) return rc;
+                continue;
+            }
             if ((rc = advance(s, outNode[s])) != CT_OK) return rc;
         }
         return CT_OK;
@@ -700,6 +771,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     S.splitDepth = split_depth;
     S.limit = node_limit;
     S.countAll = count_all != 0;
+    S.usePolicy = m->policy != nullptr;
     const int64_t p0 = m->propagations;
     int L0 = 0;
     int rc = ct_model_save(m, &L0);
@@ -709,6 +781,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     if (rc == CT_OK) rc = S.split(0, path);
     const int rr = ct_model_restore(m, L0);
     if (rc == CT_OK) rc = rr;
+    if (rc == CT_OK && !S.open.empty() && !S.stopIssue && S.usePolicy) rc = ensure_slot_features(m, S.b);
     if (rc == CT_OK && !S.open.empty() && !S.stopIssue) rc = S.run_slots();
     if (rc != CT_OK) {
         if (S.b) S.b->broken = true;
@@ -727,3 +800,111 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     }
     return CT_OK;
 }
+
+extern "C" int ct_model_lookahead(ct_model* m, int slots, float* labels_host) {
+    if (!m || !labels_host || slots < 1 || slots > 4096 || (int64_t)slots * (int64_t)m->tables.size() > kModelMaxTables) {
+        ct_set_error("ct_model_lookahead: bad argument");
+        return CT_ERR_ARG;
+    }
+    if (m->failed) {
+        ct_set_error("ct_model_lookahead: the model failed; restore a level first");
+        return CT_ERR_STATE;
+    }
+    int rc = ct_model_propagate(m);
+    if (rc != CT_OK) return rc;
+    std::vector<int> cand;
+    double L = 0.0;
+    for (int v = 0; v < m->nvars; ++v) {
+        const int sz = ct_model_popcount_var(m, v);
+        labels_host[v] = std::nanf("");
+        L += std::log2((double)sz);
+        if (sz > 1) cand.push_back(v);
+    }
+    if (cand.empty()) return CT_OK;
+    if (m->tables.empty()) {
+        // no constraint: fixing x removes log2|D(x)| and nothing else
+        for (int v : cand) labels_host[v] = (float)(std::log2((double)ct_model_popcount_var(m, v)) / L);
+        return CT_OK;
+    }
+    Search S;
+    S.m = m;
+    S.b = m->bsearch;
+    S.B = slots;
+    S.probeMode = true;
+    S.probeL = L;
+    if ((rc = S.ensure_copies()) != CT_OK) return rc;
+    const int n = S.b->n;
+    S.slots.assign(slots, Slot());
+    S.dirty.assign(n, 0);
+    S.restPos.assign(n, -1);
+    S.probeLabel.assign(slots, 0.0f);
+    for (int s = 0; s < slots; ++s) std::memcpy(S.slotDom(s), S.rootDom.data(), (size_t)m->DWg * sizeof(uint32_t));
+    std::vector<uint32_t> probe;
+    for (size_t c0 = 0; c0 < cand.size(); c0 += (size_t)slots) {
+        const int cnt = (int)std::min<size_t>((size_t)slots, cand.size() - c0);
+        for (int s = 0; s < cnt; ++s) {
+            const int x = cand[c0 + s];
+            probe = S.rootDom;
+            const int a = min_value(m, probe.data(), x);
+            for (int q = 0; q < m->nw[x]; ++q) probe[m->off[x] + q] = 0u;
+            probe[m->off[x] + (a >> 5)] = 1u << (a & 31);
+            Slot& Z = S.slots[s];
+            if ((rc = S.save_slot(s)) != CT_OK) return rc;
+            std::memcpy(S.slotDom(s), probe.data(), (size_t)m->DWg * sizeof(uint32_t));
+            for (int k = 0; k < S.b->T; ++k) S.dirty[(size_t)s * S.b->T + k] = 1;
+            Z.active = true;
+            Z.pending = true;
+        }
+        if ((rc = S.step()) != CT_OK) return rc;
+        for (int s = 0; s < cnt; ++s) labels_host[cand[c0 + s]] = S.probeLabel[s];
+    }
+    return CT_OK;
+}
+
+namespace {
+
+struct Collect {
+    int slots;
+    int64_t max;
+    float* X;
+    float* y;
+    int64_t n = 0;
+    std::vector<float> feat, lab;
+};
+
+int collect_hook(void* ctx, ct_model* m) {
+    Collect* c = static_cast<Collect*>(ctx);
+    if (c->n >= c->max) return CT_OK;
+    c->feat.resize((size_t)m->nvars * kNF);
+    c->lab.resize((size_t)m->nvars);
+    int rc = ct_model_features(m, c->feat.data());
+    if (rc == CT_OK) rc = ct_model_lookahead(m, c->slots, c->lab.data());
+    if (rc != CT_OK) return rc;
+    for (int v = 0; v < m->nvars && c->n < c->max; ++v) {
+        if (ct_model_popcount_var(m, v) < 2) continue;
+        std::memcpy(c->X + (size_t)c->n * kNF, c->feat.data() + (size_t)v * kNF, kNF * sizeof(float));
+        c->y[c->n] = c->lab[v];
+        ++c->n;
+    }
+    return CT_OK;
+}
+
+}  // namespace
+
+extern "C" int ct_search_collect(ct_model* m, int64_t node_limit, int slots, int64_t max_samples, float* features_host,
+                                 float* labels_host, int64_t* samples_out) {
+    if (!m || !features_host || !labels_host || !samples_out || max_samples < 0 || slots < 1 || slots > 4096) {
+        ct_set_error("ct_search_collect: bad argument");
+        return CT_ERR_ARG;
+    }
+    Collect c;
+    c.slots = slots;
+    c.max = max_samples;
+    c.X = features_host;
+    c.y = labels_host;
+    ct_search_stats st{};
+    const int rc = ct_model_dfs(m, node_limit, true, false, &st, nullptr, collect_hook, &c);
+    *samples_out = c.n;
+    return rc;
+}
+

@@ -90,6 +90,7 @@ def _as_dict(s):
 
 _P = ctypes.c_void_p
 _I32P = ctypes.POINTER(ctypes.c_int32)
+_F32P = ctypes.POINTER(ctypes.c_float)
 _U32P = ctypes.POINTER(ctypes.c_uint32)
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
@@ -121,6 +122,20 @@ _SIGS = {
     "ct_search_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
+    "ct_mlp_create": (ctypes.c_int, [_F32P, _P, ctypes.POINTER(_P)]),
+    "ct_mlp_set_weights": (ctypes.c_int, [_P, _F32P]),
+    "ct_mlp_get_weights": (ctypes.c_int, [_P, _F32P]),
+    "ct_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "ct_mlp_grad": (ctypes.c_int, [_P, _F32P, _F32P, ctypes.c_int, _F32P, _F32P]),
+    "ct_mlp_train": (ctypes.c_int, [_P, _F32P, _F32P, ctypes.c_int64, _I32P, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_float, _F32P]),
+    "ct_mlp_destroy": (ctypes.c_int, [_P]),
+    "ct_model_features": (ctypes.c_int, [_P, _F32P]),
+    "ct_model_set_policy": (ctypes.c_int, [_P, _P]),
+    "ct_model_set_trace": (ctypes.c_int, [_P, _I32P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "ct_model_lookahead": (ctypes.c_int, [_P, ctypes.c_int, _F32P]),
+    "ct_search_collect": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, _F32P, _F32P,
+                                         ctypes.POINTER(ctypes.c_int64)]),
     "ct_last_error": (ctypes.c_char_p, []),
     "ct_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ct_version": (ctypes.c_int, []),
@@ -413,6 +428,115 @@ def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True):
     d = _as_dict(s)
     d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
     return st, d, _as_dict(info)
+
+
+# --------------------------------------------------------------------------
+# learned branching order
+# --------------------------------------------------------------------------
+MLP_FEATURES, MLP_HIDDEN, MLP_WEIGHTS, MLP_MAX_BATCH = 8, 64, 4801, 128
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} floats, got {a.size}")
+    return a
+
+
+def ct_mlp_create(weights, stream=None):
+    w = _f32(weights, MLP_WEIGHTS)
+    h = _P()
+    st = load().ct_mlp_create(w.ctypes.data_as(_F32P), _stream_ptr(stream), ctypes.byref(h))
+    return st, h.value
+
+
+def ct_mlp_set_weights(m, weights):
+    w = _f32(weights, MLP_WEIGHTS)
+    return load().ct_mlp_set_weights(m, w.ctypes.data_as(_F32P))
+
+
+def ct_mlp_get_weights(m):
+    w = np.zeros(MLP_WEIGHTS, dtype=np.float32)
+    st = load().ct_mlp_get_weights(m, w.ctypes.data_as(_F32P))
+    return st, w
+
+
+def ct_mlp_forward(m, x_dev, n, scores_dev):
+    """x_dev / scores_dev: device pointers (int) or tensors with data_ptr()."""
+    xp = x_dev.data_ptr() if hasattr(x_dev, "data_ptr") else int(x_dev)
+    sp = scores_dev.data_ptr() if hasattr(scores_dev, "data_ptr") else int(scores_dev)
+    return load().ct_mlp_forward(m, xp, int(n), sp)
+
+
+def ct_mlp_grad(m, X, y):
+    X = _f32(X)
+    y = _f32(y)
+    n = y.size
+    loss = ctypes.c_float()
+    g = np.zeros(MLP_WEIGHTS, dtype=np.float32)
+    st = load().ct_mlp_grad(m, X.ctypes.data_as(_F32P), y.ctypes.data_as(_F32P), int(n), ctypes.byref(loss),
+                            g.ctypes.data_as(_F32P))
+    return st, float(loss.value), g
+
+
+def ct_mlp_train(m, X, y, orders, batch, lr):
+    """orders: int32 [epochs, n] permutations. Returns (status, epoch losses)."""
+    X = _f32(X)
+    y = _f32(y)
+    orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int32))
+    epochs = orders.shape[0]
+    losses = np.zeros(epochs, dtype=np.float32)
+    st = load().ct_mlp_train(m, X.ctypes.data_as(_F32P), y.ctypes.data_as(_F32P), int(y.size),
+                             orders.ctypes.data_as(_I32P), int(epochs), int(batch), float(lr),
+                             losses.ctypes.data_as(_F32P))
+    return st, losses
+
+
+def ct_mlp_destroy(m):
+    return load().ct_mlp_destroy(m)
+
+
+def ct_model_features(m, nvars):
+    F = np.zeros((nvars, MLP_FEATURES), dtype=np.float32)
+    st = load().ct_model_features(m, F.ctypes.data_as(_F32P))
+    return st, F
+
+
+def ct_model_set_policy(m, mlp):
+    return load().ct_model_set_policy(m, mlp)
+
+
+class Trace:
+    """Host buffers of ct_model_set_trace (keep the object alive while searching)."""
+
+    def __init__(self, capacity):
+        self.buf = np.zeros(int(capacity), dtype=np.int32)
+        self.count = ctypes.c_int64(0)
+
+    def decisions(self):
+        return self.buf[: int(self.count.value)].tolist()
+
+
+def ct_model_set_trace(m, trace):
+    if trace is None:
+        return load().ct_model_set_trace(m, None, 0, None)
+    return load().ct_model_set_trace(m, trace.buf.ctypes.data_as(_I32P), int(trace.buf.size),
+                                     ctypes.byref(trace.count))
+
+
+def ct_model_lookahead(m, nvars, slots):
+    lab = np.zeros(nvars, dtype=np.float32)
+    st = load().ct_model_lookahead(m, int(slots), lab.ctypes.data_as(_F32P))
+    return st, lab
+
+
+def ct_search_collect(m, node_limit, slots, max_samples):
+    X = np.zeros((int(max_samples), MLP_FEATURES), dtype=np.float32)
+    y = np.zeros(int(max_samples), dtype=np.float32)
+    n = ctypes.c_int64(0)
+    st = load().ct_search_collect(m, int(node_limit), int(slots), int(max_samples), X.ctypes.data_as(_F32P),
+                                  y.ctypes.data_as(_F32P), ctypes.byref(n))
+    return st, X[: n.value], y[: n.value]
 
 
 def ct_model_destroy(m):
