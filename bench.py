@@ -62,9 +62,14 @@ def parse():
     p.add_argument("--seed", type=int, default=20250724)
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--case", default="stream", choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search"],
+    p.add_argument("--case", default="stream",
+                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned"],
                    help="bulk*: only the one-call bandwidth case (for profiling); "
-                        "search: only the plain vs batched search figures")
+                        "search: only the plain vs batched search figures; "
+                        "learned: the learned-order experiment at full size")
+    p.add_argument("--learned-eval", type=int, default=200, help="held-out instances of --case learned")
+    p.add_argument("--learned-full", type=int, default=10,
+                   help="instances at config-4 size (30-60 vars, 40-120 tables) in --case learned")
     return p.parse_args()
 
 
@@ -531,6 +536,43 @@ def search_extras(C):
     return out
 
 
+LEARNED_SMALL = dict(nvars=(20, 30), dom=(8, 16), ntables=(30, 50), arity=(3, 4), tuples=(1e3, 2e4))
+
+
+def learned_extras(C, n_train=40, n_eval=20, node_limit=5000, train_nodes=300, max_samples=100_000, epochs=20,
+                   full_eval=0):
+    """Train the branching network on first-fail traces of seeded instances and
+    compare first-fail and the network, plain and batched, on held-out seeds:
+    time and nodes to the first solution or to a proof of infeasibility."""
+    from paper_2507_18413_gb300 import learn as LN
+    t0 = time.perf_counter()
+    train_specs = [G.learned_csp(s, **LEARNED_SMALL) for s in range(n_train)]
+    eval_specs = [G.learned_csp(100_000 + s, **LEARNED_SMALL) for s in range(n_eval)]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    X, y = LN.collect(train_specs, node_limit=train_nodes, slots=64, max_samples=max_samples)
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, losses = LN.train(X, y, epochs=epochs)
+    train_s = time.perf_counter() - t0
+    try:
+        rows = LN.compare(eval_specs, net, node_limit=node_limit, batched=(64, 6))
+        out = {"instances": "learned_csp seeds, 20-30 vars, d 8-16, 30-50 tables of arity 3-4, 1e3-2e4 "
+                            "tuples, expected 2^4 solutions (config 4 scaled to instances first-fail "
+                            "finishes within the limit)",
+               "train_instances": n_train, "eval_instances": n_eval, "node_limit": node_limit,
+               "samples": int(len(y)), "collect_s": round(collect_s, 2), "train_s": round(train_s, 3),
+               "epochs": epochs, "loss_first_last": [round(float(losses[0]), 5), round(float(losses[-1]), 5)],
+               "generate_s": round(gen_s, 1), "summary": LN.summarize(rows)}
+        if full_eval:
+            full = [G.learned_csp(200_000 + s) for s in range(full_eval)]
+            frows = LN.compare(full, net, node_limit=node_limit, batched=(64, 6))
+            out["config4_full_scale"] = {"instances": full_eval, "summary": LN.summarize(frows)}
+    finally:
+        C.ct_mlp_destroy(net)
+    return out
+
+
 def extras(args, C, torch, stream):
     out = {}
     try:
@@ -542,6 +584,7 @@ def extras(args, C, torch, stream):
         out["dfs_plain_first_fail"] = _dfs_rate(C)
         out["dfs_plain_first_fail_host_queue"] = _dfs_rate(C, host_fixpoint=1)
         out["search_batched_vs_plain"] = search_extras(C)
+        out["learned_order"] = learned_extras(C)
     except Exception as e:  # context figures must not hide the main line
         out["error"] = repr(e)
     return out
@@ -649,6 +692,9 @@ def main():
         stream = torch.cuda.current_stream()
         if args.case == "search":
             print(json.dumps(search_extras(C)))
+        elif args.case == "learned":
+            print(json.dumps(learned_extras(C, n_train=200, n_eval=args.learned_eval, node_limit=20_000,
+                                            full_eval=args.learned_full)))
         elif args.case == "bulk1e6":
             print(json.dumps(_bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)))
         elif args.case == "bulk4e6":

@@ -301,11 +301,14 @@ int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all,
  *   count_all    1: count every solution; 0: stop once the first solution in
  *                depth-first order is known (nodes after it are not started,
  *                nodes before it are finished), so first_solution equals
- *                ct_search_dfs's while nodes and fails can differ
+ *                ct_search_dfs's while nodes and fails can differ; 2: stop at
+ *                the first solution any slot finds (no new node is started;
+ *                the nodes of that launch still finish)
  *   out          host, receives the counters as in ct_search_dfs
  *   first_solution  host int32[nvars] or NULL: the first solution in
  *                depth-first order among those found (with count_all = 1, or
  *                with count_all = 0 and no node limit, ct_search_dfs's)
+ * Returns CT_ERR_ARG for count_all outside 0..2.
  *   info         host or NULL: counters of the batching itself
  * Returns CT_OK, CT_ERR_ARG (bad sizes), CT_ERR_STATE (a failed model),
  * CT_ERR_OOM, CT_ERR_CUDA or CT_ERR_TIMEOUT. The model's domains and tables

@@ -233,12 +233,30 @@ void ct_table_batch_done(ct_table* ct, int trailTop, int live);
 // Host bookkeeping of a restore; returns 1 (and fills d) when a device undo is needed.
 int ct_table_restore_prepare(ct_table* ct, int level, ctk::RestoreDesc* d);
 int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);
-ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status);
+// Device memory handed out in 256-byte aligned pieces of one allocation (the
+// batched search's table clones); its owner frees it as a whole.
+struct DeviceArena {
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    void* take(size_t bytes) {
+        const size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+// Arena bytes one clone of src takes (dynamic buffers, 8 levels and a trail of
+// 2 * W4 + 64 entries, each piece rounded up to 256 bytes).
+size_t ct_table_clone_bytes(const ct_table* src);
+// A clone of src (see ct_table.cu); its dynamic buffers come from `arena` when
+// given (else from cudaMalloc), its Ctrl is `ctrl` when given.
+ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* arena, ctk::Ctrl* ctrl, int* status);
 void ct_table_free(ct_table* ct);
 int ct_table_save_host(ct_table* ct);
 int ct_table_depth(const ct_table* ct);
 void ct_table_adopt_state(ct_table* dst, const ct_table* src);
 int ct_table_live(const ct_table* ct);
+int ct_table_trail_cap(const ct_table* ct);
 int ct_table_dom_words(const ct_table* ct);
 const int32_t* ct_table_var_ld(const ct_table* ct);
 int ct_table_changed_words(const ct_table* ct);

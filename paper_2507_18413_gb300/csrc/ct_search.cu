@@ -103,6 +103,7 @@ struct ct_batch {
     int32_t* h_status = nullptr;  // mapped: header, (trail_top, live) per table, domains, node statuses
     ModelDev md{};
     uint64_t* d_phase = nullptr;  // [kModelPhases] with ct_options.profile
+    DeviceArena arena;            // the clones' dynamic buffers (in `allocs`)
     FeatView* fview = nullptr;    // features of the slots (built when a policy is first used)
     uint8_t* d_active = nullptr;  // [B] slots whose features are wanted
     std::vector<uint8_t> h_active;
@@ -160,14 +161,29 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     b->n = n;
     b->stream = m->stream;
     int st = CT_OK;
+    // one allocation for every clone's dynamic buffers, first levels and trail,
+    // one array for their Ctrl blocks
+    size_t perSlot = 0;
+    for (int k = 0; k < T; ++k) perSlot += ct_table_clone_bytes(m->tables[k]);
+    if ((st = b_alloc(b, &b->arena.base, perSlot * (size_t)B)) != CT_OK) return st;
+    b->arena.size = perSlot * (size_t)B;
+    Ctrl* dCtrls = nullptr;
+    if ((st = b_alloc(b, &dCtrls, (size_t)n)) != CT_OK) return st;
     b->tabs.reserve(n);
+    std::vector<Ctrl> hc(n);
     for (int s = 0; s < B; ++s) {
         for (int k = 0; k < T; ++k) {
-            ct_table* c = ct_table_clone(m->tables[k], m->stream, &st);
+            const int j = s * T + k;
+            ct_table* c = ct_table_clone(m->tables[k], m->stream, &b->arena, dCtrls + j, &st);
             if (!c) return st;
             b->tabs.push_back(c);
+            hc[j] = Ctrl{};
+            hc[j].cur_mark = -1;
+            hc[j].trail_cap = ct_table_trail_cap(c);
         }
     }
+    CT_CUDA(cudaMemcpyAsync(dCtrls, hc.data(), (size_t)n * sizeof(Ctrl), cudaMemcpyHostToDevice, m->stream));
+    CT_CUDA(cudaStreamSynchronize(m->stream));
     const int DWs = B * m->DWg;
     std::vector<int32_t> base(n + 1, 0), off, var;
     for (int s = 0; s < B; ++s) {
@@ -302,6 +318,7 @@ struct Search {
     int B = 0, splitDepth = 0;
     int64_t limit = 0;
     bool countAll = true;
+    bool anyStop = false;  // stop at the first solution any slot finds
     ct_search_stats st{};
     ct_batch_info info{};
     bool hitLimit = false;
@@ -465,6 +482,7 @@ struct Search {
 
     // The slot's current node goes into the next launch.
     int issue(int s, int depth) {
+        if (anyStop && haveBest) return cancel(s);
         if (limit > 0 && st.nodes >= limit) {
             hitLimit = stopIssue = true;
             return cancel(s);
@@ -493,6 +511,7 @@ struct Search {
     // An idle slot takes the next open node, else the untried right branch
     // nearest the root among the other slots' subtrees.
     int assign(int s) {
+        if (anyStop && haveBest) return CT_OK;
         while (!stopIssue && nextOpen < open.size()) {
             const OpenNode& o = open[nextOpen++];
             if (!countAll && haveBest && after(o.path, bestPath)) continue;
@@ -744,7 +763,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
         ct_set_error("ct_search_batch: null argument");
         return CT_ERR_ARG;
     }
-    if (slots < 1 || slots > 4096 || split_depth < 0 || split_depth > 64 ||
+    if (slots < 1 || slots > 4096 || split_depth < 0 || split_depth > 64 || count_all < 0 || count_all > 2 ||
         (int64_t)slots * (int64_t)m->tables.size() > kModelMaxTables) {
         ct_set_error("ct_search_batch: slots %d or split depth %d out of range", slots, split_depth);
         return CT_ERR_ARG;
@@ -756,7 +775,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     if (info) std::memset(info, 0, sizeof(*info));
     if (m->tables.empty() || m->staticInfeasible) {
         // nothing to propagate on the device: the plain search is the same search
-        const int rc = ct_search_dfs(m, node_limit, count_all, out, first_solution);
+        const int rc = ct_search_dfs(m, node_limit, count_all == 1, out, first_solution);
         if (info) {
             info->slots = slots;
             info->split_nodes = rc == CT_OK ? out->nodes : 0;
@@ -770,7 +789,8 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     S.B = slots;
     S.splitDepth = split_depth;
     S.limit = node_limit;
-    S.countAll = count_all != 0;
+    S.countAll = count_all == 1;
+    S.anyStop = count_all == 2;
     S.usePolicy = m->policy != nullptr;
     const int64_t p0 = m->propagations;
     int L0 = 0;
@@ -781,8 +801,9 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     if (rc == CT_OK) rc = S.split(0, path);
     const int rr = ct_model_restore(m, L0);
     if (rc == CT_OK) rc = rr;
-    if (rc == CT_OK && !S.open.empty() && !S.stopIssue && S.usePolicy) rc = ensure_slot_features(m, S.b);
-    if (rc == CT_OK && !S.open.empty() && !S.stopIssue) rc = S.run_slots();
+    const bool runSlots = !S.open.empty() && !S.stopIssue && !(S.anyStop && S.haveBest);
+    if (rc == CT_OK && runSlots && S.usePolicy) rc = ensure_slot_features(m, S.b);
+    if (rc == CT_OK && runSlots) rc = S.run_slots();
     if (rc != CT_OK) {
         if (S.b) S.b->broken = true;
         return rc;

@@ -83,6 +83,8 @@ struct ct_table {
     int64_t deviceBytes = 0;
     uint32_t* d_domScratch = nullptr;
     std::vector<void*> allocs;
+    bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
+    bool levelsInArena = false;
 };
 
 namespace {
@@ -143,8 +145,9 @@ int ensure_trail(ct_table* ct, int64_t need) {
     int32_t capi = (int32_t)cap;
     CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->trail_cap, &capi, sizeof(int32_t), cudaMemcpyHostToDevice, ct->stream));
     CT_CUDA(cudaStreamSynchronize(ct->stream));
-    if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
-    if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
+    if (ct->dev.trailKey && !ct->trailInArena) cudaFree(ct->dev.trailKey);
+    if (ct->dev.trailOld && !ct->trailInArena) cudaFree(ct->dev.trailOld);
+    ct->trailInArena = false;
     ct->deviceBytes += (cap - ct->trailCap) * (int64_t)(sizeof(int2) + sizeof(uint4));
     ct->dev.trailKey = nk;
     ct->dev.trailOld = no;
@@ -174,8 +177,9 @@ int ensure_levels(ct_table* ct, int need) {
                                 cudaMemcpyDeviceToDevice, ct->stream));
     }
     CT_CUDA(cudaStreamSynchronize(ct->stream));
-    if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
-    if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+    if (ct->dev.levelSeg && !ct->levelsInArena) cudaFree(ct->dev.levelSeg);
+    if (ct->dev.levelDom && !ct->levelsInArena) cudaFree(ct->dev.levelDom);
+    ct->levelsInArena = false;
     ct->deviceBytes += (int64_t)(cap - ct->levelCap) * (ct->nseg * 4 + ct->DW * 4);
     ct->dev.levelSeg = ns;
     ct->dev.levelDom = nd;
@@ -188,10 +192,14 @@ void free_table(ct_table* ct) {
     if (!ct) return;
     if (ct->stream) cudaStreamSynchronize(ct->stream);
     for (void* p : ct->allocs) cudaFree(p);
-    if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
-    if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
-    if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
-    if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+    if (!ct->trailInArena) {
+        if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
+        if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
+    }
+    if (!ct->levelsInArena) {
+        if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
+        if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+    }
     if (ct->h_status) cudaFreeHost(ct->h_status);
     for (auto& e : ct->ev)
         if (e) cudaEventDestroy(e);
@@ -563,11 +571,40 @@ void ct_table_batch_done(ct_table* ct, int trailTop, int live) {
     ct->failed = false;
 }
 
+namespace {
+
+constexpr int kCloneLevels = 8;
+
+int64_t clone_trail_entries(const ct_table* src) { return 2 * src->W4 + 64; }
+
+size_t rnd256(size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); }
+
+// Bytes of every dynamic buffer of a clone, in allocation order.
+std::vector<size_t> clone_pieces(const ct_table* src) {
+    const size_t padChunks = (size_t)src->nseg * 32;
+    const size_t R = (size_t)src->R, n = (size_t)src->arity;
+    const size_t tr = (size_t)clone_trail_entries(src);
+    return {padChunks * sizeof(uint4), (size_t)src->nseg * 4, padChunks * 4, R * 4, (size_t)src->DW * 4, R * 4,
+            n * 4, n * 4, n * 4, n * 4, R * 4, R * 4,
+            (size_t)kCloneLevels * std::max(src->nseg, 1) * 4, (size_t)kCloneLevels * std::max(src->DW, 1) * 4,
+            tr * sizeof(int2), tr * sizeof(uint4)};
+}
+
+}  // namespace
+
+size_t ct_table_clone_bytes(const ct_table* src) {
+    size_t b = 0;
+    for (size_t p : clone_pieces(src)) b += rnd256(p);
+    return b + 256;
+}
+
 // A table that shares `src`'s static buffers (supports rows and the layout
 // tables, which stay owned by src) with dynamic buffers of its own (currTable,
 // index, lastDom, residues, trail, levels), filled by launch_clone_state. Used
-// for the independent search nodes of a batched search.
-ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status) {
+// for the independent search nodes of a batched search. With an arena the
+// dynamic buffers, 8 levels and a first trail come out of it in one piece;
+// a trail or level stack that outgrows them moves to its own allocation.
+ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* arena, Ctrl* ctrl, int* status) {
     *status = CT_ERR_ARG;
     if (!src || src->empty) return nullptr;
     ct_table* ct = new (std::nothrow) ct_table();
@@ -601,12 +638,55 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status) 
     d.trailOld = nullptr;
     d.levelSeg = nullptr;
     d.levelDom = nullptr;
+    d.statusBlk = src->dev.statusBlk;  // never written by the batched path; kept valid
+    if (arena) {
+        const std::vector<size_t> pc = clone_pieces(src);
+        void* p[16];
+        for (int i = 0; i < 16; ++i) {
+            p[i] = arena->take(pc[i]);
+            if (!p[i]) {
+                free_table(ct);
+                ct_set_error("clone arena exhausted");
+                *status = CT_ERR_OOM;
+                return nullptr;
+            }
+        }
+        d.curr = static_cast<uint4*>(p[0]);
+        d.segMask = static_cast<uint32_t*>(p[1]);
+        d.lastpos = static_cast<int32_t*>(p[2]);
+        d.residue = static_cast<int32_t*>(p[3]);
+        d.lastDom = static_cast<uint32_t*>(p[4]);
+        d.codes = static_cast<int32_t*>(p[5]);
+        d.planK = static_cast<int32_t*>(p[6]);
+        d.planRowOff = static_cast<int32_t*>(p[7]);
+        d.varSup = static_cast<int32_t*>(p[8]);
+        d.changed = static_cast<int32_t*>(p[9]);
+        d.hardRow = static_cast<int32_t*>(p[10]);
+        d.foundChunk = static_cast<int32_t*>(p[11]);
+        d.levelSeg = static_cast<uint32_t*>(p[12]);
+        d.levelDom = static_cast<uint32_t*>(p[13]);
+        d.trailKey = static_cast<int2*>(p[14]);
+        d.trailOld = static_cast<uint4*>(p[15]);
+        ct->levelCap = kCloneLevels;
+        ct->levelsInArena = true;
+        ct->trailCap = (int)clone_trail_entries(src);
+        ct->trailInArena = true;
+        int st = CT_OK;
+        if (ctrl) d.ctrl = ctrl;
+        else if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) {
+            free_table(ct);
+            *status = st;
+            return nullptr;
+        }
+        *status = CT_OK;
+        return ct;
+    }
     const size_t padChunks = (size_t)ct->nseg * 32;
     int st = CT_OK;
     if ((st = dalloc(ct, &d.curr, padChunks)) != CT_OK || (st = dalloc(ct, &d.segMask, (size_t)ct->nseg)) != CT_OK ||
         (st = dalloc(ct, &d.lastpos, padChunks)) != CT_OK || (st = dalloc(ct, &d.residue, (size_t)ct->R)) != CT_OK ||
-        (st = dalloc(ct, &d.lastDom, (size_t)ct->DW)) != CT_OK || (st = dalloc(ct, &d.ctrl, 1)) != CT_OK ||
-        (st = dalloc(ct, &d.codes, (size_t)ct->R)) != CT_OK || (st = dalloc(ct, &d.planK, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.lastDom, (size_t)ct->DW)) != CT_OK || (st = dalloc(ct, &d.codes, (size_t)ct->R)) != CT_OK ||
+        (st = dalloc(ct, &d.planK, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.planRowOff, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.varSup, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.changed, (size_t)ct->arity)) != CT_OK ||
@@ -615,8 +695,13 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status) 
         *status = st;
         return nullptr;
     }
-    d.statusBlk = src->dev.statusBlk;  // never written by the batched path; kept valid
-    if ((st = ensure_levels(ct, 8)) != CT_OK) {
+    if (ctrl) d.ctrl = ctrl;
+    else if ((st = dalloc(ct, &d.ctrl, 1)) != CT_OK) {
+        free_table(ct);
+        *status = st;
+        return nullptr;
+    }
+    if ((st = ensure_levels(ct, kCloneLevels)) != CT_OK) {
         free_table(ct);
         *status = st;
         return nullptr;
@@ -624,6 +709,8 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, int* status) 
     *status = CT_OK;
     return ct;
 }
+
+int ct_table_trail_cap(const ct_table* ct) { return ct->trailCap; }
 
 // Host side of a clone taking its source's state (the device side is
 // launch_clone_state): empty trail, no levels, the source's live count.

@@ -419,11 +419,14 @@ def ct_search_dfs(m, nvars, node_limit=0, count_all=True):
 
 
 def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True):
-    """Batched search: returns (status, stats dict with first_solution, batch info dict)."""
+    """Batched search: returns (status, stats dict with first_solution, batch info dict).
+    count_all: True/1 all solutions, False/0 the depth-first first solution,
+    2 (or "any") the first solution any slot finds."""
     s = ct_search_stats()
     info = ct_batch_info()
     sol = np.zeros(nvars, dtype=np.int32)
-    st = load().ct_search_batch(m, int(slots), int(split_depth), int(node_limit), 1 if count_all else 0,
+    mode = 2 if count_all == "any" else int(count_all)
+    st = load().ct_search_batch(m, int(slots), int(split_depth), int(node_limit), mode,
                                 ctypes.byref(s), sol.ctypes.data_as(_I32P), ctypes.byref(info))
     d = _as_dict(s)
     d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None

@@ -195,3 +195,24 @@ def test_batch_without_tables_and_bad_arguments():
     assert C.ct_search_batch(h, csp.nvars, 0, 1)[0] == C.CT_ERR_ARG
     assert C.ct_search_batch(h, csp.nvars, 4, 65)[0] == C.CT_ERR_ARG
     C.ct_model_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_batch_any_solution_mode(seed):
+    """count_all = 2 stops at the first solution any slot finds: it must be a
+    solution of every table; without solutions the whole tree is visited."""
+    csp, raw = _random(500 + seed, nvars=8, ntables=6, arity=3, d=5, t=40)
+    want = O.dfs(csp)
+    h = _model(csp, raw)
+    for slots, split in [(4, 2), (16, 0), (9, 4)]:
+        got, _ = _batch(h, csp, slots, split, count_all="any")
+        assert got["complete"] == 1
+        assert (got["solutions"] > 0) == (want.solutions > 0)
+        if want.solutions:
+            sol = got["first_solution"]
+            for scope, tup in csp.tables:
+                assert any(all(int(row[k]) == sol[v] for k, v in enumerate(scope)) for row in tup)
+        else:
+            assert (got["nodes"], got["fails"]) == (want.nodes, want.fails)
+    assert C.ct_search_batch(h, csp.nvars, 4, 1, 0, 3)[0] == C.CT_ERR_ARG
+    C.ct_model_destroy(h)
