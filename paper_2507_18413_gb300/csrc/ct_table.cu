@@ -78,7 +78,11 @@ struct ct_table {
     bool empty = false;
     ct_call_stats last{};
     bool profile = false;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // profile: event pairs around launches, read back lazily (a ring of pairs;
+    // the oldest pair is read when the ring is full or the profile is asked for)
+    static constexpr int kEvRing = 4096;
+    cudaEvent_t ev[2 * kEvRing] = {};
+    int evNext = 0, evPending = 0;
     ct_profile prof{};
     int64_t deviceBytes = 0;
     uint32_t* d_domScratch = nullptr;
@@ -436,6 +440,29 @@ void fill_stats(ct_table* ct) {
 // ---------------------------------------------------------------------------
 // internal entry points for the model
 // ---------------------------------------------------------------------------
+namespace {
+
+// Read the oldest pending event pair into the profile (waits for it).
+int drain_event(ct_table* ct) {
+    if (ct->evPending == 0) return CT_OK;
+    const int slot = (ct->evNext - ct->evPending + ct_table::kEvRing) % ct_table::kEvRing;
+    float a = 0.f;
+    CT_CUDA(cudaEventSynchronize(ct->ev[2 * slot + 1]));
+    CT_CUDA(cudaEventElapsedTime(&a, ct->ev[2 * slot], ct->ev[2 * slot + 1]));
+    ct->prof.kernel_ms += a;
+    ct->evPending -= 1;
+    return CT_OK;
+}
+
+int drain_events(ct_table* ct) {
+    int st = CT_OK;
+    while (ct->evPending > 0 && (st = drain_event(ct)) == CT_OK) {
+    }
+    return st;
+}
+
+}  // namespace
+
 int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
                           uint32_t* changed) {
     if (!ct || !dom) {
@@ -469,9 +496,18 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.prevLive = ct->live;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
-    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[0], s));
+    int evSlot = 0;
+    if (ct->profile) {
+        if (ct->evPending == ct_table::kEvRing && (st = drain_event(ct)) != CT_OK) return st;
+        evSlot = ct->evNext;
+        CT_CUDA(cudaEventRecord(ct->ev[2 * evSlot], s));
+    }
     CT_CUDA(launch_propagate(ct->dev, ct->variant, ct->grid, dom, domOffDev, P, s));
-    if (ct->profile) CT_CUDA(cudaEventRecord(ct->ev[1], s));
+    if (ct->profile) {
+        CT_CUDA(cudaEventRecord(ct->ev[2 * evSlot + 1], s));
+        ct->evNext = (ct->evNext + 1) % ct_table::kEvRing;
+        ct->evPending += 1;
+    }
     const auto t1 = std::chrono::steady_clock::now();
     ct->pendingFrom = (int)ct->marks.size();
     // Wait for the status word the kernel publishes last (bounded), then fall
@@ -509,15 +545,11 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     ct->trailTop = h[kSlotTrailTop];
     if (status == CT_OK) ct->live = h[kSlotLiveOut];
     if (ct->profile) {
-        float a = 0.f;
-        CT_CUDA(cudaEventSynchronize(ct->ev[1]));
-        CT_CUDA(cudaEventElapsedTime(&a, ct->ev[0], ct->ev[1]));
         ct->prof.host_ms +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         ct->prof.launch_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
         ct->prof.wait_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
         ct->prof.calls += 1;
-        ct->prof.kernel_ms += a;
         ct->prof.update_bytes += ct->last.update_bytes;
         ct->prof.filter_bytes += ct->last.filter_bytes;
         ct->prof.device_ms += ct->last.phase_ns[3] * 1e-6;
@@ -985,14 +1017,17 @@ extern "C" int ct_get_profile(ct_table* ct, ct_profile* prof) {
         ct_set_error("ct_get_profile: null argument");
         return CT_ERR_ARG;
     }
+    const int st = drain_events(ct);
+    if (st != CT_OK) return st;
     *prof = ct->prof;
     return CT_OK;
 }
 
 extern "C" int ct_reset_profile(ct_table* ct) {
     if (!ct) return CT_ERR_ARG;
+    const int st = drain_events(ct);
     ct->prof = ct_profile{};
-    return CT_OK;
+    return st;
 }
 
 extern "C" int ct_destroy(ct_table* ct) {
