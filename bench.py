@@ -438,9 +438,9 @@ def _bulk_update(C, torch, stream, t, arity, d, seed, reps=5):
             "device_us": prof["device_ms"] * 1e3 / reps, "phase_ns_last": stats["phase_ns"]}
 
 
-def _stream_rate(C, torch, stream, t, calls, seed):
+def _stream_rate(C, torch, stream, t, calls, seed, opt=None):
     dom_lo, dom_size, tup = G.large_table(seed, t, ARITY, DOM)
-    st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, stream=stream)
+    st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, opt=opt, stream=stream)
     C.check(st)
     off, _ = C.dom_layout(dom_size)
     dom = torch.zeros(int(off[-1]), dtype=torch.int32, device="cuda")
@@ -578,6 +578,13 @@ def extras(args, C, torch, stream):
     try:
         out["stream_props_per_s"] = {str(t): _stream_rate(C, torch, stream, t, 128, 99 + t)
                                      for t in (100_000, 1_000_000)}
+        # the paper's propagators copy currTable host<->device around every call
+        # (Sec. 4); the same streams with those copies added
+        out["copy_state_ablation_props_per_s"] = {
+            str(t): {"resident": _stream_rate(C, torch, stream, t, 128, 99 + t),
+                     "currtable_copied_each_call": _stream_rate(C, torch, stream, t, 128, 99 + t,
+                                                                opt=C.make_options(copy_state=1))}
+            for t in (100_000, 1_000_000, 4_000_000)}
         out["bulk_update_1e6"] = _bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)
         out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
         out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)

@@ -64,7 +64,12 @@ typedef struct ct_options {
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
     int32_t host_fixpoint;    /* models: 1 = run the fixpoint queue on the host, one launch per table
                                  propagation (default: the whole fixpoint in one launch) */
-    int32_t reserved[3];
+    int32_t copy_state;       /* 1 = ablation of the paper's propagators (Sec. 4: CT_CU^u/^f/^uf copy
+                                 _currTable host->device before and device->host after every
+                                 propagation): ct_propagate round-trips currTable through a pinned
+                                 host copy each call (and ct_restore refreshes it). Results are the
+                                 same; only the copies' cost is added. */
+    int32_t reserved[2];
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */
@@ -81,7 +86,7 @@ typedef struct ct_table_info {
     int32_t depth;         /* saved levels on the stack */
     int32_t local_plan;    /* 1: every CTA computes the update plan in shared memory */
     int32_t grid_blocks;   /* CTAs of the propagation launch */
-    int32_t reserved;
+    int32_t short_tuples;  /* retained tuples with at least one CT_STAR component */
     int64_t device_bytes;  /* device memory held by the table */
 } ct_table_info;
 
@@ -121,6 +126,9 @@ typedef struct ct_profile {
     double wait_ms;       /* ... of which waiting for the result */
 } ct_profile;
 
+/* The wildcard component of a short tuple (any value of the variable). */
+#define CT_STAR ((int32_t)(-2147483647 - 1))
+
 /* ---------------------------------------------------------------- table --
  * ct_create: build a table constraint (Sec. 2; constructor of class Table,
  * Sec. 3, and its device copy, Sec. 4).
@@ -134,6 +142,14 @@ typedef struct ct_profile {
  *   opt        tuning knobs or NULL
  *   cuda_stream cudaStream_t to run on, or NULL for a stream owned by the table
  *   out        receives the handle (also on CT_INFEASIBLE)
+ * A component equal to CT_STAR is a wildcard ("*", any value of the
+ * variable): short tables, the extension of Compact-Table to short tuples
+ * that the paper cites (Sec. 1) but does not evaluate. A short tuple stands
+ * for every tuple obtained by replacing its wildcards with values; it is
+ * valid while its other components are in their domains. Its supports rows
+ * hold it for every value of a wildcard position (filtering and the reset
+ * update); the delta update removes only tuples whose component equals a
+ * removed value.
  * Tuples with a value outside the initial domains are dropped. Returns
  * CT_INFEASIBLE when no tuple is left (the constructor's unsatisfiability
  * check, Sec. 3); the handle is still valid and every propagation of it

@@ -312,6 +312,7 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
     const int lp = S.lp;
     uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
     const uint4* base = T.sup + w;
+    const uint4* baseDelta = T.supDelta + w;  // the same rows unless the table has short tuples
     const size_t W4 = (size_t)T.W4;
     // Batches of U rows: U independent 128-bit loads in flight per lane; the
     // codes of the next batch are read from shared memory meanwhile.
@@ -321,7 +322,9 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
     for (int q0 = 0; q0 < nrows; q0 += U) {
         uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(base + (size_t)(code[u] & kCodeRow) * W4, act && q0 + u < nrows);
+        for (int u = 0; u < U; ++u)
+            v[u] = ld_sup_pred(((code[u] & kCodeDelta) ? baseDelta : base) + (size_t)(code[u] & kCodeRow) * W4,
+                               act && q0 + u < nrows);
         int nxt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {

@@ -89,7 +89,8 @@ struct Ctrl {
 
 // Everything a kernel needs, passed by value.
 struct TableDev {
-    const uint4* sup;
+    const uint4* sup;        // [R][W4] supports rows (short tuples in every row of a wildcard position)
+    const uint4* supDelta;   // rows OR-ed on the delta path: sup itself, or without the wildcards
     uint4* curr;
     uint32_t* segMask;
     int32_t* lastpos;

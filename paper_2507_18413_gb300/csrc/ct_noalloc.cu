@@ -154,6 +154,7 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     const int nseg = (int)((W4 + 31) / 32);
     TableDev T{};
     T.sup = reinterpret_cast<const uint4*>(supports);
+    T.supDelta = T.sup;
     T.curr = reinterpret_cast<uint4*>(curr_table);
     T.segMask = S->segMask;
     T.residue = S->residue;

@@ -87,6 +87,9 @@ struct ct_table {
     int64_t deviceBytes = 0;
     uint32_t* d_domScratch = nullptr;
     std::vector<void*> allocs;
+    int64_t shortTuples = 0;     // retained tuples with a wildcard
+    bool copyState = false;      // ablation: currTable round-trips through h_curr every call
+    uint32_t* h_curr = nullptr;  // pinned host copy of currTable (copy_state)
     bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
     bool levelsInArena = false;
 };
@@ -205,6 +208,7 @@ void free_table(ct_table* ct) {
         if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
     }
     if (ct->h_status) cudaFreeHost(ct->h_status);
+    if (ct->h_curr) cudaFreeHost(ct->h_curr);
     for (auto& e : ct->ev)
         if (e) cudaEventDestroy(e);
     if (ct->ownStream && ct->stream) cudaStreamDestroy(ct->stream);
@@ -236,22 +240,33 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < ct->size[i]; ++a) ct->rowVar[ct->row0[i] + a] = i;
 
-    // Retained tuples: every value inside its initial domain (input order kept).
+    // Retained tuples: every value inside its initial domain or a wildcard
+    // (input order kept).
     std::vector<int64_t> keep;
     keep.reserve((size_t)t);
+    int64_t nShort = 0;
     for (int64_t j = 0; j < t; ++j) {
         const int32_t* tu = tuples + j * n;
-        bool ok = true;
+        bool ok = true, star = false;
         for (int i = 0; i < n && ok; ++i) {
+            if (tu[i] == CT_STAR) {
+                star = true;
+                continue;
+            }
             const int64_t off = (int64_t)tu[i] - ct->lo[i];
             ok = off >= 0 && off < ct->size[i];
         }
-        if (ok) keep.push_back(j);
+        if (ok) {
+            keep.push_back(j);
+            nShort += star;
+        }
     }
+    ct->shortTuples = nShort;
     ct->t = (int64_t)keep.size();
     ct->W = (ct->t + 31) / 32;
     ct->W4 = (ct->W + 3) / 4;
     ct->profile = opt && opt->profile;
+    ct->copyState = opt && opt->copy_state;
     if (ct->t == 0) {
         ct->empty = true;
         return CT_INFEASIBLE;
@@ -266,15 +281,24 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     ct->localPlan = n <= kLocalMaxArity && DW <= kLocalMaxDW && R <= kCodeCap;
 
     // supports rows (Sec. 2), value-major, 16-byte aligned rows of W4 chunks
+    // (a short tuple is in every row of its wildcard positions; the delta rows
+    // hold only the tuples whose component equals the row's value)
     const size_t rowWords = (size_t)W4 * 4;
     std::vector<uint32_t> hsup((size_t)R * rowWords, 0u);
+    std::vector<uint32_t> hdel;
+    if (nShort > 0) hdel.assign((size_t)R * rowWords, 0u);
     for (int64_t jj = 0; jj < ct->t; ++jj) {
         const int32_t* tu = tuples + keep[(size_t)jj] * n;
         const uint32_t bit = 1u << (jj & 31);
         const size_t word = (size_t)(jj >> 5);
         for (int i = 0; i < n; ++i) {
+            if (tu[i] == CT_STAR) {
+                for (int a = 0; a < ct->size[i]; ++a) hsup[(size_t)(ct->row0[i] + a) * rowWords + word] |= bit;
+                continue;
+            }
             const int row = ct->row0[i] + (tu[i] - ct->lo[i]);
             hsup[(size_t)row * rowWords + word] |= bit;
+            if (nShort > 0) hdel[(size_t)row * rowWords + word] |= bit;
         }
     }
     std::vector<int32_t> hres(R, 0);
@@ -308,6 +332,8 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     uint4* sup = nullptr;
     int32_t *rowVar = nullptr, *varRow0 = nullptr, *varNW = nullptr, *varLD = nullptr;
     if ((st = dalloc(ct, &sup, (size_t)R * W4)) != CT_OK) return st;
+    uint4* supDel = sup;
+    if (nShort > 0 && (st = dalloc(ct, &supDel, (size_t)R * W4)) != CT_OK) return st;
     // currTable and lastpos are padded to whole 32-chunk segments.
     const size_t padChunks = (size_t)ct->nseg * 32;
     if ((st = dalloc(ct, &d.curr, padChunks)) != CT_OK) return st;
@@ -330,6 +356,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     ct->statusInts = (size_t)kStatusHdr + ct->nChW + DW;
     if ((st = dalloc(ct, &ct->d_domScratch, (size_t)DW)) != CT_OK) return st;
     d.sup = sup;
+    d.supDelta = supDel;
     d.rowVar = rowVar;
     d.varRow0 = varRow0;
     d.varNW = varNW;
@@ -378,6 +405,9 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     }
 
     CT_CUDA(cudaMemcpyAsync(sup, hsup.data(), hsup.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ct->stream));
+    if (nShort > 0)
+        CT_CUDA(cudaMemcpyAsync(supDel, hdel.data(), hdel.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                ct->stream));
     CT_CUDA(cudaMemsetAsync(d.curr, 0, padChunks * sizeof(uint4), ct->stream));
     CT_CUDA(cudaMemcpyAsync(d.curr, hcurr.data(), hcurr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                             ct->stream));
@@ -454,6 +484,20 @@ int drain_event(ct_table* ct) {
     return CT_OK;
 }
 
+// copy_state ablation: the host copy of currTable, (re)read from the device.
+int fetch_host_curr(ct_table* ct) {
+    const size_t bytes = (size_t)ct->W4 * sizeof(uint4);
+    if (!ct->h_curr && cudaHostAlloc((void**)&ct->h_curr, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        ct->h_curr = nullptr;
+        ct_set_error("copy_state: pinned host copy of currTable");
+        return CT_ERR_OOM;
+    }
+    CT_CUDA(cudaMemcpyAsync(ct->h_curr, ct->dev.curr, bytes, cudaMemcpyDeviceToHost, ct->stream));
+    CT_CUDA(cudaStreamSynchronize(ct->stream));
+    return CT_OK;
+}
+
 int drain_events(ct_table* ct) {
     int st = CT_OK;
     while (ct->evPending > 0 && (st = drain_event(ct)) == CT_OK) {
@@ -496,6 +540,11 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.prevLive = ct->live;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
+    if (ct->copyState) {
+        // the paper's propagators copy currTable to the device before each call
+        if (!ct->h_curr && (st = fetch_host_curr(ct)) != CT_OK) return st;
+        CT_CUDA(cudaMemcpyAsync(ct->dev.curr, ct->h_curr, (size_t)ct->W4 * sizeof(uint4), cudaMemcpyHostToDevice, s));
+    }
     int evSlot = 0;
     if (ct->profile) {
         if (ct->evPending == ct_table::kEvRing && (st = drain_event(ct)) != CT_OK) return st;
@@ -523,6 +572,11 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
             break;
     }
     if (!seen) CT_CUDA(cudaStreamSynchronize(s));
+    if (ct->copyState) {
+        // ... and back to the host after it
+        CT_CUDA(cudaMemcpyAsync(ct->h_curr, ct->dev.curr, (size_t)ct->W4 * sizeof(uint4), cudaMemcpyDeviceToHost, s));
+        CT_CUDA(cudaStreamSynchronize(s));
+    }
     const auto t2 = std::chrono::steady_clock::now();
     int status = hv[kSlotStatus];
     if (status == kNoChunk) {
@@ -910,6 +964,10 @@ extern "C" int ct_restore(ct_table* ct, int level) {
     if (!ct->empty && level < ct->pendingFrom) {
         CT_CUDA(launch_restore(ct->dev, level, mark, ct->trailTop, -1, ct->stream));
         ct->trailTop = mark;
+        if (ct->copyState && ct->h_curr) {
+            const int st = fetch_host_curr(ct);
+            if (st != CT_OK) return st;
+        }
     }
     // A level saved after the last propagation still equals the current state.
     ct->failed = false;
@@ -994,6 +1052,7 @@ extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
     r.depth = (int)ct->marks.size();
     r.local_plan = ct->localPlan ? 1 : 0;
     r.grid_blocks = ct->grid;
+    r.short_tuples = (int32_t)std::min<int64_t>(ct->shortTuples, 0x7fffffff);
     r.device_bytes = ct->deviceBytes;
     int64_t live = 0;
     const int st = ct_get_index(ct, nullptr, &live);

@@ -16,6 +16,7 @@ import numpy as np
 
 from . import build as _build
 
+CT_STAR = -2**31  # wildcard component of a short tuple
 CT_OK = 0
 CT_INFEASIBLE = 1
 CT_ERR_ARG = -1
@@ -35,7 +36,8 @@ class CtError(RuntimeError):
 class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("host_fixpoint", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("host_fixpoint", ctypes.c_int32), ("copy_state", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -43,7 +45,7 @@ class ct_table_info(ctypes.Structure):
                 ("words", ctypes.c_int64), ("chunks", ctypes.c_int64), ("segments", ctypes.c_int32),
                 ("seg_capacity", ctypes.c_int32), ("live_chunks", ctypes.c_int64),
                 ("trail_size", ctypes.c_int64), ("depth", ctypes.c_int32),
-                ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("short_tuples", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64)]
 
 
@@ -220,9 +222,10 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0):
     o = ct_options()
     o.host_fixpoint = host_fixpoint
+    o.copy_state = copy_state
     o.grid_blocks = grid_blocks
     o.no_residues = no_residues
     o.profile = profile

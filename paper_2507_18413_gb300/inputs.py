@@ -344,3 +344,16 @@ def learned_csp(seed: int, nvars=(30, 60), dom=(16, 64), ntables=(40, 120), arit
         csp.tables.append(TableSpec(scope=sc, tuples=tup))
     return csp
 
+
+STAR = -2 ** 31  # the wildcard component of a short tuple
+
+
+def short_tuples(seed: int, dom_lo, dom_size, t: int, star_prob: float = 0.2) -> np.ndarray:
+    """``t`` distinct uniform tuples in which every component is independently
+    replaced by the wildcard STAR with probability ``star_prob`` (seeded)."""
+    tup = distinct_uniform_tuples(seed, dom_lo, dom_size, t).astype(np.int64)
+    rng = Rng(derive_seed(seed, 0x5747))
+    u = rng.uniform(tup.size).reshape(tup.shape)
+    tup[u < star_prob] = STAR
+    return tup.astype(np.int32)
+

@@ -135,6 +135,13 @@ def test_large_stream_1e5():
     assert seen["delta"] > 0 and seen["reset"] > 0
 
 
+def test_copy_state_ablation_gives_the_same_results():
+    """copy_state round-trips currTable through host memory around every call
+    (the paper's per-call copies); every call must still match the oracle."""
+    seen = _large_stream(100_000, calls=120, seed=13, opt=C.make_options(copy_state=1))
+    assert seen["delta"] > 0 and seen["reset"] > 0
+
+
 @pytest.mark.parametrize("grid", [1, 5, 0])
 def test_large_stream_grid_sizes(grid):
     _large_stream(60_000, calls=60, seed=12, opt=C.make_options(grid_blocks=grid), depth=12)
