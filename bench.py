@@ -63,10 +63,11 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--case", default="stream",
-                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned"],
+                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned", "net512"],
                    help="bulk*: only the one-call bandwidth case (for profiling); "
                         "search: only the plain vs batched search figures; "
-                        "learned: the learned-order experiment at full size")
+                        "learned: the learned-order experiment at full size; "
+                        "net512: the 512-table network fixpoints")
     p.add_argument("--learned-eval", type=int, default=200, help="held-out instances of --case learned")
     p.add_argument("--learned-full", type=int, default=10,
                    help="instances at config-4 size (30-60 vars, 40-120 tables) in --case learned")
@@ -536,6 +537,68 @@ def search_extras(C):
     return out
 
 
+def network_extras(C, tuples=(1e3, 1e6), edits=60, seed=3):
+    """512 tables (arity 2-8, log-uniform tuple counts, domains 8-128, half Zipf)
+    over 1,024 variables propagated to their common fixpoint in one cooperative
+    launch per fixpoint: the root fixpoint, then a stream of edits (1 value or
+    half a domain of a random variable) with saves, restoring to the root on
+    failure or after 5 edits. Bytes are the algorithmic bytes of every table
+    propagation (ct_model_stats), time the host-observed launch-to-result time."""
+    hbm, _ = peaks()
+    t0 = time.perf_counter()
+    spec = G.network_tables(seed, tuples=tuples)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m = _build_model(C, spec)
+    build_s = time.perf_counter() - t0
+    try:
+        C.ct_model_reset_stats(m)
+        st = C.ct_model_propagate(m)
+        C.check(st)
+        st, root = C.ct_model_get_stats(m)
+        C.ct_model_reset_stats(m)
+        st, lv0 = C.ct_model_save(m)
+        off, _ = C.dom_layout(spec.dom_size)
+        rng = G.Rng(G.derive_seed(seed, 99))
+        depth = fails = 0
+        for i in range(edits):
+            st, w = C.ct_model_get_domains(m, int(off[-1]))
+            masks = C.words_to_masks(w, spec.dom_size)
+            cand = [v for v, mk in enumerate(masks) if mk.sum() > 1]
+            v = cand[rng.int(len(cand))]
+            vals = np.flatnonzero(masks[v])
+            k = 1 if rng.int(2) == 0 else len(vals) // 2
+            order = np.argsort(rng.u64(len(vals)), kind="stable")[:k]
+            masks[v][vals[order]] = False
+            C.check(C.ct_model_save(m)[0])
+            C.check(C.ct_model_set_domains(m, C.masks_to_words(masks)))
+            st = C.ct_model_propagate(m)
+            depth += 1
+            if st == C.CT_INFEASIBLE or depth >= 5:
+                fails += st == C.CT_INFEASIBLE
+                C.check(C.ct_model_restore(m, lv0))
+                C.check(C.ct_model_save(m)[0])
+                depth = 0
+        st, ed = C.ct_model_get_stats(m)
+    finally:
+        C.ct_model_destroy(m)
+
+    def summary(d):
+        b = d["update_bytes"] + d["filter_bytes"]
+        gbs = b / d["wait_seconds"] / 1e9 if d["wait_seconds"] > 0 else 0.0
+        return {"fixpoints": d["fixpoints"], "rounds": d["rounds"], "table_propagations": d["propagations"],
+                "seconds": round(d["wait_seconds"], 4),
+                "ms_per_fixpoint": round(1e3 * d["wait_seconds"] / max(1, d["fixpoints"]), 3),
+                "update_bytes": d["update_bytes"], "filter_bytes": d["filter_bytes"],
+                "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4)}
+
+    return {"tables": len(spec.tables), "variables": spec.nvars,
+            "tuples_total": int(sum(len(tb.tuples) for tb in spec.tables)),
+            "tuple_range": [int(tuples[0]), int(tuples[1])], "generate_s": round(gen_s, 1),
+            "build_s": round(build_s, 1), "root_fixpoint": summary(root), "edit_fixpoints": summary(ed),
+            "edit_failures": fails}
+
+
 LEARNED_SMALL = dict(nvars=(20, 30), dom=(8, 16), ntables=(30, 50), arity=(3, 4), tuples=(1e3, 2e4))
 
 
@@ -576,6 +639,7 @@ def learned_extras(C, n_train=40, n_eval=20, node_limit=5000, train_nodes=300, m
 def extras(args, C, torch, stream):
     out = {}
     try:
+        out["network_512_tables"] = network_extras(C)
         out["stream_props_per_s"] = {str(t): _stream_rate(C, torch, stream, t, 128, 99 + t)
                                      for t in (100_000, 1_000_000)}
         # the paper's propagators copy currTable host<->device around every call
@@ -699,6 +763,8 @@ def main():
         stream = torch.cuda.current_stream()
         if args.case == "search":
             print(json.dumps(search_extras(C)))
+        elif args.case == "net512":
+            print(json.dumps(network_extras(C)))
         elif args.case == "learned":
             print(json.dumps(learned_extras(C, n_train=200, n_eval=args.learned_eval, node_limit=20_000,
                                             full_eval=args.learned_full)))

@@ -282,6 +282,26 @@ int ct_model_propagate(ct_model* m);
 int ct_model_get_domains(ct_model* m, uint32_t* words_host);
 int ct_model_set_domains(ct_model* m, const uint32_t* words_host);
 
+/* Counters of the model's fixpoints since creation or ct_model_reset_stats
+ * (the one-launch fixpoint fills all of them; the host queue only
+ * propagations). Bytes are algorithmic, as for one table: updateTable
+ * 4 * (non-zero words at entry) * (rows OR-ed + 2) per table propagation;
+ * filterDomains 16 per residue hit, 512 per window probed and 16 per live
+ * chunk of every full scan. */
+typedef struct ct_model_stats {
+    int64_t fixpoints;     /* launches of the fixpoint kernel */
+    int64_t rounds;        /* Jacobi rounds in them */
+    int64_t propagations;  /* table propagations */
+    int64_t residue_hits;
+    int64_t window_hits;
+    int64_t hard_values;
+    int64_t update_bytes;
+    int64_t filter_bytes;
+    double wait_seconds;   /* host time from each launch to its published result */
+} ct_model_stats;
+int ct_model_get_stats(ct_model* m, ct_model_stats* out);
+int ct_model_reset_stats(ct_model* m);
+
 int ct_model_save(ct_model* m, int* level_out);
 int ct_model_restore(ct_model* m, int level);
 
@@ -340,6 +360,8 @@ typedef struct ct_batch_info {
     int64_t residue_hits; /* slots' phase, Algorithm 3: values whose residue still held a support, */
     int64_t window_hits;  /* values found in the windows after the residue, */
     int64_t hard_values;  /* values left for the full index scan (found or pruned there) */
+    int64_t update_bytes; /* slots' phase: algorithmic bytes as in ct_model_stats */
+    int64_t filter_bytes;
     int32_t slots;
     int32_t split_depth;
     double setup_seconds; /* building or refreshing the copies */

@@ -133,7 +133,10 @@ struct CallParams {
 // ---------------------------------------------------------------------------
 constexpr int kModelMaxTables = 1 << 20;
 constexpr int kPrefixSmem = 2047;      // rounds of up to this many tables keep their prefix arrays in shared memory
-constexpr int kModelHdr = 8;           // status block: header ints before the per-table pairs
+constexpr int kModelHdr = 12;          // status block: header ints before the per-table pairs
+// header: [0] status, [1] rounds, [2] table propagations, [3] residue hits,
+// [4] window hits, [5] hard values, [6] windows, [8..9] updateTable bytes,
+// [10..11] filterDomains bytes (64-bit, little end first)
 
 struct RestoreDesc {
     int32_t table, level, mark, top;
@@ -158,6 +161,8 @@ struct ModelCtrl {
     uint32_t hard;       // values left for the full index scan
     uint32_t windows;    // windows probed
     int32_t pad[4];
+    unsigned long long bytesUpdate;  // algorithmic bytes of updateTable: 4 * words at entry * (rows + 2)
+    unsigned long long bytesFilter;  // of the full scans: 16 * hard values * live chunks
 };
 
 struct ModelDev {

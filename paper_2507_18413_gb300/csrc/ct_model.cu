@@ -158,6 +158,7 @@ int batch_propagate(ct_model* m) {
             break;
     }
     if (!seen) CT_CUDA(cudaStreamSynchronize(m->stream));
+    m->stats.wait_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     const int status = H[0];
     if (status == kNoChunk) {
         ct_set_error("model: the fixpoint kernel did not publish (a device-side wait ran out)");
@@ -166,6 +167,14 @@ int batch_propagate(ct_model* m) {
         return CT_ERR_TIMEOUT;
     }
     m->propagations += H[2];
+    m->stats.fixpoints += 1;
+    m->stats.rounds += H[1];
+    m->stats.propagations += H[2];
+    m->stats.residue_hits += (uint32_t)H[3];
+    m->stats.window_hits += (uint32_t)H[4];
+    m->stats.hard_values += (uint32_t)H[5];
+    m->stats.update_bytes += (int64_t)(((uint64_t)(uint32_t)H[9] << 32) | (uint32_t)H[8]);
+    m->stats.filter_bytes += (int64_t)(((uint64_t)(uint32_t)H[11] << 32) | (uint32_t)H[10]);
     for (int t = 0; t < n; ++t) ct_table_batch_done(m->tables[t], H[kModelHdr + 2 * t], H[kModelHdr + 2 * t + 1]);
     if (status == CT_OK && H[kModelHdr + 2 * n + m->DWg] == CT_INFEASIBLE) {
         m->failed = true;
@@ -412,6 +421,7 @@ extern "C" int ct_model_propagate(ct_model* m) {
         changed.assign((size_t)ct_table_changed_words(tab), 0u);
         const int st = ct_table_propagate_on(tab, m->d_dom, m->d_tabOff[T], m->tabOff[T].data(), changed.data());
         m->propagations += 1;
+        m->stats.propagations += 1;
         if (st == CT_INFEASIBLE) {
             m->failed = true;
             return CT_INFEASIBLE;
@@ -685,6 +695,24 @@ extern "C" int ct_model_features(ct_model* m, float* features_host) {
     CT_CUDA(cudaMemcpyAsync(features_host, m->fview->feat, (size_t)m->nvars * kNF * sizeof(float),
                             cudaMemcpyDeviceToHost, m->stream));
     CT_CUDA(cudaStreamSynchronize(m->stream));
+    return CT_OK;
+}
+
+extern "C" int ct_model_get_stats(ct_model* m, ct_model_stats* out) {
+    if (!m || !out) {
+        ct_set_error("ct_model_get_stats: null argument");
+        return CT_ERR_ARG;
+    }
+    *out = m->stats;
+    return CT_OK;
+}
+
+extern "C" int ct_model_reset_stats(ct_model* m) {
+    if (!m) {
+        ct_set_error("ct_model_reset_stats: null handle");
+        return CT_ERR_ARG;
+    }
+    m->stats = ct_model_stats{};
     return CT_OK;
 }
 

@@ -31,6 +31,7 @@ struct ct_model {
     bool staticInfeasible = false;
     bool failed = false;
     int64_t propagations = 0;
+    ct_model_stats stats{};  // counters of the one-launch fixpoints
     // the one-launch fixpoint
     bool batch = true;
     bool batchReady = false;

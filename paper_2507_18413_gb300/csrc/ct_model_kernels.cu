@@ -309,7 +309,14 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             const int gtid = blockIdx.x * kThreads + tid, gth = gridDim.x * kThreads;
             for (int k = gtid; k < nwork; k += gth) {
                 Ctrl* Tc = M.tabs[__ldcg(&work[k])].ctrl;
-                if (__ldcg(&Tc->nrows) > 0) Tc->live_state = (int32_t)__ldcg(&Tc->live);
+                const int nr = __ldcg(&Tc->nrows);
+                const unsigned long long live = nr > 0 ? __ldcg(&Tc->live) : (unsigned long long)__ldcg(&Tc->live_state);
+                if (nr > 0) {
+                    Tc->live_state = (int32_t)live;
+                    atomicAdd(&C->bytesUpdate, 4ull * __ldcg(&Tc->words_in) * (unsigned long long)(nr + 2));
+                }
+                const unsigned nh = __ldcg(&Tc->nhard);
+                if (nh) atomicAdd(&C->bytesFilter, 16ull * nh * live);
                 Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
             }
             for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
@@ -378,7 +385,18 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         H[4] = (int32_t)__ldcg(&C->local);
         H[5] = (int32_t)__ldcg(&C->hard);
         H[6] = (int32_t)__ldcg(&C->windows);
+        // filterDomains bytes as for one table: 16 per residue hit, 512 per window
+        // probed, 16 per live chunk of every full scan
+        const unsigned long long bf = __ldcg(&C->bytesFilter) + 16ull * __ldcg(&C->hits) +
+                                      512ull * __ldcg(&C->windows);
+        const unsigned long long bu = __ldcg(&C->bytesUpdate);
+        H[8] = (int32_t)(bu & 0xffffffffull);
+        H[9] = (int32_t)(bu >> 32);
+        H[10] = (int32_t)(bf & 0xffffffffull);
+        H[11] = (int32_t)(bf >> 32);
         C->hits = C->local = C->hard = C->windows = 0u;
+        C->bytesUpdate = 0ull;
+        C->bytesFilter = 0ull;
         C->status = CT_OK;
         C->rounds = 0;
         C->props = 0;

@@ -21,6 +21,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ct_model.cuh"
 
 using namespace ctk;
@@ -676,6 +678,8 @@ struct Search {
         info.residue_hits += (uint32_t)H[3];
         info.window_hits += (uint32_t)H[4];
         info.hard_values += (uint32_t)H[5];
+        info.update_bytes += (int64_t)(((uint64_t)(uint32_t)H[9] << 32) | (uint32_t)H[8]);
+        info.filter_bytes += (int64_t)(((uint64_t)(uint32_t)H[11] << 32) | (uint32_t)H[10]);
         for (int j = 0; j < n; ++j) {
             ct_table_batch_done(b->tabs[j], H[kModelHdr + 2 * j], H[kModelHdr + 2 * j + 1]);
             restPos[j] = -1;
@@ -719,6 +723,14 @@ struct Search {
     }
 
     int run_slots() {
+        // a named range for profilers (no cost without one attached)
+        nvtxRangePushA("ct_search_batch_slots");
+        const int rc = run_slots_timed();
+        nvtxRangePop();
+        return rc;
+    }
+
+    int run_slots_timed() {
         const auto s0 = std::chrono::steady_clock::now();
         if (b->d_phase) CT_CUDA(cudaMemsetAsync(b->d_phase, 0, kModelPhases * sizeof(uint64_t), b->stream));
         int rc = run_slots_inner();

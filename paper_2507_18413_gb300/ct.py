@@ -73,10 +73,17 @@ class ct_search_stats(ctypes.Structure):
                 ("complete", ctypes.c_int32), ("seconds", ctypes.c_double)]
 
 
+class ct_model_stats(ctypes.Structure):
+    _fields_ = [("fixpoints", ctypes.c_int64), ("rounds", ctypes.c_int64), ("propagations", ctypes.c_int64),
+                ("residue_hits", ctypes.c_int64), ("window_hits", ctypes.c_int64), ("hard_values", ctypes.c_int64),
+                ("update_bytes", ctypes.c_int64), ("filter_bytes", ctypes.c_int64), ("wait_seconds", ctypes.c_double)]
+
+
 class ct_batch_info(ctypes.Structure):
     _fields_ = [("open_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("steals", ctypes.c_int64), ("slot_nodes", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("residue_hits", ctypes.c_int64), ("window_hits", ctypes.c_int64), ("hard_values", ctypes.c_int64),
+                ("update_bytes", ctypes.c_int64), ("filter_bytes", ctypes.c_int64),
                 ("slots", ctypes.c_int32), ("split_depth", ctypes.c_int32), ("setup_seconds", ctypes.c_double),
                 ("wait_seconds", ctypes.c_double), ("slot_seconds", ctypes.c_double),
                 ("phase_seconds", ctypes.c_double * 8)]
@@ -124,6 +131,8 @@ _SIGS = {
     "ct_search_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
+    "ct_model_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ct_model_stats)]),
+    "ct_model_reset_stats": (ctypes.c_int, [_P]),
     "ct_mlp_create": (ctypes.c_int, [_F32P, _P, ctypes.POINTER(_P)]),
     "ct_mlp_set_weights": (ctypes.c_int, [_P, _F32P]),
     "ct_mlp_get_weights": (ctypes.c_int, [_P, _F32P]),
@@ -543,6 +552,16 @@ def ct_search_collect(m, node_limit, slots, max_samples):
     st = load().ct_search_collect(m, int(node_limit), int(slots), int(max_samples), X.ctypes.data_as(_F32P),
                                   y.ctypes.data_as(_F32P), ctypes.byref(n))
     return st, X[: n.value], y[: n.value]
+
+
+def ct_model_get_stats(m):
+    s = ct_model_stats()
+    st = load().ct_model_get_stats(m, ctypes.byref(s))
+    return st, _as_dict(s)
+
+
+def ct_model_reset_stats(m):
+    return load().ct_model_reset_stats(m)
 
 
 def ct_model_destroy(m):

@@ -357,3 +357,28 @@ def short_tuples(seed: int, dom_lo, dom_size, t: int, star_prob: float = 0.2) ->
     tup[u < star_prob] = STAR
     return tup.astype(np.int32)
 
+
+def network_tables(seed: int, ntables: int = 512, nvars: int = 1024, arity=(2, 8), tuples=(1e3, 1e6),
+                   dom=(8, 128), zipf_s: float = 1.2) -> CspSpec:
+    """The many-table network of the batching experiments: ``nvars`` variables with
+    domain sizes uniform in ``dom``; ``ntables`` tables of arity uniform in ``arity``
+    over random scopes, each with a log-uniform tuple count in ``tuples``. Even
+    tables hold distinct uniform tuples (capped at half the tuple space), odd
+    tables per-column Zipf(zipf_s) tuples (duplicates possible)."""
+    rng = Rng(seed)
+    sizes = [dom[0] + rng.int(dom[1] - dom[0] + 1) for _ in range(nvars)]
+    csp = CspSpec(nvars=nvars, dom_lo=[0] * nvars, dom_size=sizes)
+    lo, hi = math.log(tuples[0]), math.log(tuples[1])
+    for k in range(ntables):
+        a = arity[0] + rng.int(arity[1] - arity[0] + 1)
+        sc = random_scope(rng, nvars, a)
+        ds = [sizes[v] for v in sc]
+        t = int(round(math.exp(lo + float(rng.uniform(1)[0]) * (hi - lo))))
+        ts = derive_seed(seed, k)
+        if k % 2 == 0:
+            tup = distinct_uniform_tuples(ts, [0] * a, ds, cap_distinct(ds, t))
+        else:
+            tup = zipf_tuples(ts, [0] * a, ds, t, s=zipf_s)
+        csp.tables.append(TableSpec(scope=sc, tuples=tup))
+    return csp
+

@@ -89,7 +89,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [C.ct_options, C.ct_table_info, C.ct_call_stats, C.ct_profile, C.ct_search_stats, C.ct_batch_info]
+    structs = [C.ct_options, C.ct_table_info, C.ct_call_stats, C.ct_profile, C.ct_search_stats, C.ct_batch_info,
+               C.ct_model_stats]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ct.h"', "int main(void){"]
     for st in structs:
         n = st.__name__
