@@ -415,33 +415,113 @@ __device__ __forceinline__ void trail_warp(const TableDev& T, const TrailItem& i
 // ---------------------------------------------------------------------------
 // probe: Algorithm 3 with residues, a warp per value whose residue missed
 // ---------------------------------------------------------------------------
-// A value whose residue missed (whole warp): windows of 32 chunks after the
-// residue; a value missed there too goes to the table's hard list.
-__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
+// Position of the k-th (0-based) set bit of m (k < popcount(m)): halve the
+// word, keeping the half that holds it.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// A value whose residue missed (whole warp, r and res uniform): Algorithm 3's
+// search for a support over the live chunks (the non-zero index) that follow
+// the residue in cyclic order, 32 chunks per window, at most kLocalProbes
+// windows over at most kWindowGroups x 32 index segments. Found: the residue
+// moves there. Not found with every live chunk tested: the value has no
+// support and goes to the hard list as ~r (removed without a scan). Else it
+// goes to the hard list as r for the full scan. (Measured against windows of
+// the chunks that follow the residue, dead or alive: the same on the dense
+// bench stream, 8-10% more search nodes per second in the batched search.)
+__device__ __noinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    bool complete = false;
     if (T.useResidues) {
-        const int W4 = T.W4;
-        const uint4* row = T.sup + (size_t)r * W4;
-        for (int b = 0; b < kLocalProbes; ++b) {
-            if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
-            const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
-            const bool h = nz(and4(ld_sup(row + c), __ldcg(T.curr + c)));
-            const unsigned bal = __ballot_sync(0xffffffffu, h);
-            if (bal) {
-                const int cf = __shfl_sync(0xffffffffu, c, __ffs(bal) - 1);
-                if (lane == 0) {
-                    T.residue[r] = cf;
-                    atomicAdd(&s_cnt[kCntLocal], 1u);
+        const uint4* row = T.sup + (size_t)r * T.W4;
+        const int nseg = T.nseg;
+        const int s0 = res >> 5, b0 = res & 31;
+        const uint32_t above = b0 == 31 ? 0u : (0xffffffffu << (b0 + 1));
+        const uint32_t below = (1u << b0) - 1u;
+        // virtual segments: s0 (chunks above res), s0+1, ..., s0-1 (cyclic), s0 (chunks below res)
+        const int nvirt = nseg + 1;
+        int tested = 0;
+        complete = true;
+        for (int g = 0, v0 = 0; v0 < nvirt && complete; ++g, v0 += 32) {
+            if (g == kWindowGroups || tested >= 32 * kLocalProbes) {
+                complete = false;
+                break;
+            }
+            const int v = v0 + lane;
+            uint32_t mk = 0u;
+            int sg = 0;
+            if (v < nvirt) {
+                sg = s0 + v;
+                if (sg >= nseg) sg -= nseg;
+                mk = __ldcg(&T.segMask[sg]);
+                if (v == 0) mk &= above;
+                else if (v == nseg) mk &= below;
+            }
+            const int c = __popc(mk);
+            int inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const int total = __shfl_sync(FULL, inc, 31);
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                if (tested >= 32 * kLocalProbes) {
+                    complete = false;
+                    break;
                 }
-                return;
+                if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
+                const int q = q0 + lane;
+                // the lane whose segment holds live chunk q of the group: smallest j with inc_j > q
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int it = 0; it < 5; ++it) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__shfl_sync(FULL, inc, mid) > q) hi = mid;
+                    else lo = mid + 1;
+                }
+                const uint32_t mj = __shfl_sync(FULL, mk, lo);
+                const int before = __shfl_sync(FULL, inc, lo) - __shfl_sync(FULL, c, lo);
+                const int sj = __shfl_sync(FULL, sg, lo);
+                bool h = false;
+                int chunk = 0;
+                if (q < total) {
+                    chunk = sj * 32 + nth_set_bit(mj, q - before);
+                    h = nz(and4(ld_sup(row + chunk), __ldcg(T.curr + chunk)));
+                }
+                tested += min(32, total - q0);
+                const unsigned bal = __ballot_sync(FULL, h);
+                if (bal) {
+                    const int cf = __shfl_sync(FULL, chunk, __ffs(bal) - 1);
+                    if (lane == 0) {
+                        T.residue[r] = cf;
+                        atomicAdd(&s_cnt[kCntLocal], 1u);
+                    }
+                    return;
+                }
             }
         }
     }
     if (lane == 0) {
         const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
-        T.hardRow[m] = r;
+        T.hardRow[m] = complete ? ~r : r;
         T.foundChunk[m] = kNoChunk;
-        atomicAdd(&s_cnt[kCntMiss], 1u);
+        if (!complete) {
+            atomicAdd(&T.ctrl->nscan, 1);
+            atomicAdd(&s_cnt[kCntMiss], 1u);
+        }
     }
 }
 
@@ -480,7 +560,7 @@ __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh,
             hit[u] = false;
             if (act && mm < nh) {
                 const int r = (!kGlobal && mm < kCodeCap) ? s_rows[mm] : __ldcg(&T.hardRow[mm]);
-                hit[u] = nz(and4(ld_sup(T.sup + (size_t)r * W4 + w), cur));
+                if (r >= 0) hit[u] = nz(and4(ld_sup(T.sup + (size_t)r * W4 + w), cur));  // ~r: known unsupported
             }
         }
 #pragma unroll

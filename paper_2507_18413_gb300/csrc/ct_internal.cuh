@@ -36,7 +36,8 @@ constexpr int32_t kNoChunk = 0x7fffffff;
 constexpr int32_t kCodeLast = 1 << 30;   // last row of its variable: apply the mask
 constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~OR(rows)
 constexpr int32_t kCodeRow = (1 << 29) - 1;
-constexpr int kLocalProbes = 2;          // 32-chunk windows searched after a residue miss
+constexpr int kLocalProbes = 2;          // windows of 32 live chunks searched after a residue miss
+constexpr int kWindowGroups = 8;         // index segments read for them: at most 8 x 32 (8,192 chunks)
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
 constexpr int kParamArity = 16;        // scopes up to this arity carry their layout in kernel parameters
@@ -83,7 +84,7 @@ struct Ctrl {
     int32_t nval, ndelta, nreset, nsup;
     int32_t hits, pruned, trail_added, local_found, misses, windows;
     int32_t live_state;  // live chunks after the last update (kept across calls)
-    int32_t pad;
+    int32_t nscan;       // per call: hard values that need the full scan (the others are known unsupported)
     uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
 };
 

@@ -56,7 +56,8 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
-            const int r = __ldcg(&T.hardRow[m]);
+            int r = __ldcg(&T.hardRow[m]);
+            if (r < 0) r = ~r;  // unsupported without a scan
             const int fc = __ldcg(&T.foundChunk[m]);
             if (fc != kNoChunk) {
                 T.residue[r] = fc;
@@ -107,7 +108,7 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
             case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
             case kSlotLocal: v = __ldcg(&C->local_found); break;
-            case kSlotHard: v = nh; break;
+            case kSlotHard: v = __ldcg(&C->nscan); break;
             case kSlotWindows: v = __ldcg(&C->windows); break;
             case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
             case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
@@ -120,7 +121,7 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     __syncthreads();
     // Reset the per-call counters for the next call (after every read above).
     if (tid == 0) {
-        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u;
+        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u; C->nscan = 0;
         C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
         C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
         C->status = CT_OK;
@@ -286,9 +287,10 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     if (blockIdx.x == 0 && tid == 0) C->t[3] = gtimer();
 
     const int nh = (int)__ldcg(&C->nhard);
-    if (nh == 0) {
-        // Every value kept its support: CTA 0 publishes, the others are done.
-        if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
+    if (__ldcg(&C->nscan) == 0) {
+        // Every value kept its support or is known unsupported: CTA 0 applies
+        // the removals and publishes, the others are done.
+        if (blockIdx.x == 0) finalize(T, V, dom, sm, nh);
         return;
     }
     // full scan of the hard values

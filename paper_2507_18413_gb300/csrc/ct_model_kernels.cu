@@ -260,9 +260,8 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         for (int u = gwarp; u < totalUnits; u += nwarps) {
             const int k = find_prefix(pU, nwork, u, gpre);
             const TableDev& T = M.tabs[__ldcg(&work[k])];
-            const int nh = (int)__ldcg(&T.ctrl->nhard);
-            if (nh == 0) continue;
-            scan_segment<U, true>(T, u - pre_at(pU, k, gpre), nh, nullptr);
+            if (__ldcg(&T.ctrl->nscan) == 0) continue;
+            scan_segment<U, true>(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
         }
         if (!sync()) return;
         phase(4);
@@ -274,7 +273,8 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             const int nh = (int)__ldcg(&T.ctrl->nhard);
             const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
             for (int m = tid; m < nh; m += kThreads) {
-                const int r = __ldcg(&T.hardRow[m]);
+                int r = __ldcg(&T.hardRow[m]);
+                if (r < 0) r = ~r;  // unsupported without a scan
                 const int fc = __ldcg(&T.foundChunk[m]);
                 if (fc != kNoChunk) {
                     T.residue[r] = fc;
@@ -315,9 +315,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                     Tc->live_state = (int32_t)live;
                     atomicAdd(&C->bytesUpdate, 4ull * __ldcg(&Tc->words_in) * (unsigned long long)(nr + 2));
                 }
-                const unsigned nh = __ldcg(&Tc->nhard);
-                if (nh) atomicAdd(&C->bytesFilter, 16ull * nh * live);
-                Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+                const unsigned ns = (unsigned)__ldcg(&Tc->nscan);
+                if (ns) atomicAdd(&C->bytesFilter, 16ull * ns * live);
+                Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0; Tc->nscan = 0;
             }
             for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
                 const int t = t0 + lane;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         H[kModelHdr + 2 * t] = __ldcg(&Tc->trail_top);
         H[kModelHdr + 2 * t + 1] = __ldcg(&Tc->live_state);
         // leave every table's per-call counters clear
-        Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0;
+        Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0; Tc->nscan = 0;
         Tc->hits = 0; Tc->local_found = 0; Tc->misses = 0; Tc->windows = 0; Tc->trail_added = 0;
         Tc->status = CT_OK;
     }
@@ -385,9 +385,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         H[4] = (int32_t)__ldcg(&C->local);
         H[5] = (int32_t)__ldcg(&C->hard);
         H[6] = (int32_t)__ldcg(&C->windows);
-        // filterDomains bytes as for one table: 16 per residue hit, 512 per window
-        // probed, 16 per live chunk of every full scan
-        const unsigned long long bf = __ldcg(&C->bytesFilter) + 16ull * __ldcg(&C->hits) +
+        // filterDomains bytes as for one table: one word per residue hit, 128
+        // words per window probed, 16 bytes per live chunk of every full scan
+        const unsigned long long bf = __ldcg(&C->bytesFilter) + 4ull * __ldcg(&C->hits) +
                                       512ull * __ldcg(&C->windows);
         const unsigned long long bu = __ldcg(&C->bytesUpdate);
         H[8] = (int32_t)(bu & 0xffffffffull);
