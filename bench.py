@@ -439,10 +439,14 @@ def _bulk_update(C, torch, stream, t, arity, d, seed, reps=5):
             "device_us": prof["device_ms"] * 1e3 / reps, "phase_ns_last": stats["phase_ns"]}
 
 
-def _stream_rate(C, torch, stream, t, calls, seed, opt=None):
+def _stream_rate(C, torch, stream, t, calls, seed, opt=None, shape=None):
     dom_lo, dom_size, tup = G.large_table(seed, t, ARITY, DOM)
     st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, opt=opt, stream=stream)
     C.check(st)
+    if shape is not None:
+        inf = C.ct_get_info(h)[1]
+        shape.update(grid_blocks=inf["grid_blocks"], loads_in_flight=inf["loads_in_flight"],
+                     autotuned=inf["autotuned"])
     off, _ = C.dom_layout(dom_size)
     dom = torch.zeros(int(off[-1]), dtype=torch.int32, device="cuda")
     full = C.masks_to_words([np.ones(x, bool) for x in dom_size])
@@ -649,6 +653,14 @@ def extras(args, C, torch, stream):
                      "currtable_copied_each_call": _stream_rate(C, torch, stream, t, 128, 99 + t,
                                                                 opt=C.make_options(copy_state=1))}
             for t in (100_000, 1_000_000, 4_000_000)}
+        # launch shape chosen by trial propagations at creation against the default rule
+        tuned = {}
+        for t in (100_000, 1_000_000, 4_000_000):
+            d0, d1 = {}, {}
+            r0 = _stream_rate(C, torch, stream, t, 128, 99 + t, shape=d0)
+            r1 = _stream_rate(C, torch, stream, t, 128, 99 + t, opt=C.make_options(autotune=1), shape=d1)
+            tuned[str(t)] = {"default": {"props_per_s": r0, **d0}, "autotuned": {"props_per_s": r1, **d1}}
+        out["autotune_props_per_s"] = tuned
         out["bulk_update_1e6"] = _bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)
         out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
         out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)

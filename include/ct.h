@@ -64,12 +64,18 @@ typedef struct ct_options {
     int32_t profile;          /* 1 = time each kernel with CUDA events (see ct_get_profile) */
     int32_t host_fixpoint;    /* models: 1 = run the fixpoint queue on the host, one launch per table
                                  propagation (default: the whole fixpoint in one launch) */
+    int32_t autotune;         /* 1 = pick the launch shape at creation by timing trial propagations:
+                                 for a table, batches of 16 or 8 row loads in flight (2 or 3 CTAs
+                                 per SM) and the CTA count (segments per CTA); for a model, the CTA
+                                 count of the fixpoint launch (tables and segments per CTA). The
+                                 trials run between a save and a restore, so the state is unchanged.
+                                 Ignored when grid_blocks is set. */
     int32_t copy_state;       /* 1 = ablation of the paper's propagators (Sec. 4: CT_CU^u/^f/^uf copy
                                  _currTable host->device before and device->host after every
                                  propagation): ct_propagate round-trips currTable through a pinned
                                  host copy each call (and ct_restore refreshes it). Results are the
                                  same; only the copies' cost is added. */
-    int32_t reserved[2];
+    int32_t reserved;
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */
@@ -88,6 +94,8 @@ typedef struct ct_table_info {
     int32_t grid_blocks;   /* CTAs of the propagation launch */
     int32_t short_tuples;  /* retained tuples with at least one CT_STAR component */
     int64_t device_bytes;  /* device memory held by the table */
+    int32_t loads_in_flight; /* 16 (2 CTAs per SM) or 8 (3 CTAs per SM) row loads per lane */
+    int32_t autotuned;     /* 1 if the launch shape was chosen by trial propagations */
 } ct_table_info;
 
 /* Figures of the last ct_propagate call (ct_get_call_stats). */

@@ -120,9 +120,71 @@ int batch_setup(ct_model* m) {
     return CT_OK;
 }
 
+int batch_propagate(ct_model* m);
+int popcount_var(const ct_model* m, int v);
+int set_var(ct_model* m, int v, const uint32_t* words);
+
+// CTA count of the fixpoint launch chosen by trial fixpoints (ct_options.autotune):
+// half of the 4 largest domains removed, propagated, restored; best of 3 per candidate.
+int tune_grid(ct_model* m) {
+    const int maxCo = max_coresident_model_blocks();
+    if (maxCo <= 0 || m->tables.empty()) return CT_OK;
+    const int want = m->grid;
+    std::vector<int> cands;
+    for (int g : {want / 4, want / 2, want, 2 * want, maxCo / 2, maxCo}) {
+        g = std::max(1, std::min(g, maxCo));
+        if (std::find(cands.begin(), cands.end(), g) == cands.end()) cands.push_back(g);
+    }
+    std::vector<int> order(m->nvars);
+    for (int v = 0; v < m->nvars; ++v) order[v] = v;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return popcount_var(m, a) > popcount_var(m, b); });
+    double best = 1e30;
+    int bestGrid = want;
+    int st = CT_OK;
+    for (int g : cands) {
+        m->grid = g;
+        double tmin = 1e30;
+        for (int rep = 0; rep < 3 && st == CT_OK; ++rep) {
+            int L = 0;
+            if ((st = ct_model_save(m, &L)) != CT_OK) break;
+            for (int k = 0; k < std::min(4, m->nvars); ++k) {
+                const int v = order[k];
+                std::vector<uint32_t> w(m->h_dom.begin() + m->off[v], m->h_dom.begin() + m->off[v] + m->nw[v]);
+                int seen = 0, keep = std::max(1, popcount_var(m, v) / 2);
+                for (int q = 0; q < m->nw[v]; ++q)
+                    for (int b = 0; b < 32; ++b)
+                        if ((w[q] >> b) & 1u) {
+                            if (seen >= keep) w[q] &= ~(1u << b);
+                            ++seen;
+                        }
+                if ((st = set_var(m, v, w.data())) != CT_OK) break;
+            }
+            const auto t0 = std::chrono::steady_clock::now();
+            const int r = st == CT_OK ? batch_propagate(m) : st;
+            tmin = std::min(tmin, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+            if (r < 0) st = r;
+            const int rr = ct_model_restore(m, L);
+            if (st == CT_OK) st = rr;
+        }
+        if (st != CT_OK) break;
+        if (tmin < best) {
+            best = tmin;
+            bestGrid = g;
+        }
+    }
+    m->grid = st == CT_OK ? bestGrid : want;
+    m->stats = ct_model_stats{};
+    m->propagations = 0;
+    return st;
+}
+
 int batch_propagate(ct_model* m) {
     int st;
-    if (!m->batchReady && (st = batch_setup(m)) != CT_OK) return st;
+    if (!m->batchReady) {
+        if ((st = batch_setup(m)) != CT_OK) return st;
+        if (m->opt.autotune && m->opt.grid_blocks <= 0 && (st = tune_grid(m)) != CT_OK) return st;
+    }
     const int n = (int)m->tables.size();
     int nwork = 0;
     for (int t = 0; t < n; ++t) {

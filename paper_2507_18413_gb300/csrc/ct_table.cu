@@ -88,6 +88,7 @@ struct ct_table {
     uint32_t* d_domScratch = nullptr;
     std::vector<void*> allocs;
     int64_t shortTuples = 0;     // retained tuples with a wildcard
+    bool autotuned = false;      // launch shape chosen by trial propagations
     bool copyState = false;      // ablation: currTable round-trips through h_curr every call
     uint32_t* h_curr = nullptr;  // pinned host copy of currTable (copy_state)
     bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
@@ -857,6 +858,87 @@ int ct_table_changed_words(const ct_table* ct) { return ct->nChW; }
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+
+// Launch-shape autotuner: time trial propagations of every candidate shape
+// (row loads in flight x CTA count) between a save and a restore, keep the
+// fastest. Trials: a delta call (one value of the largest domain removed) and
+// a reset call (every domain cut to a quarter); the score is the sum of their
+// best-of-3 host-observed latencies (launch to published result).
+int autotune(ct_table* ct) {
+    if (ct->empty || ct->R < 1) return CT_OK;
+    const int narrow = ct->localPlan ? 1 : 0;
+    const int base = std::max((ct->nseg + kWarps - 1) / kWarps, (ct->R + 2 * kWarps - 1) / (2 * kWarps));
+    std::vector<std::pair<int, int>> cands;
+    for (int wide = 0; wide < 2; ++wide) {
+        const int var = narrow | (wide ? 2 : 0);
+        const int maxCo = max_coresident_blocks(var);
+        if (maxCo <= 0) continue;
+        for (int g : {base / 4, base / 2, base, 2 * base, maxCo / 2, maxCo}) {
+            g = std::max(1, std::min(g, maxCo));
+            if (std::find(cands.begin(), cands.end(), std::make_pair(var, g)) == cands.end()) cands.push_back({var, g});
+        }
+    }
+    if (cands.empty()) return CT_OK;
+    // trial domains in the table's packed layout
+    std::vector<uint32_t> full((size_t)ct->DW, 0u), delta, reset;
+    int big = 0;
+    for (int i = 0; i < ct->arity; ++i) {
+        for (int a = 0; a < ct->size[i]; ++a) full[(size_t)ct->ld[i] + a / 32] |= 1u << (a % 32);
+        if (ct->size[i] > ct->size[big]) big = i;
+    }
+    delta = full;
+    reset = full;
+    if (ct->size[big] > 1) delta[(size_t)ct->ld[big]] &= ~1u;
+    for (int i = 0; i < ct->arity; ++i) {
+        const int keep = std::max(1, ct->size[i] / 4);
+        for (int a = keep; a < ct->size[i]; ++a) reset[(size_t)ct->ld[i] + a / 32] &= ~(1u << (a % 32));
+    }
+    const int saveVar = ct->variant, saveGrid = ct->grid;
+    const bool saveProfile = ct->profile;
+    ct->profile = false;
+    int L = 0;
+    int st = ct_save(ct, &L);
+    if (st != CT_OK) return st;
+    double best = 1e30;
+    int bestVar = saveVar, bestGrid = saveGrid;
+    for (const auto& c : cands) {
+        ct->variant = c.first;
+        ct->grid = c.second;
+        double score = 0.0;
+        for (const std::vector<uint32_t>* trial : {&delta, &reset}) {
+            double tmin = 1e30;
+            for (int rep = 0; rep < 3 && st == CT_OK; ++rep) {
+                CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, trial->data(), trial->size() * sizeof(uint32_t),
+                                        cudaMemcpyHostToDevice, ct->stream));
+                CT_CUDA(cudaStreamSynchronize(ct->stream));
+                const auto t0 = std::chrono::steady_clock::now();
+                const int r = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, ct->ld.data(), nullptr);
+                const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (r < 0) st = r;
+                tmin = std::min(tmin, dt);
+                if (st == CT_OK && (st = ct_restore(ct, L)) == CT_OK) st = ct_save(ct, &L);
+            }
+            score += tmin;
+        }
+        if (st != CT_OK) break;
+        if (score < best) {
+            best = score;
+            bestVar = c.first;
+            bestGrid = c.second;
+        }
+    }
+    const int rs = ct_restore(ct, L);
+    ct->variant = st == CT_OK ? bestVar : saveVar;
+    ct->grid = st == CT_OK ? bestGrid : saveGrid;
+    ct->profile = saveProfile;
+    ct->prof = ct_profile{};
+    ct->autotuned = st == CT_OK;
+    return st != CT_OK ? st : rs;
+}
+
+}  // namespace
+
 extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
                          int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out) {
     if (!out) {
@@ -891,6 +973,13 @@ extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_si
     if (st < 0) {
         free_table(ct);
         return st;
+    }
+    if (st == CT_OK && opt && opt->autotune && opt->grid_blocks <= 0) {
+        const int at = autotune(ct);
+        if (at < 0) {
+            free_table(ct);
+            return at;
+        }
     }
     *out = ct;
     return st;
@@ -1053,6 +1142,8 @@ extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
     r.local_plan = ct->localPlan ? 1 : 0;
     r.grid_blocks = ct->grid;
     r.short_tuples = (int32_t)std::min<int64_t>(ct->shortTuples, 0x7fffffff);
+    r.loads_in_flight = (ct->variant & 2) ? 8 : 16;
+    r.autotuned = ct->autotuned ? 1 : 0;
     r.device_bytes = ct->deviceBytes;
     int64_t live = 0;
     const int st = ct_get_index(ct, nullptr, &live);

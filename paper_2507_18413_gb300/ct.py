@@ -36,8 +36,8 @@ class CtError(RuntimeError):
 class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("host_fixpoint", ctypes.c_int32), ("copy_state", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("host_fixpoint", ctypes.c_int32), ("autotune", ctypes.c_int32), ("copy_state", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -46,7 +46,7 @@ class ct_table_info(ctypes.Structure):
                 ("seg_capacity", ctypes.c_int32), ("live_chunks", ctypes.c_int64),
                 ("trail_size", ctypes.c_int64), ("depth", ctypes.c_int32),
                 ("local_plan", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("short_tuples", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("loads_in_flight", ctypes.c_int32), ("autotuned", ctypes.c_int32)]
 
 
 class ct_call_stats(ctypes.Structure):
@@ -231,8 +231,9 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0):
     o = ct_options()
+    o.autotune = autotune
     o.host_fixpoint = host_fixpoint
     o.copy_state = copy_state
     o.grid_blocks = grid_blocks

@@ -171,3 +171,13 @@ def test_large_config_search_prefix(mode):
     gm = GpuModel(csp, raw, host_fixpoint=mode)
     _assert_search_equal(gm, csp, node_limit=60)
     gm.close()
+
+
+def test_autotuned_fixpoint_grid_search():
+    """ct_options.autotune picks the fixpoint launch's CTA count with trial
+    fixpoints between a save and a restore: the search is unchanged."""
+    csp, raw = _build(305, nvars=7, ntables=5, arity=3, d=5, t=55)
+    gm = GpuModel(csp, raw, opt=C.make_options(autotune=1))
+    _assert_search_equal(gm, csp)
+    gm.close()
+

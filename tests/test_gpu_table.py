@@ -135,6 +135,21 @@ def test_large_stream_1e5():
     assert seen["delta"] > 0 and seen["reset"] > 0
 
 
+def test_autotuned_launch_shape_gives_the_same_results():
+    """ct_options.autotune times trial propagations at creation (between a save
+    and a restore): the table must start from its creation state and match the
+    oracle on every call."""
+    seen = _large_stream(100_000, calls=100, seed=21, opt=C.make_options(autotune=1))
+    assert seen["delta"] > 0 and seen["reset"] > 0
+    dom_lo, dom_size, tup = G.large_table(21, 100_000)
+    gt = GpuTable(dom_lo, dom_size, tup, opt=C.make_options(autotune=1))
+    assert gt.info["autotuned"] == 1 and gt.info["loads_in_flight"] in (8, 16)
+    assert gt.info["depth"] == 0 and gt.info["trail_size"] == 0
+    w, nz = gt.currtable()
+    assert nz == gt.info["words"]  # every tuple valid again after the trials
+    gt.close()
+
+
 def test_copy_state_ablation_gives_the_same_results():
     """copy_state round-trips currTable through host memory around every call
     (the paper's per-call copies); every call must still match the oracle."""
