@@ -63,11 +63,11 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--case", default="stream",
-                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned", "net512"],
+                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned", "net512", "planning"],
                    help="bulk*: only the one-call bandwidth case (for profiling); "
                         "search: only the plain vs batched search figures; "
                         "learned: the learned-order experiment at full size; "
-                        "net512: the 512-table network fixpoints")
+                        "net512: the 512-table network fixpoints; planning: the planning chains")
     p.add_argument("--learned-eval", type=int, default=200, help="held-out instances of --case learned")
     p.add_argument("--learned-full", type=int, default=10,
                    help="instances at config-4 size (30-60 vars, 40-120 tables) in --case learned")
@@ -603,6 +603,29 @@ def network_extras(C, tuples=(1e3, 1e6), edits=60, seed=3):
             "edit_failures": fails}
 
 
+def planning_extras(C, n_eval=3, n_train=8, node_limit=100_000):
+    """Planning-style chains (256 states x 32 actions, 30 steps, fixed initial and
+    goal states): nodes and time to the first plan with first-fail and with a
+    network trained on other chains, plain and batched (64 slots; the model
+    searches alone for 256 nodes, then the slots take the frontier it leaves,
+    stopping at the first plan any slot finds)."""
+    from paper_2507_18413_gb300 import learn as LN
+    t0 = time.perf_counter()
+    X, y = LN.collect([G.planning_csp(1000 + s) for s in range(n_train)], node_limit=150, slots=64,
+                      max_samples=60_000)
+    net, losses = LN.train(X, y, epochs=20)
+    train_s = time.perf_counter() - t0
+    try:
+        rows = LN.compare([G.planning_csp(s) for s in range(n_eval)], net, node_limit=node_limit, batched=(64, 64))
+    finally:
+        C.ct_mlp_destroy(net)
+    return {"instances": "planning_csp seeds 0..%d: 61 variables (31 states of 256 values, 30 actions of 32), "
+                         "30 transition tables of ~20k tuples" % (n_eval - 1),
+            "train": {"instances": n_train, "samples": int(len(y)), "seconds": round(train_s, 2),
+                      "loss_first_last": [round(float(losses[0]), 5), round(float(losses[-1]), 5)]},
+            "node_limit": node_limit, "per_instance": rows, "summary": LN.summarize(rows)}
+
+
 LEARNED_SMALL = dict(nvars=(20, 30), dom=(8, 16), ntables=(30, 50), arity=(3, 4), tuples=(1e3, 2e4))
 
 
@@ -623,7 +646,7 @@ def learned_extras(C, n_train=40, n_eval=20, node_limit=5000, train_nodes=300, m
     net, losses = LN.train(X, y, epochs=epochs)
     train_s = time.perf_counter() - t0
     try:
-        rows = LN.compare(eval_specs, net, node_limit=node_limit, batched=(64, 6))
+        rows = LN.compare(eval_specs, net, node_limit=node_limit, batched=(64, 64))
         out = {"instances": "learned_csp seeds, 20-30 vars, d 8-16, 30-50 tables of arity 3-4, 1e3-2e4 "
                             "tuples, expected 2^4 solutions (config 4 scaled to instances first-fail "
                             "finishes within the limit)",
@@ -633,7 +656,7 @@ def learned_extras(C, n_train=40, n_eval=20, node_limit=5000, train_nodes=300, m
                "generate_s": round(gen_s, 1), "summary": LN.summarize(rows)}
         if full_eval:
             full = [G.learned_csp(200_000 + s) for s in range(full_eval)]
-            frows = LN.compare(full, net, node_limit=node_limit, batched=(64, 6))
+            frows = LN.compare(full, net, node_limit=node_limit, batched=(64, 64))
             out["config4_full_scale"] = {"instances": full_eval, "summary": LN.summarize(frows)}
     finally:
         C.ct_mlp_destroy(net)
@@ -668,6 +691,7 @@ def extras(args, C, torch, stream):
         out["dfs_plain_first_fail_host_queue"] = _dfs_rate(C, host_fixpoint=1)
         out["search_batched_vs_plain"] = search_extras(C)
         out["learned_order"] = learned_extras(C)
+        out["planning_chain"] = planning_extras(C)
     except Exception as e:  # context figures must not hide the main line
         out["error"] = repr(e)
     return out
@@ -775,6 +799,8 @@ def main():
         stream = torch.cuda.current_stream()
         if args.case == "search":
             print(json.dumps(search_extras(C)))
+        elif args.case == "planning":
+            print(json.dumps(planning_extras(C, n_eval=10)))
         elif args.case == "net512":
             print(json.dumps(network_extras(C)))
         elif args.case == "learned":

@@ -347,7 +347,11 @@ int ct_search_dfs(ct_model* m, int64_t node_limit, int count_all,
  *                nodes before it are finished), so first_solution equals
  *                ct_search_dfs's while nodes and fails can differ; 2: stop at
  *                the first solution any slot finds (no new node is started;
- *                the nodes of that launch still finish)
+ *                the nodes of that launch still finish); in this mode the
+ *                model first searches depth-first alone for up to 4 nodes per
+ *                slot (above split_depth), and the open nodes are the nodes
+ *                at split_depth plus the frontier that search leaves (the node
+ *                it stopped at and every untried right branch above it)
  *   out          host, receives the counters as in ct_search_dfs
  *   first_solution  host int32[nvars] or NULL: the first solution in
  *                depth-first order among those found (with count_all = 1, or

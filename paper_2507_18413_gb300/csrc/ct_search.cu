@@ -326,6 +326,8 @@ struct Search {
     bool hitLimit = false;
     bool stopIssue = false;  // no new node is started (node limit)
     bool splitStop = false;  // the split phase found the first solution it was asked for
+    int64_t splitBudget = 0;   // > 0: the model's share of nodes before the slots take over
+    bool budgetHit = false;
     bool haveBest = false;
     std::vector<uint8_t> bestPath;
     std::vector<int32_t> bestVals;
@@ -384,7 +386,14 @@ struct Search {
 
     // ---- split phase: depth-first on the model itself ----
     int split(int depth, std::vector<uint8_t>& path) {
-        if (depth == splitDepth) {
+        if (depth == splitDepth || budgetHit) {
+            open.push_back(OpenNode{m->h_dom, depth, path});
+            return CT_OK;
+        }
+        if (splitBudget > 0 && info.split_nodes >= splitBudget) {
+            // the model searched its share: this node and every untried right
+            // branch above it (recorded on the way back) go to the slots
+            budgetHit = true;
             open.push_back(OpenNode{m->h_dom, depth, path});
             return CT_OK;
         }
@@ -401,7 +410,6 @@ struct Search {
             st.fails += 1;
             return CT_OK;
         }
-        if (depth == 0 && (r = ensure_copies()) != CT_OK) return r;
         int x = -1;
         if ((r = ct_model_pick_var(m, usePolicy, &x)) != CT_OK) return r;
         if (x < 0) {
@@ -415,6 +423,14 @@ struct Search {
         left[a >> 5] = 1u << (a & 31);
         right[a >> 5] &= ~(1u << (a & 31));
         for (int br = 0; br < 2; ++br) {
+            if (br == 1 && budgetHit) {
+                std::vector<uint32_t> dom = m->h_dom;
+                std::copy(right.begin(), right.end(), dom.begin() + m->off[x]);
+                path.push_back(1);
+                open.push_back(OpenNode{std::move(dom), depth + 1, path});
+                path.pop_back();
+                break;
+            }
             int L = 0;
             int rc = ct_model_save(m, &L);
             if (rc != CT_OK) return rc;
@@ -425,8 +441,11 @@ struct Search {
             const int rr = ct_model_restore(m, L);
             if (rc != CT_OK) return rc;
             if (rr != CT_OK) return rr;
-            if (stopIssue || splitStop) return CT_OK;
+            if (stopIssue || splitStop) break;
         }
+        // Back at the root fixpoint: the slot copies take this state, only when
+        // open nodes are left for them.
+        if (depth == 0 && !open.empty() && !copiesReady) return ensure_copies();
         return CT_OK;
     }
 
@@ -803,6 +822,9 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     S.limit = node_limit;
     S.countAll = count_all == 1;
     S.anyStop = count_all == 2;
+    // any solution: the model first searches alone for 4 nodes per slot; easy
+    // instances end there, the others continue from the frontier it leaves
+    if (S.anyStop) S.splitBudget = 4 * (int64_t)slots;
     S.usePolicy = m->policy != nullptr;
     const int64_t p0 = m->propagations;
     int L0 = 0;

@@ -382,3 +382,37 @@ def network_tables(seed: int, ntables: int = 512, nvars: int = 1024, arity=(2, 8
         csp.tables.append(TableSpec(scope=sc, tuples=tup))
     return csp
 
+
+def planning_csp(seed: int, states: int = 256, actions: int = 32, horizon: int = 30, alternatives=(0, 3)) -> CspSpec:
+    """A planning-style chain: state variables s_0..s_H (domain 0..states-1) and
+    action variables a_0..a_{H-1} (0..actions-1), one transition table
+    T(s_t, a_t, s_{t+1}) per step holding, for every (s, a), its successor plus
+    0-3 alternatives drawn uniformly (the same relation at every step). s_0 is
+    fixed to state 0 and s_H to the end of a seeded random walk of H steps from
+    it, so at least one plan exists. Variables: s_t is t, a_t is H + 1 + t."""
+    rng = Rng(seed)
+    succ = rng.below(states * actions, states).reshape(states, actions)
+    rows = []
+    for st in range(states):
+        for ac in range(actions):
+            nxt = [int(succ[st, ac])]
+            k = alternatives[0] + rng.int(alternatives[1] - alternatives[0] + 1)
+            while len(nxt) < 1 + k:
+                c = rng.int(states)
+                if c not in nxt:
+                    nxt.append(c)
+            rows.extend((st, ac, n) for n in nxt)
+    tup = np.asarray(rows, dtype=np.int32)
+    cur = 0
+    for _ in range(horizon):
+        cur = int(succ[cur, rng.int(actions)])
+    nv = 2 * horizon + 1
+    lo = [0] * nv
+    size = [states] * (horizon + 1) + [actions] * horizon
+    lo[0], size[0] = 0, 1
+    lo[horizon], size[horizon] = cur, 1
+    csp = CspSpec(nvars=nv, dom_lo=lo, dom_size=size)
+    for t in range(horizon):
+        csp.tables.append(TableSpec(scope=[t, horizon + 1 + t, t + 1], tuples=tup))
+    return csp
+

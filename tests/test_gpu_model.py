@@ -181,3 +181,19 @@ def test_autotuned_fixpoint_grid_search():
     _assert_search_equal(gm, csp)
     gm.close()
 
+
+@pytest.mark.parametrize("seed", range(3))
+def test_planning_chain_first_plan(seed):
+    """A small planning chain (16 states, 4 actions, 6 steps): the first plan and
+    the nodes to reach it equal the oracle's first-fail search."""
+    spec = G.planning_csp(seed, states=16, actions=4, horizon=6)
+    csp = O.Csp(spec.dom_lo, spec.dom_size)
+    raw = []
+    for tb in spec.tables:
+        csp.add_table(tb.scope, tb.tuples)
+        raw.append((tb.scope, tb.tuples))
+    gm = GpuModel(csp, raw)
+    got = _assert_search_equal(gm, csp, count_all=False)
+    assert got["solutions"] == 1
+    gm.close()
+
