@@ -164,6 +164,22 @@ typedef struct ct_profile {
  * fails. The first ct_propagate starts from the initial domains, so values
  * already removed by the caller count as removed since the last call.
  */
+/* ct_create_negative: a negative table (the tuples are the FORBIDDEN ones), the
+ * extension of Compact-Table to negative tables that the paper cites (Sec. 1)
+ * but does not evaluate. Arguments as ct_create; duplicate tuples count once,
+ * wildcards are refused. currTable holds the valid forbidden tuples; value a
+ * of scope variable x keeps its support while the valid forbidden tuples with
+ * x = a are fewer than prod_{y != x} |D(y)| (popcount of supports[x,a] AND
+ * currTable, counted only when that product does not exceed the valid
+ * forbidden tuples). A negative table never fails because its currTable is
+ * empty. One ct_propagate is one such filtering pass over the input domains;
+ * unlike a positive table's it is not always a fixpoint (a removal shrinks
+ * the other variables' products): call again until nothing changes (a model
+ * does so). Limits: arity <= 512, <= 2,048 domain words, <= 4,096 values;
+ * CT_ERR_ARG when no tuple is inside the domains. */
+int ct_create_negative(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
+                       int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out);
+
 int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size,
               const int32_t* tuples, int64_t t, const ct_options* opt,
               void* cuda_stream, ct_table** out);
@@ -279,6 +295,12 @@ int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* dom_size,
  * the initial domains (the model then has no solution). */
 int ct_model_add_table(ct_model* m, const int32_t* scope, int arity,
                        const int32_t* tuples, int64_t t);
+
+/* ct_model_add_negative_table: a negative table (see ct_create_negative) over
+ * `scope`. A model holding one propagates with the host queue (one launch per
+ * table propagation; the one-launch fixpoint kernel handles positive tables
+ * only) and refuses ct_search_batch, features and lookahead (CT_ERR_ARG). */
+int ct_model_add_negative_table(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t);
 
 /* ct_model_propagate: run table propagations until no domain changes
  * (fixpoint) or a table fails (CT_INFEASIBLE). */

@@ -116,6 +116,8 @@ struct Smem {
     int32_t k[kLocalMaxArity];      // rows to OR per variable | kCodeDelta
     int32_t rowOff[kLocalMaxArity]; // first code of each variable
     int32_t sup[kLocalMaxArity];    // |dom| > 1
+    int32_t nd[kLocalMaxArity];     // |dom| (local plan)
+    unsigned long long other[kLocalMaxArity];  // negative tables: product of the other domain sizes (saturated)
     int32_t scan[kThreads];
     uint32_t cnt[12];
     int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
@@ -124,7 +126,7 @@ struct Smem {
     int trBase;
 };
 
-enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin };
+enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin, kCntTuples };
 
 // ---------------------------------------------------------------------------
 // plan: Algorithm 1 lines 1-3 and the row selection of Algorithm 2.
@@ -164,6 +166,7 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
             if (domCopy) domCopy[V.ld(i) + q] = dv;
         }
         sup[i] = nd > 1;
+        if (i < kLocalMaxArity) sm.nd[i] = nd;
         if (grow) atomicExch(&sm.flags[0], 1);
         if (nd == 0) atomicExch(&sm.flags[1], 1);
         if (nd > 1) atomicAdd(&sm.flags[5], 1);
@@ -345,6 +348,13 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
     out.w = w;
     out.lp = lp;
     out.cur = cur;
+    if (T.negative) {
+        // negative tables filter by counts: the valid tuples left
+        uint32_t tc = act ? __popc(nv.x) + __popc(nv.y) + __popc(nv.z) + __popc(nv.w) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
+        if (lane == 0 && tc) atomicAdd(&s_cnt[kCntTuples], tc);
+    }
     // The segment's part of the non-zero index: the live chunks after the update.
     const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
     uint32_t words = nzwords(cur);
@@ -570,6 +580,29 @@ __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh,
                 if (lane == 0 && bal) atomicMin(&T.foundChunk[m0 + u], seg * 32 + __ffs(bal) - 1);
             }
         }
+    }
+}
+
+// Negative tables: the valid tuples carrying each hard value, summed over the
+// live chunks of one segment (foundChunk[m] holds the count).
+__device__ __forceinline__ void count_segment(const TableDev& T, int seg, int nh, const int32_t* s_rows) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t mask = __ldcg(&T.segMask[seg]);
+    if (mask == 0u) return;
+    const bool act = (mask >> lane) & 1u;
+    const int w = seg * 32 + lane;
+    const uint4 cur = act ? __ldcg(T.curr + w) : make_uint4(0u, 0u, 0u, 0u);
+    const size_t W4 = (size_t)T.W4;
+    for (int m = 0; m < nh; ++m) {
+        const int r = m < kCodeCap && s_rows ? s_rows[m] : __ldcg(&T.hardRow[m]);
+        uint32_t c = 0u;
+        if (act) {
+            const uint4 v = and4(ld_sup(T.sup + (size_t)r * W4 + w), cur);
+            c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0 && c) atomicAdd(&T.foundChunk[m], (int)c);
     }
 }
 

@@ -85,6 +85,8 @@ struct Ctrl {
     int32_t hits, pruned, trail_added, local_found, misses, windows;
     int32_t live_state;  // live chunks after the last update (kept across calls)
     int32_t nscan;       // per call: hard values that need the full scan (the others are known unsupported)
+    uint32_t tuples;     // per call, negative tables: valid tuples after the update
+    int32_t pad2;
     uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
 };
 
@@ -115,6 +117,7 @@ struct TableDev {
     uint32_t* levelSeg;      // [levelCap][nseg] live masks
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
+    int32_t negative;        // 1: the tuples are forbidden (negative table; one-table kernel only)
     // Scopes of at most kParamArity variables: words, lastDom offset and first
     // supports row of each variable, so that the plan reads no global table.
     int32_t pNW[kParamArity], pLD[kParamArity], pRow0[kParamArity];
@@ -264,6 +267,7 @@ int ct_table_depth(const ct_table* ct);
 void ct_table_adopt_state(ct_table* dst, const ct_table* src);
 int ct_table_live(const ct_table* ct);
 int ct_table_trail_cap(const ct_table* ct);
+int ct_table_is_negative(const ct_table* ct);
 int ct_table_dom_words(const ct_table* ct);
 const int32_t* ct_table_var_ld(const ct_table* ct);
 int ct_table_changed_words(const ct_table* ct);

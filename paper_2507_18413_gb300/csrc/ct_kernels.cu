@@ -59,14 +59,19 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             int r = __ldcg(&T.hardRow[m]);
             if (r < 0) r = ~r;  // unsupported without a scan
             const int fc = __ldcg(&T.foundChunk[m]);
-            if (fc != kNoChunk) {
-                T.residue[r] = fc;
+            // negative tables: fc counts the valid forbidden tuples with the value
+            const bool keep = T.negative ? (unsigned long long)fc < sm.other[T.rowVar[r]] : fc != kNoChunk;
+            if (keep) {
+                if (!T.negative) T.residue[r] = fc;
             } else {
                 // Algorithm 3 line 4: no live tuple carries the value.
                 const int i = T.rowVar[r];
                 const int a = r - V.row0(i);
                 atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
-                atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+                // a positive table's removed value carries no valid tuple, so
+                // lastDom may drop it now; a negative table's value still has
+                // valid forbidden tuples, which the next call removes as Delta
+                if (!T.negative) atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 T.changed[i] = 1;
                 ++pruned;
             }
@@ -121,7 +126,7 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     __syncthreads();
     // Reset the per-call counters for the next call (after every read above).
     if (tid == 0) {
-        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u; C->nscan = 0;
+        C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u; C->nscan = 0; C->tuples = 0u;
         C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
         C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
         C->status = CT_OK;
@@ -169,6 +174,27 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         plan(T, V, dom, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm);
         ok = !(sm.flags[0] || sm.flags[1]);
         nrows = sm.flags[6];
+        if (T.negative && ok) {
+            // every value of x_i is excluded when all prod_{j != i} |D_j| combinations
+            // with it are forbidden: the products, saturated at 2^62
+            if (tid == 0) {
+                const unsigned long long cap = 1ull << 62;
+                auto mul = [&](unsigned long long a, unsigned long long b) {
+                    return (b != 0 && a > cap / b) ? cap : a * b;
+                };
+                unsigned long long pre = 1ull;
+                for (int i = 0; i < T.arity; ++i) {
+                    sm.other[i] = pre;
+                    pre = mul(pre, (unsigned long long)sm.nd[i]);
+                }
+                unsigned long long suf = 1ull;
+                for (int i = T.arity - 1; i >= 0; --i) {
+                    sm.other[i] = mul(sm.other[i], suf);
+                    suf = mul(suf, (unsigned long long)sm.nd[i]);
+                }
+            }
+            __syncthreads();
+        }
         if (blockIdx.x == 0 && tid == 0) {
             C->nval = sm.flags[2]; C->ndelta = sm.flags[3]; C->nreset = sm.flags[4]; C->nsup = sm.flags[5];
             C->nrows = nrows;
@@ -191,7 +217,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     }
     if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
 
-    if (!ok || nrows == 0) {
+    if (!ok || (nrows == 0 && !T.negative)) {
         // Nothing to update: currTable stays as it is. Pending level snapshots
         // of the index are still taken.
         for (int seg = gwarp; seg < T.nseg; seg += nwarps) {
@@ -231,11 +257,13 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             atomicAdd(&C->live_in, sm.cnt[kCntLiveIn]);
             atomicAdd(&C->words_in, sm.cnt[kCntWords]);
             if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
+            if (sm.cnt[kCntTuples]) atomicAdd(&C->tuples, sm.cnt[kCntTuples]);
         }
         if (!grid_sync(C, &sm.flag[0])) return;
         if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
-        // Algorithm 1 line 5: fail when currTable is all zero.
-        if (__ldcg(&C->status) != CT_OK || __ldcg(&C->live) == 0u) {
+        // Algorithm 1 line 5: fail when currTable is all zero (a negative
+        // table with no valid forbidden tuple forbids nothing).
+        if (__ldcg(&C->status) != CT_OK || (!T.negative && __ldcg(&C->live) == 0u)) {
             if (blockIdx.x == 0) {
                 if (tid == 0 && __ldcg(&C->status) == CT_OK) C->status = CT_INFEASIBLE;
                 __syncthreads();
@@ -258,6 +286,23 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
                 for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = dom[V.off(i) + q];
         }
     }
+    if (kLocal && T.negative) {
+        // Negative tables: a value loses its support only when the valid
+        // forbidden tuples carrying it are all prod_{j != i} |D_j| combinations;
+        // values whose product exceeds the valid tuples keep it without a count.
+        const unsigned long long liveT = __ldcg(&C->tuples);
+        for (int r = blockIdx.x * kThreads + tid; r < T.R; r += gridDim.x * kThreads) {
+            const int i = __ldg(&T.rowVar[r]);
+            const int a = r - V.row0(i);
+            const bool present = (sm.dom[V.ld(i) + (a >> 5)] >> (a & 31)) & 1u;
+            if (present && sm.other[i] <= liveT) {
+                const unsigned m = atomicAdd(&C->nhard, 1u);
+                T.hardRow[m] = r;
+                T.foundChunk[m] = 0;
+                atomicAdd(&C->nscan, 1);
+            }
+        }
+    } else
     for (int r = gwarp; r < T.R; r += nwarps) {
         const int i = __ldg(&T.rowVar[r]);
         const int a = r - V.row0(i);
@@ -298,7 +343,11 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         const int staged = min(nh, kCodeCap);
         for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.hardRow[q]);
         __syncthreads();
-        for (int seg = gwarp; seg < T.nseg; seg += nwarps) scan_segment<U>(T, seg, nh, sm.codes);
+        if (T.negative) {
+            for (int seg = gwarp; seg < T.nseg; seg += nwarps) count_segment(T, seg, nh, sm.codes);
+        } else {
+            for (int seg = gwarp; seg < T.nseg; seg += nwarps) scan_segment<U>(T, seg, nh, sm.codes);
+        }
     }
     // last-block-done
     __threadfence();

@@ -284,6 +284,10 @@ namespace {
 // The model's feature view and an up-to-date device copy of every table.
 int ensure_features(ct_model* m) {
     int st;
+    if (m->hasNegative) {
+        ct_set_error("features: not defined for models with negative tables");
+        return CT_ERR_ARG;
+    }
     if (!m->batchReady && (st = batch_setup(m)) != CT_OK) return st;
     const int n = (int)m->tables.size();
     for (int t = 0; t < n; ++t) {
@@ -403,7 +407,21 @@ extern "C" int ct_model_create(int nvars, const int32_t* dom_lo, const int32_t* 
     return CT_OK;
 }
 
+namespace {
+int add_table_impl(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t, bool negative);
+}  // namespace
+
 extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t) {
+    return add_table_impl(m, scope, arity, tuples, t, false);
+}
+
+extern "C" int ct_model_add_negative_table(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples,
+                                           int64_t t) {
+    return add_table_impl(m, scope, arity, tuples, t, true);
+}
+
+namespace {
+int add_table_impl(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t, bool negative) {
     if (!m || !scope || arity < 1 || arity > kMaxArity) {
         ct_set_error("ct_model_add_table: bad argument");
         return CT_ERR_ARG;
@@ -428,8 +446,14 @@ extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, 
         offs[k] = m->off[sc[k]];
     }
     ct_table* tab = nullptr;
-    const int st = ct_create(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab);
+    const int st = negative ? ct_create_negative(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab)
+                            : ct_create(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab);
     if (st < 0) return st;
+    if (negative) {
+        // the one-launch fixpoint kernel handles positive tables only
+        m->hasNegative = true;
+        m->batch = false;
+    }
     int32_t* d_off = nullptr;
     cudaError_t e = cudaMalloc(&d_off, (size_t)arity * sizeof(int32_t));
     if (e == cudaSuccess)
@@ -450,6 +474,7 @@ extern "C" int ct_model_add_table(ct_model* m, const int32_t* scope, int arity, 
     if (st == CT_INFEASIBLE) m->staticInfeasible = true;
     return st;
 }
+}  // namespace
 
 extern "C" int ct_model_propagate(ct_model* m) {
     if (!m) {
@@ -493,11 +518,15 @@ extern "C" int ct_model_propagate(ct_model* m) {
         const uint32_t* newDom = reinterpret_cast<const uint32_t*>(h + kStatusHdr + ct_table_changed_words(tab));
         const int32_t* ld = ct_table_var_ld(tab);
         const std::vector<int>& sc = m->scopes[T];
+        // One pass of a positive table is GAC for it; a negative table's pass is
+        // not (a removal shrinks the other variables' products), so it is
+        // scheduled again by its own removals.
+        const int self = ct_table_is_negative(tab) ? -1 : T;
         for (int k = 0; k < (int)sc.size(); ++k) {
             if (!((changed[k >> 5] >> (k & 31)) & 1u)) continue;
             const int v = sc[k];
             std::memcpy(m->h_dom.data() + m->off[v], newDom + ld[k], (size_t)m->nw[v] * sizeof(uint32_t));
-            mark_var(m, v, T, &q);
+            mark_var(m, v, self, &q);
         }
     }
     return CT_OK;

@@ -803,6 +803,10 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
         ct_set_error("ct_search_batch: the model failed; restore a level first");
         return CT_ERR_STATE;
     }
+    if (m->hasNegative) {
+        ct_set_error("ct_search_batch: models with negative tables search with ct_search_dfs");
+        return CT_ERR_ARG;
+    }
     if (info) std::memset(info, 0, sizeof(*info));
     if (m->tables.empty() || m->staticInfeasible) {
         // nothing to propagate on the device: the plain search is the same search
@@ -864,6 +868,10 @@ extern "C" int ct_model_lookahead(ct_model* m, int slots, float* labels_host) {
     if (m->failed) {
         ct_set_error("ct_model_lookahead: the model failed; restore a level first");
         return CT_ERR_STATE;
+    }
+    if (m->hasNegative) {
+        ct_set_error("ct_model_lookahead: not available for models with negative tables");
+        return CT_ERR_ARG;
     }
     int rc = ct_model_propagate(m);
     if (rc != CT_OK) return rc;

@@ -88,6 +88,7 @@ struct ct_table {
     uint32_t* d_domScratch = nullptr;
     std::vector<void*> allocs;
     int64_t shortTuples = 0;     // retained tuples with a wildcard
+    bool negative = false;       // the tuples are forbidden
     bool autotuned = false;      // launch shape chosen by trial propagations
     bool copyState = false;      // ablation: currTable round-trips through h_curr every call
     uint32_t* h_curr = nullptr;  // pinned host copy of currTable (copy_state)
@@ -218,7 +219,7 @@ void free_table(ct_table* ct) {
 }
 
 int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples, int64_t t,
-          const ct_options* opt) {
+          const ct_options* opt, bool negative) {
     const int n = ct->arity;
     ct->lo.assign(dom_lo, dom_lo + n);
     ct->size.assign(dom_size, dom_size + n);
@@ -263,6 +264,39 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
         }
     }
     ct->shortTuples = nShort;
+    if (negative) {
+        // forbidden tuples: no wildcard, each counted once (the filter compares counts)
+        if (nShort > 0) {
+            ct_set_error("ct_create_negative: wildcards are not allowed in a negative table");
+            return CT_ERR_ARG;
+        }
+        std::vector<std::pair<std::vector<int32_t>, int64_t>> keyed;
+        keyed.reserve(keep.size());
+        for (int64_t j : keep) keyed.push_back({std::vector<int32_t>(tuples + j * n, tuples + j * n + n), j});
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t q = 1; q < keyed.size(); ++q)
+            if (keyed[q].first == keyed[q - 1].first) keyed[q].second = -1 - keyed[q].second;
+        std::vector<int64_t> drop;
+        for (const auto& kv : keyed)
+            if (kv.second < 0) drop.push_back(-1 - kv.second);
+        std::sort(drop.begin(), drop.end());
+        std::vector<int64_t> kept2;
+        kept2.reserve(keep.size());
+        for (int64_t j : keep)
+            if (!std::binary_search(drop.begin(), drop.end(), j)) kept2.push_back(j);
+        keep.swap(kept2);
+        if (keep.empty()) {
+            ct_set_error("ct_create_negative: a negative table needs at least one tuple inside the domains");
+            return CT_ERR_ARG;
+        }
+        if (!(n <= kLocalMaxArity && ct->DW <= kLocalMaxDW && ct->R <= kCodeCap)) {
+            ct_set_error("ct_create_negative: arity <= %d, <= %d domain words and <= %d values", kLocalMaxArity,
+                         kLocalMaxDW, kCodeCap);
+            return CT_ERR_ARG;
+        }
+        ct->negative = true;
+    }
     ct->t = (int64_t)keep.size();
     ct->W = (ct->t + 31) / 32;
     ct->W4 = (ct->W + 3) / 4;
@@ -358,6 +392,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = dalloc(ct, &ct->d_domScratch, (size_t)DW)) != CT_OK) return st;
     d.sup = sup;
     d.supDelta = supDel;
+    d.negative = ct->negative ? 1 : 0;
     d.rowVar = rowVar;
     d.varRow0 = varRow0;
     d.varNW = varNW;
@@ -587,7 +622,8 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         status = c.status == CT_OK ? CT_ERR_TIMEOUT : c.status;
         c.bar_count = 0;
         c.status = CT_OK;
-        c.live = c.live_in = c.words_in = c.nhard = c.done = 0u;
+        c.live = c.live_in = c.words_in = c.nhard = c.done = c.tuples = 0u;
+        c.nscan = 0;
         CT_CUDA(cudaMemcpy(ct->dev.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
         ct->failed = true;
         ct->broken = true;
@@ -939,8 +975,26 @@ int autotune(ct_table* ct) {
 
 }  // namespace
 
+namespace {
+int create_impl(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples, int64_t t,
+                const ct_options* opt, void* cuda_stream, ct_table** out, bool negative);
+}  // namespace
+
 extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
                          int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out) {
+    return create_impl(arity, dom_lo, dom_size, tuples, t, opt, cuda_stream, out, false);
+}
+
+extern "C" int ct_create_negative(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
+                                  int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out) {
+    return create_impl(arity, dom_lo, dom_size, tuples, t, opt, cuda_stream, out, true);
+}
+
+int ct_table_is_negative(const ct_table* ct) { return ct->negative ? 1 : 0; }
+
+namespace {
+int create_impl(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples, int64_t t,
+                const ct_options* opt, void* cuda_stream, ct_table** out, bool negative) {
     if (!out) {
         ct_set_error("ct_create: out is null");
         return CT_ERR_ARG;
@@ -969,7 +1023,7 @@ extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_si
         }
         ct->ownStream = true;
     }
-    const int st = build(ct, dom_lo, dom_size, tuples, t, opt);
+    const int st = build(ct, dom_lo, dom_size, tuples, t, opt, negative);
     if (st < 0) {
         free_table(ct);
         return st;
@@ -984,6 +1038,7 @@ extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_si
     *out = ct;
     return st;
 }
+}  // namespace
 
 extern "C" int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_vars) {
     if (!ct) {

@@ -131,6 +131,9 @@ _SIGS = {
     "ct_search_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
+    "ct_create_negative": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.POINTER(ct_options),
+                                          _P, ctypes.POINTER(_P)]),
+    "ct_model_add_negative_table": (ctypes.c_int, [_P, _I32P, ctypes.c_int, _I32P, ctypes.c_int64]),
     "ct_model_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ct_model_stats)]),
     "ct_model_reset_stats": (ctypes.c_int, [_P]),
     "ct_mlp_create": (ctypes.c_int, [_F32P, _P, ctypes.POINTER(_P)]),
@@ -277,8 +280,9 @@ def words_to_masks(words, dom_size):
 # table
 # --------------------------------------------------------------------------
 
-def ct_create(arity, dom_lo, dom_size, tuples, opt=None, stream=None):
-    """Returns (status, handle). tuples: int32 [t, arity] (host)."""
+def ct_create(arity, dom_lo, dom_size, tuples, opt=None, stream=None, negative=False):
+    """Returns (status, handle). tuples: int32 [t, arity] (host); negative=True
+    makes them the forbidden tuples (ct_create_negative)."""
     L = load()
     lo, plo = _i32(dom_lo)
     sz, psz = _i32(dom_size)
@@ -286,8 +290,9 @@ def ct_create(arity, dom_lo, dom_size, tuples, opt=None, stream=None):
     t = tup.shape[0]
     ptup = tup.ctypes.data_as(_I32P) if t else None
     h = _P()
-    st = L.ct_create(int(arity), plo, psz, ptup, int(t), ctypes.byref(opt) if opt is not None else None,
-                     _stream_ptr(stream), ctypes.byref(h))
+    fn = L.ct_create_negative if negative else L.ct_create
+    st = fn(int(arity), plo, psz, ptup, int(t), ctypes.byref(opt) if opt is not None else None,
+            _stream_ptr(stream), ctypes.byref(h))
     return st, h
 
 
@@ -389,11 +394,12 @@ def ct_model_create(dom_lo, dom_size, opt=None, stream=None):
     return st, h
 
 
-def ct_model_add_table(m, scope, tuples):
+def ct_model_add_table(m, scope, tuples, negative=False):
     sc, psc = _i32(scope)
     tup = np.ascontiguousarray(np.asarray(tuples, dtype=np.int32).reshape(-1, len(sc)))
     ptup = tup.ctypes.data_as(_I32P) if tup.shape[0] else None
-    return load().ct_model_add_table(m, psc, len(sc), ptup, int(tup.shape[0]))
+    fn = load().ct_model_add_negative_table if negative else load().ct_model_add_table
+    return fn(m, psc, len(sc), ptup, int(tup.shape[0]))
 
 
 def ct_model_propagate(m):
