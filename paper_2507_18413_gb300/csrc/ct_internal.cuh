@@ -32,6 +32,7 @@ constexpr int kLocalMaxArity = 512;    // every CTA plans for itself up to this 
 constexpr int kLocalMaxDW = 2048;      // this many domain words and kCodeCap rows
 constexpr int kStatusHdr = 24;         // int32 slots before the changed mask
 constexpr int32_t kNoChunk = 0x7fffffff;
+constexpr int32_t kNoSupport = -2;         // hard-list mark: no live chunk supports the value (no scan needed)
 // Row code of the update plan: supports row | flags.
 constexpr int32_t kCodeLast = 1 << 30;   // last row of its variable: apply the mask
 constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~OR(rows)

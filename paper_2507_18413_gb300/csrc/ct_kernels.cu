@@ -56,11 +56,11 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
-            int r = __ldcg(&T.hardRow[m]);
-            if (r < 0) r = ~r;  // unsupported without a scan
+            const int r = __ldcg(&T.hardRow[m]);
             const int fc = __ldcg(&T.foundChunk[m]);
+            // positive tables: a chunk holding a support, or kNoChunk / kNoSupport;
             // negative tables: fc counts the valid forbidden tuples with the value
-            const bool keep = T.negative ? (unsigned long long)fc < sm.other[T.rowVar[r]] : fc != kNoChunk;
+            const bool keep = T.negative ? (unsigned long long)fc < sm.other[T.rowVar[r]] : (fc >= 0 && fc != kNoChunk);
             if (keep) {
                 if (!T.negative) T.residue[r] = fc;
             } else {
@@ -113,7 +113,7 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
             case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
             case kSlotLocal: v = __ldcg(&C->local_found); break;
-            case kSlotHard: v = __ldcg(&C->nscan); break;
+            case kSlotHard: v = nh; break;
             case kSlotWindows: v = __ldcg(&C->windows); break;
             case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
             case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
@@ -319,7 +319,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
         }
         res = __shfl_sync(0xffffffffu, res, 0);
-        probe_row(T, r, present, res, sr, sm.cnt);
+        probe_row<false>(T, r, present, res, sr, sm.cnt);
     }
     __syncthreads();
     if (tid == 0) {
@@ -332,10 +332,9 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     if (blockIdx.x == 0 && tid == 0) C->t[3] = gtimer();
 
     const int nh = (int)__ldcg(&C->nhard);
-    if (__ldcg(&C->nscan) == 0) {
-        // Every value kept its support or is known unsupported: CTA 0 applies
-        // the removals and publishes, the others are done.
-        if (blockIdx.x == 0) finalize(T, V, dom, sm, nh);
+    if (nh == 0) {
+        // Every value kept its support: CTA 0 publishes, the others are done.
+        if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
         return;
     }
     // full scan of the hard values

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                 const int l = __ffs(miss) - 1;
                 miss &= miss - 1u;
                 const int tl = __shfl_sync(0xffffffffu, t, l);
-                probe_miss(M.tabs[tl], __shfl_sync(0xffffffffu, r, l), __shfl_sync(0xffffffffu, res, l), sm.cnt);
+                probe_miss<true>(M.tabs[tl], __shfl_sync(0xffffffffu, r, l), __shfl_sync(0xffffffffu, res, l), sm.cnt);
             }
         }
         if (!sync()) return;
@@ -273,10 +273,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             const int nh = (int)__ldcg(&T.ctrl->nhard);
             const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
             for (int m = tid; m < nh; m += kThreads) {
-                int r = __ldcg(&T.hardRow[m]);
-                if (r < 0) r = ~r;  // unsupported without a scan
+                const int r = __ldcg(&T.hardRow[m]);
                 const int fc = __ldcg(&T.foundChunk[m]);
-                if (fc != kNoChunk) {
+                if (fc >= 0 && fc != kNoChunk) {  // else kNoChunk / kNoSupport: removed
                     T.residue[r] = fc;
                 } else {
                     const int i = T.rowVar[r];
