@@ -165,7 +165,8 @@ struct ModelCtrl {
     uint32_t local;      // values found in the windows after the residue
     uint32_t hard;       // values left for the full index scan
     uint32_t windows;    // windows probed
-    int32_t pad[4];
+    int32_t nmiss[2];    // residue misses queued in round r, in nmiss[r & 1]
+    int32_t pad[2];
     unsigned long long bytesUpdate;  // algorithmic bytes of updateTable: 4 * words at entry * (rows + 2)
     unsigned long long bytesFilter;  // of the full scans: 16 * hard values * live chunks
 };
@@ -192,6 +193,7 @@ struct ModelDev {
     int32_t nrestores;
     const int32_t* nworkIn;     // null: the count is already in ctrl->nwork
     uint64_t* phaseNs;          // null, or [kModelPhases] nanoseconds added per phase (CTA 0's view)
+    int4* missQ;                // [sum of the tables' rows] residue misses of a round: (table, row, residue)
 };
 constexpr int kModelPhases = 8;  // prologue, plan, update, probe, scan, apply, next round, publish
 constexpr int kRestoreBatch = 256;

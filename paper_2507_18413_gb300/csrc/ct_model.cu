@@ -112,6 +112,7 @@ int batch_setup(ct_model* m) {
         segs += ct_table_dev(tab).nseg;
         rows += ct_table_dev(tab).R;
     }
+    if ((st = m_alloc(m, &M.missQ, (size_t)std::max<int64_t>(rows, 1))) != CT_OK) return st;
     int64_t want = std::max<int64_t>({(int64_t)n, (segs + kWarps - 1) / kWarps, (rows + 2 * kWarps - 1) / (2 * kWarps), 1});
     if (m->opt.grid_blocks > 0) want = m->opt.grid_blocks;
     m->grid = (int)std::min<int64_t>(want, maxCo);

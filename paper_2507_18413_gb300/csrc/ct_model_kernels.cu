@@ -137,8 +137,12 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         const int32_t* work = M.work + (size_t)cur * M.ntables;
         int32_t* pruned = M.prunedBy + (size_t)(round & 1) * M.nvars;       // written by this round
         int32_t* prunedNext = M.prunedBy + (size_t)((round + 1) & 1) * M.nvars;
-        // the collector of the next round's tables was last read two rounds ago
-        if (blockIdx.x == 0 && tid == 0) C->nnext[(round + 1) & 1] = 0;
+        // the collector of the next round's tables was last read two rounds ago,
+        // and so was the other miss counter
+        if (blockIdx.x == 0 && tid == 0) {
+            C->nnext[(round + 1) & 1] = 0;
+            C->nmiss[(round + 1) & 1] = 0;
+        }
 
         // plan (Algorithm 1 lines 1-3), one CTA per table of the round
         for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
@@ -213,9 +217,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                 for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = __ldcg(&M.dom[V.off(i) + q]);
         }
         // filterDomains (Algorithm 3): the residue test of every (table, row) unit,
-        // one unit per lane; a warp then takes its lanes' misses one by one
-        // through the windows after the residue, and what misses there too
-        // goes to the full scan.
+        // one unit per lane; the misses are queued for the whole grid (after a
+        // barrier, one warp per miss searches the live chunks after the
+        // residue), and what misses there too goes to the full scan.
         // rows per warp: up to 32, fewer when that spreads the rows (and their
         // misses) over more warps
         const int rpw = min(32, max(1, (totalRows + nwarps - 1) / nwarps));
@@ -243,14 +247,22 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                     need = !hit;
                 }
             }
-            unsigned miss = __ballot_sync(0xffffffffu, need);
+            const unsigned miss = __ballot_sync(0xffffffffu, need);
             const int nhit = __popc(__ballot_sync(0xffffffffu, hit));
             if (lane == 0 && nhit) atomicAdd(&sm.cnt[kCntHits], (unsigned)nhit);
-            while (miss) {
-                const int l = __ffs(miss) - 1;
-                miss &= miss - 1u;
-                const int tl = __shfl_sync(0xffffffffu, t, l);
-                probe_miss<true>(M.tabs[tl], __shfl_sync(0xffffffffu, r, l), __shfl_sync(0xffffffffu, res, l), sm.cnt);
+            if (miss) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&C->nmiss[round & 1], __popc(miss));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (need) M.missQ[base + __popc(miss & lanemask_lt())] = make_int4(t, r, res, 0);
+            }
+        }
+        if (!sync()) return;
+        {
+            const int nm = __ldcg(&C->nmiss[round & 1]);
+            for (int q = gwarp; q < nm; q += nwarps) {
+                const int4 e = __ldcg(&M.missQ[q]);
+                probe_miss<true>(M.tabs[e.x], e.y, e.z, sm.cnt);
             }
         }
         if (!sync()) return;
@@ -396,6 +408,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         C->hits = C->local = C->hard = C->windows = 0u;
         C->bytesUpdate = 0ull;
         C->bytesFilter = 0ull;
+        C->nmiss[0] = C->nmiss[1] = 0;
         C->status = CT_OK;
         C->rounds = 0;
         C->props = 0;

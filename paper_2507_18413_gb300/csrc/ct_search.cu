@@ -273,6 +273,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
         segs += ct_table_dev(tab).nseg;
         rows += ct_table_dev(tab).R;
     }
+    if ((st = b_alloc(b, &M.missQ, (size_t)std::max<int64_t>(B * rows, 1))) != CT_OK) return st;
     int64_t want = std::max<int64_t>({(int64_t)n, B * ((segs + kWarps - 1) / kWarps),
                                       B * ((rows + 2 * kWarps - 1) / (2 * kWarps)), 1});
     if (m->opt.grid_blocks > 0) want = m->opt.grid_blocks;
