@@ -108,7 +108,14 @@ __global__ void ct_counts_kernel(const FeatArgs A) {
                 if (r < T.R) {
                     const int i = __ldg(&T.rowVar[r]);
                     const int a = r - __ldg(&T.varRow0[i]);
-                    const bool present = (A.dom[__ldg(&sOff[i]) + (a >> 5)] >> (a & 31)) & 1u;
+                    const uint32_t* dv = A.dom + __ldg(&sOff[i]);
+                    bool present = (dv[a >> 5] >> (a & 31)) & 1u;
+                    if (present) {
+                        // a fixed variable's features are zero: its rows need no count
+                        int sz = 0;
+                        for (int q = 0, nw = __ldg(&T.varNW[i]); q < nw && sz < 2; ++q) sz += __popc(dv[q]);
+                        present = sz > 1;
+                    }
                     if (present && act) {
                         const uint4 s = __ldg(T.sup + (size_t)r * W4 + w);
                         n[j] = popc4(make_uint4(s.x & cur.x, s.y & cur.y, s.z & cur.z, s.w & cur.w));
