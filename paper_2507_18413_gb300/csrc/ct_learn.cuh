@@ -21,7 +21,7 @@ constexpr int kTrainBatch = 128;  // largest training batch (one CTA holds it in
 struct FeatView {
     // static, built once
     int32_t* rowBase = nullptr;   // [nt + 1] prefix of the tables' supports rows
-    int32_t* unitBase = nullptr;  // [nt + 1] prefix of the tables' segments
+    int32_t* unitBase = nullptr;  // [nt + 1] prefix of segments x scope domain words per table
     int32_t* adjBase = nullptr;   // [nv + 1] tables holding each variable
     int2* adj = nullptr;          // (table, scope position)
     int32_t* varOff = nullptr;    // [nv] word offset of each domain
