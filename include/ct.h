@@ -328,6 +328,9 @@ typedef struct ct_model_stats {
     int64_t update_bytes;
     int64_t filter_bytes;
     double wait_seconds;   /* host time from each launch to its published result */
+    double phase_seconds[8]; /* with ct_options.profile: fixpoint kernel time by phase, as in
+                                ct_batch_info (prologue, plan, updateTable, residue probes,
+                                index scans, removals, next-round selection, publication) */
 } ct_model_stats;
 int ct_model_get_stats(ct_model* m, ct_model_stats* out);
 int ct_model_reset_stats(ct_model* m);

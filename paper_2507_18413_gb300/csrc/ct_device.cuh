@@ -441,17 +441,21 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
     return pos;
 }
 
+// Outcomes of the window search of a residue miss.
+enum { kProbeFound = 1, kProbeGone = 0, kProbeUndecided = -1 };
+
 // A value whose residue missed (whole warp, r and res uniform): Algorithm 3's
 // search for a support over the live chunks (the non-zero index) that follow
-// the residue in cyclic order, 32 chunks per window, at most kLocalProbes
-// windows over at most kWindowGroups x 32 index segments. Found: the residue
-// moves there. Not found with every live chunk tested: the value has no
-// support and goes to the hard list marked kNoSupport (removed without a
-// scan). Else it goes to the hard list for the full scan. (Measured against windows of
-// the chunks that follow the residue, dead or alive: the same on the dense
-// bench stream, 8-10% more search nodes per second in the batched search.)
+// the residue in cyclic order (kLive), 32 chunks per window, at most
+// kLocalProbes windows over at most kWindowGroups x 32 index segments; without
+// kLive, the chunks that follow the residue, dead or alive. Found: the residue
+// moves there (kProbeFound). Not found with every live chunk tested: the value
+// has no support (kProbeGone). Else kProbeUndecided: a full scan decides.
+// (Measured against windows of the chunks that follow the residue, dead or
+// alive: the same on the dense bench stream, 8-10% more search nodes per
+// second in the batched search.)
 template <bool kLive>
-__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
+__device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     bool complete = false;
@@ -470,7 +474,7 @@ __device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, ui
                     T.residue[r] = cf;
                     atomicAdd(&s_cnt[kCntLocal], 1u);
                 }
-                return;
+                return kProbeFound;
             }
         }
     } else if (T.useResidues) {
@@ -538,15 +542,25 @@ __device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, ui
                         T.residue[r] = cf;
                         atomicAdd(&s_cnt[kCntLocal], 1u);
                     }
-                    return;
+                    return kProbeFound;
                 }
             }
         }
     }
-    if (lane == 0) {
+    return complete ? kProbeGone : kProbeUndecided;
+}
+
+// A residue miss searched by probe_windows; a value not found goes to the
+// hard list, marked kNoSupport when it has no support (removed without a
+// scan; a scan keeps the mark, atomicMin), else for the full scan.
+template <bool kLive>
+__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
+    const int o = probe_windows<kLive>(T, r, res, s_cnt);
+    if (o != kProbeFound && (threadIdx.x & 31) == 0) {
+        const bool complete = o == kProbeGone;
         const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
         T.hardRow[m] = r;
-        T.foundChunk[m] = complete ? kNoSupport : kNoChunk;  // a scan keeps kNoSupport (atomicMin)
+        T.foundChunk[m] = complete ? kNoSupport : kNoChunk;
         if (!complete) {
             atomicAdd(&T.ctrl->nscan, 1);
             atomicAdd(&s_cnt[kCntMiss], 1u);

@@ -166,7 +166,7 @@ struct ModelCtrl {
     uint32_t hard;       // values left for the full index scan
     uint32_t windows;    // windows probed
     int32_t nmiss[2];    // residue misses queued in round r, in nmiss[r & 1]
-    int32_t pad[2];
+    int32_t nscanAll[2]; // values of round r left for full scans, in nscanAll[r & 1]
     unsigned long long bytesUpdate;  // algorithmic bytes of updateTable: 4 * words at entry * (rows + 2)
     unsigned long long bytesFilter;  // of the full scans: 16 * hard values * live chunks
 };

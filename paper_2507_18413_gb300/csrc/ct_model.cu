@@ -113,6 +113,10 @@ int batch_setup(ct_model* m) {
         rows += ct_table_dev(tab).R;
     }
     if ((st = m_alloc(m, &M.missQ, (size_t)std::max<int64_t>(rows, 1))) != CT_OK) return st;
+    if (m->opt.profile) {
+        if ((st = m_alloc(m, &M.phaseNs, kModelPhases)) != CT_OK) return st;
+        CT_CUDA(cudaMemsetAsync(M.phaseNs, 0, kModelPhases * sizeof(uint64_t), m->stream));
+    }
     int64_t want = std::max<int64_t>({(int64_t)n, (segs + kWarps - 1) / kWarps, (rows + 2 * kWarps - 1) / (2 * kWarps), 1});
     if (m->opt.grid_blocks > 0) want = m->opt.grid_blocks;
     m->grid = (int)std::min<int64_t>(want, maxCo);
@@ -796,6 +800,12 @@ extern "C" int ct_model_get_stats(ct_model* m, ct_model_stats* out) {
         return CT_ERR_ARG;
     }
     *out = m->stats;
+    if (m->batchReady && m->md.phaseNs) {
+        uint64_t ns[kModelPhases];
+        CT_CUDA(cudaMemcpyAsync(ns, m->md.phaseNs, sizeof(ns), cudaMemcpyDeviceToHost, m->stream));
+        CT_CUDA(cudaStreamSynchronize(m->stream));
+        for (int p = 0; p < kModelPhases; ++p) out->phase_seconds[p] = 1e-9 * (double)ns[p];
+    }
     return CT_OK;
 }
 
@@ -805,6 +815,8 @@ extern "C" int ct_model_reset_stats(ct_model* m) {
         return CT_ERR_ARG;
     }
     m->stats = ct_model_stats{};
+    if (m->batchReady && m->md.phaseNs)
+        CT_CUDA(cudaMemsetAsync(m->md.phaseNs, 0, kModelPhases * sizeof(uint64_t), m->stream));
     return CT_OK;
 }
 

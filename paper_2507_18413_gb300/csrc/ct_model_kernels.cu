@@ -72,6 +72,19 @@ __device__ void block_prefix(const int32_t* work, int n, F val, int32_t* out, Sm
     __syncthreads();
 }
 
+// Value r of table t has no support: clear it from the shared domains and the
+// table's lastDom, and mark its variable as pruned by t (-2: by several tables).
+__device__ __forceinline__ void remove_value(const ModelDev& M, const TableDev& T, int t, int r, int32_t* pruned) {
+    const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+    const int i = T.rowVar[r];
+    const int a = r - V.row0(i);
+    atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+    const int v = M.scopeVar[M.scopeBase[t] + i];
+    const int old = atomicCAS(&pruned[v], -1, t);
+    if (old != -1 && old != t) atomicExch(&pruned[v], -2);
+}
+
 template <int U>
 __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_constant__ ModelDev M) {
     __shared__ Smem sm;
@@ -142,6 +155,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         if (blockIdx.x == 0 && tid == 0) {
             C->nnext[(round + 1) & 1] = 0;
             C->nmiss[(round + 1) & 1] = 0;
+            C->nscanAll[(round + 1) & 1] = 0;
         }
 
         // plan (Algorithm 1 lines 1-3), one CTA per table of the round
@@ -258,47 +272,56 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             }
         }
         if (!sync()) return;
-        {
-            const int nm = __ldcg(&C->nmiss[round & 1]);
-            for (int q = gwarp; q < nm; q += nwarps) {
-                const int4 e = __ldcg(&M.missQ[q]);
-                probe_miss<true>(M.tabs[e.x], e.y, e.z, sm.cnt);
-            }
-        }
-        if (!sync()) return;
-        phase(3);
-
-        // full scans of the values whose residues and windows missed
-        for (int u = gwarp; u < totalUnits; u += nwarps) {
-            const int k = find_prefix(pU, nwork, u, gpre);
-            const TableDev& T = M.tabs[__ldcg(&work[k])];
-            if (__ldcg(&T.ctrl->nscan) == 0) continue;
-            scan_segment<U, true>(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
-        }
-        if (!sync()) return;
-        phase(4);
-
-        // Algorithm 3 line 4: remove the values no live tuple carries
-        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
-            const int t = __ldcg(&work[k]);
-            const TableDev& T = M.tabs[t];
-            const int nh = (int)__ldcg(&T.ctrl->nhard);
-            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
-            for (int m = tid; m < nh; m += kThreads) {
-                const int r = __ldcg(&T.hardRow[m]);
-                const int fc = __ldcg(&T.foundChunk[m]);
-                if (fc >= 0 && fc != kNoChunk) {  // else kNoChunk / kNoSupport: removed
-                    T.residue[r] = fc;
+        // One warp per queued miss. A value left without support after every
+        // live chunk was tested is removed here; the undecided ones go to the
+        // hard lists for the full scan. Rounds without a miss skip the probe
+        // phase's barrier, rounds without a scan the scan and removal phases.
+        const int nm = __ldcg(&C->nmiss[round & 1]);
+        for (int q = gwarp; q < nm; q += nwarps) {
+            const int4 e = __ldcg(&M.missQ[q]);
+            const TableDev& T = M.tabs[e.x];
+            const int o = probe_windows<true>(T, e.y, e.z, sm.cnt);
+            if (o != kProbeFound && lane == 0) {
+                if (o == kProbeGone) {
+                    remove_value(M, T, e.x, e.y, pruned);
                 } else {
-                    const int i = T.rowVar[r];
-                    const int a = r - V.row0(i);
-                    atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
-                    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
-                    const int v = M.scopeVar[M.scopeBase[t] + i];
-                    const int old = atomicCAS(&pruned[v], -1, t);
-                    if (old != -1 && old != t) atomicExch(&pruned[v], -2);
+                    const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
+                    T.hardRow[m] = e.y;
+                    T.foundChunk[m] = kNoChunk;
+                    atomicAdd(&T.ctrl->nscan, 1);
+                    atomicAdd(&sm.cnt[kCntMiss], 1u);
+                    atomicAdd(&C->nscanAll[round & 1], 1);
                 }
             }
+        }
+        if (nm > 0 && !sync()) return;
+        phase(3);
+
+        if (nm > 0 && __ldcg(&C->nscanAll[round & 1]) > 0) {
+            // full scans of the values whose residues and windows missed
+            for (int u = gwarp; u < totalUnits; u += nwarps) {
+                const int k = find_prefix(pU, nwork, u, gpre);
+                const TableDev& T = M.tabs[__ldcg(&work[k])];
+                if (__ldcg(&T.ctrl->nscan) == 0) continue;
+                scan_segment<U, true>(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
+            }
+            if (!sync()) return;
+            phase(4);
+
+            // Algorithm 3 line 4: remove the values no live tuple carries
+            for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
+                const int t = __ldcg(&work[k]);
+                const TableDev& T = M.tabs[t];
+                const int nh = (int)__ldcg(&T.ctrl->nhard);
+                for (int m = tid; m < nh; m += kThreads) {
+                    const int r = __ldcg(&T.hardRow[m]);
+                    const int fc = __ldcg(&T.foundChunk[m]);
+                    if (fc >= 0 && fc != kNoChunk) T.residue[r] = fc;
+                    else remove_value(M, T, t, r, pruned);
+                }
+            }
+            if (!sync()) return;
+            phase(5);
         }
         __syncthreads();
         if (tid == 0) {
@@ -308,8 +331,6 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             if (sm.cnt[kCntWin]) atomicAdd(&C->windows, sm.cnt[kCntWin]);
             sm.cnt[kCntHits] = sm.cnt[kCntLocal] = sm.cnt[kCntMiss] = sm.cnt[kCntWin] = 0u;
         }
-        if (!sync()) return;
-        phase(5);
 
         // next round (whole grid): every table of a live node that shares a
         // variable another table pruned; the other parity's marks are cleared
@@ -409,6 +430,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         C->bytesUpdate = 0ull;
         C->bytesFilter = 0ull;
         C->nmiss[0] = C->nmiss[1] = 0;
+        C->nscanAll[0] = C->nscanAll[1] = 0;
         C->status = CT_OK;
         C->rounds = 0;
         C->props = 0;

@@ -76,7 +76,8 @@ class ct_search_stats(ctypes.Structure):
 class ct_model_stats(ctypes.Structure):
     _fields_ = [("fixpoints", ctypes.c_int64), ("rounds", ctypes.c_int64), ("propagations", ctypes.c_int64),
                 ("residue_hits", ctypes.c_int64), ("window_hits", ctypes.c_int64), ("hard_values", ctypes.c_int64),
-                ("update_bytes", ctypes.c_int64), ("filter_bytes", ctypes.c_int64), ("wait_seconds", ctypes.c_double)]
+                ("update_bytes", ctypes.c_int64), ("filter_bytes", ctypes.c_int64), ("wait_seconds", ctypes.c_double),
+                ("phase_seconds", ctypes.c_double * 8)]
 
 
 class ct_batch_info(ctypes.Structure):
