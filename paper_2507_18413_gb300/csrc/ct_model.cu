@@ -37,6 +37,19 @@ int m_alloc(ct_model* m, T** p, size_t n) {
     return CT_OK;
 }
 
+// The device domains made equal to the host copy when a set or a restore
+// changed the host copy since the last upload (synchronous: the staging
+// buffer is free again on return).
+int sync_dom(ct_model* m) {
+    if (!m->domStale) return CT_OK;
+    std::memcpy(m->h_stage, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t));
+    CT_CUDA(cudaMemcpyAsync(m->d_dom, m->h_stage, (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            m->stream));
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    m->domStale = false;
+    return CT_OK;
+}
+
 // Device descriptors of the network for the one-launch fixpoint (built once,
 // after the last table was added).
 int batch_setup(ct_model* m) {
@@ -54,11 +67,23 @@ int batch_setup(ct_model* m) {
     int32_t *dBase, *dOff, *dVar, *dPruned, *dNode;
     ModelCtrl* dCtrl;
     if ((st = m_alloc(m, &m->d_tabs, n)) != CT_OK) return st;
-    if ((st = m_alloc(m, &m->d_calls, n)) != CT_OK) return st;
+    // One block, its head copied at once per launch: [count, 3 pad | calls[n] |
+    // domains[DWg] | work[2][n]]; the domains move into it.
+    const size_t blkWords = 4 + 4 * (size_t)n + (size_t)m->DWg + 2 * (size_t)n;
+    static_assert(sizeof(ModelTabCall) == 4 * sizeof(int32_t), "ModelTabCall is four words");
+    if ((st = m_alloc(m, &m->d_blk, blkWords)) != CT_OK) return st;
+    m->d_calls = reinterpret_cast<ModelTabCall*>(m->d_blk + 4);
+    uint32_t* blkDom = reinterpret_cast<uint32_t*>(m->d_blk + 4 + 4 * (size_t)n);
+    if ((st = sync_dom(m)) != CT_OK) return st;
+    CT_CUDA(cudaMemcpyAsync(blkDom, m->d_dom, (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyDeviceToDevice, m->stream));
+    CT_CUDA(cudaStreamSynchronize(m->stream));
+    cudaFree(m->d_dom);
+    m->d_dom = blkDom;
+    m->domInBlk = true;
     if ((st = m_alloc(m, &dBase, n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &dOff, off.size())) != CT_OK) return st;
     if ((st = m_alloc(m, &dVar, var.size())) != CT_OK) return st;
-    if ((st = m_alloc(m, &M.work, 2 * (size_t)n)) != CT_OK) return st;
+    M.work = m->d_blk + 4 + 4 * (size_t)n + m->DWg;
     if ((st = m_alloc(m, &M.unitPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &M.rowPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &dPruned, 2 * (size_t)m->nvars)) != CT_OK) return st;
@@ -74,8 +99,7 @@ int batch_setup(ct_model* m) {
     }
     CT_CUDA(cudaMemsetAsync(dPruned, 0xff, 2 * (size_t)m->nvars * 4, m->stream));
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), m->stream));
-    if (cudaHostAlloc((void**)&m->h_calls, std::max(n, 1) * sizeof(ModelTabCall), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&m->h_work, (size_t)(n + 1) * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+    if (cudaHostAlloc((void**)&m->h_blk, blkWords * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg + nnodes) * sizeof(int32_t),
                       cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
@@ -84,8 +108,11 @@ int batch_setup(ct_model* m) {
     }
     int32_t* dStatus = nullptr;
     CT_CUDA(cudaHostGetDevicePointer((void**)&dStatus, m->h_mstatus, 0));
+    m->h_calls = reinterpret_cast<ModelTabCall*>(m->h_blk + 4);
+    m->h_list = m->h_blk + 4 + 4 * (size_t)n + m->DWg;
     M.tabs = m->d_tabs;
     M.calls = m->d_calls;
+    M.nworkIn = m->d_blk;
     M.scopeBase = dBase;
     M.scopeOff = dOff;
     M.scopeVar = dVar;
@@ -194,7 +221,7 @@ int batch_propagate(ct_model* m) {
     int nwork = 0;
     for (int t = 0; t < n; ++t) {
         if ((st = ct_table_batch_prepare(m->tables[t], &m->h_calls[t])) != CT_OK) return st;
-        if (m->dirty[t]) m->h_work[1 + nwork++] = t;
+        if (m->dirty[t]) m->h_list[nwork++] = t;
     }
     if (nwork == 0) return CT_OK;
     // device copies of the tables whose buffers moved (trail or level growth)
@@ -206,11 +233,13 @@ int batch_propagate(ct_model* m) {
             m->tabVersion[t] = v;
         }
     }
-    m->h_work[0] = nwork;
-    CT_CUDA(cudaMemcpyAsync(m->d_calls, m->h_calls, (size_t)n * sizeof(ModelTabCall), cudaMemcpyHostToDevice, m->stream));
-    CT_CUDA(cudaMemcpyAsync(m->md.work, m->h_work + 1, (size_t)nwork * sizeof(int32_t), cudaMemcpyHostToDevice,
-                            m->stream));
-    CT_CUDA(cudaMemcpyAsync(&m->md.ctrl->nwork, m->h_work, sizeof(int32_t), cudaMemcpyHostToDevice, m->stream));
+    // count, calls, domains (the host copy is authoritative) and the first
+    // round's tables in one copy
+    m->h_blk[0] = nwork;
+    std::memcpy(m->h_blk + 4 + 4 * (size_t)n, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t));
+    CT_CUDA(cudaMemcpyAsync(m->d_blk, m->h_blk, (4 + 4 * (size_t)n + (size_t)m->DWg + (size_t)nwork) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, m->stream));
+    m->domStale = false;
     volatile int32_t* H = m->h_mstatus;
     H[0] = kNoChunk;
     const auto t0 = std::chrono::steady_clock::now();
@@ -272,10 +301,12 @@ void mark_var(ct_model* m, int v, int except, std::deque<int>* q) {
     }
 }
 
-// Replace the domain of variable v (host mirror and device), scheduling its tables.
+// Replace the domain of variable v, scheduling its tables. The host copy is
+// authoritative; the device copy follows with the next fixpoint launch (or
+// sync_dom).
 int set_var(ct_model* m, int v, const uint32_t* words) {
     std::memcpy(m->h_dom.data() + m->off[v], words, (size_t)m->nw[v] * sizeof(uint32_t));
-    CT_CUDA(launch_set_words(m->d_dom + m->off[v], words, m->nw[v], m->stream));
+    m->domStale = true;
     mark_var(m, v, -1, nullptr);
     return CT_OK;
 }
@@ -331,6 +362,7 @@ int ct_model_pick_var(ct_model* m, bool usePolicy, int* x) {
         for (int v = 0; v < m->nvars && !any; ++v) any = popcount_var(m, v) > 1;
         if (!any) return CT_OK;
         int st = ensure_features(m);
+        if (st == CT_OK) st = sync_dom(m);
         if (st == CT_OK) st = ct_feat_compute(m->fview, m->d_tabs, m->d_dom, nullptr, m->stream);
         if (st == CT_OK) st = ct_feat_scores(m->fview, m->policy, m->stream);
         if (st != CT_OK) return st;
@@ -501,6 +533,7 @@ extern "C" int ct_model_propagate(ct_model* m) {
         }
     }
     if (m->batch && (int)m->tables.size() <= kModelMaxTables) return batch_propagate(m);
+    if (const int sst = sync_dom(m); sst != CT_OK) return sst;
     std::deque<int> q;
     for (int T = 0; T < (int)m->tables.size(); ++T)
         if (m->dirty[T]) q.push_back(T);
@@ -630,12 +663,9 @@ extern "C" int ct_model_restore(ct_model* m, int level) {
         }
     }
     CT_CUDA(launch_restore_batch(m->d_tabs, B, m->stream));
-    // The host copy is authoritative: send it back through the pinned stage
-    // (stream-ordered before any later kernel of the model).
+    // The host copy is authoritative; the device copy follows lazily.
     m->h_dom = m->levels[level].dom;
-    std::memcpy(m->h_stage, m->h_dom.data(), (size_t)m->DWg * sizeof(uint32_t));
-    CT_CUDA(cudaMemcpyAsync(m->d_dom, m->h_stage, (size_t)m->DWg * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                            m->stream));
+    m->domStale = true;
     m->dirty = m->levels[level].dirty;
     m->levels.resize(level);
     m->failed = false;
@@ -786,6 +816,7 @@ extern "C" int ct_model_features(ct_model* m, float* features_host) {
         return CT_ERR_STATE;
     }
     int st = ensure_features(m);
+    if (st == CT_OK) st = sync_dom(m);
     if (st == CT_OK) st = ct_feat_compute(m->fview, m->d_tabs, m->d_dom, nullptr, m->stream);
     if (st != CT_OK) return st;
     CT_CUDA(cudaMemcpyAsync(features_host, m->fview->feat, (size_t)m->nvars * kNF * sizeof(float),
@@ -850,11 +881,10 @@ extern "C" int ct_model_destroy(ct_model* m) {
     }
     for (ct_table* t : m->tables) ct_destroy(t);
     for (int32_t* p : m->d_tabOff) cudaFree(p);
-    if (m->d_dom) cudaFree(m->d_dom);
+    if (m->d_dom && !m->domInBlk) cudaFree(m->d_dom);
     if (m->h_stage) cudaFreeHost(m->h_stage);
     for (void* p : m->allocs) cudaFree(p);
-    if (m->h_calls) cudaFreeHost(m->h_calls);
-    if (m->h_work) cudaFreeHost(m->h_work);
+    if (m->h_blk) cudaFreeHost(m->h_blk);
     if (m->h_mstatus) cudaFreeHost(m->h_mstatus);
     if (m->ownStream && m->stream) cudaStreamDestroy(m->stream);
     cudaGetLastError();

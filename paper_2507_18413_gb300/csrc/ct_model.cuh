@@ -24,7 +24,9 @@ struct ct_model {
         std::vector<char> dirty;
     };
     std::vector<Level> levels;
-    uint32_t* h_stage = nullptr;  // pinned staging of the domains copied back on restore
+    uint32_t* h_stage = nullptr;  // pinned staging of the domains (sync_dom)
+    bool domStale = false;        // h_dom changed since the device copy was written
+    bool domInBlk = false;        // d_dom lives in d_blk
     cudaStream_t stream = nullptr;
     bool ownStream = false;
     ct_options opt{};
@@ -37,9 +39,11 @@ struct ct_model {
     bool batchReady = false;
     ctk::ModelDev md{};
     ctk::TableDev* d_tabs = nullptr;
-    ctk::ModelTabCall* d_calls = nullptr;
-    ctk::ModelTabCall* h_calls = nullptr;  // pinned
-    int32_t* h_work = nullptr;        // pinned: [0] = count, then the tables
+    int32_t* d_blk = nullptr;         // [count, 3 pad | calls[n] | work[2][n]]
+    int32_t* h_blk = nullptr;         // pinned mirror of d_blk's head (count, calls, first work list)
+    ctk::ModelTabCall* d_calls = nullptr;  // in d_blk
+    ctk::ModelTabCall* h_calls = nullptr;  // in h_blk
+    int32_t* h_list = nullptr;        // in h_blk: the first round's tables
     int32_t* h_mstatus = nullptr;     // mapped pinned
     std::vector<int> tabVersion;
     std::vector<void*> allocs;

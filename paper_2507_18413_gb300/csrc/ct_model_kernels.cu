@@ -47,28 +47,56 @@ __device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u, boo
     return lo + (31 - __clz(b));
 }
 
-// Exclusive prefix of val(work[k]) over k < n into out[0..n] (one CTA).
-template <typename F>
-__device__ void block_prefix(const int32_t* work, int n, F val, int32_t* out, Smem& sm) {
-    const int tid = threadIdx.x;
+// Exclusive prefixes of the segments and of the supports rows of work[k] over
+// k < n into unitOut[0..n] and rowOut[0..n] (one CTA): each thread sums a run
+// of entries, warps scan by shuffles, warp totals go through shared memory.
+__device__ void work_prefix(const ModelDev& M, const int32_t* work, int n, int32_t* unitOut, int32_t* rowOut,
+                            Smem& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n + kThreads - 1) / kThreads;
     const int b0 = tid * per, b1 = min(n, b0 + per);
-    int sum = 0;
-    for (int k = b0; k < b1; ++k) sum += val(__ldcg(&work[k]));
-    sm.scan[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < kThreads; off <<= 1) {
-        const int a = tid >= off ? sm.scan[tid - off] : 0;
-        __syncthreads();
-        sm.scan[tid] += a;
-        __syncthreads();
-    }
-    int run = sm.scan[tid] - sum;
+    int su = 0, sr = 0;
     for (int k = b0; k < b1; ++k) {
-        out[k] = run;
-        run += val(__ldcg(&work[k]));
+        const TableDev& T = M.tabs[__ldcg(&work[k])];
+        su += T.nseg;
+        sr += T.R;
     }
-    if (tid == kThreads - 1) out[n] = sm.scan[kThreads - 1];
+    int iu = su, ir = sr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, iu, o);
+        const int c = __shfl_up_sync(0xffffffffu, ir, o);
+        if (lane >= o) {
+            iu += a;
+            ir += c;
+        }
+    }
+    if (lane == 31) {
+        sm.scan[warp] = iu;
+        sm.scan[kWarps + warp] = ir;
+    }
+    __syncthreads();
+    int ru = iu - su, rr = ir - sr, tu = 0, tr = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        const int wu = sm.scan[w], wr = sm.scan[kWarps + w];
+        if (w < warp) {
+            ru += wu;
+            rr += wr;
+        }
+        tu += wu;
+        tr += wr;
+    }
+    for (int k = b0; k < b1; ++k) {
+        const TableDev& T = M.tabs[__ldcg(&work[k])];
+        unitOut[k] = ru;
+        rowOut[k] = rr;
+        ru += T.nseg;
+        rr += T.R;
+    }
+    if (tid == 0) {
+        unitOut[n] = tu;
+        rowOut[n] = tr;
+    }
     __syncthreads();
 }
 
@@ -176,10 +204,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             }
             __syncthreads();
         }
-        if (blockIdx.x == 0) {
-            block_prefix(work, nwork, [&](int t) { return M.tabs[t].nseg; }, M.unitPrefix, sm);
-            block_prefix(work, nwork, [&](int t) { return M.tabs[t].R; }, M.rowPrefix, sm);
-        }
+        // the prefixes by the last CTA, which plans no table when the work
+        // list is shorter than the grid
+        if (blockIdx.x == gridDim.x - 1) work_prefix(M, work, nwork, M.unitPrefix, M.rowPrefix, sm);
         if (!sync()) return;
         phase(1);
         if (__ldcg(&C->status) != CT_OK) break;
@@ -354,11 +381,21 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
                 const int t = t0 + lane;
                 bool dirty = false;
-                if (t < M.ntables && __ldcg(&M.nodeStatus[t / M.nodeTables]) == CT_OK) {
-                    for (int j = M.scopeBase[t]; j < M.scopeBase[t + 1] && !dirty; ++j) {
-                        const int p = __ldcg(&pruned[M.scopeVar[j]]);
-                        dirty = p != -1 && p != t;
+                if (t < M.ntables) {
+                    // scope variables eight at a time, their marks loaded together
+                    const bool alive = __ldcg(&M.nodeStatus[t / M.nodeTables]) == CT_OK;
+                    const int j1 = M.scopeBase[t + 1];
+                    for (int j = M.scopeBase[t]; j < j1; j += 8) {
+                        int v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[u] = j + u < j1 ? M.scopeVar[j + u] : -1;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int p = v[u] >= 0 ? __ldcg(&pruned[v[u]]) : -1;
+                            dirty |= p != -1 && p != t;
+                        }
                     }
+                    dirty &= alive;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, dirty);
                 if (bal) {
