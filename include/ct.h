@@ -75,7 +75,13 @@ typedef struct ct_options {
                                  propagation): ct_propagate round-trips currTable through a pinned
                                  host copy each call (and ct_restore refreshes it). Results are the
                                  same; only the copies' cost is added. */
-    int32_t reserved;
+    int32_t shard;            /* 1 = the table is one word-range shard of a larger table (the
+                                 data-parallel split of one table, see ct_sharded_create):
+                                 filterDomains clears the values none of THIS table's valid
+                                 tuples supports, an empty currTable is not a failure (every
+                                 value is cleared, status CT_OK), and the last-seen domains keep
+                                 the call's input domains, since another shard may support a
+                                 value this one cleared. Positive tables only. */
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */
@@ -268,6 +274,55 @@ int ct_destroy(ct_table* ct);
 int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t t, const uint32_t* supports,
                          uint32_t* curr_table, uint32_t* dom_bits, uint32_t* last_dom_bits,
                          uint32_t* changed_vars, void* cuda_stream);
+
+/* ------------------------------------------------------ word-range shards --
+ * One table split into K shards of contiguous retained tuples (whole 128-tuple
+ * chunks of currTable), run on one device: the data-parallel split of one
+ * table's propagation. updateTable is local to each shard; a value is
+ * supported iff some valid tuple of some shard carries it (the GAC definition
+ * of Sec. 2), so the domains are the OR of what each shard supports, and the
+ * table fails iff every shard's currTable is empty. The OR runs as one small
+ * kernel here, where a split over several GPUs would all-reduce the bits.
+ */
+typedef struct ct_sharded ct_sharded;
+
+/* ct_shard_bounds: the split of t >= 1 retained tuples into K shards of whole
+ * 128-tuple chunks (host only): bounds_out (host int64[K + 1]) receives
+ * bounds_out[0] = 0 < bounds_out[1] < ... < bounds_out[K] = t, shard k holding
+ * tuples [bounds_out[k], bounds_out[k + 1]), each bound but the last a
+ * multiple of 128 and every shard non-empty. CT_ERR_ARG if K > ceil(t / 128). */
+int ct_shard_bounds(int64_t t, int K, int64_t* bounds_out);
+
+/* ct_sharded_create: the table of ct_create (same arguments and conventions;
+ * positive tables, wildcards allowed) split by ct_shard_bounds over its
+ * retained tuples into K tables created with ct_options.shard = 1 on one
+ * stream. CT_INFEASIBLE and no handle when no tuple is inside the domains. */
+int ct_sharded_create(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
+                      int64_t t, int K, const ct_options* opt, void* cuda_stream, ct_sharded** out);
+
+/* ct_sharded_propagate: ct_propagate of the whole table. Every shard filters
+ * its own device copy of dom_bits, and dom_bits (device, in/out) becomes the
+ * OR of the copies. changed_vars as in ct_propagate. CT_INFEASIBLE iff a
+ * domain became empty; the shards are then restored with ct_sharded_restore
+ * before the next call. Blocks until the result is known. */
+int ct_sharded_propagate(ct_sharded* sh, uint32_t* dom_bits, uint32_t* changed_vars);
+
+/* ct_sharded_save / ct_sharded_restore: ct_save / ct_restore on every shard
+ * (the shards' level stacks stay equal). */
+int ct_sharded_save(ct_sharded* sh, int* level_out);
+int ct_sharded_restore(ct_sharded* sh, int level);
+
+/* ct_sharded_get_currtable: currTable of the whole table (host
+ * uint32[ceil(t/32)] or NULL, t the retained tuples): shard k's words at word
+ * bounds[k] / 32; *nonzero_words_out (or NULL) the non-zero words of all. */
+int ct_sharded_get_currtable(ct_sharded* sh, uint32_t* words_host, int64_t* nonzero_words_out);
+
+/* ct_sharded_get_shard: shard k's table handle, owned by sh (for its
+ * statistics and info; propagate it only through ct_sharded_propagate). */
+int ct_sharded_get_shard(ct_sharded* sh, int k, ct_table** table_out);
+
+/* ct_sharded_destroy: free the shards (NULL is accepted). */
+int ct_sharded_destroy(ct_sharded* sh);
 
 /* ---------------------------------------------------------------- model --
  * A model is a set of integer variables and table constraints over them,

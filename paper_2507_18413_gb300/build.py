@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libct.so")
-SOURCES = ["ct_kernels.cu", "ct_model_kernels.cu", "ct_learn.cu", "ct_table.cu", "ct_model.cu", "ct_search.cu", "ct_noalloc.cu"]
+SOURCES = ["ct_kernels.cu", "ct_model_kernels.cu", "ct_learn.cu", "ct_table.cu", "ct_model.cu", "ct_search.cu", "ct_noalloc.cu", "ct_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -119,6 +119,8 @@ struct TableDev {
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
     int32_t negative;        // 1: the tuples are forbidden (negative table; one-table kernel only)
+    int32_t shard;           // 1: a word-range shard (one-table kernel only): no failure on an
+                             // empty currTable, lastDom keeps the call's input domains
     // Scopes of at most kParamArity variables: words, lastDom offset and first
     // supports row of each variable, so that the plan reads no global table.
     int32_t pNW[kParamArity], pLD[kParamArity], pRow0[kParamArity];

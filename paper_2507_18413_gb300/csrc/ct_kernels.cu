@@ -70,8 +70,9 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
                 atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
                 // a positive table's removed value carries no valid tuple, so
                 // lastDom may drop it now; a negative table's value still has
-                // valid forbidden tuples, which the next call removes as Delta
-                if (!T.negative) atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+                // valid forbidden tuples, which the next call removes as Delta;
+                // a shard's value may be supported by another shard
+                if (!T.negative && !T.shard) atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 T.changed[i] = 1;
                 ++pruned;
             }
@@ -262,8 +263,9 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         if (!grid_sync(C, &sm.flag[0])) return;
         if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
         // Algorithm 1 line 5: fail when currTable is all zero (a negative
-        // table with no valid forbidden tuple forbids nothing).
-        if (__ldcg(&C->status) != CT_OK || (!T.negative && __ldcg(&C->live) == 0u)) {
+        // table with no valid forbidden tuple forbids nothing; an empty shard
+        // supports no value, which the filter finds).
+        if (__ldcg(&C->status) != CT_OK || (!T.negative && !T.shard && __ldcg(&C->live) == 0u)) {
             if (blockIdx.x == 0) {
                 if (tid == 0 && __ldcg(&C->status) == CT_OK) C->status = CT_INFEASIBLE;
                 __syncthreads();

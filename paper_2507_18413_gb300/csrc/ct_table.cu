@@ -393,6 +393,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     d.sup = sup;
     d.supDelta = supDel;
     d.negative = ct->negative ? 1 : 0;
+    d.shard = (opt && opt->shard) ? 1 : 0;
     d.rowVar = rowVar;
     d.varRow0 = varRow0;
     d.varNW = varNW;
@@ -1009,6 +1010,10 @@ int create_impl(int arity, const int32_t* dom_lo, const int32_t* dom_size, const
             ct_set_error("ct_create: dom_size[%d] = %d out of [1, %d]", i, dom_size[i], kMaxDomSize);
             return CT_ERR_ARG;
         }
+    }
+    if (negative && opt && opt->shard) {
+        ct_set_error("ct_create_negative: negative tables cannot be shards");
+        return CT_ERR_ARG;
     }
     ct_table* ct = new (std::nothrow) ct_table();
     if (!ct) return CT_ERR_OOM;

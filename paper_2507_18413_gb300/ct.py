@@ -37,7 +37,7 @@ class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("host_fixpoint", ctypes.c_int32), ("autotune", ctypes.c_int32), ("copy_state", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("shard", ctypes.c_int32)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -120,6 +120,15 @@ _SIGS = {
     "ct_reset_profile": (ctypes.c_int, [_P]),
     "ct_destroy": (ctypes.c_int, [_P]),
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
+    "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
+    "ct_sharded_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.c_int,
+                                         _P, _P, ctypes.POINTER(_P)]),
+    "ct_sharded_propagate": (ctypes.c_int, [_P, _P, _U32P]),
+    "ct_sharded_save": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "ct_sharded_restore": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ct_sharded_get_currtable": (ctypes.c_int, [_P, _U32P, _I64P]),
+    "ct_sharded_get_shard": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "ct_sharded_destroy": (ctypes.c_int, [_P]),
     "ct_model_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, ctypes.POINTER(ct_options), _P,
                                        ctypes.POINTER(_P)]),
     "ct_model_add_table": (ctypes.c_int, [_P, _I32P, ctypes.c_int, _I32P, ctypes.c_int64]),
@@ -235,8 +244,9 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0, shard=0):
     o = ct_options()
+    o.shard = shard
     o.autotune = autotune
     o.host_fixpoint = host_fixpoint
     o.copy_state = copy_state
@@ -295,6 +305,59 @@ def ct_create(arity, dom_lo, dom_size, tuples, opt=None, stream=None, negative=F
     st = fn(int(arity), plo, psz, ptup, int(t), ctypes.byref(opt) if opt is not None else None,
             _stream_ptr(stream), ctypes.byref(h))
     return st, h
+
+
+def ct_shard_bounds(t, K):
+    """Returns (status, int64 bounds[K + 1]) of the split of t retained tuples."""
+    b = np.zeros(int(K) + 1, dtype=np.int64)
+    st = load().ct_shard_bounds(int(t), int(K), b.ctypes.data_as(_I64P))
+    return st, b
+
+
+def ct_sharded_create(arity, dom_lo, dom_size, tuples, K, opt=None, stream=None):
+    """Returns (status, handle) of the table split into K word-range shards."""
+    lo, plo = _i32(dom_lo)
+    sz, psz = _i32(dom_size)
+    tup = np.ascontiguousarray(np.asarray(tuples, dtype=np.int32).reshape(-1, arity))
+    t = tup.shape[0]
+    h = _P()
+    st = load().ct_sharded_create(int(arity), plo, psz, tup.ctypes.data_as(_I32P) if t else None, int(t), int(K),
+                                  ctypes.byref(opt) if opt is not None else None, _stream_ptr(stream),
+                                  ctypes.byref(h))
+    return st, h
+
+
+def ct_sharded_propagate(h, dom_bits, changed_words: int = 0):
+    ch, pch = _u32_out(changed_words)
+    st = load().ct_sharded_propagate(h, _dev_ptr(dom_bits), pch if changed_words else None)
+    return st, ch[:changed_words]
+
+
+def ct_sharded_save(h):
+    lv = ctypes.c_int(-1)
+    st = load().ct_sharded_save(h, ctypes.byref(lv))
+    return st, lv.value
+
+
+def ct_sharded_restore(h, level):
+    return load().ct_sharded_restore(h, int(level))
+
+
+def ct_sharded_get_currtable(h, nwords):
+    w, pw = _u32_out(nwords)
+    nz = ctypes.c_int64(0)
+    st = load().ct_sharded_get_currtable(h, pw, ctypes.byref(nz))
+    return st, w[:nwords], nz.value
+
+
+def ct_sharded_get_shard(h, k):
+    t = _P()
+    st = load().ct_sharded_get_shard(h, int(k), ctypes.byref(t))
+    return st, t
+
+
+def ct_sharded_destroy(h):
+    return load().ct_sharded_destroy(h)
 
 
 def ct_propagate(h, dom_bits, changed_words: int = 0):
