@@ -356,6 +356,38 @@ def run_ours(args, rank, world):
     e2e = {"value": e2e_props / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
            "h2d_bytes_per_step": h2d // max(args.steps, 1), "d2h_bytes_per_step": d2h // max(args.steps, 1)}
 
+    # The timed steps once more, outside the timed region: (1) with warm L2
+    # (no flush between steps), (2) one CUDA-event pair around every
+    # propagation, for the distribution of the per-call latency.
+    warm_ms, warm_props, lat = 0.0, 0, []
+    for s in range(args.warmup, nsteps):
+        calls, (n, _, _) = replay(plans[s], dev_in[s].clone())
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        run_calls(calls)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        warm_ms += ev0.elapsed_time(ev1)
+        warm_props += n
+    for s in range(args.warmup, nsteps):
+        calls, _ = replay(plans[s], dev_in[s].clone())
+        flush.zero_()
+        pairs = []
+        torch.cuda.synchronize()
+        for f, a in calls:
+            if f is f_prop:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if f(*a) < 0:
+                    raise RuntimeError(C.last_error())
+                e1.record(stream)
+                pairs.append((e0, e1))
+            elif f(*a) < 0:
+                raise RuntimeError(C.last_error())
+        torch.cuda.synchronize()
+        lat += [a.elapsed_time(b) * 1e3 for a, b in pairs]
+    lat = np.sort(np.asarray(lat))
+
     peak, peak_kind = peaks()
     alg = prof["update_bytes"] + prof["filter_bytes"]
     achieved = (alg / (prof["kernel_ms"] / 1e3) / 1e9) if prof["kernel_ms"] > 0 else 0.0
@@ -386,6 +418,15 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "roofline": roofline,
         "clocks": clocks,
+        "warm_l2": {"value": round(warm_props / (warm_ms / 1e3), 1) if warm_ms > 0 else None, "unit": UNIT,
+                    "ms_per_step": round(warm_ms / max(args.steps, 1), 4),
+                    "note": "the timed steps replayed without the L2 flush between steps (untimed pass)"},
+        "call_latency_us": {"calls": int(len(lat)),
+                            "p10": round(float(np.percentile(lat, 10)), 2) if len(lat) else None,
+                            "p50": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
+                            "p90": round(float(np.percentile(lat, 90)), 2) if len(lat) else None,
+                            "note": "CUDA events around each ct_propagate of the timed steps, L2 flushed "
+                                    "between steps (untimed pass)"},
     }
     C.ct_destroy(h)
     del flush
