@@ -238,6 +238,10 @@ int ct_get_info(ct_table* ct, ct_table_info* info);
 int ct_get_call_stats(ct_table* ct, ct_call_stats* stats);
 int ct_get_profile(ct_table* ct, ct_profile* prof);
 int ct_reset_profile(ct_table* ct);
+/* ct_set_profile: switch the per-launch timing of ct_options.profile on (1)
+ * or off (0) for the following calls; accumulated figures are kept (pending
+ * timings are collected before switching off). */
+int ct_set_profile(ct_table* ct, int on);
 
 /* ct_destroy: free the table (NULL is accepted). */
 int ct_destroy(ct_table* ct);

@@ -1233,6 +1233,22 @@ extern "C" int ct_get_profile(ct_table* ct, ct_profile* prof) {
     return CT_OK;
 }
 
+extern "C" int ct_set_profile(ct_table* ct, int on) {
+    if (!ct) {
+        ct_set_error("ct_set_profile: null handle");
+        return CT_ERR_ARG;
+    }
+    if (on && !ct->ev[0]) {
+        for (auto& e : ct->ev) CT_CUDA(cudaEventCreate(&e));
+    }
+    if (!on) {
+        const int st = drain_events(ct);
+        if (st != CT_OK) return st;
+    }
+    ct->profile = on != 0;
+    return CT_OK;
+}
+
 extern "C" int ct_reset_profile(ct_table* ct) {
     if (!ct) return CT_ERR_ARG;
     const int st = drain_events(ct);

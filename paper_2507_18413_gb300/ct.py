@@ -118,6 +118,7 @@ _SIGS = {
     "ct_get_call_stats": (ctypes.c_int, [_P, ctypes.POINTER(ct_call_stats)]),
     "ct_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ct_profile)]),
     "ct_reset_profile": (ctypes.c_int, [_P]),
+    "ct_set_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "ct_destroy": (ctypes.c_int, [_P]),
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
     "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
@@ -429,6 +430,10 @@ def ct_get_profile(h):
 
 def ct_reset_profile(h):
     return load().ct_reset_profile(h)
+
+
+def ct_set_profile(h, on):
+    return load().ct_set_profile(h, 1 if on else 0)
 
 
 def ct_destroy(h):

@@ -362,6 +362,31 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     gt.close()
 
 
+def test_profiling_switched_on_and_off():
+    """ct_set_profile: calls are timed only while profiling is on; results
+    are the oracle's either way."""
+    dom_lo, dom_size, tup = G.large_table(33, 20_000)
+    tup_ret = O.retained_tuples(tup, dom_lo, dom_size)
+    gt = GpuTable(dom_lo, dom_size, tup)
+    rng = G.Rng(9)
+    masks = [np.ones(d, bool) for d in dom_size]
+    timed = []
+    for k in range(6):
+        assert C.ct_set_profile(gt.h, k % 2) == C.CT_OK
+        new, _ = G.delta_step(rng, masks)
+        st, out, _ = gt.propagate(new)
+        timed.append(k % 2)
+        st_o, out_o, _ = oracle_step(tup_ret, dom_lo, new)
+        assert st == st_o
+        if st != O.OK:
+            break
+        assert all(np.array_equal(a, b) for a, b in zip(out, out_o))
+        masks = out_o
+    st, prof = C.ct_get_profile(gt.h)
+    assert st == C.CT_OK and prof["calls"] == sum(timed) and prof["kernel_ms"] > 0
+    gt.close()
+
+
 # --------------------------------------------------------------------------
 # full-size workloads, sampled against the oracle
 # --------------------------------------------------------------------------
