@@ -450,6 +450,9 @@ def run_ours(args, rank, world):
     if rank == 0:
         result["cpu_baseline"] = cpu_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
         result["cpu_baseline_bitset"] = cpu_bitset_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
+        if not args.no_extra:
+            result["cpu_baseline_bitset_all_cores"] = cpu_bitset_baseline_cores(args, plans[args.warmup:], dom_lo,
+                                                                                dom_size, tup)
     return result
 
 
@@ -783,6 +786,59 @@ def cpu_bitset_baseline(args, plans, dom_lo, dom_size, tup, seconds=8.0):
     ct.close()
     return {"value": round(done / dt, 1), "unit": UNIT, "cores": 1, "kind": "serial bitset CT (Algorithms 1-3)",
             "sample": f"{done} propagations of the timed stream with their saves/restores, {dt:.1f} s, one thread"}
+
+
+def cpu_bitset_baseline_cores(args, plans, dom_lo, dom_size, tup, seconds=6.0):
+    """The same serial bitset CT on every host core: one independent replica
+    per thread, each replaying the planned calls with their saves and restores
+    (the C calls release the GIL, so the replicas run in parallel)."""
+    import threading
+    from oracle.serial_ct import SerialCT
+    import paper_2507_18413_gb300.ct as C
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    full = C.masks_to_words([np.ones(d, bool) for d in dom_size])
+    inputs = [[w.copy() for w in rp.inputs] for rp in plans]
+    counts = [0] * cores
+    ready = threading.Barrier(cores + 1)
+    stop = threading.Event()
+
+    def worker(k):
+        ct = SerialCT(dom_lo, dom_size, tup)
+        ct.propagate(full.copy())
+        ct.save()
+        ready.wait()
+        done = 0
+        while not stop.is_set():
+            for rp, ins in zip(plans, inputs):
+                buf = [w.copy() for w in ins]
+                for op in rp.ops:
+                    if op[0] == "save":
+                        ct.save()
+                    elif op[0] == "restore":
+                        ct.restore(op[1])
+                    else:
+                        ct.propagate(buf[op[1]])
+                        done += 1
+                if stop.is_set():
+                    break
+        counts[k] = done
+        ct.close()
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(cores)]
+    for th in threads:
+        th.start()
+    ready.wait()
+    t0 = time.perf_counter()
+    time.sleep(seconds)
+    stop.set()
+    for th in threads:
+        th.join()
+    dt = time.perf_counter() - t0
+    total = sum(counts)
+    return {"value": round(total / dt, 1), "unit": UNIT, "cores": cores,
+            "kind": "serial bitset CT (Algorithms 1-3), one independent replica per core",
+            "sample": f"{total} propagations of the timed stream with their saves/restores over {cores} threads, "
+                      f"{dt:.1f} s"}
 
 
 def cpu_baseline(args, plans, dom_lo, dom_size, tup):
