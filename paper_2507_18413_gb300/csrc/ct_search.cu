@@ -346,6 +346,15 @@ struct Search {
     bool probeMode = false;
     double probeL = 0.0;
     std::vector<float> probeLabel;
+    // breadth-first split: per slot, the result of the node it propagated
+    struct SplitOut {
+        int status = CT_OK;
+        int x = -1;  // branching variable, -1: a solution
+        std::vector<uint32_t> dom;
+    };
+    bool splitMode = false;
+    bool slotsReady = false;
+    std::vector<SplitOut> splitOut;
     std::chrono::steady_clock::time_point t0;
 
     uint32_t* slotDom(int s) { return b->domHost() + (size_t)s * m->DWg; }
@@ -450,6 +459,90 @@ struct Search {
         return CT_OK;
     }
 
+    // ---- split phase, breadth-first in the slots ----
+    // The root is propagated on the model; then every level of the tree above
+    // the split depth is propagated together, up to B nodes per launch, each
+    // node in a slot from the root state (the slot is put back at the root
+    // afterwards, its undo staged for the next launch). Children are made in
+    // the order of their parents, left before right, so each level, and the
+    // open nodes left at the split depth, stay in depth-first order. The nodes
+    // visited are those of the depth-first split.
+    void children(std::vector<OpenNode>& out, const std::vector<uint32_t>& dom, int x, int depth,
+                  const std::vector<uint8_t>& path) {
+        const int a = min_value(m, dom.data(), x);
+        for (int br = 0; br < 2; ++br) {
+            OpenNode c{dom, depth, path};
+            uint32_t* w = c.dom.data() + m->off[x];
+            if (br == 0) {
+                for (int q = 0; q < m->nw[x]; ++q) w[q] = 0u;
+                w[a >> 5] = 1u << (a & 31);
+            } else {
+                w[a >> 5] &= ~(1u << (a & 31));
+            }
+            c.path.push_back((uint8_t)br);
+            if (!countAll && haveBest && after(c.path, bestPath)) continue;
+            out.push_back(std::move(c));
+        }
+    }
+
+    int split_bfs() {
+        if (limit > 0 && st.nodes >= limit) {
+            hitLimit = stopIssue = true;
+            return CT_OK;
+        }
+        st.nodes += 1;
+        info.split_nodes += 1;
+        int r = ct_model_propagate(m);
+        if (r < 0) return r;
+        if (r == CT_INFEASIBLE) {
+            st.fails += 1;
+            return CT_OK;
+        }
+        int x = -1;
+        if ((r = ct_model_pick_var(m, usePolicy, &x)) != CT_OK) return r;
+        if (x < 0) {
+            record_solution(std::vector<uint8_t>(), m->h_dom.data());
+            return CT_OK;
+        }
+        if ((r = ensure_copies()) != CT_OK) return r;
+        if (usePolicy && (r = ensure_slot_features(m, b)) != CT_OK) return r;
+        init_slots();
+        splitOut.assign(B, SplitOut());
+        std::vector<OpenNode> F, G;
+        children(F, m->h_dom, x, 1, std::vector<uint8_t>());
+        for (int depth = 1; depth < splitDepth && !F.empty() && !stopIssue; ++depth) {
+            G.clear();
+            for (size_t i0 = 0; i0 < F.size() && !stopIssue; i0 += (size_t)B) {
+                const size_t i1 = std::min(F.size(), i0 + (size_t)B);
+                splitMode = true;
+                bool any = false;
+                for (size_t i = i0; i < i1 && !stopIssue; ++i) {
+                    if (!countAll && haveBest && after(F[i].path, bestPath)) continue;
+                    const int s = (int)(i - i0);
+                    if ((r = start(s, F[i].dom.data(), F[i].depth, F[i].path)) != CT_OK) return r;
+                    any |= slots[s].pending;
+                }
+                if (any) r = step();
+                splitMode = false;
+                if (r != CT_OK) return r;
+                if (!any) break;
+                for (size_t i = i0; i < i1; ++i) {
+                    const int s = (int)(i - i0);
+                    if (slots[s].pending) continue;  // never issued
+                    SplitOut& o = splitOut[s];
+                    if (o.dom.empty()) continue;
+                    if (o.status != CT_OK) st.fails += 1;
+                    else if (o.x < 0) record_solution(F[i].path, o.dom.data());
+                    else children(G, o.dom, o.x, depth + 1, F[i].path);
+                    o.dom.clear();
+                }
+            }
+            F.swap(G);
+        }
+        for (OpenNode& o : F) open.push_back(std::move(o));
+        return CT_OK;
+    }
+
     // ---- slot bookkeeping ----
     void mark_var(int s, int v) {
         for (int k : m->varTables[v]) dirty[(size_t)s * b->T + k] = 1;
@@ -510,7 +603,8 @@ struct Search {
             return cancel(s);
         }
         st.nodes += 1;
-        info.slot_nodes += 1;
+        if (splitMode) info.split_nodes += 1;
+        else info.slot_nodes += 1;
         if (depth > st.max_depth) st.max_depth = depth;
         slots[s].pending = true;
         return CT_OK;
@@ -606,6 +700,21 @@ struct Search {
         return cancel(s);  // subtree done: back to the root state, idle
     }
 
+    // Branching variable of slot s's propagated node (the policy's best score
+    // or first-fail); -1 when every variable is fixed.
+    int pick(int s) const {
+        int x = -1;
+        const uint32_t* dom = const_cast<Search*>(this)->slotDom(s);
+        if (scores) {
+            const float* sc = scores + (size_t)s * m->nvars;
+            for (int v = 0; v < m->nvars; ++v)
+                if (popcount_words(dom + m->off[v], m->nw[v]) > 1 && (x < 0 || sc[v] > sc[x])) x = v;
+        } else {
+            x = first_fail(m, dom);
+        }
+        return x;
+    }
+
     // The result of slot s's node (status of its fixpoint, domains in slotDom).
     int advance(int s, int nodeStatus) {
         Slot& S = slots[s];
@@ -615,15 +724,7 @@ struct Search {
             st.fails += 1;
             return backtrack(s);
         }
-        int x = -1;
-        if (scores) {
-            const float* sc = scores + (size_t)s * m->nvars;
-            const uint32_t* dom = slotDom(s);
-            for (int v = 0; v < m->nvars; ++v)
-                if (popcount_words(dom + m->off[v], m->nw[v]) > 1 && (x < 0 || sc[v] > sc[x])) x = v;
-        } else {
-            x = first_fail(m, slotDom(s));
-        }
+        const int x = pick(s);
         if (x < 0) {
             record_solution(S.path, slotDom(s));
             return backtrack(s);
@@ -639,7 +740,7 @@ struct Search {
         for (int j = 0; j < n; ++j)
             if (dirty[j]) work[nwork++] = j;
         info.steps += 1;
-        if (nwork == 0 && nrest == 0 && !usePolicy && !probeMode) {  // the nodes are their own fixpoints
+        if (nwork == 0 && nrest == 0 && !usePolicy && !probeMode && !splitMode) {  // the nodes are their own fixpoints
             std::vector<int> ps;
             for (int s = 0; s < B; ++s)
                 if (slots[s].pending) ps.push_back(s);
@@ -728,6 +829,15 @@ struct Search {
         }
         for (int s = 0; s < B; ++s) {
             if (!slots[s].pending) continue;
+            if (splitMode) {
+                SplitOut& o = splitOut[s];
+                o.status = outNode[s];
+                o.x = o.status == CT_OK ? pick(s) : -1;
+                o.dom.assign(slotDom(s), slotDom(s) + m->DWg);
+                slots[s].pending = false;
+                if ((rc = cancel(s)) != CT_OK) return rc;
+                continue;
+            }
             if (probeMode) {
                 slots[s].pending = false;
                 double L2 = 0.0;
@@ -764,13 +874,21 @@ struct Search {
         return rc;
     }
 
-    int run_slots_inner() {
+    // Idle slots at the root state (kept when the split phase already ran in
+    // them: their undos may still be staged for the next launch).
+    void init_slots() {
+        if (slotsReady) return;
         const int n = b->n;
         slots.assign(B, Slot());
         dirty.assign(n, 0);
         restPos.assign(n, -1);
         nrest = 0;
         for (int s = 0; s < B; ++s) std::memcpy(slotDom(s), rootDom.data(), (size_t)m->DWg * sizeof(uint32_t));
+        slotsReady = true;
+    }
+
+    int run_slots_inner() {
+        init_slots();
         for (;;) {
             for (int s = 0; s < B; ++s) {
                 if (slots[s].active) continue;
@@ -836,8 +954,14 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     int rc = ct_model_save(m, &L0);
     if (rc != CT_OK) return rc;
     std::vector<uint8_t> path;
-    if (split_depth == 0) rc = S.ensure_copies();
-    if (rc == CT_OK) rc = S.split(0, path);
+    // the breadth-first split in the slots, except for the budgeted
+    // any-solution search (the model searches its share depth-first first)
+    if (split_depth >= 2 && !S.anyStop) {
+        rc = S.split_bfs();
+    } else {
+        if (split_depth == 0) rc = S.ensure_copies();
+        if (rc == CT_OK) rc = S.split(0, path);
+    }
     const int rr = ct_model_restore(m, L0);
     if (rc == CT_OK) rc = rr;
     const bool runSlots = !S.open.empty() && !S.stopIssue && !(S.anyStop && S.haveBest);
