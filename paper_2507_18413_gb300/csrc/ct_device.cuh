@@ -447,14 +447,14 @@ enum { kProbeFound = 1, kProbeGone = 0, kProbeUndecided = -1 };
 // A value whose residue missed (whole warp, r and res uniform): Algorithm 3's
 // search for a support over the live chunks (the non-zero index) that follow
 // the residue in cyclic order (kLive), 32 chunks per window, at most
-// kLocalProbes windows over at most kWindowGroups x 32 index segments; without
+// kProbes windows over at most kWindowGroups x 32 index segments; without
 // kLive, the chunks that follow the residue, dead or alive. Found: the residue
 // moves there (kProbeFound). Not found with every live chunk tested: the value
 // has no support (kProbeGone). Else kProbeUndecided: a full scan decides.
 // (Measured against windows of the chunks that follow the residue, dead or
 // alive: the same on the dense bench stream, 8-10% more search nodes per
 // second in the batched search.)
-template <bool kLive>
+template <bool kLive, int kProbes = kLocalProbes>
 __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -463,7 +463,7 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
         // the chunks that follow the residue, dead or alive
         const int W4 = T.W4;
         const uint4* row = T.sup + (size_t)r * W4;
-        for (int b = 0; b < kLocalProbes; ++b) {
+        for (int b = 0; b < kProbes; ++b) {
             if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
             const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
             const bool h = nz(and4(ld_sup(row + c), __ldcg(T.curr + c)));
@@ -488,7 +488,7 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
         int tested = 0;
         complete = true;
         for (int g = 0, v0 = 0; v0 < nvirt && complete; ++g, v0 += 32) {
-            if (g == kWindowGroups || tested >= 32 * kLocalProbes) {
+            if (g == kWindowGroups || tested >= 32 * kProbes) {
                 complete = false;
                 break;
             }
@@ -511,7 +511,7 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
             }
             const int total = __shfl_sync(FULL, inc, 31);
             for (int q0 = 0; q0 < total; q0 += 32) {
-                if (tested >= 32 * kLocalProbes) {
+                if (tested >= 32 * kProbes) {
                     complete = false;
                     break;
                 }

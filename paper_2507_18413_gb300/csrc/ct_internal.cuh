@@ -37,7 +37,8 @@ constexpr int32_t kNoSupport = -2;         // hard-list mark: no live chunk supp
 constexpr int32_t kCodeLast = 1 << 30;   // last row of its variable: apply the mask
 constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~OR(rows)
 constexpr int32_t kCodeRow = (1 << 29) - 1;
-constexpr int kLocalProbes = 2;          // windows of 32 live chunks searched after a residue miss
+constexpr int kLocalProbes = 4;          // windows of 32 chunks searched after a residue miss (one table)
+constexpr int kModelProbes = 8;          // the same in the network kernel (live chunks)
 constexpr int kWindowGroups = 8;         // index segments read for them: at most 8 x 32 (8,192 chunks)
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         for (int q = gwarp; q < nm; q += nwarps) {
             const int4 e = __ldcg(&M.missQ[q]);
             const TableDev& T = M.tabs[e.x];
-            const int o = probe_windows<true>(T, e.y, e.z, sm.cnt);
+            const int o = probe_windows<true, kModelProbes>(T, e.y, e.z, sm.cnt);
             if (o != kProbeFound && lane == 0) {
                 if (o == kProbeGone) {
                     remove_value(M, T, e.x, e.y, pruned);
