@@ -751,10 +751,11 @@ struct Search {
             return CT_OK;
         }
         int rc;
+        // per table, one visit: its call (trail room, mark, pending level
+        // snapshots) and, when its buffers moved, its device descriptor
         ModelTabCall* calls = b->callsHost();
-        for (int j = 0; j < n; ++j)
-            if ((rc = ct_table_batch_prepare(b->tabs[j], &calls[j])) != CT_OK) return rc;
         for (int j = 0; j < n; ++j) {
+            if ((rc = ct_table_batch_prepare(b->tabs[j], &calls[j])) != CT_OK) return rc;
             const int v = ct_table_version(b->tabs[j]);
             if (v != b->tabVersion[j]) {
                 CT_CUDA(cudaMemcpyAsync(b->d_tabs + j, &ct_table_dev(b->tabs[j]), sizeof(TableDev),
