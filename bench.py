@@ -150,11 +150,11 @@ def clocks_stop(proc):
 
 def kernel_source_hash():
     """First 16 hex digits of the sha256 of the propagation kernel's sources
-    (ct_device.cuh followed by ct_kernels.cu)."""
+    (ct_internal.cuh, ct_device.cuh and ct_kernels.cu, in that order)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2507_18413_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("ct_device.cuh", "ct_kernels.cu"):
+    for name in ("ct_internal.cuh", "ct_device.cuh", "ct_kernels.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -562,7 +562,7 @@ def _build_model(C, spec):
     return m
 
 
-def _search_compare(C, name, spec, slots=256, split=10, plain_limit=3000, batch_limit=20000):
+def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_limit=20000):
     """Nodes/s of the plain search (one node per launch) and of the batched search
     (slots x tables propagated per launch) on the same CSP, counting all solutions
     up to a node limit; the batched figure is the second of two calls (the first
