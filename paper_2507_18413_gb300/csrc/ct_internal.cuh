@@ -181,6 +181,7 @@ struct ModelDev {
     const int32_t* scopeOff;    // word offset of every scope variable in dom
     const int32_t* scopeVar;    // global index of every scope variable
     int32_t* work;              // [2][ntables] work lists (ping-pong by round)
+    int32_t* snapTaken;         // [ntables] 1: the table's pending level snapshots were taken in this launch
     int32_t* unitPrefix;        // [ntables + 1] segments of the work list
     int32_t* rowPrefix;         // [ntables + 1] supports rows of the work list
     int32_t* prunedBy;          // [2][nvars] by round parity: -1 none, t one table, -2 several
@@ -245,7 +246,7 @@ const ctk::TableDev& ct_table_dev(const ct_table* ct);
 int ct_table_version(const ct_table* ct);
 int ct_table_is_empty(const ct_table* ct);
 int ct_table_batch_prepare(ct_table* ct, ctk::ModelTabCall* call);
-void ct_table_batch_done(ct_table* ct, int trailTop, int live);
+void ct_table_batch_done(ct_table* ct, int trailTop, int live, bool snapped);
 // Host bookkeeping of a restore; returns 1 (and fills d) when a device undo is needed.
 int ct_table_restore_prepare(ct_table* ct, int level, ctk::RestoreDesc* d);
 int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);

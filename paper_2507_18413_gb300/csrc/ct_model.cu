@@ -87,6 +87,8 @@ int batch_setup(ct_model* m) {
     if ((st = m_alloc(m, &M.unitPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &M.rowPrefix, (size_t)n + 1)) != CT_OK) return st;
     if ((st = m_alloc(m, &dPruned, 2 * (size_t)m->nvars)) != CT_OK) return st;
+    if ((st = m_alloc(m, &M.snapTaken, (size_t)n)) != CT_OK) return st;
+    CT_CUDA(cudaMemsetAsync(M.snapTaken, 0, std::max<size_t>(n, 1) * sizeof(int32_t), m->stream));
     if ((st = m_alloc(m, &dCtrl, 1)) != CT_OK) return st;
     const int nodeTables = std::max(n, 1);  // the whole network is one node
     const int nnodes = 1;
@@ -100,7 +102,7 @@ int batch_setup(ct_model* m) {
     CT_CUDA(cudaMemsetAsync(dPruned, 0xff, 2 * (size_t)m->nvars * 4, m->stream));
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), m->stream));
     if (cudaHostAlloc((void**)&m->h_blk, blkWords * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg + nnodes) * sizeof(int32_t),
+        cudaHostAlloc((void**)&m->h_mstatus, (size_t)(kModelHdr + 2 * n + m->DWg + nnodes + n) * sizeof(int32_t),
                       cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         ct_set_error("model: pinned host buffers");
@@ -271,7 +273,9 @@ int batch_propagate(ct_model* m) {
     m->stats.hard_values += (uint32_t)H[5];
     m->stats.update_bytes += (int64_t)(((uint64_t)(uint32_t)H[9] << 32) | (uint32_t)H[8]);
     m->stats.filter_bytes += (int64_t)(((uint64_t)(uint32_t)H[11] << 32) | (uint32_t)H[10]);
-    for (int t = 0; t < n; ++t) ct_table_batch_done(m->tables[t], H[kModelHdr + 2 * t], H[kModelHdr + 2 * t + 1]);
+    const int32_t* snapped = const_cast<const int32_t*>(H) + kModelHdr + 2 * n + m->DWg + 1;  // after the one node
+    for (int t = 0; t < n; ++t)
+        ct_table_batch_done(m->tables[t], H[kModelHdr + 2 * t], H[kModelHdr + 2 * t + 1], snapped[t] != 0);
     if (status == CT_OK && H[kModelHdr + 2 * n + m->DWg] == CT_INFEASIBLE) {
         m->failed = true;
         return CT_INFEASIBLE;

@@ -162,15 +162,6 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
         if (!sync()) return;
     }
-    // Levels saved since each table's last propagation snapshot it as it is now.
-    for (int t = blockIdx.x; t < M.ntables; t += gridDim.x) {
-        const TableDev& T = M.tabs[t];
-        const ModelTabCall cl = M.calls[t];
-        for (int l = cl.snapFrom; l < cl.snapTo; ++l) {
-            for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[(size_t)l * T.nseg + q] = __ldcg(&T.segMask[q]);
-            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = __ldcg(&T.lastDom[q]);
-        }
-    }
     int cur = 0, round = 0;
     for (;;) {
         const int nwork = round > 0 ? __ldcg(&C->nnext[round & 1]) : M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
@@ -191,6 +182,17 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             const int t = __ldcg(&work[k]);
             const TableDev& T = M.tabs[t];
             const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+            // Levels saved since the table's last propagation all hold its state
+            // as it is now: one snapshot, in the lowest one's slot, taken before
+            // this launch first changes the table (a table this launch does not
+            // propagate keeps them pending).
+            const ModelTabCall cl = M.calls[t];
+            if (cl.snapFrom < cl.snapTo && __ldcg(&M.snapTaken[t]) == 0) {
+                const size_t l = (size_t)cl.snapFrom;
+                for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[l * T.nseg + q] = __ldcg(&T.segMask[q]);
+                for (int q = tid; q < T.DW; q += kThreads) T.levelDom[l * T.DW + q] = __ldcg(&T.lastDom[q]);
+                if (tid == 0) M.snapTaken[t] = 1;
+            }
             plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
             if (tid == 0) {
                 Ctrl* Tc = T.ctrl;
@@ -443,6 +445,11 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     for (int q = tid; q < nnodes; q += kThreads) {
         outNode[q] = __ldcg(&M.nodeStatus[q]);
         M.nodeStatus[q] = CT_OK;
+    }
+    int32_t* outSnap = outNode + nnodes;
+    for (int t = tid; t < M.ntables; t += kThreads) {
+        outSnap[t] = __ldcg(&M.snapTaken[t]);
+        M.snapTaken[t] = 0;
     }
     for (int v = tid; v < 2 * M.nvars; v += kThreads) M.prunedBy[v] = -1;
     __syncthreads();

@@ -198,14 +198,15 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
             }
         }
     }
-    int32_t *dBase, *dOff, *dVar, *dPruned, *dNode, *dUnit, *dRow;
+    int32_t *dBase, *dOff, *dVar, *dPruned, *dNode, *dUnit, *dRow, *dSnap;
     ModelCtrl* dCtrl;
     if (m->opt.profile && (st = b_alloc(b, &b->d_phase, kModelPhases)) != CT_OK) return st;
     if ((st = b_alloc(b, &b->d_tabs, n)) != CT_OK || (st = b_alloc(b, &b->d_src, T)) != CT_OK ||
         (st = b_alloc(b, &dBase, n + 1)) != CT_OK || (st = b_alloc(b, &dOff, off.size())) != CT_OK ||
         (st = b_alloc(b, &dVar, var.size())) != CT_OK || (st = b_alloc(b, &dPruned, 2 * (size_t)B * m->nvars)) != CT_OK ||
         (st = b_alloc(b, &dNode, B)) != CT_OK || (st = b_alloc(b, &dUnit, n + 1)) != CT_OK ||
-        (st = b_alloc(b, &dRow, n + 1)) != CT_OK || (st = b_alloc(b, &dCtrl, 1)) != CT_OK)
+        (st = b_alloc(b, &dRow, n + 1)) != CT_OK || (st = b_alloc(b, &dCtrl, 1)) != CT_OK ||
+        (st = b_alloc(b, &dSnap, n)) != CT_OK)
         return st;
     b->offCalls = 16;
     b->offDom = align16(b->offCalls + (size_t)n * sizeof(ModelTabCall));
@@ -213,7 +214,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     b->offRest = align16(b->offWork + 2 * (size_t)n * sizeof(int32_t));
     b->stageBytes = align16(b->offRest + (size_t)n * sizeof(RestoreDesc));
     if ((st = b_alloc(b, &b->d_stage, b->stageBytes)) != CT_OK) return st;
-    const size_t statusInts = (size_t)kModelHdr + 2 * (size_t)n + DWs + B;
+    const size_t statusInts = (size_t)kModelHdr + 2 * (size_t)n + DWs + B + n;
     if (cudaHostAlloc((void**)&b->h_stage, b->stageBytes, cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void**)&b->h_status, statusInts * sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
@@ -230,6 +231,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     CT_CUDA(cudaMemsetAsync(dPruned, 0xff, 2 * (size_t)B * m->nvars * 4, s));
     CT_CUDA(cudaMemsetAsync(dNode, 0, (size_t)B * 4, s));
     CT_CUDA(cudaMemsetAsync(dCtrl, 0, sizeof(ModelCtrl), s));
+    CT_CUDA(cudaMemsetAsync(dSnap, 0, (size_t)n * sizeof(int32_t), s));
     std::vector<TableDev> td(n);
     b->tabVersion.resize(n);
     for (int j = 0; j < n; ++j) {
@@ -249,6 +251,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     M.rowPrefix = dRow;
     M.prunedBy = dPruned;
     M.ctrl = dCtrl;
+    M.snapTaken = dSnap;
     M.dom = reinterpret_cast<uint32_t*>(b->d_stage + b->offDom);
     M.statusBlk = dStatus;
     M.nodeStatus = dNode;
@@ -802,8 +805,9 @@ struct Search {
         info.hard_values += (uint32_t)H[5];
         info.update_bytes += (int64_t)(((uint64_t)(uint32_t)H[9] << 32) | (uint32_t)H[8]);
         info.filter_bytes += (int64_t)(((uint64_t)(uint32_t)H[11] << 32) | (uint32_t)H[10]);
+        const int32_t* snapped = const_cast<const int32_t*>(H) + kModelHdr + 2 * n + (size_t)B * m->DWg + B;
         for (int j = 0; j < n; ++j) {
-            ct_table_batch_done(b->tabs[j], H[kModelHdr + 2 * j], H[kModelHdr + 2 * j + 1]);
+            ct_table_batch_done(b->tabs[j], H[kModelHdr + 2 * j], H[kModelHdr + 2 * j + 1], snapped[j] != 0);
             restPos[j] = -1;
         }
         nrest = 0;

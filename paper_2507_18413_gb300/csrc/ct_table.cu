@@ -71,6 +71,9 @@ struct ct_table {
     int trailTop = 0, trailCap = 0;
     std::vector<int> marks;       // trail position of each saved level
     std::vector<int> levelLive;   // live chunks of each saved level
+    std::vector<int> levelSnap;   // snapshot slot of each saved level: levels saved between two
+                                  // propagations hold one state and share the lowest one's slot
+                                  // (the one-launch fixpoint writes one snapshot for them)
     int live = 0;                 // live chunks of the current state
     int levelCap = 0;
     bool failed = false;
@@ -688,10 +691,15 @@ int ct_table_batch_prepare(ct_table* ct, ModelTabCall* call) {
     return CT_OK;
 }
 
-void ct_table_batch_done(ct_table* ct, int trailTop, int live) {
+void ct_table_batch_done(ct_table* ct, int trailTop, int live, bool snapped) {
     ct->trailTop = trailTop;
     if (live > 0) ct->live = live;
-    ct->pendingFrom = (int)ct->marks.size();
+    // levels stay pending until the launch that first changes the table,
+    // which snapshots them all into the lowest one's slot
+    if (snapped) {
+        for (int l = ct->pendingFrom; l < (int)ct->marks.size(); ++l) ct->levelSnap[l] = ct->pendingFrom;
+        ct->pendingFrom = (int)ct->marks.size();
+    }
     ct->failed = false;
 }
 
@@ -843,6 +851,7 @@ void ct_table_adopt_state(ct_table* dst, const ct_table* src) {
     dst->trailTop = 0;
     dst->marks.clear();
     dst->levelLive.clear();
+    dst->levelSnap.clear();
     dst->pendingFrom = 0;
     dst->failed = false;
 }
@@ -875,7 +884,7 @@ int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
     int need = 0;
     const int mark = ct->marks[level];
     if (!ct->empty && level < ct->pendingFrom) {
-        d->level = level;
+        d->level = ct->levelSnap[level];
         d->mark = mark;
         d->top = ct->trailTop;
         ct->trailTop = mark;
@@ -885,6 +894,7 @@ int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
     ct->live = ct->levelLive[level];
     ct->marks.resize(level);
     ct->levelLive.resize(level);
+    ct->levelSnap.resize(level);
     ct->pendingFrom = std::min(ct->pendingFrom, level);
     return need;
 }
@@ -1092,6 +1102,7 @@ extern "C" int ct_save(ct_table* ct, int* level_out) {
     // level is restored before any propagation changed the state).
     ct->marks.push_back(ct->trailTop);
     ct->levelLive.push_back(ct->live);
+    ct->levelSnap.push_back(L);
     if (level_out) *level_out = L;
     return CT_OK;
 }
@@ -1111,7 +1122,7 @@ extern "C" int ct_restore(ct_table* ct, int level) {
     }
     const int mark = ct->marks[level];
     if (!ct->empty && level < ct->pendingFrom) {
-        CT_CUDA(launch_restore(ct->dev, level, mark, ct->trailTop, -1, ct->stream));
+        CT_CUDA(launch_restore(ct->dev, ct->levelSnap[level], mark, ct->trailTop, -1, ct->stream));
         ct->trailTop = mark;
         if (ct->copyState && ct->h_curr) {
             const int st = fetch_host_curr(ct);
@@ -1123,6 +1134,7 @@ extern "C" int ct_restore(ct_table* ct, int level) {
     ct->live = ct->levelLive[level];
     ct->marks.resize(level);
     ct->levelLive.resize(level);
+    ct->levelSnap.resize(level);
     ct->pendingFrom = std::min(ct->pendingFrom, level);
     return CT_OK;
 }
