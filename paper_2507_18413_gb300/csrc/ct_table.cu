@@ -61,7 +61,7 @@ struct ct_table {
     int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
     bool localPlan = true;
     int variant = 1;
-    int pendingFrom = 0;  // levels [pendingFrom, marks.size()) are not snapshotted yet
+    int pendingFrom = 0;  // levels [pendingFrom, levels.size()) are not snapshotted yet
     int version = 0;      // bumped when device buffers behind `dev` are reallocated
     TableDev dev{};
     cudaStream_t stream = nullptr;
@@ -69,11 +69,13 @@ struct ct_table {
     int32_t* h_status = nullptr;
     size_t statusInts = 0;
     int trailTop = 0, trailCap = 0;
-    std::vector<int> marks;       // trail position of each saved level
-    std::vector<int> levelLive;   // live chunks of each saved level
-    std::vector<int> levelSnap;   // snapshot slot of each saved level: levels saved between two
-                                  // propagations hold one state and share the lowest one's slot
-                                  // (the one-launch fixpoint writes one snapshot for them)
+    struct Level {
+        int mark;  // trail position
+        int live;  // live chunks
+        int snap;  // snapshot slot: levels saved between two propagations hold one state and
+                   // share the lowest one's slot (the one-launch fixpoint writes one snapshot)
+    };
+    std::vector<Level> levels;    // the saved levels, oldest first
     int live = 0;                 // live chunks of the current state
     int levelCap = 0;
     bool failed = false;
@@ -181,7 +183,7 @@ int ensure_levels(ct_table* ct, int need) {
         ct_set_error("level stack growth: %s", cudaGetErrorString(e));
         return CT_ERR_OOM;
     }
-    const int used = (int)ct->marks.size();
+    const int used = (int)ct->levels.size();
     if (used > 0) {
         CT_CUDA(cudaMemcpyAsync(ns, ct->dev.levelSeg, (size_t)used * ct->nseg * sizeof(uint32_t),
                                 cudaMemcpyDeviceToDevice, ct->stream));
@@ -568,15 +570,15 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         return CT_ERR_STATE;
     }
     int st;
-    if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
+    if (!ct->levels.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
     cudaStream_t s = ct->stream;
     int32_t* h = ct->h_status;
     volatile int32_t* hv = h;
     const auto t0 = std::chrono::steady_clock::now();
     CallParams P{};
-    P.mark = ct->marks.empty() ? -1 : ct->marks.back();
+    P.mark = ct->levels.empty() ? -1 : ct->levels.back().mark;
     P.snapFrom = ct->pendingFrom;
-    P.snapTo = (int)ct->marks.size();
+    P.snapTo = (int)ct->levels.size();
     P.prevLive = ct->live;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
@@ -598,7 +600,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         ct->evPending += 1;
     }
     const auto t1 = std::chrono::steady_clock::now();
-    ct->pendingFrom = (int)ct->marks.size();
+    ct->pendingFrom = (int)ct->levels.size();
     // Wait for the status word the kernel publishes last (bounded), then fall
     // back to a stream synchronisation to collect any CUDA error.
     bool seen = false;
@@ -683,10 +685,10 @@ int ct_table_batch_prepare(ct_table* ct, ModelTabCall* call) {
         return CT_ERR_TIMEOUT;
     }
     int st;
-    if (!ct->marks.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
-    call->mark = ct->marks.empty() ? -1 : ct->marks.back();
+    if (!ct->levels.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
+    call->mark = ct->levels.empty() ? -1 : ct->levels.back().mark;
     call->snapFrom = ct->pendingFrom;
-    call->snapTo = (int)ct->marks.size();
+    call->snapTo = (int)ct->levels.size();
     call->pad = 0;
     return CT_OK;
 }
@@ -697,8 +699,8 @@ void ct_table_batch_done(ct_table* ct, int trailTop, int live, bool snapped) {
     // levels stay pending until the launch that first changes the table,
     // which snapshots them all into the lowest one's slot
     if (snapped) {
-        for (int l = ct->pendingFrom; l < (int)ct->marks.size(); ++l) ct->levelSnap[l] = ct->pendingFrom;
-        ct->pendingFrom = (int)ct->marks.size();
+        for (int l = ct->pendingFrom; l < (int)ct->levels.size(); ++l) ct->levels[l].snap = ct->pendingFrom;
+        ct->pendingFrom = (int)ct->levels.size();
     }
     ct->failed = false;
 }
@@ -849,9 +851,7 @@ int ct_table_trail_cap(const ct_table* ct) { return ct->trailCap; }
 void ct_table_adopt_state(ct_table* dst, const ct_table* src) {
     dst->live = src->live;
     dst->trailTop = 0;
-    dst->marks.clear();
-    dst->levelLive.clear();
-    dst->levelSnap.clear();
+    dst->levels.clear();
     dst->pendingFrom = 0;
     dst->failed = false;
 }
@@ -865,7 +865,7 @@ int ct_table_save_host(ct_table* ct) {
     return ct_save(ct, &lv);
 }
 
-int ct_table_depth(const ct_table* ct) { return (int)ct->marks.size(); }
+int ct_table_depth(const ct_table* ct) { return (int)ct->levels.size(); }
 
 int ct_table_restore_device(ct_table* ct, const RestoreDesc& d) {
     CT_CUDA(launch_restore(ct->dev, d.level, d.mark, d.top, -1, ct->stream));
@@ -873,8 +873,8 @@ int ct_table_restore_device(ct_table* ct, const RestoreDesc& d) {
 }
 
 int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
-    if (level < 0 || level >= (int)ct->marks.size()) {
-        ct_set_error("restore: level %d not in [0, %d)", level, (int)ct->marks.size());
+    if (level < 0 || level >= (int)ct->levels.size()) {
+        ct_set_error("restore: level %d not in [0, %d)", level, (int)ct->levels.size());
         return CT_ERR_LEVEL;
     }
     if (ct->broken) {
@@ -882,19 +882,17 @@ int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
         return CT_ERR_TIMEOUT;
     }
     int need = 0;
-    const int mark = ct->marks[level];
+    const int mark = ct->levels[level].mark;
     if (!ct->empty && level < ct->pendingFrom) {
-        d->level = ct->levelSnap[level];
+        d->level = ct->levels[level].snap;
         d->mark = mark;
         d->top = ct->trailTop;
         ct->trailTop = mark;
         need = 1;
     }
     ct->failed = false;
-    ct->live = ct->levelLive[level];
-    ct->marks.resize(level);
-    ct->levelLive.resize(level);
-    ct->levelSnap.resize(level);
+    ct->live = ct->levels[level].live;
+    ct->levels.resize(level);
     ct->pendingFrom = std::min(ct->pendingFrom, level);
     return need;
 }
@@ -1093,16 +1091,14 @@ extern "C" int ct_save(ct_table* ct, int* level_out) {
         ct_set_error("ct_save: the previous call failed; restore a level first");
         return CT_ERR_STATE;
     }
-    const int L = (int)ct->marks.size();
+    const int L = (int)ct->levels.size();
     if (!ct->empty) {
         int st;
         if ((st = ensure_levels(ct, L + 1)) != CT_OK) return st;
     }
     // The snapshot itself is taken by the next propagation (or never, if the
     // level is restored before any propagation changed the state).
-    ct->marks.push_back(ct->trailTop);
-    ct->levelLive.push_back(ct->live);
-    ct->levelSnap.push_back(L);
+    ct->levels.push_back(ct_table::Level{ct->trailTop, ct->live, L});
     if (level_out) *level_out = L;
     return CT_OK;
 }
@@ -1112,17 +1108,17 @@ extern "C" int ct_restore(ct_table* ct, int level) {
         ct_set_error("ct_restore: null handle");
         return CT_ERR_ARG;
     }
-    if (level < 0 || level >= (int)ct->marks.size()) {
-        ct_set_error("ct_restore: level %d not in [0, %d)", level, (int)ct->marks.size());
+    if (level < 0 || level >= (int)ct->levels.size()) {
+        ct_set_error("ct_restore: level %d not in [0, %d)", level, (int)ct->levels.size());
         return CT_ERR_LEVEL;
     }
     if (ct->broken) {
         ct_set_error("ct_restore: the table is unusable after a device-side timeout");
         return CT_ERR_TIMEOUT;
     }
-    const int mark = ct->marks[level];
+    const int mark = ct->levels[level].mark;
     if (!ct->empty && level < ct->pendingFrom) {
-        CT_CUDA(launch_restore(ct->dev, ct->levelSnap[level], mark, ct->trailTop, -1, ct->stream));
+        CT_CUDA(launch_restore(ct->dev, ct->levels[level].snap, mark, ct->trailTop, -1, ct->stream));
         ct->trailTop = mark;
         if (ct->copyState && ct->h_curr) {
             const int st = fetch_host_curr(ct);
@@ -1131,10 +1127,8 @@ extern "C" int ct_restore(ct_table* ct, int level) {
     }
     // A level saved after the last propagation still equals the current state.
     ct->failed = false;
-    ct->live = ct->levelLive[level];
-    ct->marks.resize(level);
-    ct->levelLive.resize(level);
-    ct->levelSnap.resize(level);
+    ct->live = ct->levels[level].live;
+    ct->levels.resize(level);
     ct->pendingFrom = std::min(ct->pendingFrom, level);
     return CT_OK;
 }
@@ -1210,7 +1204,7 @@ extern "C" int ct_get_info(ct_table* ct, ct_table_info* info) {
     r.segments = ct->nseg;
     r.seg_capacity = ct->S;
     r.trail_size = ct->trailTop;
-    r.depth = (int)ct->marks.size();
+    r.depth = (int)ct->levels.size();
     r.local_plan = ct->localPlan ? 1 : 0;
     r.grid_blocks = ct->grid;
     r.short_tuples = (int32_t)std::min<int64_t>(ct->shortTuples, 0x7fffffff);
