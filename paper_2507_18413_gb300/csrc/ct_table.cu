@@ -61,13 +61,9 @@ struct ct_table {
     int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
     bool localPlan = true;
     int variant = 1;
+    // state read on every call and every step of a batched search, kept together
     int pendingFrom = 0;  // levels [pendingFrom, levels.size()) are not snapshotted yet
     int version = 0;      // bumped when device buffers behind `dev` are reallocated
-    TableDev dev{};
-    cudaStream_t stream = nullptr;
-    bool ownStream = false;
-    int32_t* h_status = nullptr;
-    size_t statusInts = 0;
     int trailTop = 0, trailCap = 0;
     struct Level {
         int mark;  // trail position
@@ -81,12 +77,17 @@ struct ct_table {
     bool failed = false;
     bool broken = false;  // a device-side wait ran out: the table is unusable
     bool empty = false;
+    TableDev dev{};
+    cudaStream_t stream = nullptr;
+    bool ownStream = false;
+    int32_t* h_status = nullptr;
+    size_t statusInts = 0;
     ct_call_stats last{};
     bool profile = false;
     // profile: event pairs around launches, read back lazily (a ring of pairs;
     // the oldest pair is read when the ring is full or the profile is asked for)
     static constexpr int kEvRing = 4096;
-    cudaEvent_t ev[2 * kEvRing] = {};
+    std::vector<cudaEvent_t> ev;  // 2 * kEvRing events, created when profiling is first on
     int evNext = 0, evPending = 0;
     ct_profile prof{};
     int64_t deviceBytes = 0;
@@ -132,6 +133,13 @@ int sync(ct_table* ct) {
 }
 
 // Grow the trail so that `need` entries fit.
+// The event ring of ct_options.profile (created once, on first use).
+int create_events(ct_table* ct) {
+    ct->ev.assign(2 * ct_table::kEvRing, nullptr);
+    for (auto& e : ct->ev) CT_CUDA(cudaEventCreate(&e));
+    return CT_OK;
+}
+
 int ensure_trail(ct_table* ct, int64_t need) {
     if (need <= ct->trailCap) return CT_OK;
     if (need > 0x7fffffffLL) {
@@ -472,7 +480,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = sync(ct)) != CT_OK) return st;
     if ((st = ensure_levels(ct, 8)) != CT_OK) return st;
     if (ct->profile) {
-        for (auto& e : ct->ev) CT_CUDA(cudaEventCreate(&e));
+        if ((st = create_events(ct)) != CT_OK) return st;
     }
     return sync(ct);
 }
@@ -1244,8 +1252,9 @@ extern "C" int ct_set_profile(ct_table* ct, int on) {
         ct_set_error("ct_set_profile: null handle");
         return CT_ERR_ARG;
     }
-    if (on && !ct->ev[0]) {
-        for (auto& e : ct->ev) CT_CUDA(cudaEventCreate(&e));
+    if (on && ct->ev.empty()) {
+        const int st = create_events(ct);
+        if (st != CT_OK) return st;
     }
     if (!on) {
         const int st = drain_events(ct);
