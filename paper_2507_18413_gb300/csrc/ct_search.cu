@@ -361,6 +361,7 @@ struct Search {
     std::chrono::steady_clock::time_point t0;
 
     uint32_t* slotDom(int s) { return b->domHost() + (size_t)s * m->DWg; }
+    const uint32_t* slotDom(int s) const { return b->domHost() + (size_t)s * m->DWg; }
 
     void record_solution(const std::vector<uint8_t>& path, const uint32_t* dom) {
         st.solutions += 1;
@@ -707,7 +708,7 @@ struct Search {
     // or first-fail); -1 when every variable is fixed.
     int pick(int s) const {
         int x = -1;
-        const uint32_t* dom = const_cast<Search*>(this)->slotDom(s);
+        const uint32_t* dom = slotDom(s);
         if (scores) {
             const float* sc = scores + (size_t)s * m->nvars;
             for (int v = 0; v < m->nvars; ++v)
