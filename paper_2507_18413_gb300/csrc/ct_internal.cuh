@@ -242,13 +242,7 @@ int ct_cuda_fail(cudaError_t e, const char* what);
 int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
                           uint32_t* changed);
 const int32_t* ct_table_status_host(const ct_table* ct);
-const ctk::TableDev& ct_table_dev(const ct_table* ct);
-int ct_table_version(const ct_table* ct);
 int ct_table_is_empty(const ct_table* ct);
-int ct_table_batch_prepare(ct_table* ct, ctk::ModelTabCall* call);
-void ct_table_batch_done(ct_table* ct, int trailTop, int live, bool snapped);
-// Host bookkeeping of a restore; returns 1 (and fills d) when a device undo is needed.
-int ct_table_restore_prepare(ct_table* ct, int level, ctk::RestoreDesc* d);
 int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);
 // Device memory handed out in 256-byte aligned pieces of one allocation (the
 // batched search's table clones); its owner frees it as a whole.
@@ -269,7 +263,6 @@ size_t ct_table_clone_bytes(const ct_table* src);
 // given (else from cudaMalloc), its Ctrl is `ctrl` when given.
 ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* arena, ctk::Ctrl* ctrl, int* status);
 void ct_table_free(ct_table* ct);
-int ct_table_save_host(ct_table* ct);
 int ct_table_depth(const ct_table* ct);
 void ct_table_adopt_state(ct_table* dst, const ct_table* src);
 int ct_table_live(const ct_table* ct);

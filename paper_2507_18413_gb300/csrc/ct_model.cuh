@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "ct_learn.cuh"
+#include "ct_table.cuh"
 
 struct ct_batch;  // the slots of a batched search (ct_search.cu)
 

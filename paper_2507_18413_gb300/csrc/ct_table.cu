@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "ct_internal.cuh"
+#include "ct_table.cuh"
 
 using namespace ctk;
 
@@ -50,57 +50,6 @@ extern "C" const char* ct_status_string(int s) {
 
 extern "C" int ct_version(void) { return 10000; }
 
-// ---------------------------------------------------------------------------
-// the table object
-// ---------------------------------------------------------------------------
-struct ct_table {
-    int arity = 0;
-    std::vector<int32_t> lo, size, nw, ld, row0, rowVar;
-    int R = 0;
-    int64_t t = 0, W = 0, W4 = 0;
-    int nseg = 0, S = 32, grid = 1, DW = 0, nChW = 0;
-    bool localPlan = true;
-    int variant = 1;
-    // state read on every call and every step of a batched search, kept together
-    int pendingFrom = 0;  // levels [pendingFrom, levels.size()) are not snapshotted yet
-    int version = 0;      // bumped when device buffers behind `dev` are reallocated
-    int trailTop = 0, trailCap = 0;
-    struct Level {
-        int mark;  // trail position
-        int live;  // live chunks
-        int snap;  // snapshot slot: levels saved between two propagations hold one state and
-                   // share the lowest one's slot (the one-launch fixpoint writes one snapshot)
-    };
-    std::vector<Level> levels;    // the saved levels, oldest first
-    int live = 0;                 // live chunks of the current state
-    int levelCap = 0;
-    bool failed = false;
-    bool broken = false;  // a device-side wait ran out: the table is unusable
-    bool empty = false;
-    TableDev dev{};
-    cudaStream_t stream = nullptr;
-    bool ownStream = false;
-    int32_t* h_status = nullptr;
-    size_t statusInts = 0;
-    ct_call_stats last{};
-    bool profile = false;
-    // profile: event pairs around launches, read back lazily (a ring of pairs;
-    // the oldest pair is read when the ring is full or the profile is asked for)
-    static constexpr int kEvRing = 4096;
-    std::vector<cudaEvent_t> ev;  // 2 * kEvRing events, created when profiling is first on
-    int evNext = 0, evPending = 0;
-    ct_profile prof{};
-    int64_t deviceBytes = 0;
-    uint32_t* d_domScratch = nullptr;
-    std::vector<void*> allocs;
-    int64_t shortTuples = 0;     // retained tuples with a wildcard
-    bool negative = false;       // the tuples are forbidden
-    bool autotuned = false;      // launch shape chosen by trial propagations
-    bool copyState = false;      // ablation: currTable round-trips through h_curr every call
-    uint32_t* h_curr = nullptr;  // pinned host copy of currTable (copy_state)
-    bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
-    bool levelsInArena = false;
-};
 
 namespace {
 
@@ -683,35 +632,10 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
 const int32_t* ct_table_status_host(const ct_table* ct) { return ct->h_status; }
 
 // --- the batched network path (ct_model.cu) ---
-const TableDev& ct_table_dev(const ct_table* ct) { return ct->dev; }
-int ct_table_version(const ct_table* ct) { return ct->version; }
 int ct_table_is_empty(const ct_table* ct) { return ct->empty ? 1 : 0; }
 
-int ct_table_batch_prepare(ct_table* ct, ModelTabCall* call) {
-    if (ct->broken) {
-        ct_set_error("a table is unusable after a device-side timeout");
-        return CT_ERR_TIMEOUT;
-    }
-    int st;
-    if (!ct->levels.empty() && (st = ensure_trail(ct, (int64_t)ct->trailTop + ct->W4)) != CT_OK) return st;
-    call->mark = ct->levels.empty() ? -1 : ct->levels.back().mark;
-    call->snapFrom = ct->pendingFrom;
-    call->snapTo = (int)ct->levels.size();
-    call->pad = 0;
-    return CT_OK;
-}
+int ct_table_grow_trail(ct_table* ct, int64_t need) { return ensure_trail(ct, need); }
 
-void ct_table_batch_done(ct_table* ct, int trailTop, int live, bool snapped) {
-    ct->trailTop = trailTop;
-    if (live > 0) ct->live = live;
-    // levels stay pending until the launch that first changes the table,
-    // which snapshots them all into the lowest one's slot
-    if (snapped) {
-        for (int l = ct->pendingFrom; l < (int)ct->levels.size(); ++l) ct->levels[l].snap = ct->pendingFrom;
-        ct->pendingFrom = (int)ct->levels.size();
-    }
-    ct->failed = false;
-}
 
 namespace {
 
@@ -868,10 +792,6 @@ int ct_table_live(const ct_table* ct) { return ct->live; }
 
 void ct_table_free(ct_table* ct) { free_table(ct); }
 
-int ct_table_save_host(ct_table* ct) {
-    int lv = 0;
-    return ct_save(ct, &lv);
-}
 
 int ct_table_depth(const ct_table* ct) { return (int)ct->levels.size(); }
 
@@ -880,30 +800,6 @@ int ct_table_restore_device(ct_table* ct, const RestoreDesc& d) {
     return CT_OK;
 }
 
-int ct_table_restore_prepare(ct_table* ct, int level, RestoreDesc* d) {
-    if (level < 0 || level >= (int)ct->levels.size()) {
-        ct_set_error("restore: level %d not in [0, %d)", level, (int)ct->levels.size());
-        return CT_ERR_LEVEL;
-    }
-    if (ct->broken) {
-        ct_set_error("restore: the table is unusable after a device-side timeout");
-        return CT_ERR_TIMEOUT;
-    }
-    int need = 0;
-    const int mark = ct->levels[level].mark;
-    if (!ct->empty && level < ct->pendingFrom) {
-        d->level = ct->levels[level].snap;
-        d->mark = mark;
-        d->top = ct->trailTop;
-        ct->trailTop = mark;
-        need = 1;
-    }
-    ct->failed = false;
-    ct->live = ct->levels[level].live;
-    ct->levels.resize(level);
-    ct->pendingFrom = std::min(ct->pendingFrom, level);
-    return need;
-}
 int ct_table_dom_words(const ct_table* ct) { return ct->DW; }
 const int32_t* ct_table_var_ld(const ct_table* ct) { return ct->ld.data(); }
 int ct_table_changed_words(const ct_table* ct) { return ct->nChW; }
