@@ -39,6 +39,7 @@ constexpr int32_t kCodeDelta = 1 << 29;  // variable on the delta path: mask = ~
 constexpr int32_t kCodeRow = (1 << 29) - 1;
 constexpr int kLocalProbes = 4;          // windows of 32 chunks searched after a residue miss (one table)
 constexpr int kModelProbes = 8;          // the same in the network kernel (live chunks)
+constexpr int kWidePublish = 2048;       // network kernel: tables from which the whole grid publishes
 constexpr int kWindowGroups = 8;         // index segments read for them: at most 8 x 32 (8,192 chunks)
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync

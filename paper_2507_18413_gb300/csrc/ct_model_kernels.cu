@@ -423,13 +423,18 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
     }
 
-    // publish (CTA 0; every CTA left the loop at the same point)
-    if (blockIdx.x != 0) return;
+    // publish (every CTA left the loop at the same point): the per-table
+    // results and resets by CTA 0 alone for a small network, by the whole grid
+    // for a large one (then a barrier); CTA 0 releases the status word last
+    const bool wide = M.ntables >= kWidePublish;
+    if (!wide && blockIdx.x != 0) return;
     phase(6);
     __threadfence();
     __syncthreads();
+    const int ptid = wide ? blockIdx.x * kThreads + tid : tid;
+    const int pth = wide ? gridDim.x * kThreads : kThreads;
     int32_t* H = M.statusBlk;
-    for (int t = tid; t < M.ntables; t += kThreads) {
+    for (int t = ptid; t < M.ntables; t += pth) {
         Ctrl* Tc = M.tabs[t].ctrl;
         H[kModelHdr + 2 * t] = __ldcg(&Tc->trail_top);
         H[kModelHdr + 2 * t + 1] = __ldcg(&Tc->live_state);
@@ -439,19 +444,26 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         Tc->status = CT_OK;
     }
     uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kModelHdr + 2 * M.ntables);
-    for (int q = tid; q < M.DWg; q += kThreads) outDom[q] = __ldcg(&M.dom[q]);
+    for (int q = ptid; q < M.DWg; q += pth) outDom[q] = __ldcg(&M.dom[q]);
     const int nnodes = M.ntables / M.nodeTables;
     int32_t* outNode = H + kModelHdr + 2 * M.ntables + M.DWg;
-    for (int q = tid; q < nnodes; q += kThreads) {
+    for (int q = ptid; q < nnodes; q += pth) {
         outNode[q] = __ldcg(&M.nodeStatus[q]);
         M.nodeStatus[q] = CT_OK;
     }
     int32_t* outSnap = outNode + nnodes;
-    for (int t = tid; t < M.ntables; t += kThreads) {
+    for (int t = ptid; t < M.ntables; t += pth) {
         outSnap[t] = __ldcg(&M.snapTaken[t]);
         M.snapTaken[t] = 0;
     }
-    for (int v = tid; v < 2 * M.nvars; v += kThreads) M.prunedBy[v] = -1;
+    for (int v = ptid; v < 2 * M.nvars; v += pth) M.prunedBy[v] = -1;
+    if (wide) {
+        // every CTA's writes to the host-mapped block are visible system-wide
+        // before CTA 0 publishes the status word
+        __threadfence_system();
+        if (!sync()) return;
+        if (blockIdx.x != 0) return;
+    }
     __syncthreads();
     if (tid == 0) {
         const int st = __ldcg(&C->status);
