@@ -320,7 +320,8 @@ def run_ours(args, rank, world):
         if s >= args.warmup:
             step_ms.append(ev0.elapsed_time(ev1))
             props += n
-            launches += KERNELS_PER_PROPAGATE * n + ns + nr
+            # one launch per propagation and per restore; ct_save launches nothing
+            launches += KERNELS_PER_PROPAGATE * n + nr
     clocks = clocks_stop(clk)
     if world > 1:
         torch.distributed.barrier()
