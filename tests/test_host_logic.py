@@ -1,0 +1,99 @@
+"""Host-side logic that runs without a GPU: the seeded workload generators'
+structure, the learned-order comparison summary, and the all-cores CPU
+baseline of the bench."""
+import math
+import types
+
+import numpy as np
+import pytest
+
+from oracle import ct_oracle as O
+from paper_2507_18413_gb300 import ct as C
+from paper_2507_18413_gb300 import inputs as G
+from paper_2507_18413_gb300 import learn as L
+
+
+def test_planning_chain_structure_and_a_plan_exists():
+    """Variables s_0..s_H then a_0..a_{H-1}; s_0 and s_H fixed; every step's
+    table holds each (s, a)'s successor plus 0-3 alternatives, the same
+    relation at every step; the oracle's search finds a plan."""
+    H, S, A = 5, 12, 3
+    spec = G.planning_csp(4, states=S, actions=A, horizon=H)
+    assert spec.nvars == 2 * H + 1
+    assert spec.dom_size[0] == 1 and spec.dom_lo[0] == 0 and spec.dom_size[H] == 1
+    assert spec.dom_size[1:H] == [S] * (H - 1) and spec.dom_size[H + 1:] == [A] * H
+    rel = spec.tables[0].tuples
+    for t, tb in enumerate(spec.tables):
+        assert tb.scope == [t, H + 1 + t, t + 1]
+        assert np.array_equal(tb.tuples, rel)
+    pairs, counts = np.unique(rel[:, :2], axis=0, return_counts=True)
+    assert len(pairs) == S * A and counts.min() >= 1 and counts.max() <= 4
+    assert len(np.unique(rel, axis=0)) == len(rel), "successor and alternatives are distinct"
+    csp = O.Csp(spec.dom_lo, spec.dom_size)
+    for tb in spec.tables:
+        csp.add_table(tb.scope, tb.tuples)
+    r = O.dfs(csp, count_all=False)
+    assert r.solutions == 1 and r.first_solution[0] == 0
+
+
+def test_network_tables_shapes():
+    spec = G.network_tables(7, ntables=24, nvars=40, arity=(2, 5), tuples=(50, 400), dom=(4, 9))
+    assert len(spec.tables) == 24 and spec.nvars == 40
+    assert all(4 <= d <= 9 for d in spec.dom_size)
+    for k, tb in enumerate(spec.tables):
+        a = len(tb.scope)
+        assert 2 <= a <= 5 and len(set(tb.scope)) == a
+        ds = np.array([spec.dom_size[v] for v in tb.scope])
+        assert tb.tuples.shape[1] == a
+        assert (tb.tuples >= 0).all() and (tb.tuples < ds).all()
+        if k % 2 == 0:  # distinct uniform tuples
+            assert len(np.unique(tb.tuples, axis=0)) == len(tb.tuples)
+    again = G.network_tables(7, ntables=24, nvars=40, arity=(2, 5), tuples=(50, 400), dom=(4, 9))
+    assert all(np.array_equal(a.tuples, b.tuples) for a, b in zip(spec.tables, again.tables)), "seeded"
+
+
+def _row(ff, lr, ffb=None, lrb=None):
+    def arm(n, s, fin=True):
+        return {"nodes": n, "seconds": s, "finished": fin, "solution": True}
+    r = {"nvars": 5, "tables": 3, "first_fail": arm(*ff), "learned": arm(*lr)}
+    if ffb:
+        r["first_fail_batched"] = arm(*ffb)
+        r["learned_batched"] = arm(*lrb)
+    return r
+
+
+def test_learned_summary_arithmetic():
+    rows = [_row((100, 1.0), (50, 2.0), (80, 0.5), (40, 0.25)),
+            _row((10, 0.1), (40, 0.4), (10, 0.2), (5, 0.05)),
+            _row((30, 0.3, False), (20, 0.2), (30, 0.3), (20, 0.2))]
+    s = L.summarize(rows)
+    assert s["instances"] == 3 and s["finished_by_all"] == 2
+    assert s["first_fail"]["finished"] == 2 and s["learned"]["finished"] == 3
+    assert s["learned"]["nodes"] == 110 and math.isclose(s["learned"]["seconds"], 2.6)
+    # geometric means over the two instances every arm finished
+    assert math.isclose(s["learned"]["geomean_nodes_vs_first_fail"], round(math.sqrt(0.5 * 4.0), 3))
+    assert math.isclose(s["learned"]["geomean_time_vs_first_fail"], round(math.sqrt(2.0 * 4.0), 3))
+    assert math.isclose(s["learned_batched"]["geomean_nodes_vs_first_fail"], round(math.sqrt(0.4 * 0.5), 3))
+    assert s["first_fail"]["geomean_nodes_vs_first_fail"] == 1.0
+
+
+def test_all_cores_cpu_baseline_replays_the_plans():
+    """One replica per core replays save / propagate / restore plans of a
+    small table and reports propagations per second over its threads."""
+    bench = pytest.importorskip("bench")
+    dom_lo, dom_size, tup = G.large_table(seed=1, t=3000, arity=4, d=8)
+    rng = G.Rng(3)
+    plans = []
+    for s in range(3):
+        rp = types.SimpleNamespace(inputs=[], ops=[])
+        masks = [np.ones(d, bool) for d in dom_size]
+        for c in range(4):
+            new = bench.next_edit(rng, masks)
+            rp.inputs.append(C.masks_to_words(new))
+            rp.ops += [("save",), ("prop", c)]
+            masks = new
+        rp.ops.append(("restore", 1))
+        plans.append(rp)
+    r = bench.cpu_bitset_baseline_cores(types.SimpleNamespace(), plans, dom_lo, dom_size, tup, seconds=0.3)
+    assert r["cores"] >= 1 and r["value"] > 0
+    assert r["kind"].startswith("serial bitset CT")
