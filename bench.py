@@ -112,11 +112,18 @@ def clocks_start(gpu_index):
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     try:
-        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                 "-lms", "200", "-i", str(gpu_index)],
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "50", "-i", str(gpu_index)],
                                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except (OSError, FileNotFoundError):
         return None
+    # the first sample (taken before the timed region, discarded) shows the
+    # sampler is running when the timed region starts; wait at most 5 s for it
+    import select
+    ready, _, _ = select.select([proc.stdout], [], [], 5.0)
+    if ready:
+        proc.stdout.readline()
+    return proc
 
 
 def clocks_stop(proc):
