@@ -457,6 +457,7 @@ def run_ours(args, rank, world):
         result["extra"] = extras(args, C, torch, stream)
     if rank == 0:
         result["cpu_baseline"] = cpu_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
+        result["cpu_baseline"]["cpu"] = cpu_model()
         result["cpu_baseline_bitset"] = cpu_bitset_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
         if not args.no_extra:
             result["cpu_baseline_bitset_all_cores"] = cpu_bitset_baseline_cores(args, plans[args.warmup:], dom_lo,
@@ -804,6 +805,18 @@ def cpu_bitset_baseline(args, plans, dom_lo, dom_size, tup, seconds=8.0):
     ct.close()
     return {"value": round(done / dt, 1), "unit": UNIT, "cores": 1, "kind": "serial bitset CT (Algorithms 1-3)",
             "sample": f"{done} propagations of the timed stream with their saves/restores, {dt:.1f} s, one thread"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return None
+    for line in out.splitlines():
+        if line.strip().lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    return None
 
 
 def cpu_bitset_baseline_cores(args, plans, dom_lo, dom_size, tup, seconds=6.0):
