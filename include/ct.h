@@ -308,7 +308,8 @@ int ct_sharded_create(int arity, const int32_t* dom_lo, const int32_t* dom_size,
  * its own device copy of dom_bits, and dom_bits (device, in/out) becomes the
  * OR of the copies. changed_vars as in ct_propagate. CT_INFEASIBLE iff a
  * domain became empty; the shards are then restored with ct_sharded_restore
- * before the next call. Blocks until the result is known. */
+ * before the next call. dom_bits is read and written on the stream given to
+ * ct_sharded_create; the call blocks until the result is known. */
 int ct_sharded_propagate(ct_sharded* sh, uint32_t* dom_bits, uint32_t* changed_vars);
 
 /* ct_sharded_save / ct_sharded_restore: ct_save / ct_restore on every shard
