@@ -97,3 +97,29 @@ def test_all_cores_cpu_baseline_replays_the_plans():
     r = bench.cpu_bitset_baseline_cores(types.SimpleNamespace(), plans, dom_lo, dom_size, tup, seconds=0.3)
     assert r["cores"] >= 1 and r["value"] > 0
     assert r["kind"].startswith("serial bitset CT")
+
+
+class _FakeSampler:
+    """Stands in for the nvidia-smi process of the bench's clock record."""
+
+    def __init__(self, text):
+        self.text = text
+
+    def terminate(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+
+def test_clock_record_parsing():
+    bench = pytest.importorskip("bench")
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2055, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 1980, 2070, 1400.0, 0x8, Active, Not Active, Not Active, Active",
+             "garbage line"]
+    r = bench.clocks_stop(_FakeSampler("\n".join(lines) + "\n"))
+    assert r["samples"] == 3 and r["sm_mhz"] == 2055.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.clocks_stop(_FakeSampler("")) is None
+    assert bench.clocks_stop(None) is None
