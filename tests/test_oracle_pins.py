@@ -387,3 +387,55 @@ def test_pins_catch_planted_branching_mistake(monkeypatch, golden_dir):
     monkeypatch.setattr(O, "select_first_fail", max_first)
     with pytest.raises(AssertionError):
         test_table1_search_tree(golden_dir)
+
+
+# --------------------------------------------------------------------------
+# currTable packing beyond word 0 (Sec. 3: 32-bit words)
+# --------------------------------------------------------------------------
+
+def test_pack_words_multiword_hand_computed():
+    """Tuple j sits at word j // 32, bit j % 32 (Sec. 3 fixes 32-bit words; the bit
+    order is the reading pinned by Table 1(c)). Worked by hand: 70 tuples with
+    validity bits at 0, 31, 32, 33 and 69 give word 0 = bits 0 and 31 =
+    0x80000001, word 1 = bits 0 and 1 = 0x3, word 2 = bit 5 (69 - 64) = 0x20."""
+    bits = np.zeros(70, dtype=bool)
+    bits[[0, 31, 32, 33, 69]] = True
+    assert O.pack_words(bits).tolist() == [0x80000001, 0x3, 0x20]
+    # word count: ceil(t / 32); a 97th tuple opens a fourth word
+    assert O.pack_words(np.zeros(96, dtype=bool)).tolist() == [0, 0, 0]
+    b97 = np.zeros(97, dtype=bool)
+    b97[96] = True
+    assert O.pack_words(b97).tolist() == [0, 0, 0, 1]
+    # currTable of a table is the packed validity vector: tuples 32..63 valid
+    # (value 1 of a unary table) fill word 1 and nothing else
+    tup = np.array([[0]] * 32 + [[1]] * 32 + [[0]] * 6, dtype=np.int64)
+    st, _, valid = O.gac_table(tup, [0], [np.array([False, True])])
+    assert st == O.OK
+    assert O.currtable_words(valid).tolist() == [0, 0xFFFFFFFF, 0]
+
+
+def _pack_reversed_words(bits):
+    bits = np.asarray(bits, dtype=bool)
+    nw = (bits.shape[0] + 31) // 32
+    w = np.zeros(nw, dtype=np.uint64)
+    for j in np.flatnonzero(bits):
+        w[nw - 1 - j // 32] |= np.uint64(1) << np.uint64(j % 32)
+    return w.astype(np.uint32)
+
+
+def _pack_split_off_by_one(bits):
+    bits = np.asarray(bits, dtype=bool)
+    nw = (bits.shape[0] + 31) // 32
+    w = np.zeros(nw, dtype=np.uint64)
+    for j in np.flatnonzero(bits):
+        w[min(j // 31, nw - 1)] |= np.uint64(1) << np.uint64(j % 32)
+    return w.astype(np.uint32)
+
+
+@pytest.mark.parametrize("mutant", [_pack_reversed_words, _pack_split_off_by_one])
+def test_pins_catch_planted_word_index_mistakes(monkeypatch, mutant, golden_dir):
+    """Both mutants pass the Table 1 pins (5 tuples, one word) but not the multi-word pin."""
+    monkeypatch.setattr(O, "pack_words", mutant)
+    test_table1_currtable_and_filter(golden_dir)
+    with pytest.raises(AssertionError):
+        test_pack_words_multiword_hand_computed()
