@@ -82,6 +82,11 @@ typedef struct ct_options {
                                  value is cleared, status CT_OK), and the last-seen domains keep
                                  the call's input domains, since another shard may support a
                                  value this one cleared. Positive tables only. */
+    int32_t no_split;         /* 1 = updateTable gives each 32-chunk segment to one warp, which walks
+                                 the call's whole row list (default: the row list of a segment is
+                                 cut over up to 8 warps of a CTA, one batch of row loads each where
+                                 the list allows, and their partial masks are combined in shared
+                                 memory; results are the same). */
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */
@@ -245,6 +250,17 @@ int ct_set_profile(ct_table* ct, int on);
 
 /* ct_destroy: free the table (NULL is accepted). */
 int ct_destroy(ct_table* ct);
+
+/* ct_arm_wait_timeout: test hook for the bounded device waits (no fault, no
+ * hang). The next ct_propagate on `ct` (ct == NULL: the next
+ * ct_propagate_noalloc on the calling thread's current device) starts with its
+ * grid barrier's arrival count set where no CTA can complete it, and with each
+ * barrier wait limited to `polls` polls (> 0): every wait runs out, the kernel
+ * records CT_ERR_TIMEOUT and returns without publishing, and that call
+ * returns CT_ERR_TIMEOUT. A table whose wait ran out refuses every later
+ * propagate and restore with CT_ERR_TIMEOUT (destroy it); the allocation-free
+ * entry point starts afresh on its next call. Returns CT_ERR_ARG for polls == 0. */
+int ct_arm_wait_timeout(ct_table* ct, uint32_t polls);
 
 /* ct_propagate_noalloc: one propagation of a table held entirely in buffers
  * the caller owns, for callers that cannot allocate device memory when they

@@ -73,41 +73,60 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs resident). The last CTA
-// to arrive resets the count and advances the generation; the others poll the
-// generation at most kBarrierSpinLimit times. Returns false (after setting
-// CT_ERR_TIMEOUT) when the wait ran out.
-__device__ bool grid_sync_raw(unsigned* count, unsigned* gen, int* status, int* s_flag) {
+// Grid-wide barrier for a cooperative launch (all CTAs resident). Thread 0 of
+// every CTA keeps the barrier's generation in a register, read once at the
+// start of the launch (no CTA of the launch can move it before this CTA's first
+// arrival), so a barrier costs the arrival atomic plus, for every CTA but the
+// last to arrive, the polls of the generation word. The last arrival resets
+// the count and advances the generation; the others poll at most `limit`
+// times. bar_sync returns 0 (after setting CT_ERR_TIMEOUT) when the wait ran
+// out, 2 to the CTA that arrived last (it has acquired every other CTA's
+// writes and goes on at once), 1 to the others.
+struct GridBarrier {
+    unsigned* count;
+    unsigned* gen;
+    int* status;
+    unsigned limit;
+    unsigned g;  // generation of the next barrier (thread 0)
+};
+
+__device__ __forceinline__ void bar_init(GridBarrier& b, unsigned* count, unsigned* gen, int* status,
+                                         unsigned limit) {
+    b.count = count;
+    b.gen = gen;
+    b.status = status;
+    b.limit = limit;
+    b.g = threadIdx.x == 0 ? ld_acquire(gen) : 0u;
+}
+
+__device__ int bar_sync(GridBarrier& b, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire(gen);
+        int r = 1;
         unsigned arrived;
         // Release this CTA's writes (ordered before by the CTA barrier) and, for
         // the last arrival, acquire everybody else's.
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(count) : "memory");
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(b.count) : "memory");
         if (arrived == gridDim.x - 1) {
-            *count = 0u;
-            st_release(gen, g + 1u);
+            *b.count = 0u;
+            st_release(b.gen, b.g + 1u);
+            r = 2;
         } else {
             unsigned it = 0;
-            while (ld_acquire(gen) == g) {
-                if (++it > kBarrierSpinLimit) {
-                    ok = 0;
-                    atomicExch(status, CT_ERR_TIMEOUT);
+            while (ld_acquire(b.gen) == b.g) {
+                if (++it > b.limit) {
+                    r = 0;
+                    atomicExch(b.status, CT_ERR_TIMEOUT);
                     break;
                 }
                 if (it > 64) __nanosleep(32);
             }
         }
-        *s_flag = ok;
+        b.g += 1u;
+        *s_flag = r;
     }
     __syncthreads();
-    return *s_flag != 0;
-}
-
-__device__ __forceinline__ bool grid_sync(Ctrl* C, int* s_flag) {
-    return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, s_flag);
+    return *s_flag;
 }
 
 struct Smem {
@@ -122,8 +141,6 @@ struct Smem {
     uint32_t cnt[12];
     int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
     int flag[4];
-    int tr[kWarps];                 // trail entries per warp, then their offsets
-    int trBase;
 };
 
 enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin, kCntTuples };
@@ -147,8 +164,12 @@ struct VarLayout {
     __device__ int off(int i) const { return (small && pOff) ? pOff[i] : domOff[i]; }
 };
 
+// snapFrom/snapTo: levels saved since the last call, whose lastDom snapshot
+// (the last-seen domains as they are at entry) this CTA writes from the words
+// it loads anyway (an empty range in every CTA but one).
 __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __restrict__ dom, int32_t* K,
-                     int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm) {
+                     int32_t* rowOff, int32_t* sup, int32_t* codes, uint32_t* domCopy, Smem& sm,
+                     int snapFrom = 0, int snapTo = 0) {
     const int tid = threadIdx.x;
     if (tid < 8) sm.flags[tid] = 0;
     __syncthreads();
@@ -164,6 +185,7 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
             nd += __popc(dv);
             ndel += __popc(lv & ~dv);
             if (domCopy) domCopy[V.ld(i) + q] = dv;
+            for (int lv0 = snapFrom; lv0 < snapTo; ++lv0) T.levelDom[(size_t)lv0 * T.DW + V.ld(i) + q] = lv;
         }
         sup[i] = nd > 1;
         if (i < kLocalMaxArity) sm.nd[i] = nd;
@@ -267,23 +289,6 @@ __device__ __forceinline__ SegState load_segment(const TableDev& T, int seg, int
     return st;
 }
 
-// OR the batch into the running mask; at the last row of a variable apply the
-// mask to the accumulator, complemented on the delta path (Algorithm 2).
-template <int U>
-__device__ __forceinline__ void combine_batch(int q0, int nrows, const int (&code)[U], const uint4 (&v)[U], uint4& m,
-                                              uint4& acc) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        if (q0 + u < nrows) {
-            m = or4(m, v[u]);
-            if (code[u] & kCodeLast) {
-                acc = and4(acc, (code[u] & kCodeDelta) ? not4(m) : m);
-                m = make_uint4(0u, 0u, 0u, 0u);
-            }
-        }
-    }
-}
-
 struct TrailItem {
     bool need;  // the chunk changed and has no entry above the newest mark yet
     int w;
@@ -299,54 +304,149 @@ __device__ __forceinline__ int code_at(const TableDev& T, const int32_t* s_codes
     return q < kCodeCap ? s_codes[q] : __ldcg(&T.codes[q]);
 }
 
-template <int U, bool kGlobal = false>
-__device__ __forceinline__ void update_segment(const TableDev& T, int mark, int snapFrom, int snapTo, int seg,
-                                               const SegState& S, int nrows, const int32_t* s_codes,
-                                               uint32_t* s_cnt, TrailItem& out) {
+// Algorithm 2 on one warp's slice [qa, qb) of a call's row list on one
+// segment (lane l holds chunk 32*seg + l). Algorithm 2 ANDs one mask per
+// changed variable into currTable, each mask the OR of that variable's rows
+// (complemented on the delta path), so the row list may be cut anywhere: a
+// slice ANDs the masks of the variables whose rows it holds entirely (the
+// return value), and with kSplit leaves in S (warp w) the ORs of the rows of
+// a variable cut at its start (head) or at its end (tail), for the warp that
+// combines the slices in row order (combine_slices).
+//
+// Rows go in batches of U independent 128-bit loads per lane, predicated on
+// the chunk being live and not kept in L1. Codes in shared memory are read
+// at the start of each batch; codes in global memory (kGlobal) are read one
+// batch ahead. A slice whose masks already clear every live chunk of the
+// segment stops early: the AND of all slices is then zero on every live chunk
+// whatever the other slices hold.
+template <int U, bool kGlobal, bool kSplit>
+__device__ __forceinline__ uint4 slice_rows(const TableDev& T, int seg, bool act, const uint4& cur, int qa, int qb,
+                                            const int32_t* s_codes, SliceSmem* S, int w) {
+    const int lane = threadIdx.x & 31;
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+    int headKind = 0, headDelta = 0, tailKind = 0;
+    if (qa < qb) {
+        const uint4* base = T.sup + seg * 32 + lane;
+        const uint4* baseDelta = T.supDelta + seg * 32 + lane;  // the same rows unless the table has short tuples
+        const size_t W4 = (size_t)T.W4;
+        bool started = !kSplit || qa == 0 || (code_at<kGlobal>(T, s_codes, qa - 1) & kCodeLast) != 0;
+        uint4 m = make_uint4(0u, 0u, 0u, 0u);
+        bool cut = false;
+        int code[U];
+        if (kGlobal) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) code[u] = qa + u < qb ? code_at<kGlobal>(T, s_codes, qa + u) : 0;
+        }
+        for (int q0 = qa; q0 < qb; q0 += U) {
+            if (!kGlobal) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) code[u] = q0 + u < qb ? code_at<kGlobal>(T, s_codes, q0 + u) : 0;
+            }
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                v[u] = ld_sup_pred(((code[u] & kCodeDelta) ? baseDelta : base) + (size_t)(code[u] & kCodeRow) * W4,
+                                   act && q0 + u < qb);
+            int nxt[kGlobal ? U : 1];
+            if (kGlobal) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + U + u;
+                    nxt[kGlobal ? u : 0] = q < qb ? code_at<kGlobal>(T, s_codes, q) : 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q0 + u < qb) {
+                    m = or4(m, v[u]);
+                    if (code[u] & kCodeLast) {
+                        const bool dl = (code[u] & kCodeDelta) != 0;
+                        if (started) {
+                            acc = and4(acc, dl ? not4(m) : m);
+                        } else if (kSplit) {
+                            S->head[w][lane] = m;
+                            headKind = 1;
+                            headDelta = dl;
+                        }
+                        m = make_uint4(0u, 0u, 0u, 0u);
+                        started = true;
+                    }
+                }
+            }
+            if (kGlobal) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) code[u] = nxt[kGlobal ? u : 0];
+            }
+            // Every live chunk of this segment is already zero: later masks cannot revive it.
+            if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) {
+                cut = true;
+                break;
+            }
+        }
+        if (kSplit && !cut) {
+            const int lastc = code_at<kGlobal>(T, s_codes, qb - 1);
+            if (!(lastc & kCodeLast)) {
+                if (started) {
+                    S->tail[w][lane] = m;
+                    tailKind = 1;
+                } else {
+                    S->head[w][lane] = m;
+                    headKind = 2;
+                    headDelta = (lastc & kCodeDelta) != 0;
+                }
+            }
+        }
+    }
+    if (kSplit) {
+        S->acc[w][lane] = acc;
+        if (lane == 0) {
+            S->headKind[w] = headKind;
+            S->headDelta[w] = headDelta;
+            S->tailKind[w] = tailKind;
+        }
+    }
+    return acc;
+}
+
+// The mask of a segment from the parts of its G slices (warps w0 .. w0+G-1),
+// in row order, lane-wise: a head that ends in its slice closes the variable
+// the previous slices left open.
+__device__ __forceinline__ uint4 combine_slices(const SliceSmem& S, int w0, int G) {
+    const int lane = threadIdx.x & 31;
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), run = make_uint4(0u, 0u, 0u, 0u);
+    for (int g = 0; g < G; ++g) {
+        const int w = w0 + g;
+        acc = and4(acc, S.acc[w][lane]);
+        const int hk = S.headKind[w];
+        if (hk) {
+            run = or4(run, S.head[w][lane]);
+            if (hk == 1) {
+                acc = and4(acc, S.headDelta[w] ? not4(run) : run);
+                run = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        if (S.tailKind[w]) run = S.tail[w][lane];
+    }
+    return acc;
+}
+
+// The end of Algorithm 2 on one segment, given the AND of its masks: the new
+// chunks, the trail item of a changed chunk, and the segment's part of the
+// non-zero index rebuilt by one warp ballot.
+__device__ __forceinline__ void finish_segment(const TableDev& T, int mark, int seg, const SegState& S,
+                                               const uint4& acc, uint32_t* s_cnt, TrailItem& out) {
     const int lane = threadIdx.x & 31;
     const uint32_t mask = S.mask;
-    out.need = false;
-    // Levels saved since the last call snapshot the index as it is now.
-    for (int l = snapFrom + lane; l < snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = mask;
-    if (mask == 0u) return;
     const bool act = (mask >> lane) & 1u;
     const int w = seg * 32 + lane;
     const uint4 cur = S.cur;
-    const int lp = S.lp;
-    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
-    const uint4* base = T.sup + w;
-    const uint4* baseDelta = T.supDelta + w;  // the same rows unless the table has short tuples
-    const size_t W4 = (size_t)T.W4;
-    // Batches of U rows: U independent 128-bit loads in flight per lane; the
-    // codes of the next batch are read from shared memory meanwhile.
-    int code[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) code[u] = u < nrows ? code_at<kGlobal>(T, s_codes, u) : 0;
-    for (int q0 = 0; q0 < nrows; q0 += U) {
-        uint4 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            v[u] = ld_sup_pred(((code[u] & kCodeDelta) ? baseDelta : base) + (size_t)(code[u] & kCodeRow) * W4,
-                               act && q0 + u < nrows);
-        int nxt[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = q0 + U + u;
-            nxt[u] = q < nrows ? code_at<kGlobal>(T, s_codes, q) : 0;
-        }
-        combine_batch<U>(q0, nrows, code, v, m, acc);
-#pragma unroll
-        for (int u = 0; u < U; ++u) code[u] = nxt[u];
-        // Every chunk of this warp is already zero: later masks cannot revive it.
-        if (!__any_sync(0xffffffffu, act && nz(and4(acc, cur)))) break;
-    }
     const uint4 nv = and4(cur, acc);
     const bool chg = act && !eq4(nv, cur);
     const bool alive = act && nz(nv);
     if (chg) T.curr[w] = nv;
-    out.need = chg && mark >= 0 && lp < mark;
+    out.need = chg && mark >= 0 && S.lp < mark;
     out.w = w;
-    out.lp = lp;
+    out.lp = S.lp;
     out.cur = cur;
     if (T.negative) {
         // negative tables filter by counts: the valid tuples left
@@ -355,7 +455,6 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
         for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
         if (lane == 0 && tc) atomicAdd(&s_cnt[kCntTuples], tc);
     }
-    // The segment's part of the non-zero index: the live chunks after the update.
     const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
     uint32_t words = nzwords(cur);
 #pragma unroll
@@ -368,36 +467,60 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
     }
 }
 
-// Trail entries of one round of segments: one reservation per CTA.
-__device__ __forceinline__ void trail_round(const TableDev& T, const TrailItem& it, int cap, Smem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t nb = __ballot_sync(0xffffffffu, it.need);
-    if (lane == 0) sm.tr[warp] = __popc(nb);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int k = 0; k < kWarps; ++k) {
-            const int c = sm.tr[k];
-            sm.tr[k] = tot;
-            tot += c;
-        }
-        int base = 0;
-        if (tot) {
-            base = atomicAdd(&T.ctrl->trail_top, tot);
-            if (base + tot > cap) {
-                atomicExch(&T.ctrl->status, CT_ERR_OOM);
-                base = -1;
-            }
-            sm.cnt[kCntTrail] += (uint32_t)tot;
-        }
-        sm.trBase = base;
+// Algorithm 2 on one segment by one warp (the whole row list): the network kernel's update.
+template <int U, bool kGlobal = false>
+__device__ __forceinline__ void update_segment(const TableDev& T, int mark, int snapFrom, int snapTo, int seg,
+                                               const SegState& S, int nrows, const int32_t* s_codes,
+                                               uint32_t* s_cnt, TrailItem& out) {
+    const int lane = threadIdx.x & 31;
+    out.need = false;
+    // Levels saved since the last call snapshot the index as it is now.
+    for (int l = snapFrom + lane; l < snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = S.mask;
+    if (S.mask == 0u) return;
+    const uint4 acc = slice_rows<U, kGlobal, false>(T, seg, (S.mask >> lane) & 1u, S.cur, 0, nrows, s_codes, nullptr, 0);
+    finish_segment(T, mark, seg, S, acc, s_cnt, out);
+}
+
+// Trail slots of one segment, reserved by its warp before the segment's rows
+// are read: one slot for every live chunk whose newest entry lies below the
+// newest mark (the chunks that need an entry if they change), so that the
+// atomic's latency hides behind the row loads. trail_write fills the slots of
+// the chunks that changed and gives the others an unused key (previous
+// position INT_MAX, which no undo takes for a chunk below its mark).
+struct TrailSlots {
+    uint32_t cand;  // lanes holding a slot
+    int base;       // first slot (lane 0)
+};
+
+__device__ __forceinline__ TrailSlots trail_reserve(const TableDev& T, const SegState& S, int mark) {
+    const int lane = threadIdx.x & 31;
+    TrailSlots r;
+    r.base = 0;
+    r.cand = __ballot_sync(0xffffffffu, mark >= 0 && ((S.mask >> lane) & 1u) && S.lp < mark);
+    if (r.cand && lane == 0) r.base = atomicAdd(&T.ctrl->trail_top, __popc(r.cand));
+    return r;
+}
+
+__device__ __forceinline__ void trail_write(const TableDev& T, const TrailSlots& R, const TrailItem& it, int cap,
+                                            uint32_t* s_cnt) {
+    if (!R.cand) return;
+    const int lane = threadIdx.x & 31;
+    const int base = __shfl_sync(0xffffffffu, R.base, 0);
+    const int n = __popc(R.cand);
+    if (base + n > cap) {
+        if (lane == 0) atomicExch(&T.ctrl->status, CT_ERR_OOM);
+        return;
     }
-    __syncthreads();
-    if (it.need && sm.trBase >= 0) {
-        const int p = sm.trBase + sm.tr[warp] + __popc(nb & lanemask_lt());
-        T.trailKey[p] = make_int2(it.w, it.lp);
-        T.trailOld[p] = it.cur;
-        T.lastpos[it.w] = p;
+    if (lane == 0) atomicAdd(&s_cnt[kCntTrail], (uint32_t)n);
+    if ((R.cand >> lane) & 1u) {
+        const int p = base + __popc(R.cand & lanemask_lt());
+        if (it.need) {
+            T.trailKey[p] = make_int2(it.w, it.lp);
+            T.trailOld[p] = it.cur;
+            T.lastpos[it.w] = p;
+        } else {
+            T.trailKey[p] = make_int2(-1, 0x7fffffff);
+        }
     }
 }
 

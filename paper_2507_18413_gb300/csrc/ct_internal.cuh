@@ -41,7 +41,7 @@ constexpr int kLocalProbes = 4;          // windows of 32 chunks searched after 
 constexpr int kModelProbes = 8;          // the same in the network kernel (live chunks)
 constexpr int kWidePublish = 2048;       // network kernel: tables from which the whole grid publishes
 constexpr int kWindowGroups = 8;         // index segments read for them: at most 8 x 32 (8,192 chunks)
-constexpr unsigned kBarrierSpinLimit = 1u << 24;
+constexpr unsigned kBarrierSpinLimit = 1u << 24;  // default polls of a grid-barrier wait
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
 constexpr int kParamArity = 16;        // scopes up to this arity carry their layout in kernel parameters
 
@@ -134,8 +134,22 @@ struct CallParams {
     int32_t snapFrom;  // levels [snapFrom, snapTo) were saved since the last call:
     int32_t snapTo;    // the kernel snapshots the index and lastDom into them first
     int32_t prevLive;  // live chunks of the current state (reported when no row is OR-ed)
+    uint32_t spinLimit;  // polls of a grid-barrier wait before it gives up (CT_ERR_TIMEOUT)
+    int32_t maxSplit;    // most warps that share one segment's row list (1, 2, 4 or 8)
     int32_t domOff[kParamArity];  // word offset of each scope domain (arity <= kParamArity)
 };
+
+// Dynamic shared memory of the propagation kernel: the partial results of the
+// warps that share a segment's row list (updateTable split over warps).
+struct SliceSmem {
+    uint4 acc[kWarps][32];   // AND of the masks of the variables whose rows all lie in the slice
+    uint4 head[kWarps][32];  // OR of the slice's rows of a variable that began before the slice
+    uint4 tail[kWarps][32];  // OR of the slice's rows of a variable that goes on after the slice
+    int32_t headKind[kWarps];   // 0 none; 1 that variable ends in the slice; 2 the slice lies inside it
+    int32_t headDelta[kWarps];  // the head variable is on the delta path
+    int32_t tailKind[kWarps];   // 1: an open tail
+};
+constexpr int kMaxSplit = kWarps;  // warps of one CTA that may share a segment
 
 // ---------------------------------------------------------------------------
 // A network of tables propagated to its fixpoint in one launch.
@@ -199,6 +213,7 @@ struct ModelDev {
     const int32_t* nworkIn;     // null: the count is already in ctrl->nwork
     uint64_t* phaseNs;          // null, or [kModelPhases] nanoseconds added per phase (CTA 0's view)
     int4* missQ;                // [sum of the tables' rows] residue misses of a round: (table, row, residue)
+    uint32_t spinLimit;         // polls of a grid-barrier wait before it gives up (0: kBarrierSpinLimit)
 };
 constexpr int kModelPhases = 8;  // prologue, plan, update, probe, scan, apply, next round, publish
 constexpr int kRestoreBatch = 256;
@@ -229,6 +244,10 @@ cudaError_t launch_set_words(uint32_t* dst, const uint32_t* words, int n, cudaSt
 cudaError_t launch_copy_words(uint32_t* dst, const uint32_t* src, int n, cudaStream_t s);
 
 }  // namespace ctk
+
+// Test hook of ct_propagate_noalloc (ct_noalloc.cu): the next call on the
+// current device runs its barrier waits out after `polls` polls.
+int ct_noalloc_arm_wait_timeout(uint32_t polls);
 
 // Error helpers shared by the host sources (ct_table.cu, ct_model.cu).
 void ct_set_error(const char* fmt, ...);

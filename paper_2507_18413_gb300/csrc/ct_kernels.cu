@@ -7,25 +7,31 @@
 //            of supports rows to OR (row codes). For tables whose plan fits in
 //            shared memory every CTA computes it for itself; otherwise CTA 0
 //            writes it to global memory and a grid barrier follows.
-//   update   one warp per 32-chunk segment of currTable (grid-stride):
-//            Algorithm 2 on every live 128-bit chunk. The row list is walked
-//            flat across variables in batches of 16 (or 8) independent
-//            128-bit loads per lane that bypass L1; each variable's OR is complemented on the delta
-//            path and AND-ed into the chunk. Changed chunks go to the trail;
-//            the segment's live mask (the non-zero index) is rebuilt with one
-//            warp ballot.
+//   update   Algorithm 2 on every live 128-bit chunk, over (segment, slice)
+//            units: a segment is 32 chunks (lane l owns chunk 32s + l) and its
+//            row list is cut into G = 1, 2, 4 or 8 slices held by adjacent
+//            warps of one CTA, so that long lists spread over the whole grid;
+//            each slice is walked in batches of 16 (or 8) independent 128-bit
+//            loads per lane that bypass L1, a variable's OR is complemented on
+//            the delta path and AND-ed in, and the slices of a segment are
+//            combined in shared memory. Changed chunks go to the trail; the
+//            segment's live mask (the non-zero index) is rebuilt with one warp
+//            ballot.
 //   -- grid barrier --
 //   probe    Algorithm 1 line 5 (fail when currTable = 0), then one warp per
 //            value of s_sup (Algorithm 3 with residues): the residue chunk
-//            first; on a miss, two 32-chunk windows after it; values still
-//            unresolved go to the hard list.
+//            first (loaded beside the failure test); on a miss, up to four
+//            32-chunk windows after it; values still unresolved go to the
+//            hard list.
 //   -- grid barrier --
-//   scan     one warp per segment holds its live chunks in registers and
-//            tests every hard value against them; the last CTA to finish
-//            removes the values no chunk supports, stores new residues, writes
-//            lastDom and the status block (mapped host memory), and resets the
-//            per-call counters for the next call.
+//   publish  with no hard value, the CTA that arrived last at the barrier
+//            writes lastDom's removals, the status block (mapped host memory)
+//            and resets the per-call counters; otherwise every warp holds a
+//            segment's live chunks and tests every hard value against them,
+//            and the last CTA to finish removes the values no chunk supports,
+//            stores new residues and publishes.
 // Grid barriers spin with a bounded iteration count; running out sets
+// CT_ERR_TIMEOUT in the control block and every CTA returns.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -36,23 +42,49 @@ namespace ctk {
 namespace {
 
 // ---------------------------------------------------------------------------
-// last CTA: apply Algorithm 3's removals, publish, reset the call counters
+// one CTA: apply Algorithm 3's removals, publish, reset the call counters
 // ---------------------------------------------------------------------------
 
-// Run by exactly one CTA once every other CTA is done with the call.
-__device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh) {
+// Run by exactly one CTA once every other CTA is done with the call (the last
+// to arrive at the final barrier, or the last to finish the full scan). Every
+// counter of the call is read in one round of loads (thread k reads header
+// slot k); t3 is the caller's stamp of the end of the probes (0: read it from
+// the control block).
+__device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh,
+                         uint64_t t3) {
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
     int32_t* H = T.statusBlk;
-    if (tid == 0) {
-        // Thread 0 may have written control fields just before: make them
-        // visible at device scope, then share the status through shared memory.
-        __threadfence();
-        sm.flag[2] = __ldcg(&C->status);
-        sm.cnt[kCntPruned] = 0u;
+    __syncthreads();  // counters thread 0 of this CTA may have written just before
+    if (tid < kStatusHdr) {
+        int32_t v = 0;
+        switch (tid) {
+            case kSlotStatus: v = __ldcg(&C->status); break;
+            case kSlotLiveOut: v = (int32_t)__ldcg(&C->live); break;
+            case kSlotWordsIn: v = (int32_t)__ldcg(&C->words_in); break;
+            case kSlotTrailTop: v = __ldcg(&C->trail_top); break;
+            case kSlotMisses: v = __ldcg(&C->misses); break;
+            case kSlotHits: v = __ldcg(&C->hits); break;
+            case kSlotRowsOred: v = __ldcg(&C->nrows); break;
+            case kSlotNval: v = __ldcg(&C->nval); break;
+            case kSlotNsup: v = __ldcg(&C->nsup); break;
+            case kSlotNdelta: v = __ldcg(&C->ndelta); break;
+            case kSlotNreset: v = __ldcg(&C->nreset); break;
+            case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
+            case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
+            case kSlotLocal: v = __ldcg(&C->local_found); break;
+            case kSlotWindows: v = __ldcg(&C->windows); break;
+            case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
+            case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
+            case kSlotT3: v = (int32_t)((t3 ? t3 : __ldcg(&C->t[3])) - __ldcg(&C->t[0])); break;
+            case kSlotT4: v = (int32_t)__ldcg(&C->t[0]); break;  // start stamp, low word (see below)
+            default: v = 0;
+        }
+        sm.scan[tid] = v;
     }
+    if (tid == 0) sm.cnt[kCntPruned] = 0u;
     __syncthreads();
-    const int st = sm.flag[2];
+    const int st = sm.scan[kSlotStatus];
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
@@ -96,33 +128,13 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             }
         }
     }
-    // Header: one counter per thread, loaded in parallel.
-    if (tid < kStatusHdr) {
-        int32_t v = 0;
-        switch (tid) {
-            case kSlotLiveOut: v = (int32_t)__ldcg(&C->live); break;
-            case kSlotWordsIn: v = (int32_t)__ldcg(&C->words_in); break;
-            case kSlotTrailTop: v = __ldcg(&C->trail_top); break;
-            case kSlotMisses: v = __ldcg(&C->misses); break;
-            case kSlotPruned: v = (int32_t)sm.cnt[kCntPruned]; break;
-            case kSlotHits: v = __ldcg(&C->hits); break;
-            case kSlotRowsOred: v = __ldcg(&C->nrows); break;
-            case kSlotNval: v = __ldcg(&C->nval); break;
-            case kSlotNsup: v = __ldcg(&C->nsup); break;
-            case kSlotNdelta: v = __ldcg(&C->ndelta); break;
-            case kSlotNreset: v = __ldcg(&C->nreset); break;
-            case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
-            case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
-            case kSlotLocal: v = __ldcg(&C->local_found); break;
-            case kSlotHard: v = nh; break;
-            case kSlotWindows: v = __ldcg(&C->windows); break;
-            case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
-            case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
-            case kSlotT3: v = (int32_t)(__ldcg(&C->t[3]) - __ldcg(&C->t[0])); break;
-            case kSlotT4: v = (int32_t)(gtimer() - __ldcg(&C->t[0])); break;
-            default: v = 0;
-        }
-        if (tid != kSlotStatus) H[tid] = v;
+    // Header: one slot per thread.
+    if (tid < kStatusHdr && tid != kSlotStatus) {
+        int32_t v = sm.scan[tid];
+        if (tid == kSlotPruned) v = (int32_t)sm.cnt[kCntPruned];
+        else if (tid == kSlotHard) v = nh;
+        else if (tid == kSlotT4) v = (int32_t)((uint32_t)gtimer() - (uint32_t)v);
+        H[tid] = v;
     }
     __syncthreads();
     // Reset the per-call counters for the next call (after every read above).
@@ -136,6 +148,31 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     }
 }
 
+// The residue test of value r with its residue chunk already loaded (lane 0),
+// then Algorithm 3's window search on a miss.
+__device__ __forceinline__ void probe_loaded(const TableDev& T, int r, bool present, int res, const uint4& supRes,
+                                             const uint4& curRes, uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (!present) return;
+    if (T.useResidues) {
+        const bool hit = __shfl_sync(0xffffffffu, lane == 0 && nz(and4(supRes, curRes)), 0);
+        if (hit) {
+            if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
+            return;
+        }
+    }
+    probe_miss<false>(T, r, res, s_cnt);
+}
+
+// Per-CTA counters of a phase into the control block (zero counts skipped).
+__device__ __forceinline__ void flush_update_counters(Ctrl* C, Smem& sm) {
+    if (sm.cnt[kCntLive]) atomicAdd(&C->live, sm.cnt[kCntLive]);
+    if (sm.cnt[kCntLiveIn]) atomicAdd(&C->live_in, sm.cnt[kCntLiveIn]);
+    if (sm.cnt[kCntWords]) atomicAdd(&C->words_in, sm.cnt[kCntWords]);
+    if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
+    if (sm.cnt[kCntTuples]) atomicAdd(&C->tuples, sm.cnt[kCntTuples]);
+}
+
 // ---------------------------------------------------------------------------
 // the propagation kernel
 // ---------------------------------------------------------------------------
@@ -144,16 +181,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ dom,
                     const int32_t* __restrict__ domOff, const __grid_constant__ CallParams P) {
     __shared__ Smem sm;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    SliceSmem& parts = *reinterpret_cast<SliceSmem*>(s_dyn);
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
     const VarLayout V(T, P.domOff, domOff);
+    GridBarrier bar;
+    bar_init(bar, &C->bar_count, &C->bar_gen, &C->status, P.spinLimit ? P.spinLimit : kBarrierSpinLimit);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
 
-    // Prologue loads that do not depend on the plan: the warp's first segment
-    // and the residue (with its supports chunk) of the first value it probes.
+    // Prologue loads that do not depend on the plan: the first segment of the
+    // warp when every warp takes a whole segment, and the residue (with its
+    // supports chunk) of the first value it probes.
     SegState seg0;
     if (gwarp < T.nseg) seg0 = load_segment(T, gwarp, P.mark);
     int res0 = 0;
@@ -162,17 +204,13 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         res0 = T.residue[gwarp];
         supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
     }
-    // Levels saved since the last call snapshot lastDom as it is now.
-    if (blockIdx.x == 0) {
-        for (int l = P.snapFrom; l < P.snapTo; ++l)
-            for (int q = tid; q < T.DW; q += kThreads) T.levelDom[(size_t)l * T.DW + q] = T.lastDom[q];
-    }
 
-    // plan
+    // plan (CTA 0 also snapshots lastDom into the levels saved since the last call)
     int nrows;
     bool ok;
     if (kLocal) {
-        plan(T, V, dom, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm);
+        const bool snap = blockIdx.x == 0;
+        plan(T, V, dom, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm, snap ? P.snapFrom : 0, snap ? P.snapTo : 0);
         ok = !(sm.flags[0] || sm.flags[1]);
         nrows = sm.flags[6];
         if (T.negative && ok) {
@@ -203,14 +241,14 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         }
     } else {
         if (blockIdx.x == 0) {
-            plan(T, V, dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            plan(T, V, dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm, P.snapFrom, P.snapTo);
             if (tid == 0) {
                 C->nval = sm.flags[2]; C->ndelta = sm.flags[3]; C->nreset = sm.flags[4]; C->nsup = sm.flags[5];
                 C->nrows = sm.flags[6];
                 if (sm.flags[0] || sm.flags[1]) C->status = sm.flags[0] ? CT_ERR_STATE : CT_INFEASIBLE;
             }
         }
-        if (!grid_sync(C, &sm.flag[0])) return;
+        if (!bar_sync(bar, &sm.flag[0])) return;
         ok = __ldcg(&C->status) == CT_OK;
         nrows = __ldcg(&C->nrows);
         const int staged = min(nrows, kCodeCap);
@@ -218,6 +256,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     }
     if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
 
+    uint4 curRes0 = make_uint4(0u, 0u, 0u, 0u);
     if (!ok || (nrows == 0 && !T.negative)) {
         // Nothing to update: currTable stays as it is. Pending level snapshots
         // of the index are still taken.
@@ -227,7 +266,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         }
         if (!ok) {
             // Domain error or empty domain: publish without filtering.
-            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
+            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0, 0ull);
             return;
         }
         if (blockIdx.x == 0 && tid == 0) {
@@ -235,41 +274,85 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             C->live_in = (uint32_t)P.prevLive;
             C->t[2] = C->t[1];
         }
+        if (T.useResidues && gwarp < T.R && lane == 0) curRes0 = __ldcg(T.curr + res0);
     } else {
-        // update (Algorithm 2)
+        // update (Algorithm 2): the row list of a segment is cut into G slices,
+        // G a power of two and at most P.maxSplit, as large as keeps every
+        // (segment, slice) unit in one round of the grid's warps and no larger
+        // than one batch of U rows per slice needs; warp w of a round takes
+        // slice w % G of segment (round base + w) / G, and the slices of one
+        // segment, held by the G adjacent warps of one CTA, are combined in
+        // shared memory.
         if (tid < 12) sm.cnt[tid] = 0u;
+        int G = 1, lg = 0;
+        {
+            const int need = (nrows + U - 1) / U;
+            while (G < P.maxSplit && G < need && (T.nseg << (lg + 1)) <= nwarps) {
+                G <<= 1;
+                ++lg;
+            }
+        }
+        const int units = T.nseg << lg;
+        const int per = (nrows + G - 1) >> lg;  // rows per slice
         __syncthreads();
         const int cap = __ldcg(&C->trail_cap);
-        // Rounds of one segment per warp; every warp of a CTA runs every round
-        // so that the trail reservation can synchronise the CTA.
-        for (int base = blockIdx.x * kWarps; base < T.nseg; base += nwarps) {
-            const int seg = base + warp;
+        // Rounds of one unit per warp; with G > 1 every warp of a CTA runs
+        // every round so that the slice combination can synchronise the CTA.
+        for (int base = blockIdx.x * kWarps; base < units; base += nwarps) {
+            const int u = base + warp;
+            if (G == 1 && u >= units) break;
+            const int seg = u >> lg, slice = u & (G - 1);
             TrailItem it;
             it.need = false;
-            if (seg < T.nseg) {
-                const SegState S = seg == gwarp ? seg0 : load_segment(T, seg, P.mark);
-                update_segment<U>(T, P.mark, P.snapFrom, P.snapTo, seg, S, nrows, sm.codes, sm.cnt, it);
+            SegState S;
+            S.mask = 0u;
+            TrailSlots slots;
+            slots.cand = 0u;
+            if (u < units) {
+                S = (G == 1 && seg == gwarp) ? seg0 : load_segment(T, seg, P.mark);
+                if (slice == 0) {
+                    // levels saved since the last call snapshot the index as it is now
+                    for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = S.mask;
+                    slots = trail_reserve(T, S, P.mark);
+                }
             }
-            if (P.mark >= 0) trail_round(T, it, cap, sm);
+            uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+            if (G == 1) {
+                if (S.mask != 0u)
+                    acc = slice_rows<U, false, false>(T, seg, (S.mask >> lane) & 1u, S.cur, 0, nrows, sm.codes,
+                                                      nullptr, 0);
+            } else {
+                if (S.mask != 0u) {
+                    const int qa = min(nrows, slice * per);
+                    slice_rows<U, false, true>(T, seg, (S.mask >> lane) & 1u, S.cur, qa, min(nrows, qa + per),
+                                               sm.codes, &parts, warp);
+                }
+                __syncthreads();
+                if (S.mask != 0u && slice == 0) acc = combine_slices(parts, warp, G);
+            }
+            if (S.mask != 0u && slice == 0) {
+                finish_segment(T, P.mark, seg, S, acc, sm.cnt, it);
+                trail_write(T, slots, it, cap, sm.cnt);
+            }
+            if (G > 1) __syncthreads();  // the parts are rewritten by the next round
         }
         __syncthreads();
-        if (tid == 0) {
-            atomicAdd(&C->live, sm.cnt[kCntLive]);
-            atomicAdd(&C->live_in, sm.cnt[kCntLiveIn]);
-            atomicAdd(&C->words_in, sm.cnt[kCntWords]);
-            if (sm.cnt[kCntTrail]) atomicAdd(&C->trail_added, (int)sm.cnt[kCntTrail]);
-            if (sm.cnt[kCntTuples]) atomicAdd(&C->tuples, sm.cnt[kCntTuples]);
-        }
-        if (!grid_sync(C, &sm.flag[0])) return;
-        if (blockIdx.x == 0 && tid == 0) C->t[2] = gtimer();
+        if (tid == 0) flush_update_counters(C, sm);
+        const int r1 = bar_sync(bar, &sm.flag[0]);
+        if (!r1) return;
+        if (r1 == 2 && tid == 0) C->t[2] = gtimer();
         // Algorithm 1 line 5: fail when currTable is all zero (a negative
         // table with no valid forbidden tuple forbids nothing; an empty shard
-        // supports no value, which the filter finds).
-        if (__ldcg(&C->status) != CT_OK || (!T.negative && !T.shard && __ldcg(&C->live) == 0u)) {
-            if (blockIdx.x == 0) {
-                if (tid == 0 && __ldcg(&C->status) == CT_OK) C->status = CT_INFEASIBLE;
+        // supports no value, which the filter finds). The residue chunk of the
+        // warp's first probe is loaded beside the failure test.
+        if (T.useResidues && gwarp < T.R && lane == 0) curRes0 = __ldcg(T.curr + res0);
+        const int st1 = __ldcg(&C->status);
+        const uint32_t live1 = __ldcg(&C->live);
+        if (st1 != CT_OK || (!T.negative && !T.shard && live1 == 0u)) {
+            if (r1 == 2) {
+                if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
                 __syncthreads();
-                finalize(T, V, dom, sm, 0);
+                finalize(T, V, dom, sm, 0, 0ull);
             }
             return;
         }
@@ -315,13 +398,14 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             present = __ldcg(&T.varSup[i]) && ((dom[V.off(i) + (a >> 5)] >> (a & 31)) & 1u);
         }
         int res = res0;
-        uint4 sr = supRes0;
+        uint4 sr = supRes0, cr = curRes0;
         if (r != gwarp && T.useResidues && present && lane == 0) {
             res = T.residue[r];
             sr = ld_sup(T.sup + (size_t)r * T.W4 + res);
+            cr = __ldcg(T.curr + res);
         }
         res = __shfl_sync(0xffffffffu, res, 0);
-        probe_row<false>(T, r, present, res, sr, sm.cnt);
+        probe_loaded(T, r, present, res, sr, cr, sm.cnt);
     }
     __syncthreads();
     if (tid == 0) {
@@ -330,15 +414,17 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         if (sm.cnt[kCntMiss]) atomicAdd(&C->misses, (int)sm.cnt[kCntMiss]);
         if (sm.cnt[kCntWin]) atomicAdd(&C->windows, (int)sm.cnt[kCntWin]);
     }
-    if (!grid_sync(C, &sm.flag[0])) return;
-    if (blockIdx.x == 0 && tid == 0) C->t[3] = gtimer();
-
+    const int r2 = bar_sync(bar, &sm.flag[0]);
+    if (!r2) return;
+    const uint64_t t3 = r2 == 2 ? gtimer() : 0ull;
     const int nh = (int)__ldcg(&C->nhard);
     if (nh == 0) {
-        // Every value kept its support: CTA 0 publishes, the others are done.
-        if (blockIdx.x == 0) finalize(T, V, dom, sm, 0);
+        // Every value kept its support: the CTA that arrived last publishes,
+        // the others are done.
+        if (r2 == 2) finalize(T, V, dom, sm, 0, t3);
         return;
     }
+    if (r2 == 2 && tid == 0) C->t[3] = t3;
     // full scan of the hard values
     {
         const int staged = min(nh, kCodeCap);
@@ -360,7 +446,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     __syncthreads();
     if (!sm.flag[1]) return;
     __threadfence();
-    finalize(T, V, dom, sm, nh);
+    finalize(T, V, dom, sm, nh, 0ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,14 +498,26 @@ __global__ void ct_copy_words_kernel(uint32_t* dst, const uint32_t* src, int n) 
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) dst[q] = src[q];
 }
 
+// Static and dynamic shared memory together exceed 48 KB: opt in once per
+// kernel variant before its first occupancy query or launch.
+template <bool L, int U, int B>
+cudaError_t allow_slice_smem() {
+    static const cudaError_t e = cudaFuncSetAttribute((const void*)ct_propagate_kernel<L, U, B>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sizeof(SliceSmem));
+    return e;
+}
+
 template <bool L, int U, int B>
 cudaError_t launch_coop(const TableDev& T, int grid, uint32_t* dom, const int32_t* domOff, const CallParams& P,
                         cudaStream_t s) {
+    const cudaError_t e = allow_slice_smem<L, U, B>();
+    if (e != cudaSuccess) return e;
     TableDev t = T;
     CallParams p = P;
     void* args[] = {&t, &dom, (void*)&domOff, &p};
     return cudaLaunchCooperativeKernel((const void*)ct_propagate_kernel<L, U, B>, dim3(grid), dim3(kThreads), args,
-                                       0, s);
+                                       sizeof(SliceSmem), s);
 }
 
 template <bool L, int U, int B>
@@ -427,7 +525,9 @@ int coresident() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, U, B>, kThreads, 0) != cudaSuccess)
+    if (allow_slice_smem<L, U, B>() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_propagate_kernel<L, U, B>, kThreads,
+                                                      sizeof(SliceSmem)) != cudaSuccess)
         return 0;
     return per * sms;
 }

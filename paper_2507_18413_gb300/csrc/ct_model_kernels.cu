@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
     const int nwarps = gridDim.x * kWarps;
     int32_t* preU = sm.codes;                               // unit prefix of the round (smem copy)
     int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
-    auto sync = [&]() { return grid_sync_raw(&C->bar_count, &C->bar_gen, &C->status, &sm.flag[0]); };
+    GridBarrier bar;
+    bar_init(bar, &C->bar_count, &C->bar_gen, &C->status, M.spinLimit ? M.spinLimit : kBarrierSpinLimit);
+    auto sync = [&]() { return bar_sync(bar, &sm.flag[0]) != 0; };
     // optional phase clock: CTA 0 adds the time since its previous mark (a grid
     // barrier ends every phase, so this is the phase's length across the grid)
     uint64_t tmark = (M.phaseNs && blockIdx.x == 0 && tid == 0) ? gtimer() : 0ull;

@@ -17,6 +17,7 @@
 // kNaMaxRows supports rows (sum of the domain sizes) and kNaMaxChunks 128-bit
 // chunks of currTable (8,388,608 tuples). Backtracking is the caller's
 // business (it keeps copies of the buffers it wants to return to).
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -58,9 +59,14 @@ struct NaInit {
     int32_t rowVar[kNaMaxRows];  // scope position of each supports row
     int32_t R;
     int32_t nseg;
-    uint32_t lastMask;           // live chunks of the last (partial) segment
+    int32_t W4;                  // 128-bit chunks of currTable
+    uint32_t barCount;           // initial grid-barrier count (0; the timeout test hook sets it unreachable)
+    const uint4* curr;           // the caller's currTable
 };
 
+// The non-zero index of the caller's currTable is rebuilt from its chunks
+// (one warp ballot per 32-chunk segment), so dead chunks left by earlier calls
+// are neither read by updateTable nor scanned by filterDomains.
 __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
     NaScratch* S = reinterpret_cast<NaScratch*>(g_ct_noalloc_scratch);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,10 +77,25 @@ __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
         S->residue[q] = 0;
         S->rowVar[q] = p.rowVar[q];
     }
-    for (int q = tid; q < p.nseg; q += nth) S->segMask[q] = q == p.nseg - 1 ? p.lastMask : 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int seg0 = (tid >> 5) << 5; seg0 < p.nseg * 32; seg0 += nth) {
+        const int w = seg0 + lane;  // chunk; seg0 is a multiple of 32
+        bool live = false;
+        if (w < p.W4) {
+            const uint4 v = p.curr[w];
+            live = (v.x | v.y | v.z | v.w) != 0u;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, live);
+        if (lane == 0) S->segMask[seg0 >> 5] = m;
+    }
     for (int q = tid; q < kNaMaxArity; q += nth) S->changed[q] = 0;
-    if (tid == 0) S->status[kSlotStatus] = kNaPending;
+    if (tid == 0) {
+        S->status[kSlotStatus] = kNaPending;
+        S->ctrl.bar_count = p.barCount;
+    }
 }
+
+std::atomic<uint32_t> g_na_arm{0};  // test hook: polls of the next call's barrier waits (0: off)
 
 struct NaDevice {
     NaScratch* scratch = nullptr;  // device address of g_ct_noalloc_scratch
@@ -107,6 +128,11 @@ int na_setup(int dev, NaDevice** out) {
 }
 
 }  // namespace
+
+int ct_noalloc_arm_wait_timeout(uint32_t polls) {
+    g_na_arm.store(polls);
+    return CT_OK;
+}
 
 extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t t, const uint32_t* supports,
                                     uint32_t* curr_table, uint32_t* dom_bits, uint32_t* last_dom_bits,
@@ -184,14 +210,18 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     }
 
     // The array keeps the previous call's contents: clear what must start at
-    // zero (counters and barrier, residues, changed flags), mark every chunk of
-    // this table live, reload the row -> variable map, reset the status word.
+    // zero (counters and barrier, residues, changed flags), rebuild the
+    // non-zero index from the caller's currTable, reload the row -> variable
+    // map, reset the status word.
     NaInit init;
     for (int i = 0; i < arity; ++i)
         for (int a = 0; a < dom_size[i]; ++a) init.rowVar[row0[i] + a] = i;
     init.R = R;
     init.nseg = nseg;
-    init.lastMask = (W4 % 32) ? ((1u << (W4 % 32)) - 1u) : 0xffffffffu;
+    init.W4 = (int32_t)W4;
+    init.curr = T.curr;
+    const uint32_t armed = g_na_arm.exchange(0u);
+    init.barCount = armed ? 0x40000000u : 0u;
     ct_noalloc_init_kernel<<<8, 256, 0, s>>>(init);
     CT_CUDA(cudaGetLastError());
 
@@ -200,6 +230,8 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     P.snapFrom = 0;
     P.snapTo = 0;
     P.prevLive = (int32_t)W4;
+    P.spinLimit = armed ? armed : kBarrierSpinLimit;
+    P.maxSplit = 1;
     for (int i = 0; i < arity; ++i) P.domOff[i] = ld[i];
     const int variant = nseg > nd->maxCo[1] * kWarps ? 3 : 1;
     int grid = (nseg + kWarps - 1) / kWarps;

@@ -387,9 +387,14 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     std::memset(ct->h_status, 0, ct->statusInts * sizeof(int32_t));
     CT_CUDA(cudaHostGetDevicePointer((void**)&d.statusBlk, ct->h_status, 0));
     {
-        // 16 loads in flight per lane at 2 CTAs per SM while one wave of warps
-        // covers every segment; beyond that 8 loads at 3 CTAs per SM.
+        // 16 loads in flight per lane at 2 CTAs per SM. With the row list of a
+        // segment cut over up to kMaxSplit warps of a CTA, every segment can
+        // keep a whole CTA busy: one CTA per segment (a long row list then
+        // spreads over the whole grid), capped at residency, and at least one
+        // warp per two values for the probes.
+        ct->maxSplit = (opt && opt->no_split) ? 1 : kMaxSplit;
         const int narrow = (ct->localPlan ? 1 : 0);
+        // more segments than one wave of warps at 2 CTAs per SM: 8 loads at 3 CTAs per SM
         const int maxNarrow = max_coresident_blocks(narrow);
         ct->variant = (ct->nseg > maxNarrow * kWarps) ? (narrow | 2) : narrow;
         const int maxCo = max_coresident_blocks(ct->variant);
@@ -397,7 +402,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
             ct_set_error("ct_create: the propagation kernel cannot be made resident on this device");
             return CT_ERR_CUDA;
         }
-        int want = (ct->nseg + kWarps - 1) / kWarps;
+        int want = (ct->nseg * ct->maxSplit + kWarps - 1) / kWarps;
         want = std::max(want, (R + 2 * kWarps - 1) / (2 * kWarps));
         if (opt && opt->grid_blocks > 0) want = opt->grid_blocks;
         ct->grid = std::max(1, std::min(want, maxCo));
@@ -537,8 +542,18 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.snapFrom = ct->pendingFrom;
     P.snapTo = (int)ct->levels.size();
     P.prevLive = ct->live;
+    P.spinLimit = kBarrierSpinLimit;
+    P.maxSplit = ct->maxSplit;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
+    if (ct->armPolls) {
+        // Test hook (ct_arm_wait_timeout): an arrival count that no CTA can
+        // complete, so every barrier wait of this call runs out after armPolls polls.
+        const uint32_t unreachable = 0x40000000u;
+        CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->bar_count, &unreachable, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        P.spinLimit = ct->armPolls;
+        ct->armPolls = 0;
+    }
     if (ct->copyState) {
         // the paper's propagators copy currTable to the device before each call
         if (!ct->h_curr && (st = fetch_host_curr(ct)) != CT_OK) return st;
@@ -560,15 +575,21 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     ct->pendingFrom = (int)ct->levels.size();
     // Wait for the status word the kernel publishes last (bounded), then fall
     // back to a stream synchronisation to collect any CUDA error.
+    // A kernel that returned without publishing (a barrier wait ran out) is
+    // noticed when the stream has gone idle.
     bool seen = false;
     for (uint64_t it = 0;; ++it) {
         if (hv[kSlotStatus] != kNoChunk) {
             seen = true;
             break;
         }
-        if ((it & 1023u) == 1023u &&
-            std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(kHostWaitMs))
-            break;
+        if ((it & 1023u) == 1023u) {
+            if (cudaStreamQuery(s) == cudaSuccess) {
+                seen = hv[kSlotStatus] != kNoChunk;
+                break;
+            }
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(kHostWaitMs)) break;
+        }
     }
     if (!seen) CT_CUDA(cudaStreamSynchronize(s));
     if (ct->copyState) {
@@ -696,6 +717,7 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* 
     ct->nChW = src->nChW;
     ct->localPlan = src->localPlan;
     ct->variant = src->variant;
+    ct->maxSplit = src->maxSplit;
     ct->live = src->live;
     ct->stream = stream;
     ct->dev = src->dev;  // static pointers shared; dynamic ones replaced below
@@ -817,7 +839,7 @@ namespace {
 int autotune(ct_table* ct) {
     if (ct->empty || ct->R < 1) return CT_OK;
     const int narrow = ct->localPlan ? 1 : 0;
-    const int base = std::max((ct->nseg + kWarps - 1) / kWarps, (ct->R + 2 * kWarps - 1) / (2 * kWarps));
+    const int base = std::max((ct->nseg * ct->maxSplit + kWarps - 1) / kWarps, (ct->R + 2 * kWarps - 1) / (2 * kWarps));
     std::vector<std::pair<int, int>> cands;
     for (int wide = 0; wide < 2; ++wide) {
         const int var = narrow | (wide ? 2 : 0);
@@ -963,6 +985,16 @@ extern "C" int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_
         return CT_ERR_ARG;
     }
     return ct_table_propagate_on(ct, dom_bits, ct->dev.varLD, ct->ld.data(), changed_vars);
+}
+
+extern "C" int ct_arm_wait_timeout(ct_table* ct, uint32_t polls) {
+    if (polls == 0) {
+        ct_set_error("ct_arm_wait_timeout: polls must be positive");
+        return CT_ERR_ARG;
+    }
+    if (!ct) return ct_noalloc_arm_wait_timeout(polls);
+    ct->armPolls = polls;
+    return CT_OK;
 }
 
 extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t* changed_vars) {

@@ -59,6 +59,8 @@ struct ct_table {
     uint32_t* h_curr = nullptr;  // pinned host copy of currTable (copy_state)
     bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
     bool levelsInArena = false;
+    int maxSplit = ctk::kMaxSplit;  // most warps sharing one segment's row list (1: ct_options.no_split)
+    uint32_t armPolls = 0;          // test hook: the next call's barrier waits run out after this many polls
 };
 
 // Out of line: the device trail grown to hold `need` entries (ct_table.cu).

@@ -37,7 +37,7 @@ class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("host_fixpoint", ctypes.c_int32), ("autotune", ctypes.c_int32), ("copy_state", ctypes.c_int32),
-                ("shard", ctypes.c_int32)]
+                ("shard", ctypes.c_int32), ("no_split", ctypes.c_int32)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -121,6 +121,7 @@ _SIGS = {
     "ct_set_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "ct_destroy": (ctypes.c_int, [_P]),
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
+    "ct_arm_wait_timeout": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
     "ct_sharded_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.c_int,
                                          _P, _P, ctypes.POINTER(_P)]),
@@ -245,8 +246,10 @@ def _stream_ptr(stream):
     return h if h != 0 else _CUDA_STREAM_LEGACY
 
 
-def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0, shard=0):
+def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0, shard=0,
+                 no_split=0):
     o = ct_options()
+    o.no_split = no_split
     o.shard = shard
     o.autotune = autotune
     o.host_fixpoint = host_fixpoint
@@ -366,6 +369,12 @@ def ct_propagate(h, dom_bits, changed_words: int = 0):
     ch, pch = _u32_out(changed_words)
     st = load().ct_propagate(h, _dev_ptr(dom_bits), pch if changed_words else None)
     return st, ch[:changed_words]
+
+
+def ct_arm_wait_timeout(h, polls):
+    """Test hook: the next ct_propagate on h (None: the next ct_propagate_noalloc) runs
+    its barrier waits out after `polls` polls and returns CT_ERR_TIMEOUT."""
+    return load().ct_arm_wait_timeout(h, int(polls))
 
 
 def ct_propagate_host(h, dom_words: np.ndarray, changed_words: int = 0):
