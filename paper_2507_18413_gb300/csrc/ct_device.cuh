@@ -69,6 +69,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
+// Plain (relaxed) read of a word another launch wrote: no ordering imposed on
+// the loads that follow.
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -96,7 +104,7 @@ __device__ __forceinline__ void bar_init(GridBarrier& b, unsigned* count, unsign
     b.gen = gen;
     b.status = status;
     b.limit = limit;
-    b.g = threadIdx.x == 0 ? ld_acquire(gen) : 0u;
+    b.g = threadIdx.x == 0 ? ld_relaxed(gen) : 0u;
 }
 
 __device__ int bar_sync(GridBarrier& b, int* s_flag) {
@@ -141,6 +149,8 @@ struct Smem {
     uint32_t cnt[12];
     int flags[8];                   // grow, empty, nval, ndelta, nreset, nsup, nrows
     int flag[4];
+    int trw[kWarps];  // trail slots of each warp's segment, then their offsets in the CTA's block
+    int trBase;       // first trail slot of the CTA's block
 };
 
 enum { kCntLive = 0, kCntLiveIn, kCntWords, kCntTrail, kCntHits, kCntLocal, kCntMiss, kCntPruned, kCntWin, kCntTuples };
@@ -481,25 +491,17 @@ __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int 
     finish_segment(T, mark, seg, S, acc, s_cnt, out);
 }
 
-// Trail slots of one segment, reserved by its warp before the segment's rows
-// are read: one slot for every live chunk whose newest entry lies below the
-// newest mark (the chunks that need an entry if they change), so that the
-// atomic's latency hides behind the row loads. trail_write fills the slots of
-// the chunks that changed and gives the others an unused key (previous
-// position INT_MAX, which no undo takes for a chunk below its mark).
+// Trail slots of a round of segments. Each segment's warp counts one slot for
+// every live chunk whose newest entry lies below the newest mark (the chunks
+// that need an entry if they change); one atomic per CTA reserves the block
+// before the rows are read, so its latency hides behind the row loads.
+// trail_write fills the slots of the chunks that changed and gives the others
+// an unused key (previous position INT_MAX, which no undo takes for a chunk
+// below its mark).
 struct TrailSlots {
     uint32_t cand;  // lanes holding a slot
-    int base;       // first slot (lane 0)
+    int base;       // the warp's first slot
 };
-
-__device__ __forceinline__ TrailSlots trail_reserve(const TableDev& T, const SegState& S, int mark) {
-    const int lane = threadIdx.x & 31;
-    TrailSlots r;
-    r.base = 0;
-    r.cand = __ballot_sync(0xffffffffu, mark >= 0 && ((S.mask >> lane) & 1u) && S.lp < mark);
-    if (r.cand && lane == 0) r.base = atomicAdd(&T.ctrl->trail_top, __popc(r.cand));
-    return r;
-}
 
 __device__ __forceinline__ void trail_write(const TableDev& T, const TrailSlots& R, const TrailItem& it, int cap,
                                             uint32_t* s_cnt) {
@@ -583,21 +585,32 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
     const unsigned FULL = 0xffffffffu;
     bool complete = false;
     if (!kLive && T.useResidues) {
-        // the chunks that follow the residue, dead or alive
+        // the chunks that follow the residue, dead or alive: two windows per
+        // round of loads, tested in order
         const int W4 = T.W4;
         const uint4* row = T.sup + (size_t)r * W4;
-        for (int b = 0; b < kProbes; ++b) {
-            if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
-            const int c = (int)(((long long)res + 1 + b * 32 + lane) % W4);
-            const bool h = nz(and4(ld_sup(row + c), __ldcg(T.curr + c)));
-            const unsigned bal = __ballot_sync(FULL, h);
-            if (bal) {
-                const int cf = __shfl_sync(FULL, c, __ffs(bal) - 1);
-                if (lane == 0) {
-                    T.residue[r] = cf;
-                    atomicAdd(&s_cnt[kCntLocal], 1u);
+        for (int b = 0; b < kProbes; b += 2) {
+            const int c0 = (int)(((long long)res + 1 + b * 32 + lane) % W4);
+            const int c1 = (int)(((long long)res + 1 + (b + 1) * 32 + lane) % W4);
+            const bool two = b + 1 < kProbes;
+            const uint4 s0 = ld_sup(row + c0), t0 = __ldcg(T.curr + c0);
+            uint4 s1 = make_uint4(0u, 0u, 0u, 0u), t1 = s1;
+            if (two) {
+                s1 = ld_sup(row + c1);
+                t1 = __ldcg(T.curr + c1);
+            }
+            for (int k = 0; k < (two ? 2 : 1); ++k) {
+                if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
+                const int c = k ? c1 : c0;
+                const unsigned bal = __ballot_sync(FULL, k ? nz(and4(s1, t1)) : nz(and4(s0, t0)));
+                if (bal) {
+                    const int cf = __shfl_sync(FULL, c, __ffs(bal) - 1);
+                    if (lane == 0) {
+                        T.residue[r] = cf;
+                        atomicAdd(&s_cnt[kCntLocal], 1u);
+                    }
+                    return kProbeFound;
                 }
-                return kProbeFound;
             }
         }
     } else if (T.useResidues) {
@@ -676,9 +689,9 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
 // A residue miss searched by probe_windows; a value not found goes to the
 // hard list, marked kNoSupport when it has no support (removed without a
 // scan; a scan keeps the mark, atomicMin), else for the full scan.
-template <bool kLive>
+template <bool kLive, int kProbes = kLocalProbes>
 __device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
-    const int o = probe_windows<kLive>(T, r, res, s_cnt);
+    const int o = probe_windows<kLive, kProbes>(T, r, res, s_cnt);
     if (o != kProbeFound && (threadIdx.x & 31) == 0) {
         const bool complete = o == kProbeGone;
         const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
@@ -733,8 +746,11 @@ __device__ __forceinline__ void scan_segment(const TableDev& T, int seg, int nh,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (m0 + u < nh) {
+                // any supporting chunk is a valid new residue: whichever
+                // segment's store lands last stays (a plain store: no
+                // round trip and no contended atomic per value)
                 const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
-                if (lane == 0 && bal) atomicMin(&T.foundChunk[m0 + u], seg * 32 + __ffs(bal) - 1);
+                if (lane == 0 && bal) T.foundChunk[m0 + u] = seg * 32 + __ffs(bal) - 1;
             }
         }
     }

@@ -68,6 +68,7 @@ enum StatusSlot {
     kSlotT2 = 18,  // update done (after the barrier),
     kSlotT3 = 19,  // probes done (after the barrier),
     kSlotT4 = 20,  // finalize
+    kSlotScan = 21,  // hard values left undecided by the windows (the full scan's)
 };
 
 // Per-table control block: persistent state and per-call counters.

@@ -39,6 +39,28 @@
 
 namespace ctk {
 
+#ifdef CT_PHASE_TRACE
+// Diagnostic build only (-DCT_PHASE_TRACE): %globaltimer stamps of thread 0 of
+// the first kTraceCtas CTAs at the phase boundaries of the last propagation,
+// read with ct_trace_read. The default build has none of this.
+constexpr int kTraceCtas = 1024, kTraceStamps = 16;
+__device__ unsigned long long g_ct_trace[kTraceCtas * kTraceStamps];
+#define CT_STAMP(k)                                                          \
+    do {                                                                     \
+        if (threadIdx.x == 0 && blockIdx.x < kTraceCtas)                     \
+            g_ct_trace[blockIdx.x * kTraceStamps + (k)] = gtimer_trace();    \
+    } while (0)
+__device__ __forceinline__ unsigned long long gtimer_trace() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#else
+#define CT_STAMP(k) \
+    do {            \
+    } while (0)
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -50,7 +72,10 @@ namespace {
 // counter of the call is read in one round of loads (thread k reads header
 // slot k); t3 is the caller's stamp of the end of the probes (0: read it from
 // the control block).
-__device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh,
+// nh < 0: the hard-value counts are read with the header, and with values
+// left undecided for the full scan the CTA returns false without publishing
+// (the hard values known unsupported are removed here).
+__device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh,
                          uint64_t t3) {
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
@@ -59,6 +84,8 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     if (tid < kStatusHdr) {
         int32_t v = 0;
         switch (tid) {
+            case kSlotHard: v = nh < 0 ? (int32_t)__ldcg(&C->nhard) : nh; break;
+            case kSlotScan: v = __ldcg(&C->nscan); break;
             case kSlotStatus: v = __ldcg(&C->status); break;
             case kSlotLiveOut: v = (int32_t)__ldcg(&C->live); break;
             case kSlotWordsIn: v = (int32_t)__ldcg(&C->words_in); break;
@@ -83,7 +110,12 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
         sm.scan[tid] = v;
     }
     if (tid == 0) sm.cnt[kCntPruned] = 0u;
+    // bit i of sm.scan[kChgBase + i / 32]: scope variable i lost a value
+    constexpr int kChgBase = 32;
+    for (int q = tid; q < T.nChangedWords; q += kThreads) sm.scan[kChgBase + q] = 0;
     __syncthreads();
+    if (nh < 0 && sm.scan[kSlotScan] > 0) return false;
+    nh = sm.scan[kSlotHard];
     const int st = sm.scan[kSlotStatus];
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
@@ -105,26 +137,20 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
                 // valid forbidden tuples, which the next call removes as Delta;
                 // a shard's value may be supported by another shard
                 if (!T.negative && !T.shard) atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
-                T.changed[i] = 1;
+                atomicOr(reinterpret_cast<unsigned*>(&sm.scan[kChgBase + (i >> 5)]), 1u << (i & 31));
                 ++pruned;
             }
         }
         if (pruned) atomicAdd(&sm.cnt[kCntPruned], pruned);
         __syncthreads();
         if (sm.cnt[kCntPruned]) {
-            // Domains of the variables that lost values go to the host.
+            // The changed mask and the domains of the variables that lost values
+            // go to the host (one thread per variable, all read at once).
             uint32_t* outDom = reinterpret_cast<uint32_t*>(H + kStatusHdr + T.nChangedWords);
-            for (int q = tid; q < T.nChangedWords; q += kThreads) {
-                uint32_t bits = 0u;
-                for (int b = 0; b < 32 && q * 32 + b < T.arity; ++b) {
-                    const int i = q * 32 + b;
-                    if (__ldcg(&T.changed[i])) {
-                        bits |= 1u << b;
-                        T.changed[i] = 0;
-                        for (int k = 0; k < V.nw(i); ++k) outDom[V.ld(i) + k] = __ldcg(&dom[V.off(i) + k]);
-                    }
-                }
-                H[kStatusHdr + q] = (int32_t)bits;
+            for (int q = tid; q < T.nChangedWords; q += kThreads) H[kStatusHdr + q] = sm.scan[kChgBase + q];
+            for (int i = tid; i < T.arity; i += kThreads) {
+                if (!((sm.scan[kChgBase + (i >> 5)] >> (i & 31)) & 1)) continue;
+                for (int k = 0; k < V.nw(i); ++k) outDom[V.ld(i) + k] = __ldcg(&dom[V.off(i) + k]);
             }
         }
     }
@@ -132,7 +158,6 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     if (tid < kStatusHdr && tid != kSlotStatus) {
         int32_t v = sm.scan[tid];
         if (tid == kSlotPruned) v = (int32_t)sm.cnt[kCntPruned];
-        else if (tid == kSlotHard) v = nh;
         else if (tid == kSlotT4) v = (int32_t)((uint32_t)gtimer() - (uint32_t)v);
         H[tid] = v;
     }
@@ -146,12 +171,16 @@ __device__ void finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
         // Everything written above reaches the host before the word that publishes it.
         st_release_sys(&H[kSlotStatus], st);
     }
+    return true;
 }
 
 // The residue test of value r with its residue chunk already loaded (lane 0),
-// then Algorithm 3's window search on a miss.
+// then Algorithm 3's window search on a miss: over the chunks that follow the
+// residue while most chunks are live, over the LIVE chunks that follow it
+// (found through the non-zero index) when fewer than half are, where a value
+// whose windows covered every live chunk is known unsupported without a scan.
 __device__ __forceinline__ void probe_loaded(const TableDev& T, int r, bool present, int res, const uint4& supRes,
-                                             const uint4& curRes, uint32_t* s_cnt) {
+                                             const uint4& curRes, bool sparse, uint32_t* s_cnt) {
     const int lane = threadIdx.x & 31;
     if (!present) return;
     if (T.useResidues) {
@@ -161,7 +190,8 @@ __device__ __forceinline__ void probe_loaded(const TableDev& T, int r, bool pres
             return;
         }
     }
-    probe_miss<false>(T, r, res, s_cnt);
+    if (sparse) probe_miss<true, kModelProbes>(T, r, res, s_cnt);
+    else probe_miss<false, kLocalProbes>(T, r, res, s_cnt);
 }
 
 // Per-CTA counters of a phase into the control block (zero counts skipped).
@@ -192,18 +222,18 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     GridBarrier bar;
     bar_init(bar, &C->bar_count, &C->bar_gen, &C->status, P.spinLimit ? P.spinLimit : kBarrierSpinLimit);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
+    CT_STAMP(0);
 
     // Prologue loads that do not depend on the plan: the first segment of the
     // warp when every warp takes a whole segment, and the residue (with its
     // supports chunk) of the first value it probes.
     SegState seg0;
     if (gwarp < T.nseg) seg0 = load_segment(T, gwarp, P.mark);
+    // (the supports chunk at the residue is loaded after the plan, so that the
+    // warp does not wait for the residue before the plan's loads)
     int res0 = 0;
     uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
-    if (T.useResidues && gwarp < T.R && lane == 0) {
-        res0 = T.residue[gwarp];
-        supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
-    }
+    if (T.useResidues && gwarp < T.R && lane == 0) res0 = T.residue[gwarp];
 
     // plan (CTA 0 also snapshots lastDom into the levels saved since the last call)
     int nrows;
@@ -255,8 +285,11 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.codes[q]);
     }
     if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
+    CT_STAMP(1);
+    if (T.useResidues && gwarp < T.R && lane == 0) supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
 
     uint4 curRes0 = make_uint4(0u, 0u, 0u, 0u);
+    bool sparse = 2 * P.prevLive < T.W4;  // fewer than half the chunks live (after the update: recomputed)
     if (!ok || (nrows == 0 && !T.negative)) {
         // Nothing to update: currTable stays as it is. Pending level snapshots
         // of the index are still taken.
@@ -296,11 +329,11 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         const int per = (nrows + G - 1) >> lg;  // rows per slice
         __syncthreads();
         const int cap = __ldcg(&C->trail_cap);
-        // Rounds of one unit per warp; with G > 1 every warp of a CTA runs
-        // every round so that the slice combination can synchronise the CTA.
+        // Rounds of one unit per warp; every warp of a CTA runs every round so
+        // that the trail reservation and the slice combination can
+        // synchronise the CTA.
         for (int base = blockIdx.x * kWarps; base < units; base += nwarps) {
             const int u = base + warp;
-            if (G == 1 && u >= units) break;
             const int seg = u >> lg, slice = u & (G - 1);
             TrailItem it;
             it.need = false;
@@ -313,9 +346,22 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
                 if (slice == 0) {
                     // levels saved since the last call snapshot the index as it is now
                     for (int l = P.snapFrom + lane; l < P.snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = S.mask;
-                    slots = trail_reserve(T, S, P.mark);
+                    slots.cand = __ballot_sync(0xffffffffu, P.mark >= 0 && ((S.mask >> lane) & 1u) && S.lp < P.mark);
                 }
             }
+            if (lane == 0) sm.trw[warp] = __popc(slots.cand);
+            __syncthreads();
+            int ctaBase = 0;  // thread 0: the CTA's block of slots, waited for after the row loads
+            if (tid == 0) {
+                int tot = 0;
+                for (int k = 0; k < kWarps; ++k) {
+                    const int c = sm.trw[k];
+                    sm.trw[k] = tot;
+                    tot += c;
+                }
+                if (tot) ctaBase = atomicAdd(&C->trail_top, tot);
+            }
+            CT_STAMP(8);
             uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
             if (G == 1) {
                 if (S.mask != 0u)
@@ -330,16 +376,23 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
                 __syncthreads();
                 if (S.mask != 0u && slice == 0) acc = combine_slices(parts, warp, G);
             }
+            CT_STAMP(9);
+            if (tid == 0) sm.trBase = ctaBase;
+            __syncthreads();
+            CT_STAMP(10);
             if (S.mask != 0u && slice == 0) {
                 finish_segment(T, P.mark, seg, S, acc, sm.cnt, it);
+                slots.base = sm.trBase + sm.trw[warp];
                 trail_write(T, slots, it, cap, sm.cnt);
             }
-            if (G > 1) __syncthreads();  // the parts are rewritten by the next round
+            __syncthreads();  // the slot counts and the parts are rewritten by the next round
         }
         __syncthreads();
+        CT_STAMP(2);
         if (tid == 0) flush_update_counters(C, sm);
         const int r1 = bar_sync(bar, &sm.flag[0]);
         if (!r1) return;
+        CT_STAMP(3);
         if (r1 == 2 && tid == 0) C->t[2] = gtimer();
         // Algorithm 1 line 5: fail when currTable is all zero (a negative
         // table with no valid forbidden tuple forbids nothing; an empty shard
@@ -348,6 +401,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         if (T.useResidues && gwarp < T.R && lane == 0) curRes0 = __ldcg(T.curr + res0);
         const int st1 = __ldcg(&C->status);
         const uint32_t live1 = __ldcg(&C->live);
+        sparse = 2u * live1 < (uint32_t)T.W4;
         if (st1 != CT_OK || (!T.negative && !T.shard && live1 == 0u)) {
             if (r1 == 2) {
                 if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
@@ -405,7 +459,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             cr = __ldcg(T.curr + res);
         }
         res = __shfl_sync(0xffffffffu, res, 0);
-        probe_loaded(T, r, present, res, sr, cr, sm.cnt);
+        probe_loaded(T, r, present, res, sr, cr, sparse, sm.cnt);
     }
     __syncthreads();
     if (tid == 0) {
@@ -414,22 +468,29 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         if (sm.cnt[kCntMiss]) atomicAdd(&C->misses, (int)sm.cnt[kCntMiss]);
         if (sm.cnt[kCntWin]) atomicAdd(&C->windows, (int)sm.cnt[kCntWin]);
     }
+    CT_STAMP(4);
     const int r2 = bar_sync(bar, &sm.flag[0]);
     if (!r2) return;
+    CT_STAMP(5);
     const uint64_t t3 = r2 == 2 ? gtimer() : 0ull;
-    const int nh = (int)__ldcg(&C->nhard);
-    if (nh == 0) {
-        // Every value kept its support: the CTA that arrived last publishes,
-        // the others are done.
-        if (r2 == 2) finalize(T, V, dom, sm, 0, t3);
+    // The CTA that arrived last reads the hard-value counts with the counters
+    // it publishes: with none left undecided (every value kept its support,
+    // or its windows covered every live chunk) it removes the unsupported
+    // values and publishes, and the others are done.
+    if (r2 == 2 && finalize(T, V, dom, sm, -1, t3)) {
+        CT_STAMP(6);
         return;
     }
+    if (__ldcg(&C->nscan) == 0) return;
+    const int nh = (int)__ldcg(&C->nhard);
     if (r2 == 2 && tid == 0) C->t[3] = t3;
     // full scan of the hard values
+    CT_STAMP(11);
     {
         const int staged = min(nh, kCodeCap);
         for (int q = tid; q < staged; q += kThreads) sm.codes[q] = __ldcg(&T.hardRow[q]);
         __syncthreads();
+        CT_STAMP(12);
         if (T.negative) {
             for (int seg = gwarp; seg < T.nseg; seg += nwarps) count_segment(T, seg, nh, sm.codes);
         } else {
@@ -437,6 +498,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         }
     }
     // last-block-done
+    CT_STAMP(13);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -444,9 +506,11 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         sm.flag[1] = (t == gridDim.x - 1);
     }
     __syncthreads();
+    CT_STAMP(14);
     if (!sm.flag[1]) return;
     __threadfence();
     finalize(T, V, dom, sm, nh, 0ull);
+    CT_STAMP(7);
 }
 
 // ---------------------------------------------------------------------------
@@ -556,6 +620,13 @@ cudaError_t launch_propagate(const TableDev& T, int variant, int grid, uint32_t*
         default: return launch_coop<true, 8, 3>(T, grid, dom, domOff, P, s);
     }
 }
+
+#ifdef CT_PHASE_TRACE
+extern "C" int ct_trace_read(unsigned long long* out, int n) {
+    if (n > kTraceCtas * kTraceStamps) n = kTraceCtas * kTraceStamps;
+    return cudaMemcpyFromSymbol(out, g_ct_trace, (size_t)n * sizeof(unsigned long long)) == cudaSuccess ? 0 : -3;
+}
+#endif
 
 cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s) {
     const int n = T.nseg > T.DW ? T.nseg : T.DW;
