@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the context measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--case", default="stream",
-                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "search", "learned", "net512", "planning"],
+                   choices=["stream", "bulk1e6", "bulk4e6", "bulk1e7", "stream1e7", "search", "learned", "net512",
+                            "planning"],
                    help="bulk*: only the one-call bandwidth case (for profiling); "
                         "search: only the plain vs batched search figures; "
                         "learned: the learned-order experiment at full size; "
@@ -203,6 +204,7 @@ class Replay:
         self.ops = []      # ("save",) | ("restore", level) | ("prop", k)
         self.inputs = []   # uint32 words per propagation
         self.statuses = []
+        self.outputs = []  # filtered domains of each propagation (None after a failure)
 
 
 def plan_steps(C, torch, h, dom, dom_size, root_words, nsteps, calls, depth, seed):
@@ -225,6 +227,8 @@ def plan_steps(C, torch, h, dom, dom_size, root_words, nsteps, calls, depth, see
             st, _ = C.ct_propagate(h, dom, 0)
             C.check(st)
             rp.statuses.append(st)
+            out_words = dom.cpu().numpy().view(np.uint32).copy()
+            rp.outputs.append(out_words if st == C.CT_OK else None)
             d += 1
             if st == C.CT_INFEASIBLE or d >= depth:
                 C.check(C.ct_restore(h, 1))
@@ -232,7 +236,7 @@ def plan_steps(C, torch, h, dom, dom_size, root_words, nsteps, calls, depth, see
                 masks = C.words_to_masks(root_words, dom_size)
                 d = 0
             else:
-                masks = C.words_to_masks(dom.cpu().numpy().view(np.uint32), dom_size)
+                masks = C.words_to_masks(out_words, dom_size)
         if d:
             C.check(C.ct_restore(h, 1))
             rp.ops.append(("restore", 1))
@@ -296,10 +300,34 @@ def run_ours(args, rank, world):
         nres = len(rp.ops) - nprop - nsave
         return calls, (nprop, nsave, nres)
 
-    def run_calls(calls):
+    def run_calls(calls, statuses=None):
         for f, a in calls:
-            if f(*a) < 0:
+            r = f(*a)
+            if r < 0:
                 raise RuntimeError(C.last_error())
+            if statuses is not None and f is f_prop:
+                statuses.append(r)
+
+    W = int(info["words"])
+    st, root_ct, _ = C.ct_get_currtable(h, W)
+    C.check(st)
+    import hashlib
+    root_digest = hashlib.sha256(root_ct.tobytes()).hexdigest()[:16]
+    mismatches = []
+
+    def verify(s_idx, rp, work, statuses):
+        """The replayed step did the planned work: same statuses, same filtered
+        domains, and currTable back at the root state at the end of the step."""
+        if statuses != rp.statuses:
+            mismatches.append(f"step {s_idx}: statuses differ")
+        got = work.cpu().numpy().view(np.uint32).reshape(len(rp.inputs), DW)
+        for k, want in enumerate(rp.outputs):
+            if want is not None and not np.array_equal(got[k], want):
+                mismatches.append(f"step {s_idx} call {k}: domains differ")
+                break
+        st, words, _ = C.ct_get_currtable(h, W)
+        if st != C.CT_OK or hashlib.sha256(words.tobytes()).hexdigest()[:16] != root_digest:
+            mismatches.append(f"step {s_idx}: currTable not back at the root state")
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -319,17 +347,21 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             clk = clocks_start(gpu_index if world == 1 else local)
         calls, (n, ns, nr) = replay(rp, work)
+        sts = []
         torch.cuda.synchronize()
         ev0.record(stream)
-        run_calls(calls)
+        run_calls(calls, sts)
         ev1.record(stream)
         torch.cuda.synchronize()
+        verify(s, rp, work, sts)
         if s >= args.warmup:
             step_ms.append(ev0.elapsed_time(ev1))
             props += n
             # one launch per propagation and per restore; ct_save launches nothing
             launches += KERNELS_PER_PROPAGATE * n + nr
     clocks = clocks_stop(clk)
+    if mismatches:
+        raise SystemExit("timed replay differs from the planned calls: " + "; ".join(mismatches[:5]))
     if world > 1:
         torch.distributed.barrier()
     # profiled replay of the timed steps (untimed): per-launch CUDA events and
@@ -451,9 +483,22 @@ def run_ours(args, rank, world):
                             "note": "CUDA events around each ct_propagate of the timed steps, L2 flushed "
                                     "between steps (untimed pass)"},
     }
+    result["replay_check"] = {"steps": len(plans), "propagations": sum(len(rp.inputs) for rp in plans),
+                              "statuses_equal": True, "domains_equal": True, "currtable_back_at_root": True,
+                              "note": "every timed step was compared, after its timed region, with the "
+                                      "planning pass: status and filtered domains of each call, and the "
+                                      "currTable digest at the end of the step; a mismatch exits non-zero"}
     C.ct_destroy(h)
     del flush
     if rank == 0 and not args.no_extra:
+        # figures of the other configurations, at the top level of the line
+        result["bulk_update"] = {
+            "t1e6_arity6_d32": _bulk_update(C, torch, stream, 1_000_000, 6, 32, 5),
+            "t4e6_arity6_d32": _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5),
+            "t1e7_arity5_d64": _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)}
+        result["stream_1e7_arity5_d64"] = _stream_rate(C, torch, stream, 10_000_000, 128, 99 + 10_000_000,
+                                                       arity=5, d=64, roofline=True)
+        result["search"] = search_extras(C)
         result["extra"] = extras(args, C, torch, stream)
     if rank == 0:
         result["cpu_baseline"] = cpu_baseline(args, plans[args.warmup:], dom_lo, dom_size, tup)
@@ -465,9 +510,38 @@ def run_ours(args, rank, world):
     return result
 
 
-def _bulk_update(C, torch, stream, t, arity, d, seed, reps=5):
+def _read_ceiling(torch, nbytes, flush, reps=7):
+    """What one stock library kernel reaches reading `nbytes` once on this GPU:
+    torch's float32 sum over a buffer of that size, L2 flushed before each
+    launch, CUDA events around it (median). A single launch this short pays
+    launch and ramp-up latency that a long copy amortises, so this is the
+    bandwidth a one-call propagation of that many bytes could hope for."""
+    x = torch.ones(max(1, int(nbytes) // 4), dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        x.sum()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    del x
+    return x_bytes_per_s(nbytes, statistics.median(ms))
+
+
+def x_bytes_per_s(nbytes, ms):
+    return nbytes / (ms / 1e3) / 1e9
+
+
+def _bulk_update(C, torch, stream, t, arity, d, seed, reps=9):
     """One big reset call per repetition (every variable keeps < half its values):
-    the bandwidth regime of updateTable on a large table, L2 flushed before each."""
+    the bandwidth regime of updateTable on a large table, L2 flushed before each.
+    Medians over the repetitions of: the CUDA-event interval around the launch,
+    the device-timer span, and the update phase by the device timer (plan end to
+    the barrier after updateTable); beside them the contiguous-read ceiling of
+    the same bytes (_read_ceiling)."""
     dom_lo, dom_size, tup = G.large_table(seed, t, arity, d)
     st, h = C.ct_create(arity, dom_lo, dom_size, tup, opt=C.make_options(profile=1), stream=stream)
     C.check(st)
@@ -486,33 +560,57 @@ def _bulk_update(C, torch, stream, t, arity, d, seed, reps=5):
         masks.append(m)
     w = C.masks_to_words(masks).view(np.int32).copy()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
-    C.ct_reset_profile(h)
+    ev, dev, upd = [], [], []
     stats = None
     for r in range(reps):
         C.check(C.ct_save(h)[0])
         dom.copy_(torch.from_numpy(w))
         flush.zero_()
         torch.cuda.synchronize()
+        C.ct_reset_profile(h)
         st, _ = C.ct_propagate(h, dom, 0)
         C.check(st)
+        prof = C.ct_get_profile(h)[1]
         stats = C.ct_get_call_stats(h)[1]
+        ev.append(prof["kernel_ms"] * 1e3)
+        ph = stats["phase_ns"]
+        dev.append(ph[3] / 1e3)
+        upd.append((ph[1] - ph[0]) / 1e3)
         C.check(C.ct_restore(h, 1))
-    st, prof = C.ct_get_profile(h)
+    info = C.ct_get_info(h)[1]
     C.ct_destroy(h)
-    alg = prof["update_bytes"] + prof["filter_bytes"]
-    gbs = alg / (prof["kernel_ms"] / 1e3) / 1e9
+    alg = stats["update_bytes"] + stats["filter_bytes"]
+    hbm = peaks()[0]
+    ev_us, dev_us, upd_us = statistics.median(ev), statistics.median(dev), statistics.median(upd)
+    gbs = alg / ev_us / 1e3
+    ceiling = _read_ceiling(torch, alg, flush)
+    del flush
     return {"tuples": t, "arity": arity, "domain": d, "rows_ored": stats["rows_ored"],
-            "bytes_per_launch": alg / reps, "launch_us": prof["kernel_ms"] * 1e3 / reps,
-            "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peaks()[0], 4),
-            "device_us": prof["device_ms"] * 1e3 / reps, "phase_ns_last": stats["phase_ns"]}
+            "grid_blocks": info["grid_blocks"], "loads_in_flight": info["loads_in_flight"],
+            "bytes_per_launch": alg, "launch_us": round(ev_us, 2), "GBps": round(gbs, 1),
+            "frac_of_hbm": round(gbs / hbm, 4),
+            "device_us": round(dev_us, 2),
+            "update_phase_us": round(upd_us, 2),
+            "update_phase_GBps": round(stats["update_bytes"] / upd_us / 1e3, 1),
+            "update_phase_frac_of_hbm": round(stats["update_bytes"] / upd_us / 1e3 / hbm, 4),
+            "read_ceiling_GBps": round(ceiling, 1),
+            "frac_of_read_ceiling": round(gbs / ceiling, 4),
+            "phase_ns_last": stats["phase_ns"],
+            "note": "medians of %d one-call repetitions, L2 flushed before each; GBps by CUDA events "
+                    "around the launch; update phase by the device timer (plan end to the barrier "
+                    "after updateTable); read ceiling: one torch float32 sum over the same bytes" % reps}
 
 
-def _stream_rate(C, torch, stream, t, calls, seed, opt=None, shape=None):
-    dom_lo, dom_size, tup = G.large_table(seed, t, ARITY, DOM)
-    st, h = C.ct_create(ARITY, dom_lo, dom_size, tup, opt=opt, stream=stream)
+def _stream_rate(C, torch, stream, t, calls, seed, opt=None, shape=None, arity=ARITY, d=DOM, roofline=False):
+    """Propagations/s of a planned delta/reset stream on one table (best of two
+    planned steps, host wall time, inputs in HBM). With roofline: also a
+    profiled replay of the same steps (CUDA events around every launch) and the
+    algorithmic bytes of its calls, as for the headline stream."""
+    dom_lo, dom_size, tup = G.large_table(seed, t, arity, d)
+    st, h = C.ct_create(arity, dom_lo, dom_size, tup, opt=opt, stream=stream)
     C.check(st)
+    inf = C.ct_get_info(h)[1]
     if shape is not None:
-        inf = C.ct_get_info(h)[1]
         shape.update(grid_blocks=inf["grid_blocks"], loads_in_flight=inf["loads_in_flight"],
                      autotuned=inf["autotuned"])
     off, _ = C.dom_layout(dom_size)
@@ -525,22 +623,44 @@ def _stream_rate(C, torch, stream, t, calls, seed, opt=None, shape=None):
     plans = plan_steps(C, torch, h, dom, dom_size, root, 2, calls, 8, seed)
     DW = int(off[-1])
     best = None
-    for rp in plans:
-        work = torch.from_numpy(np.stack(rp.inputs).view(np.int32).copy()).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+
+    def replay(rp, work):
         for op in rp.ops:
             if op[0] == "save":
                 C.ct_save(h)
             elif op[0] == "restore":
                 C.ct_restore(h, op[1])
             else:
-                C.ct_propagate(h, work.data_ptr() + op[1] * DW * 4, 0)
+                C.check(C.ct_propagate(h, work.data_ptr() + op[1] * DW * 4, 0)[0])
+
+    for rp in plans:
+        work = torch.from_numpy(np.stack(rp.inputs).view(np.int32).copy()).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        replay(rp, work)
         torch.cuda.synchronize()
         rate = len(rp.inputs) / (time.perf_counter() - t0)
         best = rate if best is None else max(best, rate)
+    out = round(best, 1)
+    if roofline:
+        C.check(C.ct_set_profile(h, 1))
+        C.check(C.ct_reset_profile(h))
+        for rp in plans:
+            replay(rp, torch.from_numpy(np.stack(rp.inputs).view(np.int32).copy()).cuda())
+        torch.cuda.synchronize()
+        prof = C.ct_get_profile(h)[1]
+        alg = prof["update_bytes"] + prof["filter_bytes"]
+        hbm, kind = peaks()
+        ach = alg / (prof["kernel_ms"] / 1e3) / 1e9
+        out = {"value": out, "unit": UNIT, "tuples": t, "arity": arity, "domain": d, "calls": len(plans) * calls,
+               "grid_blocks": inf["grid_blocks"],
+               "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                            "frac": round(ach / hbm, 4), "peak_kind": kind,
+                            "avg_bytes_per_launch": alg / max(prof["calls"], 1),
+                            "avg_launch_us": prof["kernel_ms"] * 1e3 / max(prof["calls"], 1),
+                            "avg_device_us": prof["device_ms"] * 1e3 / max(prof["calls"], 1)}}
     C.ct_destroy(h)
-    return round(best, 1)
+    return out
 
 
 def _dfs_rate(C, node_limit=3000, host_fixpoint=0):
@@ -571,18 +691,19 @@ def _build_model(C, spec):
     return m
 
 
-def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_limit=20000):
+def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_limit=20000, assign=False):
     """Nodes/s of the plain search (one node per launch) and of the batched search
     (slots x tables propagated per launch) on the same CSP, counting all solutions
     up to a node limit; the batched figure is the second of two calls (the first
-    builds the slot copies and grows their trails)."""
+    builds the slot copies and grows their trails). assign: the split depth
+    counts assignments on a node's path (ct_search_batch_assign)."""
     m = _build_model(C, spec)
     try:
         st, p = C.ct_search_dfs(m, spec.nvars, plain_limit, True)
         C.check(st)
         first = None
         for _ in range(2):
-            st, b, info = C.ct_search_batch(m, spec.nvars, slots, split, batch_limit, True)
+            st, b, info = C.ct_search_batch(m, spec.nvars, slots, split, batch_limit, True, split_assignments=assign)
             C.check(st)
             first = first or (b["seconds"], info["setup_seconds"])
     finally:
@@ -591,7 +712,9 @@ def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_
     batch_nps = b["nodes"] / b["seconds"]
     return {"csp": name, "plain": {"nodes": p["nodes"], "seconds": round(p["seconds"], 3),
                                    "nodes_per_s": round(plain_nps, 1)},
-            "batched": {"slots": slots, "split_depth": split, "nodes": b["nodes"], "fails": b["fails"],
+            "batched": {"slots": slots, "split_depth": split,
+                        "split_counts": "assignments on the path" if assign else "binary levels",
+                        "nodes": b["nodes"], "fails": b["fails"],
                         "solutions": b["solutions"], "seconds": round(b["seconds"], 3),
                         "nodes_per_s": round(batch_nps, 1), "launches": info["steps"],
                         "rounds": info["rounds"], "open_nodes": info["open_nodes"], "steals": info["steals"],
@@ -604,8 +727,11 @@ def search_extras(C):
     out = {}
     out["config2_20v_8t_arity6_1e5"] = _search_compare(
         C, "20 vars d=32, 8 tables arity 6 x 1e5 tuples", G.random_csp(2024, 20, 8, 6, 32, 100_000))
+    # 1,024 independent search nodes: the frontier of the binary first-fail
+    # tree at depth 10 (at most 2^10 = 1,024 open nodes), one slot each
     out["config3_40v_60t_arity4"] = _search_compare(
-        C, "40 vars d=24, 60 tables arity 4 x log-uniform 1e4..2e5 tuples", G.batching_csp(3003))
+        C, "40 vars d=24, 60 tables arity 4 x log-uniform 1e4..2e5 tuples", G.batching_csp(3003),
+        slots=1024, split=10)
     return out
 
 
@@ -762,12 +888,8 @@ def extras(args, C, torch, stream):
             r1 = _stream_rate(C, torch, stream, t, 128, 99 + t, opt=C.make_options(autotune=1), shape=d1)
             tuned[str(t)] = {"default": {"props_per_s": r0, **d0}, "autotuned": {"props_per_s": r1, **d1}}
         out["autotune_props_per_s"] = tuned
-        out["bulk_update_1e6"] = _bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)
-        out["bulk_update_4e6"] = _bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)
-        out["bulk_update_1e7_arity5_d64"] = _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)
         out["dfs_plain_first_fail"] = _dfs_rate(C)
         out["dfs_plain_first_fail_host_queue"] = _dfs_rate(C, host_fixpoint=1)
-        out["search_batched_vs_plain"] = search_extras(C)
         out["learned_order"] = learned_extras(C)
         out["planning_chain"] = planning_extras(C)
     except Exception as e:  # context figures must not hide the main line
@@ -951,6 +1073,9 @@ def main():
                                             full_eval=args.learned_full)))
         elif args.case == "bulk1e6":
             print(json.dumps(_bulk_update(C, torch, stream, 1_000_000, 6, 32, 5)))
+        elif args.case == "stream1e7":
+            print(json.dumps(_stream_rate(C, torch, stream, 10_000_000, 128, 99 + 10_000_000, arity=5, d=64,
+                                          roofline=True)))
         elif args.case == "bulk4e6":
             print(json.dumps(_bulk_update(C, torch, stream, 4_000_000, 6, 32, 5)))
         else:

@@ -488,6 +488,19 @@ typedef struct ct_batch_info {
 int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,
                     ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
 
+/* ct_search_batch_assign: ct_search_batch with the tree split where a node's
+ * path holds `assign_depth` assignments (left branches x = v) instead of at a
+ * number of binary levels: every node above the split is expanded breadth-first
+ * in the slots (a right branch x != v keeps its parent's count), and the nodes
+ * that reach assign_depth assignments are the open nodes, put in depth-first
+ * order. The tree is the one ct_search_dfs visits, so with count_all = 1 and
+ * no node limit the counts equal its counts. This reads "search nodes split
+ * at depth d" of a d-way enumeration as d assignments of the binary tree.
+ *   assign_depth 1 .. 16; count_all 0 or 1 (else CT_ERR_ARG); the rest as in
+ *                ct_search_batch (info->open_nodes: the open nodes made). */
+int ct_search_batch_assign(ct_model* m, int slots, int assign_depth, int64_t node_limit, int count_all,
+                           ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
+
 int ct_model_destroy(ct_model* m);
 
 /* ------------------------------------------------------- learned order -- */

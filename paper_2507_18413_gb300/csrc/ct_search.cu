@@ -322,6 +322,7 @@ struct Search {
     ct_model* m = nullptr;
     ct_batch* b = nullptr;
     int B = 0, splitDepth = 0;
+    bool splitAssign = false;  // splitDepth counts assignments (left branches) on a node's path
     int64_t limit = 0;
     bool countAll = true;
     bool anyStop = false;  // stop at the first solution any slot finds
@@ -514,7 +515,20 @@ struct Search {
         splitOut.assign(B, SplitOut());
         std::vector<OpenNode> F, G;
         children(F, m->h_dom, x, 1, std::vector<uint8_t>());
-        for (int depth = 1; depth < splitDepth && !F.empty() && !stopIssue; ++depth) {
+        for (int depth = 1; !F.empty() && !stopIssue; ++depth) {
+            if (!splitAssign && depth >= splitDepth) break;
+            if (splitAssign) {
+                // nodes with splitDepth assignments on their path are open nodes
+                std::vector<OpenNode> rest;
+                for (OpenNode& o : F) {
+                    int a = 0;
+                    for (uint8_t br : o.path) a += br == 0;
+                    if (a >= splitDepth) open.push_back(std::move(o));
+                    else rest.push_back(std::move(o));
+                }
+                F.swap(rest);
+                if (F.empty()) break;
+            }
             G.clear();
             for (size_t i0 = 0; i0 < F.size() && !stopIssue; i0 += (size_t)B) {
                 const size_t i1 = std::min(F.size(), i0 + (size_t)B);
@@ -544,6 +558,14 @@ struct Search {
             F.swap(G);
         }
         for (OpenNode& o : F) open.push_back(std::move(o));
+        if (splitAssign) {
+            // open nodes met at different tree depths, put in depth-first order:
+            // no open node is an ancestor of another, so that is the
+            // lexicographic order of the paths (left before right)
+            std::sort(open.begin(), open.end(), [](const OpenNode& a, const OpenNode& b) {
+                return std::lexicographical_compare(a.path.begin(), a.path.end(), b.path.begin(), b.path.end());
+            });
+        }
         return CT_OK;
     }
 
@@ -913,8 +935,28 @@ struct Search {
 
 }  // namespace
 
+namespace {
+int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int64_t node_limit, int count_all,
+                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
+}  // namespace
+
 extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,
                                ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
+    return search_batch(m, slots, split_depth, false, node_limit, count_all, out, first_solution, info);
+}
+
+extern "C" int ct_search_batch_assign(ct_model* m, int slots, int assign_depth, int64_t node_limit, int count_all,
+                                      ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
+    if (assign_depth < 1 || assign_depth > 16 || count_all == 2) {
+        ct_set_error("ct_search_batch_assign: assign_depth %d out of [1, 16] or count_all %d", assign_depth, count_all);
+        return CT_ERR_ARG;
+    }
+    return search_batch(m, slots, assign_depth, true, node_limit, count_all, out, first_solution, info);
+}
+
+namespace {
+int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int64_t node_limit, int count_all,
+                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
     if (!m || !out) {
         ct_set_error("ct_search_batch: null argument");
         return CT_ERR_ARG;
@@ -948,6 +990,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     S.b = m->bsearch;
     S.B = slots;
     S.splitDepth = split_depth;
+    S.splitAssign = split_assign;
     S.limit = node_limit;
     S.countAll = count_all == 1;
     S.anyStop = count_all == 2;
@@ -962,7 +1005,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     std::vector<uint8_t> path;
     // the breadth-first split in the slots, except for the budgeted
     // any-solution search (the model searches its share depth-first first)
-    if (split_depth >= 2 && !S.anyStop) {
+    if ((split_depth >= 2 || split_assign) && !S.anyStop) {
         rc = S.split_bfs();
     } else {
         if (split_depth == 0) rc = S.ensure_copies();
@@ -990,6 +1033,7 @@ extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t 
     }
     return CT_OK;
 }
+}  // namespace
 
 extern "C" int ct_model_lookahead(ct_model* m, int slots, float* labels_host) {
     if (!m || !labels_host || slots < 1 || slots > 4096 || (int64_t)slots * (int64_t)m->tables.size() > kModelMaxTables) {

@@ -142,6 +142,8 @@ _SIGS = {
     "ct_search_dfs": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ct_search_stats), _I32P]),
     "ct_search_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
+    "ct_search_batch_assign": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
     "ct_create_negative": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.POINTER(ct_options),
                                           _P, ctypes.POINTER(_P)]),
@@ -515,16 +517,18 @@ def ct_search_dfs(m, nvars, node_limit=0, count_all=True):
     return st, d
 
 
-def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True):
+def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True, split_assignments=False):
     """Batched search: returns (status, stats dict with first_solution, batch info dict).
     count_all: True/1 all solutions, False/0 the depth-first first solution,
-    2 (or "any") the first solution any slot finds."""
+    2 (or "any") the first solution any slot finds. split_assignments: the
+    split depth counts assignments on a node's path (ct_search_batch_assign)."""
     s = ct_search_stats()
     info = ct_batch_info()
     sol = np.zeros(nvars, dtype=np.int32)
     mode = 2 if count_all == "any" else int(count_all)
-    st = load().ct_search_batch(m, int(slots), int(split_depth), int(node_limit), mode,
-                                ctypes.byref(s), sol.ctypes.data_as(_I32P), ctypes.byref(info))
+    fn = load().ct_search_batch_assign if split_assignments else load().ct_search_batch
+    st = fn(m, int(slots), int(split_depth), int(node_limit), mode,
+            ctypes.byref(s), sol.ctypes.data_as(_I32P), ctypes.byref(info))
     d = _as_dict(s)
     d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
     return st, d, _as_dict(info)

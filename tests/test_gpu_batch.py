@@ -216,3 +216,65 @@ def test_batch_any_solution_mode(seed):
             assert (got["nodes"], got["fails"]) == (want.nodes, want.fails)
     assert C.ct_search_batch(h, csp.nvars, 4, 1, 0, 3)[0] == C.CT_ERR_ARG
     C.ct_model_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# split at a number of assignments (ct_search_batch_assign)
+# --------------------------------------------------------------------------
+
+def _open_nodes_by_assignments(csp, depth):
+    """Oracle count of the nodes that reach `depth` assignments (left branches)
+    in the depth-first tree, i.e. the open nodes of the split."""
+    count = 0
+
+    def node(m, a):
+        nonlocal count
+        if a == depth:
+            count += 1
+            return
+        st, m2, _ = O.gac_network(csp, m)
+        if st == O.INFEASIBLE:
+            return
+        x = O.select_first_fail(m2)
+        if x is None:
+            return
+        v = int(np.flatnonzero(m2[x])[0])
+        left = [mm.copy() for mm in m2]
+        left[x] = np.zeros_like(m2[x])
+        left[x][v] = True
+        right = [mm.copy() for mm in m2]
+        right[x][v] = False
+        node(left, a + 1)
+        node(right, a)
+
+    node(csp.full_masks(), 0)
+    return count
+
+
+@pytest.mark.parametrize("slots,depth", [(4, 1), (16, 2), (64, 3), (5, 4)])
+@pytest.mark.parametrize("seed", range(4))
+def test_batch_assignment_split_counts_equal_the_oracle_search(seed, slots, depth):
+    csp, raw = _random(700 + seed, nvars=7, ntables=5, arity=3, d=5, t=35 + 5 * seed)
+    want = O.dfs(csp, count_all=True)
+    h = _model(csp, raw)
+    st, got, info = C.ct_search_batch(h, csp.nvars, slots, depth, 0, True, split_assignments=True)
+    assert st == C.CT_OK, C.last_error()
+    _assert_counts(got, want)
+    assert info["split_nodes"] + info["slot_nodes"] == got["nodes"]
+    assert info["open_nodes"] == _open_nodes_by_assignments(csp, depth)
+    # first solution mode returns the depth-first first solution
+    want1 = O.dfs(csp, count_all=False)
+    st, got1, _ = C.ct_search_batch(h, csp.nvars, slots, depth, 0, False, split_assignments=True)
+    assert st == C.CT_OK
+    if want1.solutions:
+        assert got1["first_solution"] == want1.first_solution
+    C.ct_model_destroy(h)
+
+
+def test_batch_assignment_split_bad_arguments():
+    csp, raw = _random(710, nvars=5, ntables=3, arity=3, d=4, t=20)
+    h = _model(csp, raw)
+    for depth, mode in [(0, True), (17, True), (3, "any")]:
+        st, _, _ = C.ct_search_batch(h, csp.nvars, 4, depth, 0, mode, split_assignments=True)
+        assert st == C.CT_ERR_ARG
+    C.ct_model_destroy(h)
