@@ -691,7 +691,20 @@ def _build_model(C, spec):
     return m
 
 
-def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_limit=20000, assign=False):
+def _device_search(C, m, spec, slots, split, limit):
+    """The batched search with the slots' search run on the device (second of two
+    calls: the first builds the device buffers and sizes their capacities)."""
+    for _ in range(2):
+        st, d, info = C.ct_search_batch_device(m, spec.nvars, slots, split, limit)
+        C.check(st)
+    return {"slots": slots, "split_depth": split, "nodes": d["nodes"], "fails": d["fails"],
+            "solutions": d["solutions"], "seconds": round(d["seconds"], 3),
+            "nodes_per_s": round(d["nodes"] / d["seconds"], 1), "launches": info["steps"],
+            "rounds": info["rounds"], "open_nodes": info["open_nodes"], "split_nodes": info["split_nodes"]}
+
+
+def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_limit=20000, assign=False,
+                    long_limit=0):
     """Nodes/s of the plain search (one node per launch) and of the batched search
     (slots x tables propagated per launch) on the same CSP, counting all solutions
     up to a node limit; the batched figure is the second of two calls (the first
@@ -706,6 +719,15 @@ def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_
             st, b, info = C.ct_search_batch(m, spec.nvars, slots, split, batch_limit, True, split_assignments=assign)
             C.check(st)
             first = first or (b["seconds"], info["setup_seconds"])
+        dev = _device_search(C, m, spec, slots, split, batch_limit)
+        longer = None
+        if long_limit:
+            st, bl, il = C.ct_search_batch(m, spec.nvars, slots, split, long_limit, True)
+            C.check(st)
+            longer = {"node_limit": long_limit,
+                      "batched_host_stepped": {"nodes": bl["nodes"], "seconds": round(bl["seconds"], 3),
+                                               "nodes_per_s": round(bl["nodes"] / bl["seconds"], 1)},
+                      "batched_device": _device_search(C, m, spec, slots, split, long_limit)}
     finally:
         C.ct_model_destroy(m)
     plain_nps = p["nodes"] / p["seconds"]
@@ -720,18 +742,22 @@ def _search_compare(C, name, spec, slots=512, split=10, plain_limit=3000, batch_
                         "rounds": info["rounds"], "open_nodes": info["open_nodes"], "steals": info["steals"],
                         "device_wait_s": round(info["wait_seconds"], 3),
                         "first_call_s": round(first[0], 3), "copies_setup_s": round(first[1], 3)},
-            "speedup": round(batch_nps / plain_nps, 2)}
+            "batched_device": dev,
+            "speedup": round(batch_nps / plain_nps, 2),
+            "speedup_device": round(dev["nodes_per_s"] / plain_nps, 2),
+            "longer_run": longer}
 
 
 def search_extras(C):
     out = {}
     out["config2_20v_8t_arity6_1e5"] = _search_compare(
-        C, "20 vars d=32, 8 tables arity 6 x 1e5 tuples", G.random_csp(2024, 20, 8, 6, 32, 100_000))
+        C, "20 vars d=32, 8 tables arity 6 x 1e5 tuples", G.random_csp(2024, 20, 8, 6, 32, 100_000),
+        long_limit=100_000)
     # 1,024 independent search nodes: the frontier of the binary first-fail
     # tree at depth 10 (at most 2^10 = 1,024 open nodes), one slot each
     out["config3_40v_60t_arity4"] = _search_compare(
         C, "40 vars d=24, 60 tables arity 4 x log-uniform 1e4..2e5 tuples", G.batching_csp(3003),
-        slots=1024, split=10)
+        slots=1024, split=10, long_limit=100_000)
     return out
 
 

@@ -501,6 +501,26 @@ int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit,
 int ct_search_batch_assign(ct_model* m, int slots, int assign_depth, int64_t node_limit, int count_all,
                            ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
 
+/* ct_search_batch_device: ct_search_batch counting every solution (count_all
+ * = 1, first-fail branching, no policy) with the slots' search run on the
+ * device instead of stepped by the host. The tree above split_depth is
+ * expanded as by ct_search_batch; its open nodes go to a device queue, and
+ * the fixpoint kernel, between its rounds, moves every slot whose node is at
+ * its fixpoint (or failed) on: branch on the first-fail variable, backtrack
+ * to the deepest untried right branch (trails undone and index snapshots
+ * restored on the device), or take the next open node. Each launch runs at
+ * most 1,024 rounds; the host launches again until every slot is idle and
+ * the queue is empty. The device keeps, per slot, up to L levels below its
+ * open node and, per table copy, a trail of F x its chunks + 1,024 entries;
+ * a deeper subtree or a fuller trail makes the host rebuild them with L or F
+ * doubled and run the device search again (L from 64 to 1,024, F from 16 to
+ * 128; beyond those CT_ERR_LEVEL or CT_ERR_OOM). With no node limit the
+ * counts and the first solution equal ct_search_dfs's.
+ *   slots 1 .. 4096, split_depth 0 .. 64, node_limit as in ct_search_batch;
+ *   CT_ERR_ARG when the model has a policy (ct_model_set_policy). */
+int ct_search_batch_device(ct_model* m, int slots, int split_depth, int64_t node_limit, ct_search_stats* out,
+                           int32_t* first_solution, ct_batch_info* info);
+
 int ct_model_destroy(ct_model* m);
 
 /* ------------------------------------------------------- learned order -- */

@@ -190,6 +190,56 @@ struct ModelCtrl {
     unsigned long long bytesFilter;  // of the full scans: 16 * hard values * live chunks
 };
 
+// ---------------------------------------------------------------------------
+// The batched search run on the device (ct_search_batch_device): B slots, each
+// a copy of the network (T tables, nv variables, DWs domain words), search the
+// subtrees of open nodes taken from a device queue, depth-first with
+// first-fail branching, between the rounds of the fixpoint kernel.
+// ---------------------------------------------------------------------------
+struct SearchCtr {
+    unsigned long long nodes, fails, solutions;
+    int32_t maxDepth;
+    int32_t nextOpen;    // next open node to hand out
+    int32_t nrestQ;      // table restores queued by the decision phase of a round
+    int32_t error;       // CT_OK, or why the search stopped (CT_ERR_LEVEL: deeper than the level capacity)
+    int32_t started;     // the first decision phase ran
+    int32_t cur, round;  // work-list parity to resume a launch with
+    int32_t done;        // every slot idle and no open node left (or the node limit reached)
+    int32_t pad[2];
+};
+
+struct SearchDev {
+    int32_t B, T, nv, DWs, maxLevels, segTotal;
+    int32_t nopen;
+    int32_t roundBudget;          // rounds per launch before it returns (the host launches again)
+    long long nodeLimit;          // <= 0: none
+    SearchCtr* ctr;
+    // per slot
+    int32_t* depth;               // [B] frames on the stack
+    int32_t* active;              // [B]
+    int32_t* busy;                // [B] the slot has tables in the next round (set by the collection)
+    int32_t* openIdx;             // [B] open node of the current subtree
+    int32_t* depth0;              // [B] tree depth of that open node
+    int4* frames;                 // [B][maxLevels] (x, a, branch, -)
+    uint32_t* levelDom;           // [B][maxLevels + 1][DWs] domains at each level (level 0: the root)
+    int32_t* markAt;              // [B][maxLevels + 1][T] trail position of each table at each level
+    int32_t* liveAt;              // [B][maxLevels + 1][T] live chunks of each table at each level
+    uint32_t* snapSeg;            // [B][maxLevels + 1][segTotal] index masks of every table at each level
+    int32_t* firstOpen;           // [B] open node of the slot's first solution (INT_MAX: none)
+    uint32_t* firstSol;           // [B][DWs] the domains of that solution
+    int4* restQ;                  // [B * T] queued restores: (slot table j, level, -, -)
+    ModelTabCall* calls;          // [B * T] the fixpoint kernel's per-table calls (mark kept current)
+    // per model variable and table
+    const int32_t* varOff;        // [nv] first domain word of each variable in a slot
+    const int32_t* varNW;         // [nv]
+    const int32_t* varTabStart;   // [nv + 1] tables of each variable (model table indices)
+    const int32_t* varTabList;
+    const int32_t* segOff;        // [T] first word of each table's index mask in a level's snapshot
+    // open nodes
+    const uint32_t* openDom;      // [nopen][DWs]
+    const int32_t* openDepth;     // [nopen]
+};
+
 struct ModelDev {
     const TableDev* tabs;       // [ntables]
     const ModelTabCall* calls;  // [ntables]
@@ -215,6 +265,7 @@ struct ModelDev {
     uint64_t* phaseNs;          // null, or [kModelPhases] nanoseconds added per phase (CTA 0's view)
     int4* missQ;                // [sum of the tables' rows] residue misses of a round: (table, row, residue)
     uint32_t spinLimit;         // polls of a grid-barrier wait before it gives up (0: kBarrierSpinLimit)
+    SearchDev* search;          // device copy of the search state (search mode only)
 };
 constexpr int kModelPhases = 8;  // prologue, plan, update, probe, scan, apply, next round, publish
 constexpr int kRestoreBatch = 256;
@@ -225,6 +276,14 @@ struct RestoreBatch {
 
 int max_coresident_model_blocks();
 cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s);
+// The fixpoint kernel in search mode (M.search set): decision and restore
+// phases between rounds, until the search is done or the launch's round budget
+// is spent. The grid is max_coresident_model_blocks()-bounded as for launch_model.
+cudaError_t launch_model_search(const ModelDev& M, int grid, cudaStream_t s);
+// Level 0 of every slot: the root state of its tables (after a state copy
+// into hostTabs), each with an empty trail of trailFactor * W4 + 1024 entries.
+cudaError_t launch_search_init(const ModelDev& M, const TableDev* hostTabs, const SearchDev& S,
+                               const uint32_t* rootDom, int trailFactor, cudaStream_t s);
 cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s);
 // dst[j] (n clones, j = slot * nsrc + k) takes the state of src[k]: currTable,
 // index, residues, lastDom; empty trail (lastpos = -1) and cleared counters.

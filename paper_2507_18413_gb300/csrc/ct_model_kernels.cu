@@ -113,7 +113,269 @@ __device__ __forceinline__ void remove_value(const ModelDev& M, const TableDev& 
     if (old != -1 && old != t) atomicExch(&pruned[v], -2);
 }
 
-template <int U>
+// ---------------------------------------------------------------------------
+// The batched search on the device (search mode). Between two rounds of the
+// fixpoint, one warp per slot decides: a slot whose node is at its fixpoint
+// (no table of it in the next round) or failed branches on the first-fail
+// variable (left: x = min D(x)), backtracks to the deepest frame whose right
+// branch (x != min) is untried, or, with its subtree done, takes the next
+// open node from the device queue. Restores are queued and done by the whole
+// grid after a barrier: a table's trail entries above the level's mark are
+// undone (each chunk written once), its non-zero index comes from the level's
+// snapshot, and its last-seen domains from the level's domains (a level is
+// saved at a fixpoint, where every table has seen the domains of its scope).
+// ---------------------------------------------------------------------------
+constexpr unsigned FULLM = 0xffffffffu;
+
+__device__ __forceinline__ size_t lvl(const SearchDev& S, int s, int L) {
+    return (size_t)s * (S.maxLevels + 1) + L;
+}
+
+// Append table k (model index) of slot s for each k in list[0..n) to the next
+// round's work list (warp-aggregated).
+__device__ void append_tables(const SearchDev& S, int s, const int32_t* list, int n, int32_t* next, int32_t* nnext) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool ok = i < n;
+        const unsigned bal = __ballot_sync(FULLM, ok);
+        int base = 0;
+        if (lane == 0) base = atomicAdd(nnext, __popc(bal));
+        base = __shfl_sync(FULLM, base, 0);
+        if (ok) next[base + __popc(bal & lanemask_lt())] = s * S.T + (list ? list[i] : i);
+    }
+}
+
+// First-fail over the slot's domains: the unfixed variable with the smallest
+// domain, ties to the lowest index; -1 when every variable is fixed (warp-wide).
+__device__ int warp_first_fail(const SearchDev& S, const uint32_t* dom) {
+    const int lane = threadIdx.x & 31;
+    int best = 0x7fffffff, bx = -1;
+    for (int v = lane; v < S.nv; v += 32) {
+        int sz = 0;
+        const int o = S.varOff[v], nw = S.varNW[v];
+        for (int q = 0; q < nw; ++q) sz += __popc(__ldcg(dom + o + q));
+        if (sz > 1 && sz < best) {
+            best = sz;
+            bx = v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int ob = __shfl_xor_sync(FULLM, best, o), ox = __shfl_xor_sync(FULLM, bx, o);
+        if (ob < best || (ob == best && ox >= 0 && (bx < 0 || ox < bx))) {
+            best = ob;
+            bx = ox;
+        }
+    }
+    return bx;
+}
+
+__device__ int min_value_dev(const SearchDev& S, const uint32_t* dom, int x) {
+    for (int q = 0; q < S.varNW[x]; ++q) {
+        const uint32_t w = __ldcg(dom + S.varOff[x] + q);
+        if (w) return q * 32 + __ffs(w) - 1;
+    }
+    return 0;
+}
+
+// Level L of slot s holds the current state: domains, each table's trail mark,
+// live count and non-zero index; the tables' calls trail from that mark on.
+__device__ void save_level(const ModelDev& M, const SearchDev& S, int s, int L) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t* dom = M.dom + (size_t)s * S.DWs;
+    uint32_t* ld = S.levelDom + lvl(S, s, L) * S.DWs;
+    for (int q = lane; q < S.DWs; q += 32) ld[q] = __ldcg(dom + q);
+    for (int k = lane; k < S.T; k += 32) {
+        const int j = s * S.T + k;
+        const TableDev& T = M.tabs[j];
+        const int top = __ldcg(&T.ctrl->trail_top);
+        S.markAt[lvl(S, s, L) * S.T + k] = top;
+        S.liveAt[lvl(S, s, L) * S.T + k] = __ldcg(&T.ctrl->live_state);
+        S.calls[j].mark = top;
+        uint32_t* snap = S.snapSeg + lvl(S, s, L) * S.segTotal + S.segOff[k];
+        for (int q = 0; q < T.nseg; ++q) snap[q] = __ldcg(&T.segMask[q]);
+    }
+}
+
+// Queue the restore of every table of slot s to level L; their calls trail
+// from that level's marks again.
+__device__ void queue_restore(const SearchDev& S, int s, int L) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&S.ctr->nrestQ, S.T);
+    base = __shfl_sync(FULLM, base, 0);
+    // (at most one restore per slot and decision phase: the queue holds B * T)
+    for (int k = lane; k < S.T; k += 32) {
+        S.restQ[base + k] = make_int4(s * S.T + k, L, 0, 0);
+        S.calls[s * S.T + k].mark = S.markAt[lvl(S, s, L) * S.T + k];
+    }
+}
+
+// A node is issued (counted) unless the node limit is reached.
+__device__ bool issue_node(const SearchDev& S, int depth) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long o = 0;
+    if (lane == 0) {
+        o = atomicAdd(&S.ctr->nodes, 1ull);
+        if (S.nodeLimit <= 0 || (long long)o < S.nodeLimit) atomicMax(&S.ctr->maxDepth, depth);
+    }
+    o = __shfl_sync(FULLM, o, 0);
+    return S.nodeLimit <= 0 || (long long)o < S.nodeLimit;
+}
+
+// The tables of variable x of slot s go to the next round; a variable in no
+// table still takes one round (table 0 of the slot, which finds nothing to
+// do), so that every issued node is decided after a round and every queued
+// restore is done before the slot saves a level again.
+__device__ void append_var(const SearchDev& S, int s, int x, int32_t* next, int32_t* nnext) {
+    const int t0 = S.varTabStart[x], t1 = S.varTabStart[x + 1];
+    if (t1 > t0) {
+        append_tables(S, s, S.varTabList + t0, t1 - t0, next, nnext);
+    } else {
+        const int32_t zero = 0;
+        append_tables(S, s, &zero, 1, next, nnext);
+    }
+}
+
+// One warp: move slot s on when its node is done. Returns after issuing a
+// node (its tables are in the next round) or with the slot idle; at most one
+// restore of the slot is queued.
+__device__ void decide_slot(const ModelDev& M, const SearchDev& S, int s, int32_t* next, int32_t* nnext) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* dom = M.dom + (size_t)s * S.DWs;
+    for (int guard = 0; guard < 2; ++guard) {
+        if (!S.active[s]) {
+            // an idle slot takes the next open node (its tables back at level 0, the root)
+            if (__ldcg(&S.ctr->error) != CT_OK) return;
+            int o = 0;
+            if (lane == 0) o = atomicAdd(&S.ctr->nextOpen, 1);
+            o = __shfl_sync(FULLM, o, 0);
+            if (o >= S.nopen) return;
+            if (!issue_node(S, S.openDepth[o])) return;
+            queue_restore(S, s, 0);
+            for (int q = lane; q < S.DWs; q += 32) dom[q] = S.openDom[(size_t)o * S.DWs + q];
+            if (lane == 0) {
+                S.active[s] = 1;
+                S.depth[s] = 0;
+                S.openIdx[s] = o;
+                S.depth0[s] = S.openDepth[o];
+                S.busy[s] = 0;
+                M.nodeStatus[s] = CT_OK;
+            }
+            append_tables(S, s, nullptr, S.T, next, nnext);
+            return;
+        }
+        if (__ldcg(&S.busy[s])) {  // its node is still propagating
+            if (lane == 0) S.busy[s] = 0;
+            return;
+        }
+        const bool failed = __ldcg(&M.nodeStatus[s]) != CT_OK;
+        if (lane == 0) M.nodeStatus[s] = CT_OK;
+        int d = S.depth[s];
+        if (!failed) {
+            const int x = warp_first_fail(S, dom);
+            if (x >= 0) {
+                // left branch x = min D(x), after saving level d + 1
+                if (d >= S.maxLevels) {
+                    if (lane == 0) atomicCAS(&S.ctr->error, CT_OK, CT_ERR_LEVEL);
+                    if (lane == 0) S.active[s] = 0;
+                    return;
+                }
+                if (!issue_node(S, S.depth0[s] + d + 1)) {
+                    if (lane == 0) S.active[s] = 0;
+                    return;
+                }
+                const int a = min_value_dev(S, dom, x);
+                save_level(M, S, s, d + 1);
+                __syncwarp();
+                for (int q = lane; q < S.varNW[x]; q += 32) dom[S.varOff[x] + q] = q == (a >> 5) ? 1u << (a & 31) : 0u;
+                if (lane == 0) {
+                    S.frames[(size_t)s * S.maxLevels + d] = make_int4(x, a, 0, 0);
+                    S.depth[s] = d + 1;
+                }
+                append_var(S, s, x, next, nnext);
+                return;
+            }
+            // every variable fixed: a solution. A slot takes open nodes in
+            // increasing (depth-first) order and searches each subtree
+            // depth-first, so its first solution is the first of its subtrees;
+            // it is kept for the host.
+            bool first = false;
+            if (lane == 0) {
+                atomicAdd(&S.ctr->solutions, 1ull);
+                first = S.openIdx[s] < S.firstOpen[s];
+                if (first) S.firstOpen[s] = S.openIdx[s];
+            }
+            first = __shfl_sync(FULLM, first, 0);
+            if (first)
+                for (int q = lane; q < S.DWs; q += 32) S.firstSol[(size_t)s * S.DWs + q] = __ldcg(dom + q);
+        } else if (lane == 0) {
+            atomicAdd(&S.ctr->fails, 1ull);
+        }
+        // backtrack: the deepest frame with an untried right branch
+        while (d > 0 && S.frames[(size_t)s * S.maxLevels + d - 1].z != 0) --d;
+        if (d == 0) {
+            if (lane == 0) {
+                S.depth[s] = 0;
+                S.active[s] = 0;
+            }
+            __syncwarp();
+            continue;  // the subtree is done: take the next open node
+        }
+        const int4 f = S.frames[(size_t)s * S.maxLevels + d - 1];
+        if (!issue_node(S, S.depth0[s] + d)) {
+            if (lane == 0) S.active[s] = 0;
+            return;
+        }
+        queue_restore(S, s, d);
+        const uint32_t* ld = S.levelDom + lvl(S, s, d) * S.DWs;
+        for (int q = lane; q < S.DWs; q += 32) dom[q] = ld[q];
+        __syncwarp();
+        if (lane == 0) {
+            dom[S.varOff[f.x] + (f.y >> 5)] &= ~(1u << (f.y & 31));
+            S.frames[(size_t)s * S.maxLevels + d - 1] = make_int4(f.x, f.y, 1, 0);
+            S.depth[s] = d;
+        }
+        append_var(S, s, f.x, next, nnext);
+        return;
+    }
+}
+
+// One warp per queued restore: table j back to level L of its slot.
+__device__ void restore_table(const ModelDev& M, const SearchDev& S, int j, int L) {
+    const int lane = threadIdx.x & 31;
+    const int s = j / S.T, k = j - s * S.T;
+    const TableDev& T = M.tabs[j];
+    // (the decision phase ran on other CTAs: its records are read through L2)
+    const int mark = __ldcg(&S.markAt[lvl(S, s, L) * S.T + k]);
+    const int top = __ldcg(&T.ctrl->trail_top);
+    for (int p = mark + lane; p < top; p += 32) {
+        const int2 key = __ldcg(&T.trailKey[p]);
+        if (key.y < mark) {
+            T.curr[key.x] = __ldcg(&T.trailOld[p]);
+            T.lastpos[key.x] = key.y;
+        }
+    }
+    const uint32_t* snap = S.snapSeg + lvl(S, s, L) * S.segTotal + S.segOff[k];
+    for (int q = lane; q < T.nseg; q += 32) T.segMask[q] = __ldcg(snap + q);
+    // last-seen domains: the level's domains of the table's scope
+    const uint32_t* ld = S.levelDom + lvl(S, s, L) * S.DWs;
+    const int b0 = M.scopeBase[j];
+    for (int i = lane; i < T.arity; i += 32) {
+        const VarLayout V(T, nullptr, M.scopeOff + b0);
+        const int o = V.off(i) - s * S.DWs;
+        for (int q = 0; q < V.nw(i); ++q) T.lastDom[V.ld(i) + q] = __ldcg(ld + o + q);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        T.ctrl->trail_top = mark;
+        T.ctrl->live_state = __ldcg(&S.liveAt[lvl(S, s, L) * S.T + k]);
+        T.ctrl->status = CT_OK;
+    }
+}
+
+template <int U, bool kSearch>
 __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_constant__ ModelDev M) {
     __shared__ Smem sm;
     ModelCtrl* C = M.ctrl;
@@ -164,9 +426,41 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         }
         if (!sync()) return;
     }
-    int cur = 0, round = 0;
+    int cur = 0, round = 0, launchRounds = 0;
+    // search mode: the search state, and its step between two rounds (the
+    // decisions, a barrier, the queued restores, a barrier)
+    SearchDev Sd{};
+    if (kSearch) Sd = *M.search;
+    auto search_step = [&]() -> bool {
+        int32_t* nl = M.work + (size_t)cur * M.ntables;
+        int32_t* nc = &C->nnext[round & 1];
+        for (int s = gwarp; s < Sd.B; s += nwarps) decide_slot(M, Sd, s, nl, nc);
+        if (!sync()) return false;
+        const int nr = __ldcg(&Sd.ctr->nrestQ);
+        for (int q = gwarp; q < nr; q += nwarps) {
+            const int4 e = __ldcg(&Sd.restQ[q]);
+            restore_table(M, Sd, e.x, e.y);
+        }
+        if (!sync()) return false;
+        if (blockIdx.x == 0 && tid == 0) Sd.ctr->nrestQ = 0;  // read by no CTA before the next decisions
+        return true;
+    };
+    if (kSearch) {
+        cur = __ldcg(&Sd.ctr->cur);
+        round = __ldcg(&Sd.ctr->round);
+        if (!__ldcg(&Sd.ctr->started)) {
+            if (!search_step()) return;
+            if (blockIdx.x == 0 && tid == 0) Sd.ctr->started = 1;
+        }
+    }
     for (;;) {
-        const int nwork = round > 0 ? __ldcg(&C->nnext[round & 1]) : M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
+        const int nwork = kSearch ? __ldcg(&C->nnext[round & 1])
+                                  : round > 0 ? __ldcg(&C->nnext[round & 1]) : M.nworkIn ? __ldcg(M.nworkIn) : __ldcg(&C->nwork);
+        if (kSearch && nwork == 0) {
+            // every slot idle, no open node left (or the node limit reached)
+            if (blockIdx.x == 0 && tid == 0) Sd.ctr->done = 1;
+            break;
+        }
         phase(round == 0 ? 0 : 6);
         const int32_t* work = M.work + (size_t)cur * M.ntables;
         int32_t* pruned = M.prunedBy + (size_t)(round & 1) * M.nvars;       // written by this round
@@ -188,7 +482,10 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             // as it is now: one snapshot, in the lowest one's slot, taken before
             // this launch first changes the table (a table this launch does not
             // propagate keeps them pending).
-            const ModelTabCall cl = M.calls[t];
+            ModelTabCall cl;
+            cl.mark = __ldcg(&M.calls[t].mark);
+            cl.snapFrom = __ldcg(&M.calls[t].snapFrom);
+            cl.snapTo = __ldcg(&M.calls[t].snapTo);
             if (cl.snapFrom < cl.snapTo && __ldcg(&M.snapTaken[t]) == 0) {
                 const size_t l = (size_t)cl.snapFrom;
                 for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[l * T.nseg + q] = __ldcg(&T.segMask[q]);
@@ -235,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
             const int nrows = __ldcg(&T.ctrl->nrows);
             if (nrows == 0) continue;
             const int seg = u - pre_at(pU, k, gpre);
-            const int mark = M.calls[t].mark;
+            const int mark = __ldcg(&M.calls[t].mark);
             const SegState S = load_segment(T, seg, mark);
             TrailItem it;
             update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
@@ -408,6 +705,7 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
                     base = __shfl_sync(0xffffffffu, base, 0);
                     if (dirty) next[base + __popc(bal & lanemask_lt())] = t;
                 }
+                if (kSearch && dirty) Sd.busy[t / M.nodeTables] = 1;  // its node goes on next round
             }
             for (int v = gtid; v < M.nvars; v += gth) prunedNext[v] = -1;
             if (blockIdx.x == 0 && tid == 0) {
@@ -418,6 +716,18 @@ __global__ void __launch_bounds__(kThreads, 2) ct_model_kernel(const __grid_cons
         cur ^= 1;
         ++round;
         if (!sync()) return;
+        if (kSearch) {
+            if (!search_step()) return;
+            if (++launchRounds >= Sd.roundBudget) {
+                // the launch's share of rounds is spent: the host launches again
+                if (blockIdx.x == 0 && tid == 0) {
+                    Sd.ctr->cur = cur;
+                    Sd.ctr->round = round;
+                }
+                break;
+            }
+            continue;
+        }
         if (__ldcg(&C->nnext[round & 1]) == 0) break;
         if (round >= M.maxRounds) {
             if (blockIdx.x == 0 && tid == 0) atomicCAS(&C->status, CT_OK, CT_ERR_TIMEOUT);
@@ -554,7 +864,7 @@ __global__ void ct_clone_state_kernel(const TableDev* __restrict__ src, const Ta
 int max_coresident_model_blocks() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_model_kernel<16>, kThreads, 0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ct_model_kernel<16, true>, kThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -564,7 +874,54 @@ int max_coresident_model_blocks() {
 cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s) {
     ModelDev m = M;
     void* args[] = {&m};
-    return cudaLaunchCooperativeKernel((const void*)ct_model_kernel<16>, dim3(grid), dim3(kThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)ct_model_kernel<16, false>, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+cudaError_t launch_model_search(const ModelDev& M, int grid, cudaStream_t s) {
+    ModelDev m = M;
+    void* args[] = {&m};
+    return cudaLaunchCooperativeKernel((const void*)ct_model_kernel<16, true>, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+// Level 0 of every slot (one CTA per slot): the root domains, and for every
+// table an empty trail of trailFactor * W4 + 1024 entries in its own control
+// block (the live count taken from the state copy's), mark 0 and the
+// non-zero index as the state copy left it.
+__global__ void ct_search_init_kernel(const __grid_constant__ ModelDev M, const TableDev* __restrict__ hostTabs,
+                                      const SearchDev* __restrict__ Sp, const uint32_t* __restrict__ rootDom,
+                                      int trailFactor) {
+    const SearchDev& S = *Sp;
+    const int s = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < S.DWs; q += blockDim.x) S.levelDom[lvl(S, s, 0) * S.DWs + q] = rootDom[q];
+    for (int k = tid; k < S.T; k += blockDim.x) {
+        const int j = s * S.T + k;
+        const TableDev& T = M.tabs[j];
+        const int live = hostTabs[j].ctrl->live_state;
+        int32_t* c = reinterpret_cast<int32_t*>(T.ctrl);
+        for (int q = 0; q < (int)(sizeof(Ctrl) / sizeof(int32_t)); ++q) c[q] = 0;
+        T.ctrl->cur_mark = -1;
+        T.ctrl->trail_cap = trailFactor * T.W4 + 1024;
+        T.ctrl->live_state = live;
+        S.markAt[lvl(S, s, 0) * S.T + k] = 0;
+        S.liveAt[lvl(S, s, 0) * S.T + k] = live;
+        S.calls[j] = ModelTabCall{0, 0, 0, 0};
+        uint32_t* snap = S.snapSeg + lvl(S, s, 0) * S.segTotal + S.segOff[k];
+        for (int q = 0; q < T.nseg; ++q) snap[q] = T.segMask[q];
+    }
+    if (tid == 0) {
+        S.depth[s] = 0;
+        S.active[s] = 0;
+        S.busy[s] = 0;
+        S.firstOpen[s] = 0x7fffffff;
+        M.nodeStatus[s] = CT_OK;
+    }
+}
+
+cudaError_t launch_search_init(const ModelDev& M, const TableDev* hostTabs, const SearchDev& S,
+                               const uint32_t* rootDom, int trailFactor, cudaStream_t s) {
+    ct_search_init_kernel<<<S.B, 128, 0, s>>>(M, hostTabs, M.search, rootDom, trailFactor);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_restore_batch(const TableDev* tabs, const RestoreBatch& B, cudaStream_t s) {

@@ -112,6 +112,7 @@ struct ct_batch {
     int grid = 1;
     std::vector<void*> allocs;
     bool broken = false;
+    struct DevSearch* dsearch = nullptr;  // buffers of the search run on the device (built on first use)
 
     int32_t* nworkHost() { return reinterpret_cast<int32_t*>(h_stage); }
     ModelTabCall* callsHost() { return reinterpret_cast<ModelTabCall*>(h_stage + offCalls); }
@@ -120,9 +121,34 @@ struct ct_batch {
     RestoreDesc* restHost() { return reinterpret_cast<RestoreDesc*>(h_stage + offRest); }
 };
 
+// The search run on the device (ct_search_batch_device): per-slot stacks,
+// level records and the open-node queue; the clones' descriptors with their
+// own trails (larger than the host-stepped search's, which grows them on the
+// host) and control blocks, sharing every other buffer with the clones.
+struct DevSearch {
+    int B = 0, maxLevels = 0, nopenCap = 0, trailFactor = 0;
+    SearchDev hs{};              // device pointers, host copy
+    SearchDev* d_sd = nullptr;   // device copy
+    TableDev* d_tabs = nullptr;  // [n]
+    Ctrl* d_ctrl = nullptr;      // [n]
+    uint32_t* d_openDom = nullptr;
+    int32_t* d_openDepth = nullptr;
+    uint32_t* d_root = nullptr;  // [DWs] root domains
+    std::vector<void*> allocs;
+};
+
+void dsearch_free(DevSearch* d) {
+    if (!d) return;
+    for (void* p : d->allocs) cudaFree(p);
+    if (d->d_openDom) cudaFree(d->d_openDom);
+    if (d->d_openDepth) cudaFree(d->d_openDepth);
+    delete d;
+}
+
 void ct_batch_free(ct_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    dsearch_free(b->dsearch);
     for (ct_table* t : b->tabs) ct_table_free(t);
     for (void* p : b->allocs) cudaFree(p);
     if (b->h_stage) cudaFreeHost(b->h_stage);
@@ -315,6 +341,97 @@ int sync_copies(ct_model* m, ct_batch* b) {
     CT_CUDA(launch_clone_state(b->d_src, b->d_tabs, b->T, b->n, b->stream));
     CT_CUDA(cudaStreamSynchronize(b->stream));
     for (int j = 0; j < b->n; ++j) ct_table_adopt_state(b->tabs[j], m->tables[j % b->T]);
+    return CT_OK;
+}
+
+template <typename T>
+int d_alloc(DevSearch* d, T** p, size_t n) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ct_set_error("device search: cudaMalloc of %zu bytes: %s", std::max<size_t>(n, 1) * sizeof(T),
+                     cudaGetErrorString(e));
+        return CT_ERR_OOM;
+    }
+    d->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CT_OK;
+}
+
+// First capacities of the device search, doubled (up to the maxima) and the
+// search run again when a subtree needs more.
+constexpr int kDevLevels = 64, kDevLevelsMax = 1024;        // levels below an open node
+constexpr int kDevTrailFactor = 16, kDevTrailFactorMax = 128;  // trail entries per table: factor x chunks + 1024
+constexpr int kDevRoundBudget = 1024;  // rounds per launch
+
+// The device search's buffers for the B slots of b (kept with b).
+int build_dsearch(ct_model* m, ct_batch* b, int levels, int trailFactor, DevSearch** out) {
+    DevSearch* d = new (std::nothrow) DevSearch();
+    if (!d) return CT_ERR_OOM;
+    *out = d;
+    const int B = b->B, T = b->T, n = b->n, DWs = m->DWg, nv = m->nvars, L = levels;
+    d->B = B;
+    d->maxLevels = L;
+    d->trailFactor = trailFactor;
+    std::vector<int32_t> segOff(T + 1, 0), varTabStart(nv + 1, 0), varTabList;
+    for (int k = 0; k < T; ++k) segOff[k + 1] = segOff[k] + ct_table_dev(m->tables[k]).nseg;
+    for (int v = 0; v < nv; ++v) {
+        for (int k : m->varTables[v]) varTabList.push_back(k);
+        varTabStart[v + 1] = (int32_t)varTabList.size();
+    }
+    SearchDev& S = d->hs;
+    S.B = B;
+    S.T = T;
+    S.nv = nv;
+    S.DWs = DWs;
+    S.maxLevels = L;
+    S.segTotal = segOff[T];
+    S.roundBudget = kDevRoundBudget;
+    const size_t lv = (size_t)B * (L + 1);
+    int st = CT_OK;
+    int32_t *vOff, *vNW, *vTS, *vTL, *sOff;
+    if ((st = d_alloc(d, &S.ctr, 1)) || (st = d_alloc(d, &S.depth, B)) || (st = d_alloc(d, &S.active, B)) ||
+        (st = d_alloc(d, &S.busy, B)) || (st = d_alloc(d, &S.openIdx, B)) || (st = d_alloc(d, &S.depth0, B)) ||
+        (st = d_alloc(d, &S.frames, (size_t)B * L)) || (st = d_alloc(d, &S.levelDom, lv * DWs)) ||
+        (st = d_alloc(d, &S.markAt, lv * T)) || (st = d_alloc(d, &S.liveAt, lv * T)) ||
+        (st = d_alloc(d, &S.snapSeg, lv * S.segTotal)) || (st = d_alloc(d, &S.firstOpen, B)) ||
+        (st = d_alloc(d, &S.firstSol, (size_t)B * DWs)) || (st = d_alloc(d, &S.restQ, (size_t)n)) ||
+        (st = d_alloc(d, &vOff, nv)) || (st = d_alloc(d, &vNW, nv)) || (st = d_alloc(d, &vTS, nv + 1)) ||
+        (st = d_alloc(d, &vTL, varTabList.size())) || (st = d_alloc(d, &sOff, T + 1)) ||
+        (st = d_alloc(d, &d->d_sd, 1)) || (st = d_alloc(d, &d->d_tabs, n)) || (st = d_alloc(d, &d->d_ctrl, n)) ||
+        (st = d_alloc(d, &d->d_root, DWs)))
+        return st;
+    S.calls = reinterpret_cast<ModelTabCall*>(b->d_stage + b->offCalls);
+    S.varOff = vOff;
+    S.varNW = vNW;
+    S.varTabStart = vTS;
+    S.varTabList = vTL;
+    S.segOff = sOff;
+    cudaStream_t str = b->stream;
+    CT_CUDA(cudaMemcpyAsync(vOff, m->off.data(), nv * 4, cudaMemcpyHostToDevice, str));
+    CT_CUDA(cudaMemcpyAsync(vNW, m->nw.data(), nv * 4, cudaMemcpyHostToDevice, str));
+    CT_CUDA(cudaMemcpyAsync(vTS, varTabStart.data(), (nv + 1) * 4, cudaMemcpyHostToDevice, str));
+    if (!varTabList.empty())
+        CT_CUDA(cudaMemcpyAsync(vTL, varTabList.data(), varTabList.size() * 4, cudaMemcpyHostToDevice, str));
+    CT_CUDA(cudaMemcpyAsync(sOff, segOff.data(), (T + 1) * 4, cudaMemcpyHostToDevice, str));
+    // the clones' descriptors with their own trails and control blocks
+    std::vector<TableDev> td(n);
+    size_t entries = 0;
+    for (int j = 0; j < n; ++j) entries += (size_t)trailFactor * ct_table_dev(b->tabs[j]).W4 + 1024;
+    int2* keys = nullptr;
+    uint4* olds = nullptr;
+    if ((st = d_alloc(d, &keys, entries)) || (st = d_alloc(d, &olds, entries))) return st;
+    size_t at = 0;
+    for (int j = 0; j < n; ++j) {
+        td[j] = ct_table_dev(b->tabs[j]);
+        td[j].trailKey = keys + at;
+        td[j].trailOld = olds + at;
+        td[j].ctrl = d->d_ctrl + j;
+        at += (size_t)trailFactor * td[j].W4 + 1024;
+    }
+    CT_CUDA(cudaMemcpyAsync(d->d_tabs, td.data(), n * sizeof(TableDev), cudaMemcpyHostToDevice, str));
+    CT_CUDA(cudaStreamSynchronize(str));  // the host vectors above go out of scope
     return CT_OK;
 }
 
@@ -880,6 +997,188 @@ struct Search {
         return CT_OK;
     }
 
+    // ---- the slots' search on the device (count_all, first-fail) ----
+    // The open nodes go to a device queue; the fixpoint kernel in search mode
+    // decides for every slot between its rounds, launched again until the
+    // search is done (each launch is bounded to kDevRoundBudget rounds).
+    int run_device() {
+        int rc;
+        int L1 = 0;
+        if ((rc = ct_model_save(m, &L1)) != CT_OK) return rc;
+        rc = ct_model_propagate(m);  // the root fixpoint, for the state copies
+        int levels = b && b->dsearch ? b->dsearch->maxLevels : kDevLevels;
+        int factor = b && b->dsearch ? b->dsearch->trailFactor : kDevTrailFactor;
+        for (;;) {
+            if (rc == CT_OK) rc = ensure_copies();
+            if (rc == CT_OK && b->dsearch && (b->dsearch->maxLevels < levels || b->dsearch->trailFactor < factor)) {
+                dsearch_free(b->dsearch);
+                b->dsearch = nullptr;
+            }
+            if (rc == CT_OK) rc = run_device_inner(levels, factor);
+            // a subtree deeper, or a trail fuller, than the capacities: larger
+            // ones, from the start again (the counts are the same)
+            if (rc == CT_ERR_LEVEL && levels < kDevLevelsMax) {
+                levels *= 2;
+            } else if (rc == CT_ERR_OOM && devTrailFull && factor < kDevTrailFactorMax) {
+                factor *= 2;
+            } else {
+                break;
+            }
+            b->broken = false;
+            devRetries += 1;
+            rc = CT_OK;
+        }
+        const int rr = ct_model_restore(m, L1);
+        return rc != CT_OK ? rc : rr;
+    }
+
+    bool devTrailFull = false;
+    int devRetries = 0;
+
+    int run_device_inner(int levels, int factor) {
+        int rc;
+        devTrailFull = false;
+        if (!b->dsearch) {
+            DevSearch* nd = nullptr;
+            rc = build_dsearch(m, b, levels, factor, &nd);
+            if (rc != CT_OK) {
+                dsearch_free(nd);
+                return rc;
+            }
+            b->dsearch = nd;
+        }
+        DevSearch* d = b->dsearch;
+        SearchDev S = d->hs;
+        const int nopen = (int)open.size();
+        const int DWs = m->DWg;
+        if (nopen > d->nopenCap) {
+            if (d->d_openDom) cudaFree(d->d_openDom);
+            if (d->d_openDepth) cudaFree(d->d_openDepth);
+            d->d_openDom = nullptr;
+            d->d_openDepth = nullptr;
+            d->nopenCap = 0;
+            if (cudaMalloc(&d->d_openDom, (size_t)nopen * DWs * 4) != cudaSuccess ||
+                cudaMalloc(&d->d_openDepth, (size_t)nopen * 4) != cudaSuccess) {
+                cudaGetLastError();
+                ct_set_error("device search: open-node queue of %d nodes", nopen);
+                return CT_ERR_OOM;
+            }
+            d->nopenCap = nopen;
+        }
+        std::vector<uint32_t> od((size_t)nopen * DWs);
+        std::vector<int32_t> odep(nopen);
+        for (int o = 0; o < nopen; ++o) {
+            std::memcpy(od.data() + (size_t)o * DWs, open[o].dom.data(), (size_t)DWs * 4);
+            odep[o] = open[o].depth;
+        }
+        cudaStream_t str = b->stream;
+        CT_CUDA(cudaMemcpyAsync(d->d_openDom, od.data(), od.size() * 4, cudaMemcpyHostToDevice, str));
+        CT_CUDA(cudaMemcpyAsync(d->d_openDepth, odep.data(), odep.size() * 4, cudaMemcpyHostToDevice, str));
+        CT_CUDA(cudaMemcpyAsync(d->d_root, rootDom.data(), (size_t)DWs * 4, cudaMemcpyHostToDevice, str));
+        S.openDom = d->d_openDom;
+        S.openDepth = d->d_openDepth;
+        S.nopen = nopen;
+        const int64_t remaining = limit > 0 ? std::max<int64_t>(limit - st.nodes, 0) : 0;
+        S.nodeLimit = limit > 0 ? std::max<int64_t>(remaining, 0) : 0;
+        if (limit > 0 && remaining == 0) {
+            hitLimit = true;
+            return CT_OK;
+        }
+        CT_CUDA(cudaMemcpyAsync(d->d_sd, &S, sizeof(S), cudaMemcpyHostToDevice, str));
+        CT_CUDA(cudaMemsetAsync(S.ctr, 0, sizeof(SearchCtr), str));
+        ModelDev md = b->md;
+        CT_CUDA(cudaMemsetAsync(md.ctrl, 0, sizeof(ModelCtrl), str));
+        md.tabs = d->d_tabs;
+        md.search = d->d_sd;
+        md.nrestores = 0;
+        md.nworkIn = nullptr;
+        CT_CUDA(launch_search_init(md, b->d_tabs, S, d->d_root, d->trailFactor, str));
+        SearchCtr c{};
+        unsigned long long lastNodes = ~0ull;
+        int idleLaunches = 0;
+        volatile int32_t* H = b->h_status;
+        for (;;) {
+            H[0] = kNoChunk;
+            const auto w0 = std::chrono::steady_clock::now();
+            CT_CUDA(launch_model_search(md, b->grid, str));
+            bool seen = false;
+            for (uint64_t it = 0;; ++it) {
+                if (H[0] != kNoChunk) {
+                    seen = true;
+                    break;
+                }
+                if ((it & 1023u) == 1023u) {
+                    if (cudaStreamQuery(str) == cudaSuccess) {
+                        seen = H[0] != kNoChunk;
+                        break;
+                    }
+                    if (std::chrono::steady_clock::now() - w0 > std::chrono::milliseconds(kHostWaitMs)) break;
+                }
+            }
+            if (!seen) CT_CUDA(cudaStreamSynchronize(str));
+            info.wait_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
+            info.steps += 1;
+            const int status = H[0];
+            if (status != CT_OK) {
+                b->broken = true;
+                if (status == kNoChunk) {
+                    ct_set_error("device search: the fixpoint kernel did not publish (a device-side wait ran out)");
+                    return CT_ERR_TIMEOUT;
+                }
+                ct_set_error("device search: fixpoint kernel status %d (a trail overflow is CT_ERR_OOM)", status);
+                devTrailFull = status == CT_ERR_OOM;
+                return status < 0 ? status : CT_ERR_STATE;
+            }
+            st.propagations += H[2];
+            info.rounds += H[1];
+            CT_CUDA(cudaMemcpyAsync(&c, S.ctr, sizeof(c), cudaMemcpyDeviceToHost, str));
+            CT_CUDA(cudaStreamSynchronize(str));
+            if (c.done || c.error != CT_OK) break;
+            // every launch issues nodes unless the search is stuck
+            idleLaunches = c.nodes == lastNodes ? idleLaunches + 1 : 0;
+            lastNodes = c.nodes;
+            if (idleLaunches >= 2) {
+                b->broken = true;
+                ct_set_error("device search: no node issued in two launches");
+                return CT_ERR_STATE;
+            }
+        }
+        if (c.error != CT_OK) {
+            ct_set_error("device search: %s", c.error == CT_ERR_LEVEL ? "a subtree is deeper than the device levels"
+                                                                     : "stopped");
+            return c.error;
+        }
+        const int64_t issued = S.nodeLimit > 0 ? std::min<int64_t>((int64_t)c.nodes, S.nodeLimit) : (int64_t)c.nodes;
+        if (S.nodeLimit > 0 && (int64_t)c.nodes >= S.nodeLimit) hitLimit = true;
+        st.nodes += issued;
+        st.fails += (int64_t)c.fails;
+        st.solutions += (int64_t)c.solutions;
+        st.max_depth = std::max(st.max_depth, c.maxDepth);
+        info.slot_nodes += issued;
+        info.open_nodes += std::min(c.nextOpen, nopen);
+        if (c.solutions > 0) {
+            // the first solution in depth-first order: the slots' first
+            // solutions in their lowest open node, against the split's
+            std::vector<int32_t> fo(B);
+            CT_CUDA(cudaMemcpyAsync(fo.data(), S.firstOpen, (size_t)B * 4, cudaMemcpyDeviceToHost, str));
+            CT_CUDA(cudaStreamSynchronize(str));
+            int bs = -1;
+            for (int q = 0; q < B; ++q)
+                if (fo[q] < nopen && (bs < 0 || fo[q] < fo[bs])) bs = q;
+            if (bs >= 0 && (!haveBest || after(bestPath, open[fo[bs]].path))) {
+                std::vector<uint32_t> sol(DWs);
+                CT_CUDA(cudaMemcpyAsync(sol.data(), S.firstSol + (size_t)bs * DWs, (size_t)DWs * 4,
+                                        cudaMemcpyDeviceToHost, str));
+                CT_CUDA(cudaStreamSynchronize(str));
+                haveBest = true;
+                bestPath = open[fo[bs]].path;
+                bestVals.resize(m->nvars);
+                for (int v = 0; v < m->nvars; ++v) bestVals[v] = m->lo[v] + min_value(m, sol.data(), v);
+            }
+        }
+        return CT_OK;
+    }
+
     int run_slots() {
         // a named range for profilers (no cost without one attached)
         nvtxRangePushA("ct_search_batch_slots");
@@ -937,8 +1236,17 @@ struct Search {
 
 namespace {
 int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int64_t node_limit, int count_all,
-                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info);
+                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info, bool on_device = false);
 }  // namespace
+
+extern "C" int ct_search_batch_device(ct_model* m, int slots, int split_depth, int64_t node_limit,
+                                      ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
+    if (m && m->policy) {
+        ct_set_error("ct_search_batch_device: branches first-fail only (the model has a policy set)");
+        return CT_ERR_ARG;
+    }
+    return search_batch(m, slots, split_depth, false, node_limit, 1, out, first_solution, info, true);
+}
 
 extern "C" int ct_search_batch(ct_model* m, int slots, int split_depth, int64_t node_limit, int count_all,
                                ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
@@ -956,7 +1264,7 @@ extern "C" int ct_search_batch_assign(ct_model* m, int slots, int assign_depth, 
 
 namespace {
 int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int64_t node_limit, int count_all,
-                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info) {
+                 ct_search_stats* out, int32_t* first_solution, ct_batch_info* info, bool on_device) {
     if (!m || !out) {
         ct_set_error("ct_search_batch: null argument");
         return CT_ERR_ARG;
@@ -1015,7 +1323,7 @@ int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int
     if (rc == CT_OK) rc = rr;
     const bool runSlots = !S.open.empty() && !S.stopIssue && !(S.anyStop && S.haveBest);
     if (rc == CT_OK && runSlots && S.usePolicy) rc = ensure_slot_features(m, S.b);
-    if (rc == CT_OK && runSlots) rc = S.run_slots();
+    if (rc == CT_OK && runSlots) rc = on_device ? S.run_device() : S.run_slots();
     if (rc != CT_OK) {
         if (S.b) S.b->broken = true;
         return rc;

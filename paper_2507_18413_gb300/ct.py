@@ -144,6 +144,8 @@ _SIGS = {
                                        ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_search_batch_assign": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                               ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
+    "ct_search_batch_device": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                              ctypes.POINTER(ct_search_stats), _I32P, ctypes.POINTER(ct_batch_info)]),
     "ct_model_destroy": (ctypes.c_int, [_P]),
     "ct_create_negative": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.POINTER(ct_options),
                                           _P, ctypes.POINTER(_P)]),
@@ -515,6 +517,19 @@ def ct_search_dfs(m, nvars, node_limit=0, count_all=True):
     d = _as_dict(s)
     d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
     return st, d
+
+
+def ct_search_batch_device(m, nvars, slots, split_depth, node_limit=0):
+    """The batched search with the slots' search run on the device (count all
+    solutions, first-fail): returns (status, stats dict with first_solution, batch info dict)."""
+    s = ct_search_stats()
+    info = ct_batch_info()
+    sol = np.zeros(nvars, dtype=np.int32)
+    st = load().ct_search_batch_device(m, int(slots), int(split_depth), int(node_limit), ctypes.byref(s),
+                                       sol.ctypes.data_as(_I32P), ctypes.byref(info))
+    d = _as_dict(s)
+    d["first_solution"] = sol.tolist() if d["solutions"] > 0 else None
+    return st, d, _as_dict(info)
 
 
 def ct_search_batch(m, nvars, slots, split_depth, node_limit=0, count_all=True, split_assignments=False):

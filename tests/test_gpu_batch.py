@@ -278,3 +278,70 @@ def test_batch_assignment_split_bad_arguments():
         st, _, _ = C.ct_search_batch(h, csp.nvars, 4, depth, 0, mode, split_assignments=True)
         assert st == C.CT_ERR_ARG
     C.ct_model_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# the slots' search run on the device (ct_search_batch_device)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("slots,split", [(1, 0), (4, 2), (16, 3), (7, 5), (64, 1)])
+@pytest.mark.parametrize("seed", range(5))
+def test_device_search_counts_equal_the_oracle_search(seed, slots, split):
+    csp, raw = _random(300 + seed, nvars=7, ntables=5, arity=3, d=5, t=30 + 5 * seed)
+    want = O.dfs(csp, count_all=True)
+    h = _model(csp, raw)
+    before = _domains(h, csp)
+    st, got, info = C.ct_search_batch_device(h, csp.nvars, slots, split)
+    assert st == C.CT_OK, C.last_error()
+    _assert_counts(got, want)
+    assert info["split_nodes"] + info["slot_nodes"] == got["nodes"]
+    assert np.array_equal(_domains(h, csp), before), "the model's domains changed"
+    # the model and the host-stepped search are intact afterwards
+    got2, _ = _batch(h, csp, slots, split)
+    _assert_counts(got2, want)
+    st, got3, _ = C.ct_search_batch_device(h, csp.nvars, slots, split)
+    assert st == C.CT_OK
+    _assert_counts(got3, want)
+    C.ct_model_destroy(h)
+
+
+def test_device_search_tiny_config_and_unconstrained_variable():
+    """The config-1 CSP (200 solutions), and a network with a variable that no
+    table holds (its branches propagate nothing)."""
+    dom_lo, dom_size, tup = G.tiny_table(seed=1)
+    csp = O.Csp(dom_lo, dom_size)
+    csp.add_table([0, 1, 2], tup)
+    want = O.dfs(csp)
+    h = _model(csp, [([0, 1, 2], tup)])
+    for slots, split in [(8, 2), (32, 4), (128, 0)]:
+        st, got, _ = C.ct_search_batch_device(h, csp.nvars, slots, split)
+        assert st == C.CT_OK, C.last_error()
+        _assert_counts(got, want)
+        assert got["solutions"] == 200
+    C.ct_model_destroy(h)
+    csp2, raw2 = _random(321, nvars=6, ntables=3, arity=2, d=4, t=10)
+    free = O.Csp([0] * 7, [4] * 7)  # variable 6 in no table
+    for scope, tup in raw2:
+        free.add_table(scope, tup)
+    want2 = O.dfs(free)
+    h2 = _model(free, raw2)
+    st, got, _ = C.ct_search_batch_device(h2, free.nvars, 8, 2)
+    assert st == C.CT_OK, C.last_error()
+    _assert_counts(got, want2)
+    C.ct_model_destroy(h2)
+
+
+def test_device_search_node_limit_and_bad_arguments():
+    csp, raw = _random(303, nvars=7, ntables=5, arity=3, d=5, t=45)
+    full = O.dfs(csp)
+    h = _model(csp, raw)
+    for slots, split, limit in [(4, 2, 25), (8, 0, 40), (2, 6, 10), (16, 3, 500)]:
+        st, got, _ = C.ct_search_batch_device(h, csp.nvars, slots, split, limit)
+        assert st == C.CT_OK, C.last_error()
+        assert got["nodes"] == min(limit, full.nodes)
+        assert got["fails"] + got["solutions"] <= got["nodes"]
+    st, got, _ = C.ct_search_batch_device(h, csp.nvars, 4, 2, full.nodes + 5)
+    _assert_counts(got, full)
+    st, _, _ = C.ct_search_batch_device(h, csp.nvars, 0, 2)
+    assert st == C.CT_ERR_ARG
+    C.ct_model_destroy(h)
