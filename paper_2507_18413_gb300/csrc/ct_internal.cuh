@@ -235,6 +235,8 @@ struct SearchDev {
     const int32_t* varTabStart;   // [nv + 1] tables of each variable (model table indices)
     const int32_t* varTabList;
     const int32_t* segOff;        // [T] first word of each table's index mask in a level's snapshot
+    const int32_t* segTabOf;      // [segTotal] the model table of each word of a level's snapshot
+    uint32_t* const* segPtr;      // [B * T] the index masks of every table copy
     // open nodes
     const uint32_t* openDom;      // [nopen][DWs]
     const int32_t* openDepth;     // [nopen]

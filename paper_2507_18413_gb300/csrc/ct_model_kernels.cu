@@ -188,13 +188,29 @@ __device__ void save_level(const ModelDev& M, const SearchDev& S, int s, int L) 
     for (int q = lane; q < S.DWs; q += 32) ld[q] = __ldcg(dom + q);
     for (int k = lane; k < S.T; k += 32) {
         const int j = s * S.T + k;
-        const TableDev& T = M.tabs[j];
-        const int top = __ldcg(&T.ctrl->trail_top);
+        const Ctrl* c = M.tabs[j].ctrl;
+        const int top = __ldcg(&c->trail_top);
         S.markAt[lvl(S, s, L) * S.T + k] = top;
-        S.liveAt[lvl(S, s, L) * S.T + k] = __ldcg(&T.ctrl->live_state);
+        S.liveAt[lvl(S, s, L) * S.T + k] = __ldcg(&c->live_state);
         S.calls[j].mark = top;
-        uint32_t* snap = S.snapSeg + lvl(S, s, L) * S.segTotal + S.segOff[k];
-        for (int q = 0; q < T.nseg; ++q) snap[q] = __ldcg(&T.segMask[q]);
+    }
+    // the index masks of all the slot's tables, word by word over the lanes,
+    // four loads in flight per lane
+    uint32_t* snap = S.snapSeg + lvl(S, s, L) * S.segTotal;
+    for (int i0 = lane; i0 < S.segTotal; i0 += 128) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 32 * u;
+            v[u] = 0u;
+            if (i < S.segTotal) {
+                const int k = __ldg(&S.segTabOf[i]);
+                v[u] = __ldcg(S.segPtr[s * S.T + k] + (i - __ldg(&S.segOff[k])));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + 32 * u < S.segTotal) snap[i0 + 32 * u] = v[u];
     }
 }
 
@@ -350,11 +366,23 @@ __device__ void restore_table(const ModelDev& M, const SearchDev& S, int j, int 
     // (the decision phase ran on other CTAs: its records are read through L2)
     const int mark = __ldcg(&S.markAt[lvl(S, s, L) * S.T + k]);
     const int top = __ldcg(&T.ctrl->trail_top);
-    for (int p = mark + lane; p < top; p += 32) {
-        const int2 key = __ldcg(&T.trailKey[p]);
-        if (key.y < mark) {
-            T.curr[key.x] = __ldcg(&T.trailOld[p]);
-            T.lastpos[key.x] = key.y;
+    for (int p0 = mark + lane; p0 < top; p0 += 128) {  // four entries in flight per lane
+        int2 key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + 32 * u;
+            key[u] = p < top ? __ldcg(&T.trailKey[p]) : make_int2(-1, 0x7fffffff);
+        }
+        uint4 old[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (key[u].y < mark) old[u] = __ldcg(&T.trailOld[p0 + 32 * u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (key[u].y < mark) {
+                T.curr[key[u].x] = old[u];
+                T.lastpos[key[u].x] = key[u].y;
+            }
         }
     }
     const uint32_t* snap = S.snapSeg + lvl(S, s, L) * S.segTotal + S.segOff[k];

@@ -390,7 +390,8 @@ int build_dsearch(ct_model* m, ct_batch* b, int levels, int trailFactor, DevSear
     S.roundBudget = kDevRoundBudget;
     const size_t lv = (size_t)B * (L + 1);
     int st = CT_OK;
-    int32_t *vOff, *vNW, *vTS, *vTL, *sOff;
+    int32_t *vOff, *vNW, *vTS, *vTL, *sOff, *sTab;
+    uint32_t** sPtr;
     if ((st = d_alloc(d, &S.ctr, 1)) || (st = d_alloc(d, &S.depth, B)) || (st = d_alloc(d, &S.active, B)) ||
         (st = d_alloc(d, &S.busy, B)) || (st = d_alloc(d, &S.openIdx, B)) || (st = d_alloc(d, &S.depth0, B)) ||
         (st = d_alloc(d, &S.frames, (size_t)B * L)) || (st = d_alloc(d, &S.levelDom, lv * DWs)) ||
@@ -399,6 +400,7 @@ int build_dsearch(ct_model* m, ct_batch* b, int levels, int trailFactor, DevSear
         (st = d_alloc(d, &S.firstSol, (size_t)B * DWs)) || (st = d_alloc(d, &S.restQ, (size_t)n)) ||
         (st = d_alloc(d, &vOff, nv)) || (st = d_alloc(d, &vNW, nv)) || (st = d_alloc(d, &vTS, nv + 1)) ||
         (st = d_alloc(d, &vTL, varTabList.size())) || (st = d_alloc(d, &sOff, T + 1)) ||
+        (st = d_alloc(d, &sTab, S.segTotal)) || (st = d_alloc(d, &sPtr, (size_t)n)) ||
         (st = d_alloc(d, &d->d_sd, 1)) || (st = d_alloc(d, &d->d_tabs, n)) || (st = d_alloc(d, &d->d_ctrl, n)) ||
         (st = d_alloc(d, &d->d_root, DWs)))
         return st;
@@ -408,7 +410,17 @@ int build_dsearch(ct_model* m, ct_batch* b, int levels, int trailFactor, DevSear
     S.varTabStart = vTS;
     S.varTabList = vTL;
     S.segOff = sOff;
+    S.segTabOf = sTab;
+    S.segPtr = sPtr;
+    std::vector<int32_t> segTab(S.segTotal);
+    for (int k = 0; k < T; ++k)
+        for (int q = segOff[k]; q < segOff[k + 1]; ++q) segTab[q] = k;
+    std::vector<uint32_t*> segPtrs(n);
+    for (int j = 0; j < n; ++j) segPtrs[j] = ct_table_dev(b->tabs[j]).segMask;
     cudaStream_t str = b->stream;
+    if (S.segTotal > 0)
+        CT_CUDA(cudaMemcpyAsync(sTab, segTab.data(), segTab.size() * 4, cudaMemcpyHostToDevice, str));
+    CT_CUDA(cudaMemcpyAsync(sPtr, segPtrs.data(), n * sizeof(uint32_t*), cudaMemcpyHostToDevice, str));
     CT_CUDA(cudaMemcpyAsync(vOff, m->off.data(), nv * 4, cudaMemcpyHostToDevice, str));
     CT_CUDA(cudaMemcpyAsync(vNW, m->nw.data(), nv * 4, cudaMemcpyHostToDevice, str));
     CT_CUDA(cudaMemcpyAsync(vTS, varTabStart.data(), (nv + 1) * 4, cudaMemcpyHostToDevice, str));
