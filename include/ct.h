@@ -515,7 +515,9 @@ int ct_search_batch_assign(ct_model* m, int slots, int assign_depth, int64_t nod
  * a deeper subtree or a fuller trail makes the host rebuild them with L or F
  * doubled and run the device search again (L from 64 to 1,024, F from 16 to
  * 128; beyond those CT_ERR_LEVEL or CT_ERR_OOM). With no node limit the
- * counts and the first solution equal ct_search_dfs's.
+ * counts and the first solution equal ct_search_dfs's. Slots do not take
+ * right branches from each other here: the breadth-first split goes on below
+ * split_depth until there are at least two open nodes per slot (or depth 48).
  *   slots 1 .. 4096, split_depth 0 .. 64, node_limit as in ct_search_batch;
  *   CT_ERR_ARG when the model has a policy (ct_model_set_policy). */
 int ct_search_batch_device(ct_model* m, int slots, int split_depth, int64_t node_limit, ct_search_stats* out,

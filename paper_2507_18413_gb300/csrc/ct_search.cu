@@ -364,6 +364,8 @@ int d_alloc(DevSearch* d, T** p, size_t n) {
 constexpr int kDevLevels = 64, kDevLevelsMax = 1024;        // levels below an open node
 constexpr int kDevTrailFactor = 16, kDevTrailFactorMax = 128;  // trail entries per table: factor x chunks + 1024
 constexpr int kDevRoundBudget = 1024;  // rounds per launch
+constexpr int kDevOpenPerSlot = 2;      // the device search splits until this many open nodes per slot
+constexpr int kMaxSplitDepth = 48;      // ... or this depth
 
 // The device search's buffers for the B slots of b (kept with b).
 int build_dsearch(ct_model* m, ct_batch* b, int levels, int trailFactor, DevSearch** out) {
@@ -452,6 +454,7 @@ struct Search {
     ct_batch* b = nullptr;
     int B = 0, splitDepth = 0;
     bool splitAssign = false;  // splitDepth counts assignments (left branches) on a node's path
+    int64_t minOpen = 0;       // the breadth-first split goes on below splitDepth while fewer open nodes
     int64_t limit = 0;
     bool countAll = true;
     bool anyStop = false;  // stop at the first solution any slot finds
@@ -645,7 +648,8 @@ struct Search {
         std::vector<OpenNode> F, G;
         children(F, m->h_dom, x, 1, std::vector<uint8_t>());
         for (int depth = 1; !F.empty() && !stopIssue; ++depth) {
-            if (!splitAssign && depth >= splitDepth) break;
+            if (!splitAssign && depth >= splitDepth && ((int64_t)F.size() >= minOpen || depth >= kMaxSplitDepth))
+                break;
             if (splitAssign) {
                 // nodes with splitDepth assignments on their path are open nodes
                 std::vector<OpenNode> rest;
@@ -1314,6 +1318,9 @@ int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int
     S.limit = node_limit;
     S.countAll = count_all == 1;
     S.anyStop = count_all == 2;
+    // the device search keeps no slot waiting for another's right branches:
+    // it splits on until every slot has several open nodes to take
+    if (on_device) S.minOpen = (int64_t)kDevOpenPerSlot * slots;
     // any solution: the model first searches alone for 4 nodes per slot; easy
     // instances end there, the others continue from the frontier it leaves
     if (S.anyStop) S.splitBudget = 4 * (int64_t)slots;
@@ -1325,7 +1332,7 @@ int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int
     std::vector<uint8_t> path;
     // the breadth-first split in the slots, except for the budgeted
     // any-solution search (the model searches its share depth-first first)
-    if ((split_depth >= 2 || split_assign) && !S.anyStop) {
+    if ((split_depth >= 2 || split_assign || on_device) && !S.anyStop) {
         rc = S.split_bfs();
     } else {
         if (split_depth == 0) rc = S.ensure_copies();
