@@ -276,12 +276,14 @@ struct RestoreBatch {
     int32_t n;
 };
 
-int max_coresident_model_blocks();
+// The fixpoint kernel's variant depends on the launch's table count (M.ntables).
+int max_coresident_model_blocks(int ntables);
 cudaError_t launch_model(const ModelDev& M, int grid, cudaStream_t s);
 // The fixpoint kernel in search mode (M.search set): decision and restore
 // phases between rounds, until the search is done or the launch's round budget
 // is spent. The grid is max_coresident_model_blocks()-bounded as for launch_model.
 cudaError_t launch_model_search(const ModelDev& M, int grid, cudaStream_t s);
+int max_coresident_search_blocks();
 // Level 0 of every slot: the root state of its tables (after a state copy
 // into hostTabs), each with an empty trail of trailFactor * W4 + 1024 entries.
 cudaError_t launch_search_init(const ModelDev& M, const TableDev* hostTabs, const SearchDev& S,

@@ -131,7 +131,7 @@ int batch_setup(ct_model* m) {
     for (int v = 0; v < m->nvars; ++v) domBits += m->size[v];
     M.maxRounds = (int)std::min<int64_t>(domBits + 2, 1 << 30);
     m->tabVersion.assign(n, -1);
-    const int maxCo = max_coresident_model_blocks();
+    const int maxCo = max_coresident_model_blocks(n);
     if (maxCo <= 0) {
         ct_set_error("model: the fixpoint kernel cannot be made resident on this device");
         return CT_ERR_CUDA;
@@ -161,7 +161,7 @@ int set_var(ct_model* m, int v, const uint32_t* words);
 // CTA count of the fixpoint launch chosen by trial fixpoints (ct_options.autotune):
 // half of the 4 largest domains removed, propagated, restored; best of 3 per candidate.
 int tune_grid(ct_model* m) {
-    const int maxCo = max_coresident_model_blocks();
+    const int maxCo = max_coresident_model_blocks((int)m->tables.size());
     if (maxCo <= 0 || m->tables.empty()) return CT_OK;
     const int want = m->grid;
     std::vector<int> cands;

@@ -292,7 +292,7 @@ int build_batch(ct_model* m, int B, ct_batch** out) {
     M.nrestores = 0;
     M.nworkIn = reinterpret_cast<const int32_t*>(b->d_stage);
     M.phaseNs = b->d_phase;
-    const int maxCo = max_coresident_model_blocks();
+    const int maxCo = max_coresident_model_blocks(n);
     if (maxCo <= 0) {
         ct_set_error("batched search: the fixpoint kernel cannot be made resident on this device");
         return CT_ERR_CUDA;
@@ -1109,6 +1109,14 @@ struct Search {
         md.nrestores = 0;
         md.nworkIn = nullptr;
         CT_CUDA(launch_search_init(md, b->d_tabs, S, d->d_root, d->trailFactor, str));
+        if (b->d_phase) CT_CUDA(cudaMemsetAsync(b->d_phase, 0, kModelPhases * sizeof(uint64_t), str));
+        // the fixpoint launch's grid rule with the search variant's residency
+        const int maxCoS = max_coresident_search_blocks();
+        if (maxCoS <= 0) {
+            ct_set_error("device search: the search kernel cannot be made resident on this device");
+            return CT_ERR_CUDA;
+        }
+        const int searchGrid = m->opt.grid_blocks > 0 ? std::min(m->opt.grid_blocks, maxCoS) : maxCoS;
         SearchCtr c{};
         unsigned long long lastNodes = ~0ull;
         int idleLaunches = 0;
@@ -1116,7 +1124,7 @@ struct Search {
         for (;;) {
             H[0] = kNoChunk;
             const auto w0 = std::chrono::steady_clock::now();
-            CT_CUDA(launch_model_search(md, b->grid, str));
+            CT_CUDA(launch_model_search(md, searchGrid, str));
             bool seen = false;
             for (uint64_t it = 0;; ++it) {
                 if (H[0] != kNoChunk) {
@@ -1163,6 +1171,13 @@ struct Search {
             ct_set_error("device search: %s", c.error == CT_ERR_LEVEL ? "a subtree is deeper than the device levels"
                                                                      : "stopped");
             return c.error;
+        }
+        if (b->d_phase) {
+            // the phase clock (ct_options.profile): the rounds of the device search
+            uint64_t ns[kModelPhases];
+            CT_CUDA(cudaMemcpyAsync(ns, b->d_phase, sizeof(ns), cudaMemcpyDeviceToHost, str));
+            CT_CUDA(cudaStreamSynchronize(str));
+            for (int q = 0; q < kModelPhases; ++q) info.phase_seconds[q] = 1e-9 * (double)ns[q];
         }
         const int64_t issued = S.nodeLimit > 0 ? std::min<int64_t>((int64_t)c.nodes, S.nodeLimit) : (int64_t)c.nodes;
         if (S.nodeLimit > 0 && (int64_t)c.nodes >= S.nodeLimit) hitLimit = true;
