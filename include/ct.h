@@ -286,7 +286,7 @@ int ct_arm_wait_timeout(ct_table* ct, uint32_t polls);
  * It allocates nothing: its scratch is one static device array of about 32 KB
  * that every GPU loading the library keeps until the process exits. The first
  * call on a device looks the array's device address up (and the kernel's
- * residency); make that first call before any stream capture. All calls on a
+ * residency). All calls on a
  * device share the array and it keeps the last call's contents (each call
  * clears what it needs cleared), so calls that overlap on the GPU -- two host
  * threads, or two streams -- race and must be serialised by the caller.

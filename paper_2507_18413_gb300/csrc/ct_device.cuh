@@ -81,30 +81,35 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs resident). Thread 0 of
-// every CTA keeps the barrier's generation in a register, read once at the
-// start of the launch (no CTA of the launch can move it before this CTA's first
-// arrival), so a barrier costs the arrival atomic plus, for every CTA but the
-// last to arrive, the polls of the generation word. The last arrival resets
-// the count and advances the generation; the others poll at most `limit`
-// times. bar_sync returns 0 (after setting CT_ERR_TIMEOUT) when the wait ran
-// out, 2 to the CTA that arrived last (it has acquired every other CTA's
-// writes and goes on at once), 1 to the others.
+// Grid-wide barrier for a cooperative launch (all CTAs resident). The arrival
+// count only grows: barrier k of a launch is complete when the count reaches
+// base + k * gridDim.x, where base is the count every launch starts from (the
+// last target the previous launch reached, stored by the last arrival of each
+// barrier). Thread 0 of every CTA reads base once at the start of the launch
+// (no CTA of the launch can store it before this CTA's first arrival, which
+// releases that read) and keeps the next target in a register. Waiters poll
+// the count itself, so a barrier costs the arrival atomic plus the time for
+// the last arrival to reach the count (no second word to publish). Every
+// launch must run the same barrier sequence in every CTA. bar_sync returns 0
+// (after setting CT_ERR_TIMEOUT) when the wait ran out after `limit` polls, 2
+// to the CTA that arrived last (it has acquired every other CTA's writes and
+// goes on at once), 1 to the others. The signed difference keeps the test
+// valid across the 32-bit wrap.
 struct GridBarrier {
     unsigned* count;
-    unsigned* gen;
+    unsigned* base;
     int* status;
     unsigned limit;
-    unsigned g;  // generation of the next barrier (thread 0)
+    unsigned target;  // count that completes the current barrier (thread 0)
 };
 
-__device__ __forceinline__ void bar_init(GridBarrier& b, unsigned* count, unsigned* gen, int* status,
+__device__ __forceinline__ void bar_init(GridBarrier& b, unsigned* count, unsigned* base, int* status,
                                          unsigned limit) {
     b.count = count;
-    b.gen = gen;
+    b.base = base;
     b.status = status;
     b.limit = limit;
-    b.g = threadIdx.x == 0 ? ld_relaxed(gen) : 0u;
+    b.target = threadIdx.x == 0 ? ld_relaxed(base) : 0u;
 }
 
 __device__ int bar_sync(GridBarrier& b, int* s_flag) {
@@ -112,16 +117,16 @@ __device__ int bar_sync(GridBarrier& b, int* s_flag) {
     if (threadIdx.x == 0) {
         int r = 1;
         unsigned arrived;
+        b.target += gridDim.x;
         // Release this CTA's writes (ordered before by the CTA barrier) and, for
         // the last arrival, acquire everybody else's.
         asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(b.count) : "memory");
-        if (arrived == gridDim.x - 1) {
-            *b.count = 0u;
-            st_release(b.gen, b.g + 1u);
+        if (arrived == b.target - 1u) {
+            *b.base = b.target;  // read by the next launch only
             r = 2;
         } else {
             unsigned it = 0;
-            while (ld_acquire(b.gen) == b.g) {
+            while ((int)(ld_acquire(b.count) - b.target) < 0) {
                 if (++it > b.limit) {
                     r = 0;
                     atomicExch(b.status, CT_ERR_TIMEOUT);
@@ -130,7 +135,6 @@ __device__ int bar_sync(GridBarrier& b, int* s_flag) {
                 if (it > 64) __nanosleep(32);
             }
         }
-        b.g += 1u;
         *s_flag = r;
     }
     __syncthreads();

@@ -82,8 +82,8 @@ struct Ctrl {
     uint32_t words_in;   // per call: non-zero 32-bit words at entry
     uint32_t nhard;      // per call: values left for the full index scan
     uint32_t done;       // last-block-done ticket
-    uint32_t bar_count;  // grid barrier arrivals
-    uint32_t bar_gen;    // grid barrier generation
+    uint32_t bar_count;  // grid barrier arrivals (only grows)
+    uint32_t bar_base;   // grid barrier count at the start of the next launch
     int32_t nrows;       // rows in the update plan
     int32_t nval, ndelta, nreset, nsup;
     int32_t hits, pruned, trail_added, local_found, misses, windows;
@@ -175,7 +175,7 @@ struct ModelTabCall {
 
 struct ModelCtrl {
     int32_t status;
-    uint32_t bar_count, bar_gen;
+    uint32_t bar_count, bar_base;  // grid barrier arrivals and the next launch's starting count
     int32_t nwork;       // tables of the first round (when not passed in nworkIn)
     int32_t rounds;
     int32_t props;       // table propagations done

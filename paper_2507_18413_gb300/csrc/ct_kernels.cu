@@ -220,7 +220,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     const int nwarps = gridDim.x * kWarps;
     const VarLayout V(T, P.domOff, domOff);
     GridBarrier bar;
-    bar_init(bar, &C->bar_count, &C->bar_gen, &C->status, P.spinLimit ? P.spinLimit : kBarrierSpinLimit);
+    bar_init(bar, &C->bar_count, &C->bar_base, &C->status, P.spinLimit ? P.spinLimit : kBarrierSpinLimit);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
     CT_STAMP(0);
 

@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
     int32_t* preU = sm.codes;                               // unit prefix of the round (smem copy)
     int32_t* preR = reinterpret_cast<int32_t*>(sm.dom);     // row prefix of the round (smem copy)
     GridBarrier bar;
-    bar_init(bar, &C->bar_count, &C->bar_gen, &C->status, M.spinLimit ? M.spinLimit : kBarrierSpinLimit);
+    bar_init(bar, &C->bar_count, &C->bar_base, &C->status, M.spinLimit ? M.spinLimit : kBarrierSpinLimit);
     auto sync = [&]() { return bar_sync(bar, &sm.flag[0]) != 0; };
     // optional phase clock: CTA 0 adds the time since its previous mark (a grid
     // barrier ends every phase, so this is the phase's length across the grid)

@@ -60,7 +60,7 @@ struct NaInit {
     int32_t R;
     int32_t nseg;
     int32_t W4;                  // 128-bit chunks of currTable
-    uint32_t barCount;           // initial grid-barrier count (0; the timeout test hook sets it unreachable)
+    uint32_t barCount;           // initial grid-barrier count (0; the timeout test hook sets it 2^30 behind)
     const uint4* curr;           // the caller's currTable
 };
 
@@ -92,6 +92,7 @@ __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
     if (tid == 0) {
         S->status[kSlotStatus] = kNaPending;
         S->ctrl.bar_count = p.barCount;
+        S->ctrl.bar_base = 0u;
     }
 }
 
@@ -221,7 +222,7 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     init.W4 = (int32_t)W4;
     init.curr = T.curr;
     const uint32_t armed = g_na_arm.exchange(0u);
-    init.barCount = armed ? 0x40000000u : 0u;
+    init.barCount = armed ? 0xC0000000u : 0u;
     ct_noalloc_init_kernel<<<8, 256, 0, s>>>(init);
     CT_CUDA(cudaGetLastError());
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -547,10 +548,12 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->armPolls) {
-        // Test hook (ct_arm_wait_timeout): an arrival count that no CTA can
-        // complete, so every barrier wait of this call runs out after armPolls polls.
-        const uint32_t unreachable = 0x40000000u;
-        CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->bar_count, &unreachable, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        // Test hook (ct_arm_wait_timeout): an arrival count 2^30 behind every
+        // target of this call (base 0), so no barrier completes and every wait
+        // runs out after armPolls polls.
+        const uint32_t unreachable[2] = {0xC0000000u, 0u};  // bar_count, bar_base
+        static_assert(offsetof(Ctrl, bar_base) == offsetof(Ctrl, bar_count) + sizeof(uint32_t), "adjacent words");
+        CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->bar_count, unreachable, sizeof(unreachable), cudaMemcpyHostToDevice, s));
         P.spinLimit = ct->armPolls;
         ct->armPolls = 0;
     }
@@ -604,7 +607,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         Ctrl c{};
         CT_CUDA(cudaMemcpy(&c, ct->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
         status = c.status == CT_OK ? CT_ERR_TIMEOUT : c.status;
-        c.bar_count = 0;
+        c.bar_count = c.bar_base = 0;
         c.status = CT_OK;
         c.live = c.live_in = c.words_in = c.nhard = c.done = c.tuples = 0u;
         c.nscan = 0;
