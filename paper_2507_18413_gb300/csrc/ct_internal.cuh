@@ -82,8 +82,6 @@ struct Ctrl {
     uint32_t words_in;   // per call: non-zero 32-bit words at entry
     uint32_t nhard;      // per call: values left for the full index scan
     uint32_t done;       // last-block-done ticket
-    uint32_t bar_count;  // grid barrier arrivals (only grows)
-    uint32_t bar_base;   // grid barrier count at the start of the next launch
     int32_t nrows;       // rows in the update plan
     int32_t nval, ndelta, nreset, nsup;
     int32_t hits, pruned, trail_added, local_found, misses, windows;
@@ -92,6 +90,11 @@ struct Ctrl {
     uint32_t tuples;     // per call, negative tables: valid tuples after the update
     int32_t pad2;
     uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
+    // The barrier words on a line of their own: the arrivals and polls of
+    // every CTA would otherwise hold up the finalizing CTA's reads of the
+    // counters above.
+    alignas(128) uint32_t bar_count;  // grid barrier arrivals (only grows)
+    uint32_t bar_base;                // grid barrier count at the start of the next launch
 };
 
 // Everything a kernel needs, passed by value.
@@ -175,7 +178,6 @@ struct ModelTabCall {
 
 struct ModelCtrl {
     int32_t status;
-    uint32_t bar_count, bar_base;  // grid barrier arrivals and the next launch's starting count
     int32_t nwork;       // tables of the first round (when not passed in nworkIn)
     int32_t rounds;
     int32_t props;       // table propagations done
@@ -188,6 +190,9 @@ struct ModelCtrl {
     int32_t nscanAll[2]; // values of round r left for full scans, in nscanAll[r & 1]
     unsigned long long bytesUpdate;  // algorithmic bytes of updateTable: 4 * words at entry * (rows + 2)
     unsigned long long bytesFilter;  // of the full scans: 16 * hard values * live chunks
+    // on a line of their own, away from the counters every CTA reads after a barrier
+    alignas(128) uint32_t bar_count;  // grid barrier arrivals (only grows)
+    uint32_t bar_base;                // grid barrier count at the start of the next launch
 };
 
 // ---------------------------------------------------------------------------

@@ -32,6 +32,7 @@
 //            stores new residues and publishes.
 // Grid barriers spin with a bounded iteration count; running out sets
 // CT_ERR_TIMEOUT in the control block and every CTA returns.
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -67,6 +68,26 @@ namespace {
 // one CTA: apply Algorithm 3's removals, publish, reset the call counters
 // ---------------------------------------------------------------------------
 
+// Word of the control block read into each status header slot (-1: none),
+// and the word subtracted from it (-1: none; the stamps are sent as ns since
+// the start stamp, from their low words, and the start stamp as its low word).
+#define CT_CW(f) (int16_t)(offsetof(Ctrl, f) / sizeof(int32_t))
+#define CT_TLO(k) (int16_t)(offsetof(Ctrl, t) / sizeof(int32_t) + 2 * (k))
+__constant__ int16_t kHdrWord[kStatusHdr] = {
+    CT_CW(status), CT_CW(live), CT_CW(words_in), CT_CW(trail_top), CT_CW(misses), -1, CT_CW(hits), CT_CW(nrows),
+    CT_CW(nval), CT_CW(nsup), CT_CW(ndelta), CT_CW(nreset), CT_CW(trail_added), CT_CW(live_in), CT_CW(local_found),
+    CT_CW(nhard), CT_CW(windows), CT_TLO(1), CT_TLO(2), CT_TLO(3), CT_TLO(0), CT_CW(nscan), -1, -1};
+__constant__ int16_t kHdrSub[kStatusHdr] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                            CT_TLO(0), CT_TLO(0), CT_TLO(0), -1, -1, -1, -1};
+#undef CT_CW
+#undef CT_TLO
+static_assert(kSlotStatus == 0 && kSlotLiveOut == 1 && kSlotWordsIn == 2 && kSlotTrailTop == 3 && kSlotMisses == 4 &&
+                  kSlotPruned == 5 && kSlotHits == 6 && kSlotRowsOred == 7 && kSlotNval == 8 && kSlotNsup == 9 &&
+                  kSlotNdelta == 10 && kSlotNreset == 11 && kSlotTrailAdded == 12 && kSlotLiveIn == 13 &&
+                  kSlotLocal == 14 && kSlotHard == 15 && kSlotWindows == 16 && kSlotT1 == 17 && kSlotT2 == 18 &&
+                  kSlotT3 == 19 && kSlotT4 == 20 && kSlotScan == 21 && kStatusHdr == 24,
+              "status header slots as the tables above list them");
+
 // Run by exactly one CTA once every other CTA is done with the call (the last
 // to arrive at the final barrier, or the last to finish the full scan). Every
 // counter of the call is read in one round of loads (thread k reads header
@@ -75,53 +96,53 @@ namespace {
 // nh < 0: the hard-value counts are read with the header, and with values
 // left undecided for the full scan the CTA returns false without publishing
 // (the hard values known unsupported are removed here).
+// Nothing but this CTA writes the domains during a call, so the first hard
+// entries (read whether or not they belong to this call, kept only below the
+// count) and the domain words are loaded in the same round as the header;
+// the removals go to a shared copy of the domains, which is what the host
+// receives. localDom: sm.dom already holds the call's domains (local plan).
 __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh,
-                         uint64_t t3) {
+                         uint64_t t3, bool localDom) {
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
     int32_t* H = T.statusBlk;
     __syncthreads();  // counters thread 0 of this CTA may have written just before
-    if (tid < kStatusHdr) {
-        int32_t v = 0;
-        switch (tid) {
-            case kSlotHard: v = nh < 0 ? (int32_t)__ldcg(&C->nhard) : nh; break;
-            case kSlotScan: v = __ldcg(&C->nscan); break;
-            case kSlotStatus: v = __ldcg(&C->status); break;
-            case kSlotLiveOut: v = (int32_t)__ldcg(&C->live); break;
-            case kSlotWordsIn: v = (int32_t)__ldcg(&C->words_in); break;
-            case kSlotTrailTop: v = __ldcg(&C->trail_top); break;
-            case kSlotMisses: v = __ldcg(&C->misses); break;
-            case kSlotHits: v = __ldcg(&C->hits); break;
-            case kSlotRowsOred: v = __ldcg(&C->nrows); break;
-            case kSlotNval: v = __ldcg(&C->nval); break;
-            case kSlotNsup: v = __ldcg(&C->nsup); break;
-            case kSlotNdelta: v = __ldcg(&C->ndelta); break;
-            case kSlotNreset: v = __ldcg(&C->nreset); break;
-            case kSlotTrailAdded: v = __ldcg(&C->trail_added); break;
-            case kSlotLiveIn: v = (int32_t)__ldcg(&C->live_in); break;
-            case kSlotLocal: v = __ldcg(&C->local_found); break;
-            case kSlotWindows: v = __ldcg(&C->windows); break;
-            case kSlotT1: v = (int32_t)(__ldcg(&C->t[1]) - __ldcg(&C->t[0])); break;
-            case kSlotT2: v = (int32_t)(__ldcg(&C->t[2]) - __ldcg(&C->t[0])); break;
-            case kSlotT3: v = (int32_t)((t3 ? t3 : __ldcg(&C->t[3])) - __ldcg(&C->t[0])); break;
-            case kSlotT4: v = (int32_t)__ldcg(&C->t[0]); break;  // start stamp, low word (see below)
-            default: v = 0;
+    const bool smemDom = localDom || T.DW <= kLocalMaxDW;
+    int preRow = 0, preFc = 0;
+    if (nh != 0) {
+        if (tid < T.R) {
+            preRow = __ldcg(&T.hardRow[tid]);
+            preFc = __ldcg(&T.foundChunk[tid]);
         }
-        sm.scan[tid] = v;
+        if (!localDom && smemDom)
+            for (int i = tid; i < T.arity; i += kThreads)
+                for (int k = 0; k < V.nw(i); ++k) sm.dom[V.ld(i) + k] = __ldcg(&dom[V.off(i) + k]);
+    }
+    if (tid < kStatusHdr) {
+        // one predicated load (two for a stamp difference) per slot, no
+        // divergent branches: the header is read in one round
+        const int32_t* cw = reinterpret_cast<const int32_t*>(C);
+        const int a = kHdrWord[tid], b = kHdrSub[tid];
+        int32_t v = a >= 0 ? __ldcg(cw + a) : 0;
+        const int32_t w = b >= 0 ? __ldcg(cw + b) : 0;
+        if (tid == kSlotHard && nh >= 0) v = nh;
+        if (tid == kSlotT3 && t3) v = (int32_t)(uint32_t)t3;
+        sm.scan[tid] = v - w;
     }
     if (tid == 0) sm.cnt[kCntPruned] = 0u;
     // bit i of sm.scan[kChgBase + i / 32]: scope variable i lost a value
     constexpr int kChgBase = 32;
     for (int q = tid; q < T.nChangedWords; q += kThreads) sm.scan[kChgBase + q] = 0;
     __syncthreads();
+    CT_STAMP(15);
     if (nh < 0 && sm.scan[kSlotScan] > 0) return false;
     nh = sm.scan[kSlotHard];
     const int st = sm.scan[kSlotStatus];
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
-            const int r = __ldcg(&T.hardRow[m]);
-            const int fc = __ldcg(&T.foundChunk[m]);
+            const int r = m == tid ? preRow : __ldcg(&T.hardRow[m]);
+            const int fc = m == tid ? preFc : __ldcg(&T.foundChunk[m]);
             // positive tables: a chunk holding a support, or kNoChunk / kNoSupport;
             // negative tables: fc counts the valid forbidden tuples with the value
             const bool keep = T.negative ? (unsigned long long)fc < sm.other[T.rowVar[r]] : (fc >= 0 && fc != kNoChunk);
@@ -132,6 +153,7 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
                 const int i = T.rowVar[r];
                 const int a = r - V.row0(i);
                 atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+                if (smemDom) atomicAnd(&sm.dom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 // a positive table's removed value carries no valid tuple, so
                 // lastDom may drop it now; a negative table's value still has
                 // valid forbidden tuples, which the next call removes as Delta;
@@ -150,7 +172,8 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             for (int q = tid; q < T.nChangedWords; q += kThreads) H[kStatusHdr + q] = sm.scan[kChgBase + q];
             for (int i = tid; i < T.arity; i += kThreads) {
                 if (!((sm.scan[kChgBase + (i >> 5)] >> (i & 31)) & 1)) continue;
-                for (int k = 0; k < V.nw(i); ++k) outDom[V.ld(i) + k] = __ldcg(&dom[V.off(i) + k]);
+                for (int k = 0; k < V.nw(i); ++k)
+                    outDom[V.ld(i) + k] = smemDom ? sm.dom[V.ld(i) + k] : __ldcg(&dom[V.off(i) + k]);
             }
         }
     }
@@ -299,7 +322,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         }
         if (!ok) {
             // Domain error or empty domain: publish without filtering.
-            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0, 0ull);
+            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0, 0ull, kLocal);
             return;
         }
         if (blockIdx.x == 0 && tid == 0) {
@@ -406,7 +429,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             if (r1 == 2) {
                 if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
                 __syncthreads();
-                finalize(T, V, dom, sm, 0, 0ull);
+                finalize(T, V, dom, sm, 0, 0ull, kLocal);
             }
             return;
         }
@@ -477,7 +500,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     // it publishes: with none left undecided (every value kept its support,
     // or its windows covered every live chunk) it removes the unsupported
     // values and publishes, and the others are done.
-    if (r2 == 2 && finalize(T, V, dom, sm, -1, t3)) {
+    if (r2 == 2 && finalize(T, V, dom, sm, -1, t3, kLocal)) {
         CT_STAMP(6);
         return;
     }
@@ -509,7 +532,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     CT_STAMP(14);
     if (!sm.flag[1]) return;
     __threadfence();
-    finalize(T, V, dom, sm, nh, 0ull);
+    finalize(T, V, dom, sm, nh, 0ull, kLocal);
     CT_STAMP(7);
 }
 

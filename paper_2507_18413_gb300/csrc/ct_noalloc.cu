@@ -18,6 +18,7 @@
 // chunks of currTable (8,388,608 tuples). Backtracking is the caller's
 // business (it keeps copies of the buffers it wants to return to).
 #include <atomic>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -72,7 +73,9 @@ __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
     int32_t* c = reinterpret_cast<int32_t*>(&S->ctrl);
-    for (int q = tid; q < (int)(sizeof(Ctrl) / sizeof(int32_t)); q += nth) c[q] = 0;
+    // one writer per word: the barrier count starts at p.barCount, the rest at 0
+    constexpr int kBarWord = (int)(offsetof(Ctrl, bar_count) / sizeof(int32_t));
+    for (int q = tid; q < (int)(sizeof(Ctrl) / sizeof(int32_t)); q += nth) c[q] = q == kBarWord ? (int32_t)p.barCount : 0;
     for (int q = tid; q < p.R; q += nth) {
         S->residue[q] = 0;
         S->rowVar[q] = p.rowVar[q];
@@ -91,8 +94,6 @@ __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
     for (int q = tid; q < kNaMaxArity; q += nth) S->changed[q] = 0;
     if (tid == 0) {
         S->status[kSlotStatus] = kNaPending;
-        S->ctrl.bar_count = p.barCount;
-        S->ctrl.bar_base = 0u;
     }
 }
 
