@@ -12,6 +12,30 @@
 namespace ctk {
 namespace {
 
+#ifdef CT_PHASE_TRACE
+// Diagnostic build only (-DCT_PHASE_TRACE): %globaltimer stamps of thread 0 of
+// the first kTraceCtas CTAs at the phase boundaries of the last propagation,
+// read with ct_trace_read (one array per translation unit; the propagation
+// kernel's is read). The default build has none of this.
+constexpr int kTraceCtas = 1024, kTraceStamps = 24;
+__device__ unsigned long long g_ct_trace[kTraceCtas * kTraceStamps];
+__device__ __forceinline__ unsigned long long gtimer_trace() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define CT_STAMP(k)                                                          \
+    do {                                                                     \
+        if (threadIdx.x == 0 && blockIdx.x < kTraceCtas)                     \
+            g_ct_trace[blockIdx.x * kTraceStamps + (k)] = gtimer_trace();    \
+    } while (0)
+#else
+#define CT_STAMP(k) \
+    do {            \
+    } while (0)
+#endif
+
+
 
 __device__ __forceinline__ bool nz(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
 
@@ -187,6 +211,7 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
     const int tid = threadIdx.x;
     if (tid < 8) sm.flags[tid] = 0;
     __syncthreads();
+    CT_STAMP(16);
     for (int i = tid; i < T.arity; i += kThreads) {
         const int nw = V.nw(i);
         const uint32_t* d = dom + V.off(i);
@@ -216,6 +241,7 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
         K[i] = k;
     }
     __syncthreads();
+    CT_STAMP(17);
     if (sm.flags[0] || sm.flags[1]) {
         if (tid == 0) sm.flags[6] = 0;
         __syncthreads();
@@ -256,6 +282,7 @@ __device__ void plan(const TableDev& T, const VarLayout& V, const uint32_t* __re
         }
         __syncthreads();
     }
+    CT_STAMP(18);
     // Codes: the removed values (delta) or the remaining ones (reset).
     for (int i = tid; i < T.arity; i += kThreads) {
         const int k = K[i] & kCodeRow;

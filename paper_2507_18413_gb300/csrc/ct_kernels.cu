@@ -40,27 +40,6 @@
 
 namespace ctk {
 
-#ifdef CT_PHASE_TRACE
-// Diagnostic build only (-DCT_PHASE_TRACE): %globaltimer stamps of thread 0 of
-// the first kTraceCtas CTAs at the phase boundaries of the last propagation,
-// read with ct_trace_read. The default build has none of this.
-constexpr int kTraceCtas = 1024, kTraceStamps = 16;
-__device__ unsigned long long g_ct_trace[kTraceCtas * kTraceStamps];
-#define CT_STAMP(k)                                                          \
-    do {                                                                     \
-        if (threadIdx.x == 0 && blockIdx.x < kTraceCtas)                     \
-            g_ct_trace[blockIdx.x * kTraceStamps + (k)] = gtimer_trace();    \
-    } while (0)
-__device__ __forceinline__ unsigned long long gtimer_trace() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-#else
-#define CT_STAMP(k) \
-    do {            \
-    } while (0)
-#endif
 
 namespace {
 
@@ -258,6 +237,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
     if (T.useResidues && gwarp < T.R && lane == 0) res0 = T.residue[gwarp];
 
+    CT_STAMP(19);
     // plan (CTA 0 also snapshots lastDom into the levels saved since the last call)
     int nrows;
     bool ok;
@@ -351,6 +331,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         const int units = T.nseg << lg;
         const int per = (nrows + G - 1) >> lg;  // rows per slice
         __syncthreads();
+        CT_STAMP(20);
         const int cap = __ldcg(&C->trail_cap);
         // Rounds of one unit per warp; every warp of a CTA runs every round so
         // that the trail reservation and the slice combination can
@@ -373,6 +354,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
                 }
             }
             if (lane == 0) sm.trw[warp] = __popc(slots.cand);
+            CT_STAMP(21);
             __syncthreads();
             int ctaBase = 0;  // thread 0: the CTA's block of slots, waited for after the row loads
             if (tid == 0) {
