@@ -373,9 +373,12 @@ int ct_model_add_table(ct_model* m, const int32_t* scope, int arity,
                        const int32_t* tuples, int64_t t);
 
 /* ct_model_add_negative_table: a negative table (see ct_create_negative) over
- * `scope`. A model holding one propagates with the host queue (one launch per
- * table propagation; the one-launch fixpoint kernel handles positive tables
- * only) and refuses ct_search_batch, features and lookahead (CT_ERR_ARG). */
+ * `scope`. The one-launch fixpoint kernel and the batched searches propagate
+ * it beside the positive tables: a value whose valid forbidden tuples number
+ * as many as the combinations of the other scope domains is removed, and the
+ * table runs again after its own removals (one pass of a negative table is
+ * not GAC for it). A model holding one refuses features and lookahead
+ * (CT_ERR_ARG). */
 int ct_model_add_negative_table(ct_model* m, const int32_t* scope, int arity, const int32_t* tuples, int64_t t);
 
 /* ct_model_propagate: run table propagations until no domain changes

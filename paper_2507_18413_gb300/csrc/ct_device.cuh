@@ -473,9 +473,11 @@ __device__ __forceinline__ uint4 combine_slices(const SliceSmem& S, int w0, int 
 
 // The end of Algorithm 2 on one segment, given the AND of its masks: the new
 // chunks, the trail item of a changed chunk, and the segment's part of the
-// non-zero index rebuilt by one warp ballot.
+// non-zero index rebuilt by one warp ballot. s_cnt: the live/words counters;
+// tuples: a negative table's count of valid tuples.
 __device__ __forceinline__ void finish_segment(const TableDev& T, int mark, int seg, const SegState& S,
-                                               const uint4& acc, uint32_t* s_cnt, TrailItem& out) {
+                                               const uint4& acc, uint32_t* s_cnt, uint32_t* tuples,
+                                               TrailItem& out) {
     const int lane = threadIdx.x & 31;
     const uint32_t mask = S.mask;
     const bool act = (mask >> lane) & 1u;
@@ -494,7 +496,7 @@ __device__ __forceinline__ void finish_segment(const TableDev& T, int mark, int 
         uint32_t tc = act ? __popc(nv.x) + __popc(nv.y) + __popc(nv.z) + __popc(nv.w) : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
-        if (lane == 0 && tc) atomicAdd(&s_cnt[kCntTuples], tc);
+        if (lane == 0 && tc) atomicAdd(tuples, tc);
     }
     const uint32_t nmask = __ballot_sync(0xffffffffu, alive);
     uint32_t words = nzwords(cur);
@@ -512,14 +514,14 @@ __device__ __forceinline__ void finish_segment(const TableDev& T, int mark, int 
 template <int U, bool kGlobal = false>
 __device__ __forceinline__ void update_segment(const TableDev& T, int mark, int snapFrom, int snapTo, int seg,
                                                const SegState& S, int nrows, const int32_t* s_codes,
-                                               uint32_t* s_cnt, TrailItem& out) {
+                                               uint32_t* s_cnt, uint32_t* tuples, TrailItem& out) {
     const int lane = threadIdx.x & 31;
     out.need = false;
     // Levels saved since the last call snapshot the index as it is now.
     for (int l = snapFrom + lane; l < snapTo; l += 32) T.levelSeg[(size_t)l * T.nseg + seg] = S.mask;
     if (S.mask == 0u) return;
     const uint4 acc = slice_rows<U, kGlobal, false>(T, seg, (S.mask >> lane) & 1u, S.cur, 0, nrows, s_codes, nullptr, 0);
-    finish_segment(T, mark, seg, S, acc, s_cnt, out);
+    finish_segment(T, mark, seg, S, acc, s_cnt, tuples, out);
 }
 
 // Trail slots of a round of segments. Each segment's warp counts one slot for

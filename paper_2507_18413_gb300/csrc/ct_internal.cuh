@@ -113,7 +113,8 @@ struct TableDev {
     int32_t* planK;          // [arity] rows to OR | delta flag (global plan mode)
     int32_t* planRowOff;     // [arity] first code of each variable (global plan mode)
     int32_t* varSup;         // [arity] 1 if |dom| > 1 (s_sup, global plan mode)
-    int32_t* changed;        // [arity]
+    unsigned long long* other;  // [arity] negative tables in the network kernel: product of the
+                                // other scope domains' sizes (saturated), written by the plan
     int32_t* hardRow;        // [R] values left for the full scan
     int32_t* foundChunk;     // [R]
     const int32_t* rowVar;   // [R] scope position of each row
@@ -124,7 +125,7 @@ struct TableDev {
     uint32_t* levelSeg;      // [levelCap][nseg] live masks
     uint32_t* levelDom;      // [levelCap][DW]
     int32_t arity, R, W4, nseg, S, DW, nChangedWords, useResidues;
-    int32_t negative;        // 1: the tuples are forbidden (negative table; one-table kernel only)
+    int32_t negative;        // 1: the tuples are forbidden (negative table)
     int32_t shard;           // 1: a word-range shard (one-table kernel only): no failure on an
                              // empty currTable, lastDom keeps the call's input domains
     // Scopes of at most kParamArity variables: words, lastDom offset and first

@@ -386,7 +386,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             __syncthreads();
             CT_STAMP(10);
             if (S.mask != 0u && slice == 0) {
-                finish_segment(T, P.mark, seg, S, acc, sm.cnt, it);
+                finish_segment(T, P.mark, seg, S, acc, sm.cnt, &sm.cnt[kCntTuples], it);
                 slots.base = sm.trBase + sm.trw[warp];
                 trail_write(T, slots, it, cap, sm.cnt);
             }

@@ -490,11 +490,7 @@ int add_table_impl(ct_model* m, const int32_t* scope, int arity, const int32_t* 
     const int st = negative ? ct_create_negative(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab)
                             : ct_create(arity, lo.data(), sz.data(), tuples, t, &m->opt, m->stream, &tab);
     if (st < 0) return st;
-    if (negative) {
-        // the one-launch fixpoint kernel handles positive tables only
-        m->hasNegative = true;
-        m->batch = false;
-    }
+    if (negative) m->hasNegative = true;  // no ordering features (they count positive supports)
     int32_t* d_off = nullptr;
     cudaError_t e = cudaMalloc(&d_off, (size_t)arity * sizeof(int32_t));
     if (e == cudaSuccess)

@@ -50,7 +50,7 @@ struct ct_model {
     std::vector<void*> allocs;
     int grid = 1;
     ct_batch* bsearch = nullptr;  // built by the first batched search, kept for the next ones
-    bool hasNegative = false;     // a negative table: host-queue fixpoint, no batched search or features
+    bool hasNegative = false;     // a negative table: no ordering features or lookahead labels
     // learned branching order
     ct_mlp* policy = nullptr;          // NULL: first-fail
     ctk::FeatView* fview = nullptr;    // feature view of the model (one node), built on first use

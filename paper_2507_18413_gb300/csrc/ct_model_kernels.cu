@@ -1,6 +1,7 @@
 // ct_model_kernels.cu -- a network of tables propagated to its fixpoint in one
 // cooperative launch, the batched trail undo of several tables, and the state
 // copies of the batched search's table clones.
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -19,6 +20,11 @@ namespace {
 // round when another table removed a value of one of its variables. The GAC
 // closure is unique, so the order of the propagations does not matter.
 // ---------------------------------------------------------------------------
+
+// The update's live/words counters are a table's control block from `live` on.
+static_assert(offsetof(Ctrl, live_in) == offsetof(Ctrl, live) + 4 * kCntLiveIn &&
+                  offsetof(Ctrl, words_in) == offsetof(Ctrl, live) + 4 * kCntWords && kCntLive == 0,
+              "counter block layout");
 
 // Entry k of a round's prefix array: the shared-memory copy, or the global
 // array itself (read through L2) when the round is too long for the copy.
@@ -100,15 +106,24 @@ __device__ void work_prefix(const ModelDev& M, const int32_t* work, int n, int32
     __syncthreads();
 }
 
-// Value r of table t has no support: clear it from the shared domains and the
-// table's lastDom, and mark its variable as pruned by t (-2: by several tables).
+// Value r of table t has no support: clear it from the shared domains and, for
+// a positive table, from the table's lastDom (no valid tuple carries it), and
+// mark its variable as pruned by t (-2: by several tables). A negative table's
+// removed value still has valid forbidden tuples, which its next pass removes
+// as Delta, and that pass is due: one pass of a negative table is not GAC for
+// it (a removal shrinks the products the other values are compared with), so
+// its own removals schedule it again (-2).
 __device__ __forceinline__ void remove_value(const ModelDev& M, const TableDev& T, int t, int r, int32_t* pruned) {
     const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
     const int i = T.rowVar[r];
     const int a = r - V.row0(i);
     atomicAnd(&M.dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
-    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
     const int v = M.scopeVar[M.scopeBase[t] + i];
+    if (T.negative) {
+        atomicExch(&pruned[v], -2);
+        return;
+    }
+    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
     const int old = atomicCAS(&pruned[v], -1, t);
     if (old != -1 && old != t) atomicExch(&pruned[v], -2);
 }
@@ -521,6 +536,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                 if (tid == 0) M.snapTaken[t] = 1;
             }
             plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+            if (T.negative && tid == 0 && !sm.flags[0] && !sm.flags[1]) {
+                // a value of x_i loses its support when its valid forbidden
+                // tuples are all prod_{j != i} |D_j| combinations: the products,
+                // saturated at 2^62
+                const unsigned long long cap = 1ull << 62;
+                auto mul = [&](unsigned long long x, unsigned long long y) {
+                    return (y != 0 && x > cap / y) ? cap : x * y;
+                };
+                unsigned long long pre = 1ull;
+                for (int i = 0; i < T.arity; ++i) {
+                    T.other[i] = pre;
+                    pre = mul(pre, (unsigned long long)sm.nd[i]);
+                }
+                unsigned long long suf = 1ull;
+                for (int i = T.arity - 1; i >= 0; --i) {
+                    T.other[i] = mul(T.other[i], suf);
+                    suf = mul(suf, (unsigned long long)sm.nd[i]);
+                }
+            }
             if (tid == 0) {
                 Ctrl* Tc = T.ctrl;
                 Tc->nrows = sm.flags[6];
@@ -558,25 +592,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
             const int t = __ldcg(&work[k]);
             const TableDev& T = M.tabs[t];
             const int nrows = __ldcg(&T.ctrl->nrows);
-            if (nrows == 0) continue;
+            // a negative table goes through even with no row to OR: its
+            // filter compares counts with the valid tuples left
+            if (nrows == 0 && !T.negative) continue;
             const int seg = u - pre_at(pU, k, gpre);
             const int mark = __ldcg(&M.calls[t].mark);
             const SegState S = load_segment(T, seg, mark);
             TrailItem it;
             update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
-                                    reinterpret_cast<uint32_t*>(&T.ctrl->live), it);
+                                    reinterpret_cast<uint32_t*>(&T.ctrl->live), &T.ctrl->tuples, it);
             trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
         }
         if (!sync()) return;
         phase(2);
 
         if (__ldcg(&C->status) != CT_OK) break;
-        // Algorithm 1 line 5: a table whose currTable became zero fails its node;
+        // Algorithm 1 line 5: a table whose currTable became zero fails its node
+        // (a negative table with no valid forbidden tuple forbids nothing);
         // the node's tables leave the work list from the next round on.
         for (int k = blockIdx.x * kThreads + tid; k < nwork; k += gridDim.x * kThreads) {
             const int t = __ldcg(&work[k]);
-            const Ctrl* Tc = M.tabs[t].ctrl;
-            if (__ldcg(&Tc->nrows) > 0 && __ldcg(&Tc->live) == 0u) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;
+            const TableDev& T = M.tabs[t];
+            if (!T.negative && __ldcg(&T.ctrl->nrows) > 0 && __ldcg(&T.ctrl->live) == 0u)
+                M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;
         }
         // lastDom := the domains of this round (removals below clear their bits)
         for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
@@ -607,9 +645,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                 r = u - pre_at(pR, k, gpre);
                 const int i = __ldg(&T.rowVar[r]);
                 const int a = r - V.row0(i);
-                const bool present =
-                    __ldcg(&T.varSup[i]) && ((__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u);
-                if (present) {
+                const bool inDom = (__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u;
+                if (T.negative) {
+                    // counted by the full scan unless the valid forbidden tuples
+                    // are fewer than the value's combinations (a support then exists)
+                    if (inDom && __ldcg(&T.other[i]) <= (unsigned long long)__ldcg(&T.ctrl->tuples)) {
+                        const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
+                        T.hardRow[m] = r;
+                        T.foundChunk[m] = 0;
+                        atomicAdd(&T.ctrl->nscan, 1);
+                        atomicAdd(&C->nscanAll[round & 1], 1);
+                    }
+                } else if (__ldcg(&T.varSup[i]) && inDom) {
                     if (T.useResidues) {
                         res = T.residue[r];
                         hit = nz(and4(ld_sup(T.sup + (size_t)r * T.W4 + res), __ldcg(T.curr + res)));
@@ -653,13 +700,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
         if (nm > 0 && !sync()) return;
         phase(3);
 
-        if (nm > 0 && __ldcg(&C->nscanAll[round & 1]) > 0) {
-            // full scans of the values whose residues and windows missed
+        // (no write to nscanAll after the last barrier: every CTA reads the same count)
+        if (__ldcg(&C->nscanAll[round & 1]) > 0) {
+            // full scans of the values whose residues and windows missed, and
+            // the counts of a negative table's values
             for (int u = gwarp; u < totalUnits; u += nwarps) {
                 const int k = find_prefix(pU, nwork, u, gpre);
                 const TableDev& T = M.tabs[__ldcg(&work[k])];
                 if (__ldcg(&T.ctrl->nscan) == 0) continue;
-                scan_segment<U, true>(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
+                if (T.negative) count_segment(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
+                else scan_segment<U, true>(T, u - pre_at(pU, k, gpre), (int)__ldcg(&T.ctrl->nhard), nullptr);
             }
             if (!sync()) return;
             phase(4);
@@ -672,8 +722,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                 for (int m = tid; m < nh; m += kThreads) {
                     const int r = __ldcg(&T.hardRow[m]);
                     const int fc = __ldcg(&T.foundChunk[m]);
-                    if (fc >= 0 && fc != kNoChunk) T.residue[r] = fc;
-                    else remove_value(M, T, t, r, pruned);
+                    if (T.negative) {
+                        // fc: the value's valid forbidden tuples
+                        if ((unsigned long long)(unsigned)fc >= __ldcg(&T.other[T.rowVar[r]]))
+                            remove_value(M, T, t, r, pruned);
+                    } else if (fc >= 0 && fc != kNoChunk) {
+                        T.residue[r] = fc;
+                    } else {
+                        remove_value(M, T, t, r, pruned);
+                    }
                 }
             }
             if (!sync()) return;
@@ -706,6 +763,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                 const unsigned ns = (unsigned)__ldcg(&Tc->nscan);
                 if (ns) atomicAdd(&C->bytesFilter, 16ull * ns * live);
                 Tc->live = 0u; Tc->live_in = 0u; Tc->words_in = 0u; Tc->nhard = 0u; Tc->nrows = 0; Tc->nscan = 0;
+                Tc->tuples = 0u;
             }
             for (int t0 = gtid - lane; t0 < M.ntables; t0 += gth) {  // warp-uniform trip count
                 const int t = t0 + lane;
@@ -875,7 +933,7 @@ __global__ void ct_clone_state_kernel(const TableDev* __restrict__ src, const Ta
     for (int q = tid; q < S.nseg; q += nth) D.segMask[q] = S.segMask[q];
     for (int q = tid; q < S.R; q += nth) D.residue[q] = S.residue[q];
     for (int q = tid; q < S.DW; q += nth) D.lastDom[q] = S.lastDom[q];
-    for (int q = tid; q < S.arity; q += nth) D.changed[q] = 0;
+    for (int q = tid; q < S.arity; q += nth) D.other[q] = 0ull;
     if (tid == 0) {
         const int32_t cap = D.ctrl->trail_cap;
         const int32_t live = S.ctrl->live_state;

@@ -48,7 +48,6 @@ struct NaScratch {
     int32_t varSup[kNaMaxArity];
     int32_t planK[kNaMaxArity];
     int32_t planRowOff[kNaMaxArity];
-    int32_t changed[kNaMaxArity];
 };
 
 // The scratch of every ct_propagate_noalloc call on a device (about 32 KB).
@@ -91,7 +90,6 @@ __global__ void ct_noalloc_init_kernel(const __grid_constant__ NaInit p) {
         const uint32_t m = __ballot_sync(0xffffffffu, live);
         if (lane == 0) S->segMask[seg0 >> 5] = m;
     }
-    for (int q = tid; q < kNaMaxArity; q += nth) S->changed[q] = 0;
     if (tid == 0) {
         S->status[kSlotStatus] = kNaPending;
     }
@@ -192,7 +190,7 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     T.planK = S->planK;
     T.planRowOff = S->planRowOff;
     T.varSup = S->varSup;
-    T.changed = S->changed;
+    T.other = nullptr;  // positive tables only
     T.hardRow = S->hardRow;
     T.foundChunk = S->foundChunk;
     T.rowVar = S->rowVar;
@@ -212,7 +210,7 @@ extern "C" int ct_propagate_noalloc(int arity, const int32_t* dom_size, int64_t 
     }
 
     // The array keeps the previous call's contents: clear what must start at
-    // zero (counters and barrier, residues, changed flags), rebuild the
+    // zero (counters and barrier, residues), rebuild the
     // non-zero index from the caller's currTable, reload the row -> variable
     // map, reset the status word.
     NaInit init;

@@ -1309,10 +1309,6 @@ int search_batch(ct_model* m, int slots, int split_depth, bool split_assign, int
         ct_set_error("ct_search_batch: the model failed; restore a level first");
         return CT_ERR_STATE;
     }
-    if (m->hasNegative) {
-        ct_set_error("ct_search_batch: models with negative tables search with ct_search_dfs");
-        return CT_ERR_ARG;
-    }
     if (info) std::memset(info, 0, sizeof(*info));
     if (m->tables.empty() || m->staticInfeasible) {
         // nothing to propagate on the device: the plain search is the same search

@@ -344,7 +344,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = dalloc(ct, &d.planK, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.planRowOff, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.varSup, (size_t)n)) != CT_OK) return st;
-    if ((st = dalloc(ct, &d.changed, (size_t)n)) != CT_OK) return st;
+    if ((st = dalloc(ct, &d.other, (size_t)n)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.hardRow, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &d.foundChunk, (size_t)R)) != CT_OK) return st;
     if ((st = dalloc(ct, &rowVar, (size_t)R)) != CT_OK) return st;
@@ -424,7 +424,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     if ((st = upload(ct, varRow0, ct->row0)) != CT_OK) return st;
     if ((st = upload(ct, varNW, ct->nw)) != CT_OK) return st;
     if ((st = upload(ct, varLD, ct->ld)) != CT_OK) return st;
-    CT_CUDA(cudaMemsetAsync(d.changed, 0, (size_t)n * sizeof(int32_t), ct->stream));
+    CT_CUDA(cudaMemsetAsync(d.other, 0, (size_t)n * sizeof(unsigned long long), ct->stream));
 
     Ctrl c{};
     c.status = CT_OK;
@@ -675,7 +675,7 @@ std::vector<size_t> clone_pieces(const ct_table* src) {
     const size_t R = (size_t)src->R, n = (size_t)src->arity;
     const size_t tr = (size_t)clone_trail_entries(src);
     return {padChunks * sizeof(uint4), (size_t)src->nseg * 4, padChunks * 4, R * 4, (size_t)src->DW * 4, R * 4,
-            n * 4, n * 4, n * 4, n * 4, R * 4, R * 4,
+            n * 4, n * 4, n * 4, n * 8, R * 4, R * 4,
             (size_t)kCloneLevels * std::max(src->nseg, 1) * 4, (size_t)kCloneLevels * std::max(src->DW, 1) * 4,
             tr * sizeof(int2), tr * sizeof(uint4)};
 }
@@ -751,7 +751,7 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* 
         d.planK = static_cast<int32_t*>(p[6]);
         d.planRowOff = static_cast<int32_t*>(p[7]);
         d.varSup = static_cast<int32_t*>(p[8]);
-        d.changed = static_cast<int32_t*>(p[9]);
+        d.other = static_cast<unsigned long long*>(p[9]);
         d.hardRow = static_cast<int32_t*>(p[10]);
         d.foundChunk = static_cast<int32_t*>(p[11]);
         d.levelSeg = static_cast<uint32_t*>(p[12]);
@@ -780,7 +780,7 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* 
         (st = dalloc(ct, &d.planK, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.planRowOff, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.varSup, (size_t)ct->arity)) != CT_OK ||
-        (st = dalloc(ct, &d.changed, (size_t)ct->arity)) != CT_OK ||
+        (st = dalloc(ct, &d.other, (size_t)ct->arity)) != CT_OK ||
         (st = dalloc(ct, &d.hardRow, (size_t)ct->R)) != CT_OK || (st = dalloc(ct, &d.foundChunk, (size_t)ct->R)) != CT_OK) {
         free_table(ct);
         *status = st;

@@ -105,8 +105,120 @@ def test_network_with_negative_tables_search(seed):
     assert (got["nodes"], got["fails"], got["solutions"]) == (want.nodes, want.fails, want.solutions)
     if want.solutions:
         assert got["first_solution"] == want.first_solution
-    assert C.ct_search_batch(h, nv, 4, 1)[0] == C.CT_ERR_ARG
+    # the batched searches: host-stepped and on the device
+    for slots, split in ((4, 1), (16, 3)):
+        st, got, _ = C.ct_search_batch(h, nv, slots, split, 0, True)
+        assert st == C.CT_OK, C.last_error()
+        assert (got["nodes"], got["fails"], got["solutions"]) == (want.nodes, want.fails, want.solutions)
+        assert got["max_depth"] == want.max_depth
+        if want.solutions:
+            assert got["first_solution"] == want.first_solution
+        st, got, _ = C.ct_search_batch_device(h, nv, slots, split)
+        assert st == C.CT_OK, C.last_error()
+        assert (got["nodes"], got["fails"], got["solutions"]) == (want.nodes, want.fails, want.solutions)
     C.ct_model_destroy(h)
+
+
+def _mixed_network(seed, nv, d, ntables, arity, t_pos, t_neg, every=2):
+    """Tables over random scopes, every `every`-th one negative: the library's
+    form (forbidden tuples for the negative ones) and the oracle's network of
+    allowed tuples (a negative table's complement)."""
+    rng = G.Rng(seed)
+    allowed = O.Csp([0] * nv, [d] * nv)
+    raw = []
+    for k in range(ntables):
+        sc = G.random_scope(rng, nv, arity)
+        neg = k % every == 0
+        tt = G.cap_distinct([d] * arity, t_neg if neg else t_pos)
+        tup = G.distinct_uniform_tuples(G.derive_seed(seed, k), [0] * arity, [d] * arity, tt)
+        if neg:
+            ret = N.retained_negative(tup, [0] * arity, [d] * arity)
+            allowed.add_table(sc, N.complement(ret, [0] * arity, [d] * arity))
+        else:
+            allowed.add_table(sc, tup)
+        raw.append((sc, tup, neg))
+    return allowed, raw
+
+
+def _mixed_model(allowed, raw, host_fixpoint):
+    torch = torch_cuda()
+    st, h = C.ct_model_create(allowed.dom_lo, allowed.dom_size, opt=C.make_options(host_fixpoint=host_fixpoint),
+                              stream=torch.cuda.current_stream())
+    assert st == C.CT_OK, C.last_error()
+    for sc, tup, neg in raw:
+        assert C.ct_model_add_table(h, sc, tup, negative=neg) >= 0, C.last_error()
+    return h
+
+
+def _model_masks(h, csp):
+    off, _ = C.dom_layout(csp.dom_size)
+    st, w = C.ct_model_get_domains(h, int(off[-1]))
+    assert st == C.CT_OK
+    return C.words_to_masks(w, csp.dom_size)
+
+
+@pytest.mark.parametrize("mode", [pytest.param(0, id="device_fixpoint"), pytest.param(1, id="host_queue")])
+@pytest.mark.parametrize("seed", range(4))
+def test_network_fixpoint_with_negative_tables(seed, mode):
+    """The fixpoint of a network of positive and negative tables equals the
+    oracle's GAC closure of the allowed tuples, from the initial domains and
+    after random domain cuts (each undone by a restore)."""
+    allowed, raw = _mixed_network(8200 + seed, nv=10, d=5, ntables=9, arity=3, t_pos=80, t_neg=45)
+    h = _mixed_model(allowed, raw, mode)
+    st = C.ct_model_propagate(h)
+    st_o, masks_o, _ = O.gac_network(allowed, allowed.full_masks())
+    assert st == st_o, C.last_error()
+    if st != C.CT_OK:
+        C.ct_model_destroy(h)
+        return
+    for a, b in zip(_model_masks(h, allowed), masks_o):
+        assert np.array_equal(a, b)
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for step in range(6):
+        st, lv = C.ct_model_save(h)
+        assert st == C.CT_OK
+        before = _model_masks(h, allowed)
+        cut = [m.copy() for m in before]
+        for v in rng.choice(allowed.nvars, size=2, replace=False):
+            vals = np.flatnonzero(cut[v])
+            if len(vals) > 1:
+                cut[v][rng.choice(vals, size=len(vals) // 2, replace=False)] = False
+        assert C.ct_model_set_domains(h, C.masks_to_words(cut)) == C.CT_OK
+        st = C.ct_model_propagate(h)
+        st_o, mo, _ = O.gac_network(allowed, cut)
+        assert st == st_o, (step, C.last_error())
+        if st == C.CT_OK:
+            checked += 1
+            for a, b in zip(_model_masks(h, allowed), mo):
+                assert np.array_equal(a, b), step
+        assert C.ct_model_restore(h, lv) == C.CT_OK
+        for a, b in zip(_model_masks(h, allowed), before):
+            assert np.array_equal(a, b)
+    C.ct_model_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_negative_only_network_reaches_the_closure(seed):
+    """Networks of negative tables only (each pass of one may enable another
+    removal by the same table): the one-launch fixpoint, the host queue and
+    the oracle agree, and so do the searches."""
+    allowed, raw = _mixed_network(8300 + seed, nv=7, d=4, ntables=6, arity=3, t_pos=0, t_neg=30, every=1)
+    st_o, masks_o, _ = O.gac_network(allowed, allowed.full_masks())
+    want = O.dfs(allowed)
+    for mode in (0, 1):
+        h = _mixed_model(allowed, raw, mode)
+        st = C.ct_model_propagate(h)
+        assert st == st_o, C.last_error()
+        if st == C.CT_OK:
+            for a, b in zip(_model_masks(h, allowed), masks_o):
+                assert np.array_equal(a, b)
+        C.ct_model_destroy(h)
+        h = _mixed_model(allowed, raw, mode)
+        st, got = C.ct_search_dfs(h, allowed.nvars, 0, True)
+        assert st == C.CT_OK, C.last_error()
+        assert (got["nodes"], got["fails"], got["solutions"]) == (want.nodes, want.fails, want.solutions)
+        C.ct_model_destroy(h)
 
 
 def test_negative_table_arguments():
