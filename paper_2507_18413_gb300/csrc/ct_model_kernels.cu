@@ -53,6 +53,18 @@ __device__ __forceinline__ int find_prefix(const int32_t* pre, int n, int u, boo
     return lo + (31 - __clz(b));
 }
 
+// The same search by one lane for its own u (binary search: the lanes of a
+// warp look up different units at once).
+__device__ __forceinline__ int lane_find_prefix(const int32_t* pre, int n, int u, bool global) {
+    int lo = 0, hi = n - 1;  // pre[lo] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre_at(pre, mid, global) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Exclusive prefixes of the segments and of the supports rows of work[k] over
 // k < n into unitOut[0..n] and rowOut[0..n] (one CTA): each thread sums a run
 // of entries, warps scan by shuffles, warp totals go through shared memory.
@@ -586,22 +598,54 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
         const int totalUnits = pre_at(pU, nwork, gpre);
         const int totalRows = pre_at(pR, nwork, gpre);
 
-        // updateTable (Algorithm 2) over (table, segment) units
-        for (int u = gwarp; u < totalUnits; u += nwarps) {
-            const int k = find_prefix(pU, nwork, u, gpre);
-            const int t = __ldcg(&work[k]);
-            const TableDev& T = M.tabs[t];
-            const int nrows = __ldcg(&T.ctrl->nrows);
+        // updateTable (Algorithm 2) over (table, segment) units, unit u to warp
+        // u % nwarps (a crowded table's segments spread over the grid). A warp
+        // looks up the tables of its next 32 units at once (one lane each:
+        // work-list entry, row count, mark), and loads the next unit's segment
+        // state while the current unit's rows are read.
+        for (int ub = gwarp; ub < totalUnits; ub += 32 * nwarps) {
+            const int ul = ub + lane * nwarps;
+            int lt = 0, lseg = 0, lrows = 0, lmark = -1, lneg = 0;
+            if (ul < totalUnits) {
+                const int k = lane_find_prefix(pU, nwork, ul, gpre);
+                lt = __ldcg(&work[k]);
+                lseg = ul - pre_at(pU, k, gpre);
+                lrows = __ldcg(&M.tabs[lt].ctrl->nrows);
+                lmark = __ldcg(&M.calls[lt].mark);
+                lneg = M.tabs[lt].negative;
+            }
             // a negative table goes through even with no row to OR: its
             // filter compares counts with the valid tuples left
-            if (nrows == 0 && !T.negative) continue;
-            const int seg = u - pre_at(pU, k, gpre);
-            const int mark = __ldcg(&M.calls[t].mark);
-            const SegState S = load_segment(T, seg, mark);
-            TrailItem it;
-            update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
-                                    reinterpret_cast<uint32_t*>(&T.ctrl->live), &T.ctrl->tuples, it);
-            trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
+            const bool lwork = ul < totalUnits && (lrows > 0 || lneg);
+            const unsigned todo = __ballot_sync(0xffffffffu, lwork);
+            SegState next;
+            next.mask = 0u;
+            int j = todo ? __ffs(todo) - 1 : 32;
+            if (j < 32) {
+                const int t0 = __shfl_sync(0xffffffffu, lt, j);
+                next = load_segment(M.tabs[t0], __shfl_sync(0xffffffffu, lseg, j),
+                                    __shfl_sync(0xffffffffu, lmark, j));
+            }
+            while (j < 32) {
+                const int t = __shfl_sync(0xffffffffu, lt, j);
+                const int seg = __shfl_sync(0xffffffffu, lseg, j);
+                const int nrows = __shfl_sync(0xffffffffu, lrows, j);
+                const int mark = __shfl_sync(0xffffffffu, lmark, j);
+                const SegState S = next;
+                const unsigned rest = todo & ~((2u << j) - 1u);
+                const int jn = rest ? __ffs(rest) - 1 : 32;
+                if (jn < 32) {
+                    const int tn = __shfl_sync(0xffffffffu, lt, jn);
+                    next = load_segment(M.tabs[tn], __shfl_sync(0xffffffffu, lseg, jn),
+                                        __shfl_sync(0xffffffffu, lmark, jn));
+                }
+                const TableDev& T = M.tabs[t];
+                TrailItem it;
+                update_segment<U, true>(T, mark, 0, 0, seg, S, nrows, nullptr,
+                                        reinterpret_cast<uint32_t*>(&T.ctrl->live), &T.ctrl->tuples, it);
+                trail_warp(T, it, __ldcg(&T.ctrl->trail_cap), &C->status);
+                j = jn;
+            }
         }
         if (!sync()) return;
         phase(2);
