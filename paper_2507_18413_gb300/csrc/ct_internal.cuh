@@ -44,6 +44,7 @@ constexpr int kWindowGroups = 8;         // index segments read for them: at mos
 constexpr unsigned kBarrierSpinLimit = 1u << 24;  // default polls of a grid-barrier wait
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
 constexpr int kParamArity = 16;        // scopes up to this arity carry their layout in kernel parameters
+constexpr int kParamDomWords = 16;     // host-buffer calls of up to this many domain words pass them as parameters
 
 // Status block header slots (written to mapped host memory after every call).
 enum StatusSlot {
@@ -142,6 +143,9 @@ struct CallParams {
     uint32_t spinLimit;  // polls of a grid-barrier wait before it gives up (CT_ERR_TIMEOUT)
     int32_t maxSplit;    // most warps that share one segment's row list (1, 2, 4 or 8)
     int32_t domOff[kParamArity];  // word offset of each scope domain (arity <= kParamArity)
+    int32_t domInParams;          // 1: the domains are domWords (local plan only); the result
+                                  // leaves through the status block alone
+    uint32_t domWords[kParamDomWords];
 };
 
 // Dynamic shared memory of the propagation kernel: the partial results of the
@@ -330,7 +334,7 @@ int ct_cuda_fail(cudaError_t e, const char* what);
 
 // Internal table entry points used by the model (ct_table.cu).
 int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
-                          uint32_t* changed);
+                          uint32_t* changed, const uint32_t* domHost = nullptr);
 const int32_t* ct_table_status_host(const ct_table* ct);
 int ct_table_is_empty(const ct_table* ct);
 int ct_table_restore_device(ct_table* ct, const ctk::RestoreDesc& d);

@@ -131,7 +131,7 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
                 // Algorithm 3 line 4: no live tuple carries the value.
                 const int i = T.rowVar[r];
                 const int a = r - V.row0(i);
-                atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
+                if (dom) atomicAnd(&dom[V.off(i) + (a >> 5)], ~(1u << (a & 31)));
                 if (smemDom) atomicAnd(&sm.dom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 // a positive table's removed value carries no valid tuple, so
                 // lastDom may drop it now; a negative table's value still has
@@ -221,6 +221,12 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
     const VarLayout V(T, P.domOff, domOff);
+    // Host-buffer calls of local-plan tables pass the domains as parameters:
+    // the plan reads them there, and the result leaves through the status
+    // block alone (the finalizing CTA publishes it from its shared copy).
+    const bool domParams = kLocal && P.domInParams;
+    const uint32_t* domIn = domParams ? P.domWords : dom;
+    uint32_t* domOut = domParams ? nullptr : dom;
     GridBarrier bar;
     bar_init(bar, &C->bar_count, &C->bar_base, &C->status, P.spinLimit ? P.spinLimit : kBarrierSpinLimit);
     if (blockIdx.x == 0 && tid == 0) C->t[0] = gtimer();
@@ -243,7 +249,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     bool ok;
     if (kLocal) {
         const bool snap = blockIdx.x == 0;
-        plan(T, V, dom, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm, snap ? P.snapFrom : 0, snap ? P.snapTo : 0);
+        plan(T, V, domIn, sm.k, sm.rowOff, sm.sup, sm.codes, sm.dom, sm, snap ? P.snapFrom : 0, snap ? P.snapTo : 0);
         ok = !(sm.flags[0] || sm.flags[1]);
         nrows = sm.flags[6];
         if (T.negative && ok) {
@@ -302,7 +308,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         }
         if (!ok) {
             // Domain error or empty domain: publish without filtering.
-            if (blockIdx.x == 0) finalize(T, V, dom, sm, 0, 0ull, kLocal);
+            if (blockIdx.x == 0) finalize(T, V, domOut, sm, 0, 0ull, kLocal);
             return;
         }
         if (blockIdx.x == 0 && tid == 0) {
@@ -411,7 +417,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
             if (r1 == 2) {
                 if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
                 __syncthreads();
-                finalize(T, V, dom, sm, 0, 0ull, kLocal);
+                finalize(T, V, domOut, sm, 0, 0ull, kLocal);
             }
             return;
         }
@@ -482,7 +488,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     // it publishes: with none left undecided (every value kept its support,
     // or its windows covered every live chunk) it removes the unsupported
     // values and publishes, and the others are done.
-    if (r2 == 2 && finalize(T, V, dom, sm, -1, t3, kLocal)) {
+    if (r2 == 2 && finalize(T, V, domOut, sm, -1, t3, kLocal)) {
         CT_STAMP(6);
         return;
     }
@@ -514,7 +520,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     CT_STAMP(14);
     if (!sm.flag[1]) return;
     __threadfence();
-    finalize(T, V, dom, sm, nh, 0ull, kLocal);
+    finalize(T, V, domOut, sm, nh, 0ull, kLocal);
     CT_STAMP(7);
 }
 

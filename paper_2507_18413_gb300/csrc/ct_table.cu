@@ -512,9 +512,13 @@ int drain_events(ct_table* ct) {
 
 }  // namespace
 
+// domHost (host memory, the table's packed layout; local-plan tables with at
+// most kParamDomWords domain words): the domains travel in the kernel
+// parameters instead of `dom`, which may then be null; the filtered domains
+// are in the status block when the call returns.
 int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev, const int32_t* domOffHost,
-                          uint32_t* changed) {
-    if (!ct || !dom) {
+                          uint32_t* changed, const uint32_t* domHost) {
+    if (!ct || (!dom && !domHost)) {
         ct_set_error("ct_propagate: null argument");
         return CT_ERR_ARG;
     }
@@ -546,6 +550,14 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.spinLimit = kBarrierSpinLimit;
     P.maxSplit = ct->maxSplit;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
+    if (domHost) {
+        if (!ct->localPlan || ct->DW > kParamDomWords) {
+            ct_set_error("ct_propagate: domains in parameters need a local plan and <= %d words", kParamDomWords);
+            return CT_ERR_ARG;
+        }
+        P.domInParams = 1;
+        std::memcpy(P.domWords, domHost, (size_t)ct->DW * sizeof(uint32_t));
+    }
     hv[kSlotStatus] = kNoChunk;  // overwritten by the kernel's last CTA
     if (ct->armPolls) {
         // Test hook (ct_arm_wait_timeout): an arrival count 2^30 behind every
@@ -1006,9 +1018,15 @@ extern "C" int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t
         return CT_ERR_ARG;
     }
     if (ct->empty) return ct_table_propagate_on(ct, dom_bits_host, nullptr, nullptr, changed_vars);
-    CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, dom_bits_host, (size_t)ct->DW * sizeof(uint32_t),
-                            cudaMemcpyHostToDevice, ct->stream));
-    const int st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, ct->ld.data(), changed_vars);
+    int st;
+    if (ct->localPlan && ct->DW <= kParamDomWords && !ct->copyState) {
+        // a few domain words: they go to the device with the launch itself
+        st = ct_table_propagate_on(ct, nullptr, ct->dev.varLD, ct->ld.data(), changed_vars, dom_bits_host);
+    } else {
+        CT_CUDA(cudaMemcpyAsync(ct->d_domScratch, dom_bits_host, (size_t)ct->DW * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, ct->stream));
+        st = ct_table_propagate_on(ct, ct->d_domScratch, ct->dev.varLD, ct->ld.data(), changed_vars);
+    }
     if (st == CT_OK && ct->h_status[kSlotPruned] > 0) {
         // Only the variables that lost values differ from the input.
         const int32_t* h = ct->h_status;

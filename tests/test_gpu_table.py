@@ -362,6 +362,61 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     gt.close()
 
 
+@pytest.mark.parametrize("arity,d,t", [(6, 32, 20_000), (3, 1000, 5_000)])
+def test_host_buffer_calls_with_backtracking(arity, d, t):
+    """ct_propagate_host over a delta/reset stream with saves, restores and
+    wipe-outs: status, domains and changed mask equal the oracle's call by
+    call. With 6 words of domains they travel in the launch parameters (up to
+    16 words do); with 96 words (d = 1000) they are copied."""
+    seed = 7100 + d
+    dom_lo, dom_size, tup = G.large_table(seed, t, arity, d)
+    tup_ret = O.retained_tuples(tup, dom_lo, dom_size)
+    gt = GpuTable(dom_lo, dom_size, tup)
+    nch = (arity + 31) // 32
+    rng = G.Rng(G.derive_seed(seed, 1))
+    root = [np.ones(x, bool) for x in dom_size]
+    assert gt.save() == 0
+    masks, depth, seen = root, 0, {"ok": 0, "fail": 0, "pruned": 0}
+    for k in range(40):
+        gt.save()
+        new, _ = G.reset_step(rng, masks) if k % 2 else G.delta_step(rng, masks)
+        words = C.masks_to_words(new)
+        st, ch = C.ct_propagate_host(gt.h, words, nch)
+        st_o, out_o, _ = oracle_step(tup_ret, dom_lo, new)
+        assert st == st_o, (k, C.last_error())
+        depth += 1
+        if st != O.OK:
+            seen["fail"] += 1
+            gt.restore(1)  # the dive's first save: the root state (level 0 stays)
+            masks, depth = root, 0
+            continue
+        seen["ok"] += 1
+        got = C.words_to_masks(words, dom_size)
+        changed = 0
+        for i in range(arity):
+            assert np.array_equal(got[i], out_o[i]), (k, i)
+            if not np.array_equal(out_o[i], new[i]):
+                changed |= 1 << i
+        assert int(ch[0]) == changed, k
+        seen["pruned"] += changed != 0
+        masks = out_o
+        if depth >= 8:
+            gt.restore(1)
+            masks, depth = root, 0
+    # a grown domain is refused on the host path as on the device path
+    gt.restore(0)
+    gt.save()
+    cut = [m.copy() for m in root]
+    cut[0][np.flatnonzero(cut[0])[1:]] = False
+    st, _ = C.ct_propagate_host(gt.h, C.masks_to_words(cut), nch)
+    assert st in (C.CT_OK, C.CT_INFEASIBLE)
+    if st == C.CT_OK:
+        st, _ = C.ct_propagate_host(gt.h, C.masks_to_words(root), nch)
+        assert st == C.CT_ERR_STATE
+    assert seen["ok"] > 0 and seen["pruned"] > 0, seen
+    gt.close()
+
+
 def test_profiling_switched_on_and_off():
     """ct_set_profile: calls are timed only while profiling is on; results
     are the oracle's either way."""
