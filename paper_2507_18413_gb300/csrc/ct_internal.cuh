@@ -44,6 +44,7 @@ constexpr int kWindowGroups = 8;         // index segments read for them: at mos
 constexpr unsigned kBarrierSpinLimit = 1u << 24;  // default polls of a grid-barrier wait
 constexpr int kHostWaitMs = 2000;      // host poll of the status word before a stream sync
 constexpr int kParamArity = 16;        // scopes up to this arity carry their layout in kernel parameters
+constexpr int kWarpPlanWords = 4;      // domain words per variable a one-warp plan holds in registers
 constexpr int kParamDomWords = 16;     // host-buffer calls of up to this many domain words pass them as parameters
 
 // Status block header slots (written to mapped host memory after every call).
@@ -129,6 +130,8 @@ struct TableDev {
     int32_t negative;        // 1: the tuples are forbidden (negative table)
     int32_t shard;           // 1: a word-range shard (one-table kernel only): no failure on an
                              // empty currTable, lastDom keeps the call's input domains
+    int32_t warpPlan;        // 1: the network kernel plans it with one warp (positive, arity
+                             // <= 32, every domain <= kWarpPlanWords words)
     // Scopes of at most kParamArity variables: words, lastDom offset and first
     // supports row of each variable, so that the plan reads no global table.
     int32_t pNW[kParamArity], pLD[kParamArity], pRow0[kParamArity];

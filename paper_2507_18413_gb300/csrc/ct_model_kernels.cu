@@ -73,11 +73,19 @@ __device__ void work_prefix(const ModelDev& M, const int32_t* work, int n, int32
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n + kThreads - 1) / kThreads;
     const int b0 = tid * per, b1 = min(n, b0 + per);
+    // the run's tables eight at a time, their loads issued together
+    constexpr int kB = 8;
     int su = 0, sr = 0;
-    for (int k = b0; k < b1; ++k) {
-        const TableDev& T = M.tabs[__ldcg(&work[k])];
-        su += T.nseg;
-        sr += T.R;
+    for (int k0 = b0; k0 < b1; k0 += kB) {
+        int t[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) t[u] = k0 + u < b1 ? __ldcg(&work[k0 + u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (t[u] >= 0) {
+                su += M.tabs[t[u]].nseg;
+                sr += M.tabs[t[u]].R;
+            }
     }
     int iu = su, ir = sr;
 #pragma unroll
@@ -104,18 +112,109 @@ __device__ void work_prefix(const ModelDev& M, const int32_t* work, int n, int32
         tu += wu;
         tr += wr;
     }
-    for (int k = b0; k < b1; ++k) {
-        const TableDev& T = M.tabs[__ldcg(&work[k])];
-        unitOut[k] = ru;
-        rowOut[k] = rr;
-        ru += T.nseg;
-        rr += T.R;
+    for (int k0 = b0; k0 < b1; k0 += kB) {
+        int t[kB], ns[kB], nr[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) t[u] = k0 + u < b1 ? __ldcg(&work[k0 + u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            ns[u] = t[u] >= 0 ? M.tabs[t[u]].nseg : 0;
+            nr[u] = t[u] >= 0 ? M.tabs[t[u]].R : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (t[u] >= 0) {
+                unitOut[k0 + u] = ru;
+                rowOut[k0 + u] = rr;
+                ru += ns[u];
+                rr += nr[u];
+            }
     }
     if (tid == 0) {
         unitOut[n] = tu;
         rowOut[n] = tr;
     }
     __syncthreads();
+}
+
+// Algorithm 1 lines 1-3 and the row list of Algorithm 2 for a table with
+// warpPlan set, by one warp (lane i holds variable i and its domain words in
+// registers): the outputs of plan() in global mode (row counts and delta
+// flags, first code of each variable, s_sup, row codes in variable order,
+// each variable's last code marked) and the table's call counters. A domain
+// that grew since the table's last propagation is a state error; an empty one
+// fails the table's node.
+__device__ void plan_warp(const ModelDev& M, const TableDev& T, const VarLayout& V, int t) {
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const bool own = lane < T.arity;
+    uint32_t d[kWarpPlanWords], l[kWarpPlanWords];
+    int nw = 0, nd = 0, ndel = 0;
+    uint32_t grow = 0u;
+    if (own) {
+        nw = V.nw(lane);
+        const uint32_t* dp = M.dom + V.off(lane);
+        const uint32_t* lp = T.lastDom + V.ld(lane);
+#pragma unroll
+        for (int q = 0; q < kWarpPlanWords; ++q) {
+            d[q] = q < nw ? __ldcg(dp + q) : 0u;
+            l[q] = q < nw ? __ldcg(lp + q) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kWarpPlanWords; ++q) {
+            grow |= d[q] & ~l[q];
+            nd += __popc(d[q]);
+            ndel += __popc(l[q] & ~d[q]);
+        }
+    }
+    // Algorithm 2, line 3: the delta mask when |Delta| < |dom| (strict)
+    const bool delta = ndel > 0 && ndel < nd;
+    const int k = ndel > 0 ? (delta ? ndel : nd) : 0;
+    const bool bad = __ballot_sync(FULL, grow != 0u) != 0u;
+    const bool empty = __ballot_sync(FULL, own && nd == 0) != 0u;
+    const int nval = __popc(__ballot_sync(FULL, ndel > 0));
+    const int ndelta = __popc(__ballot_sync(FULL, delta));
+    const int nsup = __popc(__ballot_sync(FULL, nd > 1));
+    if (own) {
+        T.planK[lane] = delta ? (k | kCodeDelta) : k;
+        T.varSup[lane] = nd > 1;
+    }
+    int rows = (bad || empty) ? 0 : k;
+    int incl = rows;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += a;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (own) T.planRowOff[lane] = incl - rows;
+    if (rows > 0) {
+        const int row0 = V.row0(lane);
+        int out = incl - rows;
+        const int last = incl - 1;
+#pragma unroll
+        for (int q = 0; q < kWarpPlanWords; ++q) {
+            uint32_t bits = delta ? (l[q] & ~d[q]) : d[q];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                int code = row0 + q * 32 + b;
+                if (delta) code |= kCodeDelta;
+                if (out == last) code |= kCodeLast;
+                T.codes[out++] = code;
+            }
+        }
+    }
+    if (lane == 0) {
+        Ctrl* Tc = T.ctrl;
+        Tc->nrows = total;
+        Tc->nval = nval;
+        Tc->ndelta = ndelta;
+        Tc->nreset = nval - ndelta;
+        Tc->nsup = nsup;
+        if (bad) atomicCAS(&M.ctrl->status, CT_OK, CT_ERR_STATE);
+        else if (empty) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;
+    }
 }
 
 // Value r of table t has no support: clear it from the shared domains and, for
@@ -528,56 +627,93 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
             C->nscanAll[(round + 1) & 1] = 0;
         }
 
-        // plan (Algorithm 1 lines 1-3), one CTA per table of the round
-        for (int k = blockIdx.x; k < nwork; k += gridDim.x) {
-            const int t = __ldcg(&work[k]);
-            const TableDev& T = M.tabs[t];
-            const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
-            // Levels saved since the table's last propagation all hold its state
-            // as it is now: one snapshot, in the lowest one's slot, taken before
-            // this launch first changes the table (a table this launch does not
-            // propagate keeps them pending).
-            ModelTabCall cl;
-            cl.mark = __ldcg(&M.calls[t].mark);
-            cl.snapFrom = __ldcg(&M.calls[t].snapFrom);
-            cl.snapTo = __ldcg(&M.calls[t].snapTo);
-            if (cl.snapFrom < cl.snapTo && __ldcg(&M.snapTaken[t]) == 0) {
-                const size_t l = (size_t)cl.snapFrom;
-                for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[l * T.nseg + q] = __ldcg(&T.segMask[q]);
-                for (int q = tid; q < T.DW; q += kThreads) T.levelDom[l * T.DW + q] = __ldcg(&T.lastDom[q]);
-                if (tid == 0) M.snapTaken[t] = 1;
-            }
-            plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
-            if (T.negative && tid == 0 && !sm.flags[0] && !sm.flags[1]) {
-                // a value of x_i loses its support when its valid forbidden
-                // tuples are all prod_{j != i} |D_j| combinations: the products,
-                // saturated at 2^62
-                const unsigned long long cap = 1ull << 62;
-                auto mul = [&](unsigned long long x, unsigned long long y) {
-                    return (y != 0 && x > cap / y) ? cap : x * y;
-                };
-                unsigned long long pre = 1ull;
-                for (int i = 0; i < T.arity; ++i) {
-                    T.other[i] = pre;
-                    pre = mul(pre, (unsigned long long)sm.nd[i]);
-                }
-                unsigned long long suf = 1ull;
-                for (int i = T.arity - 1; i >= 0; --i) {
-                    T.other[i] = mul(T.other[i], suf);
-                    suf = mul(suf, (unsigned long long)sm.nd[i]);
+        // plan (Algorithm 1 lines 1-3): one warp per small table (warpPlan), by
+        // the warps of every CTA but the last, which computes the round's
+        // prefixes; one CTA per other table
+        {
+            const int planCtas = gridDim.x > 1 ? gridDim.x - 1 : 1;
+            if (blockIdx.x < planCtas) {
+                for (int k = gwarp; k < nwork; k += planCtas * kWarps) {
+                    const int t = __ldcg(&work[k]);
+                    const TableDev& T = M.tabs[t];
+                    if (!T.warpPlan) continue;
+                    const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+                    // the pending level snapshot, as in the CTA path below
+                    const int sf = __ldcg(&M.calls[t].snapFrom), stp = __ldcg(&M.calls[t].snapTo);
+                    if (sf < stp && __ldcg(&M.snapTaken[t]) == 0) {
+                        const size_t l = (size_t)sf;
+                        for (int q = lane; q < T.nseg; q += 32) T.levelSeg[l * T.nseg + q] = __ldcg(&T.segMask[q]);
+                        for (int q = lane; q < T.DW; q += 32) T.levelDom[l * T.DW + q] = __ldcg(&T.lastDom[q]);
+                        __syncwarp();
+                        if (lane == 0) M.snapTaken[t] = 1;
+                    }
+                    __syncwarp();  // the snapshot reads lastDom before the plan's loads of it
+                    plan_warp(M, T, V, t);
                 }
             }
-            if (tid == 0) {
-                Ctrl* Tc = T.ctrl;
-                Tc->nrows = sm.flags[6];
-                Tc->nval = sm.flags[2];
-                Tc->ndelta = sm.flags[3];
-                Tc->nreset = sm.flags[4];
-                Tc->nsup = sm.flags[5];
-                if (sm.flags[0]) atomicCAS(&C->status, CT_OK, CT_ERR_STATE);
-                else if (sm.flags[1]) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;  // an empty domain
+        }
+        // the CTA's share of the work list (entries blockIdx.x + j * gridDim.x),
+        // 256 entries tested at once (one per thread); the tables without a
+        // warp plan are planned one after the other by the whole CTA
+        // (sm.codes is free until the round's prefixes are staged)
+        for (int k0 = blockIdx.x; k0 < nwork; k0 += gridDim.x * kThreads) {
+            const int kt = k0 + tid * gridDim.x;
+            const bool need = kt < nwork && !M.tabs[__ldcg(&work[kt])].warpPlan;
+            sm.codes[tid] = need ? kt : -1;
+            if (!__syncthreads_or(need)) continue;
+            for (int j = 0; j < kThreads; ++j) {
+                const int k = sm.codes[j];
+                if (k < 0) continue;  // the same for every thread of the CTA
+                const int t = __ldcg(&work[k]);
+                const TableDev& T = M.tabs[t];
+                const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
+                // Levels saved since the table's last propagation all hold its state
+                // as it is now: one snapshot, in the lowest one's slot, taken before
+                // this launch first changes the table (a table this launch does not
+                // propagate keeps them pending).
+                ModelTabCall cl;
+                cl.mark = __ldcg(&M.calls[t].mark);
+                cl.snapFrom = __ldcg(&M.calls[t].snapFrom);
+                cl.snapTo = __ldcg(&M.calls[t].snapTo);
+                if (cl.snapFrom < cl.snapTo && __ldcg(&M.snapTaken[t]) == 0) {
+                    const size_t l = (size_t)cl.snapFrom;
+                    for (int q = tid; q < T.nseg; q += kThreads) T.levelSeg[l * T.nseg + q] = __ldcg(&T.segMask[q]);
+                    for (int q = tid; q < T.DW; q += kThreads) T.levelDom[l * T.DW + q] = __ldcg(&T.lastDom[q]);
+                    if (tid == 0) M.snapTaken[t] = 1;
+                }
+                plan(T, V, M.dom, T.planK, T.planRowOff, T.varSup, T.codes, nullptr, sm);
+                if (T.negative && tid == 0 && !sm.flags[0] && !sm.flags[1]) {
+                    // a value of x_i loses its support when its valid forbidden
+                    // tuples are all prod_{j != i} |D_j| combinations: the products,
+                    // saturated at 2^62
+                    const unsigned long long cap = 1ull << 62;
+                    auto mul = [&](unsigned long long x, unsigned long long y) {
+                        return (y != 0 && x > cap / y) ? cap : x * y;
+                    };
+                    unsigned long long pre = 1ull;
+                    for (int i = 0; i < T.arity; ++i) {
+                        T.other[i] = pre;
+                        pre = mul(pre, (unsigned long long)sm.nd[i]);
+                    }
+                    unsigned long long suf = 1ull;
+                    for (int i = T.arity - 1; i >= 0; --i) {
+                        T.other[i] = mul(T.other[i], suf);
+                        suf = mul(suf, (unsigned long long)sm.nd[i]);
+                    }
+                }
+                if (tid == 0) {
+                    Ctrl* Tc = T.ctrl;
+                    Tc->nrows = sm.flags[6];
+                    Tc->nval = sm.flags[2];
+                    Tc->ndelta = sm.flags[3];
+                    Tc->nreset = sm.flags[4];
+                    Tc->nsup = sm.flags[5];
+                    if (sm.flags[0]) atomicCAS(&C->status, CT_OK, CT_ERR_STATE);
+                    else if (sm.flags[1]) M.nodeStatus[t / M.nodeTables] = CT_INFEASIBLE;  // an empty domain
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            __syncthreads();  // sm.codes is rewritten by the next stride
         }
         // the prefixes by the last CTA, which plans no table when the work
         // list is shorter than the grid

@@ -369,6 +369,9 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
     d.DW = DW;
     d.nChangedWords = ct->nChW;
     d.useResidues = (opt && opt->no_residues) ? 0 : 1;
+    d.warpPlan = (!ct->negative && n <= 32) ? 1 : 0;
+    for (int i = 0; i < n; ++i)
+        if (ct->nw[i] > kWarpPlanWords) d.warpPlan = 0;
     for (int i = 0; i < n && i < kParamArity; ++i) {
         d.pNW[i] = ct->nw[i];
         d.pLD[i] = ct->ld[i];
