@@ -209,8 +209,11 @@ int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size,
  */
 int ct_propagate(ct_table* ct, uint32_t* dom_bits, uint32_t* changed_vars);
 
-/* ct_propagate_host: as ct_propagate, with dom_bits in host memory; the
- * domains are copied to the device and the filtered domains back. */
+/* ct_propagate_host: as ct_propagate, with dom_bits in host memory, filtered
+ * in place on CT_OK. Domains of at most 16 words in all (tables whose plan
+ * fits in shared memory) travel to the device inside the launch's parameters,
+ * larger ones by a copy; the filtered domains come back through the mapped
+ * status block of the call. */
 int ct_propagate_host(ct_table* ct, uint32_t* dom_bits_host, uint32_t* changed_vars);
 
 /* ct_save: push a backtrack level (the trail of Sec. 4: MiniCP alternates
