@@ -823,6 +823,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                 const TableDev& T = M.tabs[t];
                 const VarLayout V(T, nullptr, M.scopeOff + M.scopeBase[t]);
                 r = u - pre_at(pR, k, gpre);
+                // the residue and its two chunks are loaded before the presence
+                // test (a residue is always a valid chunk): the test's own loads
+                // (the row's variable, its domain offset and word) go alongside
+                const bool spec = T.useResidues && !T.negative;
+                uint4 sv = make_uint4(0u, 0u, 0u, 0u), cv = sv;
+                if (spec) {
+                    res = __ldcg(&T.residue[r]);
+                    sv = ld_sup(T.sup + (size_t)r * T.W4 + res);
+                    cv = __ldcg(T.curr + res);
+                }
                 const int i = __ldg(&T.rowVar[r]);
                 const int a = r - V.row0(i);
                 const bool inDom = (__ldcg(&M.dom[V.off(i) + (a >> 5)]) >> (a & 31)) & 1u;
@@ -837,10 +847,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) ct_model_kernel(const __
                         atomicAdd(&C->nscanAll[round & 1], 1);
                     }
                 } else if (__ldcg(&T.varSup[i]) && inDom) {
-                    if (T.useResidues) {
-                        res = T.residue[r];
-                        hit = nz(and4(ld_sup(T.sup + (size_t)r * T.W4 + res), __ldcg(T.curr + res)));
-                    }
+                    if (spec) hit = nz(and4(sv, cv));
                     need = !hit;
                 }
             }
