@@ -498,6 +498,26 @@ def run_ours(args, rank, world):
             "t1e7_arity5_d64": _bulk_update(C, torch, stream, 10_000_000, 5, 64, 6)}
         result["stream_1e7_arity5_d64"] = _stream_rate(C, torch, stream, 10_000_000, 128, 99 + 10_000_000,
                                                        arity=5, d=64, roofline=True)
+        # the same kernel's bandwidth on the bulk calls and the huge table's
+        # stream, kept beside the headline stream's roofline
+        hbm = peaks()[0]
+        roofline["bulk_reset_calls"] = {
+            k: {"bytes": v["bytes_per_launch"], "frac_events": v["frac_of_hbm"],
+                "frac_update_phase": v["update_phase_frac_of_hbm"],
+                "read_ceiling_frac": round(v["read_ceiling_GBps"] / hbm, 4),
+                "frac_of_read_ceiling": v["frac_of_read_ceiling"]}
+            for k, v in result["bulk_update"].items()}
+        s7 = result["stream_1e7_arity5_d64"]
+        roofline["stream_1e7_arity5_d64"] = {"props_per_s": s7["value"], "frac": s7["roofline"]["frac"],
+                                             "avg_bytes_per_launch": s7["roofline"]["avg_bytes_per_launch"]}
+        # the filter run after the update's barrier on every call (the kernel
+        # before its filter ran beside the update), same stream and table
+        result["early_filter_ablation"] = {
+            "tuples": args.tuples,
+            "default_props_per_s": _stream_rate(C, torch, stream, args.tuples, 256, args.seed),
+            "filter_after_barrier_props_per_s": _stream_rate(C, torch, stream, args.tuples, 256, args.seed,
+                                                             opt=C.make_options(no_early_filter=1)),
+            "note": "best of two planned 256-call steps each, host wall time"}
         result["search"] = search_extras(C)
         result["extra"] = extras(args, C, torch, stream)
         lo = result["extra"].get("learned_order") or {}
@@ -511,28 +531,64 @@ def run_ours(args, rank, world):
         if not args.no_extra:
             result["cpu_baseline_bitset_all_cores"] = cpu_bitset_baseline_cores(args, plans[args.warmup:], dom_lo,
                                                                                 dom_size, tup)
+    if rank == 0:
+        result["summary"] = summary(result)
     return result
 
 
-def _read_ceiling(torch, nbytes, flush, reps=7):
-    """What one stock library kernel reaches reading `nbytes` once on this GPU:
-    torch's float32 sum over a buffer of that size, L2 flushed before each
-    launch, CUDA events around it (median). A single launch this short pays
-    launch and ramp-up latency that a long copy amortises, so this is the
-    bandwidth a one-call propagation of that many bytes could hope for."""
-    x = torch.ones(max(1, int(nbytes) // 4), dtype=torch.float32, device="cuda")
+def summary(r):
+    """The line's main figures in a few hundred characters, as its last key."""
+    out = {"props_per_s": r["value"], "e2e_props_per_s": round(r["e2e"]["value"] or 0.0, 1),
+           "roofline_frac": r["roofline"]["frac"], "call_p50_us": r["call_latency_us"]["p50"]}
+    try:
+        b = r.get("bulk_update") or {}
+        out["bulk_frac_events"] = {k.split("_")[0]: v["frac_of_hbm"] for k, v in b.items()}
+        out["bulk_frac_update_phase"] = {k.split("_")[0]: v["update_phase_frac_of_hbm"] for k, v in b.items()}
+        out["bulk_frac_of_read_ceiling"] = {k.split("_")[0]: v["frac_of_read_ceiling"] for k, v in b.items()}
+        if "stream_1e7_arity5_d64" in r:
+            s7 = r["stream_1e7_arity5_d64"]
+            out["stream_1e7"] = {"props_per_s": s7["value"], "frac": s7["roofline"]["frac"]}
+        if "early_filter_ablation" in r:
+            e = r["early_filter_ablation"]
+            out["early_filter"] = [e["default_props_per_s"], e["filter_after_barrier_props_per_s"]]
+        for k, v in (r.get("search") or {}).items():
+            out[k.split("_")[0] + "_nodes_per_s"] = {"plain": v["plain"]["nodes_per_s"],
+                                                     "batched": v["batched"]["nodes_per_s"],
+                                                     "device": v["batched_device"]["nodes_per_s"]}
+        lo = ((r.get("learned_order") or {}).get("scaled_family") or {}).get("summary") or {}
+        if lo:
+            out["learned_geomean_time_vs_first_fail"] = {k: lo[k].get("geomean_time_vs_first_fail")
+                                                         for k in lo if isinstance(lo[k], dict)
+                                                         and "geomean_time_vs_first_fail" in lo[k]}
+    except Exception as e:  # the summary must not hide the line
+        out["error"] = repr(e)
+    out["cpu_bitset_1_core"] = (r.get("cpu_baseline_bitset") or {}).get("value")
+    out["cpu_bitset_all_cores"] = (r.get("cpu_baseline_bitset_all_cores") or {}).get("value")
+    return out
+
+
+def _read_ceiling(C, torch, nbytes, flush, reps=7):
+    """What one launch reaches reading `nbytes` once on this GPU: the library's
+    streaming-read kernel (ct_read_ceiling: 128-bit loads, eight in flight per
+    thread, four CTAs per SM) over a buffer of that size, L2 flushed before each
+    launch, CUDA events around it on the same stream (median). A launch this
+    short pays launch and ramp-up latency that a long copy amortises, so this is
+    the bandwidth a one-call propagation of that many bytes could hope for."""
+    n = max(16, (int(nbytes) + 15) // 16 * 16)
+    x = torch.ones(n // 4, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = []
     for _ in range(reps):
         flush.zero_()
         torch.cuda.synchronize()
-        e0.record()
-        x.sum()
-        e1.record()
+        e0.record(s)
+        C.check(C.ct_read_ceiling(x, n, s))
+        e1.record(s)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     del x
-    return x_bytes_per_s(nbytes, statistics.median(ms))
+    return x_bytes_per_s(n, statistics.median(ms))
 
 
 def x_bytes_per_s(nbytes, ms):
@@ -587,7 +643,7 @@ def _bulk_update(C, torch, stream, t, arity, d, seed, reps=9):
     hbm = peaks()[0]
     ev_us, dev_us, upd_us = statistics.median(ev), statistics.median(dev), statistics.median(upd)
     gbs = alg / ev_us / 1e3
-    ceiling = _read_ceiling(torch, alg, flush)
+    ceiling = _read_ceiling(C, torch, alg, flush)
     del flush
     return {"tuples": t, "arity": arity, "domain": d, "rows_ored": stats["rows_ored"],
             "grid_blocks": info["grid_blocks"], "loads_in_flight": info["loads_in_flight"],
@@ -602,7 +658,8 @@ def _bulk_update(C, torch, stream, t, arity, d, seed, reps=9):
             "phase_ns_last": stats["phase_ns"],
             "note": "medians of %d one-call repetitions, L2 flushed before each; GBps by CUDA events "
                     "around the launch; update phase by the device timer (plan end to the barrier "
-                    "after updateTable); read ceiling: one torch float32 sum over the same bytes" % reps}
+                    "after updateTable); read ceiling: one launch of the library's streaming-read kernel "
+                    "(ct_read_ceiling) over the same bytes" % reps}
 
 
 def _stream_rate(C, torch, stream, t, calls, seed, opt=None, shape=None, arity=ARITY, d=DOM, roofline=False):

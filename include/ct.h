@@ -87,6 +87,12 @@ typedef struct ct_options {
                                  cut over up to 8 warps of a CTA, one batch of row loads each where
                                  the list allows, and their partial masks are combined in shared
                                  memory; results are the same). */
+    int32_t no_early_filter;  /* 1 = filterDomains always waits for the whole update (a grid barrier).
+                                 Default: a call that ORs at most 16 supports rows (8 on tables of more
+                                 segments than one wave of warps) filters beside the update, each probed
+                                 currTable chunk recomputed from its stored value and the call's rows
+                                 (Algorithm 2 at one chunk), and one grid barrier ends both; positive
+                                 tables with residues and a plan in shared memory. Results are the same. */
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */
@@ -130,6 +136,7 @@ typedef struct ct_call_stats {
     int64_t filter_bytes;    /* algorithmic bytes of filterDomains: 4 * supports words tested */
     int32_t phase_ns[4];     /* %globaltimer, ns from the first CTA's start to: plan done, update done,
                                 probes done, result published (device-side, no launch latency) */
+    int32_t early_filter;    /* 1: filterDomains ran beside updateTable (ct_options.no_early_filter) */
 } ct_call_stats;
 
 /* Accumulated launch times (ct_options.profile = 1): CUDA events recorded on
@@ -606,6 +613,14 @@ int ct_search_collect(ct_model* m, int64_t node_limit, int slots, int64_t max_sa
                       float* labels_host, int64_t* samples_out);
 
 /* ---------------------------------------------------------------- misc -- */
+/* ct_read_ceiling: measurement support, no counterpart in the paper. Launches
+ * (asynchronously, on cuda_stream) one kernel that reads `bytes` of device
+ * memory at dev_buf once, 128-bit loads not kept in L1, eight in flight per
+ * thread, four CTAs of 256 threads per SM, and stores nothing the caller sees:
+ * the bandwidth one launch of that size reaches, to set beside a propagation
+ * moving as many bytes (time it with events on the same stream). dev_buf must
+ * be 16-byte aligned and bytes a positive multiple of 16 (else CT_ERR_ARG). */
+int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream);
 const char* ct_last_error(void);
 const char* ct_status_string(int status);
 int ct_version(void);

@@ -583,6 +583,46 @@ __device__ __forceinline__ void trail_warp(const TableDev& T, const TrailItem& i
 // ---------------------------------------------------------------------------
 // probe: Algorithm 3 with residues, a warp per value whose residue missed
 // ---------------------------------------------------------------------------
+// Chunk c of currTable as this call's update leaves it (Algorithm 2), for a
+// filter that runs beside the update: the chunk as loaded AND-ed with the
+// call's mask at c, the AND over the changed variables of the OR of their rows
+// (complemented on the delta path), rows as the update reads them. The load
+// may see the chunk before or after the warp that owns it stores the update:
+// the update stores new = old & M, and new & M = new, word by word, so a load
+// that sees part of the store gives the new chunk too. E >= the call's rows.
+template <int E>
+__device__ __forceinline__ uint4 chunk_after(const TableDev& T, const int32_t* codes, int nrows, int c) {
+    const uint4 cur = __ldcg(T.curr + c);
+    uint4 v[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        const int code = u < nrows ? codes[u] : 0;
+        v[u] = ld_sup_pred(((code & kCodeDelta) ? T.supDelta : T.sup) + (size_t)(code & kCodeRow) * T.W4 + c,
+                           u < nrows);
+    }
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u), m = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+        if (u < nrows) {
+            const int code = codes[u];  // (shared memory: read again rather than held)
+            m = or4(m, v[u]);
+            if (code & kCodeLast) {
+                acc = and4(acc, (code & kCodeDelta) ? not4(m) : m);
+                m = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+    return and4(cur, acc);
+}
+
+// currTable chunk c for a probe: as stored (kE = 0, after the update's
+// barrier), or recomputed from the call's rows beside the update (kE rows).
+template <int kE>
+__device__ __forceinline__ uint4 probe_chunk(const TableDev& T, const int32_t* codes, int nrows, int c) {
+    if constexpr (kE > 0) return chunk_after<kE>(T, codes, nrows, c);
+    else return __ldcg(T.curr + c);
+}
+
 // Position of the k-th (0-based) set bit of m (k < popcount(m)): halve the
 // word, keeping the half that holds it.
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
@@ -612,8 +652,9 @@ enum { kProbeFound = 1, kProbeGone = 0, kProbeUndecided = -1 };
 // (Measured against windows of the chunks that follow the residue, dead or
 // alive: the same on the dense bench stream, 8-10% more search nodes per
 // second in the batched search.)
-template <bool kLive, int kProbes = kLocalProbes>
-__device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, uint32_t* s_cnt) {
+template <bool kLive, int kProbes = kLocalProbes, int kE = 0>
+__device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, uint32_t* s_cnt,
+                                             const int32_t* codes = nullptr, int nrows = 0) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     bool complete = false;
@@ -622,15 +663,18 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
         // round of loads, tested in order
         const int W4 = T.W4;
         const uint4* row = T.sup + (size_t)r * W4;
-        for (int b = 0; b < kProbes; b += 2) {
+        // (one window per round when the chunks are recomputed from more than
+        // four rows: their row loads)
+        constexpr int kStep = kE > 4 ? 1 : 2;
+        for (int b = 0; b < kProbes; b += kStep) {
             const int c0 = (int)(((long long)res + 1 + b * 32 + lane) % W4);
             const int c1 = (int)(((long long)res + 1 + (b + 1) * 32 + lane) % W4);
-            const bool two = b + 1 < kProbes;
-            const uint4 s0 = ld_sup(row + c0), t0 = __ldcg(T.curr + c0);
+            const bool two = kStep == 2 && b + 1 < kProbes;
+            const uint4 s0 = ld_sup(row + c0), t0 = probe_chunk<kE>(T, codes, nrows, c0);
             uint4 s1 = make_uint4(0u, 0u, 0u, 0u), t1 = s1;
             if (two) {
                 s1 = ld_sup(row + c1);
-                t1 = __ldcg(T.curr + c1);
+                t1 = probe_chunk<kE>(T, codes, nrows, c1);
             }
             for (int k = 0; k < (two ? 2 : 1); ++k) {
                 if (lane == 0) atomicAdd(&s_cnt[kCntWin], 1u);
@@ -701,7 +745,7 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
                 int chunk = 0;
                 if (q < total) {
                     chunk = sj * 32 + nth_set_bit(mj, q - before);
-                    h = nz(and4(ld_sup(row + chunk), __ldcg(T.curr + chunk)));
+                    h = nz(and4(ld_sup(row + chunk), probe_chunk<kE>(T, codes, nrows, chunk)));
                 }
                 tested += min(32, total - q0);
                 const unsigned bal = __ballot_sync(FULL, h);
@@ -722,9 +766,7 @@ __device__ __forceinline__ int probe_windows(const TableDev& T, int r, int res, 
 // A residue miss searched by probe_windows; a value not found goes to the
 // hard list, marked kNoSupport when it has no support (removed without a
 // scan; a scan keeps the mark, atomicMin), else for the full scan.
-template <bool kLive, int kProbes = kLocalProbes>
-__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt) {
-    const int o = probe_windows<kLive, kProbes>(T, r, res, s_cnt);
+__device__ __forceinline__ void note_probe(const TableDev& T, int r, int o, uint32_t* s_cnt) {
     if (o != kProbeFound && (threadIdx.x & 31) == 0) {
         const bool complete = o == kProbeGone;
         const unsigned m = atomicAdd(&T.ctrl->nhard, 1u);
@@ -735,6 +777,31 @@ __device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, ui
             atomicAdd(&s_cnt[kCntMiss], 1u);
         }
     }
+}
+
+template <bool kLive, int kProbes = kLocalProbes, int kE = 0>
+__device__ __forceinline__ void probe_miss(const TableDev& T, int r, int res, uint32_t* s_cnt,
+                                           const int32_t* codes = nullptr, int nrows = 0) {
+    note_probe(T, r, probe_windows<kLive, kProbes, kE>(T, r, res, s_cnt, codes, nrows), s_cnt);
+}
+
+// Whole warp: wait (bounded) until every CTA of the launch has released its
+// part of the update (Ctrl::upd_done); false when the wait ran out, with
+// CT_ERR_TIMEOUT set in the control block.
+__device__ __forceinline__ bool wait_update_done(Ctrl* C, unsigned limit) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned it = 0;
+        while (ld_acquire(&C->upd_done) < gridDim.x) {
+            if (++it > limit) {
+                ok = false;
+                atomicExch(&C->status, CT_ERR_TIMEOUT);
+                break;
+            }
+            if (it > 64) __nanosleep(32);
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 template <bool kLive>

@@ -71,6 +71,7 @@ enum StatusSlot {
     kSlotT3 = 19,  // probes done (after the barrier),
     kSlotT4 = 20,  // finalize
     kSlotScan = 21,  // hard values left undecided by the windows (the full scan's)
+    kSlotEarly = 22,  // 1: the filter ran beside the update (one grid barrier)
 };
 
 // Per-table control block: persistent state and per-call counters.
@@ -90,7 +91,7 @@ struct Ctrl {
     int32_t live_state;  // live chunks after the last update (kept across calls)
     int32_t nscan;       // per call: hard values that need the full scan (the others are known unsupported)
     uint32_t tuples;     // per call, negative tables: valid tuples after the update
-    int32_t pad2;
+    uint32_t upd_done;   // per call: CTAs done with the update (a filter beside it may wait on it)
     uint64_t t[4];       // %globaltimer stamps of CTA 0 (diagnostics)
     // The barrier words on a line of their own: the arrivals and polls of
     // every CTA would otherwise hold up the finalizing CTA's reads of the
@@ -149,6 +150,7 @@ struct CallParams {
     int32_t domInParams;          // 1: the domains are domWords (local plan only); the result
                                   // leaves through the status block alone
     uint32_t domWords[kParamDomWords];
+    int32_t early;     // 1: calls of at most U rows filter beside the update (local plan; see the kernel)
 };
 
 // Dynamic shared memory of the propagation kernel: the partial results of the
@@ -319,6 +321,7 @@ cudaError_t launch_save(const TableDev& T, int level, cudaStream_t s);
 cudaError_t launch_restore(const TableDev& T, int level, int mark, int top, int newMark, cudaStream_t s);
 cudaError_t launch_set_words(uint32_t* dst, const uint32_t* words, int n, cudaStream_t s);
 cudaError_t launch_copy_words(uint32_t* dst, const uint32_t* src, int n, cudaStream_t s);
+cudaError_t launch_read_ceiling(const uint4* p, size_t n16, cudaStream_t s);
 
 }  // namespace ctk
 

@@ -30,6 +30,17 @@
 //            segment's live chunks and tests every hard value against them,
 //            and the last CTA to finish removes the values no chunk supports,
 //            stores new residues and publishes.
+// Calls of at most U supports rows (positive local-plan tables with
+// residues; ct_options.no_early_filter switches this off) run the probes
+// beside the update instead: the update takes one round of the grid's warps
+// (one segment per warp), the warps after it start on the values at once, and
+// every chunk a probe tests is recomputed from its stored value and the
+// call's rows (chunk_after: the stored value may be old or new, the result is
+// the new one). One grid barrier then ends both phases and decides the
+// failure from the update's live count; a value the windows left undecided
+// waits (bounded) for the whole update and is searched again over the index
+// it left when currTable has become sparse; the finalizing CTA writes lastDom
+// (no CTA may write it before every plan is done).
 // Grid barriers spin with a bounded iteration count; running out sets
 // CT_ERR_TIMEOUT in the control block and every CTA returns.
 #include <cstddef>
@@ -80,8 +91,11 @@ static_assert(kSlotStatus == 0 && kSlotLiveOut == 1 && kSlotWordsIn == 2 && kSlo
 // count) and the domain words are loaded in the same round as the header;
 // the removals go to a shared copy of the domains, which is what the host
 // receives. localDom: sm.dom already holds the call's domains (local plan).
+// lastDomHere: the filter ran beside the update, so no CTA wrote lastDom
+// after the plans (a CTA may still be reading it in its plan before the
+// barrier): this CTA writes it, the call's domains less the values it removes.
 __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __restrict__ dom, Smem& sm, int nh,
-                         uint64_t t3, bool localDom) {
+                         uint64_t t3, bool localDom, bool lastDomHere = false) {
     Ctrl* C = T.ctrl;
     const int tid = threadIdx.x;
     int32_t* H = T.statusBlk;
@@ -106,6 +120,7 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
         const int32_t w = b >= 0 ? __ldcg(cw + b) : 0;
         if (tid == kSlotHard && nh >= 0) v = nh;
         if (tid == kSlotT3 && t3) v = (int32_t)(uint32_t)t3;
+        if (tid == kSlotEarly) v = lastDomHere ? 1 : 0;
         sm.scan[tid] = v - w;
     }
     if (tid == 0) sm.cnt[kCntPruned] = 0u;
@@ -137,7 +152,8 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
                 // lastDom may drop it now; a negative table's value still has
                 // valid forbidden tuples, which the next call removes as Delta;
                 // a shard's value may be supported by another shard
-                if (!T.negative && !T.shard) atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
+                if (!T.negative && !T.shard && !lastDomHere)
+                    atomicAnd(&T.lastDom[V.ld(i) + (a >> 5)], ~(1u << (a & 31)));
                 atomicOr(reinterpret_cast<unsigned*>(&sm.scan[kChgBase + (i >> 5)]), 1u << (i & 31));
                 ++pruned;
             }
@@ -156,6 +172,8 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
             }
         }
     }
+    if (lastDomHere && st == CT_OK)
+        for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = sm.dom[q];
     // Header: one slot per thread.
     if (tid < kStatusHdr && tid != kSlotStatus) {
         int32_t v = sm.scan[tid];
@@ -167,6 +185,7 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     // Reset the per-call counters for the next call (after every read above).
     if (tid == 0) {
         C->live = 0u; C->live_in = 0u; C->words_in = 0u; C->nhard = 0u; C->done = 0u; C->nscan = 0; C->tuples = 0u;
+        C->upd_done = 0u;
         C->hits = 0; C->trail_added = 0; C->local_found = 0; C->misses = 0; C->windows = 0;
         C->nval = 0; C->ndelta = 0; C->nreset = 0; C->nsup = 0; C->nrows = 0;
         C->status = CT_OK;
@@ -194,6 +213,31 @@ __device__ __forceinline__ void probe_loaded(const TableDev& T, int r, bool pres
     }
     if (sparse) probe_miss<true, kModelProbes>(T, r, res, s_cnt);
     else probe_miss<false, kLocalProbes>(T, r, res, s_cnt);
+}
+
+// A value of s_sup probed beside the update (r and res uniform over the
+// warp): its residue chunk and, on a miss, the windows after it, every chunk
+// recomputed from the call's row codes (chunk_after, E >= nrows rows). The
+// sparse/dense choice of windows is the state's at entry; when they leave the
+// value undecided and the update has made currTable sparse (the live count is
+// final once every CTA has released its update), the value is searched again
+// over the live chunks of the index the update left, after waiting for it.
+template <int E>
+__device__ __forceinline__ void probe_early(const TableDev& T, int r, bool present, int res, const int32_t* codes,
+                                            int nrows, bool sparse, unsigned limit, uint32_t* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (!present) return;
+    bool hit = false;
+    if (lane == 0) hit = nz(and4(ld_sup(T.sup + (size_t)r * T.W4 + res), chunk_after<E>(T, codes, nrows, res)));
+    if (__shfl_sync(0xffffffffu, hit, 0)) {
+        if (lane == 0) atomicAdd(&s_cnt[kCntHits], 1u);
+        return;
+    }
+    int o = sparse ? probe_windows<true, kModelProbes, E>(T, r, res, s_cnt, codes, nrows)
+                   : probe_windows<false, kLocalProbes, E>(T, r, res, s_cnt, codes, nrows);
+    if (o == kProbeUndecided && wait_update_done(T.ctrl, limit) && 2u * __ldcg(&T.ctrl->live) < (uint32_t)T.W4)
+        o = probe_windows<true, kModelProbes>(T, r, res, s_cnt);
+    note_probe(T, r, o, s_cnt);
 }
 
 // Per-CTA counters of a phase into the control block (zero counts skipped).
@@ -242,6 +286,12 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     int res0 = 0;
     uint4 supRes0 = make_uint4(0u, 0u, 0u, 0u);
     if (T.useResidues && gwarp < T.R && lane == 0) res0 = T.residue[gwarp];
+    // With the filter beside the update (a call of at most U rows: one warp
+    // per segment, one round), the warps after the round's segments take the
+    // values first: warp g starts at value (g - nseg) mod nwarps.
+    const int pfirstE = (gwarp - T.nseg % nwarps + nwarps) % nwarps;
+    int resE = 0;
+    if (kLocal && P.early && T.useResidues && pfirstE < T.R && lane == 0) resE = T.residue[pfirstE];
 
     CT_STAMP(19);
     // plan (CTA 0 also snapshots lastDom into the levels saved since the last call)
@@ -295,7 +345,16 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     }
     if (blockIdx.x == 0 && tid == 0) C->t[1] = gtimer();
     CT_STAMP(1);
-    if (T.useResidues && gwarp < T.R && lane == 0) supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
+    // Filter beside the update (Algorithm 3 on the chunks Algorithm 2 leaves,
+    // each recomputed from the call's rows: chunk_after): for calls of at most
+    // U rows on positive local-plan tables with residues. The probes need no
+    // barrier after the update; the one barrier after them also decides the
+    // failure (Algorithm 1 line 5) from the update's live count. Every CTA
+    // takes the same decision (each computed the same plan).
+    const bool early = kLocal && P.early && ok && nrows > 0 && nrows <= U && !T.negative && !T.shard &&
+                       T.useResidues;
+    if (T.useResidues && gwarp < T.R && lane == 0 && !early)
+        supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
 
     uint4 curRes0 = make_uint4(0u, 0u, 0u, 0u);
     bool sparse = 2 * P.prevLive < T.W4;  // fewer than half the chunks live (after the update: recomputed)
@@ -401,6 +460,14 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
         __syncthreads();
         CT_STAMP(2);
         if (tid == 0) flush_update_counters(C, sm);
+        if (early) {
+            __syncthreads();  // the counters are read before the probes clear them
+            // this CTA's part of the update and its counts, released to the
+            // probes that wait for the whole update (wait_update_done)
+            if (tid == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&C->upd_done) : "memory");
+        }
+    }
+    if (ok && (nrows > 0 || T.negative) && !early) {
         const int r1 = bar_sync(bar, &sm.flag[0]);
         if (!r1) return;
         CT_STAMP(3);
@@ -428,7 +495,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     __syncthreads();
     // lastDom := the domains of this call (values pruned below are cleared
     // again by the finalizing CTA).
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && !early) {
         if (kLocal) {
             for (int q = tid; q < T.DW; q += kThreads) T.lastDom[q] = sm.dom[q];
         } else {
@@ -451,6 +518,17 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
                 T.foundChunk[m] = 0;
                 atomicAdd(&C->nscan, 1);
             }
+        }
+    } else if (early) {
+        for (int r = pfirstE; r < T.R; r += nwarps) {
+            const int i = __ldg(&T.rowVar[r]);
+            const int a = r - V.row0(i);
+            const bool present = sm.sup[i] && ((sm.dom[V.ld(i) + (a >> 5)] >> (a & 31)) & 1u);
+            int res = resE;
+            if (r != pfirstE && present && lane == 0) res = T.residue[r];
+            res = __shfl_sync(0xffffffffu, res, 0);
+            if (nrows <= 4) probe_early<4>(T, r, present, res, sm.codes, nrows, sparse, bar.limit, sm.cnt);
+            else probe_early<U>(T, r, present, res, sm.codes, nrows, sparse, bar.limit, sm.cnt);
         }
     } else
     for (int r = gwarp; r < T.R; r += nwarps) {
@@ -484,11 +562,26 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     if (!r2) return;
     CT_STAMP(5);
     const uint64_t t3 = r2 == 2 ? gtimer() : 0ull;
+    if (early) {
+        // Algorithm 1 line 5 after the update, whose counts every CTA flushed
+        // before this barrier: the probes' results are dropped on a failure.
+        if (r2 == 2 && tid == 0) C->t[2] = t3;
+        const int st1 = __ldcg(&C->status);
+        const uint32_t live1 = __ldcg(&C->live);
+        if (st1 != CT_OK || live1 == 0u) {
+            if (r2 == 2) {
+                if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
+                __syncthreads();
+                finalize(T, V, domOut, sm, 0, 0ull, kLocal);
+            }
+            return;
+        }
+    }
     // The CTA that arrived last reads the hard-value counts with the counters
     // it publishes: with none left undecided (every value kept its support,
     // or its windows covered every live chunk) it removes the unsupported
     // values and publishes, and the others are done.
-    if (r2 == 2 && finalize(T, V, domOut, sm, -1, t3, kLocal)) {
+    if (r2 == 2 && finalize(T, V, domOut, sm, -1, t3, kLocal, early)) {
         CT_STAMP(6);
         return;
     }
@@ -520,7 +613,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     CT_STAMP(14);
     if (!sm.flag[1]) return;
     __threadfence();
-    finalize(T, V, domOut, sm, nh, 0ull, kLocal);
+    finalize(T, V, domOut, sm, nh, 0ull, kLocal, early);
     CT_STAMP(7);
 }
 
@@ -669,6 +762,33 @@ cudaError_t launch_set_words(uint32_t* dst, const uint32_t* words, int n, cudaSt
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// One streaming read of n16 chunks (ct_read_ceiling): U independent 128-bit
+// loads per thread and round, grid-strided; the XOR of what was read decides
+// a store that never happens in practice, so the loads are not dropped.
+__device__ uint32_t g_ct_read_sink;
+template <int U>
+__global__ void __launch_bounds__(256) ct_read_kernel(const uint4* __restrict__ a, size_t n16) {
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    uint32_t x = 0u;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += nth * U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_sup_pred(a + i + (size_t)u * nth, i + (size_t)u * nth < n16);
+#pragma unroll
+        for (int u = 0; u < U; ++u) x ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+    }
+    if (x == 0x9e3779b9u) g_ct_read_sink = x;
+}
+
+cudaError_t launch_read_ceiling(const uint4* p, size_t n16, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    ct_read_kernel<8><<<4 * sms, 256, 0, s>>>(p, n16);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_words(uint32_t* dst, const uint32_t* src, int n, cudaStream_t s) {

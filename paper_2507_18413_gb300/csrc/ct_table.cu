@@ -51,6 +51,20 @@ extern "C" const char* ct_status_string(int s) {
 
 extern "C" int ct_version(void) { return 10000; }
 
+extern "C" int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream) {
+    if (!dev_buf || bytes <= 0 || (bytes & 15) || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) {
+        ct_set_error("ct_read_ceiling: a 16-byte aligned buffer and a positive multiple of 16 bytes");
+        return CT_ERR_ARG;
+    }
+    const cudaError_t e = ctk::launch_read_ceiling(static_cast<const uint4*>(dev_buf), (size_t)(bytes / 16),
+                                                   static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) {
+        ct_set_error("ct_read_ceiling: %s", cudaGetErrorString(e));
+        return CT_ERR_CUDA;
+    }
+    return CT_OK;
+}
+
 
 namespace {
 
@@ -397,6 +411,7 @@ int build(ct_table* ct, const int32_t* dom_lo, const int32_t* dom_size, const in
         // spreads over the whole grid), capped at residency, and at least one
         // warp per two values for the probes.
         ct->maxSplit = (opt && opt->no_split) ? 1 : kMaxSplit;
+        ct->early = !(opt && opt->no_early_filter);
         const int narrow = (ct->localPlan ? 1 : 0);
         // more segments than one wave of warps at 2 CTAs per SM: 8 loads at 3 CTAs per SM
         const int maxNarrow = max_coresident_blocks(narrow);
@@ -471,6 +486,7 @@ void fill_stats(ct_table* ct) {
     s.phase_ns[1] = h[kSlotT2];
     s.phase_ns[2] = h[kSlotT3];
     s.phase_ns[3] = h[kSlotT4];
+    s.early_filter = h[kSlotEarly];
 }
 
 }  // namespace
@@ -552,6 +568,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.prevLive = ct->live;
     P.spinLimit = kBarrierSpinLimit;
     P.maxSplit = ct->maxSplit;
+    P.early = ct->early ? 1 : 0;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     if (domHost) {
         if (!ct->localPlan || ct->DW > kParamDomWords) {
@@ -626,6 +643,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
         c.status = CT_OK;
         c.live = c.live_in = c.words_in = c.nhard = c.done = c.tuples = 0u;
         c.nscan = 0;
+        c.upd_done = 0u;
         CT_CUDA(cudaMemcpy(ct->dev.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
         ct->failed = true;
         ct->broken = true;
@@ -736,6 +754,7 @@ ct_table* ct_table_clone(const ct_table* src, cudaStream_t stream, DeviceArena* 
     ct->localPlan = src->localPlan;
     ct->variant = src->variant;
     ct->maxSplit = src->maxSplit;
+    ct->early = src->early;
     ct->live = src->live;
     ct->stream = stream;
     ct->dev = src->dev;  // static pointers shared; dynamic ones replaced below

@@ -60,6 +60,7 @@ struct ct_table {
     bool trailInArena = false;   // the trail / level stack belong to an arena: not freed here
     bool levelsInArena = false;
     int maxSplit = ctk::kMaxSplit;  // most warps sharing one segment's row list (1: ct_options.no_split)
+    bool early = true;              // filter beside the update on calls of few rows (ct_options.no_early_filter)
     uint32_t armPolls = 0;          // test hook: the next call's barrier waits run out after this many polls
 };
 

@@ -37,7 +37,7 @@ class ct_options(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("no_residues", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("host_fixpoint", ctypes.c_int32), ("autotune", ctypes.c_int32), ("copy_state", ctypes.c_int32),
-                ("shard", ctypes.c_int32), ("no_split", ctypes.c_int32)]
+                ("shard", ctypes.c_int32), ("no_split", ctypes.c_int32), ("no_early_filter", ctypes.c_int32)]
 
 
 class ct_table_info(ctypes.Structure):
@@ -58,7 +58,8 @@ class ct_call_stats(ctypes.Structure):
                 ("pruned", ctypes.c_int32), ("trail_added", ctypes.c_int32),
                 ("live_chunks_in", ctypes.c_int64), ("live_chunks_out", ctypes.c_int64),
                 ("live_words_in", ctypes.c_int64), ("update_bytes", ctypes.c_int64),
-                ("filter_bytes", ctypes.c_int64), ("phase_ns", ctypes.c_int32 * 4)]
+                ("filter_bytes", ctypes.c_int64), ("phase_ns", ctypes.c_int32 * 4),
+                ("early_filter", ctypes.c_int32)]
 
 
 class ct_profile(ctypes.Structure):
@@ -122,6 +123,7 @@ _SIGS = {
     "ct_destroy": (ctypes.c_int, [_P]),
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
     "ct_arm_wait_timeout": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "ct_read_ceiling": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
     "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
     "ct_sharded_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.c_int,
                                          _P, _P, ctypes.POINTER(_P)]),
@@ -251,8 +253,9 @@ def _stream_ptr(stream):
 
 
 def make_options(grid_blocks=0, no_residues=0, profile=0, host_fixpoint=0, copy_state=0, autotune=0, shard=0,
-                 no_split=0):
+                 no_split=0, no_early_filter=0):
     o = ct_options()
+    o.no_early_filter = no_early_filter
     o.no_split = no_split
     o.shard = shard
     o.autotune = autotune
@@ -373,6 +376,12 @@ def ct_propagate(h, dom_bits, changed_words: int = 0):
     ch, pch = _u32_out(changed_words)
     st = load().ct_propagate(h, _dev_ptr(dom_bits), pch if changed_words else None)
     return st, ch[:changed_words]
+
+
+def ct_read_ceiling(buf, nbytes, stream=None):
+    """One streaming read of nbytes of the device buffer (a torch tensor or a raw
+    device pointer), launched on stream; time it with events on that stream."""
+    return load().ct_read_ceiling(_dev_ptr(buf), int(nbytes), _stream_ptr(stream))
 
 
 def ct_arm_wait_timeout(h, polls):

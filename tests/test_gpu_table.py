@@ -12,7 +12,7 @@ import pytest
 from oracle import ct_oracle as O
 from paper_2507_18413_gb300 import ct as C
 from paper_2507_18413_gb300 import inputs as G
-from gpu_helpers import GpuTable, check_index_invariant, compare_call, oracle_step
+from gpu_helpers import GpuTable, check_index_invariant, compare_call, oracle_step, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -105,7 +105,7 @@ def _large_stream(t, calls, seed, opt=None, check_every=1, depth=8):
     gt.save()
     masks = root
     d = 0
-    seen = {"delta": 0, "reset": 0, "fail": 0}
+    seen = {"delta": 0, "reset": 0, "fail": 0, "early": 0, "calls": 0}
     for k in range(calls):
         gt.save()
         if rng.int(2) == 0:
@@ -118,6 +118,8 @@ def _large_stream(t, calls, seed, opt=None, check_every=1, depth=8):
         s = gt.stats()
         seen["delta"] += s["delta_vars"]
         seen["reset"] += s["reset_vars"]
+        seen["early"] += s["early_filter"]
+        seen["calls"] += 1
         d += 1
         if st == O.INFEASIBLE or d >= depth:
             seen["fail"] += st == O.INFEASIBLE
@@ -183,6 +185,28 @@ def test_global_plan_path():
             continue
         masks = out
     gt.close()
+
+
+@pytest.mark.parametrize("no_early", [0, 1])
+def test_filter_beside_the_update_and_after_it(no_early):
+    """The default filters calls of few rows beside the update, each probed
+    chunk recomputed from the call's rows; with no_early_filter every call
+    filters after the update's barrier. Both match the oracle call by call."""
+    seen = _large_stream(100_000, calls=160, seed=23, opt=C.make_options(no_early_filter=no_early))
+    assert seen["delta"] > 0 and seen["reset"] > 0
+    if no_early:
+        assert seen["early"] == 0
+    else:
+        # (most calls of this stream OR at most 16 rows; a failed call
+        # reports no filter)
+        assert 0 < seen["early"] <= seen["calls"] - seen["fail"]
+
+
+@pytest.mark.parametrize("grid", [1, 3, 40])
+def test_filter_beside_the_update_small_grids(grid):
+    # few warps: the probes run on the warps that also update
+    seen = _large_stream(30_000, calls=80, seed=29, opt=C.make_options(grid_blocks=grid), depth=10)
+    assert seen["early"] > 0
 
 
 def test_large_stream_1e6_sampled():
@@ -466,4 +490,34 @@ def test_huge_1e7_arity5_sampled():
         if st != O.OK:
             break
         masks = out
+    # delta calls on the table of more segments than one wave of warps (8
+    # loads per batch): filtered beside the update
+    assert st == O.OK
+    early = 0
+    for k in range(2):
+        gt.save()
+        new, i = G.delta_step(rng, masks)
+        if i is None:
+            break
+        st, out = compare_call(gt, tup_ret, new, check_table=(k == 1))
+        early += gt.stats()["early_filter"]
+        if st != O.OK:
+            break
+        masks = out
+    assert early > 0
     gt.close()
+
+
+def test_read_ceiling_entry_point():
+    """The measurement kernel reads a device buffer and rejects what it cannot read."""
+    torch = torch_cuda()
+    C.load()
+    x = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    assert C.ct_read_ceiling(x, x.numel() * 4, s) == C.CT_OK
+    assert C.ct_read_ceiling(x, 16, s) == C.CT_OK
+    torch.cuda.synchronize()
+    assert C.ct_read_ceiling(x, 0, s) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(x, 24, s) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(x.data_ptr() + 4, 16, s) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(0, 16, s) == C.CT_ERR_ARG

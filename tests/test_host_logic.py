@@ -123,3 +123,28 @@ def test_clock_record_parsing():
     assert r["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert bench.clocks_stop(_FakeSampler("")) is None
     assert bench.clocks_stop(None) is None
+
+
+def test_bench_summary_of_a_line():
+    """The line's closing summary: the headline figures, and the other
+    configurations' when the line holds them."""
+    bench = pytest.importorskip("bench")
+    r = {"value": 40000.0, "e2e": {"value": 38000.04}, "roofline": {"frac": 0.017},
+         "call_latency_us": {"p50": 21.0}, "cpu_baseline_bitset": {"value": 900.0}}
+    s = bench.summary(r)
+    assert s["props_per_s"] == 40000.0 and s["e2e_props_per_s"] == 38000.0 and s["roofline_frac"] == 0.017
+    assert s["cpu_bitset_1_core"] == 900.0 and s["cpu_bitset_all_cores"] is None and "error" not in s
+    r["bulk_update"] = {"t1e6_arity6_d32": {"frac_of_hbm": 0.1, "update_phase_frac_of_hbm": 0.2,
+                                            "frac_of_read_ceiling": 0.5}}
+    r["stream_1e7_arity5_d64"] = {"value": 29000.0, "roofline": {"frac": 0.04}}
+    r["early_filter_ablation"] = {"default_props_per_s": 37000.0, "filter_after_barrier_props_per_s": 35000.0}
+    r["search"] = {"config3_40v_60t_arity4": {"plain": {"nodes_per_s": 1.0}, "batched": {"nodes_per_s": 2.0},
+                                              "batched_device": {"nodes_per_s": 3.0}}}
+    r["learned_order"] = {"scaled_family": {"summary": {"instances": 3, "learned": {
+        "geomean_time_vs_first_fail": 0.6}}}}
+    s = bench.summary(r)
+    assert s["bulk_frac_events"] == {"t1e6": 0.1} and s["bulk_frac_of_read_ceiling"] == {"t1e6": 0.5}
+    assert s["stream_1e7"] == {"props_per_s": 29000.0, "frac": 0.04}
+    assert s["early_filter"] == [37000.0, 35000.0]
+    assert s["config3_nodes_per_s"] == {"plain": 1.0, "batched": 2.0, "device": 3.0}
+    assert s["learned_geomean_time_vs_first_fail"] == {"learned": 0.6} and "error" not in s
