@@ -89,10 +89,11 @@ typedef struct ct_options {
                                  memory; results are the same). */
     int32_t no_early_filter;  /* 1 = filterDomains always waits for the whole update (a grid barrier).
                                  Default: a call that ORs at most 16 supports rows (8 on tables of more
-                                 segments than one wave of warps) filters beside the update, each probed
-                                 currTable chunk recomputed from its stored value and the call's rows
-                                 (Algorithm 2 at one chunk), and one grid barrier ends both; positive
-                                 tables with residues and a plan in shared memory. Results are the same. */
+                                 segments than one wave of warps) while at least half the currTable
+                                 chunks are live filters beside the update, each probed chunk
+                                 recomputed from its stored value and the call's rows (Algorithm 2 at
+                                 one chunk), and one grid barrier ends both; positive tables with
+                                 residues and a plan in shared memory. Results are the same. */
 } ct_options;
 
 /* Static shape and live state of a table (ct_get_info). */

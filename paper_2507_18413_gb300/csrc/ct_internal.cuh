@@ -150,7 +150,7 @@ struct CallParams {
     int32_t domInParams;          // 1: the domains are domWords (local plan only); the result
                                   // leaves through the status block alone
     uint32_t domWords[kParamDomWords];
-    int32_t early;     // 1: calls of at most U rows filter beside the update (local plan; see the kernel)
+    int32_t early;     // calls of at most min(early, U) rows filter beside the update (0: never; local plan)
 };
 
 // Dynamic shared memory of the propagation kernel: the partial results of the

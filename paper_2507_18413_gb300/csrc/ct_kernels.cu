@@ -31,7 +31,8 @@
 //            and the last CTA to finish removes the values no chunk supports,
 //            stores new residues and publishes.
 // Calls of at most U supports rows (positive local-plan tables with
-// residues; ct_options.no_early_filter switches this off) run the probes
+// residues, at least half the chunks live at entry; ct_options.no_early_filter
+// switches this off) run the probes
 // beside the update instead: the update takes one round of the grid's warps
 // (one segment per warp), the warps after it start on the values at once, and
 // every chunk a probe tests is recomputed from its stored value and the
@@ -129,9 +130,12 @@ __device__ bool finalize(const TableDev& T, const VarLayout& V, uint32_t* __rest
     for (int q = tid; q < T.nChangedWords; q += kThreads) sm.scan[kChgBase + q] = 0;
     __syncthreads();
     CT_STAMP(15);
-    if (nh < 0 && sm.scan[kSlotScan] > 0) return false;
+    int st = sm.scan[kSlotStatus];
+    // With the filter beside the update, the failure (Algorithm 1 line 5) is
+    // decided here from the update's live count, read in the header round.
+    if (lastDomHere && st == CT_OK && sm.scan[kSlotLiveOut] == 0) st = CT_INFEASIBLE;
+    if (nh < 0 && st == CT_OK && sm.scan[kSlotScan] > 0) return false;
     nh = sm.scan[kSlotHard];
-    const int st = sm.scan[kSlotStatus];
     if (st == CT_OK && nh > 0) {
         uint32_t pruned = 0;
         for (int m = tid; m < nh; m += kThreads) {
@@ -291,7 +295,7 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     // values first: warp g starts at value (g - nseg) mod nwarps.
     const int pfirstE = (gwarp - T.nseg % nwarps + nwarps) % nwarps;
     int resE = 0;
-    if (kLocal && P.early && T.useResidues && pfirstE < T.R && lane == 0) resE = T.residue[pfirstE];
+    if (kLocal && P.early > 0 && T.useResidues && pfirstE < T.R && lane == 0) resE = T.residue[pfirstE];
 
     CT_STAMP(19);
     // plan (CTA 0 also snapshots lastDom into the levels saved since the last call)
@@ -347,12 +351,15 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     CT_STAMP(1);
     // Filter beside the update (Algorithm 3 on the chunks Algorithm 2 leaves,
     // each recomputed from the call's rows: chunk_after): for calls of at most
-    // U rows on positive local-plan tables with residues. The probes need no
+    // U rows on positive local-plan tables with residues, while at least half
+    // the chunks are live at entry (in a sparse state the probes beside the
+    // update would walk the index before the update, whose dying chunks cost
+    // windows: measured slower there). The probes need no
     // barrier after the update; the one barrier after them also decides the
     // failure (Algorithm 1 line 5) from the update's live count. Every CTA
     // takes the same decision (each computed the same plan).
-    const bool early = kLocal && P.early && ok && nrows > 0 && nrows <= U && !T.negative && !T.shard &&
-                       T.useResidues;
+    const bool early = kLocal && ok && nrows > 0 && nrows <= U && nrows <= P.early && !T.negative && !T.shard &&
+                       T.useResidues && 2 * P.prevLive >= T.W4;
     if (T.useResidues && gwarp < T.R && lane == 0 && !early)
         supRes0 = ld_sup(T.sup + (size_t)gwarp * T.W4 + res0);
 
@@ -564,18 +571,11 @@ ct_propagate_kernel(const __grid_constant__ TableDev T, uint32_t* __restrict__ d
     const uint64_t t3 = r2 == 2 ? gtimer() : 0ull;
     if (early) {
         // Algorithm 1 line 5 after the update, whose counts every CTA flushed
-        // before this barrier: the probes' results are dropped on a failure.
+        // before this barrier: the finalizing CTA decides it in its header
+        // round (finalize), the others return on a failure (or once the
+        // finalizing CTA has cleared the count, having needed no scan).
         if (r2 == 2 && tid == 0) C->t[2] = t3;
-        const int st1 = __ldcg(&C->status);
-        const uint32_t live1 = __ldcg(&C->live);
-        if (st1 != CT_OK || live1 == 0u) {
-            if (r2 == 2) {
-                if (tid == 0 && st1 == CT_OK) C->status = CT_INFEASIBLE;
-                __syncthreads();
-                finalize(T, V, domOut, sm, 0, 0ull, kLocal);
-            }
-            return;
-        }
+        if (r2 != 2 && (__ldcg(&C->status) != CT_OK || __ldcg(&C->live) == 0u)) return;
     }
     // The CTA that arrived last reads the hard-value counts with the counters
     // it publishes: with none left undecided (every value kept its support,

@@ -568,7 +568,7 @@ int ct_table_propagate_on(ct_table* ct, uint32_t* dom, const int32_t* domOffDev,
     P.prevLive = ct->live;
     P.spinLimit = kBarrierSpinLimit;
     P.maxSplit = ct->maxSplit;
-    P.early = ct->early ? 1 : 0;
+    P.early = ct->early ? 16 : 0;
     for (int i = 0; i < ct->arity && i < kParamArity; ++i) P.domOff[i] = domOffHost[i];
     if (domHost) {
         if (!ct->localPlan || ct->DW > kParamDomWords) {
