@@ -571,22 +571,20 @@ def _read_ceiling(C, torch, nbytes, flush, reps=7):
     """What one launch reaches reading `nbytes` once on this GPU: the library's
     streaming-read kernel (ct_read_ceiling: 128-bit loads, eight in flight per
     thread, four CTAs per SM) over a buffer of that size, L2 flushed before each
-    launch, CUDA events around it on the same stream (median). A launch this
+    launch, CUDA events recorded by the library right around the launch
+    (median), as for the propagation's own launch. A launch this
     short pays launch and ramp-up latency that a long copy amortises, so this is
     the bandwidth a one-call propagation of that many bytes could hope for."""
     n = max(16, (int(nbytes) + 15) // 16 * 16)
     x = torch.ones(n // 4, dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = []
     for _ in range(reps):
         flush.zero_()
         torch.cuda.synchronize()
-        e0.record(s)
-        C.check(C.ct_read_ceiling(x, n, s))
-        e1.record(s)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
+        st, t = C.ct_read_ceiling(x, n, s, timed=True)
+        C.check(st)
+        ms.append(t)
     del x
     return x_bytes_per_s(n, statistics.median(ms))
 

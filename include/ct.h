@@ -615,13 +615,16 @@ int ct_search_collect(ct_model* m, int64_t node_limit, int slots, int64_t max_sa
 
 /* ---------------------------------------------------------------- misc -- */
 /* ct_read_ceiling: measurement support, no counterpart in the paper. Launches
- * (asynchronously, on cuda_stream) one kernel that reads `bytes` of device
- * memory at dev_buf once, 128-bit loads not kept in L1, eight in flight per
- * thread, four CTAs of 256 threads per SM, and stores nothing the caller sees:
- * the bandwidth one launch of that size reaches, to set beside a propagation
- * moving as many bytes (time it with events on the same stream). dev_buf must
- * be 16-byte aligned and bytes a positive multiple of 16 (else CT_ERR_ARG). */
-int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream);
+ * on cuda_stream one kernel that reads `bytes` of device memory at dev_buf
+ * once, 128-bit loads not kept in L1, eight in flight per thread, four CTAs of
+ * 256 threads per SM, and stores nothing the caller sees: the bandwidth one
+ * launch of that size reaches, to set beside a propagation moving as many
+ * bytes. With ms_out (host, nullable) the call records CUDA events on the
+ * stream right before and after the launch, as ct_options.profile does for a
+ * propagation, waits for the second and writes the interval in ms; without
+ * it the call returns once the kernel is launched. dev_buf must be 16-byte
+ * aligned and bytes a positive multiple of 16 (else CT_ERR_ARG). */
+int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream, float* ms_out);
 const char* ct_last_error(void);
 const char* ct_status_string(int status);
 int ct_version(void);

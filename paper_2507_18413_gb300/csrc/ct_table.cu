@@ -51,13 +51,27 @@ extern "C" const char* ct_status_string(int s) {
 
 extern "C" int ct_version(void) { return 10000; }
 
-extern "C" int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream) {
+extern "C" int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_stream, float* ms_out) {
     if (!dev_buf || bytes <= 0 || (bytes & 15) || (reinterpret_cast<uintptr_t>(dev_buf) & 15)) {
         ct_set_error("ct_read_ceiling: a 16-byte aligned buffer and a positive multiple of 16 bytes");
         return CT_ERR_ARG;
     }
-    const cudaError_t e = ctk::launch_read_ceiling(static_cast<const uint4*>(dev_buf), (size_t)(bytes / 16),
-                                                   static_cast<cudaStream_t>(cuda_stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    if (ms_out) {
+        e = cudaEventCreate(&ev[0]);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    }
+    if (e == cudaSuccess) e = ctk::launch_read_ceiling(static_cast<const uint4*>(dev_buf), (size_t)(bytes / 16), s);
+    if (ms_out && e == cudaSuccess) {
+        e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms_out, ev[0], ev[1]);
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (e != cudaSuccess) {
         ct_set_error("ct_read_ceiling: %s", cudaGetErrorString(e));
         return CT_ERR_CUDA;

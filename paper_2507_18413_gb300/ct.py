@@ -123,7 +123,7 @@ _SIGS = {
     "ct_destroy": (ctypes.c_int, [_P]),
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
     "ct_arm_wait_timeout": (ctypes.c_int, [_P, ctypes.c_uint32]),
-    "ct_read_ceiling": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
+    "ct_read_ceiling": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float)]),
     "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
     "ct_sharded_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.c_int,
                                          _P, _P, ctypes.POINTER(_P)]),
@@ -378,10 +378,15 @@ def ct_propagate(h, dom_bits, changed_words: int = 0):
     return st, ch[:changed_words]
 
 
-def ct_read_ceiling(buf, nbytes, stream=None):
+def ct_read_ceiling(buf, nbytes, stream=None, timed=False):
     """One streaming read of nbytes of the device buffer (a torch tensor or a raw
-    device pointer), launched on stream; time it with events on that stream."""
-    return load().ct_read_ceiling(_dev_ptr(buf), int(nbytes), _stream_ptr(stream))
+    device pointer), launched on stream. Returns the status, and with timed the
+    CUDA-event interval around the launch in ms (the call then waits for it)."""
+    if not timed:
+        return load().ct_read_ceiling(_dev_ptr(buf), int(nbytes), _stream_ptr(stream), None)
+    ms = ctypes.c_float(0.0)
+    st = load().ct_read_ceiling(_dev_ptr(buf), int(nbytes), _stream_ptr(stream), ctypes.byref(ms))
+    return st, float(ms.value)
 
 
 def ct_arm_wait_timeout(h, polls):

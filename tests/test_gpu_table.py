@@ -516,6 +516,8 @@ def test_read_ceiling_entry_point():
     s = torch.cuda.current_stream()
     assert C.ct_read_ceiling(x, x.numel() * 4, s) == C.CT_OK
     assert C.ct_read_ceiling(x, 16, s) == C.CT_OK
+    st, ms = C.ct_read_ceiling(x, x.numel() * 4, s, timed=True)
+    assert st == C.CT_OK and 0.0 < ms < 1000.0
     torch.cuda.synchronize()
     assert C.ct_read_ceiling(x, 0, s) == C.CT_ERR_ARG
     assert C.ct_read_ceiling(x, 24, s) == C.CT_ERR_ARG
