@@ -613,6 +613,38 @@ int ct_model_lookahead(ct_model* m, int slots, float* labels_host);
 int ct_search_collect(ct_model* m, int64_t node_limit, int slots, int64_t max_samples, float* features_host,
                       float* labels_host, int64_t* samples_out);
 
+/* ------------------------------------------------------------ test hooks -- */
+/* For tests of the library itself (no counterpart in the paper), off by
+ * default; they cover the device buffers a table owns: those ct_create
+ * allocates, the trail and the level stack (not the buffers of models and
+ * batched searches, nor arenas of table copies). Process-wide settings; each
+ * returns CT_OK unless stated.
+ *
+ * ct_debug_guard_buffers: while on (1), tables created afterwards put 256
+ * bytes of guard before and after every such buffer, filled with 0xA5 (the
+ * buffers keep their 256-byte alignment); 0 switches it off for later tables.
+ * No kernel addresses a guard, so a changed guard byte means a write outside
+ * a buffer (compute-sanitizer being unavailable where this library runs).
+ *
+ * ct_debug_check_guards: waits for the device and writes to *changed_out how
+ * many guard bytes of ct's buffers differ from 0xA5 (0 for a table created
+ * without guards). poke > 0 first overwrites `poke` bytes of the first
+ * buffer's leading guard with zeros, by a host-side memset (a check of the
+ * check itself); 0 <= poke <= 256, else CT_ERR_ARG.
+ *
+ * ct_debug_fail_alloc: after n more device allocations of table buffers the
+ * next one fails as if the device were out of memory (the call that made it
+ * returns CT_ERR_OOM and releases what it took); one failure per arming;
+ * n < 0 disarms.
+ *
+ * ct_debug_device_bytes: bytes of device memory the table buffers hold now,
+ * over all tables, counted by the library's allocator (CT_ERR_ARG if
+ * bytes_out is null). */
+int ct_debug_guard_buffers(int on);
+int ct_debug_check_guards(ct_table* ct, int poke, int64_t* changed_out);
+int ct_debug_fail_alloc(int n);
+int ct_debug_device_bytes(int64_t* bytes_out);
+
 /* ---------------------------------------------------------------- misc -- */
 /* ct_read_ceiling: measurement support, no counterpart in the paper. Launches
  * on cuda_stream one kernel that reads `bytes` of device memory at dev_buf

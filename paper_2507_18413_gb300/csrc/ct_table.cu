@@ -7,7 +7,9 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ct_table.cuh"
@@ -82,11 +84,72 @@ extern "C" int ct_read_ceiling(const void* dev_buf, int64_t bytes, void* cuda_st
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// device buffers of tables: every buffer a table owns (ct_create's buffers,
+// the trail and the level stack) is allocated and freed here, with the test
+// hooks ct_debug_*: guard regions around each buffer, a countdown that makes
+// one allocation fail, and the bytes held, counted by the allocator itself
+// ---------------------------------------------------------------------------
+constexpr size_t kGuardBytes = 256;       // before and after a guarded buffer (keeps its 256-byte alignment)
+constexpr unsigned char kGuardFill = 0xA5;
+struct DevBuf {
+    size_t bytes;
+    bool guarded;
+};
+std::mutex g_bufMu;
+std::unordered_map<void*, DevBuf> g_bufs;  // buffer as the table sees it -> size
+int64_t g_bufBytes = 0;
+bool g_guardNew = false;                   // ct_debug_guard_buffers
+long long g_failAfter = -1;                // ct_debug_fail_alloc: allocations left before one fails
+
+cudaError_t table_malloc(void** p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_bufMu);
+    *p = nullptr;
+    if (g_failAfter >= 0) {
+        if (g_failAfter == 0) {
+            g_failAfter = -1;
+            return cudaErrorMemoryAllocation;
+        }
+        --g_failAfter;
+    }
+    const bool guarded = g_guardNew;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&base), bytes + (guarded ? 2 * kGuardBytes : 0));
+    if (e != cudaSuccess) return e;
+    if (guarded) {
+        e = cudaMemset(base, kGuardFill, kGuardBytes);
+        if (e == cudaSuccess) e = cudaMemset(base + kGuardBytes + bytes, kGuardFill, kGuardBytes);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the guards are set before any use
+        if (e != cudaSuccess) {
+            cudaFree(base);
+            return e;
+        }
+    }
+    void* user = base + (guarded ? kGuardBytes : 0);
+    g_bufs[user] = DevBuf{bytes, guarded};
+    g_bufBytes += (int64_t)bytes;
+    *p = user;
+    return cudaSuccess;
+}
+
+void table_free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_bufMu);
+    const auto it = g_bufs.find(p);
+    if (it == g_bufs.end()) {
+        cudaFree(p);
+        return;
+    }
+    g_bufBytes -= (int64_t)it->second.bytes;
+    cudaFree(static_cast<char*>(p) - (it->second.guarded ? kGuardBytes : 0));
+    g_bufs.erase(it);
+}
+
 template <typename T>
 int dalloc(ct_table* ct, T** p, size_t count) {
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     void* q = nullptr;
-    const cudaError_t e = cudaMalloc(&q, bytes);
+    const cudaError_t e = table_malloc(&q, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ct_set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
@@ -128,11 +191,11 @@ int ensure_trail(ct_table* ct, int64_t need) {
     if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
     int2* nk = nullptr;
     uint4* no = nullptr;
-    cudaError_t e = cudaMalloc(&nk, (size_t)cap * sizeof(int2));
-    if (e == cudaSuccess) e = cudaMalloc(&no, (size_t)cap * sizeof(uint4));
+    cudaError_t e = table_malloc(reinterpret_cast<void**>(&nk), (size_t)cap * sizeof(int2));
+    if (e == cudaSuccess) e = table_malloc(reinterpret_cast<void**>(&no), (size_t)cap * sizeof(uint4));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (nk) cudaFree(nk);
+        table_free(nk);
         ct_set_error("trail growth to %lld entries: %s", (long long)cap, cudaGetErrorString(e));
         return CT_ERR_OOM;
     }
@@ -145,8 +208,10 @@ int ensure_trail(ct_table* ct, int64_t need) {
     int32_t capi = (int32_t)cap;
     CT_CUDA(cudaMemcpyAsync(&ct->dev.ctrl->trail_cap, &capi, sizeof(int32_t), cudaMemcpyHostToDevice, ct->stream));
     CT_CUDA(cudaStreamSynchronize(ct->stream));
-    if (ct->dev.trailKey && !ct->trailInArena) cudaFree(ct->dev.trailKey);
-    if (ct->dev.trailOld && !ct->trailInArena) cudaFree(ct->dev.trailOld);
+    if (!ct->trailInArena) {
+        table_free(ct->dev.trailKey);
+        table_free(ct->dev.trailOld);
+    }
     ct->trailInArena = false;
     ct->deviceBytes += (cap - ct->trailCap) * (int64_t)(sizeof(int2) + sizeof(uint4));
     ct->dev.trailKey = nk;
@@ -161,11 +226,12 @@ int ensure_levels(ct_table* ct, int need) {
     const int cap = std::max(need, 2 * ct->levelCap);
     uint32_t* ns = nullptr;
     uint32_t* nd = nullptr;
-    cudaError_t e = cudaMalloc(&ns, (size_t)cap * std::max(ct->nseg, 1) * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&nd, (size_t)cap * std::max(ct->DW, 1) * sizeof(uint32_t));
+    cudaError_t e = table_malloc(reinterpret_cast<void**>(&ns), (size_t)cap * std::max(ct->nseg, 1) * sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = table_malloc(reinterpret_cast<void**>(&nd), (size_t)cap * std::max(ct->DW, 1) * sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (ns) cudaFree(ns);
+        table_free(ns);
         ct_set_error("level stack growth: %s", cudaGetErrorString(e));
         return CT_ERR_OOM;
     }
@@ -177,8 +243,10 @@ int ensure_levels(ct_table* ct, int need) {
                                 cudaMemcpyDeviceToDevice, ct->stream));
     }
     CT_CUDA(cudaStreamSynchronize(ct->stream));
-    if (ct->dev.levelSeg && !ct->levelsInArena) cudaFree(ct->dev.levelSeg);
-    if (ct->dev.levelDom && !ct->levelsInArena) cudaFree(ct->dev.levelDom);
+    if (!ct->levelsInArena) {
+        table_free(ct->dev.levelSeg);
+        table_free(ct->dev.levelDom);
+    }
     ct->levelsInArena = false;
     ct->deviceBytes += (int64_t)(cap - ct->levelCap) * (ct->nseg * 4 + ct->DW * 4);
     ct->dev.levelSeg = ns;
@@ -191,14 +259,14 @@ int ensure_levels(ct_table* ct, int need) {
 void free_table(ct_table* ct) {
     if (!ct) return;
     if (ct->stream) cudaStreamSynchronize(ct->stream);
-    for (void* p : ct->allocs) cudaFree(p);
+    for (void* p : ct->allocs) table_free(p);
     if (!ct->trailInArena) {
-        if (ct->dev.trailKey) cudaFree(ct->dev.trailKey);
-        if (ct->dev.trailOld) cudaFree(ct->dev.trailOld);
+        table_free(ct->dev.trailKey);
+        table_free(ct->dev.trailOld);
     }
     if (!ct->levelsInArena) {
-        if (ct->dev.levelSeg) cudaFree(ct->dev.levelSeg);
-        if (ct->dev.levelDom) cudaFree(ct->dev.levelDom);
+        table_free(ct->dev.levelSeg);
+        table_free(ct->dev.levelDom);
     }
     if (ct->h_status) cudaFreeHost(ct->h_status);
     if (ct->h_curr) cudaFreeHost(ct->h_curr);
@@ -965,6 +1033,67 @@ namespace {
 int create_impl(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples, int64_t t,
                 const ct_options* opt, void* cuda_stream, ct_table** out, bool negative);
 }  // namespace
+
+extern "C" int ct_debug_guard_buffers(int on) {
+    std::lock_guard<std::mutex> lk(g_bufMu);
+    g_guardNew = on != 0;
+    return CT_OK;
+}
+
+extern "C" int ct_debug_fail_alloc(int n) {
+    std::lock_guard<std::mutex> lk(g_bufMu);
+    g_failAfter = n < 0 ? -1 : n;
+    return CT_OK;
+}
+
+extern "C" int ct_debug_device_bytes(int64_t* bytes_out) {
+    if (!bytes_out) {
+        ct_set_error("ct_debug_device_bytes: bytes_out is null");
+        return CT_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_bufMu);
+    *bytes_out = g_bufBytes;
+    return CT_OK;
+}
+
+extern "C" int ct_debug_check_guards(ct_table* ct, int poke, int64_t* changed_out) {
+    if (!ct || !changed_out || poke < 0 || poke > (int)kGuardBytes) {
+        ct_set_error("ct_debug_check_guards: a table, changed_out, and 0 <= poke <= %d", (int)kGuardBytes);
+        return CT_ERR_ARG;
+    }
+    if (ct->stream) CT_CUDA(cudaStreamSynchronize(ct->stream));
+    std::vector<void*> bufs(ct->allocs.begin(), ct->allocs.end());
+    if (!ct->trailInArena) {
+        bufs.push_back(ct->dev.trailKey);
+        bufs.push_back(ct->dev.trailOld);
+    }
+    if (!ct->levelsInArena) {
+        bufs.push_back(ct->dev.levelSeg);
+        bufs.push_back(ct->dev.levelDom);
+    }
+    std::vector<std::pair<char*, size_t>> guarded;
+    {
+        std::lock_guard<std::mutex> lk(g_bufMu);
+        for (void* b : bufs) {
+            const auto it = b ? g_bufs.find(b) : g_bufs.end();
+            if (it != g_bufs.end() && it->second.guarded) guarded.emplace_back(static_cast<char*>(b), it->second.bytes);
+        }
+    }
+    if (poke > 0 && !guarded.empty())
+        CT_CUDA(cudaMemset(guarded[0].first - kGuardBytes, 0, (size_t)poke));  // from the host: no kernel writes it
+    CT_CUDA(cudaDeviceSynchronize());
+    int64_t changed = 0;
+    std::vector<unsigned char> h(kGuardBytes);
+    for (const auto& g : guarded) {
+        for (int side = 0; side < 2; ++side) {
+            const char* at = side == 0 ? g.first - kGuardBytes : g.first + g.second;
+            CT_CUDA(cudaMemcpy(h.data(), at, kGuardBytes, cudaMemcpyDeviceToHost));
+            for (unsigned char c : h) changed += c != kGuardFill;
+        }
+    }
+    *changed_out = changed;
+    return CT_OK;
+}
 
 extern "C" int ct_create(int arity, const int32_t* dom_lo, const int32_t* dom_size, const int32_t* tuples,
                          int64_t t, const ct_options* opt, void* cuda_stream, ct_table** out) {

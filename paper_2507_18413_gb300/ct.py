@@ -124,6 +124,10 @@ _SIGS = {
     "ct_propagate_noalloc": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int64, _P, _P, _P, _P, _U32P, _P]),
     "ct_arm_wait_timeout": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "ct_read_ceiling": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float)]),
+    "ct_debug_guard_buffers": (ctypes.c_int, [ctypes.c_int]),
+    "ct_debug_check_guards": (ctypes.c_int, [_P, ctypes.c_int, _I64P]),
+    "ct_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int]),
+    "ct_debug_device_bytes": (ctypes.c_int, [_I64P]),
     "ct_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _I64P]),
     "ct_sharded_create": (ctypes.c_int, [ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int64, ctypes.c_int,
                                          _P, _P, ctypes.POINTER(_P)]),
@@ -376,6 +380,29 @@ def ct_propagate(h, dom_bits, changed_words: int = 0):
     ch, pch = _u32_out(changed_words)
     st = load().ct_propagate(h, _dev_ptr(dom_bits), pch if changed_words else None)
     return st, ch[:changed_words]
+
+
+def ct_debug_guard_buffers(on):
+    """Test hook: tables created from now on guard their device buffers (on=1) or not."""
+    return load().ct_debug_guard_buffers(int(bool(on)))
+
+
+def ct_debug_check_guards(h, poke=0):
+    """Changed guard bytes of table h's buffers (poke > 0: corrupt that many first)."""
+    n = ctypes.c_int64(0)
+    st = load().ct_debug_check_guards(h, int(poke), ctypes.byref(n))
+    return st, int(n.value)
+
+
+def ct_debug_fail_alloc(n):
+    """Test hook: the table-buffer allocation after the next n fails (n < 0: disarm)."""
+    return load().ct_debug_fail_alloc(int(n))
+
+
+def ct_debug_device_bytes():
+    n = ctypes.c_int64(0)
+    st = load().ct_debug_device_bytes(ctypes.byref(n))
+    return st, int(n.value)
 
 
 def ct_read_ceiling(buf, nbytes, stream=None, timed=False):
