@@ -801,6 +801,9 @@ __device__ __forceinline__ bool wait_update_done(Ctrl* C, unsigned limit) {
             if (it > 64) __nanosleep(32);
         }
     }
+    // lane 0's acquire, then a warp barrier (which orders memory among the
+    // lanes): every lane's later loads see the released update
+    __syncwarp();
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
