@@ -109,3 +109,31 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[n]) == ctypes.sizeof(st), n
         for f, _ in st._fields_:
             assert int(out[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
+
+
+def test_host_side_test_hooks_without_a_device(lib):
+    """The test hooks' settings and argument checks touch no device: they run
+    (and reject bad arguments) on a host without a GPU."""
+    assert C.ct_debug_guard_buffers(1) == C.CT_OK
+    assert C.ct_debug_guard_buffers(0) == C.CT_OK
+    assert C.ct_debug_fail_alloc(3) == C.CT_OK
+    assert C.ct_debug_fail_alloc(-1) == C.CT_OK
+    st, n = C.ct_debug_device_bytes()
+    assert st == C.CT_OK and n >= 0
+    assert lib.ct_debug_device_bytes(None) == C.CT_ERR_ARG
+    assert lib.ct_debug_check_guards(None, 0, None) == C.CT_ERR_ARG
+    # the read ceiling checks its buffer and size before launching
+    assert C.ct_read_ceiling(0, 16) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(4096 + 4, 16) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(4096, 0) == C.CT_ERR_ARG
+    assert C.ct_read_ceiling(4096, 24) == C.CT_ERR_ARG
+    assert "16-byte" in C.last_error()
+
+
+def test_options_fields_reach_the_struct():
+    o = C.make_options(grid_blocks=7, no_residues=1, profile=1, host_fixpoint=1, copy_state=1, autotune=1, shard=1,
+                       no_split=1, no_early_filter=1)
+    assert (o.reserved0, o.grid_blocks, o.no_residues, o.profile, o.host_fixpoint, o.copy_state, o.autotune,
+            o.shard, o.no_split, o.no_early_filter) == (0, 7, 1, 1, 1, 1, 1, 1, 1, 1)
+    d = C.make_options()
+    assert all(getattr(d, f) == 0 for f, _ in d._fields_)
